@@ -1,0 +1,133 @@
+/*
+ * libnn — Nested Neumann (NN) iterative matrix inversion on one GB300 (sm_103a).
+ *
+ * C ABI. Every pointer argument is a plain address; sizes are element counts.
+ * "device" pointers must point to memory of the GPU that is current on the calling
+ * thread; "host" pointers to ordinary (pageable or pinned) host memory. The caller owns
+ * every buffer it passes, including the workspace; the library allocates no device
+ * memory of its own on any of these calls and keeps no pointer after a call returns.
+ * All work is ordered on the given CUDA stream (a cudaStream_t passed as void*; NULL is
+ * the legacy default stream). Calls that return results to the host (status, residual
+ * history) synchronise that stream before returning.
+ *
+ * Errors: every entry point returns an nn_status. Calls never abort the process, never
+ * print, and leave the CUDA context usable: a bad argument returns NN_ERR_ARG before any
+ * launch; a CUDA runtime failure returns NN_ERR_CUDA (cudaGetLastError() is cleared);
+ * a device-side wait that runs past its limit makes the kernel return early and the call
+ * returns NN_ERR_TIMEOUT.
+ *
+ * Notation (the paper's): W (here A) is the N x N matrix to invert, Theta the
+ * normalisation, X_k = phi^(k) Theta the iterate after k nests with X_0 = Theta, L the
+ * inception depth. One nest (Theorem, Eq. (nestedneumann), multiplied out on the right):
+ *     R_k = I - A X_k,    X_{k+1} = X_k (I + R_k (I + R_k (... (I + R_k)))),  L factors R_k,
+ * computed as T = R_k, then L-1 times T = R_k + R_k T, then X_{k+1} = X_k + X_k T.
+ * Stop test: s_k = ||R_k||_F / N (the paper's root-mean Frobenius error, Section II).
+ */
+#ifndef NN_H
+#define NN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+typedef enum nn_status {
+  NN_OK = 0,
+  NN_ERR_ARG = 1,           /* invalid argument (null pointer, bad size, depth < 1, ...) */
+  NN_ERR_DIVERGED = 2,      /* s_k non-finite, or s_k >= 1 and s_k > s_{k-1}              */
+  NN_ERR_NOT_CONVERGED = 3, /* tol > 0 and s_k >= tol after max_nests nests               */
+  NN_ERR_OOM_BUDGET = 4,    /* workspace too small for the request                         */
+  NN_ERR_TIMEOUT = 5,       /* a device-side wait ran past its limit                       */
+  NN_ERR_CUDA = 6,          /* CUDA runtime error                                          */
+  NN_ERR_UNSUPPORTED = 7    /* combination not implemented (e.g. no sm_103a device)         */
+} nn_status;
+
+/* ---- arithmetic of the dense nest chain -------------------------------------------- */
+typedef enum nn_dtype {
+  NN_F64 = 0,        /* every GEMM and epilogue in FP64 (CUDA cores)                           */
+  NN_F32 = 1,        /* every GEMM and epilogue in FP32 (CUDA cores)                           */
+  NN_MIXED_BF16 = 2  /* tcgen05 tensor-core GEMMs on BF16 operand pieces, FP32 accumulate in
+                        TMEM, FP32 master copy of X. Bulk nests use one BF16 piece per operand;
+                        refine nests evaluate R_k with three pieces (six products, FP32-level)
+                        and the Horner/update GEMMs with two pieces (three products).        */
+} nn_dtype;
+
+/* ---- starting matrix X_0 = Theta (Section II-A, Eq. (normalization), Appendix 1) --------- */
+typedef enum nn_pc {
+  NN_PC_PAN_SCHREIBER = 0, /* X_0 = A^T / (||A||_1 ||A||_inf)                                  */
+  NN_PC_SCALAR = 1,        /* X_0 = scalar * I                                                */
+  NN_PC_TRACE = 2,         /* X_0 = I / Tr(A)   (Theta_1 of Eq. (trace))                        */
+  NN_PC_JACOBI = 3         /* X_0 = scalar * diag(A)^-1 (scalar = 1 for plain Jacobi)          */
+} nn_pc;
+
+#define NN_MAX_HISTORY 65
+
+typedef struct nn_opts {
+  int depth;           /* inception depth L >= 1 (L = 1 Newton, L = 2 Chebyshev)                 */
+  double tol;          /* stop at the first k with s_k < tol; tol <= 0 runs exactly max_nests     */
+  int max_nests;       /* 0 .. NN_MAX_HISTORY-1                                                   */
+  int dtype;           /* nn_dtype                                                                */
+  double refine_below; /* NN_MIXED_BF16: switch to refine nests once s_k * sqrt(N) < refine_below;
+                          <= 0 selects the default 0.1. A stall (s_{k+1} > 0.5 s_k) also switches. */
+  int bulk_pieces;     /* NN_MIXED_BF16: BF16 pieces per operand in bulk residuals (1..3; 0 = 1)  */
+  int flags;           /* NN_FLAG_* bits                                                           */
+} nn_opts;
+
+/* nn_opts.flags: time every tensor-core GEMM launch with CUDA events on the call's stream
+ * (fills nn_result.tc_ms; costs two event records per GEMM). */
+#define NN_FLAG_TIME_KERNELS 1
+
+typedef struct nn_result {
+  int status;                      /* nn_status of the run                                         */
+  int nests;                       /* nests applied; the returned X is X_nests                     */
+  double residual;                 /* s_nests, the last residual measured                          */
+  double history[NN_MAX_HISTORY];  /* s_0 .. s_nests                                               */
+  int pieces[NN_MAX_HISTORY];      /* BF16 pieces used for residual k (0 for FP64/FP32 paths)      */
+  int gemms;                       /* GEMM launches issued                                         */
+  double flops;                    /* algorithmic FLOPs: 2 N^3 per GEMM (split passes not counted) */
+  double hw_flops;                 /* tensor-core FLOPs issued, split passes included              */
+  int launches;                    /* kernel launches issued by the call                           */
+  int tc_launches;                 /* tcgen05 GEMM launches                                        */
+  double tc_ms;                    /* summed CUDA-event time of those launches (NN_FLAG_TIME_KERNELS) */
+  double tc_flops;                 /* 2 Np^3 per BF16 product pass of those launches               */
+} nn_result;
+
+/* Bytes of device workspace nn_invert / nn_residual need for an N x N problem of `dtype`
+ * (256-byte aligned internally). Returns 0 for invalid arguments. */
+size_t nn_workspace_bytes(int64_t n, int dtype);
+
+/* X_0 for A (device, FP64, row-major N x N with leading dimension lda >= n) into X0 (device,
+ * FP64, row-major, leading dimension ldx >= n). kind is an nn_pc; `scalar` is the alpha of
+ * NN_PC_SCALAR and the damping of NN_PC_JACOBI. Needs nn_workspace_bytes(n, NN_F64) of
+ * workspace. Section II-A (Eq. (normalization), Eq. (trace)); Appendix 1 (matrix Theta). */
+int nn_init_precond(const double* A, int64_t n, int64_t lda, int kind, double scalar,
+                    double* X0, int64_t ldx, void* workspace, size_t ws_bytes, void* stream);
+
+/* Dense NN inversion (Algorithm 1, right-multiplied form). A, X0, X are device FP64
+ * row-major with leading dimensions lda, ldx0, ldx (>= n). X receives the last iterate
+ * X_nests (also on failure statuses, so the caller can inspect it). res (host) receives
+ * the run record. The call synchronises `stream` once per nest to read s_k. */
+int nn_invert(const double* A, int64_t n, int64_t lda, const double* X0, int64_t ldx0,
+              const nn_opts* opts, double* X, int64_t ldx, nn_result* res,
+              void* workspace, size_t ws_bytes, void* stream);
+
+/* Same as nn_invert with HOST buffers: A, X0 and X are host FP64 arrays (leading dimension
+ * n). The call copies A and X0 to the device, runs, and copies X back, all on `stream`.
+ * Needs nn_workspace_bytes_host(n, dtype) of device workspace. */
+size_t nn_workspace_bytes_host(int64_t n, int dtype);
+int nn_invert_host(const double* A_host, int64_t n, const double* X0_host, const nn_opts* opts,
+                   double* X_host, nn_result* res, void* workspace, size_t ws_bytes, void* stream);
+
+/* s = ||I - A X||_F / N for device FP64 A, X (row-major), written to *rms_frob (host).
+ * dtype NN_F64 evaluates in FP64; NN_F32 in FP32. Section II (error measure). */
+int nn_residual(const double* A, int64_t lda, const double* X, int64_t ldx, int64_t n, int dtype,
+                double* rms_frob, void* workspace, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NN_H */

@@ -1,0 +1,199 @@
+"""Thin Python binding of the libnn C ABI (``include/nn.h``).
+
+Argument marshalling only: every function here checks tensor placement, dtype and
+layout, turns tensors into pointers and calls the entry point of the same name in
+``lib/libnn.so``. There is no fallback: if the library is missing, every call raises.
+PyTorch provides device memory and streams; all arithmetic runs in the CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int64, c_size_t, c_void_p
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "lib", "libnn.so")
+
+NN_OK = 0
+NN_ERR_ARG = 1
+NN_ERR_DIVERGED = 2
+NN_ERR_NOT_CONVERGED = 3
+NN_ERR_OOM_BUDGET = 4
+NN_ERR_TIMEOUT = 5
+NN_ERR_CUDA = 6
+NN_ERR_UNSUPPORTED = 7
+STATUS_NAMES = {0: "ok", 1: "arg", 2: "diverged", 3: "not_converged", 4: "oom_budget", 5: "timeout",
+                6: "cuda", 7: "unsupported"}
+
+NN_F64, NN_F32, NN_MIXED_BF16 = 0, 1, 2
+DTYPES = {"f64": NN_F64, "f32": NN_F32, "mixed_bf16": NN_MIXED_BF16}
+NN_PC_PAN_SCHREIBER, NN_PC_SCALAR, NN_PC_TRACE, NN_PC_JACOBI = 0, 1, 2, 3
+PRECONDS = {"pan_schreiber": 0, "scalar": 1, "trace": 2, "jacobi": 3}
+NN_MAX_HISTORY = 65
+
+
+class NNOpts(ctypes.Structure):
+    _fields_ = [("depth", c_int), ("tol", c_double), ("max_nests", c_int), ("dtype", c_int),
+                ("refine_below", c_double), ("bulk_pieces", c_int), ("flags", c_int)]
+
+
+class NNResult(ctypes.Structure):
+    _fields_ = [("status", c_int), ("nests", c_int), ("residual", c_double),
+                ("history", c_double * NN_MAX_HISTORY), ("pieces", c_int * NN_MAX_HISTORY),
+                ("gemms", c_int), ("flops", c_double), ("hw_flops", c_double), ("launches", c_int),
+                ("tc_launches", c_int), ("tc_ms", c_double), ("tc_flops", c_double)]
+
+    def as_dict(self) -> dict:
+        k = self.nests
+        return {"status": self.status, "status_name": STATUS_NAMES.get(self.status, "?"), "nests": k,
+                "residual": self.residual, "history": [self.history[i] for i in range(k + 1)],
+                "pieces": [self.pieces[i] for i in range(k + 1)], "gemms": self.gemms,
+                "flops": self.flops, "hw_flops": self.hw_flops, "launches": self.launches,
+                "tc_launches": self.tc_launches, "tc_ms": self.tc_ms, "tc_flops": self.tc_flops}
+
+
+_LIB = None
+
+# Every symbol include/nn.h declares, with its ctypes signature.
+_SIGNATURES = {
+    "nn_workspace_bytes": (c_size_t, [c_int64, c_int]),
+    "nn_workspace_bytes_host": (c_size_t, [c_int64, c_int]),
+    "nn_init_precond": (c_int, [c_void_p, c_int64, c_int64, c_int, c_double, c_void_p, c_int64, c_void_p, c_size_t,
+                                c_void_p]),
+    "nn_invert": (c_int, [c_void_p, c_int64, c_int64, c_void_p, c_int64, POINTER(NNOpts), c_void_p, c_int64,
+                          POINTER(NNResult), c_void_p, c_size_t, c_void_p]),
+    "nn_invert_host": (c_int, [c_void_p, c_int64, c_void_p, POINTER(NNOpts), c_void_p, POINTER(NNResult), c_void_p,
+                               c_size_t, c_void_p]),
+    "nn_residual": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int, POINTER(c_double), c_void_p,
+                            c_size_t, c_void_p]),
+}
+
+
+def lib():
+    """Loads libnn.so (built by ``paper_2212_02406_gb300.build``); raises if it is absent."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libnn.so not built ({LIB_PATH}); run python -m paper_2212_02406_gb300.build")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = handle
+    return _LIB
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGNATURES)
+
+
+# ---- marshalling helpers ---------------------------------------------------------------
+
+def _stream_ptr(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _mat(t, name, dtype=None):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be 2-D row-major (stride(1) == 1)")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    return c_void_p(t.data_ptr()), t.stride(0)
+
+
+def _ws(workspace):
+    if workspace is None:
+        return c_void_p(0), 0
+    return c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
+
+
+NN_FLAG_TIME_KERNELS = 1
+
+
+def make_opts(depth=2, tol=1e-6, max_nests=64, dtype="f64", refine_below=0.0, bulk_pieces=1,
+              flags=0) -> NNOpts:
+    d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    return NNOpts(int(depth), float(tol), int(max_nests), d, float(refine_below), int(bulk_pieces), int(flags))
+
+
+def workspace(n: int, dtype="f64", host=False, device=None):
+    """Device workspace (a uint8 CUDA tensor) sized by nn_workspace_bytes[_host]."""
+    import torch
+
+    d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    nbytes = (lib().nn_workspace_bytes_host if host else lib().nn_workspace_bytes)(int(n), d)
+    if nbytes == 0:
+        raise ValueError("invalid size or dtype")
+    return torch.empty(int(nbytes), dtype=torch.uint8, device=device or "cuda")
+
+
+# ---- entry points (same names as the C ABI) -------------------------------------------
+
+def nn_workspace_bytes(n: int, dtype) -> int:
+    d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    return int(lib().nn_workspace_bytes(int(n), d))
+
+
+def nn_workspace_bytes_host(n: int, dtype) -> int:
+    d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    return int(lib().nn_workspace_bytes_host(int(n), d))
+
+
+def nn_init_precond(A, kind, scalar, X0, workspace, stream=None) -> int:
+    import torch
+
+    pa, lda = _mat(A, "A", torch.float64)
+    px, ldx = _mat(X0, "X0", torch.float64)
+    k = PRECONDS[kind] if isinstance(kind, str) else int(kind)
+    pw, nw = _ws(workspace)
+    return lib().nn_init_precond(pa, A.shape[0], lda, k, float(scalar), px, ldx, pw, nw, _stream_ptr(stream))
+
+
+def nn_invert(A, X0, opts: NNOpts, X, workspace, stream=None):
+    """Returns (status, result dict). X receives the last iterate."""
+    import torch
+
+    pa, lda = _mat(A, "A", torch.float64)
+    p0, ld0 = _mat(X0, "X0", torch.float64)
+    px, ldx = _mat(X, "X", torch.float64)
+    pw, nw = _ws(workspace)
+    res = NNResult()
+    st = lib().nn_invert(pa, A.shape[0], lda, p0, ld0, ctypes.byref(opts), px, ldx, ctypes.byref(res), pw, nw,
+                         _stream_ptr(stream))
+    return st, res.as_dict()
+
+
+def nn_invert_host(A, X0, opts: NNOpts, X, workspace, stream=None):
+    """Host-buffer variant: A, X0, X are C-contiguous float64 NumPy arrays (X is written)."""
+    import numpy as np
+
+    for name, arr in (("A", A), ("X0", X0), ("X", X)):
+        if not (isinstance(arr, np.ndarray) and arr.dtype == np.float64 and arr.flags.c_contiguous):
+            raise TypeError(f"{name} must be a C-contiguous float64 ndarray")
+    pw, nw = _ws(workspace)
+    res = NNResult()
+    st = lib().nn_invert_host(c_void_p(A.ctypes.data), A.shape[0], c_void_p(X0.ctypes.data), ctypes.byref(opts),
+                              c_void_p(X.ctypes.data), ctypes.byref(res), pw, nw, _stream_ptr(stream))
+    return st, res.as_dict()
+
+
+def nn_residual(A, X, dtype, workspace, stream=None):
+    """Returns (status, ||I - A X||_F / N)."""
+    import torch
+
+    pa, lda = _mat(A, "A", torch.float64)
+    px, ldx = _mat(X, "X", torch.float64)
+    d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    pw, nw = _ws(workspace)
+    out = c_double(0.0)
+    st = lib().nn_residual(pa, lda, px, ldx, A.shape[0], d, ctypes.byref(out), pw, nw, _stream_ptr(stream))
+    return st, out.value

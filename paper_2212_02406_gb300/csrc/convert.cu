@@ -1,0 +1,213 @@
+// O(N^2) kernels around the nest chain: precision splitting into BF16 pieces (row-major
+// and transposed), FP32/FP64 conversions, the starting matrix X_0 (preconditioners of
+// Section II-A and Appendix 1) and the deterministic reduction of sum(R_ij^2) partials.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace nn {
+
+namespace {
+
+constexpr int TILE = 32;
+constexpr int ROWS = 8;  // 32 x 8 threads per 32 x 32 tile
+
+// BF16 pieces of a value: p0 = bf16(v), p1 = bf16(v - p0), p2 = bf16(v - p0 - p1), with the
+// remainders formed in FP64 (exact for these magnitudes).
+__device__ __forceinline__ void pieces3(double v, __nv_bfloat16 (&p)[3]) {
+  double r = v;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    p[i] = __double2bfloat16(r);
+    r -= static_cast<double>(__bfloat162float(p[i]));
+  }
+}
+
+struct PiecePtrs {
+  __nv_bfloat16* p[3];
+};
+
+__global__ void split_kernel(const double* __restrict__ src, int64_t lds, int n, int np, float* __restrict__ f32,
+                             PiecePtrs row, int n_row, PiecePtrs col, int n_col) {
+  __shared__ __nv_bfloat16 tile[3][TILE][TILE + 2];
+  const int i0 = blockIdx.y * TILE, j0 = blockIdx.x * TILE;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < TILE; r += ROWS) {
+    const int i = i0 + r, j = j0 + tx;
+    double v = (i < n && j < n) ? src[int64_t(i) * lds + j] : 0.0;
+    const int64_t off = int64_t(i) * np + j;
+    if (f32) f32[off] = static_cast<float>(v);
+    __nv_bfloat16 pc[3];
+    pieces3(v, pc);
+    for (int q = 0; q < n_row; ++q) row.p[q][off] = pc[q];
+    for (int q = 0; q < n_col; ++q) tile[q][r][tx] = pc[q];
+  }
+  if (n_col > 0) {
+    __syncthreads();
+    for (int r = ty; r < TILE; r += ROWS) {
+      // transposed: output row (j0 + r), column (i0 + tx)
+      const int64_t off = int64_t(j0 + r) * np + (i0 + tx);
+      for (int q = 0; q < n_col; ++q) col.p[q][off] = tile[q][tx][r];
+    }
+  }
+}
+
+template <typename S, typename D>
+__global__ void convert_kernel(const S* __restrict__ src, int64_t lds, int n, D* __restrict__ dst, int64_t ldd) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (i < n && j < n) dst[int64_t(i) * ldd + j] = static_cast<D>(src[int64_t(i) * lds + j]);
+}
+
+__global__ void reduce_rms_kernel(const double* __restrict__ partial, int count, double scale, double* out) {
+  __shared__ double buf[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < count; i += 256) s += partial[i];
+  buf[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) buf[threadIdx.x] += buf[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sqrt(buf[0]) * scale;
+}
+
+// Non-negative doubles order like their bit patterns, so max() can use the 64-bit integer atomic.
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+// ||A||_inf: one warp per row.
+__global__ void row_abs_max_kernel(const double* __restrict__ A, int64_t lda, int n, double* out) {
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s += fabs(A[int64_t(row) * lda + j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) atomic_max_nonneg(out, s);
+}
+
+// ||A||_1: one thread per column (coalesced across the warp).
+__global__ void col_abs_max_kernel(const double* __restrict__ A, int64_t lda, int n, double* out) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= n) return;
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += fabs(A[int64_t(i) * lda + col]);
+  atomic_max_nonneg(out, s);
+}
+
+__global__ void trace_kernel(const double* __restrict__ A, int64_t lda, int n, double* out) {
+  __shared__ double buf[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += A[int64_t(i) * lda + i];
+  buf[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) buf[threadIdx.x] += buf[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = buf[0];
+}
+
+// X0 = A^T / (||A||_1 ||A||_inf), tiled transpose.
+__global__ void pan_schreiber_kernel(const double* __restrict__ A, int64_t lda, int n, const double* norms,
+                                     double* __restrict__ X, int64_t ldx) {
+  __shared__ double tile[TILE][TILE + 1];
+  const double c = 1.0 / (norms[0] * norms[1]);
+  const int i0 = blockIdx.y * TILE, j0 = blockIdx.x * TILE;
+  for (int r = threadIdx.y; r < TILE; r += ROWS) {
+    const int i = i0 + r, j = j0 + threadIdx.x;
+    tile[r][threadIdx.x] = (i < n && j < n) ? A[int64_t(i) * lda + j] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < TILE; r += ROWS) {
+    const int i = j0 + r, j = i0 + threadIdx.x;  // X[i][j] = A[j][i] * c
+    if (i < n && j < n) X[int64_t(i) * ldx + j] = tile[threadIdx.x][r] * c;
+  }
+}
+
+// Diagonal starting matrices: kind SCALAR (value), TRACE (1 / *dev), JACOBI (value / A_ii).
+__global__ void fill_diag_kernel(const double* __restrict__ A, int64_t lda, int n, int kind, double value,
+                                 const double* dev, double* __restrict__ X, int64_t ldx) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (i >= n || j >= n) return;
+  double v = 0.0;
+  if (i == j) {
+    if (kind == NN_PC_SCALAR)
+      v = value;
+    else if (kind == NN_PC_TRACE)
+      v = 1.0 / dev[0];
+    else
+      v = value / A[int64_t(i) * lda + i];
+  }
+  X[int64_t(i) * ldx + j] = v;
+}
+
+}  // namespace
+
+int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
+                 __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col) {
+  if (np % TILE != 0 || n > np || n_row < 0 || n_row > 3 || n_col < 0 || n_col > 3) return NN_ERR_ARG;
+  PiecePtrs r{}, c{};
+  for (int q = 0; q < n_row; ++q) r.p[q] = row_pieces[q];
+  for (int q = 0; q < n_col; ++q) c.p[q] = col_pieces[q];
+  dim3 grid(np / TILE, np / TILE), block(TILE, ROWS);
+  split_kernel<<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col);
+  NN_CUDA_TRY(cudaGetLastError());
+  return NN_OK;
+}
+
+template <typename S, typename D>
+static int convert(cudaStream_t st, const S* src, int64_t lds, int n, D* dst, int64_t ldd) {
+  if (n <= 0) return NN_OK;
+  dim3 grid((n + 255) / 256, n), block(256);
+  convert_kernel<S, D><<<grid, block, 0, st>>>(src, lds, n, dst, ldd);
+  NN_CUDA_TRY(cudaGetLastError());
+  return NN_OK;
+}
+
+int f32_to_f64(cudaStream_t st, const float* src, int64_t lds, int n, double* dst, int64_t ldd) {
+  return convert(st, src, lds, n, dst, ldd);
+}
+int copy_f64(cudaStream_t st, const double* src, int64_t lds, int n, double* dst, int64_t ldd) {
+  return convert(st, src, lds, n, dst, ldd);
+}
+int f64_to_f32(cudaStream_t st, const double* src, int64_t lds, int n, float* dst, int64_t ldd) {
+  return convert(st, src, lds, n, dst, ldd);
+}
+
+int reduce_rms(cudaStream_t st, const double* partial, int count, double scale, double* out) {
+  reduce_rms_kernel<<<1, 256, 0, st>>>(partial, count, scale, out);
+  NN_CUDA_TRY(cudaGetLastError());
+  return NN_OK;
+}
+
+int precond_fill(cudaStream_t st, const double* A, int64_t lda, int n, int kind, double scalar, double* X0,
+                 int64_t ldx, double* scratch) {
+  if (n <= 0) return NN_ERR_ARG;
+  if (kind == NN_PC_PAN_SCHREIBER) {
+    NN_CUDA_TRY(cudaMemsetAsync(scratch, 0, 2 * sizeof(double), st));
+    col_abs_max_kernel<<<(n + 255) / 256, 256, 0, st>>>(A, lda, n, scratch + 0);
+    NN_CUDA_TRY(cudaGetLastError());
+    row_abs_max_kernel<<<(n + 7) / 8, 256, 0, st>>>(A, lda, n, scratch + 1);
+    NN_CUDA_TRY(cudaGetLastError());
+    dim3 grid((n + TILE - 1) / TILE, (n + TILE - 1) / TILE), block(TILE, ROWS);
+    pan_schreiber_kernel<<<grid, block, 0, st>>>(A, lda, n, scratch, X0, ldx);
+    NN_CUDA_TRY(cudaGetLastError());
+    return NN_OK;
+  }
+  if (kind == NN_PC_TRACE) {
+    trace_kernel<<<1, 256, 0, st>>>(A, lda, n, scratch + 2);
+    NN_CUDA_TRY(cudaGetLastError());
+  } else if (kind != NN_PC_SCALAR && kind != NN_PC_JACOBI) {
+    return NN_ERR_ARG;
+  }
+  dim3 grid((n + 255) / 256, n), block(256);
+  fill_diag_kernel<<<grid, block, 0, st>>>(A, lda, n, kind, scalar, scratch + 2, X0, ldx);
+  NN_CUDA_TRY(cudaGetLastError());
+  return NN_OK;
+}
+
+}  // namespace nn

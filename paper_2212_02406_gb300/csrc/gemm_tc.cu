@@ -1,0 +1,408 @@
+// tcgen05 / TMEM tensor-core GEMM for the NN nest chain on sm_103a.
+//
+// One persistent CTA per SM, 6 warps, warp-specialised:
+//   warp 0      TMA producer: 128x64 tile of A and 256x64 tile of B^T per stage (SWIZZLE_128B),
+//               4-stage ring guarded by full/empty mbarriers;
+//   warp 1      allocates 512 TMEM columns, one elected thread issues tcgen05.mma
+//               (M=128, N=256, K=16, BF16 x BF16 -> FP32) into one of two 256-column
+//               accumulators, and commits to the empty / accumulator-full barriers;
+//   warps 2-5   epilogue: tcgen05.ld of the accumulator (each warp owns its 32-lane
+//               quarter), the fused NN element-wise step (I - C, D + C), FP32 and BF16
+//               piece stores (row-major and transposed), and sum(C^2) partials.
+// The two accumulators let the epilogue of tile i overlap the main loop of tile i+1.
+//
+// "Segments" chain several (A_s, B_s) operand pairs into the same accumulator; the split
+// precisions of the mixed path (hi/lo BF16 pieces) use them, smallest products first.
+//
+// Every mbarrier wait is bounded (about 1 s, %globaltimer); a wait past the limit sets
+// an error word and makes every role leave its loop, so the kernel always returns and
+// frees its TMEM.
+#include <cudaTypedefs.h>
+#include <cuda.h>
+
+#include <mutex>
+#include <string.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace nn {
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int BK = 64;  // 64 BF16 = 128 bytes = one SWIZZLE_128B row
+constexpr int STAGES = 4;
+constexpr int A_TILE = BM * BK * 2;            // 16 KB
+constexpr int B_TILE = BN * BK * 2;            // 32 KB
+constexpr int STAGE_BYTES = A_TILE + B_TILE;   // 48 KB
+constexpr int THREADS = 192;
+constexpr int TMEM_COLS = 512;                 // two 128x256 FP32 accumulators
+constexpr int CTRL_BYTES = 256;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + CTRL_BYTES + 1024;
+constexpr int GROUP_M = 16;                    // tile raster: bands of 16 row tiles
+
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A BF16 (bits 7-9 = 1),
+// B BF16 (bits 10-12 = 1), both K-major (bits 15, 16 = 0), N>>3 at bit 17, M>>4 at bit 24.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+
+struct Params {
+  CUtensorMap map_a[kTcMaxSeg];
+  CUtensorMap map_b[kTcMaxSeg];
+  int nseg;
+  int np;
+  int tiles_m, tiles_n;
+  int n_id;
+  int mode;
+  const float* add;
+  float* out_f32;
+  __nv_bfloat16* row_pieces[3];
+  int n_row;
+  __nv_bfloat16* col_pieces[3];
+  int n_col;
+  double* partial;
+  int* err;
+};
+
+// Shared-memory matrix descriptor for a K-major tile written by TMA with SWIZZLE_128B:
+// rows of 128 bytes, 8-row swizzle atoms of 1024 bytes stacked at a 1024-byte stride (SBO).
+// Bits: start>>4 [0,14), LBO>>4 [16,30) (unused for this layout), SBO>>4 [32,46),
+// descriptor version 1 at bit 46, layout SWIZZLE_128B (2) at bits [61,64).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr & 0x3FFFFu) >> 4);
+  d |= uint64_t(1) << 16;
+  d |= uint64_t(1024 >> 4) << 32;
+  d |= uint64_t(1) << 46;
+  d |= uint64_t(2) << 61;
+  return d;
+}
+
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
+  const int per_group = GROUP_M * tiles_n;
+  const int g = t / per_group;
+  const int first_m = g * GROUP_M;
+  const int gm = min(GROUP_M, tiles_m - first_m);
+  const int r = t - g * per_group;
+  tm = first_m + r % gm;
+  tn = r / gm;
+}
+
+__device__ __forceinline__ void store_pieces_row(__nv_bfloat16* const* pieces, int n_pieces, int64_t off,
+                                                 const float (&v)[32]) {
+  float rem[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) rem[j] = v[j];
+  for (int p = 0; p < n_pieces; ++p) {
+    uint32_t packed[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      __nv_bfloat16 lo = __float2bfloat16_rn(rem[2 * j]);
+      __nv_bfloat16 hi = __float2bfloat16_rn(rem[2 * j + 1]);
+      rem[2 * j] -= __bfloat162float(lo);
+      rem[2 * j + 1] -= __bfloat162float(hi);
+      packed[j] = uint32_t(__bfloat16_as_ushort(lo)) | (uint32_t(__bfloat16_as_ushort(hi)) << 16);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(pieces[p] + off);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+  }
+}
+
+__global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_addr = smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
+  uint8_t* tiles = smem;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  double* red = reinterpret_cast<double*>(smem + STAGES * STAGE_BYTES + 128);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 0 && lane == 0) {
+    for (int s = 0; s < p.nseg; ++s) {
+      tma_prefetch_desc(&p.map_a[s]);
+      tma_prefetch_desc(&p.map_b[s]);
+    }
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int num_tiles = p.tiles_m * p.tiles_n;
+  const int kblocks = p.np / BK;
+  const int total_k = p.nseg * kblocks;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int t = blockIdx.x; t < num_tiles && !*abort_flag; t += gridDim.x) {
+        int tm, tn;
+        tile_coords(t, p.tiles_m, p.tiles_n, tm, tn);
+        for (int it = 0; it < total_k; ++it) {
+          const int seg = it / kblocks;
+          const int kb = it - seg * kblocks;
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.err)) break;
+          uint8_t* sa = tiles + stage * STAGE_BYTES;
+          uint8_t* sb = sa + A_TILE;
+          mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
+          tma_load_2d(sa, &p.map_a[seg], kb * BK, tm * BM, &full[stage]);
+          tma_load_2d(sb, &p.map_b[seg], kb * BK, tn * BN, &full[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int local = 0;
+      for (int t = blockIdx.x; t < num_tiles && !*abort_flag; t += gridDim.x, ++local) {
+        const int acc = local & 1;
+        const uint32_t acc_phase = (local >> 1) & 1;
+        if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1u, abort_flag, p.err)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + uint32_t(acc * BN);
+        bool ok = true;
+        for (int it = 0; it < total_k; ++it) {
+          if (!mbar_wait(&full[stage], phase, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(tiles + stage * STAGE_BYTES);
+          const uint64_t adesc = sw128_desc(sa);
+          const uint64_t bdesc = sw128_desc(sa + A_TILE);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            // +32 bytes along K inside the 128-byte swizzled row = +2 in the address field
+            tc_mma_bf16(d_tmem, adesc + uint64_t(2 * kk), bdesc + uint64_t(2 * kk), IDESC,
+                        (it > 0 || kk > 0) ? 1u : 0u);
+          }
+          tc_commit(&empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        tc_commit(&acc_full[acc]);
+      }
+      // Wait for every MMA this thread issued before TMEM can be released.
+      tc_commit(drain);
+      volatile int no_abort = 0;
+      mbar_wait(drain, 0, &no_abort, p.err);
+    }
+  } else {
+    // Epilogue warps 2..5; warp w reads TMEM lanes 32*(w%4) .. +31.
+    const int q = warp & 3;
+    const int row_in_tile = q * 32 + lane;
+    const int64_t ld = p.np;
+    double ss = 0.0;
+    int local = 0;
+    for (int t = blockIdx.x; t < num_tiles; t += gridDim.x, ++local) {
+      const int acc = local & 1;
+      const uint32_t acc_phase = (local >> 1) & 1;
+      if (!mbar_wait(&acc_full[acc], acc_phase, abort_flag, p.err)) break;
+      tc_fence_after();
+      int tm, tn;
+      tile_coords(t, p.tiles_m, p.tiles_n, tm, tn);
+      const int gr = tm * BM + row_in_tile;
+      for (int c = 0; c < BN / 32; ++c) {
+        const int gc0 = tn * BN + c * 32;
+        if (gc0 >= p.np) break;  // warp-uniform
+        uint32_t raw[32];
+        tmem_ld_32x32b_x32(tmem_base + uint32_t(acc * BN + c * 32) + (uint32_t(q * 32) << 16), raw);
+        tmem_ld_wait();
+        float v[32];
+        const int64_t off = int64_t(gr) * ld + gc0;
+        if (p.mode == EPI_ADD) {
+          const float4* src = reinterpret_cast<const float4*>(p.add + off);
+#pragma unroll
+          for (int j4 = 0; j4 < 8; ++j4) {
+            float4 a4 = src[j4];
+            v[4 * j4 + 0] = a4.x + __uint_as_float(raw[4 * j4 + 0]);
+            v[4 * j4 + 1] = a4.y + __uint_as_float(raw[4 * j4 + 1]);
+            v[4 * j4 + 2] = a4.z + __uint_as_float(raw[4 * j4 + 2]);
+            v[4 * j4 + 3] = a4.w + __uint_as_float(raw[4 * j4 + 3]);
+          }
+        } else if (p.mode == EPI_RESIDUAL) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int gc = gc0 + j;
+            v[j] = ((gr == gc && gr < p.n_id) ? 1.0f : 0.0f) - __uint_as_float(raw[j]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(raw[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) ss = fma(double(v[j]), double(v[j]), ss);
+        if (p.out_f32 != nullptr) {
+          float4* dst = reinterpret_cast<float4*>(p.out_f32 + off);
+#pragma unroll
+          for (int j4 = 0; j4 < 8; ++j4) dst[j4] = make_float4(v[4 * j4], v[4 * j4 + 1], v[4 * j4 + 2], v[4 * j4 + 3]);
+        }
+        if (p.n_row > 0) store_pieces_row(p.row_pieces, p.n_row, off, v);
+        if (p.n_col > 0) {
+          float rem[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) rem[j] = v[j];
+          for (int pc = 0; pc < p.n_col; ++pc) {
+            __nv_bfloat16* dst = p.col_pieces[pc] + gr;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              __nv_bfloat16 b = __float2bfloat16_rn(rem[j]);
+              rem[j] -= __bfloat162float(b);
+              dst[int64_t(gc0 + j) * ld] = b;  // lanes write consecutive rows: 64-byte runs
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[acc]);
+    }
+    // Deterministic per-CTA sum of squares over the four epilogue warps.
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+    if (lane == 0) red[q] = ss;
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (warp == 2 && lane == 0 && p.partial != nullptr) p.partial[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem_base, TMEM_COLS);
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------------------
+// Host side.
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+int g_sms = 0;
+bool g_tc_ok = false;
+std::once_flag g_once;
+
+void init_once() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return;
+  g_sms = prop.multiProcessorCount;
+  // sm_103 only: this kernel is compiled for sm_103a.
+  if (prop.major != 10 || prop.minor != 3) return;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || fn == nullptr) {
+    (void)cudaGetLastError();
+    return;
+  }
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  if (cudaFuncSetAttribute(tc::gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES) !=
+      cudaSuccess) {
+    (void)cudaGetLastError();
+    return;
+  }
+  g_tc_ok = true;
+}
+
+bool encode_bf16_2d(CUtensorMap* map, const void* ptr, int np, int box_rows) {
+  cuuint64_t dims[2] = {cuuint64_t(np), cuuint64_t(np)};
+  cuuint64_t strides[1] = {cuuint64_t(np) * 2};
+  cuuint32_t box[2] = {cuuint32_t(tc::BK), cuuint32_t(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tc_supported() {
+  std::call_once(g_once, init_once);
+  return g_tc_ok;
+}
+
+int gemm_tc_max_grid() {
+  std::call_once(g_once, init_once);
+  return g_sms > 0 ? g_sms : 1;
+}
+
+int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
+  if (!tc_supported()) return NN_ERR_UNSUPPORTED;
+  if (a.np <= 0 || a.np % 128 != 0 || a.nseg < 1 || a.nseg > kTcMaxSeg || a.n_row < 0 || a.n_row > 3 ||
+      a.n_col < 0 || a.n_col > 3 || a.err == nullptr)
+    return NN_ERR_ARG;
+  if (a.mode == EPI_ADD && a.add == nullptr) return NN_ERR_ARG;
+  tc::Params p;
+  memset(&p, 0, sizeof(p));
+  for (int s = 0; s < a.nseg; ++s) {
+    if (a.a_seg[s] == nullptr || a.b_seg[s] == nullptr) return NN_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(a.a_seg[s]) & 15) || (reinterpret_cast<uintptr_t>(a.b_seg[s]) & 15))
+      return NN_ERR_ARG;
+    if (!encode_bf16_2d(&p.map_a[s], a.a_seg[s], a.np, tc::BM)) return NN_ERR_CUDA;
+    if (!encode_bf16_2d(&p.map_b[s], a.b_seg[s], a.np, tc::BN)) return NN_ERR_CUDA;
+  }
+  for (int i = 0; i < a.n_row; ++i)
+    if (a.row_pieces[i] == nullptr) return NN_ERR_ARG;
+  for (int i = 0; i < a.n_col; ++i)
+    if (a.col_pieces[i] == nullptr) return NN_ERR_ARG;
+  p.nseg = a.nseg;
+  p.np = a.np;
+  p.tiles_m = a.np / tc::BM;
+  p.tiles_n = (a.np + tc::BN - 1) / tc::BN;
+  p.n_id = a.n_id;
+  p.mode = a.mode;
+  p.add = a.add;
+  p.out_f32 = a.out_f32;
+  for (int i = 0; i < 3; ++i) {
+    p.row_pieces[i] = a.row_pieces[i];
+    p.col_pieces[i] = a.col_pieces[i];
+  }
+  p.n_row = a.n_row;
+  p.n_col = a.n_col;
+  p.partial = a.partial;
+  p.err = a.err;
+  const int tiles = p.tiles_m * p.tiles_n;
+  const int grid = tiles < g_sms ? tiles : g_sms;
+  tc::gemm_tc_kernel<<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(p);
+  NN_CUDA_TRY(cudaGetLastError());
+  if (grid_used) *grid_used = grid;
+  return NN_OK;
+}
+
+}  // namespace nn

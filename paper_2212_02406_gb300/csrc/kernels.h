@@ -1,0 +1,68 @@
+// Internal launchers shared between the libnn translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace nn {
+
+// Epilogue modes of the GEMM kernels.
+enum : int {
+  EPI_COPY = 0,      // C = A B
+  EPI_RESIDUAL = 1,  // C = I_{n_id} - A B
+  EPI_ADD = 2        // C = D + A B
+};
+
+// ---- CUDA-core GEMM (gemm_simt.cu) ---------------------------------------------------
+template <typename T>
+int gemm_simt(cudaStream_t st, int M, int N, int K, const T* A, int64_t lda, const T* B, int64_t ldb, T* C,
+              int64_t ldc, int mode, const T* D, int64_t ldd, int n_id, double* partial);
+template <typename T>
+int gemm_simt_partials(int M, int N);
+
+// ---- tcgen05 GEMM (gemm_tc.cu) --------------------------------------------------------
+// C(Np x Np) = sum over segments s of A_s (Np x Np, row-major BF16) * B_s^T, where B_s is
+// stored row-major as the TRANSPOSE of the right operand (i.e. each B_s row is one
+// column of the right factor, K contiguous). Np must be a multiple of 128.
+// Epilogue per element (mode, I restricted to < n_id, addend `add` FP32 row-major ld=Np):
+// writes out_f32 (row-major, nullable), `n_row` BF16 pieces row-major and `n_col` BF16
+// pieces transposed (column-major = row-major of C^T); partial[cta] = sum C_ij^2 if given.
+constexpr int kTcMaxSeg = 6;
+struct TcGemmArgs {
+  int np = 0;
+  int n_id = 0;
+  int nseg = 0;
+  const __nv_bfloat16* a_seg[kTcMaxSeg] = {};
+  const __nv_bfloat16* b_seg[kTcMaxSeg] = {};
+  int mode = EPI_COPY;
+  const float* add = nullptr;
+  float* out_f32 = nullptr;
+  __nv_bfloat16* row_pieces[3] = {};
+  int n_row = 0;
+  __nv_bfloat16* col_pieces[3] = {};
+  int n_col = 0;
+  double* partial = nullptr;
+  int* err = nullptr;
+};
+int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used);
+int gemm_tc_max_grid();
+bool tc_supported();
+
+// ---- conversion / preconditioner / reduction kernels (convert.cu) -----------------------
+// Splits an n x n FP64 matrix (leading dim lds) into an Np-padded FP32 copy and BF16
+// pieces (row-major and/or transposed). Any output may be null. Padding is zero.
+int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
+                 __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col);
+// dst (FP64, ldd) = src (FP32, lds), n x n.
+int f32_to_f64(cudaStream_t st, const float* src, int64_t lds, int n, double* dst, int64_t ldd);
+// dst (T2, ldd) = src (T1, lds), n x n.
+int copy_f64(cudaStream_t st, const double* src, int64_t lds, int n, double* dst, int64_t ldd);
+int f64_to_f32(cudaStream_t st, const double* src, int64_t lds, int n, float* dst, int64_t ldd);
+// out[0] = sqrt(sum partial[0..count)) * scale, fixed summation order.
+int reduce_rms(cudaStream_t st, const double* partial, int count, double scale, double* out);
+// Preconditioners: write X0 (n x n FP64, ldx). scratch holds >= 4 doubles.
+int precond_fill(cudaStream_t st, const double* A, int64_t lda, int n, int kind, double scalar, double* X0,
+                 int64_t ldx, double* scratch);
+
+}  // namespace nn

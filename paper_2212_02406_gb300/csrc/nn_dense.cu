@@ -1,0 +1,524 @@
+// C ABI of the dense Nested Neumann path: workspace sizing, X_0, the nest loop on the
+// host (one stream, one synchronisation per nest to read s_k), and the residual call.
+//
+// Nest k (Theorem, Eq. (nestedneumann) multiplied out on the right; Algorithm 1):
+//   R   = I - A X_k                       residual GEMM (+ sum R^2 partials)
+//   T   = R;  L-1 times  T = R + R T      Horner GEMMs  (T = R + R^2 + ... + R^L)
+//   X_{k+1} = X_k + X_k T                 update GEMM   (= X_k (I + R (I + ... (I + R))))
+// The stop test rides on the residual GEMM of the next nest (s_k = ||R||_F / N), so k nests
+// cost (L+1) k + 1 GEMMs and the returned X is the iterate whose residual was measured.
+#include <math.h>
+#include <string.h>
+
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace nn {
+namespace {
+
+constexpr double kDefaultRefineBelow = 0.1;
+
+struct Simt64Ws {
+  double* X[2];
+  double* R;
+  double* T[2];
+};
+struct Simt32Ws {
+  float* A;
+  float* X[2];
+  float* R;
+  float* T[2];
+};
+struct MixedWs {
+  int np;
+  __nv_bfloat16* a_row[3];
+  float* x32[2];
+  __nv_bfloat16* x_row[2][2];
+  __nv_bfloat16* x_col[2][3];
+  float* r32;
+  __nv_bfloat16* r_row[2];
+  __nv_bfloat16* r_col[2];
+  __nv_bfloat16* t_col[2][2];
+};
+struct Common {
+  double* partial;
+  int n_partial;
+  double* scal;  // [0] s, [1..3] preconditioner scratch
+  int* err;
+};
+
+int partial_capacity(int64_t n, int dtype) {
+  if (dtype == NN_F64) return gemm_simt_partials<double>(int(n), int(n));
+  if (dtype == NN_F32) return gemm_simt_partials<float>(int(n), int(n)) > gemm_simt_partials<double>(int(n), int(n))
+                                  ? gemm_simt_partials<float>(int(n), int(n))
+                                  : gemm_simt_partials<double>(int(n), int(n));
+  return 1024 > gemm_simt_partials<double>(int(n), int(n)) ? 1024 : gemm_simt_partials<double>(int(n), int(n));
+}
+
+void carve_common(Carver& c, int64_t n, int dtype, Common& cm) {
+  cm.n_partial = partial_capacity(n, dtype);
+  cm.partial = c.take<double>(size_t(cm.n_partial));
+  cm.scal = c.take<double>(8);
+  cm.err = c.take<int>(8);
+}
+
+void carve_f64(Carver& c, int64_t n, Simt64Ws& w) {
+  const size_t e = size_t(n) * size_t(n);
+  w.X[0] = c.take<double>(e);
+  w.X[1] = c.take<double>(e);
+  w.R = c.take<double>(e);
+  w.T[0] = c.take<double>(e);
+  w.T[1] = c.take<double>(e);
+}
+
+void carve_f32(Carver& c, int64_t n, Simt32Ws& w) {
+  const size_t e = size_t(n) * size_t(n);
+  w.A = c.take<float>(e);
+  w.X[0] = c.take<float>(e);
+  w.X[1] = c.take<float>(e);
+  w.R = c.take<float>(e);
+  w.T[0] = c.take<float>(e);
+  w.T[1] = c.take<float>(e);
+}
+
+void carve_mixed(Carver& c, int64_t n, MixedWs& w) {
+  w.np = int((n + 127) / 128 * 128);
+  const size_t e = size_t(w.np) * size_t(w.np);
+  for (int i = 0; i < 3; ++i) w.a_row[i] = c.take<__nv_bfloat16>(e);
+  for (int b = 0; b < 2; ++b) {
+    w.x32[b] = c.take<float>(e);
+    for (int i = 0; i < 2; ++i) w.x_row[b][i] = c.take<__nv_bfloat16>(e);
+    for (int i = 0; i < 3; ++i) w.x_col[b][i] = c.take<__nv_bfloat16>(e);
+    for (int i = 0; i < 2; ++i) w.t_col[b][i] = c.take<__nv_bfloat16>(e);
+  }
+  w.r32 = c.take<float>(e);
+  for (int i = 0; i < 2; ++i) {
+    w.r_row[i] = c.take<__nv_bfloat16>(e);
+    w.r_col[i] = c.take<__nv_bfloat16>(e);
+  }
+}
+
+size_t ws_bytes(int64_t n, int dtype) {
+  Carver c(nullptr, 0);
+  Common cm;
+  carve_common(c, n, dtype, cm);
+  if (dtype == NN_F64) {
+    Simt64Ws w;
+    carve_f64(c, n, w);
+  } else if (dtype == NN_F32) {
+    Simt32Ws w;
+    carve_f32(c, n, w);
+    // nn_residual in FP32 converts X into this space as well
+  } else {
+    MixedWs w;
+    carve_mixed(c, n, w);
+  }
+  return align_up(c.used, 256);
+}
+
+bool valid_dtype(int d) { return d == NN_F64 || d == NN_F32 || d == NN_MIXED_BF16; }
+
+// Reads s (and the device error word) back to the host; one stream synchronisation.
+int fetch_scalar(cudaStream_t st, const Common& cm, double* s, int* dev_err) {
+  NN_CUDA_TRY(cudaMemcpyAsync(s, cm.scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+  NN_CUDA_TRY(cudaMemcpyAsync(dev_err, cm.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NN_CUDA_TRY(cudaStreamSynchronize(st));
+  return NN_OK;
+}
+
+// Applies the stop and divergence rules to s_k. Returns -1 to continue, else a status.
+int judge(const nn_opts& o, int k, const double* hist) {
+  const double s = hist[k];
+  if (!isfinite(s)) return NN_ERR_DIVERGED;
+  if (k >= 1 && s >= 1.0 && s > hist[k - 1]) return NN_ERR_DIVERGED;
+  if (o.tol > 0 && s < o.tol) return NN_OK;
+  if (k == o.max_nests) return o.tol > 0 ? NN_ERR_NOT_CONVERGED : NN_OK;
+  return -1;
+}
+
+void init_result(nn_result* r) {
+  memset(r, 0, sizeof(*r));
+  r->status = NN_ERR_ARG;
+}
+
+// ---------------------------------------------------------------------------------------
+// CUDA-core chains (FP64 / FP32).
+
+template <typename T>
+int run_simt(cudaStream_t st, int n, const T* A, int64_t lda, T* const X[2], T* R, T* const Tb[2],
+             const nn_opts& o, const Common& cm, nn_result* res, int* final_idx) {
+  const int nparts = gemm_simt_partials<T>(n, n);
+  int cur = 0;
+  res->nests = 0;
+  for (int k = 0;; ++k) {
+    NN_TRY(gemm_simt<T>(st, n, n, n, A, lda, X[cur], n, R, n, EPI_RESIDUAL, nullptr, 0, n, cm.partial));
+    NN_TRY(reduce_rms(st, cm.partial, nparts, 1.0 / double(n), cm.scal));
+    res->gemms += 1;
+    res->launches += 2;
+    double s = 0;
+    int dev_err = 0;
+    NN_TRY(fetch_scalar(st, cm, &s, &dev_err));
+    res->history[k] = s;
+    res->pieces[k] = 0;
+    res->nests = k;
+    res->residual = s;
+    const int verdict = judge(o, k, res->history);
+    if (verdict >= 0) {
+      res->status = verdict;
+      break;
+    }
+    const T* t_cur = R;
+    for (int j = 1; j < o.depth; ++j) {
+      T* t_nxt = Tb[j & 1];
+      NN_TRY(gemm_simt<T>(st, n, n, n, R, n, t_cur, n, t_nxt, n, EPI_ADD, R, n, n, nullptr));
+      t_cur = t_nxt;
+      res->gemms += 1;
+      res->launches += 1;
+    }
+    NN_TRY(gemm_simt<T>(st, n, n, n, X[cur], n, t_cur, n, X[cur ^ 1], n, EPI_ADD, X[cur], n, n, nullptr));
+    res->gemms += 1;
+    res->launches += 1;
+    cur ^= 1;
+  }
+  *final_idx = cur;
+  return NN_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Tensor-core mixed chain.
+
+// Operand-piece pairs for a split product with p pieces per operand, smallest terms first:
+// p = 1: hh;  p = 2: lh, hl, hh;  p = 3: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0).
+int seg_pairs(int p, int (*pairs)[2]) {
+  static const int p1[1][2] = {{0, 0}};
+  static const int p2[3][2] = {{1, 0}, {0, 1}, {0, 0}};
+  static const int p3[6][2] = {{2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}, {0, 0}};
+  const int(*src)[2] = p == 1 ? p1 : (p == 2 ? p2 : p3);
+  const int cnt = p == 1 ? 1 : (p == 2 ? 3 : 6);
+  for (int i = 0; i < cnt; ++i) {
+    pairs[i][0] = src[i][0];
+    pairs[i][1] = src[i][1];
+  }
+  return cnt;
+}
+
+// CUDA events around each tensor-core GEMM launch (NN_FLAG_TIME_KERNELS).
+struct LaunchTimer {
+  bool on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  ~LaunchTimer() {
+    for (auto& e : ev) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+  }
+  int begin(cudaStream_t st) {
+    if (!on) return NN_OK;
+    cudaEvent_t a, b;
+    NN_CUDA_TRY(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      (void)cudaGetLastError();
+      return NN_ERR_CUDA;
+    }
+    ev.emplace_back(a, b);
+    NN_CUDA_TRY(cudaEventRecord(a, st));
+    return NN_OK;
+  }
+  int end(cudaStream_t st) {
+    if (!on) return NN_OK;
+    NN_CUDA_TRY(cudaEventRecord(ev.back().second, st));
+    return NN_OK;
+  }
+  // After the stream has been synchronised.
+  double total_ms() {
+    double t = 0;
+    for (auto& e : ev) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) t += ms;
+    }
+    (void)cudaGetLastError();
+    return t;
+  }
+};
+
+int tc_product(cudaStream_t st, TcGemmArgs& g, int pieces, __nv_bfloat16* const* a_pieces,
+               __nv_bfloat16* const* b_pieces, const Common& cm, nn_result* res, int* grid, LaunchTimer* tm) {
+  int pairs[6][2];
+  g.nseg = seg_pairs(pieces, pairs);
+  for (int s = 0; s < g.nseg; ++s) {
+    g.a_seg[s] = a_pieces[pairs[s][0]];
+    g.b_seg[s] = b_pieces[pairs[s][1]];
+  }
+  g.err = cm.err;
+  NN_TRY(tm->begin(st));
+  NN_TRY(gemm_tc(st, g, grid));
+  NN_TRY(tm->end(st));
+  const double np3 = double(g.np) * double(g.np) * double(g.np);
+  res->gemms += 1;
+  res->launches += 1;
+  res->tc_launches += 1;
+  res->hw_flops += 2.0 * np3 * g.nseg;
+  res->tc_flops += 2.0 * np3 * g.nseg;
+  return NN_OK;
+}
+
+int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const Common& cm, nn_result* res,
+              int* final_idx) {
+  const int np = w.np;
+  const double refine_below = o.refine_below > 0 ? o.refine_below : kDefaultRefineBelow;
+  const int bulk_pieces = (o.bulk_pieces >= 1 && o.bulk_pieces <= 3) ? o.bulk_pieces : 1;
+  const double sqrt_n = sqrt(double(n));
+  bool refine = bulk_pieces >= 3;
+  int cur = 0;
+  LaunchTimer timer;
+  timer.on = (o.flags & NN_FLAG_TIME_KERNELS) != 0;
+
+  auto residual = [&](int rp, int hp, double* s_out) -> int {
+    TcGemmArgs g;
+    g.np = np;
+    g.n_id = n;
+    g.mode = EPI_RESIDUAL;
+    g.out_f32 = (o.depth >= 2) ? w.r32 : nullptr;
+    g.n_row = (o.depth >= 2) ? hp : 0;
+    g.n_col = hp;
+    for (int i = 0; i < 2; ++i) {
+      g.row_pieces[i] = w.r_row[i];
+      g.col_pieces[i] = w.r_col[i];
+    }
+    g.partial = cm.partial;
+    int grid = 0;
+    NN_TRY(tc_product(st, g, rp, w.a_row, w.x_col[cur], cm, res, &grid, &timer));
+    NN_TRY(reduce_rms(st, cm.partial, grid, 1.0 / double(n), cm.scal));
+    res->launches += 1;
+    int dev_err = 0;
+    NN_TRY(fetch_scalar(st, cm, s_out, &dev_err));
+    if (dev_err != DEV_OK) return NN_ERR_TIMEOUT;
+    return NN_OK;
+  };
+
+  for (int k = 0;; ++k) {
+    int rp = refine ? 3 : bulk_pieces;
+    int hp = refine ? 2 : 1;
+    double s = 0;
+    NN_TRY(residual(rp, hp, &s));
+    if (!refine && ((isfinite(s) && s * sqrt_n < refine_below) || (k >= 1 && !(s <= 0.5 * res->history[k - 1])))) {
+      // Refine from here on; re-measure X_k's residual at FP32-level accuracy.
+      refine = true;
+      rp = 3;
+      hp = 2;
+      NN_TRY(residual(rp, hp, &s));
+    }
+    res->history[k] = s;
+    res->pieces[k] = rp;
+    res->nests = k;
+    res->residual = s;
+    const int verdict = judge(o, k, res->history);
+    if (verdict >= 0) {
+      res->status = verdict;
+      break;
+    }
+    // Horner: T_1 = R (its column pieces), T_{j+1} = R + R T_j.
+    __nv_bfloat16* const* t_cur = w.r_col;
+    for (int j = 1; j < o.depth; ++j) {
+      TcGemmArgs g;
+      g.np = np;
+      g.n_id = n;
+      g.mode = EPI_ADD;
+      g.add = w.r32;
+      g.n_col = hp;
+      for (int i = 0; i < 2; ++i) g.col_pieces[i] = w.t_col[j & 1][i];
+      int grid = 0;
+      NN_TRY(tc_product(st, g, hp, w.r_row, t_cur, cm, res, &grid, &timer));
+      t_cur = w.t_col[j & 1];
+    }
+    // Update: X_{k+1} = X_k + X_k T.
+    {
+      TcGemmArgs g;
+      g.np = np;
+      g.n_id = n;
+      g.mode = EPI_ADD;
+      g.add = w.x32[cur];
+      g.out_f32 = w.x32[cur ^ 1];
+      g.n_row = 2;
+      g.n_col = 3;
+      for (int i = 0; i < 2; ++i) g.row_pieces[i] = w.x_row[cur ^ 1][i];
+      for (int i = 0; i < 3; ++i) g.col_pieces[i] = w.x_col[cur ^ 1][i];
+      int grid = 0;
+      NN_TRY(tc_product(st, g, hp, w.x_row[cur], t_cur, cm, res, &grid, &timer));
+    }
+    cur ^= 1;
+  }
+  *final_idx = cur;
+  if (timer.on) {
+    NN_CUDA_TRY(cudaStreamSynchronize(st));
+    res->tc_ms = timer.total_ms();
+  }
+  return NN_OK;
+}
+
+int check_opts(const nn_opts* o, int64_t n) {
+  if (o == nullptr) return NN_ERR_ARG;
+  if (o->depth < 1 || o->depth > 16) return NN_ERR_ARG;
+  if (o->max_nests < 0 || o->max_nests > NN_MAX_HISTORY - 1) return NN_ERR_ARG;
+  if (!valid_dtype(o->dtype)) return NN_ERR_ARG;
+  if (n < 1 || n > 32768) return NN_ERR_ARG;
+  if (isnan(o->tol)) return NN_ERR_ARG;
+  return NN_OK;
+}
+
+int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int64_t ldx0, const nn_opts* opts,
+                  double* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_size, cudaStream_t st) {
+  const nn_opts& o = *opts;
+  Carver c(workspace, ws_size);
+  Common cm;
+  carve_common(c, n, o.dtype, cm);
+  NN_CUDA_TRY(cudaMemsetAsync(cm.err, 0, sizeof(int), st));
+  const int ni = int(n);
+  int fin = 0;
+  if (o.dtype == NN_F64) {
+    Simt64Ws w;
+    carve_f64(c, n, w);
+    if (!c.ok) return NN_ERR_OOM_BUDGET;
+    NN_TRY(copy_f64(st, X0, ldx0, ni, w.X[0], n));
+    NN_TRY(run_simt<double>(st, ni, A, lda, w.X, w.R, w.T, o, cm, res, &fin));
+    NN_TRY(copy_f64(st, w.X[fin], n, ni, X, ldx));
+    res->launches += 2;
+  } else if (o.dtype == NN_F32) {
+    Simt32Ws w;
+    carve_f32(c, n, w);
+    if (!c.ok) return NN_ERR_OOM_BUDGET;
+    NN_TRY(f64_to_f32(st, A, lda, ni, w.A, n));
+    NN_TRY(f64_to_f32(st, X0, ldx0, ni, w.X[0], n));
+    NN_TRY(run_simt<float>(st, ni, w.A, n, w.X, w.R, w.T, o, cm, res, &fin));
+    NN_TRY(f32_to_f64(st, w.X[fin], n, ni, X, ldx));
+    res->launches += 3;
+  } else {
+    if (!tc_supported()) return NN_ERR_UNSUPPORTED;
+    MixedWs w;
+    carve_mixed(c, n, w);
+    if (!c.ok) return NN_ERR_OOM_BUDGET;
+    NN_TRY(split_matrix(st, A, lda, ni, w.np, nullptr, w.a_row, 3, nullptr, 0));
+    NN_TRY(split_matrix(st, X0, ldx0, ni, w.np, w.x32[0], w.x_row[0], 2, w.x_col[0], 3));
+    NN_TRY(run_mixed(st, ni, w, o, cm, res, &fin));
+    NN_TRY(f32_to_f64(st, w.x32[fin], w.np, ni, X, ldx));
+    res->launches += 3;
+  }
+  // Algorithmic work of the method: (L+1) GEMMs per nest plus the final residual.
+  res->flops = 2.0 * double(n) * double(n) * double(n) * double((o.depth + 1) * res->nests + 1);
+  NN_CUDA_TRY(cudaStreamSynchronize(st));
+  int dev_err = 0;
+  NN_CUDA_TRY(cudaMemcpy(&dev_err, cm.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (dev_err != DEV_OK) {
+    res->status = NN_ERR_TIMEOUT;
+    return NN_ERR_TIMEOUT;
+  }
+  return res->status;
+}
+
+}  // namespace
+}  // namespace nn
+
+using namespace nn;
+
+extern "C" {
+
+size_t nn_workspace_bytes(int64_t n, int dtype) {
+  if (n < 1 || n > 32768 || !valid_dtype(dtype)) return 0;
+  return ws_bytes(n, dtype);
+}
+
+size_t nn_workspace_bytes_host(int64_t n, int dtype) {
+  size_t b = nn_workspace_bytes(n, dtype);
+  if (b == 0) return 0;
+  return b + 3 * align_up(size_t(n) * size_t(n) * sizeof(double), 256) + 256;
+}
+
+int nn_init_precond(const double* A, int64_t n, int64_t lda, int kind, double scalar, double* X0, int64_t ldx,
+                    void* workspace, size_t ws_bytes_, void* stream) {
+  if (A == nullptr || X0 == nullptr || n < 1 || n > 32768 || lda < n || ldx < n) return NN_ERR_ARG;
+  if (kind < NN_PC_PAN_SCHREIBER || kind > NN_PC_JACOBI) return NN_ERR_ARG;
+  if (kind == NN_PC_SCALAR && !(scalar > 0)) return NN_ERR_ARG;
+  Carver c(workspace, ws_bytes_);
+  Common cm;
+  carve_common(c, n, NN_F64, cm);
+  if (!c.ok) return NN_ERR_OOM_BUDGET;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  NN_TRY(precond_fill(st, A, lda, int(n), kind, kind == NN_PC_JACOBI && scalar == 0 ? 1.0 : scalar, X0, ldx,
+                      cm.scal + 1));
+  return NN_OK;
+}
+
+int nn_invert(const double* A, int64_t n, int64_t lda, const double* X0, int64_t ldx0, const nn_opts* opts,
+              double* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_size, void* stream) {
+  if (res == nullptr) return NN_ERR_ARG;
+  init_result(res);
+  NN_TRY(check_opts(opts, n));
+  if (A == nullptr || X0 == nullptr || X == nullptr || lda < n || ldx0 < n || ldx < n) return NN_ERR_ARG;
+  if (workspace == nullptr || ws_size < nn_workspace_bytes(n, opts->dtype)) return NN_ERR_OOM_BUDGET;
+  const int s = invert_device(A, n, lda, X0, ldx0, opts, X, ldx, res, workspace, ws_size,
+                              static_cast<cudaStream_t>(stream));
+  if (s != res->status) res->status = s;
+  return s;
+}
+
+int nn_invert_host(const double* A_host, int64_t n, const double* X0_host, const nn_opts* opts, double* X_host,
+                   nn_result* res, void* workspace, size_t ws_size, void* stream) {
+  if (res == nullptr) return NN_ERR_ARG;
+  init_result(res);
+  NN_TRY(check_opts(opts, n));
+  if (A_host == nullptr || X0_host == nullptr || X_host == nullptr) return NN_ERR_ARG;
+  const size_t need = nn_workspace_bytes_host(n, opts->dtype);
+  if (workspace == nullptr || ws_size < need) return NN_ERR_OOM_BUDGET;
+  const size_t inner = nn_workspace_bytes(n, opts->dtype);
+  Carver c(static_cast<char*>(workspace) + inner, ws_size - inner);
+  const size_t e = size_t(n) * size_t(n);
+  double* dA = c.take<double>(e);
+  double* dX0 = c.take<double>(e);
+  double* dX = c.take<double>(e);
+  if (!c.ok) return NN_ERR_OOM_BUDGET;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  NN_CUDA_TRY(cudaMemcpyAsync(dA, A_host, e * sizeof(double), cudaMemcpyHostToDevice, st));
+  NN_CUDA_TRY(cudaMemcpyAsync(dX0, X0_host, e * sizeof(double), cudaMemcpyHostToDevice, st));
+  int s = invert_device(dA, n, n, dX0, n, opts, dX, n, res, workspace, inner, st);
+  if (s == NN_ERR_CUDA || s == NN_ERR_ARG || s == NN_ERR_UNSUPPORTED || s == NN_ERR_OOM_BUDGET) return s;
+  NN_CUDA_TRY(cudaMemcpyAsync(X_host, dX, e * sizeof(double), cudaMemcpyDeviceToHost, st));
+  NN_CUDA_TRY(cudaStreamSynchronize(st));
+  return s;
+}
+
+int nn_residual(const double* A, int64_t lda, const double* X, int64_t ldx, int64_t n, int dtype, double* rms_frob,
+                void* workspace, size_t ws_size, void* stream) {
+  if (A == nullptr || X == nullptr || rms_frob == nullptr || n < 1 || n > 32768 || lda < n || ldx < n)
+    return NN_ERR_ARG;
+  if (dtype != NN_F64 && dtype != NN_F32) return NN_ERR_ARG;
+  if (workspace == nullptr || ws_size < nn_workspace_bytes(n, dtype)) return NN_ERR_OOM_BUDGET;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carver c(workspace, ws_size);
+  Common cm;
+  carve_common(c, n, dtype, cm);
+  const int ni = int(n);
+  if (dtype == NN_F64) {
+    Simt64Ws w;
+    carve_f64(c, n, w);
+    if (!c.ok) return NN_ERR_OOM_BUDGET;
+    NN_TRY(gemm_simt<double>(st, ni, ni, ni, A, lda, X, ldx, w.R, n, EPI_RESIDUAL, nullptr, 0, ni, cm.partial));
+    NN_TRY(reduce_rms(st, cm.partial, gemm_simt_partials<double>(ni, ni), 1.0 / double(n), cm.scal));
+  } else {
+    Simt32Ws w;
+    carve_f32(c, n, w);
+    if (!c.ok) return NN_ERR_OOM_BUDGET;
+    NN_TRY(f64_to_f32(st, A, lda, ni, w.A, n));
+    NN_TRY(f64_to_f32(st, X, ldx, ni, w.X[0], n));
+    NN_TRY(gemm_simt<float>(st, ni, ni, ni, w.A, n, w.X[0], n, w.R, n, EPI_RESIDUAL, nullptr, 0, ni, cm.partial));
+    NN_TRY(reduce_rms(st, cm.partial, gemm_simt_partials<float>(ni, ni), 1.0 / double(n), cm.scal));
+  }
+  int dev_err = 0;
+  NN_TRY(fetch_scalar(st, cm, rms_frob, &dev_err));
+  return NN_OK;
+}
+
+}  // extern "C"

