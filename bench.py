@@ -54,6 +54,7 @@ def parse_args():
     ap.add_argument("--dtype", default="mixed_bf16", choices=["mixed_bf16", "f32", "f64"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--damping", type=float, default=1.0 / 128.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -242,6 +243,20 @@ def run_dense(args, rank, world, local_rank):
                "d2h_bytes_per_step": n * n * 8, "steps": k_e2e, "ok": st == abi.NN_OK}
         del wsh
 
+    # Independent FP64 check of the returned X on sampled rows of R = I - A X (host).
+    check = None
+    if rank == 0:
+        import numpy as np
+
+        r = np.random.Generator(np.random.PCG64(123))
+        rows = np.sort(r.choice(n, size=32, replace=False))
+        x_host = X.cpu().numpy()
+        a_rows = A[torch.from_numpy(rows).to(dev)].cpu().numpy()
+        rr = -a_rows @ x_host
+        rr[np.arange(len(rows)), rows] += 1.0
+        check = {"rows": len(rows), "s_fp64_sampled": float(np.sqrt(np.mean(np.sum(rr ** 2, axis=1)) / n))}
+        del x_host
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         a_host = A.cpu().numpy()
@@ -265,9 +280,181 @@ def run_dense(args, rank, world, local_rank):
         "status_ok": ok, "nests": last["nests"], "residual": last["residual"], "pieces": last["pieces"],
         "gemms_per_step": last["gemms"], "hw_tflops_per_step": round(last["hw_flops"] / 1e12, 3),
         "gpu_launches": launches,
+        "residual_check": check,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
     }
     return line
+
+
+# ---- sparse workload (SpMV chain) -------------------------------------------------------
+
+def sparse_chain_bytes(n, nnz, depth, nests, val_bytes):
+    """Algorithmic HBM bytes of the chain's sparse products: matrix (val + col + row_ptr) and one
+    read of the input vector per product, plus the output write and the accumulator traffic of the
+    fused variants; and of the final residual product."""
+    mat = nnz * (val_bytes + 4) + 4 * (n + 1)
+    vec = n * val_bytes
+    total = 0
+    products = 0
+    for j in range(nests):
+        t = (depth + 1) ** j
+        for blk in range(1, depth + 1):
+            for s in range(1, t + 1):
+                last_blk = s == t
+                last_fac = last_blk and blk == depth
+                b = mat + vec                      # matrix + input vector
+                b += 0 if last_fac else vec        # y write
+                b += 2 * vec if last_blk else 0    # accumulator read + write
+                total += b
+                products += 1
+    resid = mat + 2 * vec                          # residual: matrix, z, b
+    return total, products, resid
+
+
+def run_sparse(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2212_02406_gb300 import abi, build
+
+    build.build()
+    abi.lib()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    grid, depth, nests = 2048, 2, 5
+    dtype = np.float64 if args.dtype != "f32" else np.float32
+    m = synth.laplacian_5pt(grid, shift=0.5, dtype=dtype)
+    b = synth.gaussian_rhs(m.n, 1, seed=args.seed + rank, dtype=dtype)
+    rp = torch.from_numpy(m.row_ptr).to(dev)
+    col = torch.from_numpy(m.col).to(dev)
+    val = torch.from_numpy(m.val).to(dev)
+    B = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev)
+    X = torch.empty_like(B)
+    ws = abi.csr_workspace(m.n, m.nnz, 1, "f64" if dtype == np.float64 else "f32", device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        st, res = abi.nn_solve_csr(rp, col, val, B, depth, nests, 0.0, X, ws, stream)
+        assert st == abi.NN_OK, (st, res)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        st, res = abi.nn_solve_csr(rp, col, val, B, depth, nests, 0.0, X, ws, stream)
+        launches += res["launches"]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    vb = 8 if dtype == np.float64 else 4
+    chain, products, resid = sparse_chain_bytes(m.n, m.nnz, depth, nests, vb)
+    gbs = (chain + resid) / (ms / 1e3) / 1e9
+    peaks, src = load_peaks()
+    peak = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
+    return {"metric": "HBM GB/s of the sparse NN chain (5-point Laplacian 2048^2, depth 2)",
+            "value": round(gbs * world, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if vb == 8 else "f32", "data": "synthetic",
+            "config": {"workload": f"2-D 5-point Laplacian {grid}x{grid} + 0.5 I, CSR, b ~ N(0,1), Jacobi X0, "
+                                   f"depth {depth}, {nests} factors ({products} sparse products)",
+                       "n": m.n, "nnz": m.nnz, "l2": "matrix larger than L2 (streams every product)"},
+            "status_ok": st == abi.NN_OK, "residual": res["residual"], "gpu_launches": launches,
+            "roofline": {"kernel": "nn::spmv_p_kernel (whole chain timed)", "bound": "hbm", "achieved": round(gbs, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4), "traffic": None,
+                         "peak_source": f"{src} copy bandwidth",
+                         "bytes_per_product": int(chain / products)},
+            "clocks": clocks}
+
+
+# ---- batched workload (many small complex matrices) -----------------------------------------
+
+def run_batched(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2212_02406_gb300 import abi, build
+
+    build.build()
+    abi.lib()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    count, depth, nests = 16384, 2, 3
+    damping = args.damping
+    bt = synth.mimo_gram_batch(count, seed=args.seed + rank)
+    A = torch.from_numpy(bt.data).to(dev)
+    offs = torch.from_numpy(bt.offsets.astype(np.int64)).to(dev)
+    sizes = torch.from_numpy(bt.sizes.astype(np.int32)).to(dev)
+    plan = torch.from_numpy(abi.nn_batched_plan(bt.sizes, load_batched_tuning())).to(dev)
+    X = torch.empty_like(A)
+    res = torch.empty(count, dtype=torch.float32, device=dev)
+    st = torch.empty(count, dtype=torch.int32, device=dev)
+    ws = torch.empty(abi.nn_batched_workspace_bytes(count), dtype=torch.uint8, device=dev)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            assert abi.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws, s) == 0
+    torch.cuda.current_stream(dev).wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        assert abi.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws) == 0
+    for _ in range(args.warmup):
+        g.replay()
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for i in range(args.steps):
+        g.replay()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    ms = sum(per) / len(per)
+    u = bt.sizes.astype(np.float64)
+    gemms = (depth + 1) * nests + 1
+    flops = float(np.sum(8.0 * u ** 3)) * gemms
+    byts = float(np.sum(16.0 * u ** 2))  # read A, write X (complex64)
+    stats = st.cpu().numpy()
+    peaks, src = load_peaks()
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fma_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    tflops = flops / (ms / 1e3) / 1e12
+    return {"metric": "batched inversions/s (16,384 complex64 Gram matrices, U in {8..64}, depth 2, 3 nests)",
+            "value": round(count * world / (ms / 1e3), 1), "unit": "inversions/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "p99_ms": round(float(np.percentile(per, 99)), 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64 (fp32 FMA)", "data": "synthetic",
+            "config": {"workload": f"{count} Gram matrices A = H^H H + 0.1 I, H 128 x U CN(0,1), U uniform over "
+                                   f"{{8,16,24,32,48,64}}, X0 = diag(A)^-1/(1 + {damping:g} U), depth {depth}, "
+                                   f"{nests} nests, one persistent kernel replayed from a CUDA graph",
+                       "count": count, "damping": damping, "l2": "A + X = 363 MB > L2"},
+            "status_ok_fraction": float(np.mean(stats == 0)), "gpu_launches": args.steps,
+            "tflops": round(tflops, 2), "gbs": round(byts / (ms / 1e3) / 1e9, 1),
+            "roofline": {"kernel": "nn::batched_nn_kernel", "bound": "alu", "achieved": round(tflops, 2),
+                         "peak": round(fma_peak, 1), "unit": "TFLOP/s", "frac": round(tflops / fma_peak, 4),
+                         "traffic": None, "peak_source": f"FP32 FMA: {sms} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz",
+                         "hbm_frac": round(byts / (ms / 1e3) / 1e9 / float(peaks.get('hbm_gbs', 6800.0)), 4)},
+            "clocks": clocks}
+
+
+def load_batched_tuning():
+    p = os.path.join(ROOT, "paper_2212_02406_gb300", "batched_tuning.json")
+    try:
+        with open(p) as f:
+            return {int(k): int(v) for k, v in json.load(f)["cfg_by_u"].items()}
+    except Exception:
+        return None
 
 
 def run_reference(args):
@@ -328,10 +515,10 @@ def main():
         dist.init_process_group("nccl")
     if args.workload == "dense":
         line = run_dense(args, rank, world, local_rank)
+    elif args.workload == "sparse":
+        line = run_sparse(args, rank, world, local_rank)
     else:
-        from paper_2212_02406_gb300 import workloads  # noqa: F401  (sparse / batched lines)
-
-        line = workloads.run(args, rank, world, local_rank)
+        line = run_batched(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

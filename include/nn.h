@@ -72,7 +72,9 @@ typedef struct nn_opts {
   int dtype;           /* nn_dtype                                                                */
   double refine_below; /* NN_MIXED_BF16: switch to refine nests once s_k * sqrt(N) < refine_below;
                           <= 0 selects the default 0.1. A stall (s_{k+1} > 0.5 s_k) also switches. */
-  int bulk_pieces;     /* NN_MIXED_BF16: BF16 pieces per operand in bulk residuals (1..3; 0 = 1)  */
+  int bulk_pieces;     /* NN_MIXED_BF16: starting precision level 1..4 (0 = 1): the BF16 pieces of
+                          the first residuals (1, 2, 3, 3) and updates (1, 2, 2, 3); the chain
+                          raises the level itself as the residual nears each level's floor     */
   int flags;           /* NN_FLAG_* bits                                                           */
 } nn_opts;
 
@@ -125,6 +127,54 @@ int nn_invert_host(const double* A_host, int64_t n, const double* X0_host, const
  * dtype NN_F64 evaluates in FP64; NN_F32 in FP32. Section II (error measure). */
 int nn_residual(const double* A, int64_t lda, const double* X, int64_t ldx, int64_t n, int dtype,
                 double* rms_frob, void* workspace, size_t ws_bytes, void* stream);
+
+/* ---- sparse right-hand-side chain ------------------------------------------------------
+ * The explicit NN form applied to right-hand sides (Corollary 1, Eq. (NNexplicit); Corollary 6;
+ * Algorithm 2) with the Jacobi start phi^(0) = D^-1, D = diag(A):
+ *     X = D^-1 prod_{j=0}^{nests-1} ( sum_{n=0}^{L} P^{n (L+1)^j} ) B,    P = I - A D^-1,
+ * i.e. the Neumann series of order (L+1)^nests - 1 (Corollary 2), computed as (L+1)^nests - 1
+ * sparse products without forming any dense matrix. (Algorithm 2 prints the L + 1 = 2 case.)
+ *
+ * A: CSR, row_ptr[n+1] and col[nnz] int32 (device), val[nnz] (device) of `dtype` (NN_F64 or
+ * NN_F32); columns in any order; every row needs a nonzero diagonal (else NN_ERR_ARG).
+ * B, X: device, column-major n x nrhs of `dtype`, leading dimensions ldb, ldx >= n.
+ * tol > 0: after each factor j the relative residual ||B - A X_j||_F / ||B||_F (one extra
+ * sparse product) goes to res->history[j] and the chain stops at the first factor below tol
+ * (NN_ERR_NOT_CONVERGED if none is). tol <= 0 runs all `nests` factors and evaluates the
+ * residual once at the end (res->residual). res->nests = factors applied; res->flops counts
+ * 2 nnz per sparse product per right-hand side. Needs nn_csr_workspace_bytes() of workspace. */
+size_t nn_csr_workspace_bytes(int64_t n, int64_t nnz, int64_t nrhs, int dtype);
+int nn_solve_csr(const int32_t* row_ptr, const int32_t* col, const void* val, int64_t n, int64_t nnz,
+                 int dtype, const void* B, int64_t ldb, int64_t nrhs, int depth, int nests, double tol,
+                 void* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_bytes, void* stream);
+
+/* ---- batched small complex inversions ---------------------------------------------------
+ * Many independent U x U complex64 matrices (U <= 64; massive-MIMO Gram matrices, the use the
+ * paper names in Corollary 4) inverted by the right-multiplied NN loop in one persistent
+ * kernel: X_0 = diag(A)^-1 / (1 + damping * U) (Jacobi start, a diagonal Theta of Appendix 1;
+ * damping = 0 is plain Jacobi), then `nests` nests of depth L, with s_k = ||I - A X_k||_F / U
+ * and the divergence rule of nn_invert (a diverged matrix keeps the X_k at which it diverged).
+ *
+ * nn_batched_plan (host only): sorts the matrices by size (largest first) and groups equal
+ * sizes into work items. sizes_host[count] in 1..64; cfg_by_u (nullable, 65 entries indexed by
+ * U, -1 = default) picks the thread tiling per size (0: 8x8 threads per matrix, up to four
+ * matrices per CTA; 1: 16x16 threads per matrix); plan_host holds nn_batched_plan_size(count)
+ * int32. The caller copies the plan to the device and may reuse it for every launch with the
+ * same size list.
+ *
+ * nn_invert_batched_c64: A and X device complex64 (interleaved re, im) packed back to back,
+ * matrix b row-major at element offset offsets[b] (device int64) with size sizes[b] (device
+ * int32); plan = the device copy of the plan. residual[b] (device float) = s of the returned
+ * X_b; status[b] (device int32) = NN_OK or NN_ERR_DIVERGED. The call only enqueues work on
+ * `stream` (a memset and one kernel; no synchronisation, no allocation), so it can be
+ * captured in a CUDA graph. Needs nn_batched_workspace_bytes(count) of workspace. */
+int64_t nn_batched_plan_size(int64_t count);
+int nn_batched_plan(const int32_t* sizes_host, int64_t count, const int32_t* cfg_by_u, int32_t* plan_host);
+size_t nn_batched_workspace_bytes(int64_t count);
+int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* sizes, int64_t count,
+                          const int32_t* plan, int depth, int nests, double damping, void* X,
+                          float* residual, int32_t* status, void* workspace, size_t ws_bytes,
+                          void* stream);
 
 #ifdef __cplusplus
 }

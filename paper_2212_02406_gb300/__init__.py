@@ -10,6 +10,10 @@ from .abi import (  # noqa: F401
     nn_invert,
     nn_invert_host,
     nn_residual,
+    nn_csr_workspace_bytes,
+    nn_solve_csr,
+    nn_batched_plan,
+    nn_invert_batched_c64,
     nn_workspace_bytes,
     nn_workspace_bytes_host,
 )

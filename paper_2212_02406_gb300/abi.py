@@ -66,6 +66,14 @@ _SIGNATURES = {
                                c_size_t, c_void_p]),
     "nn_residual": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int, POINTER(c_double), c_void_p,
                             c_size_t, c_void_p]),
+    "nn_csr_workspace_bytes": (c_size_t, [c_int64, c_int64, c_int64, c_int]),
+    "nn_batched_plan_size": (c_int64, [c_int64]),
+    "nn_batched_plan": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
+    "nn_batched_workspace_bytes": (c_size_t, [c_int64]),
+    "nn_invert_batched_c64": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int, c_int, c_double,
+                                      c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "nn_solve_csr": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int, c_void_p, c_int64, c_int64, c_int,
+                             c_int, c_double, c_void_p, c_int64, POINTER(NNResult), c_void_p, c_size_t, c_void_p]),
 }
 
 
@@ -103,11 +111,11 @@ def _mat(t, name, dtype=None):
 
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
-    if t.dim() != 2 or t.stride(1) != 1:
+    if t.dim() != 2 or (t.stride(1) != 1 and t.shape[1] > 1):
         raise ValueError(f"{name} must be 2-D row-major (stride(1) == 1)")
     if dtype is not None and t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}")
-    return c_void_p(t.data_ptr()), t.stride(0)
+    return c_void_p(t.data_ptr()), (t.stride(0) if t.shape[0] > 1 else t.shape[1])
 
 
 def _ws(workspace):
@@ -197,3 +205,103 @@ def nn_residual(A, X, dtype, workspace, stream=None):
     out = c_double(0.0)
     st = lib().nn_residual(pa, lda, px, ldx, A.shape[0], d, ctypes.byref(out), pw, nw, _stream_ptr(stream))
     return st, out.value
+
+
+# ---- sparse chain ----------------------------------------------------------------------
+
+def _vec_dtype(t):
+    import torch
+
+    if t.dtype == torch.float64:
+        return NN_F64
+    if t.dtype == torch.float32:
+        return NN_F32
+    raise TypeError("values must be float64 or float32")
+
+
+def nn_csr_workspace_bytes(n: int, nnz: int, nrhs: int, dtype) -> int:
+    d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    return int(lib().nn_csr_workspace_bytes(int(n), int(nnz), int(nrhs), d))
+
+
+def csr_workspace(n: int, nnz: int, nrhs: int, dtype, device=None):
+    import torch
+
+    nbytes = nn_csr_workspace_bytes(n, nnz, nrhs, dtype)
+    if nbytes == 0:
+        raise ValueError("invalid CSR sizes or dtype")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def nn_solve_csr(row_ptr, col, val, B, depth, nests, tol, X, workspace, stream=None):
+    """CSR (int32 row_ptr/col, float val) on the device; B and X are (nrhs, n) row-major
+    tensors, i.e. column-major n x nrhs blocks with leading dimension n. Returns (status, result)."""
+    import torch
+
+    for name, t in (("row_ptr", row_ptr), ("col", col)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous int32 CUDA tensor")
+    d = _vec_dtype(val)
+    for name, t in (("B", B), ("X", X)):
+        if not (t.is_cuda and t.dtype == val.dtype and t.dim() == 2 and t.stride(1) == 1):
+            raise TypeError(f"{name} must be a (nrhs, n) row-major CUDA tensor of the value dtype")
+    n = row_ptr.numel() - 1
+    nrhs = B.shape[0]
+    if B.shape[1] != n or X.shape != B.shape:
+        raise ValueError("B and X must be (nrhs, n)")
+    # a dimension of extent 1 may carry any stride: the leading dimension is then n
+    ldb = B.stride(0) if nrhs > 1 else n
+    ldx = X.stride(0) if nrhs > 1 else n
+    pw, nw = _ws(workspace)
+    res = NNResult()
+    st = lib().nn_solve_csr(c_void_p(row_ptr.data_ptr()), c_void_p(col.data_ptr()), c_void_p(val.data_ptr()), n,
+                            val.numel(), d, c_void_p(B.data_ptr()), ldb, nrhs, int(depth), int(nests),
+                            float(tol), c_void_p(X.data_ptr()), ldx, ctypes.byref(res), pw, nw,
+                            _stream_ptr(stream))
+    return st, res.as_dict()
+
+
+# ---- batched small complex inversions -------------------------------------------------------
+
+def nn_batched_plan(sizes, cfg_by_u=None):
+    """Host plan for a size list (NumPy int32 array); returns the int32 plan array."""
+    import numpy as np
+
+    sizes = np.ascontiguousarray(sizes, dtype=np.int32)
+    count = sizes.shape[0]
+    plan = np.zeros(int(lib().nn_batched_plan_size(count)), dtype=np.int32)
+    cfg = None
+    if cfg_by_u is not None:
+        cfg = np.full(65, -1, dtype=np.int32)
+        for u, c in dict(cfg_by_u).items():
+            cfg[int(u)] = int(c)
+    st = lib().nn_batched_plan(c_void_p(sizes.ctypes.data), count,
+                               c_void_p(cfg.ctypes.data) if cfg is not None else c_void_p(0), c_void_p(plan.ctypes.data))
+    if st != NN_OK:
+        raise ValueError(f"nn_batched_plan failed ({STATUS_NAMES.get(st, st)})")
+    return plan
+
+
+def nn_batched_workspace_bytes(count: int) -> int:
+    return int(lib().nn_batched_workspace_bytes(int(count)))
+
+
+def nn_invert_batched_c64(A, offsets, sizes, plan, depth, nests, damping, X, residual, status, workspace,
+                          stream=None) -> int:
+    """A, X: complex64 CUDA tensors (packed); offsets int64, sizes int32, plan int32, residual float32,
+    status int32 CUDA tensors. Enqueues only (graph-capturable); returns the status code."""
+    import torch
+
+    if A.dtype != torch.complex64 or X.dtype != torch.complex64 or not (A.is_cuda and X.is_cuda):
+        raise TypeError("A and X must be complex64 CUDA tensors")
+    checks = ((offsets, torch.int64), (sizes, torch.int32), (plan, torch.int32), (residual, torch.float32),
+              (status, torch.int32))
+    for t, dt in checks:
+        if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError(f"expected contiguous CUDA {dt}")
+    pw, nw = _ws(workspace)
+    return lib().nn_invert_batched_c64(c_void_p(A.data_ptr()), c_void_p(offsets.data_ptr()),
+                                       c_void_p(sizes.data_ptr()), sizes.numel(), c_void_p(plan.data_ptr()),
+                                       int(depth), int(nests), float(damping), c_void_p(X.data_ptr()),
+                                       c_void_p(residual.data_ptr()), c_void_p(status.data_ptr()), pw, nw,
+                                       _stream_ptr(stream))

@@ -11,15 +11,18 @@ namespace {
 constexpr int TILE = 32;
 constexpr int ROWS = 8;  // 32 x 8 threads per 32 x 32 tile
 
-// BF16 pieces of a value: p0 = bf16(v), p1 = bf16(v - p0), p2 = bf16(v - p0 - p1), with the
-// remainders formed in FP64 (exact for these magnitudes).
-__device__ __forceinline__ void pieces3(double v, __nv_bfloat16 (&p)[3]) {
-  double r = v;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    p[i] = __double2bfloat16(r);
-    r -= static_cast<double>(__bfloat162float(p[i]));
-  }
+// BF16 pieces of a value with FP32 arithmetic after one FP64 split (the FP64 pipe is narrow):
+// v = hi + lo with hi = fp32(v), lo = fp32(v - hi); p0 = bf16(hi), p1 = bf16((hi - p0) + lo),
+// p2 = bf16(((hi - p0) + lo) - p1). hi - p0 and t - p1 are exact in FP32; the only rounding
+// beyond the pieces themselves is (hi - p0) + lo, at most 2^-24 |hi - p0| <= 2^-33 |v|.
+__device__ __forceinline__ float pieces3(double v, __nv_bfloat16 (&p)[3]) {
+  const float hi = static_cast<float>(v);
+  const float lo = static_cast<float>(v - static_cast<double>(hi));
+  p[0] = __float2bfloat16_rn(hi);
+  const float t = (hi - __bfloat162float(p[0])) + lo;
+  p[1] = __float2bfloat16_rn(t);
+  p[2] = __float2bfloat16_rn(t - __bfloat162float(p[1]));
+  return hi;
 }
 
 struct PiecePtrs {
@@ -27,19 +30,34 @@ struct PiecePtrs {
 };
 
 __global__ void split_kernel(const double* __restrict__ src, int64_t lds, int n, int np, float* __restrict__ f32,
-                             PiecePtrs row, int n_row, PiecePtrs col, int n_col) {
+                             PiecePtrs row, int n_row, PiecePtrs col, int n_col, double* __restrict__ sumsq) {
   __shared__ __nv_bfloat16 tile[3][TILE][TILE + 2];
+  __shared__ float red[ROWS];
   const int i0 = blockIdx.y * TILE, j0 = blockIdx.x * TILE;
   const int tx = threadIdx.x, ty = threadIdx.y;
+  float ss = 0.f;
   for (int r = ty; r < TILE; r += ROWS) {
     const int i = i0 + r, j = j0 + tx;
     double v = (i < n && j < n) ? src[int64_t(i) * lds + j] : 0.0;
     const int64_t off = int64_t(i) * np + j;
-    if (f32) f32[off] = static_cast<float>(v);
     __nv_bfloat16 pc[3];
-    pieces3(v, pc);
+    const float hi = pieces3(v, pc);
+    if (f32) f32[off] = hi;
+    ss = fmaf(hi, hi, ss);
     for (int q = 0; q < n_row; ++q) row.p[q][off] = pc[q];
     for (int q = 0; q < n_col; ++q) tile[q][r][tx] = pc[q];
+  }
+  if (sumsq != nullptr) {
+    // per-block sum of squares (FP32 within the block, fixed order), for ||src||_F
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+    if (tx == 0) red[ty] = ss;
+    __syncthreads();
+    if (tx == 0 && ty == 0) {
+      float t = 0.f;
+      for (int w = 0; w < ROWS; ++w) t += red[w];
+      sumsq[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = double(t);
+    }
   }
   if (n_col > 0) {
     __syncthreads();
@@ -69,6 +87,24 @@ __global__ void reduce_rms_kernel(const double* __restrict__ partial, int count,
     __syncthreads();
   }
   if (threadIdx.x == 0) out[0] = sqrt(buf[0]) * scale;
+}
+
+// Per-block sum of squares of an n x n matrix, grid-stride over rows (fixed block order).
+__global__ void sumsq_rows_kernel(const double* __restrict__ src, int64_t lds, int n, double* partial) {
+  __shared__ double buf[256];
+  double s = 0.0;
+  for (int i = blockIdx.x; i < n; i += gridDim.x)
+    for (int j = threadIdx.x; j < n; j += 256) {
+      const double v = src[int64_t(i) * lds + j];
+      s = fma(v, v, s);
+    }
+  buf[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) buf[threadIdx.x] += buf[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = buf[0];
 }
 
 // Non-negative doubles order like their bit patterns, so max() can use the 64-bit integer atomic.
@@ -148,16 +184,19 @@ __global__ void fill_diag_kernel(const double* __restrict__ A, int64_t lda, int 
 }  // namespace
 
 int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
-                 __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col) {
+                 __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
+                 double* sumsq_partial) {
   if (np % TILE != 0 || n > np || n_row < 0 || n_row > 3 || n_col < 0 || n_col > 3) return NN_ERR_ARG;
   PiecePtrs r{}, c{};
   for (int q = 0; q < n_row; ++q) r.p[q] = row_pieces[q];
   for (int q = 0; q < n_col; ++q) c.p[q] = col_pieces[q];
   dim3 grid(np / TILE, np / TILE), block(TILE, ROWS);
-  split_kernel<<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col);
+  split_kernel<<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial);
   NN_CUDA_TRY(cudaGetLastError());
   return NN_OK;
 }
+
+int split_blocks(int np) { return (np / TILE) * (np / TILE); }
 
 template <typename S, typename D>
 static int convert(cudaStream_t st, const S* src, int64_t lds, int n, D* dst, int64_t ldd) {
@@ -176,6 +215,15 @@ int copy_f64(cudaStream_t st, const double* src, int64_t lds, int n, double* dst
 }
 int f64_to_f32(cudaStream_t st, const double* src, int64_t lds, int n, float* dst, int64_t ldd) {
   return convert(st, src, lds, n, dst, ldd);
+}
+
+int frob_f64(cudaStream_t st, const double* src, int64_t lds, int n, double* partial, int count, double* out) {
+  int blocks = count < 1024 ? count : 1024;
+  if (blocks > n) blocks = n;
+  if (blocks < 1) return NN_ERR_ARG;
+  sumsq_rows_kernel<<<blocks, 256, 0, st>>>(src, lds, n, partial);
+  NN_CUDA_TRY(cudaGetLastError());
+  return reduce_rms(st, partial, blocks, 1.0, out);
 }
 
 int reduce_rms(cudaStream_t st, const double* partial, int count, double scale, double* out) {

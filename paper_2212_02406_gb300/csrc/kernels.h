@@ -52,13 +52,18 @@ bool tc_supported();
 // ---- conversion / preconditioner / reduction kernels (convert.cu) -----------------------
 // Splits an n x n FP64 matrix (leading dim lds) into an Np-padded FP32 copy and BF16
 // pieces (row-major and/or transposed). Any output may be null. Padding is zero.
+// sumsq_partial (nullable) receives one sum of squares per 32 x 32 block (split_blocks(np) entries).
 int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
-                 __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col);
+                 __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
+                 double* sumsq_partial);
+int split_blocks(int np);
 // dst (FP64, ldd) = src (FP32, lds), n x n.
 int f32_to_f64(cudaStream_t st, const float* src, int64_t lds, int n, double* dst, int64_t ldd);
 // dst (T2, ldd) = src (T1, lds), n x n.
 int copy_f64(cudaStream_t st, const double* src, int64_t lds, int n, double* dst, int64_t ldd);
 int f64_to_f32(cudaStream_t st, const double* src, int64_t lds, int n, float* dst, int64_t ldd);
+// out[0] = ||src||_F for an n x n FP64 matrix (partial must hold >= min(count, 1024) doubles).
+int frob_f64(cudaStream_t st, const double* src, int64_t lds, int n, double* partial, int count, double* out);
 // out[0] = sqrt(sum partial[0..count)) * scale, fixed summation order.
 int reduce_rms(cudaStream_t st, const double* partial, int count, double scale, double* out);
 // Preconditioners: write X0 (n x n FP64, ldx). scratch holds >= 4 doubles.

@@ -34,14 +34,15 @@ struct Simt32Ws {
 };
 struct MixedWs {
   int np;
+  double* split_partial;  // one per 32 x 32 block of the split kernel
   __nv_bfloat16* a_row[3];
   float* x32[2];
-  __nv_bfloat16* x_row[2][2];
+  __nv_bfloat16* x_row[2][3];
   __nv_bfloat16* x_col[2][3];
   float* r32;
-  __nv_bfloat16* r_row[2];
-  __nv_bfloat16* r_col[2];
-  __nv_bfloat16* t_col[2][2];
+  __nv_bfloat16* r_row[3];
+  __nv_bfloat16* r_col[3];
+  __nv_bfloat16* t_col[2][3];
 };
 struct Common {
   double* partial;
@@ -87,15 +88,16 @@ void carve_f32(Carver& c, int64_t n, Simt32Ws& w) {
 void carve_mixed(Carver& c, int64_t n, MixedWs& w) {
   w.np = int((n + 127) / 128 * 128);
   const size_t e = size_t(w.np) * size_t(w.np);
+  w.split_partial = c.take<double>(size_t(split_blocks(w.np)));
   for (int i = 0; i < 3; ++i) w.a_row[i] = c.take<__nv_bfloat16>(e);
   for (int b = 0; b < 2; ++b) {
     w.x32[b] = c.take<float>(e);
-    for (int i = 0; i < 2; ++i) w.x_row[b][i] = c.take<__nv_bfloat16>(e);
+    for (int i = 0; i < 3; ++i) w.x_row[b][i] = c.take<__nv_bfloat16>(e);
     for (int i = 0; i < 3; ++i) w.x_col[b][i] = c.take<__nv_bfloat16>(e);
-    for (int i = 0; i < 2; ++i) w.t_col[b][i] = c.take<__nv_bfloat16>(e);
+    for (int i = 0; i < 3; ++i) w.t_col[b][i] = c.take<__nv_bfloat16>(e);
   }
   w.r32 = c.take<float>(e);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 3; ++i) {
     w.r_row[i] = c.take<__nv_bfloat16>(e);
     w.r_col[i] = c.take<__nv_bfloat16>(e);
   }
@@ -124,6 +126,14 @@ bool valid_dtype(int d) { return d == NN_F64 || d == NN_F32 || d == NN_MIXED_BF1
 // Reads s (and the device error word) back to the host; one stream synchronisation.
 int fetch_scalar(cudaStream_t st, const Common& cm, double* s, int* dev_err) {
   NN_CUDA_TRY(cudaMemcpyAsync(s, cm.scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+  NN_CUDA_TRY(cudaMemcpyAsync(dev_err, cm.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NN_CUDA_TRY(cudaStreamSynchronize(st));
+  return NN_OK;
+}
+
+// Reads count doubles from cm.scal and the device error word; one stream synchronisation.
+int fetch_scalars(cudaStream_t st, const Common& cm, double* vals, int count, int* dev_err) {
+  NN_CUDA_TRY(cudaMemcpyAsync(vals, cm.scal, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
   NN_CUDA_TRY(cudaMemcpyAsync(dev_err, cm.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   NN_CUDA_TRY(cudaStreamSynchronize(st));
   return NN_OK;
@@ -266,18 +276,63 @@ int tc_product(cudaStream_t st, TcGemmArgs& g, int pieces, __nv_bfloat16* const*
   return NN_OK;
 }
 
-int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const Common& cm, nn_result* res,
-              int* final_idx) {
+// Precision levels of the mixed chain (BF16 pieces per operand):
+//   level 1: residual 1 piece,  Horner/update 1 piece   (bulk)
+//   level 2: residual 2 pieces, Horner/update 2 pieces
+//   level 3: residual 3 pieces, Horner/update 2 pieces   (FP32-level residual)
+//   level 4: residual 3 pieces, Horner/update 3 pieces
+// A piece-p product has relative error about 2^-(8p+1); the residual error floor of level L
+// is e(L) ~ 2^-b(L) ||A||_F ||X_k||_F / N^1.5, the rms of the rounding of sum_k a_ik x_kj
+// (N terms of typical size |a_i| |x_j| / N with random signs, |a_i| ~ ||A||_F / sqrt(N)),
+// with b = 9, 17, 19, 19 (levels 3 and 4 are bounded by the tensor core's FP32
+// accumulation, not by the pieces). The chain moves up a level once s_k < 8 e(L), when it
+// stalls (s_k > 0.9 s_{k-1}) within 30 e(L) of the floor, and before accepting s_k < tol.
+// Stability: a product with p pieces perturbs the next residual by about
+// 2^-(8p+1) ||A||_2 ||X_k||_2 ||T||_2; once that nears 1 the perturbed residual can reach
+// spectral radius 1 in a slowly converging direction and the chain diverges later even though
+// s_k still falls. K = ||A||_F ||X_k||_F / N estimates ||A||_2 ||X_k||_2 from below, so the
+// level must keep 2^-(8p+1) K * 64 <= 1 (64 covers ||T||_2 <= L+1 and the Frobenius-to-spectral
+// gap of the spectra this path is built for).
+// Levels never go down. The residual accepted for the stop test is always level >= 3.
+static int level_res_pieces(int L) { return L <= 1 ? 1 : (L == 2 ? 2 : 3); }
+static int level_upd_pieces(int L) { return L <= 1 ? 1 : (L <= 3 ? 2 : 3); }
+static int stable_level(double kest) {
+  for (int L = 1; L <= 3; ++L) {
+    const int p = level_upd_pieces(L);
+    if (ldexp(kest, -(8 * p + 1)) * 64.0 <= 1.0) return L;
+  }
+  return 4;
+}
+static double level_floor(int L, double c) {
+  const double b = L <= 1 ? 9.0 : (L == 2 ? 17.0 : 19.0);
+  return ldexp(c, -int(b));
+}
+
+// Re-splits X_0 into buffer set 0 (pieces, FP32 master) and its norm into cm.scal[1].
+struct X0Source {
+  const double* x0;
+  int64_t ldx0;
+};
+int load_x0(cudaStream_t st, int n, const MixedWs& w, const Common& cm, const X0Source& src) {
+  const int sb = split_blocks(w.np);
+  NN_TRY(split_matrix(st, src.x0, src.ldx0, n, w.np, w.x32[0], w.x_row[0], 3, w.x_col[0], 3, w.split_partial));
+  NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0, cm.scal + 1));
+  return NN_OK;
+}
+
+int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const Common& cm, double a_frob,
+              const X0Source& x0src, nn_result* res, int* final_idx) {
   const int np = w.np;
-  const double refine_below = o.refine_below > 0 ? o.refine_below : kDefaultRefineBelow;
-  const int bulk_pieces = (o.bulk_pieces >= 1 && o.bulk_pieces <= 3) ? o.bulk_pieces : 1;
   const double sqrt_n = sqrt(double(n));
-  bool refine = bulk_pieces >= 3;
+  const double n15 = double(n) * sqrt(double(n));
+  int level = (o.bulk_pieces >= 1 && o.bulk_pieces <= 4) ? o.bulk_pieces : 1;
   int cur = 0;
+  double x_frob = 0;  // ||X_k||_F, read back with s_k
   LaunchTimer timer;
   timer.on = (o.flags & NN_FLAG_TIME_KERNELS) != 0;
 
-  auto residual = [&](int rp, int hp, double* s_out) -> int {
+  auto residual = [&](int L, double* s_out) -> int {
+    const int hp = level_upd_pieces(L);
     TcGemmArgs g;
     g.np = np;
     g.n_id = n;
@@ -285,42 +340,90 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
     g.out_f32 = (o.depth >= 2) ? w.r32 : nullptr;
     g.n_row = (o.depth >= 2) ? hp : 0;
     g.n_col = hp;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 3; ++i) {
       g.row_pieces[i] = w.r_row[i];
       g.col_pieces[i] = w.r_col[i];
     }
     g.partial = cm.partial;
     int grid = 0;
-    NN_TRY(tc_product(st, g, rp, w.a_row, w.x_col[cur], cm, res, &grid, &timer));
+    NN_TRY(tc_product(st, g, level_res_pieces(L), w.a_row, w.x_col[cur], cm, res, &grid, &timer));
     NN_TRY(reduce_rms(st, cm.partial, grid, 1.0 / double(n), cm.scal));
     res->launches += 1;
     int dev_err = 0;
-    NN_TRY(fetch_scalar(st, cm, s_out, &dev_err));
+    double vals[2];
+    NN_TRY(fetch_scalars(st, cm, vals, 2, &dev_err));
     if (dev_err != DEV_OK) return NN_ERR_TIMEOUT;
+    *s_out = vals[0];
+    x_frob = vals[1];
     return NN_OK;
   };
 
+  int rollbacks = 0;
+  bool restarted = false;
+  double x_frob_prev = 0;  // ||X_{k-1}||_F, kept for a rollback
   for (int k = 0;; ++k) {
-    int rp = refine ? 3 : bulk_pieces;
-    int hp = refine ? 2 : 1;
     double s = 0;
-    NN_TRY(residual(rp, hp, &s));
-    if (!refine && ((isfinite(s) && s * sqrt_n < refine_below) || (k >= 1 && !(s <= 0.5 * res->history[k - 1])))) {
-      // Refine from here on; re-measure X_k's residual at FP32-level accuracy.
-      refine = true;
-      rp = 3;
-      hp = 2;
-      NN_TRY(residual(rp, hp, &s));
+    NN_TRY(residual(level, &s));
+    // Slow first contraction (s_1 > 0.85 s_0) marks a residual spectrum crowded near 1, i.e.
+    // large kappa: there the rounding of BF16 bulk nests, amplified by the (L+1)-fold growth of
+    // errors along eigenvalues of R close to 1, can push rho(R) past 1 nests later. Discard
+    // the bulk nest and start again from X_0 at level 2 (once).
+    if (k == 1 && level == 1 && !restarted && isfinite(s) && s > 0.85 * res->history[0]) {
+      restarted = true;
+      cur = 0;
+      k = 0;
+      level = 2;
+      NN_TRY(load_x0(st, n, w, cm, x0src));
+      res->launches += 2;
+      NN_TRY(residual(level, &s));
+    }
+    const double c = a_frob * x_frob / n15;
+    {
+      int target = level;
+      if (isfinite(s)) {
+        const int ls = stable_level(a_frob * x_frob / double(n));
+        if (target < ls) target = ls;
+        while (target < 3 && s < 8.0 * level_floor(target, c)) ++target;
+        if (k >= 1 && s > 0.9 * res->history[k - 1] && s < 30.0 * level_floor(level, c) && level < 4)
+          target = target > (level <= 2 ? 3 : 4) ? target : (level <= 2 ? 3 : 4);
+        if (o.refine_below > 0 && s * sqrt_n < o.refine_below && target < 3) target = 3;
+        if (o.tol > 0 && s < o.tol && target < 3) target = 3;
+      }
+      if (target != level) {
+        const bool remeasure = level_res_pieces(target) != level_res_pieces(level);
+        level = target;
+        if (remeasure) NN_TRY(residual(level, &s));
+      }
+    }
+    // A nest that made the residual grow below the top level was spoiled by rounding
+    // (low-precision updates amplify along slowly converging directions when kappa is
+    // large): discard X_k, return to X_{k-1} (still in the other buffer) and continue from
+    // there at the top level. NN converges from any X with rho(I - A X) < 1 (Appendix 2).
+    if (k >= 1 && level < 4 && rollbacks < 2 && !(s <= res->history[k - 1])) {
+      ++rollbacks;
+      cur ^= 1;
+      --k;
+      x_frob = x_frob_prev;
+      level = 4;
+      NN_TRY(residual(level, &s));
+      x_frob = x_frob_prev;
     }
     res->history[k] = s;
-    res->pieces[k] = rp;
+    res->pieces[k] = level_res_pieces(level);
     res->nests = k;
     res->residual = s;
-    const int verdict = judge(o, k, res->history);
+    int verdict = judge(o, k, res->history);
+    // At the top level, two nests in a row within 30 floors without a 10% gain: the residual
+    // has reached the arithmetic floor, so more nests cannot reach tol.
+    if (verdict < 0 && level == 4 && k >= 2 && o.tol > 0 && s > 0.9 * res->history[k - 1] &&
+        res->history[k - 1] > 0.9 * res->history[k - 2] && s < 30.0 * level_floor(4, c))
+      verdict = NN_ERR_NOT_CONVERGED;
     if (verdict >= 0) {
       res->status = verdict;
       break;
     }
+    const int hp = level_upd_pieces(level);
+    x_frob_prev = x_frob;
     // Horner: T_1 = R (its column pieces), T_{j+1} = R + R T_j.
     __nv_bfloat16* const* t_cur = w.r_col;
     for (int j = 1; j < o.depth; ++j) {
@@ -330,12 +433,12 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
       g.mode = EPI_ADD;
       g.add = w.r32;
       g.n_col = hp;
-      for (int i = 0; i < 2; ++i) g.col_pieces[i] = w.t_col[j & 1][i];
+      for (int i = 0; i < 3; ++i) g.col_pieces[i] = w.t_col[j & 1][i];
       int grid = 0;
       NN_TRY(tc_product(st, g, hp, w.r_row, t_cur, cm, res, &grid, &timer));
       t_cur = w.t_col[j & 1];
     }
-    // Update: X_{k+1} = X_k + X_k T.
+    // Update: X_{k+1} = X_k + X_k T, with ||X_{k+1}||_F from the epilogue partials.
     {
       TcGemmArgs g;
       g.np = np;
@@ -343,12 +446,17 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
       g.mode = EPI_ADD;
       g.add = w.x32[cur];
       g.out_f32 = w.x32[cur ^ 1];
-      g.n_row = 2;
+      g.n_row = 3;
       g.n_col = 3;
-      for (int i = 0; i < 2; ++i) g.row_pieces[i] = w.x_row[cur ^ 1][i];
-      for (int i = 0; i < 3; ++i) g.col_pieces[i] = w.x_col[cur ^ 1][i];
+      for (int i = 0; i < 3; ++i) {
+        g.row_pieces[i] = w.x_row[cur ^ 1][i];
+        g.col_pieces[i] = w.x_col[cur ^ 1][i];
+      }
+      g.partial = cm.partial;
       int grid = 0;
       NN_TRY(tc_product(st, g, hp, w.x_row[cur], t_cur, cm, res, &grid, &timer));
+      NN_TRY(reduce_rms(st, cm.partial, grid, 1.0, cm.scal + 1));
+      res->launches += 1;
     }
     cur ^= 1;
   }
@@ -401,9 +509,18 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     MixedWs w;
     carve_mixed(c, n, w);
     if (!c.ok) return NN_ERR_OOM_BUDGET;
-    NN_TRY(split_matrix(st, A, lda, ni, w.np, nullptr, w.a_row, 3, nullptr, 0));
-    NN_TRY(split_matrix(st, X0, ldx0, ni, w.np, w.x32[0], w.x_row[0], 2, w.x_col[0], 3));
-    NN_TRY(run_mixed(st, ni, w, o, cm, res, &fin));
+    // BF16 pieces of A and X_0, with ||A||_F and ||X_0||_F (for the precision-level floors)
+    // from the split kernel's per-block sums of squares
+    const int sb = split_blocks(w.np);
+    NN_TRY(split_matrix(st, A, lda, ni, w.np, nullptr, w.a_row, 3, nullptr, 0, w.split_partial));
+    NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0, cm.scal + 2));
+    const X0Source x0src{X0, ldx0};
+    NN_TRY(load_x0(st, ni, w, cm, x0src));
+    double a_frob = 0;
+    NN_CUDA_TRY(cudaMemcpyAsync(&a_frob, cm.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    NN_CUDA_TRY(cudaStreamSynchronize(st));
+    res->launches += 4;
+    NN_TRY(run_mixed(st, ni, w, o, cm, a_frob, x0src, res, &fin));
     NN_TRY(f32_to_f64(st, w.x32[fin], w.np, ni, X, ldx));
     res->launches += 3;
   }

@@ -5,10 +5,14 @@ Tolerances (derived from the arithmetic):
   they differ only by rounding, which the self-correcting iteration keeps at the level
   of the conditioning floor: ||X_gpu - X_ora||_F / ||X_ora||_F <= max(1e-12, 16 kappa u64 sqrt(N)).
 * FP32 chain: the same with u32 (and kappa u32 for the converged iterate).
-* Mixed BF16 tensor-core chain refined to s < tol: the converged iterate is within the
-  forward error of the FP32-level residual floor; relative error vs the oracle's converged
-  inverse <= 2e-6 at kappa <= 1e2 (the FP32 rounding of A alone moves A^-1 by ~8 kappa^0 u32,
-  see DESIGN), and the residual measured independently in FP64 agrees with the reported s.
+* Mixed BF16 tensor-core chain: the accepted residual is evaluated from three BF16 pieces
+  per operand (products exact to ~2^-24) but summed by the tensor core in FP32, whose
+  rounding over N/16 accumulator updates bounds the reported s against an FP64
+  re-evaluation of the returned X by e_acc(N) = 4 u32 (1 + sqrt(N)/4) (the diagonal terms
+  drift from 0 to 1, so a per-update error of u32 gives at most u32 N/16 per diagonal entry,
+  u32 sqrt(N)/16 in rms). The forward error then follows from X - A^-1 = -A^-1 R:
+  ||X - A^-1||_F / ||A^-1||_F <= 2 sqrt(N) s + 16 kappa u32 (the last term is the FP32
+  storage of X and the piece representation of A).
 """
 import math
 
@@ -39,6 +43,11 @@ def _dev(a):
     import torch
 
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def e_acc(n):
+    """Bound on |reported s - FP64 re-evaluation| for the mixed chain (module docstring)."""
+    return 4 * U32 * (1 + math.sqrt(n) / 4)
 
 
 def _rel(a, b):
@@ -156,7 +165,8 @@ def test_mixed_bf16_converges_and_matches(nn, n, depth):
     assert res["pieces"][-1] == 3  # the accepted residual was measured at FP32-level accuracy
     # the reported residual agrees with an independent FP64 evaluation of the returned X
     s64 = dense.rms_frob(dense.residual(a, x))
-    assert abs(s64 - res["residual"]) <= 0.05 * res["residual"] + 5e-8
+    assert abs(s64 - res["residual"]) <= e_acc(n)
+    assert s64 < 1e-6
     # forward error against the library inverse: residual floor + FP32 rounding of A
     inv = np.linalg.inv(a)
     assert _rel(x, inv) <= 2 * math.sqrt(n) * s64 + 16 * kappa * U32
@@ -165,15 +175,30 @@ def test_mixed_bf16_converges_and_matches(nn, n, depth):
     assert abs(res["nests"] - ora.nests) <= 1
 
 
-def test_mixed_refined_to_floor_matches_oracle_1e6(nn):
-    n, kappa, depth = 512, 1e2, 2
+@pytest.mark.parametrize("n", [128, 256])
+def test_mixed_matches_oracle_within_1e6(nn, n):
+    # Relative error against the FP64 oracle's converged inverse, at sizes where the FP32
+    # accumulation floor keeps sqrt(N) s below the 1e-6 target.
+    kappa, depth = 1e2, 2
     a, q, lam = synth.spd_spectrum(n, kappa, seed=11)
     x0 = dense.precond_scalar(n, 2.0 / (lam[0] + lam[-1]))
-    st, res, x = _run(nn, a, x0, depth, 1e-9, 40, "mixed_bf16")
-    # the FP32-level floor may stop short of 1e-9: accept OK or NOT_CONVERGED at the floor
-    assert st in (nn.NN_OK, nn.NN_ERR_NOT_CONVERGED, nn.NN_ERR_DIVERGED) or True
+    st, res, x = _run(nn, a, x0, depth, 1e-7, 12, "mixed_bf16")
+    assert st in (nn.NN_OK, nn.NN_ERR_NOT_CONVERGED), res
     ora = dense.nn_invert(a, x0, depth, tol=1e-13, max_nests=40)
-    assert _rel(x, ora.x) <= 1e-6 or res["residual"] > 1e-8
+    assert _rel(x, ora.x) <= 1e-6
+
+
+def test_mixed_kappa_1e4_does_not_diverge(nn):
+    # kappa = 1e4 needs more than FP32-level arithmetic to reach 1e-6; the level schedule must
+    # still converge to its floor without diverging, and report the floor honestly.
+    n = 512
+    a, q, lam = synth.spd_spectrum(n, 1e4, seed=5)
+    x0 = dense.precond_scalar(n, 2.0 / (lam[0] + lam[-1]))
+    st, res, x = _run(nn, a, x0, 2, 1e-6, 20, "mixed_bf16")
+    assert st in (nn.NN_OK, nn.NN_ERR_NOT_CONVERGED), res
+    s64 = dense.rms_frob(dense.residual(a, x))
+    assert s64 < 1e-4
+    assert abs(s64 - res["residual"]) <= e_acc(n) * 1e2  # floor scales with |A||X| ~ kappa
 
 
 def test_host_variant_equals_device_variant(nn):

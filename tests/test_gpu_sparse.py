@@ -1,0 +1,114 @@
+"""GPU parity of the sparse NN chain (nn_solve_csr) against the CPU oracle.
+
+The chain computes X = D^-1 prod_j sum_n P^{n (L+1)^j} B with (L+1)^k - 1 sparse products.
+Both sides run the same sequence of products; they differ by the summation order inside
+each row (at most max_row_nnz terms) and by the FP64/FP32 rounding of each product, so the
+relative difference is bounded by m * u * (1 + max_row_nnz) with m = (L+1)^k - 1 products:
+tolerance 8 m u (nnz_row + 1) per dtype, with a 1e-13 floor for FP64.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import sparse
+
+pytestmark = pytest.mark.gpu
+
+U = {np.float64: 2.0 ** -53, np.float32: 2.0 ** -24}
+
+
+@pytest.fixture(scope="module")
+def nn():
+    from paper_2212_02406_gb300 import abi, build
+
+    build.build()
+    abi.lib()
+    return abi
+
+
+def _solve(nn, m, b, depth, nests, tol=0.0, dtype=np.float64):
+    import torch
+
+    rp = torch.from_numpy(m.row_ptr.astype(np.int32)).cuda()
+    col = torch.from_numpy(m.col.astype(np.int32)).cuda()
+    val = torch.from_numpy(m.val.astype(dtype)).cuda()
+    B = torch.from_numpy(np.ascontiguousarray(b.T.astype(dtype))).cuda()  # (nrhs, n)
+    X = torch.empty_like(B)
+    ws = nn.csr_workspace(m.n, m.nnz, B.shape[0], "f64" if dtype == np.float64 else "f32")
+    st, res = nn.nn_solve_csr(rp, col, val, B, depth, nests, tol, X, ws)
+    torch.cuda.synchronize()
+    return st, res, X.cpu().numpy().T
+
+
+def _tol(m, depth, nests, dtype):
+    terms = (depth + 1) ** nests - 1
+    nnz_row = int(np.max(np.diff(m.row_ptr)))
+    t = 8 * max(terms, 1) * U[dtype] * (nnz_row + 1)
+    return max(t, 1e-13) if dtype == np.float64 else t
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("depth", [1, 2, 3])
+@pytest.mark.parametrize("kind", ["laplacian", "random"])
+@pytest.mark.parametrize("nrhs", [1, 3, 6])
+def test_chain_matches_oracle(nn, dtype, depth, kind, nrhs):
+    m = synth.laplacian_5pt(33, 29, shift=0.5) if kind == "laplacian" else synth.random_sparse_spd(1000, 7, seed=4)
+    b = synth.gaussian_rhs(m.n, nrhs, seed=3)
+    a64 = m.to_scipy()
+    for nests in (0, 1, 3):
+        if (depth + 1) ** nests > 100:
+            continue
+        st, res, x = _solve(nn, m, b, depth, nests, dtype=dtype)
+        assert st == nn.NN_OK and res["nests"] == nests
+        want = sparse.nn_sparse_solve(a64, b.astype(np.float64), depth, nests)
+        err = np.linalg.norm(x - want) / np.linalg.norm(want)
+        assert err <= _tol(m, depth, nests, dtype), (nests, err)
+        # residual reported for the returned X agrees with the oracle's
+        r = sparse.relative_residual(a64, want, b)
+        assert abs(res["residual"] - r) <= 1e-6 * r + (1e-12 if dtype == np.float64 else 1e-5)
+
+
+def test_tol_stops_at_first_factor_below(nn):
+    m = synth.laplacian_5pt(40, shift=0.5)
+    b = synth.gaussian_rhs(m.n, 1, seed=8)
+    a64 = m.to_scipy()
+    st, res, x = _solve(nn, m, b, 2, 8, tol=1e-6)
+    assert st == nn.NN_OK
+    rels = [sparse.relative_residual(a64, sparse.nn_sparse_solve(a64, b, 2, j + 1), b) for j in range(8)]
+    k = next(j for j, r in enumerate(rels) if r < 1e-6)
+    assert res["nests"] == k + 1
+    for j in range(k + 1):
+        assert abs(res["history"][j] - rels[j]) <= 1e-8 * rels[j] + 1e-14
+
+
+def test_edge_cases(nn):
+    # n = 1, nests = 0 (X = D^-1 B), a missing diagonal is rejected before the chain runs
+    m = synth.Csr(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([4.0]))
+    st, res, x = _solve(nn, m, np.array([[2.0]]), 2, 3)
+    assert st == nn.NN_OK and abs(x[0, 0] - 0.5) < 1e-15
+    m = synth.laplacian_5pt(5, shift=0.5)
+    b = synth.gaussian_rhs(m.n, 1, seed=1)
+    st, res, x = _solve(nn, m, b, 2, 0)
+    assert st == nn.NN_OK and np.allclose(x[:, 0], b[:, 0] / m.to_scipy().diagonal(), rtol=1e-15)
+    bad = synth.Csr(2, np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), np.array([1.0, 1.0]))
+    st, res, x = _solve(nn, bad, np.ones((2, 1)), 2, 1)
+    assert st == nn.NN_ERR_ARG
+
+
+def test_full_size_laplacian_2048(nn):
+    # The benchmarked configuration: 2048 x 2048 grid, shift 0.5, depth 2, 5 factors
+    # (242 sparse products), FP64, checked element-wise against the oracle.
+    m = synth.laplacian_5pt(2048, shift=0.5)
+    b = synth.gaussian_rhs(m.n, 1, seed=0)
+    st, res, x = _solve(nn, m, b, 2, 5)
+    assert st == nn.NN_OK
+    a64 = m.to_scipy()
+    want = sparse.nn_sparse_solve(a64, b, 2, 5)
+    err = np.linalg.norm(x - want) / np.linalg.norm(want)
+    assert err <= _tol(m, 2, 5, np.float64)
+    # D = 4.5 I, so b - A x_m = (I - A/4.5)^m b and ||r|| / ||b|| <= rho(P)^m, m = 3^5 terms,
+    # down to the FP64 rounding floor
+    rho = 4.0 * math.cos(math.pi / 2049) / 4.5
+    assert res["residual"] <= rho ** 243 + 1e-12
