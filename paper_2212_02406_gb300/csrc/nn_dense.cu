@@ -390,7 +390,10 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
         if (o.tol > 0 && s < o.tol && target < 3) target = 3;
       }
       if (target != level) {
-        const bool remeasure = level_res_pieces(target) != level_res_pieces(level);
+        // The residual epilogue writes R's pieces for the Horner/update GEMMs at the level's
+        // update count, so a change in either count needs a new residual.
+        const bool remeasure = level_res_pieces(target) != level_res_pieces(level) ||
+                               level_upd_pieces(target) != level_upd_pieces(level);
         level = target;
         if (remeasure) NN_TRY(residual(level, &s));
       }
