@@ -42,7 +42,8 @@ typedef enum nn_status {
   NN_ERR_OOM_BUDGET = 4,    /* workspace too small for the request                         */
   NN_ERR_TIMEOUT = 5,       /* a device-side wait ran past its limit                       */
   NN_ERR_CUDA = 6,          /* CUDA runtime error                                          */
-  NN_ERR_UNSUPPORTED = 7    /* combination not implemented (e.g. no sm_103a device)         */
+  NN_ERR_UNSUPPORTED = 7,   /* combination not implemented (e.g. no sm_103a device)         */
+  NN_ERR_TOO_LARGE = 8      /* size beyond a fixed-capacity entry point's stated maximum    */
 } nn_status;
 
 /* ---- arithmetic of the dense nest chain -------------------------------------------- */
@@ -175,6 +176,23 @@ int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* 
                           const int32_t* plan, int depth, int nests, double damping, void* X,
                           float* residual, int32_t* status, void* workspace, size_t ws_bytes,
                           void* stream);
+
+/* ---- residual without any allocation ---------------------------------------------------
+ * The paper has no counterpart: this is a deployment variant of nn_residual for callers that
+ * cannot allocate device memory (inside a CUDA graph capture, in services that forbid
+ * allocation after start-up, or when another framework owns and budgets all device memory and
+ * hands out only the operands). It computes s = ||I - A X||_F / N in FP64 from device A and X
+ * (row-major, leading dimensions lda, ldx >= n) into *rms_frob (host), using the same kernels
+ * as nn_residual, with its scratch in a fixed 16 MiB array that the library reserves in device
+ * memory on every GPU that loads it, until the process exits.
+ * Limits: n <= NN_RESIDUAL_NOALLOC_MAX_N, larger n returns NN_ERR_TOO_LARGE before any device
+ * work. The array is shared by all calls on a device: calls whose work overlaps on the GPU race
+ * on it; each call overwrites all the scratch it reads, so nothing carries over between calls.
+ * The first call on each device resolves the array's address (cudaGetSymbolAddress); make it
+ * before any stream capture on that device. Synchronises `stream` before returning. */
+#define NN_RESIDUAL_NOALLOC_MAX_N 1440
+int nn_residual_noalloc(const double* A, int64_t lda, const double* X, int64_t ldx, int64_t n,
+                        double* rms_frob, void* stream);
 
 #ifdef __cplusplus
 }

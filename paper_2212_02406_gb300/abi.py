@@ -22,8 +22,10 @@ NN_ERR_OOM_BUDGET = 4
 NN_ERR_TIMEOUT = 5
 NN_ERR_CUDA = 6
 NN_ERR_UNSUPPORTED = 7
+NN_ERR_TOO_LARGE = 8
 STATUS_NAMES = {0: "ok", 1: "arg", 2: "diverged", 3: "not_converged", 4: "oom_budget", 5: "timeout",
-                6: "cuda", 7: "unsupported"}
+                6: "cuda", 7: "unsupported", 8: "too_large"}
+NN_RESIDUAL_NOALLOC_MAX_N = 1440
 
 NN_F64, NN_F32, NN_MIXED_BF16 = 0, 1, 2
 DTYPES = {"f64": NN_F64, "f32": NN_F32, "mixed_bf16": NN_MIXED_BF16}
@@ -67,6 +69,7 @@ _SIGNATURES = {
     "nn_residual": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int, POINTER(c_double), c_void_p,
                             c_size_t, c_void_p]),
     "nn_csr_workspace_bytes": (c_size_t, [c_int64, c_int64, c_int64, c_int]),
+    "nn_residual_noalloc": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_int64, POINTER(c_double), c_void_p]),
     "nn_batched_plan_size": (c_int64, [c_int64]),
     "nn_batched_plan": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
     "nn_batched_workspace_bytes": (c_size_t, [c_int64]),
@@ -305,3 +308,19 @@ def nn_invert_batched_c64(A, offsets, sizes, plan, depth, nests, damping, X, res
                                        int(depth), int(nests), float(damping), c_void_p(X.data_ptr()),
                                        c_void_p(residual.data_ptr()), c_void_p(status.data_ptr()), pw, nw,
                                        _stream_ptr(stream))
+
+
+# ---- residual without allocation ---------------------------------------------------------
+
+def nn_residual_noalloc(A, X, stream=None):
+    """FP64 s = ||I - A X||_F / N using the library's fixed device scratch (no workspace).
+
+    For callers that cannot allocate device memory; N <= NN_RESIDUAL_NOALLOC_MAX_N.
+    Returns (status, s)."""
+    import torch
+
+    pa, lda = _mat(A, "A", torch.float64)
+    px, ldx = _mat(X, "X", torch.float64)
+    out = c_double(0.0)
+    st = lib().nn_residual_noalloc(pa, lda, px, ldx, A.shape[0], ctypes.byref(out), _stream_ptr(stream))
+    return st, out.value
