@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dense", choices=["dense", "sparse", "batched"])
+    ap.add_argument("--workload", default="dense", choices=["dense", "sparse", "batched", "serve"])
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--kappa", type=float, default=1e2)
     ap.add_argument("--depth", type=int, default=2)
@@ -55,6 +55,9 @@ def parse_args():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--damping", type=float, default=1.0 / 128.0)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--max-active", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -457,6 +460,86 @@ def load_batched_tuning():
         return None
 
 
+# ---- served stream (continuous batching) ---------------------------------------------------
+
+def run_serve(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2212_02406_gb300 import abi, build
+
+    build.build()
+    abi.lib()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    count = args.requests
+    reqs = synth.request_stream(count, rate_per_s=1.0, seed=args.seed + rank)
+    data = []
+    for r in reqs:
+        a, q, lam = synth.spd_spectrum_torch(r.n, r.kappa, seed=r.seed, device=dev)
+        del q
+        a_host = torch.empty((r.n, r.n), dtype=torch.float64, pin_memory=True)
+        a_host.copy_(a)
+        b_host = torch.empty((r.n, r.nrhs), dtype=torch.float64, pin_memory=True)
+        b_host.copy_(torch.from_numpy(synth.rng(r.seed + 1).standard_normal((r.n, r.nrhs))))
+        y_host = torch.empty((r.n, r.nrhs), dtype=torch.float64, pin_memory=True)
+        data.append((r, a_host, b_host, y_host))
+    torch.cuda.synchronize(dev)
+    budget = int(args.budget_gb * 2 ** 30)
+    arena = torch.empty(budget, dtype=torch.uint8, device=dev)
+    dtype_of = {"f32": "f32", "bf16": "mixed_bf16"}
+
+    def drive(rate):
+        srv = abi.Server(arena, max_active=args.max_active, depth=args.depth, tol=args.tol, max_nests=64)
+        try:
+            gaps = synth.rng(args.seed + 17).exponential(1.0 / rate, size=count) if rate else np.zeros(count)
+            t0 = time.perf_counter()
+            due = t0
+            for (r, a_h, b_h, y_h), g in zip(data, gaps):
+                due += g
+                while True:
+                    dt = due - time.perf_counter()
+                    if dt <= 0:
+                        break
+                    time.sleep(min(dt, 0.002))
+                st = srv.submit(r.rid, a_h.numpy(), B=b_h.numpy(), Y=y_h.numpy(), dtype=dtype_of[r.dtype],
+                                precond="trace")
+                assert st == abi.NN_OK, st
+            assert srv.wait_idle(600.0) == abi.NN_OK
+            comps = srv.poll(count + 8)
+            stats = srv.stats()
+        finally:
+            srv.close()
+        lat = np.array([c["t_done"] - c["t_submit"] for c in comps]) * 1e3
+        span = max(c["t_done"] for c in comps) - min(c["t_submit"] for c in comps)
+        ok = float(np.mean([c["status"] in (abi.NN_OK, abi.NN_ERR_NOT_CONVERGED) for c in comps]))
+        conv = float(np.mean([c["status"] == abi.NN_OK for c in comps]))
+        return {"throughput": len(comps) / span, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "ok_frac": ok, "converged_frac": conv,
+                "arena_peak_gb": stats["arena_peak"] / 2 ** 30, "span_s": span}
+
+    for _ in range(max(1, args.warmup)):
+        warm = drive(0.0)
+    cap = drive(0.0)  # closed loop: everything queued at t = 0 -> capacity
+    loads = {}
+    for frac in (0.5, 0.8, 0.95):
+        loads[str(frac)] = drive(frac * cap["throughput"])
+    head = loads["0.8"]
+    return {"metric": "served NN inversions/s and p99 latency (Poisson arrivals at 80% of capacity)",
+            "value": round(head["throughput"] * world, 3), "unit": "inversions/s", "n_gpus": world,
+            "steps": count, "warmup": args.warmup, "ms_per_step": round(1e3 / head["throughput"], 3),
+            "p50_ms": round(head["p50_ms"], 3), "p99_ms": round(head["p99_ms"], 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "mixed: f32 (CUDA cores) / bf16 pieces (tcgen05), 50/50", "data": "synthetic",
+            "config": {"workload": f"{count} SPD requests, N log-uniform [16, 2048], kappa log-uniform [10, 1e3], "
+                                   f"1-64 right-hand sides, X0 = I/Tr(A), depth {args.depth}, eps {args.tol:g}, "
+                                   f"HBM budget {args.budget_gb:g} GiB, {args.max_active} concurrent",
+                       "requests": count, "budget_gb": args.budget_gb, "max_active": args.max_active},
+            "capacity_per_s": round(cap["throughput"], 3), "loads": loads,
+            "gpu_launches": None}
+
+
 def run_reference(args):
     """The oracle as the reference arm: one nest of the FP64 oracle per step on the host."""
     import numpy as np
@@ -517,6 +600,8 @@ def main():
         line = run_dense(args, rank, world, local_rank)
     elif args.workload == "sparse":
         line = run_sparse(args, rank, world, local_rank)
+    elif args.workload == "serve":
+        line = run_serve(args, rank, world, local_rank)
     else:
         line = run_batched(args, rank, world, local_rank)
     if rank == 0:

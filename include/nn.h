@@ -177,6 +177,61 @@ int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* 
                           float* residual, int32_t* status, void* workspace, size_t ws_bytes,
                           void* stream);
 
+/* ---- serving: continuous batching of inversions and solves -----------------------------
+ * A request inverts one dense N x N matrix A (host FP64, row-major) with the NN loop of
+ * nn_invert (X_0 from `precond` with `pc_scalar`, depth / tol / max_nests from the server
+ * options, arithmetic `dtype`) and, if nrhs > 0, solves Y = X B for B (host FP64, row-major
+ * N x nrhs). X (host, N x N) and Y (host, N x nrhs) receive the results when not NULL. Host
+ * buffers must stay valid until the request's completion is polled; pinned memory gives
+ * asynchronous copies. This is the serving form of the spec workload; the paper itself
+ * describes single inversions (Algorithm 1) and linear solves (Corollary 3).
+ *
+ * The server allocates no device memory: `arena` (device, arena_bytes) is the HBM budget
+ * from which every admitted request's buffers are carved (nn_server_request_bytes() each).
+ * Up to max_active requests run at once, each on its own worker thread and CUDA stream, so
+ * their work overlaps on the GPU; a request is admitted as soon as a slot and enough arena
+ * are free (arrival order, with a bounded bypass for requests that fit while an earlier one
+ * does not). nn_server_submit never blocks (NN_ERR_OOM_BUDGET if the request can never fit);
+ * nn_server_poll returns finished requests with their status, nests, final residual and
+ * steady-clock times (seconds) of submission, start and completion. Requests not yet admitted
+ * when nn_server_destroy is called are dropped; running ones finish first. */
+typedef struct nn_server nn_server;
+typedef struct nn_server_opts {
+  void* arena;          /* device memory the server may use                                    */
+  size_t arena_bytes;
+  int max_active;       /* concurrent requests (worker threads / streams), 1..64               */
+  int depth;            /* inception depth for every request                                   */
+  double tol;           /* stop tolerance on ||I - A X||_F / N                                 */
+  int max_nests;
+} nn_server_opts;
+typedef struct nn_request {
+  int64_t id;
+  int64_t n;
+  const double* A;
+  int64_t nrhs;
+  const double* B;
+  double* Y;
+  double* X;
+  int dtype;            /* NN_F64, NN_F32 or NN_MIXED_BF16                                     */
+  int precond;          /* nn_pc                                                               */
+  double pc_scalar;
+} nn_request;
+typedef struct nn_completion {
+  int64_t id;
+  int status;
+  int nests;
+  double residual;
+  double t_submit, t_start, t_done;
+} nn_completion;
+
+size_t nn_server_request_bytes(int64_t n, int64_t nrhs, int dtype);
+int nn_server_create(const nn_server_opts* opts, nn_server** out);
+int nn_server_submit(nn_server* s, const nn_request* r);
+int nn_server_poll(nn_server* s, nn_completion* out, int max_out, int* count);
+int nn_server_wait_idle(nn_server* s, double timeout_s);
+int nn_server_stats(nn_server* s, size_t* arena_used, size_t* arena_peak, int* pending, int* active);
+int nn_server_destroy(nn_server* s);
+
 /* ---- residual without any allocation ---------------------------------------------------
  * The paper has no counterpart: this is a deployment variant of nn_residual for callers that
  * cannot allocate device memory (inside a CUDA graph capture, in services that forbid

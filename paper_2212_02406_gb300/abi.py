@@ -54,6 +54,21 @@ class NNResult(ctypes.Structure):
                 "tc_launches": self.tc_launches, "tc_ms": self.tc_ms, "tc_flops": self.tc_flops}
 
 
+class NNServerOpts(ctypes.Structure):
+    _fields_ = [("arena", c_void_p), ("arena_bytes", c_size_t), ("max_active", c_int), ("depth", c_int),
+                ("tol", c_double), ("max_nests", c_int)]
+
+
+class NNRequest(ctypes.Structure):
+    _fields_ = [("id", c_int64), ("n", c_int64), ("A", c_void_p), ("nrhs", c_int64), ("B", c_void_p),
+                ("Y", c_void_p), ("X", c_void_p), ("dtype", c_int), ("precond", c_int), ("pc_scalar", c_double)]
+
+
+class NNCompletion(ctypes.Structure):
+    _fields_ = [("id", c_int64), ("status", c_int), ("nests", c_int), ("residual", c_double),
+                ("t_submit", c_double), ("t_start", c_double), ("t_done", c_double)]
+
+
 _LIB = None
 
 # Every symbol include/nn.h declares, with its ctypes signature.
@@ -70,6 +85,13 @@ _SIGNATURES = {
                             c_size_t, c_void_p]),
     "nn_csr_workspace_bytes": (c_size_t, [c_int64, c_int64, c_int64, c_int]),
     "nn_residual_noalloc": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_int64, POINTER(c_double), c_void_p]),
+    "nn_server_request_bytes": (c_size_t, [c_int64, c_int64, c_int]),
+    "nn_server_create": (c_int, [POINTER(NNServerOpts), POINTER(c_void_p)]),
+    "nn_server_submit": (c_int, [c_void_p, POINTER(NNRequest)]),
+    "nn_server_poll": (c_int, [c_void_p, POINTER(NNCompletion), c_int, POINTER(c_int)]),
+    "nn_server_wait_idle": (c_int, [c_void_p, c_double]),
+    "nn_server_stats": (c_int, [c_void_p, POINTER(c_size_t), POINTER(c_size_t), POINTER(c_int), POINTER(c_int)]),
+    "nn_server_destroy": (c_int, [c_void_p]),
     "nn_batched_plan_size": (c_int64, [c_int64]),
     "nn_batched_plan": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
     "nn_batched_workspace_bytes": (c_size_t, [c_int64]),
@@ -324,3 +346,70 @@ def nn_residual_noalloc(A, X, stream=None):
     out = c_double(0.0)
     st = lib().nn_residual_noalloc(pa, lda, px, ldx, A.shape[0], ctypes.byref(out), _stream_ptr(stream))
     return st, out.value
+
+
+# ---- serving -------------------------------------------------------------------------------
+
+def nn_server_request_bytes(n, nrhs, dtype) -> int:
+    d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    return int(lib().nn_server_request_bytes(int(n), int(nrhs), d))
+
+
+class Server:
+    """Marshalling wrapper of nn_server_*: keeps the host arrays of in-flight requests alive."""
+
+    def __init__(self, arena, max_active=4, depth=2, tol=1e-6, max_nests=64):
+        self.arena = arena
+        opts = NNServerOpts(c_void_p(arena.data_ptr()), arena.numel() * arena.element_size(), int(max_active),
+                            int(depth), float(tol), int(max_nests))
+        h = c_void_p()
+        st = lib().nn_server_create(ctypes.byref(opts), ctypes.byref(h))
+        if st != NN_OK:
+            raise RuntimeError(f"nn_server_create failed ({STATUS_NAMES.get(st, st)})")
+        self.h = h
+        self.live = {}
+
+    def submit(self, rid, A, B=None, Y=None, X=None, dtype="f32", precond="trace", pc_scalar=1.0) -> int:
+        import numpy as np
+
+        for name, arr in (("A", A), ("B", B), ("Y", Y), ("X", X)):
+            if arr is not None and not (isinstance(arr, np.ndarray) and arr.dtype == np.float64
+                                        and arr.flags.c_contiguous):
+                raise TypeError(f"{name} must be a C-contiguous float64 ndarray")
+        d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        k = PRECONDS[precond] if isinstance(precond, str) else int(precond)
+        nrhs = 0 if B is None else B.shape[1]
+        req = NNRequest(int(rid), A.shape[0], c_void_p(A.ctypes.data), nrhs,
+                        c_void_p(B.ctypes.data) if B is not None else c_void_p(0),
+                        c_void_p(Y.ctypes.data) if Y is not None else c_void_p(0),
+                        c_void_p(X.ctypes.data) if X is not None else c_void_p(0), d, k, float(pc_scalar))
+        st = lib().nn_server_submit(self.h, ctypes.byref(req))
+        if st == NN_OK:
+            self.live[int(rid)] = (A, B, Y, X)
+        return st
+
+    def poll(self, max_out=256):
+        buf = (NNCompletion * max_out)()
+        cnt = c_int(0)
+        lib().nn_server_poll(self.h, buf, max_out, ctypes.byref(cnt))
+        out = []
+        for i in range(cnt.value):
+            c = buf[i]
+            self.live.pop(int(c.id), None)
+            out.append({"id": c.id, "status": c.status, "nests": c.nests, "residual": c.residual,
+                        "t_submit": c.t_submit, "t_start": c.t_start, "t_done": c.t_done})
+        return out
+
+    def wait_idle(self, timeout_s=0.0) -> int:
+        return lib().nn_server_wait_idle(self.h, float(timeout_s))
+
+    def stats(self):
+        used, peak = c_size_t(), c_size_t()
+        pend, act = c_int(), c_int()
+        lib().nn_server_stats(self.h, ctypes.byref(used), ctypes.byref(peak), ctypes.byref(pend), ctypes.byref(act))
+        return {"arena_used": used.value, "arena_peak": peak.value, "pending": pend.value, "active": act.value}
+
+    def close(self):
+        if self.h:
+            lib().nn_server_destroy(self.h)
+            self.h = None

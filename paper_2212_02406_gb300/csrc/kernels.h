@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "../../include/nn.h"
+
 namespace nn {
 
 // Epilogue modes of the GEMM kernels.
@@ -69,5 +71,10 @@ int reduce_rms(cudaStream_t st, const double* partial, int count, double scale, 
 // Preconditioners: write X0 (n x n FP64, ldx). scratch holds >= 4 doubles.
 int precond_fill(cudaStream_t st, const double* A, int64_t lda, int n, int kind, double scalar, double* X0,
                  int64_t ldx, double* scratch);
+
+// ---- dense NN on device buffers (nn_dense.cu), shared with the serving runtime ---------------
+int check_opts(const nn_opts* o, int64_t n);
+int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int64_t ldx0, const nn_opts* opts,
+                  double* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_size, cudaStream_t st);
 
 }  // namespace nn

@@ -471,6 +471,8 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
   return NN_OK;
 }
 
+}  // namespace
+
 int check_opts(const nn_opts* o, int64_t n) {
   if (o == nullptr) return NN_ERR_ARG;
   if (o->depth < 1 || o->depth > 16) return NN_ERR_ARG;
@@ -539,7 +541,6 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
   return res->status;
 }
 
-}  // namespace
 }  // namespace nn
 
 using namespace nn;

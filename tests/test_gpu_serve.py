@@ -1,0 +1,108 @@
+"""GPU tests of the serving runtime (continuous batching of NN inversions and solves).
+
+* Every request's result is the same alone and in the mix: the kernels are deterministic
+  (static tile schedules, fixed reduction orders), so a request run by itself and the same
+  request run among concurrent ones on other streams give identical bits.
+* Results are correct: the returned X has a small FP64-evaluated residual, and Y = X B solves
+  A Y = B to within N s (since A Y - B = -(I - A X) B).
+* The arena budget is never exceeded; a request that can never fit is refused at submission.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nn():
+    from paper_2212_02406_gb300 import abi, build
+
+    build.build()
+    abi.lib()
+    return abi
+
+
+def _requests(count, seed=0, n_max=600):
+    reqs = synth.request_stream(count, rate_per_s=1000.0, seed=seed, n_max=n_max, max_rhs=8)
+    out = []
+    for r in reqs:
+        a, q, lam = synth.spd_spectrum(r.n, r.kappa, seed=r.seed)
+        b = synth.rng(r.seed + 1).standard_normal((r.n, r.nrhs))
+        out.append((r, np.ascontiguousarray(a), np.ascontiguousarray(b)))
+    return out
+
+
+def _run(nn, reqs, max_active, arena_bytes=None, stagger=0.0):
+    import torch
+
+    need = max(nn.nn_server_request_bytes(r.n, r.nrhs, "f32" if r.dtype == "f32" else "mixed_bf16")
+               for r, _, _ in reqs)
+    arena = torch.empty(int(arena_bytes or 8 * need), dtype=torch.uint8, device="cuda")
+    srv = nn.Server(arena, max_active=max_active, depth=2, tol=1e-6, max_nests=40)
+    outs = {}
+    try:
+        for r, a, b in reqs:
+            y = np.empty_like(b)
+            x = np.empty_like(a)
+            dt = "f32" if r.dtype == "f32" else "mixed_bf16"
+            assert srv.submit(r.rid, a, B=b, Y=y, X=x, dtype=dt, precond="trace") == nn.NN_OK
+            outs[r.rid] = (x, y)
+            if stagger:
+                time.sleep(stagger)
+        assert srv.wait_idle(300.0) == nn.NN_OK
+        comps = {c["id"]: c for c in srv.poll(1024)}
+        stats = srv.stats()
+    finally:
+        srv.close()
+    return outs, comps, stats, arena.numel()
+
+
+def test_alone_equals_mix(nn):
+    reqs = _requests(10, seed=1)
+    alone, comps1, _, _ = _run(nn, reqs, max_active=1)
+    mixed, comps2, _, _ = _run(nn, reqs, max_active=4, stagger=0.002)
+    for r, a, b in reqs:
+        assert comps1[r.rid]["status"] == comps2[r.rid]["status"]
+        assert comps1[r.rid]["nests"] == comps2[r.rid]["nests"]
+        xa, ya = alone[r.rid]
+        xm, ym = mixed[r.rid]
+        assert np.array_equal(xa, xm) and np.array_equal(ya, ym), r.rid
+
+
+def test_results_are_correct(nn):
+    reqs = _requests(8, seed=2)
+    outs, comps, _, _ = _run(nn, reqs, max_active=3)
+    for r, a, b in reqs:
+        c = comps[r.rid]
+        assert c["status"] in (nn.NN_OK, nn.NN_ERR_NOT_CONVERGED), c
+        x, y = outs[r.rid]
+        s64 = np.linalg.norm(np.eye(r.n) - a @ x) / r.n
+        assert s64 < 1e-4, (r.rid, r.n, r.kappa, r.dtype, s64, c)
+        # A Y - B = -(I - A X) B, so the solve's relative residual is at most ||I - A X||_F = N s
+        rel = np.linalg.norm(a @ y - b) / np.linalg.norm(b)
+        assert rel <= r.n * s64 * 1.01 + 1e-12, (rel, s64)
+        assert np.allclose(y, x @ b, rtol=1e-10, atol=1e-12 * np.abs(y).max())
+        assert c["t_submit"] <= c["t_start"] <= c["t_done"]
+
+
+def test_budget_respected_and_oversize_refused(nn):
+    import torch
+
+    reqs = _requests(6, seed=3, n_max=300)
+    sizes = [nn.nn_server_request_bytes(r.n, r.nrhs, "f32" if r.dtype == "f32" else "mixed_bf16")
+             for r, _, _ in reqs]
+    budget = int(max(sizes) * 1.5)
+    outs, comps, stats, cap = _run(nn, reqs, max_active=4, arena_bytes=budget)
+    assert len(comps) == len(reqs)
+    assert stats["arena_peak"] <= cap and stats["arena_used"] == 0
+    arena = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    srv = nn.Server(arena, max_active=1)
+    try:
+        a = np.eye(512)
+        assert srv.submit(99, a, dtype="f64") == nn.NN_ERR_OOM_BUDGET
+    finally:
+        srv.close()
