@@ -39,26 +39,31 @@ enum : int { BM_RESID = 0, BM_ADD = 1 };
 
 // out = (mode RESID) I - P Q  or  (mode ADD) D + P Q, for a U x U complex group tile.
 // Thread (ti, tj) of the TG x TG group owns rows ti + a TG and columns tj + b TG.
-template <int TG, int T>
-__device__ __forceinline__ float group_gemm(int U, int ti, int tj, const float2* __restrict__ P,
+// UC > 0 fixes U = UC = T * TG at compile time (no bounds tests, static addressing, unrolled
+// k loop); UC = 0 handles any U <= T * TG.
+template <int TG, int T, int UC>
+__device__ __forceinline__ float group_gemm(int U_rt, int ti, int tj, const float2* __restrict__ P,
                                             const float2* __restrict__ Q, float2* __restrict__ out,
                                             const float2* __restrict__ D, int mode) {
+  const int U = UC > 0 ? UC : U_rt;
+  constexpr bool exact = UC > 0 && UC == T * TG;
   float2 acc[T][T];
 #pragma unroll
   for (int a = 0; a < T; ++a)
 #pragma unroll
     for (int b = 0; b < T; ++b) acc[a][b] = make_float2(0.f, 0.f);
+#pragma unroll(UC > 0 ? 8 : 1)
   for (int k = 0; k < U; ++k) {
     float2 pa[T], qb[T];
 #pragma unroll
     for (int a = 0; a < T; ++a) {
       const int i = ti + a * TG;
-      pa[a] = i < U ? P[i * U + k] : make_float2(0.f, 0.f);
+      pa[a] = (exact || i < U) ? P[i * U + k] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int b = 0; b < T; ++b) {
       const int j = tj + b * TG;
-      qb[b] = j < U ? Q[k * U + j] : make_float2(0.f, 0.f);
+      qb[b] = (exact || j < U) ? Q[k * U + j] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int a = 0; a < T; ++a)
@@ -74,11 +79,11 @@ __device__ __forceinline__ float group_gemm(int U, int ti, int tj, const float2*
 #pragma unroll
   for (int a = 0; a < T; ++a) {
     const int i = ti + a * TG;
-    if (i >= U) continue;
+    if (!exact && i >= U) continue;
 #pragma unroll
     for (int b = 0; b < T; ++b) {
       const int j = tj + b * TG;
-      if (j >= U) continue;
+      if (!exact && j >= U) continue;
       float2 v;
       if (mode == BM_RESID) {
         v = make_float2((i == j ? 1.f : 0.f) - acc[a][b].x, -acc[a][b].y);
@@ -122,7 +127,7 @@ __device__ __forceinline__ void group_sum(float v, int g, int lt, int nthr, floa
   __syncthreads();
 }
 
-template <int TG, int T>
+template <int TG, int T, int UC>
 __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, float2* smem, float* red_warp,
                              float* red_grp) {
   constexpr int NTHR = TG * TG;
@@ -165,7 +170,7 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
   int st = NN_OK;
   for (int k = 0; k <= p.nests; ++k) {
     float ss = 0.f;
-    if (!frozen) ss = group_gemm<TG, T>(U, ti, tj, Ab, Xb, Rb, nullptr, BM_RESID);
+    if (!frozen) ss = group_gemm<TG, T, UC>(U, ti, tj, Ab, Xb, Rb, nullptr, BM_RESID);
     group_sum(ss, g < groups ? g : 0, lt, NTHR, red_warp, red_grp);
     if (!frozen) {
       const float s = sqrtf(red_grp[g]) / float(U);
@@ -181,12 +186,12 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
     float2* t_cur = Rb;
     for (int j = 1; j < p.depth; ++j) {
       float2* dst = (t_cur == Tb) ? Wb : Tb;
-      if (!frozen) group_gemm<TG, T>(U, ti, tj, Rb, t_cur, dst, Rb, BM_ADD);
+      if (!frozen) group_gemm<TG, T, UC>(U, ti, tj, Rb, t_cur, dst, Rb, BM_ADD);
       __syncthreads();
       t_cur = dst;
     }
     float2* xdst = (t_cur == Wb) ? Tb : Wb;
-    if (!frozen) group_gemm<TG, T>(U, ti, tj, Xb, t_cur, xdst, Xb, BM_ADD);
+    if (!frozen) group_gemm<TG, T, UC>(U, ti, tj, Xb, t_cur, xdst, Xb, BM_ADD);
     __syncthreads();
     if (!frozen) {
       // the old X buffer becomes free: keep five distinct buffers for the next nest
@@ -210,16 +215,34 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
 
 template <int TG>
 __device__ void dispatch_tile(const BatchedParams& p, int U, int start, int cnt, float2* smem, float* rw, float* rg) {
+  // sizes with a compile-time path: the massive-MIMO user counts
+  if (TG == 8) {
+    switch (U) {
+      case 8: process_item<TG, 1, 8>(p, U, start, cnt, smem, rw, rg); return;
+      case 16: process_item<TG, 2, 16>(p, U, start, cnt, smem, rw, rg); return;
+      case 24: process_item<TG, 3, 24>(p, U, start, cnt, smem, rw, rg); return;
+      case 32: process_item<TG, 4, 32>(p, U, start, cnt, smem, rw, rg); return;
+      default: break;
+    }
+  } else {
+    switch (U) {
+      case 16: process_item<TG, 1, 16>(p, U, start, cnt, smem, rw, rg); return;
+      case 32: process_item<TG, 2, 32>(p, U, start, cnt, smem, rw, rg); return;
+      case 48: process_item<TG, 3, 48>(p, U, start, cnt, smem, rw, rg); return;
+      case 64: process_item<TG, 4, 64>(p, U, start, cnt, smem, rw, rg); return;
+      default: break;
+    }
+  }
   const int t = (U + TG - 1) / TG;
   switch (t) {
-    case 1: process_item<TG, 1>(p, U, start, cnt, smem, rw, rg); break;
-    case 2: process_item<TG, 2>(p, U, start, cnt, smem, rw, rg); break;
-    case 3: process_item<TG, 3>(p, U, start, cnt, smem, rw, rg); break;
-    case 4: process_item<TG, 4>(p, U, start, cnt, smem, rw, rg); break;
-    case 5: if (TG == 8) process_item<TG, 5>(p, U, start, cnt, smem, rw, rg); break;
-    case 6: if (TG == 8) process_item<TG, 6>(p, U, start, cnt, smem, rw, rg); break;
-    case 7: if (TG == 8) process_item<TG, 7>(p, U, start, cnt, smem, rw, rg); break;
-    case 8: if (TG == 8) process_item<TG, 8>(p, U, start, cnt, smem, rw, rg); break;
+    case 1: process_item<TG, 1, 0>(p, U, start, cnt, smem, rw, rg); break;
+    case 2: process_item<TG, 2, 0>(p, U, start, cnt, smem, rw, rg); break;
+    case 3: process_item<TG, 3, 0>(p, U, start, cnt, smem, rw, rg); break;
+    case 4: process_item<TG, 4, 0>(p, U, start, cnt, smem, rw, rg); break;
+    case 5: if (TG == 8) process_item<TG, 5, 0>(p, U, start, cnt, smem, rw, rg); break;
+    case 6: if (TG == 8) process_item<TG, 6, 0>(p, U, start, cnt, smem, rw, rg); break;
+    case 7: if (TG == 8) process_item<TG, 7, 0>(p, U, start, cnt, smem, rw, rg); break;
+    case 8: if (TG == 8) process_item<TG, 8, 0>(p, U, start, cnt, smem, rw, rg); break;
     default: break;
   }
 }

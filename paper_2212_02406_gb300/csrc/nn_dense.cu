@@ -427,6 +427,19 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
     }
     const int hp = level_upd_pieces(level);
     x_frob_prev = x_frob;
+    // Predict s_{k+1} from the observed order-(L+1) contraction,
+    // log(s_{k+1}/s_k) ~ (L+1) log(s_k/s_{k-1}), and raise the level of the next residual now
+    // if it will fall under this level's floor (or under tol), instead of measuring it at the
+    // old level first and again at the new one.
+    int next_level = level;
+    if (k >= 1 && level < 3 && res->history[k - 1] > 0) {
+      const double ratio = s / res->history[k - 1];
+      if (ratio > 0 && ratio < 1) {
+        const double s_pred = s * pow(ratio, double(o.depth + 1));
+        while (next_level < 3 && s_pred < 8.0 * level_floor(next_level, c)) ++next_level;
+        if (o.tol > 0 && s_pred < o.tol && next_level < 3) next_level = 3;
+      }
+    }
     // Horner: T_1 = R (its column pieces), T_{j+1} = R + R T_j.
     __nv_bfloat16* const* t_cur = w.r_col;
     for (int j = 1; j < o.depth; ++j) {
@@ -462,6 +475,7 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
       res->launches += 1;
     }
     cur ^= 1;
+    level = next_level;
   }
   *final_idx = cur;
   if (timer.on) {

@@ -4,8 +4,9 @@
 //     X = D^-1 prod_{j=0}^{k-1} ( sum_{n=0}^{L} P^{n (L+1)^j} ) B,     P = I - A D^-1.
 // D^-1 is folded into the stored values once (A' = A D^-1, so P v = v - A' v), and the chain
 // runs as (L+1)^k - 1 sparse products. Each product is HBM-bound: the kernel streams a
-// contiguous slice of (val, col) into shared memory with coalesced loads (one block = 256
-// consecutive rows), then each thread reduces its own row; the x gathers hit L2.
+// contiguous slice of (val, col) into shared memory with coalesced streaming loads (one block =
+// 256 consecutive rows), then each thread reduces its own row; the x gathers hit L2 and use
+// plain global loads (the read-only path is the texture pipeline, four requests per cycle).
 //
 // Fused variants: the last product of each block of (L+1)^j products adds its result into
 // the factor accumulator (acc_out = acc_in + y, element-wise), and the last block of a factor
@@ -45,20 +46,57 @@ spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
 #pragma unroll
   for (int r = 0; r < SP_MAXR; ++r) sum[r] = T(0);
 
+  constexpr int PER = SP_CHUNK / SP_ROWS;
   for (int base = e_begin; base < e_end; base += SP_CHUNK) {
     const int cnt = min(SP_CHUNK, e_end - base);
-    for (int i = tid; i < cnt; i += SP_ROWS) {
-      sval[i] = val[base + i];
-      scol[i] = col[base + i];
+    // Issue every load of the slice before any shared-memory store, so each thread has PER
+    // independent requests in flight; the matrix streams through (evict-first) and leaves
+    // L2 to the vector, which the gathers below reuse across rows.
+    T vv[PER];
+    int cc[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int i = tid + q * SP_ROWS;
+      if (i < cnt) {
+        vv[q] = __ldcs(val + base + i);
+        cc[q] = __ldcs(col + base + i);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int i = tid + q * SP_ROWS;
+      if (i < cnt) {
+        sval[i] = vv[q];
+        scol[i] = cc[q];
+      }
     }
     __syncthreads();
     const int lo = max(my_b, base), hi = min(my_e, base + cnt);
-    for (int e = lo; e < hi; ++e) {
+    int e = lo;
+    // four gathers in flight per step
+    for (; e + 4 <= hi; e += 4) {
+      const T a0 = sval[e - base], a1 = sval[e + 1 - base], a2 = sval[e + 2 - base], a3 = sval[e + 3 - base];
+      const int c0 = scol[e - base], c1 = scol[e + 1 - base], c2 = scol[e + 2 - base], c3 = scol[e + 3 - base];
+#pragma unroll
+      for (int r = 0; r < SP_MAXR; ++r) {
+        if (r < nrhs) {
+          const T* vr = v + r * ldv;
+          // plain cached global loads (ld.global.ca): the non-coherent path goes through the
+          // texture pipeline, which accepts only four threads' requests per cycle
+          const T x0 = __ldca(vr + c0), x1 = __ldca(vr + c1), x2 = __ldca(vr + c2), x3 = __ldca(vr + c3);
+          sum[r] = fma(a0, x0, sum[r]);
+          sum[r] = fma(a1, x1, sum[r]);
+          sum[r] = fma(a2, x2, sum[r]);
+          sum[r] = fma(a3, x3, sum[r]);
+        }
+      }
+    }
+    for (; e < hi; ++e) {
       const T a = sval[e - base];
       const int c = scol[e - base];
 #pragma unroll
       for (int r = 0; r < SP_MAXR; ++r)
-        if (r < nrhs) sum[r] = fma(a, __ldg(v + c + r * ldv), sum[r]);
+        if (r < nrhs) sum[r] = fma(a, __ldca(v + c + r * ldv), sum[r]);
     }
     __syncthreads();
   }
@@ -74,7 +112,7 @@ spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
         ss_r = fma(double(ri), double(ri), ss_r);
         ss_b = fma(double(bi), double(bi), ss_b);
       } else {
-        const T yi = v[row + r * ldv] - sum[r];
+        const T yi = __ldca(v + row + r * ldv) - sum[r];
         if (mode != SP_ACC) y[row + r * ldy] = yi;
         if (mode != SP_Y) acc_out[row + r * ld_acc] = acc_in[row + r * ld_acc] + yi;
       }
