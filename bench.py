@@ -51,13 +51,14 @@ def parse_args():
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--kappa", type=float, default=1e2)
     ap.add_argument("--depth", type=int, default=2)
-    ap.add_argument("--dtype", default="mixed_bf16", choices=["mixed_bf16", "f32", "f64"])
+    ap.add_argument("--dtype", default="mixed_bf16", choices=["mixed_bf16", "f32", "f64", "f64_df"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--damping", type=float, default=1.0 / 128.0)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--max-active", type=int, default=8)
+    ap.add_argument("--gemm-variant", type=int, default=0, choices=[0, 1, 2, 3], help="0 auto, 1 single-CTA tiles, 2 CTA pairs with multicast, 3 2-SM MMA")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -156,6 +157,7 @@ def run_dense(args, rank, world, local_rank):
 
     build.build()
     abi.lib()
+    abi.nn_set_gemm_variant(args.gemm_variant)
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     n = args.n
@@ -214,7 +216,9 @@ def run_dense(args, rank, world, local_rank):
     if tc_launches > 0 and tc_ms > 0:
         achieved = tc_flops / (tc_ms / 1e3) / 1e12
         peak = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
-        roofline = {"kernel": "nn::tc::gemm_tc_kernel", "bound": "tensor", "achieved": round(achieved, 2),
+        kernel = {1: "nn::tc::gemm_tc_kernel", 2: "nn::tc::gemm_tc_pair_kernel"}.get(args.gemm_variant,
+                                                                                 "nn::tc::gemm_tc_2sm_kernel")
+        roofline = {"kernel": kernel, "bound": "tensor", "achieved": round(achieved, 2),
                     "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                     "peak_source": f"{peak_src} bf16 burst", "launches": tc_launches,
                     "avg_launch_ms": round(tc_ms / tc_launches, 4),
@@ -279,6 +283,8 @@ def run_dense(args, rank, world, local_rank):
                                f"depth {args.depth}, eps={args.tol:g}",
                    "n": n, "kappa": args.kappa, "depth": args.depth, "tol": args.tol, "dtype": args.dtype,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "gemm_tiling": {0: "auto (2-SM MMA, cta_group::2)", 1: "single-CTA tiles",
+                                   2: "CTA pairs with TMA multicast", 3: "2-SM MMA (cta_group::2)"}[args.gemm_variant],
                    "l2": "inputs larger than L2: A fp64 512 MiB, BF16 operands 128 MiB each per GEMM"},
         "status_ok": ok, "nests": last["nests"], "residual": last["residual"], "pieces": last["pieces"],
         "gemms_per_step": last["gemms"], "hw_tflops_per_step": round(last["hw_flops"] / 1e12, 3),
@@ -326,7 +332,10 @@ def run_sparse(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     grid, depth, nests = 2048, 2, 5
-    dtype = np.float64 if args.dtype != "f32" else np.float32
+    # native FP64 by default; --dtype f32 runs FP32 data and arithmetic, --dtype f64_df FP64 data
+    # in double-float arithmetic on the FP32 pipes
+    kind = {"f32": "f32", "f64_df": "f64_df"}.get(args.dtype, "f64")
+    dtype = np.float32 if kind == "f32" else np.float64
     m = synth.laplacian_5pt(grid, shift=0.5, dtype=dtype)
     b = synth.gaussian_rhs(m.n, 1, seed=args.seed + rank, dtype=dtype)
     rp = torch.from_numpy(m.row_ptr).to(dev)
@@ -334,10 +343,11 @@ def run_sparse(args, rank, world, local_rank):
     val = torch.from_numpy(m.val).to(dev)
     B = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev)
     X = torch.empty_like(B)
-    ws = abi.csr_workspace(m.n, m.nnz, 1, "f64" if dtype == np.float64 else "f32", device=dev)
+    ws = abi.csr_workspace(m.n, m.nnz, 1, kind, device=dev)
     stream = torch.cuda.current_stream(dev)
+    dfl = kind == "f64_df"
     for _ in range(args.warmup):
-        st, res = abi.nn_solve_csr(rp, col, val, B, depth, nests, 0.0, X, ws, stream)
+        st, res = abi.nn_solve_csr(rp, col, val, B, depth, nests, 0.0, X, ws, stream, double_float=dfl)
         assert st == abi.NN_OK, (st, res)
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(local_rank)
@@ -348,7 +358,7 @@ def run_sparse(args, rank, world, local_rank):
     ev0.record(stream)
     launches = 0
     for _ in range(args.steps):
-        st, res = abi.nn_solve_csr(rp, col, val, B, depth, nests, 0.0, X, ws, stream)
+        st, res = abi.nn_solve_csr(rp, col, val, B, depth, nests, 0.0, X, ws, stream, double_float=dfl)
         launches += res["launches"]
     ev1.record(stream)
     torch.cuda.synchronize(dev)
@@ -362,7 +372,9 @@ def run_sparse(args, rank, world, local_rank):
     return {"metric": "HBM GB/s of the sparse NN chain (5-point Laplacian 2048^2, depth 2)",
             "value": round(gbs * world, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if vb == 8 else "f32", "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": {"f64_df": "f64 data, double-float arithmetic (FP32 pipes)", "f64": "f64",
+                      "f32": "f32"}[kind], "data": "synthetic",
             "config": {"workload": f"2-D 5-point Laplacian {grid}x{grid} + 0.5 I, CSR, b ~ N(0,1), Jacobi X0, "
                                    f"depth {depth}, {nests} factors ({products} sparse products)",
                        "n": m.n, "nnz": m.nnz, "l2": "matrix larger than L2 (streams every product)"},

@@ -50,10 +50,13 @@ typedef enum nn_status {
 typedef enum nn_dtype {
   NN_F64 = 0,        /* every GEMM and epilogue in FP64 (CUDA cores)                           */
   NN_F32 = 1,        /* every GEMM and epilogue in FP32 (CUDA cores)                           */
-  NN_MIXED_BF16 = 2  /* tcgen05 tensor-core GEMMs on BF16 operand pieces, FP32 accumulate in
+  NN_MIXED_BF16 = 2, /* tcgen05 tensor-core GEMMs on BF16 operand pieces, FP32 accumulate in
                         TMEM, FP32 master copy of X. Bulk nests use one BF16 piece per operand;
                         refine nests evaluate R_k with three pieces (six products, FP32-level)
                         and the Horner/update GEMMs with two pieces (three products).        */
+  NN_F64_DF = 3      /* sparse chain only: FP64 data and results, arithmetic in double-float
+                        (hi + lo FP32 pairs, 49-bit significand) on the FP32 pipes; values must
+                        lie within the FP32 exponent range                                   */
 } nn_dtype;
 
 /* ---- starting matrix X_0 = Theta (Section II-A, Eq. (normalization), Appendix 1) --------- */
@@ -61,7 +64,11 @@ typedef enum nn_pc {
   NN_PC_PAN_SCHREIBER = 0, /* X_0 = A^T / (||A||_1 ||A||_inf)                                  */
   NN_PC_SCALAR = 1,        /* X_0 = scalar * I                                                */
   NN_PC_TRACE = 2,         /* X_0 = I / Tr(A)   (Theta_1 of Eq. (trace))                        */
-  NN_PC_JACOBI = 3         /* X_0 = scalar * diag(A)^-1 (scalar = 1 for plain Jacobi)          */
+  NN_PC_JACOBI = 3,        /* X_0 = scalar * diag(A)^-1 (scalar = 1 for plain Jacobi)          */
+  NN_PC_THETA2 = 4         /* X_0 = Theta_2(k) I, k = scalar power steps from v = (1, ..., 1):
+                              Theta_2(k) = (k/(k+1)) ||A^k v||^2 / <A^k v, A^(k+1) v>, Eq. (trace)
+                              read as an inverse Rayleigh quotient (the printed ratio of squared
+                              norms has dimension 1/lambda^2); needs A positive definite      */
 } nn_pc;
 
 #define NN_MAX_HISTORY 65
@@ -98,14 +105,24 @@ typedef struct nn_result {
   double tc_flops;                 /* 2 Np^3 per BF16 product pass of those launches               */
 } nn_result;
 
+/* Tensor-core GEMM tiling for the NN_MIXED_BF16 chain (a process-wide tuning knob; the
+ * element-wise outputs of every variant are bitwise identical, only the per-CTA grouping of the
+ * residual's sum of squares differs): 0 = automatic (variant 3 when the padded size is a
+ * multiple of 256, else 1), 1 = single-CTA 128 x 256 tiles, 2 = CTA pairs in clusters of two
+ * sharing each B^T tile through TMA multicast, 3 = CTA pairs issuing one 256 x 256 MMA over
+ * both SMs' shared memory and TMEM (tcgen05 cta_group::2). Variants 2 and 3 need a padded size
+ * that is a multiple of 256; calls that cannot use the chosen one return NN_ERR_UNSUPPORTED.
+ * Returns NN_ERR_ARG for other values. Not thread-safe against concurrent inversions. */
+int nn_set_gemm_variant(int variant);
+
 /* Bytes of device workspace nn_invert / nn_residual need for an N x N problem of `dtype`
  * (256-byte aligned internally). Returns 0 for invalid arguments. */
 size_t nn_workspace_bytes(int64_t n, int dtype);
 
 /* X_0 for A (device, FP64, row-major N x N with leading dimension lda >= n) into X0 (device,
  * FP64, row-major, leading dimension ldx >= n). kind is an nn_pc; `scalar` is the alpha of
- * NN_PC_SCALAR and the damping of NN_PC_JACOBI. Needs nn_workspace_bytes(n, NN_F64) of
- * workspace. Section II-A (Eq. (normalization), Eq. (trace)); Appendix 1 (matrix Theta). */
+ * NN_PC_SCALAR, the damping of NN_PC_JACOBI and the power-step count k (1..1024) of
+ * NN_PC_THETA2. Needs nn_workspace_bytes(n, NN_F64) of workspace. Section II-A (Eq. (normalization), Eq. (trace)); Appendix 1 (matrix Theta). */
 int nn_init_precond(const double* A, int64_t n, int64_t lda, int kind, double scalar,
                     double* X0, int64_t ldx, void* workspace, size_t ws_bytes, void* stream);
 
@@ -137,7 +154,9 @@ int nn_residual(const double* A, int64_t lda, const double* X, int64_t ldx, int6
  * sparse products without forming any dense matrix. (Algorithm 2 prints the L + 1 = 2 case.)
  *
  * A: CSR, row_ptr[n+1] and col[nnz] int32 (device), val[nnz] (device) of `dtype` (NN_F64 or
- * NN_F32); columns in any order; every row needs a nonzero diagonal (else NN_ERR_ARG).
+ * NN_F32; NN_F64_DF takes FP64 data and computes in double-float, which on GB300 keeps the
+ * chain bound by HBM instead of by the narrow FP64 pipe); columns in any order; every row needs
+ * a nonzero diagonal (else NN_ERR_ARG).
  * B, X: device, column-major n x nrhs of `dtype`, leading dimensions ldb, ldx >= n.
  * tol > 0: after each factor j the relative residual ||B - A X_j||_F / ||B||_F (one extra
  * sparse product) goes to res->history[j] and the chain stops at the first factor below tol

@@ -39,7 +39,9 @@ from .dense import (  # noqa: F401
     precond_jacobi,
     precond_pan_schreiber,
     precond_scalar,
+    precond_theta2,
     precond_trace,
     residual,
+    theta2,
     rms_frob,
 )

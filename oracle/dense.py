@@ -58,6 +58,28 @@ def precond_trace(w: np.ndarray) -> np.ndarray:
     return np.eye(n, dtype=w.dtype) * (1.0 / np.trace(w).real)
 
 
+def theta2(w: np.ndarray, k: int, v: np.ndarray) -> float:
+    """Theta_2(k) of Eq. (trace), read as (k/(k+1)) ||W^k v||^2 / <W^k v, W^(k+1) v>.
+
+    The printed ratio ||W^k v||^2 / ||W^(k+1) v||^2 has the dimension of 1/lambda^2 and
+    cannot normalise W; the inverse Rayleigh quotient of the k-th power iterate has dimension
+    1/lambda, tends to 1/lambda_max from above (for PD W and a start v with a component on
+    the top eigenvector), and with the paper's safety factor k/(k+1) gives
+    Theta_2 lambda_max <= 1 up to the iteration's error, so rho(I - Theta_2 W) < 1.
+    The k products W^j v are taken one after another from the given start vector.
+    """
+    u = np.array(v, dtype=w.dtype, copy=True)
+    for _ in range(k):
+        u = w @ u
+    wu = w @ u
+    return float((k / (k + 1.0)) * np.vdot(u, u).real / np.vdot(u, wu).real)
+
+
+def precond_theta2(w: np.ndarray, k: int, v: np.ndarray) -> np.ndarray:
+    """X_0 = Theta_2(k) I, Eq. (trace)."""
+    return np.eye(w.shape[0], dtype=w.dtype) * theta2(w, k, v)
+
+
 def precond_scalar(n: int, alpha: float, dtype=np.float64) -> np.ndarray:
     """X_0 = alpha I: a scalar Theta (Appendix 1 allows any Theta with ||I - Theta W||_2 < 1)."""
     return np.eye(n, dtype=dtype) * alpha

@@ -27,10 +27,10 @@ STATUS_NAMES = {0: "ok", 1: "arg", 2: "diverged", 3: "not_converged", 4: "oom_bu
                 6: "cuda", 7: "unsupported", 8: "too_large"}
 NN_RESIDUAL_NOALLOC_MAX_N = 1440
 
-NN_F64, NN_F32, NN_MIXED_BF16 = 0, 1, 2
-DTYPES = {"f64": NN_F64, "f32": NN_F32, "mixed_bf16": NN_MIXED_BF16}
-NN_PC_PAN_SCHREIBER, NN_PC_SCALAR, NN_PC_TRACE, NN_PC_JACOBI = 0, 1, 2, 3
-PRECONDS = {"pan_schreiber": 0, "scalar": 1, "trace": 2, "jacobi": 3}
+NN_F64, NN_F32, NN_MIXED_BF16, NN_F64_DF = 0, 1, 2, 3
+DTYPES = {"f64": NN_F64, "f32": NN_F32, "mixed_bf16": NN_MIXED_BF16, "f64_df": NN_F64_DF}
+NN_PC_PAN_SCHREIBER, NN_PC_SCALAR, NN_PC_TRACE, NN_PC_JACOBI, NN_PC_THETA2 = 0, 1, 2, 3, 4
+PRECONDS = {"pan_schreiber": 0, "scalar": 1, "trace": 2, "jacobi": 3, "theta2": 4}
 NN_MAX_HISTORY = 65
 
 
@@ -73,6 +73,7 @@ _LIB = None
 
 # Every symbol include/nn.h declares, with its ctypes signature.
 _SIGNATURES = {
+    "nn_set_gemm_variant": (c_int, [c_int]),
     "nn_workspace_bytes": (c_size_t, [c_int64, c_int]),
     "nn_workspace_bytes_host": (c_size_t, [c_int64, c_int]),
     "nn_init_precond": (c_int, [c_void_p, c_int64, c_int64, c_int, c_double, c_void_p, c_int64, c_void_p, c_size_t,
@@ -171,6 +172,11 @@ def workspace(n: int, dtype="f64", host=False, device=None):
 
 # ---- entry points (same names as the C ABI) -------------------------------------------
 
+def nn_set_gemm_variant(variant: int) -> int:
+    """0 automatic, 1 single-CTA tiles, 2 CTA pairs with multicast, 3 2-SM MMA (tensor-core GEMM tiling)."""
+    return int(lib().nn_set_gemm_variant(int(variant)))
+
+
 def nn_workspace_bytes(n: int, dtype) -> int:
     d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
     return int(lib().nn_workspace_bytes(int(n), d))
@@ -258,15 +264,20 @@ def csr_workspace(n: int, nnz: int, nrhs: int, dtype, device=None):
     return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
 
 
-def nn_solve_csr(row_ptr, col, val, B, depth, nests, tol, X, workspace, stream=None):
+def nn_solve_csr(row_ptr, col, val, B, depth, nests, tol, X, workspace, stream=None, double_float=False):
     """CSR (int32 row_ptr/col, float val) on the device; B and X are (nrhs, n) row-major
-    tensors, i.e. column-major n x nrhs blocks with leading dimension n. Returns (status, result)."""
+    tensors, i.e. column-major n x nrhs blocks with leading dimension n. Returns (status, result).
+    double_float=True runs FP64 data in double-float arithmetic (NN_F64_DF)."""
     import torch
 
     for name, t in (("row_ptr", row_ptr), ("col", col)):
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()):
             raise TypeError(f"{name} must be a contiguous int32 CUDA tensor")
     d = _vec_dtype(val)
+    if double_float:
+        if d != NN_F64:
+            raise TypeError("double_float needs float64 values")
+        d = NN_F64_DF
     for name, t in (("B", B), ("X", X)):
         if not (t.is_cuda and t.dtype == val.dtype and t.dim() == 2 and t.stride(1) == 1):
             raise TypeError(f"{name} must be a (nrhs, n) row-major CUDA tensor of the value dtype")

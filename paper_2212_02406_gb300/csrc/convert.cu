@@ -1,6 +1,8 @@
 // O(N^2) kernels around the nest chain: precision splitting into BF16 pieces (row-major
 // and transposed), FP32/FP64 conversions, the starting matrix X_0 (preconditioners of
 // Section II-A and Appendix 1) and the deterministic reduction of sum(R_ij^2) partials.
+#include <utility>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -163,7 +165,48 @@ __global__ void pan_schreiber_kernel(const double* __restrict__ A, int64_t lda, 
   }
 }
 
-// Diagonal starting matrices: kind SCALAR (value), TRACE (1 / *dev), JACOBI (value / A_ii).
+// y = A x, one warp per row (coalesced row reads), FP64.
+__global__ void gemv_rows_kernel(const double* __restrict__ A, int64_t lda, int n, const double* __restrict__ x,
+                                 double* __restrict__ y) {
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s = fma(A[int64_t(row) * lda + j], x[j], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) y[row] = s;
+}
+
+__global__ void fill_value_kernel(double* __restrict__ x, int n, double v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
+// out[0] = (k/(k+1)) <u,u> / <u,w>, fixed summation order (one block).
+__global__ void theta2_kernel(const double* __restrict__ u, const double* __restrict__ w, int n, double kfac,
+                              double* out) {
+  __shared__ double a[256], b[256];
+  double x = 0, y = 0;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    x = fma(u[i], u[i], x);
+    y = fma(u[i], w[i], y);
+  }
+  a[threadIdx.x] = x;
+  b[threadIdx.x] = y;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      a[threadIdx.x] += a[threadIdx.x + s];
+      b[threadIdx.x] += b[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = kfac * a[0] / b[0];
+}
+
+// Diagonal starting matrices: kind SCALAR (value), TRACE (1 / *dev), JACOBI (value / A_ii),
+// THETA2 (*dev).
 __global__ void fill_diag_kernel(const double* __restrict__ A, int64_t lda, int n, int kind, double value,
                                  const double* dev, double* __restrict__ X, int64_t ldx) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -175,6 +218,8 @@ __global__ void fill_diag_kernel(const double* __restrict__ A, int64_t lda, int 
       v = value;
     else if (kind == NN_PC_TRACE)
       v = 1.0 / dev[0];
+    else if (kind == NN_PC_THETA2)
+      v = dev[0];
     else
       v = value / A[int64_t(i) * lda + i];
   }
@@ -233,7 +278,7 @@ int reduce_rms(cudaStream_t st, const double* partial, int count, double scale, 
 }
 
 int precond_fill(cudaStream_t st, const double* A, int64_t lda, int n, int kind, double scalar, double* X0,
-                 int64_t ldx, double* scratch) {
+                 int64_t ldx, double* scratch, double* vec_scratch) {
   if (n <= 0) return NN_ERR_ARG;
   if (kind == NN_PC_PAN_SCHREIBER) {
     NN_CUDA_TRY(cudaMemsetAsync(scratch, 0, 2 * sizeof(double), st));
@@ -248,6 +293,21 @@ int precond_fill(cudaStream_t st, const double* A, int64_t lda, int n, int kind,
   }
   if (kind == NN_PC_TRACE) {
     trace_kernel<<<1, 256, 0, st>>>(A, lda, n, scratch + 2);
+    NN_CUDA_TRY(cudaGetLastError());
+  } else if (kind == NN_PC_THETA2) {
+    // Theta_2(k) = (k/(k+1)) ||A^k v||^2 / <A^k v, A^(k+1) v>, v = ones, k = scalar
+    const int k = int(scalar);
+    if (k < 1 || vec_scratch == nullptr) return NN_ERR_ARG;
+    double* u = vec_scratch;
+    double* w = vec_scratch + n;
+    fill_value_kernel<<<(n + 255) / 256, 256, 0, st>>>(u, n, 1.0);
+    NN_CUDA_TRY(cudaGetLastError());
+    for (int it = 0; it <= k; ++it) {
+      gemv_rows_kernel<<<(n + 7) / 8, 256, 0, st>>>(A, lda, n, u, w);
+      NN_CUDA_TRY(cudaGetLastError());
+      if (it < k) std::swap(u, w);
+    }
+    theta2_kernel<<<1, 256, 0, st>>>(u, w, n, double(k) / double(k + 1), scratch + 2);
     NN_CUDA_TRY(cudaGetLastError());
   } else if (kind != NN_PC_SCALAR && kind != NN_PC_JACOBI) {
     return NN_ERR_ARG;

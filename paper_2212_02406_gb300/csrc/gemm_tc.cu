@@ -11,6 +11,16 @@
 //               piece stores (row-major and transposed), and sum(C^2) partials.
 // The two accumulators let the epilogue of tile i overlap the main loop of tile i+1.
 //
+// Three tilings of the same schedule (bitwise identical element-wise results):
+//   gemm_tc_kernel       one CTA per 128 x 256 tile, as above (any padded size, multiple of 128);
+//   gemm_tc_pair_kernel  clusters of two CTAs on vertically adjacent tiles sharing each B^T
+//                        tile through TMA multicast (halves the L2 -> SM traffic for B);
+//   gemm_tc_2sm_kernel   clusters of two CTAs computing one 256 x 256 tile with
+//                        tcgen05.mma.cta_group::2: each SM stages 32 KB per K step instead of
+//                        48 KB for the same tensor work, which lifts the per-SM shared-memory
+//                        fill rate that limits the single-CTA kernel (default where the padded
+//                        size is a multiple of 256).
+//
 // "Segments" chain several (A_s, B_s) operand pairs into the same accumulator; the split
 // precisions of the mixed path (hi/lo BF16 pieces) use them, smallest products first.
 //
@@ -78,11 +88,11 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
-  const int per_group = GROUP_M * tiles_n;
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int group, int& tm, int& tn) {
+  const int per_group = group * tiles_n;
   const int g = t / per_group;
-  const int first_m = g * GROUP_M;
-  const int gm = min(GROUP_M, tiles_m - first_m);
+  const int first_m = g * group;
+  const int gm = min(group, tiles_m - first_m);
   const int r = t - g * per_group;
   tm = first_m + r % gm;
   tn = r / gm;
@@ -109,7 +119,64 @@ __device__ __forceinline__ void store_pieces_row(__nv_bfloat16* const* pieces, i
   }
 }
 
-__global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ Params p) {
+// Epilogue of one 32-column chunk of a thread's accumulator row: applies the mode, adds the
+// squares to ss (in column order) and writes the FP32 and BF16-piece outputs.
+__device__ __forceinline__ void epilogue_chunk(const Params& p, const uint32_t (&raw)[32], int gr, int gc0,
+                                               int64_t ld, double& ss) {
+  float v[32];
+  const int64_t off = int64_t(gr) * ld + gc0;
+  if (p.mode == EPI_ADD) {
+    const float4* src = reinterpret_cast<const float4*>(p.add + off);
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4) {
+      float4 a4 = src[j4];
+      v[4 * j4 + 0] = a4.x + __uint_as_float(raw[4 * j4 + 0]);
+      v[4 * j4 + 1] = a4.y + __uint_as_float(raw[4 * j4 + 1]);
+      v[4 * j4 + 2] = a4.z + __uint_as_float(raw[4 * j4 + 2]);
+      v[4 * j4 + 3] = a4.w + __uint_as_float(raw[4 * j4 + 3]);
+    }
+  } else if (p.mode == EPI_RESIDUAL) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int gc = gc0 + j;
+      v[j] = ((gr == gc && gr < p.n_id) ? 1.0f : 0.0f) - __uint_as_float(raw[j]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(raw[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) ss = fma(double(v[j]), double(v[j]), ss);
+  if (p.out_f32 != nullptr) {
+    float4* dst = reinterpret_cast<float4*>(p.out_f32 + off);
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4) dst[j4] = make_float4(v[4 * j4], v[4 * j4 + 1], v[4 * j4 + 2], v[4 * j4 + 3]);
+  }
+  if (p.n_row > 0) store_pieces_row(p.row_pieces, p.n_row, off, v);
+  if (p.n_col > 0) {
+    float rem[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) rem[j] = v[j];
+    for (int pc = 0; pc < p.n_col; ++pc) {
+      __nv_bfloat16* dst = p.col_pieces[pc] + gr;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        __nv_bfloat16 b = __float2bfloat16_rn(rem[j]);
+        rem[j] -= __bfloat162float(b);
+        dst[int64_t(gc0 + j) * ld] = b;  // lanes write consecutive rows: 64-byte runs
+      }
+    }
+  }
+}
+
+// PAIR = false: one CTA per 128 x 256 tile. PAIR = true: CTAs run in clusters of two on
+// vertically adjacent 128 x 256 tiles that share the same 256-row B^T panel; each CTA loads its
+// own A tile and one 128-row half of the B^T tile with TMA multicast into both CTAs, so every
+// B byte crosses L2 once per pair. Each CTA's MMA thread then releases a stage on both CTAs'
+// empty barriers (multicast commit), because the stage's B half in a CTA was written by the
+// peer too.
+template <bool PAIR>
+__device__ __forceinline__ void gemm_tc_body(const Params& p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
@@ -126,10 +193,15 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 
+  const int rank = PAIR ? int(cluster_ctarank()) : 0;
+  const int unit = PAIR ? int(blockIdx.x >> 1) : int(blockIdx.x);
+  const int units = PAIR ? int(gridDim.x >> 1) : int(gridDim.x);
+  const int unit_rows = PAIR ? p.tiles_m / 2 : p.tiles_m;  // tile rows per scheduling unit row
+
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], PAIR ? 2 : 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
@@ -147,11 +219,16 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
   }
   if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
   tc_fence_before();
-  __syncthreads();
+  // PAIR: the peer's multicast loads and commits target this CTA's barriers, so both CTAs
+  // must have initialised them before either starts.
+  if (PAIR)
+    cluster_sync_all();
+  else
+    __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const int num_tiles = p.tiles_m * p.tiles_n;
+  const int num_tiles = unit_rows * p.tiles_n;
   const int kblocks = p.np / BK;
   const int total_k = p.nseg * kblocks;
 
@@ -159,18 +236,25 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      for (int t = blockIdx.x; t < num_tiles && !*abort_flag; t += gridDim.x) {
+      for (int t = unit; t < num_tiles && !*abort_flag; t += units) {
         int tm, tn;
-        tile_coords(t, p.tiles_m, p.tiles_n, tm, tn);
+        tile_coords(t, unit_rows, p.tiles_n, PAIR ? GROUP_M / 2 : GROUP_M, tm, tn);
+        if (PAIR) tm = 2 * tm + rank;
         for (int it = 0; it < total_k; ++it) {
           const int seg = it / kblocks;
           const int kb = it - seg * kblocks;
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.err)) break;
           uint8_t* sa = tiles + stage * STAGE_BYTES;
           uint8_t* sb = sa + A_TILE;
+          // PAIR: this CTA's A tile, plus its own 128-row half of B^T arriving in both CTAs;
+          // the other half arrives from the peer. Either way 48 KB land per stage.
           mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
           tma_load_2d(sa, &p.map_a[seg], kb * BK, tm * BM, &full[stage]);
-          tma_load_2d(sb, &p.map_b[seg], kb * BK, tn * BN, &full[stage]);
+          if (PAIR)
+            tma_load_2d_multicast(sb + rank * (B_TILE / 2), &p.map_b[seg], kb * BK, tn * BN + rank * (BN / 2),
+                                  &full[stage], uint16_t(0x3));
+          else
+            tma_load_2d(sb, &p.map_b[seg], kb * BK, tn * BN, &full[stage]);
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -183,7 +267,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
       int stage = 0;
       uint32_t phase = 0;
       int local = 0;
-      for (int t = blockIdx.x; t < num_tiles && !*abort_flag; t += gridDim.x, ++local) {
+      for (int t = unit; t < num_tiles && !*abort_flag; t += units, ++local) {
         const int acc = local & 1;
         const uint32_t acc_phase = (local >> 1) & 1;
         if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1u, abort_flag, p.err)) break;
@@ -205,7 +289,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
             tc_mma_bf16(d_tmem, adesc + uint64_t(2 * kk), bdesc + uint64_t(2 * kk), IDESC,
                         (it > 0 || kk > 0) ? 1u : 0u);
           }
-          tc_commit(&empty[stage]);
+          if (PAIR)
+            tc_commit_multicast(&empty[stage], uint16_t(0x3));
+          else
+            tc_commit(&empty[stage]);
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -226,13 +313,14 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
     const int64_t ld = p.np;
     double ss = 0.0;
     int local = 0;
-    for (int t = blockIdx.x; t < num_tiles; t += gridDim.x, ++local) {
+    for (int t = unit; t < num_tiles; t += units, ++local) {
       const int acc = local & 1;
       const uint32_t acc_phase = (local >> 1) & 1;
       if (!mbar_wait(&acc_full[acc], acc_phase, abort_flag, p.err)) break;
       tc_fence_after();
       int tm, tn;
-      tile_coords(t, p.tiles_m, p.tiles_n, tm, tn);
+      tile_coords(t, unit_rows, p.tiles_n, PAIR ? GROUP_M / 2 : GROUP_M, tm, tn);
+      if (PAIR) tm = 2 * tm + rank;
       const int gr = tm * BM + row_in_tile;
       for (int c = 0; c < BN / 32; ++c) {
         const int gc0 = tn * BN + c * 32;
@@ -240,50 +328,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
         uint32_t raw[32];
         tmem_ld_32x32b_x32(tmem_base + uint32_t(acc * BN + c * 32) + (uint32_t(q * 32) << 16), raw);
         tmem_ld_wait();
-        float v[32];
-        const int64_t off = int64_t(gr) * ld + gc0;
-        if (p.mode == EPI_ADD) {
-          const float4* src = reinterpret_cast<const float4*>(p.add + off);
-#pragma unroll
-          for (int j4 = 0; j4 < 8; ++j4) {
-            float4 a4 = src[j4];
-            v[4 * j4 + 0] = a4.x + __uint_as_float(raw[4 * j4 + 0]);
-            v[4 * j4 + 1] = a4.y + __uint_as_float(raw[4 * j4 + 1]);
-            v[4 * j4 + 2] = a4.z + __uint_as_float(raw[4 * j4 + 2]);
-            v[4 * j4 + 3] = a4.w + __uint_as_float(raw[4 * j4 + 3]);
-          }
-        } else if (p.mode == EPI_RESIDUAL) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int gc = gc0 + j;
-            v[j] = ((gr == gc && gr < p.n_id) ? 1.0f : 0.0f) - __uint_as_float(raw[j]);
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(raw[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) ss = fma(double(v[j]), double(v[j]), ss);
-        if (p.out_f32 != nullptr) {
-          float4* dst = reinterpret_cast<float4*>(p.out_f32 + off);
-#pragma unroll
-          for (int j4 = 0; j4 < 8; ++j4) dst[j4] = make_float4(v[4 * j4], v[4 * j4 + 1], v[4 * j4 + 2], v[4 * j4 + 3]);
-        }
-        if (p.n_row > 0) store_pieces_row(p.row_pieces, p.n_row, off, v);
-        if (p.n_col > 0) {
-          float rem[32];
-#pragma unroll
-          for (int j = 0; j < 32; ++j) rem[j] = v[j];
-          for (int pc = 0; pc < p.n_col; ++pc) {
-            __nv_bfloat16* dst = p.col_pieces[pc] + gr;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              __nv_bfloat16 b = __float2bfloat16_rn(rem[j]);
-              rem[j] -= __bfloat162float(b);
-              dst[int64_t(gc0 + j) * ld] = b;  // lanes write consecutive rows: 64-byte runs
-            }
-          }
-        }
+        epilogue_chunk(p, raw, gr, gc0, ld, ss);
       }
       tc_fence_before();
       __syncwarp();
@@ -298,9 +343,194 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
   }
 
   tc_fence_before();
-  __syncthreads();
+  // PAIR: the peer's last multicast commits land on this CTA's barriers; both CTAs leave
+  // together once every MMA of both has completed (each MMA thread drained its commits above).
+  if (PAIR)
+    cluster_sync_all();
+  else
+    __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem_base, TMEM_COLS);
+}
+
+__global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ Params p) {
+  gemm_tc_body<false>(p);
+}
+
+__global__ void __launch_bounds__(THREADS, 1) gemm_tc_pair_kernel(const __grid_constant__ Params p) {
+  gemm_tc_body<true>(p);
+}
+
+
+// ---------------------------------------------------------------------------------------
+// 2-SM variant: a CTA pair computes one 256 x 256 tile with tcgen05.mma.cta_group::2
+// (M = 256, N = 256, K = 16). Each CTA holds 128 rows of the A tile and 128 rows of the
+// B^T tile in its own shared memory (32 KB per stage instead of 48 KB), the even CTA issues
+// the MMA over both, and each CTA's TMEM receives its 128 rows of the accumulator. Both
+// CTAs' loads complete on the even CTA's full barrier; its commits release both CTAs'
+// stages and accumulators; both CTAs' epilogue warps free an accumulator on the even CTA's
+// barrier (count 8).
+constexpr int P2_STAGES = 6;
+constexpr int P2_STAGE_BYTES = A_TILE + B_TILE / 2;  // 32 KB
+constexpr int P2_SMEM_BYTES = P2_STAGES * P2_STAGE_BYTES + CTRL_BYTES + 1024;
+static_assert((2 * P2_STAGES + 5) * 8 + 8 <= 192 && 192 + 4 * 8 <= CTRL_BYTES, "control block layout");
+static_assert(P2_SMEM_BYTES <= 227 * 1024, "shared memory");
+constexpr uint32_t IDESC_P2 =
+    (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t((2 * BM) >> 4) << 24);
+
+__global__ void __launch_bounds__(THREADS, 1) gemm_tc_2sm_kernel(const __grid_constant__ Params p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_addr = smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
+  uint8_t* tiles = smem;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + P2_STAGES * P2_STAGE_BYTES);
+  uint64_t* empty = full + P2_STAGES;
+  uint64_t* acc_full = empty + P2_STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  // 17 barriers + TMEM slot + abort flag take the first 144 bytes of the control block
+  double* red = reinterpret_cast<double*>(smem + P2_STAGES * P2_STAGE_BYTES + 192);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int rank = int(cluster_ctarank());
+  const bool leader = rank == 0;
+  const int unit = int(blockIdx.x >> 1);
+  const int units = int(gridDim.x >> 1);
+  const int unit_rows = p.tiles_m / 2;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P2_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 8);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 0 && lane == 0) {
+    for (int s = 0; s < p.nseg; ++s) {
+      tma_prefetch_desc(&p.map_a[s]);
+      tma_prefetch_desc(&p.map_b[s]);
+    }
+  }
+  if (warp == 1) tmem_alloc_pair(tmem_slot, TMEM_COLS);
+  tc_fence_before();
+  cluster_sync_all();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int num_tiles = unit_rows * p.tiles_n;
+  const int kblocks = p.np / BK;
+  const int total_k = p.nseg * kblocks;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int t = unit; t < num_tiles && !*abort_flag; t += units) {
+        int tm2, tn;
+        tile_coords(t, unit_rows, p.tiles_n, GROUP_M / 2, tm2, tn);
+        for (int it = 0; it < total_k; ++it) {
+          const int seg = it / kblocks;
+          const int kb = it - seg * kblocks;
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.err)) break;
+          uint8_t* sa = tiles + stage * P2_STAGE_BYTES;
+          uint8_t* sb = sa + A_TILE;
+          if (leader) mbar_arrive_expect_tx(&full[stage], 2 * P2_STAGE_BYTES);
+          const uint32_t bar = cluster_map_shared(&full[stage], 0);
+          tma_load_2d_pair(sa, &p.map_a[seg], kb * BK, tm2 * 2 * BM + rank * BM, bar);
+          tma_load_2d_pair(sb, &p.map_b[seg], kb * BK, tn * BN + rank * (BN / 2), bar);
+          if (++stage == P2_STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && leader) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int local = 0;
+      for (int t = unit; t < num_tiles && !*abort_flag; t += units, ++local) {
+        const int acc = local & 1;
+        const uint32_t acc_phase = (local >> 1) & 1;
+        if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1u, abort_flag, p.err)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + uint32_t(acc * BN);
+        bool ok = true;
+        for (int it = 0; it < total_k; ++it) {
+          if (!mbar_wait(&full[stage], phase, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(tiles + stage * P2_STAGE_BYTES);
+          const uint64_t adesc = sw128_desc(sa);
+          const uint64_t bdesc = sw128_desc(sa + A_TILE);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            tc_mma_bf16_pair(d_tmem, adesc + uint64_t(2 * kk), bdesc + uint64_t(2 * kk), IDESC_P2,
+                             (it > 0 || kk > 0) ? 1u : 0u);
+          tc_commit_pair_multicast(&empty[stage], uint16_t(0x3));
+          if (++stage == P2_STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        tc_commit_pair_multicast(&acc_full[acc], uint16_t(0x3));
+      }
+      tc_commit_pair(drain);
+      volatile int no_abort = 0;
+      mbar_wait(drain, 0, &no_abort, p.err);
+    }
+  } else {
+    const int q = warp & 3;
+    const int row_in_tile = q * 32 + lane;
+    const int64_t ld = p.np;
+    const uint32_t leader_acc_empty[2] = {cluster_map_shared(&acc_empty[0], 0),
+                                          cluster_map_shared(&acc_empty[1], 0)};
+    double ss = 0.0;
+    int local = 0;
+    for (int t = unit; t < num_tiles; t += units, ++local) {
+      const int acc = local & 1;
+      const uint32_t acc_phase = (local >> 1) & 1;
+      if (!mbar_wait(&acc_full[acc], acc_phase, abort_flag, p.err)) break;
+      tc_fence_after();
+      int tm2, tn;
+      tile_coords(t, unit_rows, p.tiles_n, GROUP_M / 2, tm2, tn);
+      const int gr = tm2 * 2 * BM + rank * BM + row_in_tile;
+      for (int c = 0; c < BN / 32; ++c) {
+        const int gc0 = tn * BN + c * 32;
+        if (gc0 >= p.np) break;
+        uint32_t raw[32];
+        tmem_ld_32x32b_x32(tmem_base + uint32_t(acc * BN + c * 32) + (uint32_t(q * 32) << 16), raw);
+        tmem_ld_wait();
+        epilogue_chunk(p, raw, gr, gc0, ld, ss);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(leader_acc_empty[acc]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+    if (lane == 0) red[q] = ss;
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (warp == 2 && lane == 0 && p.partial != nullptr) p.partial[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+  }
+
+  tc_fence_before();
+  cluster_sync_all();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc_pair(tmem_base, TMEM_COLS);
 }
 
 }  // namespace tc
@@ -312,8 +542,42 @@ namespace {
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 int g_sms = 0;
+int g_pair_clusters = 0;  // co-resident clusters of the multicast-pair kernel (0: unavailable)
+int g_2sm_clusters = 0;   // co-resident clusters of the 2-SM MMA kernel (0: unavailable)
+int g_variant = 0;        // 0 auto (3 where possible, else 1), 1 single-CTA tiles, 2 CTA pairs with multicast, 3 2-SM MMA
 bool g_tc_ok = false;
 std::once_flag g_once;
+
+cudaLaunchConfig_t cluster_config(int grid, int smem, cudaStream_t st, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(tc::THREADS);
+  cfg.dynamicSmemBytes = size_t(smem);
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Co-resident clusters of two for a kernel (0: the kernel cannot run as clusters here).
+int max_clusters(void (*kernel)(tc::Params), int smem) {
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = cluster_config(2 * (g_sms / 2), smem, nullptr, attr);
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return clusters;
+}
 
 void init_once() {
   int dev = 0;
@@ -337,6 +601,9 @@ void init_once() {
     return;
   }
   g_tc_ok = true;
+  g_pair_clusters = max_clusters(tc::gemm_tc_pair_kernel, tc::SMEM_BYTES);
+  g_2sm_clusters = max_clusters(tc::gemm_tc_2sm_kernel, tc::P2_SMEM_BYTES);
+  (void)cudaGetLastError();
 }
 
 bool encode_bf16_2d(CUtensorMap* map, const void* ptr, int np, int box_rows) {
@@ -356,6 +623,8 @@ bool tc_supported() {
   std::call_once(g_once, init_once);
   return g_tc_ok;
 }
+
+void gemm_tc_set_variant(int v) { g_variant = (v >= 0 && v <= 3) ? v : 0; }
 
 int gemm_tc_max_grid() {
   std::call_once(g_once, init_once);
@@ -397,10 +666,35 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
   p.n_col = a.n_col;
   p.partial = a.partial;
   p.err = a.err;
-  const int tiles = p.tiles_m * p.tiles_n;
-  const int grid = tiles < g_sms ? tiles : g_sms;
-  tc::gemm_tc_kernel<<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(p);
-  NN_CUDA_TRY(cudaGetLastError());
+  // Variant choice: the 2-SM MMA by default where the size allows it, else single-CTA tiles.
+  const bool even = a.np % (2 * tc::BM) == 0;
+  int variant = g_variant;
+  if (variant == 0) variant = (even && g_2sm_clusters > 0) ? 3 : 1;
+  if ((variant == 2 && !(even && g_pair_clusters > 0)) || (variant == 3 && !(even && g_2sm_clusters > 0)))
+    return NN_ERR_UNSUPPORTED;
+  int grid = 0;
+  if (variant == 2 || variant == 3) {
+    // B^T maps load 128-row halves (one per CTA of the pair)
+    for (int s = 0; s < a.nseg; ++s)
+      if (!encode_bf16_2d(&p.map_b[s], a.b_seg[s], a.np, tc::BN / 2)) return NN_ERR_CUDA;
+    const int units = (p.tiles_m / 2) * p.tiles_n;
+    const int avail = variant == 2 ? g_pair_clusters : g_2sm_clusters;
+    const int clusters = units < avail ? units : avail;
+    grid = 2 * clusters;
+    cudaLaunchAttribute attr[1];
+    if (variant == 2) {
+      cudaLaunchConfig_t cfg = cluster_config(grid, tc::SMEM_BYTES, st, attr);
+      NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc::gemm_tc_pair_kernel, p));
+    } else {
+      cudaLaunchConfig_t cfg = cluster_config(grid, tc::P2_SMEM_BYTES, st, attr);
+      NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc::gemm_tc_2sm_kernel, p));
+    }
+  } else {
+    const int tiles = p.tiles_m * p.tiles_n;
+    grid = tiles < g_sms ? tiles : g_sms;
+    tc::gemm_tc_kernel<<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(p);
+    NN_CUDA_TRY(cudaGetLastError());
+  }
   if (grid_used) *grid_used = grid;
   return NN_OK;
 }

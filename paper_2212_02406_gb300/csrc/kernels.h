@@ -49,6 +49,9 @@ struct TcGemmArgs {
 };
 int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used);
 int gemm_tc_max_grid();
+// 0: automatic (CTA pairs with multicast when Np is a multiple of 256), 1: single-CTA tiles,
+// 2: CTA pairs only (NN_ERR_UNSUPPORTED where they do not apply).
+void gemm_tc_set_variant(int v);
 bool tc_supported();
 
 // ---- conversion / preconditioner / reduction kernels (convert.cu) -----------------------
@@ -68,9 +71,10 @@ int f64_to_f32(cudaStream_t st, const double* src, int64_t lds, int n, float* ds
 int frob_f64(cudaStream_t st, const double* src, int64_t lds, int n, double* partial, int count, double* out);
 // out[0] = sqrt(sum partial[0..count)) * scale, fixed summation order.
 int reduce_rms(cudaStream_t st, const double* partial, int count, double scale, double* out);
-// Preconditioners: write X0 (n x n FP64, ldx). scratch holds >= 4 doubles.
+// Preconditioners: write X0 (n x n FP64, ldx). scratch holds >= 4 doubles; vec_scratch
+// >= 2n doubles (power iteration of NN_PC_THETA2; may be null for the other kinds).
 int precond_fill(cudaStream_t st, const double* A, int64_t lda, int n, int kind, double scalar, double* X0,
-                 int64_t ldx, double* scratch);
+                 int64_t ldx, double* scratch, double* vec_scratch);
 
 // ---- dense NN on device buffers (nn_dense.cu), shared with the serving runtime ---------------
 int check_opts(const nn_opts* o, int64_t n);

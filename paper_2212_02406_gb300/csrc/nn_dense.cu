@@ -561,6 +561,12 @@ using namespace nn;
 
 extern "C" {
 
+int nn_set_gemm_variant(int variant) {
+  if (variant < 0 || variant > 3) return NN_ERR_ARG;
+  gemm_tc_set_variant(variant);
+  return NN_OK;
+}
+
 size_t nn_workspace_bytes(int64_t n, int dtype) {
   if (n < 1 || n > 32768 || !valid_dtype(dtype)) return 0;
   return ws_bytes(n, dtype);
@@ -575,15 +581,17 @@ size_t nn_workspace_bytes_host(int64_t n, int dtype) {
 int nn_init_precond(const double* A, int64_t n, int64_t lda, int kind, double scalar, double* X0, int64_t ldx,
                     void* workspace, size_t ws_bytes_, void* stream) {
   if (A == nullptr || X0 == nullptr || n < 1 || n > 32768 || lda < n || ldx < n) return NN_ERR_ARG;
-  if (kind < NN_PC_PAN_SCHREIBER || kind > NN_PC_JACOBI) return NN_ERR_ARG;
+  if (kind < NN_PC_PAN_SCHREIBER || kind > NN_PC_THETA2) return NN_ERR_ARG;
   if (kind == NN_PC_SCALAR && !(scalar > 0)) return NN_ERR_ARG;
+  if (kind == NN_PC_THETA2 && !(scalar >= 1 && scalar <= 1024)) return NN_ERR_ARG;
   Carver c(workspace, ws_bytes_);
   Common cm;
   carve_common(c, n, NN_F64, cm);
+  double* vec = c.take<double>(size_t(2 * n));
   if (!c.ok) return NN_ERR_OOM_BUDGET;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   NN_TRY(precond_fill(st, A, lda, int(n), kind, kind == NN_PC_JACOBI && scalar == 0 ? 1.0 : scalar, X0, ldx,
-                      cm.scal + 1));
+                      cm.scal + 1, vec));
   return NN_OK;
 }
 

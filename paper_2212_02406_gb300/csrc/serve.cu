@@ -271,7 +271,7 @@ int nn_server_submit(nn_server* s, const nn_request* r) {
   if (s == nullptr || r == nullptr || r->A == nullptr || r->n < 1 || r->nrhs < 0) return NN_ERR_ARG;
   if (r->nrhs > 0 && r->B == nullptr) return NN_ERR_ARG;
   if (r->dtype != NN_F64 && r->dtype != NN_F32 && r->dtype != NN_MIXED_BF16) return NN_ERR_ARG;
-  if (r->precond < NN_PC_PAN_SCHREIBER || r->precond > NN_PC_JACOBI) return NN_ERR_ARG;
+  if (r->precond < NN_PC_PAN_SCHREIBER || r->precond > NN_PC_THETA2) return NN_ERR_ARG;
   const size_t bytes = request_bytes(r->n, r->nrhs, r->dtype);
   if (bytes == 0) return NN_ERR_ARG;
   if (bytes > s->opts.arena_bytes) return NN_ERR_OOM_BUDGET;  // can never be admitted

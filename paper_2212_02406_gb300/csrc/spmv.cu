@@ -3,10 +3,19 @@
 // phi^(0) = D^-1:
 //     X = D^-1 prod_{j=0}^{k-1} ( sum_{n=0}^{L} P^{n (L+1)^j} ) B,     P = I - A D^-1.
 // D^-1 is folded into the stored values once (A' = A D^-1, so P v = v - A' v), and the chain
-// runs as (L+1)^k - 1 sparse products. Each product is HBM-bound: the kernel streams a
-// contiguous slice of (val, col) into shared memory with coalesced streaming loads (one block =
-// 256 consecutive rows), then each thread reduces its own row; the x gathers hit L2 and use
-// plain global loads (the read-only path is the texture pipeline, four requests per cycle).
+// runs as (L+1)^k - 1 sparse products. Each product streams a contiguous slice of (val, col)
+// into shared memory with coalesced streaming loads (one block = 256 consecutive rows), then
+// each thread reduces its own row; the vector gathers hit L2 through plain cached loads (the
+// read-only path is the texture pipeline, which takes four requests per cycle).
+//
+// Arithmetic policies: native FP64, native FP32, and double-float ("DF": a value is an
+// unevaluated sum hi + lo of two FP32 numbers, 49-bit significand) for FP64 data. GB300's FP64
+// pipe is narrow (predicated-off FP64 FMAs alone saturated it in an earlier four-right-hand-side
+// form of this kernel, hence the compile-time right-hand-side count R below); the DF policy keeps
+// the same 8 bytes per value and does its arithmetic with error-free transformations on the
+// FP32 pipes (two-sum after Knuth, two-product with FMA after Dekker, the double-float
+// additions and products of the QD library of Hida, Li and Bailey), for FP64 data on parts
+// with even less FP64 throughput.
 //
 // Fused variants: the last product of each block of (L+1)^j products adds its result into
 // the factor accumulator (acc_out = acc_in + y, element-wise), and the last block of a factor
@@ -26,12 +35,84 @@ constexpr int SP_MAXR = 4;     // right-hand sides per launch
 
 enum : int { SP_Y = 0, SP_Y_ACC = 1, SP_ACC = 2, SP_RESID = 3 };
 
-template <typename T>
-__global__ void __launch_bounds__(SP_ROWS)
-spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ col, const T* __restrict__ val,
-              const T* __restrict__ v, int64_t ldv, T* __restrict__ y, int64_t ldy, const T* acc_in, T* acc_out,
-              int64_t ld_acc, const T* __restrict__ b, int64_t ldb, int nrhs, int mode, double* __restrict__ partial) {
-  __shared__ T sval[SP_CHUNK];
+// ---- arithmetic policies ----------------------------------------------------------------
+
+struct ArithF64 {
+  using V = double;
+  using In = double;
+  __device__ static V zero() { return 0.0; }
+  __device__ static V mad(V a, V x, V acc) { return fma(a, x, acc); }
+  __device__ static V sub(V a, V b) { return a - b; }
+  __device__ static V add(V a, V b) { return a + b; }
+  __device__ static double to_d(V a) { return a; }
+  __device__ static V from_d(double a) { return a; }
+};
+
+struct ArithF32 {
+  using V = float;
+  using In = float;
+  __device__ static V zero() { return 0.f; }
+  __device__ static V mad(V a, V x, V acc) { return fmaf(a, x, acc); }
+  __device__ static V sub(V a, V b) { return a - b; }
+  __device__ static V add(V a, V b) { return a + b; }
+  __device__ static double to_d(V a) { return double(a); }
+  __device__ static V from_d(double a) { return float(a); }
+};
+
+// Double-float: (hi, lo) with |lo| <= ulp(hi)/2. The _rn intrinsics keep the compiler from
+// contracting the error-free sequences into FMAs.
+struct ArithDF {
+  using V = float2;
+  using In = double;
+  __device__ static void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  }
+  __device__ static void quick_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+  }
+  __device__ static V zero() { return make_float2(0.f, 0.f); }
+  // a + b, accurate variant (two two-sums, two renormalisations)
+  __device__ static V add(V a, V b) {
+    float s1, s2, t1, t2;
+    two_sum(a.x, b.x, s1, s2);
+    two_sum(a.y, b.y, t1, t2);
+    s2 = __fadd_rn(s2, t1);
+    quick_two_sum(s1, s2, s1, s2);
+    s2 = __fadd_rn(s2, t2);
+    quick_two_sum(s1, s2, s1, s2);
+    return make_float2(s1, s2);
+  }
+  __device__ static V sub(V a, V b) { return add(a, make_float2(-b.x, -b.y)); }
+  // a * x: exact high product from FMA, cross terms into the low part
+  __device__ static V mul(V a, V x) {
+    const float p = __fmul_rn(a.x, x.x);
+    float e = fmaf(a.x, x.x, -p);
+    e = fmaf(a.x, x.y, e);
+    e = fmaf(a.y, x.x, e);
+    float s, t;
+    quick_two_sum(p, e, s, t);
+    return make_float2(s, t);
+  }
+  __device__ static V mad(V a, V x, V acc) { return add(acc, mul(a, x)); }
+  __device__ static double to_d(V a) { return double(a.x) + double(a.y); }
+  __device__ static V from_d(double a) {
+    const float hi = float(a);
+    return make_float2(hi, float(a - double(hi)));
+  }
+};
+
+// R = right-hand sides handled per launch (compile-time, so nrhs = 1 stays lean in registers).
+template <class P, int R>
+__global__ void __launch_bounds__(SP_ROWS, R == 1 ? 5 : 1)
+spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ col, const typename P::V* val,
+              const typename P::V* v, int64_t ldv, typename P::V* y, int64_t ldy, const typename P::V* acc_in,
+              typename P::V* acc_out, int64_t ld_acc, const typename P::In* b, int64_t ldb, int nrhs, int mode,
+              double* __restrict__ partial) {
+  using V = typename P::V;
+  __shared__ V sval[SP_CHUNK];
   __shared__ int scol[SP_CHUNK];
   __shared__ double red[2][SP_ROWS / 32];
   const int tid = threadIdx.x;
@@ -42,9 +123,9 @@ spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
   const int e_end = row_ptr[r1];
   const int my_b = row < n ? row_ptr[row] : 0;
   const int my_e = row < n ? row_ptr[row + 1] : 0;
-  T sum[SP_MAXR];
+  V sum[R];
 #pragma unroll
-  for (int r = 0; r < SP_MAXR; ++r) sum[r] = T(0);
+  for (int r = 0; r < R; ++r) sum[r] = P::zero();
 
   constexpr int PER = SP_CHUNK / SP_ROWS;
   for (int base = e_begin; base < e_end; base += SP_CHUNK) {
@@ -52,7 +133,7 @@ spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
     // Issue every load of the slice before any shared-memory store, so each thread has PER
     // independent requests in flight; the matrix streams through (evict-first) and leaves
     // L2 to the vector, which the gathers below reuse across rows.
-    T vv[PER];
+    V vv[PER];
     int cc[PER];
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
@@ -75,28 +156,26 @@ spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
     int e = lo;
     // four gathers in flight per step
     for (; e + 4 <= hi; e += 4) {
-      const T a0 = sval[e - base], a1 = sval[e + 1 - base], a2 = sval[e + 2 - base], a3 = sval[e + 3 - base];
+      const V a0 = sval[e - base], a1 = sval[e + 1 - base], a2 = sval[e + 2 - base], a3 = sval[e + 3 - base];
       const int c0 = scol[e - base], c1 = scol[e + 1 - base], c2 = scol[e + 2 - base], c3 = scol[e + 3 - base];
 #pragma unroll
-      for (int r = 0; r < SP_MAXR; ++r) {
+      for (int r = 0; r < R; ++r) {
         if (r < nrhs) {
-          const T* vr = v + r * ldv;
-          // plain cached global loads (ld.global.ca): the non-coherent path goes through the
-          // texture pipeline, which accepts only four threads' requests per cycle
-          const T x0 = __ldca(vr + c0), x1 = __ldca(vr + c1), x2 = __ldca(vr + c2), x3 = __ldca(vr + c3);
-          sum[r] = fma(a0, x0, sum[r]);
-          sum[r] = fma(a1, x1, sum[r]);
-          sum[r] = fma(a2, x2, sum[r]);
-          sum[r] = fma(a3, x3, sum[r]);
+          const V* vr = v + r * ldv;
+          const V x0 = __ldca(vr + c0), x1 = __ldca(vr + c1), x2 = __ldca(vr + c2), x3 = __ldca(vr + c3);
+          sum[r] = P::mad(a0, x0, sum[r]);
+          sum[r] = P::mad(a1, x1, sum[r]);
+          sum[r] = P::mad(a2, x2, sum[r]);
+          sum[r] = P::mad(a3, x3, sum[r]);
         }
       }
     }
     for (; e < hi; ++e) {
-      const T a = sval[e - base];
+      const V a = sval[e - base];
       const int c = scol[e - base];
 #pragma unroll
-      for (int r = 0; r < SP_MAXR; ++r)
-        if (r < nrhs) sum[r] = fma(a, __ldca(v + c + r * ldv), sum[r]);
+      for (int r = 0; r < R; ++r)
+        if (r < nrhs) sum[r] = P::mad(a, __ldca(v + c + r * ldv), sum[r]);
     }
     __syncthreads();
   }
@@ -104,17 +183,17 @@ spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
   double ss_r = 0.0, ss_b = 0.0;
   if (row < n) {
 #pragma unroll
-    for (int r = 0; r < SP_MAXR; ++r) {
+    for (int r = 0; r < R; ++r) {
       if (r >= nrhs) break;
       if (mode == SP_RESID) {
-        const T bi = b[row + r * ldb];
-        const T ri = bi - sum[r];
-        ss_r = fma(double(ri), double(ri), ss_r);
-        ss_b = fma(double(bi), double(bi), ss_b);
+        const double bi = double(b[row + r * ldb]);
+        const double ri = bi - P::to_d(sum[r]);
+        ss_r = fma(ri, ri, ss_r);
+        ss_b = fma(bi, bi, ss_b);
       } else {
-        const T yi = __ldca(v + row + r * ldv) - sum[r];
+        const V yi = P::sub(__ldca(v + row + r * ldv), sum[r]);
         if (mode != SP_ACC) y[row + r * ldy] = yi;
-        if (mode != SP_Y) acc_out[row + r * ld_acc] = acc_in[row + r * ld_acc] + yi;
+        if (mode != SP_Y) acc_out[row + r * ld_acc] = P::add(acc_in[row + r * ld_acc], yi);
       }
     }
   }
@@ -141,7 +220,7 @@ spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
   }
 }
 
-// dinv[i] = 1 / A_ii; flags a missing or zero diagonal in *err.
+// dinv[i] = 1 / A_ii (in the input precision); flags a missing or zero diagonal in *err.
 template <typename T>
 __global__ void diag_inv_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ col,
                                 const T* __restrict__ val, T* __restrict__ dinv, int* err) {
@@ -158,24 +237,34 @@ __global__ void diag_inv_kernel(int n, const int* __restrict__ row_ptr, const in
   }
 }
 
-// A' = A D^-1 (column scaling).
-template <typename T>
-__global__ void scale_cols_kernel(int64_t nnz, const int* __restrict__ col, const T* __restrict__ val,
-                                  const T* __restrict__ dinv, T* __restrict__ out) {
+// A' = A D^-1 (column scaling), formed in the input precision and stored in the policy's type.
+template <class P>
+__global__ void scale_cols_kernel(int64_t nnz, const int* __restrict__ col, const typename P::In* __restrict__ val,
+                                  const typename P::In* __restrict__ dinv, typename P::V* __restrict__ out) {
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e < nnz) out[e] = val[e] * dinv[col[e]];
+  if (e < nnz) out[e] = P::from_d(double(val[e] * dinv[col[e]]));
 }
 
-// dst(n x nrhs, ldd) = src(n x nrhs, lds) [* dinv if given]
-template <typename T>
-__global__ void copy_cols_kernel(int n, int nrhs, const T* __restrict__ src, int64_t lds, T* __restrict__ dst,
-                                 int64_t ldd, const T* __restrict__ dinv) {
+// dst (policy type, n x nrhs, leading dim n) = src (input type, lds)
+template <class P>
+__global__ void load_cols_kernel(int n, int nrhs, const typename P::In* __restrict__ src, int64_t lds,
+                                 typename P::V* __restrict__ dst) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (i >= n || r >= nrhs) return;
-  T v = src[i + r * lds];
-  if (dinv) v *= dinv[i];
-  dst[i + r * ldd] = v;
+  dst[i + int64_t(r) * n] = P::from_d(double(src[i + r * lds]));
+}
+
+// X (input type, ldx) = D^-1 z
+template <class P>
+__global__ void store_cols_kernel(int n, int nrhs, const typename P::V* __restrict__ z,
+                                  const typename P::In* __restrict__ dinv, typename P::In* __restrict__ X,
+                                  int64_t ldx) {
+  using In = typename P::In;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (i >= n || r >= nrhs) return;
+  X[i + r * ldx] = In(P::to_d(z[i + int64_t(r) * n])) * dinv[i];
 }
 
 struct CsrWs {
@@ -188,33 +277,41 @@ struct CsrWs {
   int* err;
 };
 
-template <typename T>
+template <class P>
 void carve_csr(Carver& c, int64_t n, int64_t nnz, int64_t nrhs, CsrWs& w) {
+  using V = typename P::V;
+  using In = typename P::In;
   const size_t vec = size_t(n) * size_t(nrhs);
-  w.dinv = c.take<T>(size_t(n));
-  w.vals = c.take<T>(size_t(nnz));
-  w.z[0] = c.take<T>(vec);
-  w.z[1] = c.take<T>(vec);
-  w.u[0] = c.take<T>(vec);
-  w.u[1] = c.take<T>(vec);
+  w.dinv = c.take<In>(size_t(n));
+  w.vals = c.take<V>(size_t(nnz));
+  w.z[0] = c.take<V>(vec);
+  w.z[1] = c.take<V>(vec);
+  w.u[0] = c.take<V>(vec);
+  w.u[1] = c.take<V>(vec);
   const int64_t slices = (nrhs + SP_MAXR - 1) / SP_MAXR;
   w.partial = c.take<double>(size_t(2 * slices * ((n + SP_ROWS - 1) / SP_ROWS)));
   w.scal = c.take<double>(8);
   w.err = c.take<int>(8);
 }
 
-template <typename T>
-int spmv(cudaStream_t st, int n, const int* rp, const int* col, const T* vals, const T* v, T* y, const T* acc_in,
-         T* acc_out, const T* b, int64_t ldb, int nrhs, int mode, double* partial) {
+template <class P>
+int spmv(cudaStream_t st, int n, const int* rp, const int* col, const typename P::V* vals, const typename P::V* v,
+         typename P::V* y, const typename P::V* acc_in, typename P::V* acc_out, const typename P::In* b, int64_t ldb,
+         int nrhs, int mode, double* partial) {
   const int blocks = (n + SP_ROWS - 1) / SP_ROWS;
   for (int r0 = 0; r0 < nrhs; r0 += SP_MAXR) {
     const int nr = nrhs - r0 < SP_MAXR ? nrhs - r0 : SP_MAXR;
     const int64_t off = int64_t(r0) * n;
     // residual partials of slice r0/SP_MAXR follow those of the previous slices
     double* part = partial ? partial + int64_t(2) * blocks * (r0 / SP_MAXR) : nullptr;
-    spmv_p_kernel<T><<<blocks, SP_ROWS, 0, st>>>(n, rp, col, vals, v + off, n, y ? y + off : nullptr, n,
-                                                 acc_in ? acc_in + off : nullptr, acc_out ? acc_out + off : nullptr, n,
-                                                 b ? b + int64_t(r0) * ldb : nullptr, ldb, nr, mode, part);
+    if (nr == 1)
+      spmv_p_kernel<P, 1><<<blocks, SP_ROWS, 0, st>>>(n, rp, col, vals, v + off, n, y ? y + off : nullptr, n,
+                                                      acc_in ? acc_in + off : nullptr, acc_out ? acc_out + off : nullptr,
+                                                      n, b ? b + int64_t(r0) * ldb : nullptr, ldb, nr, mode, part);
+    else
+      spmv_p_kernel<P, SP_MAXR><<<blocks, SP_ROWS, 0, st>>>(
+          n, rp, col, vals, v + off, n, y ? y + off : nullptr, n, acc_in ? acc_in + off : nullptr,
+          acc_out ? acc_out + off : nullptr, n, b ? b + int64_t(r0) * ldb : nullptr, ldb, nr, mode, part);
     NN_CUDA_TRY(cudaGetLastError());
   }
   return NN_OK;
@@ -240,29 +337,30 @@ __global__ void reduce_pair_kernel(const double* __restrict__ partial, int count
   if (threadIdx.x == 0) out[0] = c[0] > 0 ? sqrt(a[0] / c[0]) : sqrt(a[0]);
 }
 
-template <typename T>
-int solve_csr(const int* rp, const int* col, const T* val, int64_t n64, int64_t nnz, const T* B, int64_t ldb,
-              int64_t nrhs64, int depth, int nests, double tol, T* X, int64_t ldx, nn_result* res, void* ws,
-              size_t ws_bytes, cudaStream_t st) {
+template <class P>
+int solve_csr(const int* rp, const int* col, const typename P::In* val, int64_t n64, int64_t nnz,
+              const typename P::In* B, int64_t ldb, int64_t nrhs64, int depth, int nests, double tol,
+              typename P::In* X, int64_t ldx, nn_result* res, void* ws, size_t ws_bytes, cudaStream_t st) {
+  using V = typename P::V;
+  using In = typename P::In;
   const int n = int(n64), nrhs = int(nrhs64);
   Carver c(ws, ws_bytes);
   CsrWs w;
-  carve_csr<T>(c, n64, nnz, nrhs64, w);
+  carve_csr<P>(c, n64, nnz, nrhs64, w);
   if (!c.ok) return NN_ERR_OOM_BUDGET;
-  T* dinv = static_cast<T*>(w.dinv);
-  T* vals = static_cast<T*>(w.vals);
-  T* z = static_cast<T*>(w.z[0]);
-  T* znew = static_cast<T*>(w.z[1]);
-  T* u[2] = {static_cast<T*>(w.u[0]), static_cast<T*>(w.u[1])};
+  In* dinv = static_cast<In*>(w.dinv);
+  V* vals = static_cast<V*>(w.vals);
+  V* z = static_cast<V*>(w.z[0]);
+  V* znew = static_cast<V*>(w.z[1]);
+  V* u[2] = {static_cast<V*>(w.u[0]), static_cast<V*>(w.u[1])};
   const int blocks = (n + SP_ROWS - 1) / SP_ROWS;
-  const int64_t vec = int64_t(n) * nrhs;
 
   NN_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-  diag_inv_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(n, rp, col, val, dinv, w.err);
+  diag_inv_kernel<In><<<(n + 255) / 256, 256, 0, st>>>(n, rp, col, val, dinv, w.err);
   NN_CUDA_TRY(cudaGetLastError());
-  scale_cols_kernel<T><<<unsigned((nnz + 255) / 256), 256, 0, st>>>(nnz, col, val, dinv, vals);
+  scale_cols_kernel<P><<<unsigned((nnz + 255) / 256), 256, 0, st>>>(nnz, col, val, dinv, vals);
   NN_CUDA_TRY(cudaGetLastError());
-  copy_cols_kernel<T><<<dim3((n + 255) / 256, nrhs), 256, 0, st>>>(n, nrhs, B, ldb, z, n, nullptr);
+  load_cols_kernel<P><<<dim3((n + 255) / 256, nrhs), 256, 0, st>>>(n, nrhs, B, ldb, z);
   NN_CUDA_TRY(cudaGetLastError());
   res->launches += 3;
   int dev_err = 0;
@@ -270,9 +368,9 @@ int solve_csr(const int* rp, const int* col, const T* val, int64_t n64, int64_t 
   NN_CUDA_TRY(cudaStreamSynchronize(st));
   if (dev_err != DEV_OK) return NN_ERR_ARG;
 
-  auto residual = [&](const T* zz, double* out) -> int {
+  auto residual = [&](const V* zz, double* out) -> int {
     // r = B - A X = B - A' z (since A X = A D^-1 z); relative Frobenius norm.
-    NN_TRY(spmv<T>(st, n, rp, col, vals, zz, nullptr, nullptr, nullptr, B, ldb, nrhs, SP_RESID, w.partial));
+    NN_TRY(spmv<P>(st, n, rp, col, vals, zz, nullptr, nullptr, nullptr, B, ldb, nrhs, SP_RESID, w.partial));
     const int slices = (nrhs + SP_MAXR - 1) / SP_MAXR;
     reduce_pair_kernel<<<1, 256, 0, st>>>(w.partial, blocks * slices, w.scal);
     NN_CUDA_TRY(cudaGetLastError());
@@ -288,22 +386,22 @@ int solve_csr(const int* rp, const int* col, const T* val, int64_t n64, int64_t 
   for (int j = 0; j < nests; ++j) {
     long long t = 1;
     for (int q = 0; q < j; ++q) t *= (depth + 1);
-    const T* src = z;
+    const V* src = z;
     int ping = 0;
     for (int blk = 1; blk <= depth; ++blk) {
       for (long long s = 1; s <= t; ++s) {
         const bool last_of_block = (s == t);
         const bool last_of_factor = last_of_block && (blk == depth);
-        T* dst = u[ping];
+        V* dst = u[ping];
         int mode = SP_Y;
-        const T* acc_in = nullptr;
-        T* acc_out = nullptr;
+        const V* acc_in = nullptr;
+        V* acc_out = nullptr;
         if (last_of_block) {
           mode = last_of_factor ? SP_ACC : SP_Y_ACC;
           acc_in = (blk == 1) ? z : znew;
           acc_out = znew;
         }
-        NN_TRY(spmv<T>(st, n, rp, col, vals, src, mode == SP_ACC ? nullptr : dst, acc_in, acc_out, nullptr, 0, nrhs,
+        NN_TRY(spmv<P>(st, n, rp, col, vals, src, mode == SP_ACC ? nullptr : dst, acc_in, acc_out, nullptr, 0, nrhs,
                        mode, nullptr));
         res->launches += (nrhs + SP_MAXR - 1) / SP_MAXR;
         res->flops += 2.0 * double(nnz) * nrhs;
@@ -312,7 +410,7 @@ int solve_csr(const int* rp, const int* col, const T* val, int64_t n64, int64_t 
       }
     }
     // znew = z + sum of the L blocks: swap
-    T* tmp = z;
+    V* tmp = z;
     z = znew;
     znew = tmp;
     applied = j + 1;
@@ -341,12 +439,23 @@ int solve_csr(const int* rp, const int* col, const T* val, int64_t n64, int64_t 
     res->residual = rel;
   }
   if (res->status == NN_OK && tol > 0 && !(res->residual < tol)) res->status = NN_ERR_NOT_CONVERGED;
-  copy_cols_kernel<T><<<dim3((n + 255) / 256, nrhs), 256, 0, st>>>(n, nrhs, z, n, X, ldx, dinv);
+  store_cols_kernel<P><<<dim3((n + 255) / 256, nrhs), 256, 0, st>>>(n, nrhs, z, dinv, X, ldx);
   NN_CUDA_TRY(cudaGetLastError());
   res->launches += 1;
   NN_CUDA_TRY(cudaStreamSynchronize(st));
-  (void)vec;
   return res->status;
+}
+
+size_t csr_ws_bytes(int64_t n, int64_t nnz, int64_t nrhs, int dtype) {
+  Carver c(nullptr, 0);
+  CsrWs w;
+  if (dtype == NN_F64)
+    carve_csr<ArithF64>(c, n, nnz, nrhs, w);
+  else if (dtype == NN_F32)
+    carve_csr<ArithF32>(c, n, nnz, nrhs, w);
+  else
+    carve_csr<ArithDF>(c, n, nnz, nrhs, w);
+  return align_up(c.used, 256);
 }
 
 }  // namespace
@@ -358,14 +467,8 @@ extern "C" {
 
 size_t nn_csr_workspace_bytes(int64_t n, int64_t nnz, int64_t nrhs, int dtype) {
   if (n < 1 || nnz < n || nrhs < 1 || n > (int64_t(1) << 30) || nnz > (int64_t(1) << 31) - 1) return 0;
-  if (dtype != NN_F64 && dtype != NN_F32) return 0;
-  Carver c(nullptr, 0);
-  CsrWs w;
-  if (dtype == NN_F64)
-    carve_csr<double>(c, n, nnz, nrhs, w);
-  else
-    carve_csr<float>(c, n, nnz, nrhs, w);
-  return align_up(c.used, 256);
+  if (dtype != NN_F64 && dtype != NN_F32 && dtype != NN_F64_DF) return 0;
+  return csr_ws_bytes(n, nnz, nrhs, dtype);
 }
 
 int nn_solve_csr(const int32_t* row_ptr, const int32_t* col, const void* val, int64_t n, int64_t nnz, int dtype,
@@ -388,11 +491,14 @@ int nn_solve_csr(const int32_t* row_ptr, const int32_t* col, const void* val, in
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int s;
   if (dtype == NN_F64)
-    s = solve_csr<double>(row_ptr, col, static_cast<const double*>(val), n, nnz, static_cast<const double*>(B), ldb,
-                          nrhs, depth, nests, tol, static_cast<double*>(X), ldx, res, workspace, ws_bytes, st);
+    s = solve_csr<ArithF64>(row_ptr, col, static_cast<const double*>(val), n, nnz, static_cast<const double*>(B), ldb,
+                            nrhs, depth, nests, tol, static_cast<double*>(X), ldx, res, workspace, ws_bytes, st);
+  else if (dtype == NN_F64_DF)
+    s = solve_csr<ArithDF>(row_ptr, col, static_cast<const double*>(val), n, nnz, static_cast<const double*>(B), ldb,
+                           nrhs, depth, nests, tol, static_cast<double*>(X), ldx, res, workspace, ws_bytes, st);
   else
-    s = solve_csr<float>(row_ptr, col, static_cast<const float*>(val), n, nnz, static_cast<const float*>(B), ldb, nrhs,
-                         depth, nests, tol, static_cast<float*>(X), ldx, res, workspace, ws_bytes, st);
+    s = solve_csr<ArithF32>(row_ptr, col, static_cast<const float*>(val), n, nnz, static_cast<const float*>(B), ldb,
+                            nrhs, depth, nests, tol, static_cast<float*>(X), ldx, res, workspace, ws_bytes, st);
   res->status = s;
   return s;
 }

@@ -67,7 +67,7 @@ def _run(nn, a_np, x0_np, depth, tol, max_nests, dtype, **kw):
     return st, res, X.cpu().numpy()
 
 
-@pytest.mark.parametrize("kind", ["pan_schreiber", "trace", "scalar", "jacobi"])
+@pytest.mark.parametrize("kind", ["pan_schreiber", "trace", "scalar", "jacobi", "theta2"])
 @pytest.mark.parametrize("n", [1, 17, 256, 257])
 def test_precond_parity(nn, kind, n):
     import torch
@@ -76,11 +76,13 @@ def test_precond_parity(nn, kind, n):
     A = _dev(a)
     X0 = torch.empty_like(A)
     ws = nn.workspace(n, "f64")
-    st = nn.nn_init_precond(A, kind, 0.37 if kind == "scalar" else 1.0, X0, ws)
+    scalar = {"scalar": 0.37, "theta2": 8}.get(kind, 1.0)
+    st = nn.nn_init_precond(A, kind, scalar, X0, ws)
     torch.cuda.synchronize()
     assert st == nn.NN_OK
     want = {"pan_schreiber": dense.precond_pan_schreiber(a), "trace": dense.precond_trace(a),
-            "scalar": dense.precond_scalar(n, 0.37), "jacobi": dense.precond_jacobi(a)}[kind]
+            "scalar": dense.precond_scalar(n, 0.37), "jacobi": dense.precond_jacobi(a),
+            "theta2": dense.precond_theta2(a, 8, np.ones(n))}[kind]
     got = X0.cpu().numpy()
     assert np.allclose(got, want, rtol=1e-14 * max(1, n), atol=0)
 
@@ -112,6 +114,26 @@ def test_f64_ragged_sizes_fixed_nests(nn, n, depth):
     st, res, x = _run(nn, a, x0, depth, 0.0, nests, "f64")
     assert st == nn.NN_OK and res["nests"] == nests
     assert _rel(x, ora.x) <= max(1e-12, 16 * np.linalg.cond(a) * U64 * math.sqrt(n))
+
+
+def test_theta2_start_speeds_up_convergence(nn):
+    # Theta_2 normalises by an estimate of lambda_max instead of the trace: fewer nests, same answer
+    import torch
+
+    n = 300
+    a, q, lam = synth.spd_spectrum(n, 1e3, seed=12)
+    A = _dev(a)
+    ws = nn.workspace(n, "f64")
+    nests = {}
+    for kind, scalar in (("trace", 1.0), ("theta2", 8)):
+        X0 = torch.empty_like(A)
+        assert nn.nn_init_precond(A, kind, scalar, X0, ws) == nn.NN_OK
+        st, res, x = _run(nn, a, X0.cpu().numpy(), 2, 1e-10, 64, "f64")
+        assert st == nn.NN_OK
+        ora = dense.nn_invert(a, X0.cpu().numpy(), 2, tol=1e-10, max_nests=64)
+        assert res["nests"] == ora.nests
+        nests[kind] = res["nests"]
+    assert nests["theta2"] < nests["trace"]
 
 
 def test_f64_zero_nests_returns_x0(nn):
@@ -234,3 +256,28 @@ def test_residual_call(nn, n):
     ws32 = nn.workspace(n, "f32")
     st, s32 = nn.nn_residual(_dev(a), _dev(x), "f32", ws32)
     assert st == nn.NN_OK and abs(s32 - want) <= 1e-3 * want + 1e-6
+
+
+@pytest.mark.parametrize("n", [512, 1024])
+def test_gemm_tilings_agree_bitwise(nn, n):
+    # Single-CTA tiles, CTA pairs sharing B^T through TMA multicast and the 2-SM MMA all run
+    # the same K-ordered BF16 products into FP32 per output element, so the iterates must
+    # agree bit for bit; only the per-CTA grouping of the residual's sum of squares differs.
+    a, q, lam = synth.spd_spectrum(n, 1e2, seed=n + 7)
+    x0 = dense.precond_scalar(n, 2.0 / (lam[0] + lam[-1]))
+    out = {}
+    try:
+        for variant in (1, 2, 3):
+            assert nn.nn_set_gemm_variant(variant) == nn.NN_OK
+            out[variant] = _run(nn, a, x0, 2, 1e-6, 40, "mixed_bf16")
+    finally:
+        nn.nn_set_gemm_variant(0)
+    st1, r1, x1 = out[1]
+    assert st1 == nn.NN_OK
+    for variant in (2, 3):
+        st2, r2, x2 = out[variant]
+        assert st2 == nn.NN_OK
+        assert r1["nests"] == r2["nests"] and r1["pieces"] == r2["pieces"]
+        assert np.array_equal(x1, x2)
+        for h1, h2 in zip(r1["history"], r2["history"]):
+            assert abs(h1 - h2) <= 1e-12 * h1

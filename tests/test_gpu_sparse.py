@@ -4,7 +4,8 @@ The chain computes X = D^-1 prod_j sum_n P^{n (L+1)^j} B with (L+1)^k - 1 sparse
 Both sides run the same sequence of products; they differ by the summation order inside
 each row (at most max_row_nnz terms) and by the FP64/FP32 rounding of each product, so the
 relative difference is bounded by m * u * (1 + max_row_nnz) with m = (L+1)^k - 1 products:
-tolerance 8 m u (nnz_row + 1) per dtype, with a 1e-13 floor for FP64.
+tolerance 8 m u (nnz_row + 1) per dtype, with a 1e-13 floor for FP64. The double-float
+arithmetic (FP64 data, hi + lo FP32 pairs) has u = 2^-48.
 """
 import math
 
@@ -16,7 +17,8 @@ from oracle import sparse
 
 pytestmark = pytest.mark.gpu
 
-U = {np.float64: 2.0 ** -53, np.float32: 2.0 ** -24}
+U = {"f64": 2.0 ** -53, "f64_df": 2.0 ** -48, "f32": 2.0 ** -24}
+NP = {"f64": np.float64, "f64_df": np.float64, "f32": np.float32}
 
 
 @pytest.fixture(scope="module")
@@ -28,16 +30,17 @@ def nn():
     return abi
 
 
-def _solve(nn, m, b, depth, nests, tol=0.0, dtype=np.float64):
+def _solve(nn, m, b, depth, nests, tol=0.0, dtype="f64"):
     import torch
 
+    npd = NP[dtype]
     rp = torch.from_numpy(m.row_ptr.astype(np.int32)).cuda()
     col = torch.from_numpy(m.col.astype(np.int32)).cuda()
-    val = torch.from_numpy(m.val.astype(dtype)).cuda()
-    B = torch.from_numpy(np.ascontiguousarray(b.T.astype(dtype))).cuda()  # (nrhs, n)
+    val = torch.from_numpy(m.val.astype(npd)).cuda()
+    B = torch.from_numpy(np.ascontiguousarray(b.T.astype(npd))).cuda()  # (nrhs, n)
     X = torch.empty_like(B)
-    ws = nn.csr_workspace(m.n, m.nnz, B.shape[0], "f64" if dtype == np.float64 else "f32")
-    st, res = nn.nn_solve_csr(rp, col, val, B, depth, nests, tol, X, ws)
+    ws = nn.csr_workspace(m.n, m.nnz, B.shape[0], dtype)
+    st, res = nn.nn_solve_csr(rp, col, val, B, depth, nests, tol, X, ws, double_float=(dtype == "f64_df"))
     torch.cuda.synchronize()
     return st, res, X.cpu().numpy().T
 
@@ -46,10 +49,10 @@ def _tol(m, depth, nests, dtype):
     terms = (depth + 1) ** nests - 1
     nnz_row = int(np.max(np.diff(m.row_ptr)))
     t = 8 * max(terms, 1) * U[dtype] * (nnz_row + 1)
-    return max(t, 1e-13) if dtype == np.float64 else t
+    return max(t, 1e-13) if dtype == "f64" else t
 
 
-@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("dtype", ["f64", "f64_df", "f32"])
 @pytest.mark.parametrize("depth", [1, 2, 3])
 @pytest.mark.parametrize("kind", ["laplacian", "random"])
 @pytest.mark.parametrize("nrhs", [1, 3, 6])
@@ -67,7 +70,7 @@ def test_chain_matches_oracle(nn, dtype, depth, kind, nrhs):
         assert err <= _tol(m, depth, nests, dtype), (nests, err)
         # residual reported for the returned X agrees with the oracle's
         r = sparse.relative_residual(a64, want, b)
-        assert abs(res["residual"] - r) <= 1e-6 * r + (1e-12 if dtype == np.float64 else 1e-5)
+        assert abs(res["residual"] - r) <= 1e-6 * r + {"f64": 1e-12, "f64_df": 1e-10, "f32": 1e-5}[dtype]
 
 
 def test_tol_stops_at_first_factor_below(nn):
@@ -97,17 +100,18 @@ def test_edge_cases(nn):
     assert st == nn.NN_ERR_ARG
 
 
-def test_full_size_laplacian_2048(nn):
+@pytest.mark.parametrize("dtype", ["f64", "f64_df"])
+def test_full_size_laplacian_2048(nn, dtype):
     # The benchmarked configuration: 2048 x 2048 grid, shift 0.5, depth 2, 5 factors
-    # (242 sparse products), FP64, checked element-wise against the oracle.
+    # (242 sparse products), FP64 data, checked element-wise against the oracle.
     m = synth.laplacian_5pt(2048, shift=0.5)
     b = synth.gaussian_rhs(m.n, 1, seed=0)
-    st, res, x = _solve(nn, m, b, 2, 5)
+    st, res, x = _solve(nn, m, b, 2, 5, dtype=dtype)
     assert st == nn.NN_OK
     a64 = m.to_scipy()
     want = sparse.nn_sparse_solve(a64, b, 2, 5)
     err = np.linalg.norm(x - want) / np.linalg.norm(want)
-    assert err <= _tol(m, 2, 5, np.float64)
+    assert err <= _tol(m, 2, 5, dtype)
     # D = 4.5 I, so b - A x_m = (I - A/4.5)^m b and ||r|| / ||b|| <= rho(P)^m, m = 3^5 terms,
     # down to the FP64 rounding floor
     rho = 4.0 * math.cos(math.pi / 2049) / 4.5

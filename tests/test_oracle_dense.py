@@ -188,3 +188,26 @@ def test_optimal_depth_claim():
     k_budget = 36
     orders = {L: (L + 1) ** (k_budget // (L + 1)) for L in (1, 2, 3, 4, 5)}
     assert max(orders, key=orders.get) == claim["optimal_inception_depth"]
+
+
+# --- Theta_2 power-iteration normalisation (Eq. (trace), read as an inverse Rayleigh quotient) ---
+
+def test_theta2_bounds_and_limit():
+    # On a diagonal matrix the k-th power iterate's Rayleigh quotient is computable by hand:
+    # with v = ones, u = W^k v has entries lambda_j^k, so <u, W u> / <u, u> =
+    # sum lambda^(2k+1) / sum lambda^(2k), which increases to lambda_max.
+    lam = np.array([1.0, 2.0, 5.0, 10.0])
+    w = np.diag(lam)
+    v = np.ones(4)
+    for k in (1, 2, 4, 8, 16):
+        rq = float(np.sum(lam ** (2 * k + 1)) / np.sum(lam ** (2 * k)))
+        assert abs(dense.theta2(w, k, v) - (k / (k + 1)) / rq) <= 1e-14 / rq
+        # never above 1 / lambda_max, so I - Theta_2 W keeps its spectrum in [0, 1)
+        assert dense.theta2(w, k, v) * lam.max() < 1.0
+    # rho(I - Theta_2 W) < 1 on an SPD matrix, and Theta_2 beats the trace normalisation
+    a, q, lamq = synth.spd_spectrum(200, 1e3, seed=4)
+    v = synth.rng(9).standard_normal(200)
+    t2 = dense.theta2(a, 8, v)
+    rho2 = np.max(np.abs(1.0 - t2 * lamq))
+    rho1 = np.max(np.abs(1.0 - lamq / np.trace(a)))
+    assert rho2 < 1.0 and rho2 < rho1
