@@ -59,6 +59,7 @@ def parse_args():
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--max-active", type=int, default=8)
     ap.add_argument("--gemm-variant", type=int, default=0, choices=[0, 1, 2, 3], help="0 auto, 1 single-CTA tiles, 2 CTA pairs with multicast, 3 2-SM MMA")
+    ap.add_argument("--spmv-variant", type=int, default=0, choices=[0, 1], help="0 auto (bulk-copy ring), 1 staged loads")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -329,6 +330,7 @@ def run_sparse(args, rank, world, local_rank):
 
     build.build()
     abi.lib()
+    abi.nn_set_spmv_variant(args.spmv_variant)
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     grid, depth, nests = 2048, 2, 5
@@ -379,7 +381,8 @@ def run_sparse(args, rank, world, local_rank):
                                    f"depth {depth}, {nests} factors ({products} sparse products)",
                        "n": m.n, "nnz": m.nnz, "l2": "matrix larger than L2 (streams every product)"},
             "status_ok": st == abi.NN_OK, "residual": res["residual"], "gpu_launches": launches,
-            "roofline": {"kernel": "nn::spmv_p_kernel (whole chain timed)", "bound": "hbm", "achieved": round(gbs, 1),
+            "roofline": {"kernel": ("nn::spmv_ring_kernel" if args.spmv_variant == 0 else "nn::spmv_p_kernel")
+                         + " (whole chain timed, residual products and reductions included)", "bound": "hbm", "achieved": round(gbs, 1),
                          "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4), "traffic": None,
                          "peak_source": f"{src} copy bandwidth",
                          "bytes_per_product": int(chain / products)},

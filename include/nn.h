@@ -162,11 +162,20 @@ int nn_residual(const double* A, int64_t lda, const double* X, int64_t ldx, int6
  * sparse product) goes to res->history[j] and the chain stops at the first factor below tol
  * (NN_ERR_NOT_CONVERGED if none is). tol <= 0 runs all `nests` factors and evaluates the
  * residual once at the end (res->residual). res->nests = factors applied; res->flops counts
- * 2 nnz per sparse product per right-hand side. Needs nn_csr_workspace_bytes() of workspace. */
+ * 2 nnz per sparse product per right-hand side. Needs nn_csr_workspace_bytes() of workspace.
+ * Returns NN_ERR_TIMEOUT if a device-side wait of the product kernel ran past its limit. */
 size_t nn_csr_workspace_bytes(int64_t n, int64_t nnz, int64_t nrhs, int dtype);
 int nn_solve_csr(const int32_t* row_ptr, const int32_t* col, const void* val, int64_t n, int64_t nnz,
                  int dtype, const void* B, int64_t ldb, int64_t nrhs, int depth, int nests, double tol,
                  void* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_bytes, void* stream);
+
+/* Sparse-product kernel for one right-hand side (a process-wide tuning knob; both variants
+ * sum each row's terms in the same order, so results are bitwise identical): 0 = automatic
+ * (a persistent kernel that streams (val, col, row_ptr) through a ring of shared-memory stages
+ * with bulk async copies, used when row_ptr, col and the values are 16-byte aligned), 1 = one
+ * block per 256 rows with staged loads. Returns NN_ERR_ARG for other values. Not thread-safe
+ * against concurrent solves. */
+int nn_set_spmv_variant(int variant);
 
 /* ---- batched small complex inversions ---------------------------------------------------
  * Many independent U x U complex64 matrices (U <= 64; massive-MIMO Gram matrices, the use the

@@ -85,6 +85,7 @@ _SIGNATURES = {
     "nn_residual": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int, POINTER(c_double), c_void_p,
                             c_size_t, c_void_p]),
     "nn_csr_workspace_bytes": (c_size_t, [c_int64, c_int64, c_int64, c_int]),
+    "nn_set_spmv_variant": (c_int, [c_int]),
     "nn_residual_noalloc": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_int64, POINTER(c_double), c_void_p]),
     "nn_server_request_bytes": (c_size_t, [c_int64, c_int64, c_int]),
     "nn_server_create": (c_int, [POINTER(NNServerOpts), POINTER(c_void_p)]),
@@ -175,6 +176,11 @@ def workspace(n: int, dtype="f64", host=False, device=None):
 def nn_set_gemm_variant(variant: int) -> int:
     """0 automatic, 1 single-CTA tiles, 2 CTA pairs with multicast, 3 2-SM MMA (tensor-core GEMM tiling)."""
     return int(lib().nn_set_gemm_variant(int(variant)))
+
+
+def nn_set_spmv_variant(variant: int) -> int:
+    """0 automatic (bulk-copy ring for one right-hand side), 1 staged loads (sparse products)."""
+    return int(lib().nn_set_spmv_variant(int(variant)))
 
 
 def nn_workspace_bytes(n: int, dtype) -> int:

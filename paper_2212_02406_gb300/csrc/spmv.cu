@@ -220,6 +220,252 @@ spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
   }
 }
 
+// ---- one right-hand side: persistent kernel with a bulk-copy ring ----------------------
+//
+// Each block runs one producer warp and ST_ROWS consumer threads (one per row of a 256-row
+// tile). The producer walks the block's tiles (blockIdx.x, + gridDim.x, ...) and, for each
+// chunk of at most ST_CAP nonzeros of a tile, issues cp.async.bulk copies of (val, col) and,
+// for a tile's first chunk, of row_ptr[r0 .. r0 + 260) into the next free stage of a
+// ST_STAGES ring; completion is counted on the stage's full barrier. Consumers reduce their
+// row over the staged chunk (vector gathers from L2) and release the stage on its empty
+// barrier. The matrix stream therefore stays in flight while the gathers of earlier tiles
+// wait on L2, which a load-then-compute block cannot do. The chunk grid starts at the tile's
+// first nonzero rounded down to a multiple of 4 (16-byte source alignment for every element
+// type); the last elements of the arrays past the last multiple of 4 are read directly.
+// Each row's terms are summed in increasing column-slot order, as in spmv_p_kernel, so both
+// kernels give identical results.
+constexpr int ST_ROWS = 256;
+constexpr int ST_THREADS = ST_ROWS + 32;
+constexpr int ST_STAGES = 3;
+constexpr int ST_CAP = 1536;             // nonzeros per stage, multiple of 4
+constexpr int ST_ROWBUF = ST_ROWS + 4;   // row_ptr entries staged per tile, multiple of 4
+
+struct StageHdr {
+  int base;      // first staged element (multiple of 4)
+  int end;       // one past the last nonzero of this chunk
+  int copy_end;  // one past the last staged element (elements in [copy_end, end) are read from global)
+  int rows;      // row_ptr entries staged (first chunk of a tile), else 0
+  int last;      // last chunk of the tile
+  int pad[3];
+};
+
+template <class P>
+struct StLayout {
+  using V = typename P::V;
+  static constexpr int kVal = ST_CAP * int(sizeof(V));
+  static constexpr int kCol = ST_CAP * 4;
+  static constexpr int kRow = ST_ROWBUF * 4;
+  static constexpr int kStage = kVal + kCol + kRow;
+  // control block: full/empty barriers, 4 reduction barriers, stage headers, abort flag,
+  // then 4 x 16 doubles of residual reduction scratch at the end
+  static constexpr int kRed = 4 * 16 * 8;
+  static constexpr int kCtrl = 1024;
+  static constexpr int kBytes = ST_STAGES * kStage + kCtrl;
+  static_assert(kVal % 16 == 0 && kCol % 16 == 0 && kRow % 16 == 0, "16-byte stage pieces");
+  static_assert((2 * ST_STAGES + 4) * 8 + ST_STAGES * int(sizeof(StageHdr)) + 16 + kRed <= kCtrl, "control block");
+};
+
+template <class P>
+__global__ void __launch_bounds__(ST_THREADS, 3)
+spmv_ring_kernel(int n, int nnz, const int* __restrict__ row_ptr, const int* __restrict__ col,
+                 const typename P::V* __restrict__ val, const typename P::V* v, typename P::V* y,
+                 const typename P::V* acc_in, typename P::V* acc_out, const typename P::In* b, int mode,
+                 double* __restrict__ partial, int* err) {
+  using V = typename P::V;
+  using L = StLayout<P>;
+  extern __shared__ __align__(128) uint8_t st_smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(st_smem + ST_STAGES * L::kStage);
+  uint64_t* empty = full + ST_STAGES;
+  uint64_t* red_bar = empty + ST_STAGES;
+  StageHdr* hdr = reinterpret_cast<StageHdr*>(red_bar + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(hdr + ST_STAGES);
+  double* red = reinterpret_cast<double*>(st_smem + ST_STAGES * L::kStage + L::kCtrl - L::kRed);
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int tiles = (n + ST_ROWS - 1) / ST_ROWS;
+  if (tid == 0) {
+    for (int s = 0; s < ST_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], ST_ROWS / 32);
+    }
+    for (int s = 0; s < 4; ++s) mbar_init(&red_bar[s], ST_ROWS / 32);
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == ST_ROWS / 32) {
+    // ---- producer warp ----
+    const uint64_t pol = l2_evict_first_policy();
+    const int nnz4 = nnz & ~3;
+    const int rows4 = (n + 1) & ~3;
+    int stage = 0;
+    uint32_t phase = 0;
+    bool stop = false;
+    for (int t0 = blockIdx.x; t0 < tiles && !stop; t0 += 32 * int(gridDim.x)) {
+      // lane j fetches the nonzero range of the block's j-th next tile
+      const int tj = t0 + lane * int(gridDim.x);
+      int eb = 0, ee = 0;
+      if (tj < tiles) {
+        eb = row_ptr[tj * ST_ROWS];
+        ee = row_ptr[min((tj + 1) * ST_ROWS, n)];
+      }
+      for (int j = 0; j < 32; ++j) {
+        const int t = t0 + j * int(gridDim.x);
+        if (t >= tiles) break;
+        const int e0 = __shfl_sync(0xffffffffu, eb, j);
+        const int e1 = __shfl_sync(0xffffffffu, ee, j);
+        const int r0 = t * ST_ROWS;
+        int base = e0 & ~3;
+        bool first = true;
+        while (true) {
+          const int end = min(base + ST_CAP, e1);
+          if (lane == 0) {
+            if (mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err)) {
+              const int copy_end = max(base, min((end + 3) & ~3, nnz4));
+              const int rows = first ? max(0, min(ST_ROWBUF, rows4 - r0)) : 0;
+              StageHdr& h = hdr[stage];
+              h.base = base;
+              h.end = end;
+              h.copy_end = copy_end;
+              h.rows = rows;
+              h.last = end >= e1 ? 1 : 0;
+              uint8_t* sp = st_smem + stage * L::kStage;
+              const uint32_t cnt = uint32_t(copy_end - base);
+              mbar_arrive_expect_tx(&full[stage], cnt * uint32_t(sizeof(V) + 4) + uint32_t(rows) * 4u);
+              if (cnt > 0) {
+                bulk_load(sp, val + base, cnt * uint32_t(sizeof(V)), &full[stage], pol);
+                bulk_load(sp + L::kVal, col + base, cnt * 4u, &full[stage], pol);
+              }
+              if (rows > 0) bulk_load(sp + L::kVal + L::kCol, row_ptr + r0, uint32_t(rows) * 4u, &full[stage], pol);
+            }
+          }
+          __syncwarp();
+          if (*abort_flag) {
+            stop = true;
+            break;
+          }
+          if (++stage == ST_STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+          first = false;
+          base += ST_CAP;
+          if (end >= e1) break;
+        }
+        if (stop) break;
+      }
+    }
+    // Leave only after the consumers have released every stage, so no copy is in flight.
+    if (lane == 0 && !stop) {
+      for (int i = 0; i < ST_STAGES; ++i) {
+        if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err)) break;
+        if (++stage == ST_STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+    return;
+  }
+
+  // ---- consumers: thread tid owns row r0 + tid of every tile ----
+  int stage = 0;
+  uint32_t phase = 0;
+  int local = 0;
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++local) {
+    const int row = t * ST_ROWS + tid;
+    const bool has_row = row < n;
+    // row-wise operands, fetched before the matrix arrives
+    V v_row = P::zero(), a_row = P::zero();
+    double b_row = 0.0;
+    if (has_row) {
+      if (mode == SP_RESID) {
+        b_row = double(b[row]);
+      } else {
+        v_row = __ldca(v + row);
+        if (mode != SP_Y) a_row = acc_in[row];
+      }
+    }
+    V sum = P::zero();
+    int my_b = 0, my_e = 0;
+    bool first = true;
+    while (true) {
+      if (!mbar_wait(&full[stage], phase, abort_flag, err)) return;
+      const StageHdr h = hdr[stage];
+      const uint8_t* sp = st_smem + stage * L::kStage;
+      const V* sval = reinterpret_cast<const V*>(sp);
+      const int* scol = reinterpret_cast<const int*>(sp + L::kVal);
+      const int* srow = reinterpret_cast<const int*>(sp + L::kVal + L::kCol);
+      if (first && has_row) {
+        my_b = tid < h.rows ? srow[tid] : row_ptr[row];
+        my_e = tid + 1 < h.rows ? srow[tid + 1] : row_ptr[row + 1];
+      }
+      const int lo = max(my_b, h.base), hi = min(my_e, h.end);
+      const int hs = min(hi, h.copy_end);
+      int e = lo;
+      for (; e + 4 <= hs; e += 4) {
+        const int q = e - h.base;
+        const V a0 = sval[q], a1 = sval[q + 1], a2 = sval[q + 2], a3 = sval[q + 3];
+        const int c0 = scol[q], c1 = scol[q + 1], c2 = scol[q + 2], c3 = scol[q + 3];
+        const V x0 = __ldca(v + c0), x1 = __ldca(v + c1), x2 = __ldca(v + c2), x3 = __ldca(v + c3);
+        sum = P::mad(a0, x0, sum);
+        sum = P::mad(a1, x1, sum);
+        sum = P::mad(a2, x2, sum);
+        sum = P::mad(a3, x3, sum);
+      }
+      for (; e < hs; ++e) sum = P::mad(sval[e - h.base], __ldca(v + scol[e - h.base]), sum);
+      for (; e < hi; ++e) sum = P::mad(val[e], __ldca(v + col[e]), sum);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[stage]);
+      if (++stage == ST_STAGES) {
+        stage = 0;
+        phase ^= 1u;
+      }
+      first = false;
+      if (h.last) break;
+    }
+    if (mode == SP_RESID) {
+      double ss_r = 0.0, ss_b = 0.0;
+      if (has_row) {
+        const double ri = b_row - P::to_d(sum);
+        ss_r = ri * ri;
+        ss_b = b_row * b_row;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ss_r += __shfl_down_sync(0xffffffffu, ss_r, o);
+        ss_b += __shfl_down_sync(0xffffffffu, ss_b, o);
+      }
+      // Per-tile sums over the 8 warps through scratch slot local % 4 and its mbarrier (no
+      // CTA-wide barrier: a warp can be at most ST_STAGES tiles ahead of warp 0, because the
+      // stages it needs are only refilled after warp 0 has released them).
+      const int slot = local & 3;
+      double* rs = red + 16 * slot;
+      if (lane == 0) {
+        rs[warp] = ss_r;
+        rs[8 + warp] = ss_b;
+        mbar_arrive(&red_bar[slot]);
+      }
+      if (tid == 0) {
+        if (!mbar_wait(&red_bar[slot], uint32_t(local >> 2) & 1u, abort_flag, err)) return;
+        double a = 0, c = 0;
+        for (int w = 0; w < ST_ROWS / 32; ++w) {
+          a += rs[w];
+          c += rs[8 + w];
+        }
+        partial[2 * t] = a;
+        partial[2 * t + 1] = c;
+      }
+    } else if (has_row) {
+      const V yi = P::sub(v_row, sum);
+      if (mode != SP_ACC) y[row] = yi;
+      if (mode != SP_Y) acc_out[row] = P::add(a_row, yi);
+    }
+  }
+}
+
 // dinv[i] = 1 / A_ii (in the input precision); flags a missing or zero diagonal in *err.
 template <typename T>
 __global__ void diag_inv_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ col,
@@ -294,24 +540,61 @@ void carve_csr(Carver& c, int64_t n, int64_t nnz, int64_t nrhs, CsrWs& w) {
   w.err = c.take<int>(8);
 }
 
+int g_spmv_variant = 0;  // 0 automatic (bulk-copy ring for one right-hand side), 1 staged loads only
+
+// Grid of the ring kernel: every SM filled with as many blocks as fit (cached per policy).
 template <class P>
-int spmv(cudaStream_t st, int n, const int* rp, const int* col, const typename P::V* vals, const typename P::V* v,
-         typename P::V* y, const typename P::V* acc_in, typename P::V* acc_out, const typename P::In* b, int64_t ldb,
-         int nrhs, int mode, double* partial) {
+struct RingOccupancy {
+  int sms = 0, per_sm = 0;
+  RingOccupancy() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(spmv_ring_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, StLayout<P>::kBytes) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmv_ring_kernel<P>, ST_THREADS, StLayout<P>::kBytes) !=
+            cudaSuccess) {
+      (void)cudaGetLastError();
+      per_sm = 0;
+    }
+  }
+};
+
+template <class P>
+int ring_grid(int tiles) {
+  static const RingOccupancy<P> occ;  // thread-safe one-time initialisation
+  if (occ.per_sm <= 0) return 0;
+  const int g = occ.sms * occ.per_sm;
+  return tiles < g ? tiles : g;
+}
+
+template <class P>
+int spmv(cudaStream_t st, int n, int nnz, const int* rp, const int* col, const typename P::V* vals,
+         const typename P::V* v, typename P::V* y, const typename P::V* acc_in, typename P::V* acc_out,
+         const typename P::In* b, int64_t ldb, int nrhs, int mode, double* partial, int* err) {
   const int blocks = (n + SP_ROWS - 1) / SP_ROWS;
+  // the ring copies (val, col, row_ptr) with 16-byte aligned bulk copies
+  const bool aligned = ((reinterpret_cast<uintptr_t>(rp) | reinterpret_cast<uintptr_t>(col) |
+                         reinterpret_cast<uintptr_t>(vals)) & 15u) == 0;
   for (int r0 = 0; r0 < nrhs; r0 += SP_MAXR) {
     const int nr = nrhs - r0 < SP_MAXR ? nrhs - r0 : SP_MAXR;
     const int64_t off = int64_t(r0) * n;
     // residual partials of slice r0/SP_MAXR follow those of the previous slices
     double* part = partial ? partial + int64_t(2) * blocks * (r0 / SP_MAXR) : nullptr;
-    if (nr == 1)
+    const int grid = (nr == 1 && aligned && g_spmv_variant != 1) ? ring_grid<P>(blocks) : 0;
+    if (grid > 0) {
+      spmv_ring_kernel<P><<<grid, ST_THREADS, StLayout<P>::kBytes, st>>>(
+          n, nnz, rp, col, vals, v + off, y ? y + off : nullptr, acc_in ? acc_in + off : nullptr,
+          acc_out ? acc_out + off : nullptr, b ? b + int64_t(r0) * ldb : nullptr, mode, part, err);
+    } else if (nr == 1) {
       spmv_p_kernel<P, 1><<<blocks, SP_ROWS, 0, st>>>(n, rp, col, vals, v + off, n, y ? y + off : nullptr, n,
                                                       acc_in ? acc_in + off : nullptr, acc_out ? acc_out + off : nullptr,
                                                       n, b ? b + int64_t(r0) * ldb : nullptr, ldb, nr, mode, part);
-    else
+    } else {
       spmv_p_kernel<P, SP_MAXR><<<blocks, SP_ROWS, 0, st>>>(
           n, rp, col, vals, v + off, n, y ? y + off : nullptr, n, acc_in ? acc_in + off : nullptr,
           acc_out ? acc_out + off : nullptr, n, b ? b + int64_t(r0) * ldb : nullptr, ldb, nr, mode, part);
+    }
     NN_CUDA_TRY(cudaGetLastError());
   }
   return NN_OK;
@@ -370,15 +653,18 @@ int solve_csr(const int* rp, const int* col, const typename P::In* val, int64_t 
 
   auto residual = [&](const V* zz, double* out) -> int {
     // r = B - A X = B - A' z (since A X = A D^-1 z); relative Frobenius norm.
-    NN_TRY(spmv<P>(st, n, rp, col, vals, zz, nullptr, nullptr, nullptr, B, ldb, nrhs, SP_RESID, w.partial));
+    NN_TRY(spmv<P>(st, n, int(nnz), rp, col, vals, zz, nullptr, nullptr, nullptr, B, ldb, nrhs, SP_RESID, w.partial,
+                   w.err));
     const int slices = (nrhs + SP_MAXR - 1) / SP_MAXR;
     reduce_pair_kernel<<<1, 256, 0, st>>>(w.partial, blocks * slices, w.scal);
     NN_CUDA_TRY(cudaGetLastError());
     res->launches += 1 + slices;
     res->flops += 2.0 * double(nnz) * nrhs;
+    int e = DEV_OK;
     NN_CUDA_TRY(cudaMemcpyAsync(out, w.scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    NN_CUDA_TRY(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     NN_CUDA_TRY(cudaStreamSynchronize(st));
-    return NN_OK;
+    return e == DEV_OK ? NN_OK : NN_ERR_TIMEOUT;  // the ring kernel's bounded waits
   };
 
   int applied = 0;
@@ -401,8 +687,8 @@ int solve_csr(const int* rp, const int* col, const typename P::In* val, int64_t 
           acc_in = (blk == 1) ? z : znew;
           acc_out = znew;
         }
-        NN_TRY(spmv<P>(st, n, rp, col, vals, src, mode == SP_ACC ? nullptr : dst, acc_in, acc_out, nullptr, 0, nrhs,
-                       mode, nullptr));
+        NN_TRY(spmv<P>(st, n, int(nnz), rp, col, vals, src, mode == SP_ACC ? nullptr : dst, acc_in, acc_out, nullptr, 0,
+                       nrhs, mode, nullptr, w.err));
         res->launches += (nrhs + SP_MAXR - 1) / SP_MAXR;
         res->flops += 2.0 * double(nnz) * nrhs;
         src = dst;
@@ -442,7 +728,10 @@ int solve_csr(const int* rp, const int* col, const typename P::In* val, int64_t 
   store_cols_kernel<P><<<dim3((n + 255) / 256, nrhs), 256, 0, st>>>(n, nrhs, z, dinv, X, ldx);
   NN_CUDA_TRY(cudaGetLastError());
   res->launches += 1;
+  int e = DEV_OK;
+  NN_CUDA_TRY(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   NN_CUDA_TRY(cudaStreamSynchronize(st));
+  if (e != DEV_OK) res->status = NN_ERR_TIMEOUT;
   return res->status;
 }
 
@@ -464,6 +753,12 @@ size_t csr_ws_bytes(int64_t n, int64_t nnz, int64_t nrhs, int dtype) {
 using namespace nn;
 
 extern "C" {
+
+int nn_set_spmv_variant(int variant) {
+  if (variant < 0 || variant > 1) return NN_ERR_ARG;
+  g_spmv_variant = variant;
+  return NN_OK;
+}
 
 size_t nn_csr_workspace_bytes(int64_t n, int64_t nnz, int64_t nrhs, int dtype) {
   if (n < 1 || nnz < n || nrhs < 1 || n > (int64_t(1) << 30) || nnz > (int64_t(1) << 31) - 1) return 0;

@@ -116,3 +116,30 @@ def test_full_size_laplacian_2048(nn, dtype):
     # down to the FP64 rounding floor
     rho = 4.0 * math.cos(math.pi / 2049) / 4.5
     assert res["residual"] <= rho ** 243 + 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_df", "f32"])
+@pytest.mark.parametrize("case", ["lap_odd_nnz", "random_ragged", "random_long_rows", "tiny"])
+def test_product_kernels_agree_bitwise(nn, dtype, case):
+    # The bulk-copy ring kernel and the staged-load kernel sum each row's terms in the same
+    # order, so iterates and residuals must agree bit for bit. The cases cover a nonzero count
+    # that is not a multiple of 4 (elements read past the last staged one), ragged rows, rows
+    # longer than one ring stage (a tile split into many chunks) and a single partial tile.
+    m = {
+        "lap_odd_nnz": lambda: synth.laplacian_5pt(33, 29, shift=0.5),
+        "random_ragged": lambda: synth.random_sparse_spd(1000, 7, seed=4),
+        "random_long_rows": lambda: synth.random_sparse_spd(3000, 300, seed=1),
+        "tiny": lambda: synth.laplacian_5pt(5, shift=0.5),
+    }[case]()
+    b = synth.gaussian_rhs(m.n, 1, seed=11)
+    out = {}
+    try:
+        for variant in (1, 0):
+            assert nn.nn_set_spmv_variant(variant) == nn.NN_OK
+            out[variant] = _solve(nn, m, b, 2, 3, tol=1e-30, dtype=dtype)
+    finally:
+        nn.nn_set_spmv_variant(0)
+    (s1, r1, x1), (s0, r0, x0) = out[1], out[0]
+    assert s1 == s0 and r1["nests"] == r0["nests"] == 3
+    assert np.array_equal(x1, x0)
+    assert r1["history"][:3] == r0["history"][:3]
