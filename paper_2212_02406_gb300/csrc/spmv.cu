@@ -40,8 +40,10 @@ enum : int { SP_Y = 0, SP_Y_ACC = 1, SP_ACC = 2, SP_RESID = 3 };
 struct ArithF64 {
   using V = double;
   using In = double;
+  static constexpr bool kWide = false;  // FP64 FMAs stay unpredicated (narrow FP64 pipe)
   __device__ static V zero() { return 0.0; }
   __device__ static V mad(V a, V x, V acc) { return fma(a, x, acc); }
+  __device__ static V nmad(V a, V x, V acc) { return fma(-a, x, acc); }
   __device__ static V sub(V a, V b) { return a - b; }
   __device__ static V add(V a, V b) { return a + b; }
   __device__ static double to_d(V a) { return a; }
@@ -51,8 +53,10 @@ struct ArithF64 {
 struct ArithF32 {
   using V = float;
   using In = float;
+  static constexpr bool kWide = true;
   __device__ static V zero() { return 0.f; }
   __device__ static V mad(V a, V x, V acc) { return fmaf(a, x, acc); }
+  __device__ static V nmad(V a, V x, V acc) { return fmaf(-a, x, acc); }
   __device__ static V sub(V a, V b) { return a - b; }
   __device__ static V add(V a, V b) { return a + b; }
   __device__ static double to_d(V a) { return double(a); }
@@ -64,6 +68,7 @@ struct ArithF32 {
 struct ArithDF {
   using V = float2;
   using In = double;
+  static constexpr bool kWide = true;
   __device__ static void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
@@ -97,6 +102,7 @@ struct ArithDF {
     return make_float2(s, t);
   }
   __device__ static V mad(V a, V x, V acc) { return add(acc, mul(a, x)); }
+  __device__ static V nmad(V a, V x, V acc) { return add(acc, mul(make_float2(-a.x, -a.y), x)); }
   __device__ static double to_d(V a) { return double(a.x) + double(a.y); }
   __device__ static V from_d(double a) {
     const float hi = float(a);
@@ -123,9 +129,12 @@ spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
   const int e_end = row_ptr[r1];
   const int my_b = row < n ? row_ptr[row] : 0;
   const int my_e = row < n ? row_ptr[row + 1] : 0;
+  // sum = v_row - sum_e a_e x_e for the products (one rounding chain started at v_row, so
+  // y = v - A'v needs no separate subtraction), sum = -sum_e a_e x_e for the residual
   V sum[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) sum[r] = P::zero();
+  for (int r = 0; r < R; ++r)
+    sum[r] = (mode != SP_RESID && row < n && r < nrhs) ? __ldca(v + row + r * ldv) : P::zero();
 
   constexpr int PER = SP_CHUNK / SP_ROWS;
   for (int base = e_begin; base < e_end; base += SP_CHUNK) {
@@ -163,10 +172,10 @@ spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
         if (r < nrhs) {
           const V* vr = v + r * ldv;
           const V x0 = __ldca(vr + c0), x1 = __ldca(vr + c1), x2 = __ldca(vr + c2), x3 = __ldca(vr + c3);
-          sum[r] = P::mad(a0, x0, sum[r]);
-          sum[r] = P::mad(a1, x1, sum[r]);
-          sum[r] = P::mad(a2, x2, sum[r]);
-          sum[r] = P::mad(a3, x3, sum[r]);
+          sum[r] = P::nmad(a0, x0, sum[r]);
+          sum[r] = P::nmad(a1, x1, sum[r]);
+          sum[r] = P::nmad(a2, x2, sum[r]);
+          sum[r] = P::nmad(a3, x3, sum[r]);
         }
       }
     }
@@ -175,7 +184,7 @@ spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
       const int c = scol[e - base];
 #pragma unroll
       for (int r = 0; r < R; ++r)
-        if (r < nrhs) sum[r] = P::mad(a, __ldca(v + c + r * ldv), sum[r]);
+        if (r < nrhs) sum[r] = P::nmad(a, __ldca(v + c + r * ldv), sum[r]);
     }
     __syncthreads();
   }
@@ -187,11 +196,11 @@ spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
       if (r >= nrhs) break;
       if (mode == SP_RESID) {
         const double bi = double(b[row + r * ldb]);
-        const double ri = bi - P::to_d(sum[r]);
+        const double ri = bi + P::to_d(sum[r]);
         ss_r = fma(ri, ri, ss_r);
         ss_b = fma(bi, bi, ss_b);
       } else {
-        const V yi = P::sub(__ldca(v + row + r * ldv), sum[r]);
+        const V yi = sum[r];
         if (mode != SP_ACC) y[row + r * ldy] = yi;
         if (mode != SP_Y) acc_out[row + r * ld_acc] = P::add(acc_in[row + r * ld_acc], yi);
       }
@@ -237,7 +246,7 @@ spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
 constexpr int ST_ROWS = 256;
 constexpr int ST_THREADS = ST_ROWS + 32;
 constexpr int ST_STAGES = 3;
-constexpr int ST_CAP = 1536;             // nonzeros per stage, multiple of 4
+constexpr int ST_CAP = 1288;             // nonzeros per stage, multiple of 4 (a 5-point tile + alignment)
 constexpr int ST_ROWBUF = ST_ROWS + 4;   // row_ptr entries staged per tile, multiple of 4
 
 struct StageHdr {
@@ -266,7 +275,7 @@ struct StLayout {
 };
 
 template <class P>
-__global__ void __launch_bounds__(ST_THREADS, 3)
+__global__ void __launch_bounds__(ST_THREADS, 4)
 spmv_ring_kernel(int n, int nnz, const int* __restrict__ row_ptr, const int* __restrict__ col,
                  const typename P::V* __restrict__ val, const typename P::V* v, typename P::V* y,
                  const typename P::V* acc_in, typename P::V* acc_out, const typename P::In* b, int mode,
@@ -388,7 +397,7 @@ spmv_ring_kernel(int n, int nnz, const int* __restrict__ row_ptr, const int* __r
         if (mode != SP_Y) a_row = acc_in[row];
       }
     }
-    V sum = P::zero();
+    V sum = mode == SP_RESID ? P::zero() : v_row;  // same rounding chain as spmv_p_kernel
     int my_b = 0, my_e = 0;
     bool first = true;
     while (true) {
@@ -405,18 +414,50 @@ spmv_ring_kernel(int n, int nnz, const int* __restrict__ row_ptr, const int* __r
       const int lo = max(my_b, h.base), hi = min(my_e, h.end);
       const int hs = min(hi, h.copy_end);
       int e = lo;
-      for (; e + 4 <= hs; e += 4) {
-        const int q = e - h.base;
-        const V a0 = sval[q], a1 = sval[q + 1], a2 = sval[q + 2], a3 = sval[q + 3];
-        const int c0 = scol[q], c1 = scol[q + 1], c2 = scol[q + 2], c3 = scol[q + 3];
-        const V x0 = __ldca(v + c0), x1 = __ldca(v + c1), x2 = __ldca(v + c2), x3 = __ldca(v + c3);
-        sum = P::mad(a0, x0, sum);
-        sum = P::mad(a1, x1, sum);
-        sum = P::mad(a2, x2, sum);
-        sum = P::mad(a3, x3, sum);
+      if (P::kWide) {
+        // eight gathers in flight: a row of up to 8 terms costs one L2 round trip
+        for (; e + 8 <= hs; e += 8) {
+          const int q = e - h.base;
+          V a[8], x[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) a[k] = sval[q + k];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) x[k] = __ldca(v + scol[q + k]);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) sum = P::nmad(a[k], x[k], sum);
+        }
+        const int rem = hs - e;
+        if (rem > 0) {
+          const int q = e - h.base;
+          V a[7], x[7];
+#pragma unroll
+          for (int k = 0; k < 7; ++k) {
+            a[k] = P::zero();
+            x[k] = P::zero();
+            if (k < rem) {
+              a[k] = sval[q + k];
+              x[k] = __ldca(v + scol[q + k]);
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 7; ++k)
+            if (k < rem) sum = P::nmad(a[k], x[k], sum);
+          e = hs;
+        }
+      } else {
+        for (; e + 4 <= hs; e += 4) {
+          const int q = e - h.base;
+          const V a0 = sval[q], a1 = sval[q + 1], a2 = sval[q + 2], a3 = sval[q + 3];
+          const int c0 = scol[q], c1 = scol[q + 1], c2 = scol[q + 2], c3 = scol[q + 3];
+          const V x0 = __ldca(v + c0), x1 = __ldca(v + c1), x2 = __ldca(v + c2), x3 = __ldca(v + c3);
+          sum = P::nmad(a0, x0, sum);
+          sum = P::nmad(a1, x1, sum);
+          sum = P::nmad(a2, x2, sum);
+          sum = P::nmad(a3, x3, sum);
+        }
+        for (; e < hs; ++e) sum = P::nmad(sval[e - h.base], __ldca(v + scol[e - h.base]), sum);
       }
-      for (; e < hs; ++e) sum = P::mad(sval[e - h.base], __ldca(v + scol[e - h.base]), sum);
-      for (; e < hi; ++e) sum = P::mad(val[e], __ldca(v + col[e]), sum);
+      for (; e < hi; ++e) sum = P::nmad(val[e], __ldca(v + col[e]), sum);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[stage]);
       if (++stage == ST_STAGES) {
@@ -429,7 +470,7 @@ spmv_ring_kernel(int n, int nnz, const int* __restrict__ row_ptr, const int* __r
     if (mode == SP_RESID) {
       double ss_r = 0.0, ss_b = 0.0;
       if (has_row) {
-        const double ri = b_row - P::to_d(sum);
+        const double ri = b_row + P::to_d(sum);
         ss_r = ri * ri;
         ss_b = b_row * b_row;
       }
@@ -459,7 +500,7 @@ spmv_ring_kernel(int n, int nnz, const int* __restrict__ row_ptr, const int* __r
         partial[2 * t + 1] = c;
       }
     } else if (has_row) {
-      const V yi = P::sub(v_row, sum);
+      const V yi = sum;
       if (mode != SP_ACC) y[row] = yi;
       if (mode != SP_Y) acc_out[row] = P::add(a_row, yi);
     }
