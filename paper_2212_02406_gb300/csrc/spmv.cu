@@ -40,7 +40,7 @@ enum : int { SP_Y = 0, SP_Y_ACC = 1, SP_ACC = 2, SP_RESID = 3 };
 struct ArithF64 {
   using V = double;
   using In = double;
-  static constexpr bool kWide = false;  // FP64 FMAs stay unpredicated (narrow FP64 pipe)
+  static constexpr bool kBranchTail = true;
   __device__ static V zero() { return 0.0; }
   __device__ static V mad(V a, V x, V acc) { return fma(a, x, acc); }
   __device__ static V nmad(V a, V x, V acc) { return fma(-a, x, acc); }
@@ -53,7 +53,7 @@ struct ArithF64 {
 struct ArithF32 {
   using V = float;
   using In = float;
-  static constexpr bool kWide = true;
+  static constexpr bool kBranchTail = false;
   __device__ static V zero() { return 0.f; }
   __device__ static V mad(V a, V x, V acc) { return fmaf(a, x, acc); }
   __device__ static V nmad(V a, V x, V acc) { return fmaf(-a, x, acc); }
@@ -68,7 +68,7 @@ struct ArithF32 {
 struct ArithDF {
   using V = float2;
   using In = double;
-  static constexpr bool kWide = true;
+  static constexpr bool kBranchTail = false;
   __device__ static void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
@@ -243,6 +243,15 @@ spmv_p_kernel(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
 // type); the last elements of the arrays past the last multiple of 4 are read directly.
 // Each row's terms are summed in increasing column-slot order, as in spmv_p_kernel, so both
 // kernels give identical results.
+// sum - a_0 x_0 - ... - a_{K-1} x_{K-1}, in that order
+template <class P, int K>
+__device__ __forceinline__ typename P::V nmad_chain(const typename P::V (&a)[7], const typename P::V (&x)[7],
+                                                    typename P::V sum) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) sum = P::nmad(a[k], x[k], sum);
+  return sum;
+}
+
 constexpr int ST_ROWS = 256;
 constexpr int ST_THREADS = ST_ROWS + 32;
 constexpr int ST_STAGES = 3;
@@ -293,6 +302,11 @@ spmv_ring_kernel(int n, int nnz, const int* __restrict__ row_ptr, const int* __r
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int tiles = (n + ST_ROWS - 1) / ST_ROWS;
+  // Programmatic dependent launch: the next product may be scheduled as soon as every block of
+  // this one is resident; its producer then streams the matrix (which no product writes) while
+  // this product finishes, and its consumers wait for this grid to complete before reading the
+  // vectors.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (tid == 0) {
     for (int s = 0; s < ST_STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -380,6 +394,8 @@ spmv_ring_kernel(int n, int nnz, const int* __restrict__ row_ptr, const int* __r
   }
 
   // ---- consumers: thread tid owns row r0 + tid of every tile ----
+  // every vector read and write comes after the previous grid in the stream has completed
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   int stage = 0;
   uint32_t phase = 0;
   int local = 0;
@@ -414,48 +430,48 @@ spmv_ring_kernel(int n, int nnz, const int* __restrict__ row_ptr, const int* __r
       const int lo = max(my_b, h.base), hi = min(my_e, h.end);
       const int hs = min(hi, h.copy_end);
       int e = lo;
-      if (P::kWide) {
-        // eight gathers in flight: a row of up to 8 terms costs one L2 round trip
-        for (; e + 8 <= hs; e += 8) {
-          const int q = e - h.base;
-          V a[8], x[8];
+      // Eight gathers in flight: a row of up to eight terms costs one L2 round trip. For FP64
+      // the multiply-adds of the last partial group run in a branch per count, so no
+      // predicated-off FMA takes a slot of the narrow FP64 pipe.
+      for (; e + 8 <= hs; e += 8) {
+        const int q = e - h.base;
+        V a[8], x[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) a[k] = sval[q + k];
+        for (int k = 0; k < 8; ++k) a[k] = sval[q + k];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) x[k] = __ldca(v + scol[q + k]);
+        for (int k = 0; k < 8; ++k) x[k] = __ldca(v + scol[q + k]);
 #pragma unroll
-          for (int k = 0; k < 8; ++k) sum = P::nmad(a[k], x[k], sum);
-        }
-        const int rem = hs - e;
-        if (rem > 0) {
-          const int q = e - h.base;
-          V a[7], x[7];
+        for (int k = 0; k < 8; ++k) sum = P::nmad(a[k], x[k], sum);
+      }
+      const int rem = hs - e;
+      if (rem > 0) {
+        const int q = e - h.base;
+        V a[7], x[7];
 #pragma unroll
-          for (int k = 0; k < 7; ++k) {
-            a[k] = P::zero();
-            x[k] = P::zero();
-            if (k < rem) {
-              a[k] = sval[q + k];
-              x[k] = __ldca(v + scol[q + k]);
-            }
+        for (int k = 0; k < 7; ++k) {
+          a[k] = P::zero();
+          x[k] = P::zero();
+          if (k < rem) {
+            a[k] = sval[q + k];
+            x[k] = __ldca(v + scol[q + k]);
           }
+        }
+        if (P::kBranchTail) {
+          switch (rem) {
+            case 1: sum = nmad_chain<P, 1>(a, x, sum); break;
+            case 2: sum = nmad_chain<P, 2>(a, x, sum); break;
+            case 3: sum = nmad_chain<P, 3>(a, x, sum); break;
+            case 4: sum = nmad_chain<P, 4>(a, x, sum); break;
+            case 5: sum = nmad_chain<P, 5>(a, x, sum); break;
+            case 6: sum = nmad_chain<P, 6>(a, x, sum); break;
+            default: sum = nmad_chain<P, 7>(a, x, sum); break;
+          }
+        } else {
 #pragma unroll
           for (int k = 0; k < 7; ++k)
             if (k < rem) sum = P::nmad(a[k], x[k], sum);
-          e = hs;
         }
-      } else {
-        for (; e + 4 <= hs; e += 4) {
-          const int q = e - h.base;
-          const V a0 = sval[q], a1 = sval[q + 1], a2 = sval[q + 2], a3 = sval[q + 3];
-          const int c0 = scol[q], c1 = scol[q + 1], c2 = scol[q + 2], c3 = scol[q + 3];
-          const V x0 = __ldca(v + c0), x1 = __ldca(v + c1), x2 = __ldca(v + c2), x3 = __ldca(v + c3);
-          sum = P::nmad(a0, x0, sum);
-          sum = P::nmad(a1, x1, sum);
-          sum = P::nmad(a2, x2, sum);
-          sum = P::nmad(a3, x3, sum);
-        }
-        for (; e < hs; ++e) sum = P::nmad(sval[e - h.base], __ldca(v + scol[e - h.base]), sum);
+        e = hs;
       }
       for (; e < hi; ++e) sum = P::nmad(val[e], __ldca(v + col[e]), sum);
       __syncwarp();
@@ -624,9 +640,20 @@ int spmv(cudaStream_t st, int n, int nnz, const int* rp, const int* col, const t
     double* part = partial ? partial + int64_t(2) * blocks * (r0 / SP_MAXR) : nullptr;
     const int grid = (nr == 1 && aligned && g_spmv_variant != 1) ? ring_grid<P>(blocks) : 0;
     if (grid > 0) {
-      spmv_ring_kernel<P><<<grid, ST_THREADS, StLayout<P>::kBytes, st>>>(
-          n, nnz, rp, col, vals, v + off, y ? y + off : nullptr, acc_in ? acc_in + off : nullptr,
-          acc_out ? acc_out + off : nullptr, b ? b + int64_t(r0) * ldb : nullptr, mode, part, err);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(unsigned(grid));
+      cfg.blockDim = dim3(ST_THREADS);
+      cfg.dynamicSmemBytes = size_t(StLayout<P>::kBytes);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, spmv_ring_kernel<P>, n, nnz, rp, col, vals, v + off,
+                                     y ? y + off : nullptr, acc_in ? acc_in + off : nullptr,
+                                     acc_out ? acc_out + off : nullptr, b ? b + int64_t(r0) * ldb : nullptr, mode,
+                                     part, err));
     } else if (nr == 1) {
       spmv_p_kernel<P, 1><<<blocks, SP_ROWS, 0, st>>>(n, rp, col, vals, v + off, n, y ? y + off : nullptr, n,
                                                       acc_in ? acc_in + off : nullptr, acc_out ? acc_out + off : nullptr,
