@@ -52,6 +52,40 @@ __device__ __forceinline__ float group_gemm(int U_rt, int ti, int tj, const floa
   for (int a = 0; a < T; ++a)
 #pragma unroll
     for (int b = 0; b < T; ++b) acc[a][b] = make_float2(0.f, 0.f);
+  if (exact && (UC % 2) == 0) {
+    // P[i, k] and P[i, k + 1] arrive in one 16-byte load (two k steps per P load), which cuts
+    // the shared-memory wavefronts of the P operand in half; same FMA order as below.
+#pragma unroll 4
+    for (int k = 0; k < UC; k += 2) {
+      float4 pa2[T];
+#pragma unroll
+      for (int a = 0; a < T; ++a) pa2[a] = *reinterpret_cast<const float4*>(P + (ti + a * TG) * UC + k);
+      float2 q0[T], q1[T];
+#pragma unroll
+      for (int b = 0; b < T; ++b) {
+        q0[b] = Q[k * UC + tj + b * TG];
+        q1[b] = Q[(k + 1) * UC + tj + b * TG];
+      }
+#pragma unroll
+      for (int a = 0; a < T; ++a)
+#pragma unroll
+        for (int b = 0; b < T; ++b) {
+          acc[a][b].x = fmaf(pa2[a].x, q0[b].x, acc[a][b].x);
+          acc[a][b].x = fmaf(-pa2[a].y, q0[b].y, acc[a][b].x);
+          acc[a][b].y = fmaf(pa2[a].x, q0[b].y, acc[a][b].y);
+          acc[a][b].y = fmaf(pa2[a].y, q0[b].x, acc[a][b].y);
+        }
+#pragma unroll
+      for (int a = 0; a < T; ++a)
+#pragma unroll
+        for (int b = 0; b < T; ++b) {
+          acc[a][b].x = fmaf(pa2[a].z, q1[b].x, acc[a][b].x);
+          acc[a][b].x = fmaf(-pa2[a].w, q1[b].y, acc[a][b].x);
+          acc[a][b].y = fmaf(pa2[a].z, q1[b].y, acc[a][b].y);
+          acc[a][b].y = fmaf(pa2[a].w, q1[b].x, acc[a][b].y);
+        }
+    }
+  } else {
 #pragma unroll(UC > 0 ? 8 : 1)
   for (int k = 0; k < U; ++k) {
     float2 pa[T], qb[T];
@@ -74,6 +108,7 @@ __device__ __forceinline__ float group_gemm(int U_rt, int ti, int tj, const floa
         acc[a][b].y = fmaf(pa[a].x, qb[b].y, acc[a][b].y);
         acc[a][b].y = fmaf(pa[a].y, qb[b].x, acc[a][b].y);
       }
+  }
   }
   float ss = 0.f;
 #pragma unroll
