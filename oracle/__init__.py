@@ -12,7 +12,8 @@ Modules
 -------
 ``dense``    Neumann series, Newton and Chebyshev iterations, NN (Algorithm 1 and
              the right-multiplied form), the explicit product form, preconditioners,
-             the residual and the stop/divergence rule.
+             the residual, the stop/divergence rule, and general solves through the
+             normal equations (Corollary 3).
 ``exact``    the same recursions over ``fractions.Fraction`` for N <= 4.
 ``sparse``   the explicit NN product form applied to right-hand sides through a
              CSR matrix (Corollary 1, Corollary 6, Algorithm 2).
@@ -35,6 +36,7 @@ from .dense import (  # noqa: F401
     nn_alg1,
     nn_explicit,
     nn_invert,
+    nn_normal_solve,
     nn_step_right,
     precond_jacobi,
     precond_pan_schreiber,

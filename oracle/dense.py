@@ -258,3 +258,24 @@ def nn_invert(w: np.ndarray, x0: np.ndarray, depth: int, tol: float, max_nests: 
             break
         x = nn_step_right(w, x, depth, r)
     return NNRun(x, max_nests, hist, STATUS_NOT_CONVERGED if tol > 0 else STATUS_OK)
+
+
+# ---------------------------------------------------------------------------
+# General (non-Hermitian, complex) systems through the normal equations (Corollary 3).
+# ---------------------------------------------------------------------------
+
+def nn_normal_solve(a: np.ndarray, b: np.ndarray, depth: int, tol: float, max_nests: int = 64):
+    """Solve A x = B for any nonsingular A (real or complex) as Corollary 3 does.
+
+    W = A^H A is Hermitian positive definite; the NN runs on W from X_0 = Theta I with
+    Theta = 1 / Tr(W) (the trace normalisation of Eq. (trace)); the solution is
+    x = X_k A^H B, the right-form counterpart of prod_j sum_n (I - Theta W)^{n (L+1)^j} Theta A^H B
+    (Eq. (nnlinearsystem)). The stop rule is the one of ``nn_invert`` applied to W.
+    Returns (x, run).
+    """
+    ah = a.conj().T
+    w = ah @ a
+    theta = 1.0 / np.trace(w).real
+    x0 = np.eye(w.shape[0], dtype=w.dtype) * theta
+    run = nn_invert(w, x0, depth, tol, max_nests)
+    return run.x @ (ah @ b), run

@@ -98,6 +98,28 @@ def spd_spectrum_torch(n: int, kappa: float, seed: int = 0, device="cuda"):
     return a, q, lam
 
 
+def haar_unitary(n: int, seed: int) -> np.ndarray:
+    """Complex Q from the QR factorisation of a CN(0,1) matrix, phases fixed so diag(R) > 0."""
+    r = rng(seed)
+    g = (r.standard_normal((n, n)) + 1j * r.standard_normal((n, n))) / np.sqrt(2.0)
+    q, rr = np.linalg.qr(g)
+    d = np.diag(rr)
+    return q * (d / np.abs(d))[None, :].conj()
+
+
+def general_svd(n: int, cond: float, seed: int = 0, complex_: bool = False):
+    """A = U diag(sigma) V^H, a general (non-Hermitian) matrix with geometric singular values
+    from 1 down to 1/cond and Haar U, V; returns (A, sigma)."""
+    sig = np.geomspace(1.0, 1.0 / cond, n)
+    if complex_:
+        u = haar_unitary(n, seed)
+        v = haar_unitary(n, seed + 7919)
+    else:
+        u = haar_orthogonal(n, seed)
+        v = haar_orthogonal(n, seed + 7919)
+    return (u * sig[None, :]) @ v.conj().T, sig
+
+
 def gaussian_rhs(n: int, k: int = 1, seed: int = 0, dtype=np.float64) -> np.ndarray:
     """N x k right-hand sides with N(0,1) entries, column-major (Fortran order)."""
     return np.asfortranarray(rng(seed + 104729).standard_normal((n, k)).astype(dtype))

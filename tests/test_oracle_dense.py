@@ -211,3 +211,56 @@ def test_theta2_bounds_and_limit():
     rho2 = np.max(np.abs(1.0 - t2 * lamq))
     rho1 = np.max(np.abs(1.0 - lamq / np.trace(a)))
     assert rho2 < 1.0 and rho2 < rho1
+
+
+# --- general systems through the normal equations (Corollary 3) -----------------------
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_normal_solve_diagonal_complex_closed_form(depth):
+    # A = diag(a_j), complex: W = A^H A = diag(|a_j|^2), Theta = 1 / sum |a_j|^2 and
+    # X_k = diag((1 - (1 - Theta |a_j|^2)^((L+1)^k)) / |a_j|^2), so x_j = X_k,jj conj(a_j) b_j.
+    # A dropped conjugate, a missing Theta or a wrong power fails this.
+    r = synth.rng(3)
+    n = 9
+    a = (r.uniform(0.5, 2.0, n) * np.exp(1j * r.uniform(0, 2 * np.pi, n)))
+    b = r.standard_normal(n) + 1j * r.standard_normal(n)
+    for nests in (0, 1, 3, 6):
+        x, run = dense.nn_normal_solve(np.diag(a), b, depth, 0.0, nests)
+        th = 1.0 / np.sum(np.abs(a) ** 2)
+        xk = (1.0 - (1.0 - th * np.abs(a) ** 2) ** ((depth + 1) ** nests)) / np.abs(a) ** 2
+        want = xk * a.conj() * b
+        assert run.nests == nests
+        assert np.max(np.abs(x - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_normal_solve_spectral_nest_count(complex_):
+    # R_k = (I - Theta W)^((L+1)^k) with W = V diag(sigma^2) V^H, so
+    # s_k = sqrt(sum_j (1 - Theta sigma_j^2)^(2 (L+1)^k)) / N: the nest count is known in advance.
+    n, cond, depth, tol = 48, 20.0, 2, 1e-9
+    a, sig = synth.general_svd(n, cond, seed=5, complex_=complex_)
+    b = synth.gaussian_rhs(n, 2, seed=6)
+    th = 1.0 / np.sum(sig ** 2)
+    pred = [math.sqrt(np.sum((1.0 - th * sig ** 2) ** (2 * (depth + 1) ** k))) / n for k in range(40)]
+    k_stop = next(k for k, s in enumerate(pred) if s < tol)
+    x, run = dense.nn_normal_solve(a, b, depth, tol, 40)
+    assert run.status == dense.STATUS_OK and run.nests == k_stop
+    for k in range(k_stop + 1):
+        assert abs(run.history[k] - pred[k]) <= 1e-9 * pred[k] + 1e3 * U64
+    # and the solution solves A x = b: with X_k = W^-1 (I - R_k) and R_k a polynomial in W,
+    # x - x* = -R_k x*, so the relative error is at most ||R_k||_2 <= N s_k, plus the FP64 floor
+    true = np.linalg.solve(a, b)
+    err = np.linalg.norm(x - true) / np.linalg.norm(true)
+    assert err <= n * run.history[-1] + 64 * cond ** 2 * U64
+
+
+def test_normal_solve_nonsymmetric_matches_library():
+    # a general complex matrix with cond(A) = 1e3: the converged NN solution equals
+    # numpy.linalg.solve within the normal equations' FP64 error bound c cond(A)^2 u
+    n, cond = 40, 1e3
+    a, _ = synth.general_svd(n, cond, seed=11, complex_=True)
+    b = synth.gaussian_rhs(n, 3, seed=12) + 1j * synth.gaussian_rhs(n, 3, seed=13)
+    x, run = dense.nn_normal_solve(a, b, 2, 1e-13, 64)
+    assert run.status in (dense.STATUS_OK, dense.STATUS_NOT_CONVERGED)
+    true = np.linalg.solve(a, b)
+    assert np.linalg.norm(x - true) <= 64 * cond ** 2 * U64 * np.linalg.norm(true)
