@@ -177,6 +177,31 @@ int nn_solve_csr(const int32_t* row_ptr, const int32_t* col, const void* val, in
  * against concurrent solves. */
 int nn_set_spmv_variant(int variant);
 
+/* ---- general systems through the normal equations ----------------------------------------
+ * Corollary 3 (Eq. (linearsystemfinal), Eq. (nnlinearsystem)): A X = B for any nonsingular A,
+ * real or complex, solved as X = (A^H A)^-1 A^H B. W = A^H A is Hermitian positive definite;
+ * the dense NN runs on W from X_0 = I / Tr(W) with the caller's options (depth, tol on
+ * ||I - W X_k||_F / m, max_nests, dtype), and X = X_k A^H B. Squaring the condition number is
+ * inherent to the method: cond(W) = cond(A)^2, so NN_F64 is the dtype for badly conditioned A
+ * (the mixed BF16 chain stops at its accuracy floor with NN_ERR_NOT_CONVERGED there).
+ *
+ * is_complex = 0: A real FP64, row-major n x n, leading dimension lda >= n; B and X real FP64,
+ *                 row-major n x nrhs, leading dimensions ldb, ldx >= nrhs.
+ * is_complex = 1: A, B, X complex128 stored as interleaved (re, im) FP64 pairs, row-major, leading
+ *                 dimensions counted in complex elements. The solve runs on the real embedding
+ *                 z -> [[Re z, -Im z], [Im z, Re z]] of size m = 2n, which maps the complex
+ *                 products and A^H exactly onto real ones.
+ * All pointers are device memory owned by the caller; X must not overlap A or B. Needs
+ * nn_normal_workspace_bytes(n, nrhs, is_complex, opts->dtype) bytes of device workspace (the
+ * library allocates nothing). res holds the inversion's nest count, W-residual history and
+ * precision schedule. Returns the inversion's status (NN_OK, NN_ERR_NOT_CONVERGED,
+ * NN_ERR_DIVERGED: X still receives the solution from the last iterate) or an argument /
+ * workspace / CUDA error before or during the call (X then undefined). Synchronises `stream`. */
+size_t nn_normal_workspace_bytes(int64_t n, int64_t nrhs, int is_complex, int dtype);
+int nn_solve_normal(const void* A, int64_t n, int64_t lda, int is_complex, const void* B, int64_t ldb,
+                    int64_t nrhs, const nn_opts* opts, void* X, int64_t ldx, nn_result* res, void* workspace,
+                    size_t ws_bytes, void* stream);
+
 /* ---- batched small complex inversions ---------------------------------------------------
  * Many independent U x U complex64 matrices (U <= 64; massive-MIMO Gram matrices, the use the
  * paper names in Corollary 4) inverted by the right-multiplied NN loop in one persistent

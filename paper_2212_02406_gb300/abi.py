@@ -86,6 +86,9 @@ _SIGNATURES = {
                             c_size_t, c_void_p]),
     "nn_csr_workspace_bytes": (c_size_t, [c_int64, c_int64, c_int64, c_int]),
     "nn_set_spmv_variant": (c_int, [c_int]),
+    "nn_normal_workspace_bytes": (c_size_t, [c_int64, c_int64, c_int, c_int]),
+    "nn_solve_normal": (c_int, [c_void_p, c_int64, c_int64, c_int, c_void_p, c_int64, c_int64, POINTER(NNOpts),
+                                c_void_p, c_int64, POINTER(NNResult), c_void_p, c_size_t, c_void_p]),
     "nn_residual_noalloc": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_int64, POINTER(c_double), c_void_p]),
     "nn_server_request_bytes": (c_size_t, [c_int64, c_int64, c_int]),
     "nn_server_create": (c_int, [POINTER(NNServerOpts), POINTER(c_void_p)]),
@@ -242,6 +245,42 @@ def nn_residual(A, X, dtype, workspace, stream=None):
     out = c_double(0.0)
     st = lib().nn_residual(pa, lda, px, ldx, A.shape[0], d, ctypes.byref(out), pw, nw, _stream_ptr(stream))
     return st, out.value
+
+
+# ---- general systems through the normal equations -----------------------------------------
+
+def nn_normal_workspace_bytes(n: int, nrhs: int, is_complex: bool, dtype) -> int:
+    d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    return int(lib().nn_normal_workspace_bytes(int(n), int(nrhs), int(bool(is_complex)), d))
+
+
+def normal_workspace(n: int, nrhs: int, is_complex: bool, dtype, device=None):
+    import torch
+
+    nbytes = nn_normal_workspace_bytes(n, nrhs, is_complex, dtype)
+    if nbytes == 0:
+        raise ValueError("invalid sizes or dtype")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def nn_solve_normal(A, B, opts: NNOpts, X, workspace, stream=None):
+    """A X = B through the normal equations. A (n x n), B and X (n x nrhs): row-major CUDA
+    tensors, all float64 or all complex128. Returns (status, result dict of the inversion of W)."""
+    import torch
+
+    if A.dtype not in (torch.float64, torch.complex128):
+        raise TypeError("A must be float64 or complex128")
+    pa, lda = _mat(A, "A", A.dtype)
+    pb, ldb = _mat(B, "B", A.dtype)
+    px, ldx = _mat(X, "X", A.dtype)
+    n, nrhs = A.shape[0], B.shape[1]
+    if A.shape[1] != n or B.shape[0] != n or tuple(X.shape) != tuple(B.shape):
+        raise ValueError("A must be n x n, B and X n x nrhs")
+    pw, nw = _ws(workspace)
+    res = NNResult()
+    st = lib().nn_solve_normal(pa, n, lda, int(A.dtype == torch.complex128), pb, ldb, nrhs, ctypes.byref(opts), px,
+                               ldx, ctypes.byref(res), pw, nw, _stream_ptr(stream))
+    return st, res.as_dict()
 
 
 # ---- sparse chain ----------------------------------------------------------------------
