@@ -47,8 +47,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dense", choices=["dense", "sparse", "batched", "serve"])
-    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--workload", default="dense", choices=["dense", "sparse", "batched", "serve", "normal"])
+    ap.add_argument("--n", type=int, default=None, help="matrix size (dense 8192, normal 2048)")
+    ap.add_argument("--cond", type=float, default=1e2, help="cond(A) of the normal-equations workload")
     ap.add_argument("--kappa", type=float, default=1e2)
     ap.add_argument("--depth", type=int, default=2)
     ap.add_argument("--dtype", default="mixed_bf16", choices=["mixed_bf16", "f32", "f64", "f64_df"])
@@ -62,7 +63,10 @@ def parse_args():
     ap.add_argument("--spmv-variant", type=int, default=0, choices=[0, 1], help="0 auto (bulk-copy ring), 1 staged loads")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.n is None:
+        args.n = 2048 if args.workload == "normal" else 8192
+    return args
 
 
 # ---- clocks ------------------------------------------------------------------------------
@@ -214,7 +218,16 @@ def run_dense(args, rank, world, local_rank):
 
     peaks, peak_src = load_peaks()
     roofline = None
-    if tc_launches > 0 and tc_ms > 0:
+    if tc_launches > 0 and tc_ms > 0 and args.dtype != "mixed_bf16":
+        achieved = tc_flops / (tc_ms / 1e3) / 1e12
+        sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        peak = simt_peak_tflops(args.dtype, sm_mhz)
+        roofline = {"kernel": f"nn::gemm_simt_kernel<{'double' if args.dtype == 'f64' else 'float'}>",
+                    "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "peak_source": f"{args.dtype} CUDA-core peak from unit counts at {sm_mhz:.0f} MHz",
+                    "launches": tc_launches, "avg_launch_ms": round(tc_ms / tc_launches, 4)}
+    elif tc_launches > 0 and tc_ms > 0:
         achieved = tc_flops / (tc_ms / 1e3) / 1e12
         peak = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
         kernel = {1: "nn::tc::gemm_tc_kernel", 2: "nn::tc::gemm_tc_pair_kernel"}.get(args.gemm_variant,
@@ -294,6 +307,118 @@ def run_dense(args, rank, world, local_rank):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
     }
     return line
+
+
+# ---- general systems through the normal equations (Corollary 3) ------------------------------
+
+def simt_peak_tflops(dtype, sm_mhz, sms=152):
+    """CUDA-core peaks from unit counts and the sampled clock: FP32 128 FMA lanes per SM; FP64
+    4 FLOP per SM per clock (the nominal 1.25 TFLOP/s of a 152-SM GB300 at 2070 MHz)."""
+    per_clk = 4.0 if dtype == "f64" else 256.0
+    return sms * per_clk * sm_mhz * 1e6 / 1e12
+
+
+def run_normal(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2212_02406_gb300 import abi, build
+
+    build.build()
+    abi.lib()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n, cond, depth, tol = args.n, args.cond, args.depth, 1e-10
+    dtype = "f64" if args.dtype == "mixed_bf16" else args.dtype
+    a, sig = synth.general_svd(n, cond, seed=args.seed + rank)
+    b = synth.gaussian_rhs(n, 1, seed=args.seed + rank + 1)
+    A = torch.from_numpy(a).to(dev)
+    B = torch.from_numpy(b).to(dev)
+    X = torch.empty_like(B)
+    ws = abi.normal_workspace(n, 1, False, dtype, device=dev)
+    opts = abi.make_opts(depth, tol, 64, dtype, flags=abi.NN_FLAG_TIME_KERNELS)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        st, res = abi.nn_solve_normal(A, B, opts, X, ws, stream)
+        assert st == abi.NN_OK, (st, res)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    results = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        results.append(abi.nn_solve_normal(A, B, opts, X, ws, stream))
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    last = results[-1][1]
+    flops = last["flops"]
+    value = flops / (ms / 1e3) / 1e12
+    gemm_ms = sum(r["tc_ms"] for _, r in results)
+    gemm_flops = sum(r["tc_flops"] for _, r in results)
+    gemm_launches = sum(r["tc_launches"] for _, r in results)
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = simt_peak_tflops(dtype, sm_mhz)
+    achieved = gemm_flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
+    # solution check: relative residual of A x = b in FP64 on the host
+    xh = X.cpu().numpy()
+    rel = float(np.linalg.norm(b - a @ xh) / np.linalg.norm(b))
+    fwd = float(np.linalg.norm(xh - np.linalg.solve(a, b)) / np.linalg.norm(np.linalg.solve(a, b)))
+    e2e = None
+    if not args.no_e2e:
+        a_pin = torch.from_numpy(a).pin_memory()
+        b_pin = torch.from_numpy(b).pin_memory()
+        x_pin = torch.empty_like(b_pin).pin_memory()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        k_e2e = max(1, min(args.steps, 3))
+        for _ in range(k_e2e):
+            A.copy_(a_pin, non_blocking=True)
+            B.copy_(b_pin, non_blocking=True)
+            st_e, r_e = abi.nn_solve_normal(A, B, opts, X, ws, stream)
+            x_pin.copy_(X, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        te = (time.perf_counter() - t0) / k_e2e
+        e2e = {"value": round(r_e["flops"] / te / 1e12, 4), "unit": "TFLOP/s", "ms_per_step": round(te * 1e3, 3),
+               "h2d_bytes_per_step": (n * n + n) * 8, "d2h_bytes_per_step": n * 8, "steps": k_e2e,
+               "ok": st_e == abi.NN_OK}
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        from oracle import dense
+
+        t0 = time.perf_counter()
+        _, run = dense.nn_normal_solve(a, b, depth, 0.0, 1)
+        t = time.perf_counter() - t0
+        cflops = 2.0 * n ** 3 * (1 + (depth + 1) * 1 + 1) + 4.0 * n * n
+        cpu = {"value": round(cflops / t / 1e12, 5), "unit": "TFLOP/s", "cores": host_cores(), "kind": "oracle",
+               "sample": f"the FP64 NumPy oracle's nn_normal_solve at N={n} capped at one nest (W = A^T A, "
+                         f"residual, depth-{depth} nest, final residual, A^T b, X A^T b); {t:.2f} s"}
+    return {"metric": "time-to-solution and FP64 TFLOP/s of a general solve through the normal equations "
+                      "(Corollary 3)",
+            "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "time_to_solution_ms": round(ms, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": f"general real A N={n}, singular values geometric 1..1/{cond:g} (cond(A)={cond:g}, "
+                                   f"cond(W)={cond * cond:g}), Haar U, V; b ~ N(0,1); W = A^T A, X0 = I/Tr(W), "
+                                   f"depth {depth}, tol {tol:g} on ||I - W X||_F/N",
+                       "n": n, "cond": cond, "depth": depth, "tol": tol,
+                       "l2": f"A and W FP64 {n * n * 8 / 2**20:.0f} MiB each"},
+            "status_ok": all(s == abi.NN_OK for s, _ in results), "nests": last["nests"],
+            "w_residual": last["residual"], "solve_rel_residual": rel, "forward_error_vs_lapack": fwd,
+            "gpu_launches": sum(r["launches"] for _, r in results),
+            "roofline": {"kernel": f"nn::gemm_simt_kernel<{'double' if dtype == 'f64' else 'float'}>",
+                         "bound": "alu", "achieved": round(achieved, 4) if achieved else None,
+                         "peak": round(peak, 3), "unit": "TFLOP/s",
+                         "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
+                         "peak_source": f"{dtype} CUDA-core peak from unit counts at {sm_mhz:.0f} MHz",
+                         "launches": gemm_launches,
+                         "avg_launch_ms": round(gemm_ms / max(gemm_launches, 1), 4)},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}
 
 
 # ---- sparse workload (SpMV chain) -------------------------------------------------------
@@ -617,6 +742,8 @@ def main():
         line = run_sparse(args, rank, world, local_rank)
     elif args.workload == "serve":
         line = run_serve(args, rank, world, local_rank)
+    elif args.workload == "normal":
+        line = run_normal(args, rank, world, local_rank)
     else:
         line = run_batched(args, rank, world, local_rank)
     if rank == 0:

@@ -86,7 +86,7 @@ typedef struct nn_opts {
   int flags;           /* NN_FLAG_* bits                                                           */
 } nn_opts;
 
-/* nn_opts.flags: time every tensor-core GEMM launch with CUDA events on the call's stream
+/* nn_opts.flags: time every GEMM launch of the chain with CUDA events on the call's stream
  * (fills nn_result.tc_ms; costs two event records per GEMM). */
 #define NN_FLAG_TIME_KERNELS 1
 
@@ -100,9 +100,10 @@ typedef struct nn_result {
   double flops;                    /* algorithmic FLOPs: 2 N^3 per GEMM (split passes not counted) */
   double hw_flops;                 /* tensor-core FLOPs issued, split passes included              */
   int launches;                    /* kernel launches issued by the call                           */
-  int tc_launches;                 /* tcgen05 GEMM launches                                        */
+  int tc_launches;                 /* GEMM launches of the chain: tcgen05 for NN_MIXED_BF16,       */
+                                   /* CUDA-core for NN_F64 / NN_F32                                */
   double tc_ms;                    /* summed CUDA-event time of those launches (NN_FLAG_TIME_KERNELS) */
-  double tc_flops;                 /* 2 Np^3 per BF16 product pass of those launches               */
+  double tc_flops;                 /* 2 Np^3 per BF16 product pass (mixed) or 2 N^3 per GEMM (F64/F32) */
 } nn_result;
 
 /* Tensor-core GEMM tiling for the NN_MIXED_BF16 chain (a process-wide tuning knob; the

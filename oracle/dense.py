@@ -236,9 +236,16 @@ class NNRun:
     status: int = STATUS_OK
 
 
-def nn_invert(w: np.ndarray, x0: np.ndarray, depth: int, tol: float, max_nests: int = 64) -> NNRun:
-    """NN outer loop with the stop and divergence rules stated in the module docstring."""
-    if depth < 1:
+def nn_invert(w: np.ndarray, x0: np.ndarray, depth: int, tol: float, max_nests: int = 64,
+              depth_schedule=None) -> NNRun:
+    """NN outer loop with the stop and divergence rules stated in the module docstring.
+
+    ``depth_schedule`` (optional) gives nest k the depth depth_schedule[min(k, len - 1)]
+    instead of ``depth``: e.g. [2, 2, 1] runs two Chebyshev nests, then Newton nests, the
+    matrix form of the CNS construction (Corollary 4, Corollary 6). After nests of depths
+    L_0 .. L_{k-1} the iterate is the Neumann series of order prod (L_j + 1) - 1.
+    """
+    if depth < 1 or (depth_schedule is not None and min(depth_schedule) < 1):
         raise ValueError("inception depth must be >= 1")
     i = _eye_like(w)
     n = w.shape[0]
@@ -256,7 +263,8 @@ def nn_invert(w: np.ndarray, x0: np.ndarray, depth: int, tol: float, max_nests: 
             return NNRun(x, k, hist, STATUS_OK)
         if k == max_nests:
             break
-        x = nn_step_right(w, x, depth, r)
+        d = depth if not depth_schedule else depth_schedule[min(k, len(depth_schedule) - 1)]
+        x = nn_step_right(w, x, d, r)
     return NNRun(x, max_nests, hist, STATUS_NOT_CONVERGED if tol > 0 else STATUS_OK)
 
 

@@ -25,11 +25,24 @@ def apply_p(a, dinv: np.ndarray, v: np.ndarray) -> np.ndarray:
 
 def nn_sparse_solve(a, b: np.ndarray, depth: int, nests: int, dinv: np.ndarray | None = None) -> np.ndarray:
     """x = D^-1 prod_j sum_n P^{n (L+1)^j} b for ``nests`` factors (FP64 or as given)."""
+    return nn_sparse_solve_sched(a, b, [depth] * nests, dinv)
+
+
+def nn_sparse_solve_sched(a, b: np.ndarray, depths, dinv: np.ndarray | None = None) -> np.ndarray:
+    """The factor product with a depth per factor:
+
+        x = D^-1 prod_j ( sum_{n=0}^{L_j} P^{n m_j} ) b,   m_j = prod_{q<j} (L_q + 1),
+
+    the Chebyshev-then-Neumann (CNS) construction of Corollary 4 and Corollary 6 when the
+    first factors have L = 2 (Chebyshev nests) and the rest L = 1 (the factorised series
+    prod_t (I + P^{2^t}) on the preconditioner those nests built). The product is the
+    Neumann series of order prod_j (L_j + 1) - 1, in that many sparse products.
+    """
     if dinv is None:
         dinv = 1.0 / a.diagonal()
     z = np.array(b, copy=True)
-    for j in range(nests):
-        t = (depth + 1) ** j
+    t = 1
+    for depth in depths:
         acc = z.copy()
         u = z
         for _n in range(depth):
@@ -37,6 +50,7 @@ def nn_sparse_solve(a, b: np.ndarray, depth: int, nests: int, dinv: np.ndarray |
                 u = apply_p(a, dinv, u)
             acc = acc + u
         z = acc
+        t *= depth + 1
     return (dinv[:, None] * z) if z.ndim == 2 else dinv * z
 
 

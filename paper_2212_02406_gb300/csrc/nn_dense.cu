@@ -154,68 +154,7 @@ void init_result(nn_result* r) {
   r->status = NN_ERR_ARG;
 }
 
-// ---------------------------------------------------------------------------------------
-// CUDA-core chains (FP64 / FP32).
-
-template <typename T>
-int run_simt(cudaStream_t st, int n, const T* A, int64_t lda, T* const X[2], T* R, T* const Tb[2],
-             const nn_opts& o, const Common& cm, nn_result* res, int* final_idx) {
-  const int nparts = gemm_simt_partials<T>(n, n);
-  int cur = 0;
-  res->nests = 0;
-  for (int k = 0;; ++k) {
-    NN_TRY(gemm_simt<T>(st, n, n, n, A, lda, X[cur], n, R, n, EPI_RESIDUAL, nullptr, 0, n, cm.partial));
-    NN_TRY(reduce_rms(st, cm.partial, nparts, 1.0 / double(n), cm.scal));
-    res->gemms += 1;
-    res->launches += 2;
-    double s = 0;
-    int dev_err = 0;
-    NN_TRY(fetch_scalar(st, cm, &s, &dev_err));
-    res->history[k] = s;
-    res->pieces[k] = 0;
-    res->nests = k;
-    res->residual = s;
-    const int verdict = judge(o, k, res->history);
-    if (verdict >= 0) {
-      res->status = verdict;
-      break;
-    }
-    const T* t_cur = R;
-    for (int j = 1; j < o.depth; ++j) {
-      T* t_nxt = Tb[j & 1];
-      NN_TRY(gemm_simt<T>(st, n, n, n, R, n, t_cur, n, t_nxt, n, EPI_ADD, R, n, n, nullptr));
-      t_cur = t_nxt;
-      res->gemms += 1;
-      res->launches += 1;
-    }
-    NN_TRY(gemm_simt<T>(st, n, n, n, X[cur], n, t_cur, n, X[cur ^ 1], n, EPI_ADD, X[cur], n, n, nullptr));
-    res->gemms += 1;
-    res->launches += 1;
-    cur ^= 1;
-  }
-  *final_idx = cur;
-  return NN_OK;
-}
-
-// ---------------------------------------------------------------------------------------
-// Tensor-core mixed chain.
-
-// Operand-piece pairs for a split product with p pieces per operand, smallest terms first:
-// p = 1: hh;  p = 2: lh, hl, hh;  p = 3: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0).
-int seg_pairs(int p, int (*pairs)[2]) {
-  static const int p1[1][2] = {{0, 0}};
-  static const int p2[3][2] = {{1, 0}, {0, 1}, {0, 0}};
-  static const int p3[6][2] = {{2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}, {0, 0}};
-  const int(*src)[2] = p == 1 ? p1 : (p == 2 ? p2 : p3);
-  const int cnt = p == 1 ? 1 : (p == 2 ? 3 : 6);
-  for (int i = 0; i < cnt; ++i) {
-    pairs[i][0] = src[i][0];
-    pairs[i][1] = src[i][1];
-  }
-  return cnt;
-}
-
-// CUDA events around each tensor-core GEMM launch (NN_FLAG_TIME_KERNELS).
+// CUDA events around each GEMM launch of a chain (NN_FLAG_TIME_KERNELS).
 struct LaunchTimer {
   bool on = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
@@ -254,6 +193,84 @@ struct LaunchTimer {
     return t;
   }
 };
+
+// ---------------------------------------------------------------------------------------
+// CUDA-core chains (FP64 / FP32).
+
+template <typename T>
+int run_simt(cudaStream_t st, int n, const T* A, int64_t lda, T* const X[2], T* R, T* const Tb[2],
+             const nn_opts& o, const Common& cm, nn_result* res, int* final_idx) {
+  const int nparts = gemm_simt_partials<T>(n, n);
+  const double gemm_flops = 2.0 * double(n) * double(n) * double(n);
+  LaunchTimer timer;
+  timer.on = (o.flags & NN_FLAG_TIME_KERNELS) != 0;
+  auto timed = [&](auto&& launch) -> int {
+    NN_TRY(timer.begin(st));
+    NN_TRY(launch());
+    NN_TRY(timer.end(st));
+    res->tc_launches += 1;
+    res->tc_flops += gemm_flops;
+    return NN_OK;
+  };
+  int cur = 0;
+  res->nests = 0;
+  for (int k = 0;; ++k) {
+    NN_TRY(timed([&] {
+      return gemm_simt<T>(st, n, n, n, A, lda, X[cur], n, R, n, EPI_RESIDUAL, nullptr, 0, n, cm.partial);
+    }));
+    NN_TRY(reduce_rms(st, cm.partial, nparts, 1.0 / double(n), cm.scal));
+    res->gemms += 1;
+    res->launches += 2;
+    double s = 0;
+    int dev_err = 0;
+    NN_TRY(fetch_scalar(st, cm, &s, &dev_err));
+    res->history[k] = s;
+    res->pieces[k] = 0;
+    res->nests = k;
+    res->residual = s;
+    const int verdict = judge(o, k, res->history);
+    if (verdict >= 0) {
+      res->status = verdict;
+      break;
+    }
+    const T* t_cur = R;
+    for (int j = 1; j < o.depth; ++j) {
+      T* t_nxt = Tb[j & 1];
+      NN_TRY(timed([&] { return gemm_simt<T>(st, n, n, n, R, n, t_cur, n, t_nxt, n, EPI_ADD, R, n, n, nullptr); }));
+      t_cur = t_nxt;
+      res->gemms += 1;
+      res->launches += 1;
+    }
+    NN_TRY(timed([&] {
+      return gemm_simt<T>(st, n, n, n, X[cur], n, t_cur, n, X[cur ^ 1], n, EPI_ADD, X[cur], n, n, nullptr);
+    }));
+    res->gemms += 1;
+    res->launches += 1;
+    cur ^= 1;
+  }
+  *final_idx = cur;
+  // every timed launch precedes the last residual read-back, which synchronised the stream
+  if (timer.on) res->tc_ms = timer.total_ms();
+  return NN_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Tensor-core mixed chain.
+
+// Operand-piece pairs for a split product with p pieces per operand, smallest terms first:
+// p = 1: hh;  p = 2: lh, hl, hh;  p = 3: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0).
+int seg_pairs(int p, int (*pairs)[2]) {
+  static const int p1[1][2] = {{0, 0}};
+  static const int p2[3][2] = {{1, 0}, {0, 1}, {0, 0}};
+  static const int p3[6][2] = {{2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}, {0, 0}};
+  const int(*src)[2] = p == 1 ? p1 : (p == 2 ? p2 : p3);
+  const int cnt = p == 1 ? 1 : (p == 2 ? 3 : 6);
+  for (int i = 0; i < cnt; ++i) {
+    pairs[i][0] = src[i][0];
+    pairs[i][1] = src[i][1];
+  }
+  return cnt;
+}
 
 int tc_product(cudaStream_t st, TcGemmArgs& g, int pieces, __nv_bfloat16* const* a_pieces,
                __nv_bfloat16* const* b_pieces, const Common& cm, nn_result* res, int* grid, LaunchTimer* tm) {

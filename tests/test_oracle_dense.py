@@ -264,3 +264,26 @@ def test_normal_solve_nonsymmetric_matches_library():
     assert run.status in (dense.STATUS_OK, dense.STATUS_NOT_CONVERGED)
     true = np.linalg.solve(a, b)
     assert np.linalg.norm(x - true) <= 64 * cond ** 2 * U64 * np.linalg.norm(true)
+
+
+# --- a depth per nest (CNS: Chebyshev nests, then Newton nests; Corollary 4, Corollary 6) ---
+
+@pytest.mark.parametrize("sched", [[2, 2, 1], [2, 1, 1, 1], [1, 3, 2], [3]])
+def test_depth_schedule_is_neumann_of_product_order(sched):
+    # After nests of depths L_0 .. L_{k-1} the iterate is the Neumann series of order
+    # prod (L_j + 1) - 1 (Corollary 2 with R_{k+1} = R_k^(L_k + 1)); on a diagonal matrix with a
+    # scalar start this is the closed form (1 - (1 - alpha lambda)^m) / lambda.
+    lam = np.array([0.2, 0.7, 1.0, 1.9, 3.0])
+    alpha = 2.0 / (lam.min() + lam.max())
+    nests = len(sched) + 1   # the last depth repeats
+    run = dense.nn_invert(np.diag(lam), dense.precond_scalar(5, alpha), 1, 0.0, nests, depth_schedule=sched)
+    m = int(np.prod([sched[min(k, len(sched) - 1)] + 1 for k in range(nests)]))
+    want = (1.0 - (1.0 - alpha * lam) ** m) / lam
+    assert np.allclose(np.diag(run.x), want, rtol=64 * U64 * m, atol=0)
+    # and on a full SPD matrix it equals the right Neumann series of that order
+    a = synth.spd_wishart(24, seed=6)
+    x0 = dense.precond_trace(a)
+    run = dense.nn_invert(a, x0, 1, 0.0, 3, depth_schedule=sched)
+    m = int(np.prod([sched[min(k, len(sched) - 1)] + 1 for k in range(3)]))
+    ns = dense.neumann_series_right(a, x0, m - 1)
+    assert np.linalg.norm(run.x - ns) <= 1e-11 * np.linalg.norm(ns)

@@ -41,6 +41,18 @@ def test_sparse_chain_equals_jacobi_sweeps(depth, kind):
         assert np.linalg.norm(x - want) <= 1e-12 * np.linalg.norm(want)
 
 
+@pytest.mark.parametrize("depths", [[2, 1, 1], [2, 2, 1, 1, 1], [1, 2], [3, 1, 2]])
+def test_sparse_schedule_equals_jacobi_sweeps(depths):
+    # a depth per factor (CNS: Chebyshev factors, then the factorised Neumann series) is the
+    # Neumann series of order prod (L_j + 1) - 1: exactly prod (L_j + 1) Jacobi sweeps
+    m = synth.random_sparse_spd(60, per_row=5, seed=9)
+    a = m.to_scipy()
+    b = synth.gaussian_rhs(m.n, 2, seed=4)
+    x = sparse.nn_sparse_solve_sched(a, b, depths)
+    want = _jacobi_sweeps(a, b, int(np.prod([d + 1 for d in depths])))
+    assert np.linalg.norm(x - want) <= 1e-12 * np.linalg.norm(want)
+
+
 @pytest.mark.parametrize("depth", [1, 2])
 def test_sparse_chain_equals_dense_explicit_form(depth):
     m = synth.random_sparse_spd(40, per_row=4, seed=8)
