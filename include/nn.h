@@ -78,12 +78,18 @@ typedef struct nn_opts {
   double tol;          /* stop at the first k with s_k < tol; tol <= 0 runs exactly max_nests     */
   int max_nests;       /* 0 .. NN_MAX_HISTORY-1                                                   */
   int dtype;           /* nn_dtype                                                                */
-  double refine_below; /* NN_MIXED_BF16: switch to refine nests once s_k * sqrt(N) < refine_below;
-                          <= 0 selects the default 0.1. A stall (s_{k+1} > 0.5 s_k) also switches. */
+  double refine_below; /* NN_MIXED_BF16: also use level-3 residuals once s_k * sqrt(N) < refine_below
+                          (<= 0: off; the floor-based level schedule alone decides)             */
   int bulk_pieces;     /* NN_MIXED_BF16: starting precision level 1..4 (0 = 1): the BF16 pieces of
                           the first residuals (1, 2, 3, 3) and updates (1, 2, 2, 3); the chain
                           raises the level itself as the residual nears each level's floor     */
   int flags;           /* NN_FLAG_* bits                                                           */
+  const int32_t* depth_schedule; /* optional host array: nest k uses depth_schedule[min(k, len-1)]
+                          instead of `depth` (each 1..16). [2, 2, 1] runs two Chebyshev nests,
+                          then Newton nests: the matrix form of the Chebyshev-then-Neumann
+                          (CNS) construction of Corollary 4 / Corollary 6; after nests of depths
+                          L_0..L_{k-1} X_k is the Neumann series of order prod(L_j + 1) - 1    */
+  int schedule_len;    /* entries of depth_schedule, 0 .. NN_MAX_HISTORY (0: every nest `depth`) */
 } nn_opts;
 
 /* nn_opts.flags: time every GEMM launch of the chain with CUDA events on the call's stream
@@ -169,6 +175,17 @@ size_t nn_csr_workspace_bytes(int64_t n, int64_t nnz, int64_t nrhs, int dtype);
 int nn_solve_csr(const int32_t* row_ptr, const int32_t* col, const void* val, int64_t n, int64_t nnz,
                  int dtype, const void* B, int64_t ldb, int64_t nrhs, int depth, int nests, double tol,
                  void* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_bytes, void* stream);
+
+/* The same chain with a depth per factor (host array depths[nfactors], each 1..16):
+ *     X = D^-1 prod_{j=0}^{nfactors-1} ( sum_{n=0}^{L_j} P^{n m_j} ) B,   m_j = prod_{q<j} (L_q + 1),
+ * i.e. Chebyshev factors (L = 2) followed by the factorised Neumann series prod_t (I + P^{2^t})
+ * (L = 1) on the preconditioner they built: the CNS construction for sparse matrices
+ * (Corollary 4, Eq. (CNS); Corollary 6). prod_j (L_j + 1) - 1 sparse products, at most 2^31 - 1
+ * (else NN_ERR_ARG). Arguments, tol, res and errors as nn_solve_csr (nests -> nfactors). */
+int nn_solve_csr_sched(const int32_t* row_ptr, const int32_t* col, const void* val, int64_t n, int64_t nnz,
+                       int dtype, const void* B, int64_t ldb, int64_t nrhs, const int32_t* depths, int nfactors,
+                       double tol, void* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_bytes,
+                       void* stream);
 
 /* Sparse-product kernel for one right-hand side (a process-wide tuning knob; both variants
  * sum each row's terms in the same order, so results are bitwise identical): 0 = automatic

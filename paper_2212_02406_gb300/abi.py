@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import POINTER, c_double, c_int, c_int64, c_size_t, c_void_p
+from ctypes import POINTER, c_double, c_int, c_int32, c_int64, c_size_t, c_void_p
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "lib", "libnn.so")
@@ -36,7 +36,8 @@ NN_MAX_HISTORY = 65
 
 class NNOpts(ctypes.Structure):
     _fields_ = [("depth", c_int), ("tol", c_double), ("max_nests", c_int), ("dtype", c_int),
-                ("refine_below", c_double), ("bulk_pieces", c_int), ("flags", c_int)]
+                ("refine_below", c_double), ("bulk_pieces", c_int), ("flags", c_int),
+                ("depth_schedule", POINTER(c_int32)), ("schedule_len", c_int)]
 
 
 class NNResult(ctypes.Structure):
@@ -86,6 +87,9 @@ _SIGNATURES = {
                             c_size_t, c_void_p]),
     "nn_csr_workspace_bytes": (c_size_t, [c_int64, c_int64, c_int64, c_int]),
     "nn_set_spmv_variant": (c_int, [c_int]),
+    "nn_solve_csr_sched": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int, c_void_p, c_int64, c_int64,
+                                   POINTER(c_int32), c_int, c_double, c_void_p, c_int64, POINTER(NNResult), c_void_p,
+                                   c_size_t, c_void_p]),
     "nn_normal_workspace_bytes": (c_size_t, [c_int64, c_int64, c_int, c_int]),
     "nn_solve_normal": (c_int, [c_void_p, c_int64, c_int64, c_int, c_void_p, c_int64, c_int64, POINTER(NNOpts),
                                 c_void_p, c_int64, POINTER(NNResult), c_void_p, c_size_t, c_void_p]),
@@ -158,9 +162,16 @@ NN_FLAG_TIME_KERNELS = 1
 
 
 def make_opts(depth=2, tol=1e-6, max_nests=64, dtype="f64", refine_below=0.0, bulk_pieces=1,
-              flags=0) -> NNOpts:
+              flags=0, depth_schedule=None) -> NNOpts:
+    """depth_schedule: optional per-nest depths (the last one repeats), e.g. [2, 2, 1]."""
     d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
-    return NNOpts(int(depth), float(tol), int(max_nests), d, float(refine_below), int(bulk_pieces), int(flags))
+    o = NNOpts(int(depth), float(tol), int(max_nests), d, float(refine_below), int(bulk_pieces), int(flags))
+    if depth_schedule:
+        arr = (c_int32 * len(depth_schedule))(*[int(x) for x in depth_schedule])
+        o.depth_schedule = ctypes.cast(arr, POINTER(c_int32))
+        o.schedule_len = len(depth_schedule)
+        o._schedule_keepalive = arr  # the C side reads the array during the call
+    return o
 
 
 def workspace(n: int, dtype="f64", host=False, device=None):
@@ -309,10 +320,7 @@ def csr_workspace(n: int, nnz: int, nrhs: int, dtype, device=None):
     return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
 
 
-def nn_solve_csr(row_ptr, col, val, B, depth, nests, tol, X, workspace, stream=None, double_float=False):
-    """CSR (int32 row_ptr/col, float val) on the device; B and X are (nrhs, n) row-major
-    tensors, i.e. column-major n x nrhs blocks with leading dimension n. Returns (status, result).
-    double_float=True runs FP64 data in double-float arithmetic (NN_F64_DF)."""
+def _csr_args(row_ptr, col, val, B, X, double_float):
     import torch
 
     for name, t in (("row_ptr", row_ptr), ("col", col)):
@@ -333,12 +341,33 @@ def nn_solve_csr(row_ptr, col, val, B, depth, nests, tol, X, workspace, stream=N
     # a dimension of extent 1 may carry any stride: the leading dimension is then n
     ldb = B.stride(0) if nrhs > 1 else n
     ldx = X.stride(0) if nrhs > 1 else n
+    return d, n, nrhs, ldb, ldx
+
+
+def nn_solve_csr(row_ptr, col, val, B, depth, nests, tol, X, workspace, stream=None, double_float=False):
+    """CSR (int32 row_ptr/col, float val) on the device; B and X are (nrhs, n) row-major
+    tensors, i.e. column-major n x nrhs blocks with leading dimension n. Returns (status, result).
+    double_float=True runs FP64 data in double-float arithmetic (NN_F64_DF)."""
+    d, n, nrhs, ldb, ldx = _csr_args(row_ptr, col, val, B, X, double_float)
     pw, nw = _ws(workspace)
     res = NNResult()
     st = lib().nn_solve_csr(c_void_p(row_ptr.data_ptr()), c_void_p(col.data_ptr()), c_void_p(val.data_ptr()), n,
                             val.numel(), d, c_void_p(B.data_ptr()), ldb, nrhs, int(depth), int(nests),
                             float(tol), c_void_p(X.data_ptr()), ldx, ctypes.byref(res), pw, nw,
                             _stream_ptr(stream))
+    return st, res.as_dict()
+
+
+def nn_solve_csr_sched(row_ptr, col, val, B, depths, tol, X, workspace, stream=None, double_float=False):
+    """nn_solve_csr with a depth per factor (e.g. [2, 2, 1, 1, 1]: the sparse CNS construction)."""
+    d, n, nrhs, ldb, ldx = _csr_args(row_ptr, col, val, B, X, double_float)
+    arr = (c_int32 * max(len(depths), 1))(*[int(x) for x in depths])
+    pw, nw = _ws(workspace)
+    res = NNResult()
+    st = lib().nn_solve_csr_sched(c_void_p(row_ptr.data_ptr()), c_void_p(col.data_ptr()), c_void_p(val.data_ptr()),
+                                  n, val.numel(), d, c_void_p(B.data_ptr()), ldb, nrhs, arr, len(depths),
+                                  float(tol), c_void_p(X.data_ptr()), ldx, ctypes.byref(res), pw, nw,
+                                  _stream_ptr(stream))
     return st, res.as_dict()
 
 

@@ -149,6 +149,21 @@ int judge(const nn_opts& o, int k, const double* hist) {
   return -1;
 }
 
+// Depth of nest k: the schedule's entry (the last one repeats), else opts.depth.
+int nest_depth(const nn_opts& o, int k) {
+  if (o.schedule_len <= 0 || o.depth_schedule == nullptr) return o.depth;
+  return o.depth_schedule[k < o.schedule_len ? k : o.schedule_len - 1];
+}
+
+int max_depth(const nn_opts& o) {
+  int d = o.depth;
+  if (o.schedule_len > 0 && o.depth_schedule != nullptr) {
+    d = 1;
+    for (int k = 0; k < o.schedule_len; ++k) d = o.depth_schedule[k] > d ? o.depth_schedule[k] : d;
+  }
+  return d;
+}
+
 void init_result(nn_result* r) {
   memset(r, 0, sizeof(*r));
   r->status = NN_ERR_ARG;
@@ -234,7 +249,7 @@ int run_simt(cudaStream_t st, int n, const T* A, int64_t lda, T* const X[2], T* 
       break;
     }
     const T* t_cur = R;
-    for (int j = 1; j < o.depth; ++j) {
+    for (int j = 1; j < nest_depth(o, k); ++j) {
       T* t_nxt = Tb[j & 1];
       NN_TRY(timed([&] { return gemm_simt<T>(st, n, n, n, R, n, t_cur, n, t_nxt, n, EPI_ADD, R, n, n, nullptr); }));
       t_cur = t_nxt;
@@ -354,8 +369,9 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
     g.np = np;
     g.n_id = n;
     g.mode = EPI_RESIDUAL;
-    g.out_f32 = (o.depth >= 2) ? w.r32 : nullptr;
-    g.n_row = (o.depth >= 2) ? hp : 0;
+    // R in FP32 and row pieces feed the Horner GEMMs of nests with depth >= 2
+    g.out_f32 = (max_depth(o) >= 2) ? w.r32 : nullptr;
+    g.n_row = (max_depth(o) >= 2) ? hp : 0;
     g.n_col = hp;
     for (int i = 0; i < 3; ++i) {
       g.row_pieces[i] = w.r_row[i];
@@ -452,14 +468,16 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
     if (k >= 1 && level < 3 && res->history[k - 1] > 0) {
       const double ratio = s / res->history[k - 1];
       if (ratio > 0 && ratio < 1) {
-        const double s_pred = s * pow(ratio, double(o.depth + 1));
+        // s_k / s_{k-1} = rho^(m_{k-1} L_{k-1}) and s_{k+1} / s_k = rho^(m_k L_k), m_k = m_{k-1} (L_{k-1} + 1)
+        const double lp = double(nest_depth(o, k - 1)), lk = double(nest_depth(o, k));
+        const double s_pred = s * pow(ratio, (lp + 1.0) * lk / lp);
         while (next_level < 3 && s_pred < 8.0 * level_floor(next_level, c)) ++next_level;
         if (o.tol > 0 && s_pred < o.tol && next_level < 3) next_level = 3;
       }
     }
     // Horner: T_1 = R (its column pieces), T_{j+1} = R + R T_j.
     __nv_bfloat16* const* t_cur = w.r_col;
-    for (int j = 1; j < o.depth; ++j) {
+    for (int j = 1; j < nest_depth(o, k); ++j) {
       TcGemmArgs g;
       g.np = np;
       g.n_id = n;
@@ -507,6 +525,12 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
 int check_opts(const nn_opts* o, int64_t n) {
   if (o == nullptr) return NN_ERR_ARG;
   if (o->depth < 1 || o->depth > 16) return NN_ERR_ARG;
+  if (o->schedule_len < 0 || o->schedule_len > NN_MAX_HISTORY) return NN_ERR_ARG;
+  if (o->schedule_len > 0) {
+    if (o->depth_schedule == nullptr) return NN_ERR_ARG;
+    for (int k = 0; k < o->schedule_len; ++k)
+      if (o->depth_schedule[k] < 1 || o->depth_schedule[k] > 16) return NN_ERR_ARG;
+  }
   if (o->max_nests < 0 || o->max_nests > NN_MAX_HISTORY - 1) return NN_ERR_ARG;
   if (!valid_dtype(o->dtype)) return NN_ERR_ARG;
   if (n < 1 || n > 32768) return NN_ERR_ARG;
@@ -561,7 +585,9 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     res->launches += 3;
   }
   // Algorithmic work of the method: (L+1) GEMMs per nest plus the final residual.
-  res->flops = 2.0 * double(n) * double(n) * double(n) * double((o.depth + 1) * res->nests + 1);
+  double gemms = 1.0;
+  for (int k = 0; k < res->nests; ++k) gemms += double(nest_depth(o, k) + 1);
+  res->flops = 2.0 * double(n) * double(n) * double(n) * gemms;
   NN_CUDA_TRY(cudaStreamSynchronize(st));
   int dev_err = 0;
   NN_CUDA_TRY(cudaMemcpy(&dev_err, cm.err, sizeof(int), cudaMemcpyDeviceToHost));

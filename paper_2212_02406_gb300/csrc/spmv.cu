@@ -690,7 +690,7 @@ __global__ void reduce_pair_kernel(const double* __restrict__ partial, int count
 
 template <class P>
 int solve_csr(const int* rp, const int* col, const typename P::In* val, int64_t n64, int64_t nnz,
-              const typename P::In* B, int64_t ldb, int64_t nrhs64, int depth, int nests, double tol,
+              const typename P::In* B, int64_t ldb, int64_t nrhs64, const int* depths, int nests, double tol,
               typename P::In* X, int64_t ldx, nn_result* res, void* ws, size_t ws_bytes, cudaStream_t st) {
   using V = typename P::V;
   using In = typename P::In;
@@ -737,9 +737,10 @@ int solve_csr(const int* rp, const int* col, const typename P::In* val, int64_t 
 
   int applied = 0;
   res->status = NN_OK;
+  long long t = 1;  // m_j = prod_{q<j} (L_q + 1): the power of P one block of factor j applies
   for (int j = 0; j < nests; ++j) {
-    long long t = 1;
-    for (int q = 0; q < j; ++q) t *= (depth + 1);
+    const int depth = depths[j];
+    if (j > 0) t *= (depths[j - 1] + 1);
     const V* src = z;
     int ping = 0;
     for (int blk = 1; blk <= depth; ++blk) {
@@ -834,17 +835,23 @@ size_t nn_csr_workspace_bytes(int64_t n, int64_t nnz, int64_t nrhs, int dtype) {
   return csr_ws_bytes(n, nnz, nrhs, dtype);
 }
 
-int nn_solve_csr(const int32_t* row_ptr, const int32_t* col, const void* val, int64_t n, int64_t nnz, int dtype,
-                 const void* B, int64_t ldb, int64_t nrhs, int depth, int nests, double tol, void* X, int64_t ldx,
-                 nn_result* res, void* workspace, size_t ws_bytes, void* stream) {
+static int solve_csr_any(const int32_t* row_ptr, const int32_t* col, const void* val, int64_t n, int64_t nnz,
+                         int dtype, const void* B, int64_t ldb, int64_t nrhs, const int* depths, int nests,
+                         double tol, void* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_bytes,
+                         void* stream) {
   if (res == nullptr) return NN_ERR_ARG;
   memset(res, 0, sizeof(*res));
   res->status = NN_ERR_ARG;
   if (row_ptr == nullptr || col == nullptr || val == nullptr || B == nullptr || X == nullptr) return NN_ERR_ARG;
-  if (depth < 1 || nests < 0 || nests > NN_MAX_HISTORY - 1 || ldb < n || ldx < n || isnan(tol)) return NN_ERR_ARG;
-  // (L+1)^nests - 1 sparse products must stay countable
-  double total = pow(double(depth + 1), double(nests));
-  if (total > 4.0e9) return NN_ERR_ARG;
+  if (nests < 0 || nests > NN_MAX_HISTORY - 1 || ldb < n || ldx < n || isnan(tol)) return NN_ERR_ARG;
+  if (nests > 0 && depths == nullptr) return NN_ERR_ARG;
+  // prod (L_j + 1) - 1 sparse products must stay countable
+  double total = 1.0;
+  for (int j = 0; j < nests; ++j) {
+    if (depths[j] < 1 || depths[j] > 16) return NN_ERR_ARG;
+    total *= double(depths[j] + 1);
+  }
+  if (total > 2147483647.0) return NN_ERR_ARG;
   const size_t need = nn_csr_workspace_bytes(n, nnz, nrhs, dtype);
   if (need == 0) return NN_ERR_ARG;
   if (workspace == nullptr || ws_bytes < need) {
@@ -855,15 +862,39 @@ int nn_solve_csr(const int32_t* row_ptr, const int32_t* col, const void* val, in
   int s;
   if (dtype == NN_F64)
     s = solve_csr<ArithF64>(row_ptr, col, static_cast<const double*>(val), n, nnz, static_cast<const double*>(B), ldb,
-                            nrhs, depth, nests, tol, static_cast<double*>(X), ldx, res, workspace, ws_bytes, st);
+                            nrhs, depths, nests, tol, static_cast<double*>(X), ldx, res, workspace, ws_bytes, st);
   else if (dtype == NN_F64_DF)
     s = solve_csr<ArithDF>(row_ptr, col, static_cast<const double*>(val), n, nnz, static_cast<const double*>(B), ldb,
-                           nrhs, depth, nests, tol, static_cast<double*>(X), ldx, res, workspace, ws_bytes, st);
+                           nrhs, depths, nests, tol, static_cast<double*>(X), ldx, res, workspace, ws_bytes, st);
   else
     s = solve_csr<ArithF32>(row_ptr, col, static_cast<const float*>(val), n, nnz, static_cast<const float*>(B), ldb,
-                            nrhs, depth, nests, tol, static_cast<float*>(X), ldx, res, workspace, ws_bytes, st);
+                            nrhs, depths, nests, tol, static_cast<float*>(X), ldx, res, workspace, ws_bytes, st);
   res->status = s;
   return s;
+}
+
+int nn_solve_csr(const int32_t* row_ptr, const int32_t* col, const void* val, int64_t n, int64_t nnz, int dtype,
+                 const void* B, int64_t ldb, int64_t nrhs, int depth, int nests, double tol, void* X, int64_t ldx,
+                 nn_result* res, void* workspace, size_t ws_bytes, void* stream) {
+  if (depth < 1 || depth > 16 || nests < 0 || nests > NN_MAX_HISTORY - 1) {
+    if (res != nullptr) {
+      memset(res, 0, sizeof(*res));
+      res->status = NN_ERR_ARG;
+    }
+    return NN_ERR_ARG;
+  }
+  int depths[NN_MAX_HISTORY];
+  for (int j = 0; j < nests; ++j) depths[j] = depth;
+  return solve_csr_any(row_ptr, col, val, n, nnz, dtype, B, ldb, nrhs, depths, nests, tol, X, ldx, res, workspace,
+                       ws_bytes, stream);
+}
+
+int nn_solve_csr_sched(const int32_t* row_ptr, const int32_t* col, const void* val, int64_t n, int64_t nnz,
+                       int dtype, const void* B, int64_t ldb, int64_t nrhs, const int32_t* depths, int nfactors,
+                       double tol, void* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_bytes,
+                       void* stream) {
+  return solve_csr_any(row_ptr, col, val, n, nnz, dtype, B, ldb, nrhs, depths, nfactors, tol, X, ldx, res, workspace,
+                       ws_bytes, stream);
 }
 
 }  // extern "C"

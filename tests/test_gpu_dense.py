@@ -281,3 +281,31 @@ def test_gemm_tilings_agree_bitwise(nn, n):
         assert np.array_equal(x1, x2)
         for h1, h2 in zip(r1["history"], r2["history"]):
             assert abs(h1 - h2) <= 1e-12 * h1
+
+
+@pytest.mark.parametrize("sched", [[2, 2, 1], [1, 3], [3, 1, 2]])
+def test_depth_schedule_matches_oracle_f64(nn, sched):
+    # per-nest depths (the matrix form of the CNS construction): same nest count, history and
+    # iterate as the oracle's scheduled loop, and flops counted per nest
+    n = 200
+    a, q, lam = synth.spd_spectrum(n, 1e2, seed=17)
+    x0 = dense.precond_scalar(n, 2.0 / (lam[0] + lam[-1]))
+    st, res, x = _run(nn, a, x0, 2, 1e-10, 40, "f64", depth_schedule=sched)
+    run = dense.nn_invert(a, x0, 2, 1e-10, 40, depth_schedule=sched)
+    assert st == nn.NN_OK and res["nests"] == run.nests
+    for s_gpu, s_cpu in zip(res["history"], run.history):
+        assert abs(s_gpu - s_cpu) <= 1e-8 * s_cpu + 1e-13
+    assert np.linalg.norm(x - run.x) <= 1e-9 * np.linalg.norm(run.x)
+    gemms = 1 + sum(sched[min(k, len(sched) - 1)] + 1 for k in range(run.nests))
+    assert res["flops"] == pytest.approx(2.0 * n ** 3 * gemms, rel=1e-12)
+
+
+def test_depth_schedule_mixed_converges(nn):
+    # the tensor-core chain under a Chebyshev-then-Newton schedule reaches tol like the fixed depth
+    n = 512
+    a, q, lam = synth.spd_spectrum(n, 1e2, seed=19)
+    x0 = dense.precond_scalar(n, 2.0 / (lam[0] + lam[-1]))
+    st, res, x = _run(nn, a, x0, 2, 1e-6, 40, "mixed_bf16", depth_schedule=[2, 2, 1])
+    assert st == nn.NN_OK and res["residual"] < 1e-6
+    r = np.eye(n) - a @ x
+    assert np.linalg.norm(r) / n < 1e-6 + 4 * 2.0 ** -24 * (1 + math.sqrt(n) / 4)

@@ -143,3 +143,29 @@ def test_product_kernels_agree_bitwise(nn, dtype, case):
     assert s1 == s0 and r1["nests"] == r0["nests"] == 3
     assert np.array_equal(x1, x0)
     assert r1["history"][:3] == r0["history"][:3]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_df", "f32"])
+@pytest.mark.parametrize("depths", [[2, 1, 1], [2, 2, 1, 1, 1], [1, 3, 2]])
+def test_schedule_matches_oracle(nn, dtype, depths):
+    # a depth per factor (CNS: Chebyshev factors, then the factorised Neumann series)
+    import torch
+
+    m = synth.random_sparse_spd(1000, 7, seed=5)
+    b = synth.gaussian_rhs(m.n, 1, seed=7)
+    npd = NP[dtype]
+    rp = torch.from_numpy(m.row_ptr.astype(np.int32)).cuda()
+    col = torch.from_numpy(m.col.astype(np.int32)).cuda()
+    val = torch.from_numpy(m.val.astype(npd)).cuda()
+    B = torch.from_numpy(np.ascontiguousarray(b.T.astype(npd))).cuda()
+    X = torch.empty_like(B)
+    ws = nn.csr_workspace(m.n, m.nnz, 1, dtype)
+    st, res = nn.nn_solve_csr_sched(rp, col, val, B, depths, 0.0, X, ws, double_float=(dtype == "f64_df"))
+    torch.cuda.synchronize()
+    assert st == nn.NN_OK and res["nests"] == len(depths)
+    x = X.cpu().numpy().T
+    want = sparse.nn_sparse_solve_sched(m.to_scipy(), b.astype(np.float64), depths)
+    terms = int(np.prod([d + 1 for d in depths])) - 1
+    nnz_row = int(np.max(np.diff(m.row_ptr)))
+    tol = max(8 * terms * U[dtype] * (nnz_row + 1), 1e-13 if dtype == "f64" else 0)
+    assert np.linalg.norm(x - want) / np.linalg.norm(want) <= tol
