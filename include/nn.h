@@ -51,12 +51,19 @@ typedef enum nn_dtype {
   NN_F64 = 0,        /* every GEMM and epilogue in FP64 (CUDA cores)                           */
   NN_F32 = 1,        /* every GEMM and epilogue in FP32 (CUDA cores)                           */
   NN_MIXED_BF16 = 2, /* tcgen05 tensor-core GEMMs on BF16 operand pieces, FP32 accumulate in
-                        TMEM, FP32 master copy of X. Bulk nests use one BF16 piece per operand;
-                        refine nests evaluate R_k with three pieces (six products, FP32-level)
-                        and the Horner/update GEMMs with two pieces (three products).        */
-  NN_F64_DF = 3      /* sparse chain only: FP64 data and results, arithmetic in double-float
+                        TMEM, FP32 master copy of X. Precision levels 1..4 use 1..3 pieces for
+                        the residual and the Horner/update products (1 to 6 BF16 passes each);
+                        the chain raises the level as s_k nears each level's rounding floor. */
+  NN_F64_DF = 3,     /* sparse chain only: FP64 data and results, arithmetic in double-float
                         (hi + lo FP32 pairs, 49-bit significand) on the FP32 pipes; values must
                         lie within the FP32 exponent range                                   */
+  NN_F64_EMU = 4     /* dense chain, nn_residual and nn_solve_normal: FP64 data and results,
+                        every product emulated on the BF16 tensor cores with exact slices
+                        (error-free splitting after Ozaki et al.: per-row / per-column
+                        power-of-two scales, signed base-2^beta digits with n 2^(2 beta) <= 2^24,
+                        slice products summed exactly in FP32 and the groups in FP64).
+                        Accurate to a few units of 2^-53 normwise. Workspace grows by two sets
+                        of BF16 slices (about 2.8 GB at N = 8192)                            */
 } nn_dtype;
 
 /* ---- starting matrix X_0 = Theta (Section II-A, Eq. (normalization), Appendix 1) --------- */
@@ -149,7 +156,8 @@ int nn_invert_host(const double* A_host, int64_t n, const double* X0_host, const
                    double* X_host, nn_result* res, void* workspace, size_t ws_bytes, void* stream);
 
 /* s = ||I - A X||_F / N for device FP64 A, X (row-major), written to *rms_frob (host).
- * dtype NN_F64 evaluates in FP64; NN_F32 in FP32. Section II (error measure). */
+ * dtype NN_F64 evaluates in FP64; NN_F32 in FP32; NN_F64_EMU with the emulated FP64 product.
+ * Section II (error measure). */
 int nn_residual(const double* A, int64_t lda, const double* X, int64_t ldx, int64_t n, int dtype,
                 double* rms_frob, void* workspace, size_t ws_bytes, void* stream);
 

@@ -72,6 +72,16 @@ struct Params {
   int n_col;
   double* partial;
   int* err;
+  // FP64-emulation epilogue (see TcGemmArgs)
+  int emu;
+  int emu_first, emu_last;
+  const int* emu_gexp;
+  double* emu_acc;
+  double* emu_out;
+  int64_t emu_ld_out;
+  const double* emu_add;
+  int64_t emu_ld_add;
+  int emu_n;
 };
 
 // Shared-memory matrix descriptor for a K-major tile written by TMA with SWIZZLE_128B:
@@ -121,8 +131,40 @@ __device__ __forceinline__ void store_pieces_row(__nv_bfloat16* const* pieces, i
 
 // Epilogue of one 32-column chunk of a thread's accumulator row: applies the mode, adds the
 // squares to ss (in column order) and writes the FP32 and BF16-piece outputs.
+// FP64-emulation epilogue of one 32-column chunk: the FP32 accumulator holds an exact sum of
+// slice products (an integer times this element's power of two), so acc * emu_scale is exact.
+__device__ __forceinline__ void emu_chunk(const Params& p, const uint32_t (&raw)[32], int gr, int gc0, double& ss) {
+  if (gr >= p.emu_n) return;
+  double* accp = p.emu_acc + int64_t(gr) * p.np + gc0;
+  const int jn = min(32, p.emu_n - gc0);
+  const double scale = ldexp(1.0, p.emu_gexp[0] + p.emu_gexp[1]);
+  // fully unrolled (static register indices into raw)
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    if (j >= jn) break;
+    double v = double(__uint_as_float(raw[j])) * scale;
+    if (!p.emu_first) v += accp[j];
+    if (!p.emu_last) {
+      accp[j] = v;
+      continue;
+    }
+    const int gc = gc0 + j;
+    double c = v;
+    if (p.mode == EPI_RESIDUAL)
+      c = ((gr == gc && gr < p.n_id) ? 1.0 : 0.0) - v;
+    else if (p.mode == EPI_ADD)
+      c = p.emu_add[int64_t(gr) * p.emu_ld_add + gc] + v;
+    ss = fma(c, c, ss);
+    p.emu_out[int64_t(gr) * p.emu_ld_out + gc] = c;
+  }
+}
+
 __device__ __forceinline__ void epilogue_chunk(const Params& p, const uint32_t (&raw)[32], int gr, int gc0,
                                                int64_t ld, double& ss) {
+  if (p.emu) {
+    emu_chunk(p, raw, gr, gc0, ss);
+    return;
+  }
   float v[32];
   const int64_t off = int64_t(gr) * ld + gc0;
   if (p.mode == EPI_ADD) {
@@ -636,7 +678,11 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
   if (a.np <= 0 || a.np % 128 != 0 || a.nseg < 1 || a.nseg > kTcMaxSeg || a.n_row < 0 || a.n_row > 3 ||
       a.n_col < 0 || a.n_col > 3 || a.err == nullptr)
     return NN_ERR_ARG;
-  if (a.mode == EPI_ADD && a.add == nullptr) return NN_ERR_ARG;
+  if (!a.emu && a.mode == EPI_ADD && a.add == nullptr) return NN_ERR_ARG;
+  if (a.emu && (a.emu_acc == nullptr || a.emu_gexp == nullptr || (a.emu_last && a.emu_out == nullptr) ||
+                (a.emu_last && a.mode == EPI_ADD && a.emu_add == nullptr) || a.n_row != 0 || a.n_col != 0 ||
+                a.out_f32 != nullptr || a.emu_n < 1 || a.emu_n > a.np))
+    return NN_ERR_ARG;
   tc::Params p;
   memset(&p, 0, sizeof(p));
   for (int s = 0; s < a.nseg; ++s) {
@@ -666,6 +712,16 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
   p.n_col = a.n_col;
   p.partial = a.partial;
   p.err = a.err;
+  p.emu = a.emu ? 1 : 0;
+  p.emu_first = a.emu_first ? 1 : 0;
+  p.emu_last = a.emu_last ? 1 : 0;
+  p.emu_gexp = a.emu_gexp;
+  p.emu_acc = a.emu_acc;
+  p.emu_out = a.emu_out;
+  p.emu_ld_out = a.emu_ld_out;
+  p.emu_add = a.emu_add;
+  p.emu_ld_add = a.emu_ld_add;
+  p.emu_n = a.emu_n;
   // Variant choice: the 2-SM MMA by default where the size allows it, else single-CTA tiles.
   const bool even = a.np % (2 * tc::BM) == 0;
   int variant = g_variant;

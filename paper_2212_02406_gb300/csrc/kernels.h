@@ -46,12 +46,38 @@ struct TcGemmArgs {
   int n_col = 0;
   double* partial = nullptr;
   int* err = nullptr;
+  // FP64-emulation epilogue (emu = true; the BF16/FP32 outputs above unused): the segments are
+  // exact-integer slice products of one diagonal group, summed exactly in FP32. The epilogue
+  // adds acc * 2^(emu_gexp[0] + emu_gexp[1]) into emu_acc (FP64, Np x Np, ld Np; the first
+  // group starts from 0) for rows and columns < emu_n; the last group applies `mode` in FP64
+  // (I restricted to < n_id, addend emu_add with ld emu_ld_add) and writes emu_out (ld
+  // emu_ld_out) and the partials. emu_gexp: device pair of the operands' global exponents.
+  bool emu = false;
+  bool emu_first = false, emu_last = false;
+  const int* emu_gexp = nullptr;
+  double* emu_acc = nullptr;
+  double* emu_out = nullptr;
+  int64_t emu_ld_out = 0;
+  const double* emu_add = nullptr;
+  int64_t emu_ld_add = 0;
+  int emu_n = 0;
 };
 int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used);
 int gemm_tc_max_grid();
-// 0: automatic (CTA pairs with multicast when Np is a multiple of 256), 1: single-CTA tiles,
-// 2: CTA pairs only (NN_ERR_UNSUPPORTED where they do not apply).
+// 0: automatic (2-SM MMA when Np is a multiple of 256, else single-CTA tiles), 1: single-CTA
+// tiles, 2: CTA pairs with multicast, 3: 2-SM MMA (2 and 3: NN_ERR_UNSUPPORTED where they do
+// not apply).
 void gemm_tc_set_variant(int v);
+
+// ---- FP64 GEMM emulated with exact BF16 slices on the tensor cores (ozaki.cu) -------------
+// C (n x n FP64, ldc) = mode(A B): EPI_COPY A B, EPI_RESIDUAL I_{n_id} - A B, EPI_ADD D + A B;
+// partial[0 .. *partials) receives per-CTA sums of C_ij^2 when non-null. A, B FP64 n x n
+// (lda, ldb). Workspace from emu_workspace_bytes(n); err is the device error word of the
+// tensor-core kernel's bounded waits.
+size_t emu_workspace_bytes(int64_t n);
+int gemm_f64_emu(cudaStream_t st, int n, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+                 int64_t ldc, int mode, const double* D, int64_t ldd, int n_id, double* partial, int* partials,
+                 void* ws, size_t ws_bytes, int* err);
 bool tc_supported();
 
 // ---- conversion / preconditioner / reduction kernels (convert.cu) -----------------------

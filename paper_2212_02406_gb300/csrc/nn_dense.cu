@@ -107,9 +107,10 @@ size_t ws_bytes(int64_t n, int dtype) {
   Carver c(nullptr, 0);
   Common cm;
   carve_common(c, n, dtype, cm);
-  if (dtype == NN_F64) {
+  if (dtype == NN_F64 || dtype == NN_F64_EMU) {
     Simt64Ws w;
     carve_f64(c, n, w);
+    if (dtype == NN_F64_EMU) (void)c.take<char>(emu_workspace_bytes(n));
   } else if (dtype == NN_F32) {
     Simt32Ws w;
     carve_f32(c, n, w);
@@ -121,7 +122,7 @@ size_t ws_bytes(int64_t n, int dtype) {
   return align_up(c.used, 256);
 }
 
-bool valid_dtype(int d) { return d == NN_F64 || d == NN_F32 || d == NN_MIXED_BF16; }
+bool valid_dtype(int d) { return d == NN_F64 || d == NN_F32 || d == NN_MIXED_BF16 || d == NN_F64_EMU; }
 
 // Reads s (and the device error word) back to the host; one stream synchronisation.
 int fetch_scalar(cudaStream_t st, const Common& cm, double* s, int* dev_err) {
@@ -212,10 +213,34 @@ struct LaunchTimer {
 // ---------------------------------------------------------------------------------------
 // CUDA-core chains (FP64 / FP32).
 
+// The GEMM of a CUDA-core-style chain: C = mode(A B) with Σ C^2 partials (count in *nparts).
 template <typename T>
+struct SimtGemm {
+  cudaStream_t st;
+  int n;
+  int operator()(const T* A, int64_t lda, const T* B, int64_t ldb, T* C, int64_t ldc, int mode, const T* D,
+                 int64_t ldd, double* partial, int* nparts) const {
+    if (nparts) *nparts = gemm_simt_partials<T>(n, n);
+    return gemm_simt<T>(st, n, n, n, A, lda, B, ldb, C, ldc, mode, D, ldd, n, partial);
+  }
+};
+
+// FP64 products emulated with exact BF16 slices on the tensor cores (NN_F64_EMU).
+struct EmuGemm {
+  cudaStream_t st;
+  int n;
+  void* ws;
+  size_t ws_bytes;
+  int* err;
+  int operator()(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int mode,
+                 const double* D, int64_t ldd, double* partial, int* nparts) const {
+    return gemm_f64_emu(st, n, A, lda, B, ldb, C, ldc, mode, D, ldd, n, partial, nparts, ws, ws_bytes, err);
+  }
+};
+
+template <typename T, typename Gemm>
 int run_simt(cudaStream_t st, int n, const T* A, int64_t lda, T* const X[2], T* R, T* const Tb[2],
-             const nn_opts& o, const Common& cm, nn_result* res, int* final_idx) {
-  const int nparts = gemm_simt_partials<T>(n, n);
+             const nn_opts& o, const Common& cm, nn_result* res, int* final_idx, const Gemm& gemm) {
   const double gemm_flops = 2.0 * double(n) * double(n) * double(n);
   LaunchTimer timer;
   timer.on = (o.flags & NN_FLAG_TIME_KERNELS) != 0;
@@ -230,9 +255,8 @@ int run_simt(cudaStream_t st, int n, const T* A, int64_t lda, T* const X[2], T* 
   int cur = 0;
   res->nests = 0;
   for (int k = 0;; ++k) {
-    NN_TRY(timed([&] {
-      return gemm_simt<T>(st, n, n, n, A, lda, X[cur], n, R, n, EPI_RESIDUAL, nullptr, 0, n, cm.partial);
-    }));
+    int nparts = 0;
+    NN_TRY(timed([&] { return gemm(A, lda, X[cur], n, R, n, EPI_RESIDUAL, nullptr, 0, cm.partial, &nparts); }));
     NN_TRY(reduce_rms(st, cm.partial, nparts, 1.0 / double(n), cm.scal));
     res->gemms += 1;
     res->launches += 2;
@@ -251,14 +275,12 @@ int run_simt(cudaStream_t st, int n, const T* A, int64_t lda, T* const X[2], T* 
     const T* t_cur = R;
     for (int j = 1; j < nest_depth(o, k); ++j) {
       T* t_nxt = Tb[j & 1];
-      NN_TRY(timed([&] { return gemm_simt<T>(st, n, n, n, R, n, t_cur, n, t_nxt, n, EPI_ADD, R, n, n, nullptr); }));
+      NN_TRY(timed([&] { return gemm(R, n, t_cur, n, t_nxt, n, EPI_ADD, R, n, nullptr, nullptr); }));
       t_cur = t_nxt;
       res->gemms += 1;
       res->launches += 1;
     }
-    NN_TRY(timed([&] {
-      return gemm_simt<T>(st, n, n, n, X[cur], n, t_cur, n, X[cur ^ 1], n, EPI_ADD, X[cur], n, n, nullptr);
-    }));
+    NN_TRY(timed([&] { return gemm(X[cur], n, t_cur, n, X[cur ^ 1], n, EPI_ADD, X[cur], n, nullptr, nullptr); }));
     res->gemms += 1;
     res->launches += 1;
     cur ^= 1;
@@ -547,12 +569,17 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
   NN_CUDA_TRY(cudaMemsetAsync(cm.err, 0, sizeof(int), st));
   const int ni = int(n);
   int fin = 0;
-  if (o.dtype == NN_F64) {
+  if (o.dtype == NN_F64 || o.dtype == NN_F64_EMU) {
     Simt64Ws w;
     carve_f64(c, n, w);
+    const size_t eb = o.dtype == NN_F64_EMU ? emu_workspace_bytes(n) : 0;
+    void* ews = eb ? c.take<char>(eb) : nullptr;
     if (!c.ok) return NN_ERR_OOM_BUDGET;
     NN_TRY(copy_f64(st, X0, ldx0, ni, w.X[0], n));
-    NN_TRY(run_simt<double>(st, ni, A, lda, w.X, w.R, w.T, o, cm, res, &fin));
+    if (o.dtype == NN_F64)
+      NN_TRY(run_simt<double>(st, ni, A, lda, w.X, w.R, w.T, o, cm, res, &fin, SimtGemm<double>{st, ni}));
+    else
+      NN_TRY(run_simt<double>(st, ni, A, lda, w.X, w.R, w.T, o, cm, res, &fin, EmuGemm{st, ni, ews, eb, cm.err}));
     NN_TRY(copy_f64(st, w.X[fin], n, ni, X, ldx));
     res->launches += 2;
   } else if (o.dtype == NN_F32) {
@@ -561,7 +588,7 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     if (!c.ok) return NN_ERR_OOM_BUDGET;
     NN_TRY(f64_to_f32(st, A, lda, ni, w.A, n));
     NN_TRY(f64_to_f32(st, X0, ldx0, ni, w.X[0], n));
-    NN_TRY(run_simt<float>(st, ni, w.A, n, w.X, w.R, w.T, o, cm, res, &fin));
+    NN_TRY(run_simt<float>(st, ni, w.A, n, w.X, w.R, w.T, o, cm, res, &fin, SimtGemm<float>{st, ni}));
     NN_TRY(f32_to_f64(st, w.X[fin], n, ni, X, ldx));
     res->launches += 3;
   } else {
@@ -680,7 +707,7 @@ int nn_residual(const double* A, int64_t lda, const double* X, int64_t ldx, int6
                 void* workspace, size_t ws_size, void* stream) {
   if (A == nullptr || X == nullptr || rms_frob == nullptr || n < 1 || n > 32768 || lda < n || ldx < n)
     return NN_ERR_ARG;
-  if (dtype != NN_F64 && dtype != NN_F32) return NN_ERR_ARG;
+  if (dtype != NN_F64 && dtype != NN_F32 && dtype != NN_F64_EMU) return NN_ERR_ARG;
   if (workspace == nullptr || ws_size < nn_workspace_bytes(n, dtype)) return NN_ERR_OOM_BUDGET;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Carver c(workspace, ws_size);
@@ -693,6 +720,17 @@ int nn_residual(const double* A, int64_t lda, const double* X, int64_t ldx, int6
     if (!c.ok) return NN_ERR_OOM_BUDGET;
     NN_TRY(gemm_simt<double>(st, ni, ni, ni, A, lda, X, ldx, w.R, n, EPI_RESIDUAL, nullptr, 0, ni, cm.partial));
     NN_TRY(reduce_rms(st, cm.partial, gemm_simt_partials<double>(ni, ni), 1.0 / double(n), cm.scal));
+  } else if (dtype == NN_F64_EMU) {
+    Simt64Ws w;
+    carve_f64(c, n, w);
+    const size_t eb = emu_workspace_bytes(n);
+    void* ews = c.take<char>(eb);
+    if (!c.ok) return NN_ERR_OOM_BUDGET;
+    NN_CUDA_TRY(cudaMemsetAsync(cm.err, 0, sizeof(int), st));
+    int nparts = 0;
+    NN_TRY(gemm_f64_emu(st, ni, A, lda, X, ldx, w.R, n, EPI_RESIDUAL, nullptr, 0, ni, cm.partial, &nparts, ews, eb,
+                        cm.err));
+    NN_TRY(reduce_rms(st, cm.partial, nparts, 1.0 / double(n), cm.scal));
   } else {
     Simt32Ws w;
     carve_f32(c, n, w);

@@ -12,9 +12,10 @@
 // embedding of B). The embedding's residual sqrt(2) ||R_k||_F / (2n) is the complex
 // ||R_k||_F / n divided by sqrt(2); the stop test and the reported history use the complex one.
 //
-// All steps run on the device: one tiled kernel writes A-hat (complex only) and A-hat^T, the
-// FP64 CUDA-core GEMM forms W, C = A-hat^T B-hat and Y = X C, and the inversion of W is the
-// dense NN of nn_invert with the caller's options.
+// All steps run on the device: one tiled kernel writes A-hat (complex only) and A-hat^T; W is
+// formed by the FP64 CUDA-core GEMM, or by the emulated FP64 product for NN_F64_EMU; C = A-hat^T
+// B-hat and Y = X C (n x nrhs) use the CUDA-core GEMM; the inversion of W is the dense NN of
+// nn_invert with the caller's options.
 #include <math.h>
 #include <string.h>
 
@@ -102,6 +103,7 @@ struct NormalWs {
   double* C;
   double* Y;
   double* scratch;
+  int* err;
 };
 
 void carve_normal(Carver& c, int64_t m, int64_t nrhs, bool is_complex, NormalWs& w) {
@@ -115,6 +117,7 @@ void carve_normal(Carver& c, int64_t m, int64_t nrhs, bool is_complex, NormalWs&
   w.C = c.take<double>(mr);
   w.Y = c.take<double>(mr);
   w.scratch = c.take<double>(8);
+  w.err = c.take<int>(8);
 }
 
 size_t outer_bytes(int64_t m, int64_t nrhs, bool is_complex) {
@@ -172,7 +175,14 @@ int nn_solve_normal(const void* A, int64_t n, int64_t lda, int is_complex, const
   const double* Ahat = is_complex ? w.Ahat : Ad;
   const int64_t ld_hat = is_complex ? m : lda;
   // W = A-hat^T A-hat, X_0 = I / Tr(W)
-  NN_TRY(gemm_simt<double>(st, mi, mi, mi, w.AhatT, m, Ahat, ld_hat, w.W, m, EPI_COPY, nullptr, 0, 0, nullptr));
+  if (opts->dtype == NN_F64_EMU) {
+    // the inversion's workspace is idle until invert_device: lend it to the emulated product
+    NN_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    NN_TRY(gemm_f64_emu(st, mi, w.AhatT, m, Ahat, ld_hat, w.W, m, EPI_COPY, nullptr, 0, 0, nullptr, nullptr, workspace,
+                        inner, w.err));
+  } else {
+    NN_TRY(gemm_simt<double>(st, mi, mi, mi, w.AhatT, m, Ahat, ld_hat, w.W, m, EPI_COPY, nullptr, 0, 0, nullptr));
+  }
   NN_TRY(precond_fill(st, w.W, m, mi, NN_PC_TRACE, 0.0, w.X0, m, w.scratch, nullptr));
   if (is_complex) {
     // The embedding doubles the trace (Tr W-hat = 2 Re Tr W): Theta = 1 / Tr(A^H A) = 2 / Tr(W-hat).
@@ -212,6 +222,14 @@ int nn_solve_normal(const void* A, int64_t n, int64_t lda, int is_complex, const
   res->launches += 5;
   res->flops += 2.0 * double(m) * double(m) * double(m) + 4.0 * double(m) * double(m) * double(nrhs);
   NN_CUDA_TRY(cudaStreamSynchronize(st));
+  if (opts->dtype == NN_F64_EMU) {
+    int e = DEV_OK;
+    NN_CUDA_TRY(cudaMemcpy(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != DEV_OK) {
+      res->status = NN_ERR_TIMEOUT;
+      return NN_ERR_TIMEOUT;
+    }
+  }
   res->status = s;
   return s;
 }
