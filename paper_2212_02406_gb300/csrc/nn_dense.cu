@@ -232,9 +232,11 @@ struct EmuGemm {
   void* ws;
   size_t ws_bytes;
   int* err;
+  double* hw_flops;
   int operator()(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int mode,
                  const double* D, int64_t ldd, double* partial, int* nparts) const {
-    return gemm_f64_emu(st, n, A, lda, B, ldb, C, ldc, mode, D, ldd, n, partial, nparts, ws, ws_bytes, err);
+    return gemm_f64_emu(st, n, A, lda, B, ldb, C, ldc, mode, D, ldd, n, partial, nparts, ws, ws_bytes, err,
+                        hw_flops);
   }
 };
 
@@ -579,7 +581,8 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     if (o.dtype == NN_F64)
       NN_TRY(run_simt<double>(st, ni, A, lda, w.X, w.R, w.T, o, cm, res, &fin, SimtGemm<double>{st, ni}));
     else
-      NN_TRY(run_simt<double>(st, ni, A, lda, w.X, w.R, w.T, o, cm, res, &fin, EmuGemm{st, ni, ews, eb, cm.err}));
+      NN_TRY(run_simt<double>(st, ni, A, lda, w.X, w.R, w.T, o, cm, res, &fin,
+                              EmuGemm{st, ni, ews, eb, cm.err, &res->hw_flops}));
     NN_TRY(copy_f64(st, w.X[fin], n, ni, X, ldx));
     res->launches += 2;
   } else if (o.dtype == NN_F32) {

@@ -215,7 +215,7 @@ size_t emu_workspace_bytes(int64_t n) {
 
 int gemm_f64_emu(cudaStream_t st, int n, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
                  int64_t ldc, int mode, const double* D, int64_t ldd, int n_id, double* partial, int* partials,
-                 void* ws, size_t ws_bytes, int* err) {
+                 void* ws, size_t ws_bytes, int* err, double* hw_flops) {
   if (n < 1 || A == nullptr || B == nullptr || C == nullptr || err == nullptr) return NN_ERR_ARG;
   if (mode == EPI_ADD && D == nullptr) return NN_ERR_ARG;
   if (!tc_supported()) return NN_ERR_UNSUPPORTED;
@@ -272,6 +272,7 @@ int gemm_f64_emu(cudaStream_t st, int n, const double* A, int64_t lda, const dou
     int grid = 0;
     NN_TRY(gemm_tc(st, g, &grid));
     if (g.emu_last && partials != nullptr) *partials = grid;
+    if (hw_flops != nullptr) *hw_flops += 2.0 * double(np) * double(np) * double(np) * double(gr.cnt);
   }
   return NN_OK;
 }
