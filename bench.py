@@ -143,6 +143,32 @@ def dense_cpu_baseline(a_host, x0_host, depth, n, steps=1):
                       f"on the same A and X_0; median of {steps}; {t:.2f} s per nest"}
 
 
+def profile_traffic(md_name, sources):
+    """DRAM bytes per launch recorded in profiles/<md_name> by an ncu capture, or None when a
+    kernel source listed there has changed since (sources: file names under the csrc folder)."""
+    import hashlib
+    import re
+
+    root = os.path.dirname(os.path.abspath(__file__))
+    try:
+        text = open(os.path.join(root, "profiles", md_name)).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch: (\d+) sources: ([^`\n]+)", text)
+    if not m:
+        return None
+    recorded = dict(kv.split("=") for kv in m.group(2).split())
+    for name in sources:
+        path = os.path.join(root, "paper_2212_02406_gb300", "csrc", name)
+        try:
+            digest = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+        except OSError:
+            return None
+        if recorded.get(name) != digest:
+            return None
+    return int(m.group(1))
+
+
 # ---- dense workload -------------------------------------------------------------------
 
 def make_dense_inputs(n, kappa, seed, device):
@@ -243,8 +269,13 @@ def run_dense(args, rank, world, local_rank):
         peak = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
         kernel = {1: "nn::tc::gemm_tc_kernel", 2: "nn::tc::gemm_tc_pair_kernel"}.get(args.gemm_variant,
                                                                                  "nn::tc::gemm_tc_2sm_kernel")
+        # ncu DRAM bytes per launch (mean over one step) of the profiled default configuration
+        traffic = None
+        if (args.gemm_variant in (0, 3) and n == 8192 and args.kappa == 1e2 and args.depth == 2
+                and args.tol == 1e-6 and args.seed == 0):
+            traffic = profile_traffic("gemm_tc_2sm_dense_n8192.md", ["gemm_tc.cu", "nn_dense.cu"])
         roofline = {"kernel": kernel, "bound": "tensor", "achieved": round(achieved, 2),
-                    "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                    "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                     "peak_source": f"{peak_src} bf16 burst", "launches": tc_launches,
                     "avg_launch_ms": round(tc_ms / tc_launches, 4),
                     "flops_per_launch": "2 Np^3 per BF16 product pass (split passes are real tensor work)"}
@@ -533,7 +564,9 @@ def run_sparse(args, rank, world, local_rank):
             "status_ok": st == abi.NN_OK, "residual": res["residual"], "gpu_launches": launches,
             "roofline": {"kernel": ("nn::spmv_ring_kernel" if args.spmv_variant == 0 else "nn::spmv_p_kernel")
                          + " (whole chain timed, residual products and reductions included)", "bound": "hbm", "achieved": round(gbs, 1),
-                         "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4), "traffic": None,
+                         "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
+                         "traffic": (profile_traffic("spmv_ring_laplacian2048.md", ["spmv.cu"])
+                                     if kind == "f64" and args.spmv_variant == 0 else None),
                          "peak_source": f"{src} copy bandwidth",
                          "bytes_per_product": int(chain / products)},
             "clocks": clocks}
