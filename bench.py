@@ -713,7 +713,8 @@ def run_serve(args, rank, world, local_rank):
         span = max(c["t_done"] for c in comps) - min(c["t_submit"] for c in comps)
         ok = float(np.mean([c["status"] in (abi.NN_OK, abi.NN_ERR_NOT_CONVERGED) for c in comps]))
         conv = float(np.mean([c["status"] == abi.NN_OK for c in comps]))
-        return {"throughput": len(comps) / span, "p50_ms": float(np.percentile(lat, 50)),
+        return {"throughput": len(comps) / span, "launches": int(sum(c["launches"] for c in comps)),
+                "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "ok_frac": ok, "converged_frac": conv,
                 "arena_peak_gb": stats["arena_peak"] / 2 ** 30, "span_s": span}
 
@@ -735,7 +736,7 @@ def run_serve(args, rank, world, local_rank):
                                    f"HBM budget {args.budget_gb:g} GiB, {args.max_active} concurrent",
                        "requests": count, "budget_gb": args.budget_gb, "max_active": args.max_active},
             "capacity_per_s": round(cap["throughput"], 3), "loads": loads,
-            "gpu_launches": None}
+            "gpu_launches": head["launches"]}
 
 
 def run_reference(args):

@@ -301,6 +301,7 @@ typedef struct nn_completion {
   int nests;
   double residual;
   double t_submit, t_start, t_done;
+  int launches;         /* kernels the request launched (X_0, the NN loop, the solve)          */
 } nn_completion;
 
 size_t nn_server_request_bytes(int64_t n, int64_t nrhs, int dtype);

@@ -68,7 +68,7 @@ class NNRequest(ctypes.Structure):
 
 class NNCompletion(ctypes.Structure):
     _fields_ = [("id", c_int64), ("status", c_int), ("nests", c_int), ("residual", c_double),
-                ("t_submit", c_double), ("t_start", c_double), ("t_done", c_double)]
+                ("t_submit", c_double), ("t_start", c_double), ("t_done", c_double), ("launches", c_int)]
 
 
 _LIB = None
@@ -483,7 +483,8 @@ class Server:
             c = buf[i]
             self.live.pop(int(c.id), None)
             out.append({"id": c.id, "status": c.status, "nests": c.nests, "residual": c.residual,
-                        "t_submit": c.t_submit, "t_start": c.t_start, "t_done": c.t_done})
+                        "t_submit": c.t_submit, "t_start": c.t_start, "t_done": c.t_done,
+                        "launches": c.launches})
         return out
 
     def wait_idle(self, timeout_s=0.0) -> int:

@@ -170,6 +170,12 @@ int run_job(nn_server* s, const Job& j, cudaStream_t st, nn_completion* c) {
   c->status = st_inv;
   c->nests = res.nests;
   c->residual = res.residual;
+  // X_0: one reduction for the scalar (trace / Theta_2 power steps / none) and the fill
+  const int pc_launches = r.precond == NN_PC_PAN_SCHREIBER ? 3
+                          : r.precond == NN_PC_TRACE         ? 2
+                          : r.precond == NN_PC_THETA2        ? 3 + int(r.pc_scalar)
+                                                             : 1;
+  c->launches = pc_launches + res.launches + (nrhs > 0 ? 1 : 0);
   if (st_inv == NN_ERR_CUDA || st_inv == NN_ERR_ARG || st_inv == NN_ERR_UNSUPPORTED || st_inv == NN_ERR_OOM_BUDGET)
     return st_inv;
   if (nrhs > 0) {
