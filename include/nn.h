@@ -149,11 +149,21 @@ int nn_invert(const double* A, int64_t n, int64_t lda, const double* X0, int64_t
               void* workspace, size_t ws_bytes, void* stream);
 
 /* Same as nn_invert with HOST buffers: A, X0 and X are host FP64 arrays (leading dimension
- * n). The call copies A and X0 to the device, runs, and copies X back, all on `stream`.
- * Needs nn_workspace_bytes_host(n, dtype) of device workspace. */
+ * n; page-locked memory lets the copies run at full speed). The call copies A and X0 to the
+ * device, runs, and copies X back, and returns after X is in host memory. For NN_MIXED_BF16
+ * with tol > 0, the nest predicted to be the last has its iterate converted and copied back on
+ * a side stream while the confirming residual runs; when the residual confirms the stop that
+ * copy is the result (otherwise X is copied after the run). Needs
+ * nn_workspace_bytes_host(n, dtype) of device workspace. */
 size_t nn_workspace_bytes_host(int64_t n, int dtype);
 int nn_invert_host(const double* A_host, int64_t n, const double* X0_host, const nn_opts* opts,
                    double* X_host, nn_result* res, void* workspace, size_t ws_bytes, void* stream);
+
+/* nn_invert_host with X_0 built on the device from a preconditioner (kind and scalar as in
+ * nn_init_precond) instead of a host matrix: only A travels to the device and only X back.
+ * Same workspace (nn_workspace_bytes_host), result and errors as nn_invert_host. */
+int nn_invert_host_pc(const double* A_host, int64_t n, int pc_kind, double pc_scalar, const nn_opts* opts,
+                      double* X_host, nn_result* res, void* workspace, size_t ws_bytes, void* stream);
 
 /* s = ||I - A X||_F / N for device FP64 A, X (row-major), written to *rms_frob (host).
  * dtype NN_F64 evaluates in FP64; NN_F32 in FP32; NN_F64_EMU with the emulated FP64 product.

@@ -84,6 +84,8 @@ _SIGNATURES = {
                           POINTER(NNResult), c_void_p, c_size_t, c_void_p]),
     "nn_invert_host": (c_int, [c_void_p, c_int64, c_void_p, POINTER(NNOpts), c_void_p, POINTER(NNResult), c_void_p,
                                c_size_t, c_void_p]),
+    "nn_invert_host_pc": (c_int, [c_void_p, c_int64, c_int, c_double, POINTER(NNOpts), c_void_p, POINTER(NNResult),
+                                  c_void_p, c_size_t, c_void_p]),
     "nn_residual": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int, POINTER(c_double), c_void_p,
                             c_size_t, c_void_p]),
     "nn_csr_workspace_bytes": (c_size_t, [c_int64, c_int64, c_int64, c_int]),
@@ -243,6 +245,22 @@ def nn_invert_host(A, X0, opts: NNOpts, X, workspace, stream=None):
     res = NNResult()
     st = lib().nn_invert_host(c_void_p(A.ctypes.data), A.shape[0], c_void_p(X0.ctypes.data), ctypes.byref(opts),
                               c_void_p(X.ctypes.data), ctypes.byref(res), pw, nw, _stream_ptr(stream))
+    return st, res.as_dict()
+
+
+def nn_invert_host_pc(A, kind, scalar, opts: NNOpts, X, workspace, stream=None):
+    """Host-buffer inversion with X_0 built on the device (kind, scalar as nn_init_precond):
+    A and X are C-contiguous float64 NumPy arrays (X is written)."""
+    import numpy as np
+
+    for name, arr in (("A", A), ("X", X)):
+        if not (isinstance(arr, np.ndarray) and arr.dtype == np.float64 and arr.flags.c_contiguous):
+            raise TypeError(f"{name} must be a C-contiguous float64 ndarray")
+    k = PRECONDS[kind] if isinstance(kind, str) else int(kind)
+    pw, nw = _ws(workspace)
+    res = NNResult()
+    st = lib().nn_invert_host_pc(c_void_p(A.ctypes.data), A.shape[0], k, float(scalar), ctypes.byref(opts),
+                                 c_void_p(X.ctypes.data), ctypes.byref(res), pw, nw, _stream_ptr(stream))
     return st, res.as_dict()
 
 

@@ -105,7 +105,9 @@ int precond_fill(cudaStream_t st, const double* A, int64_t lda, int n, int kind,
 
 // ---- dense NN on device buffers (nn_dense.cu), shared with the serving runtime ---------------
 int check_opts(const nn_opts* o, int64_t n);
+struct HostOut;  // speculative copy of the likely-final iterate to host memory (nn_dense.cu)
 int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int64_t ldx0, const nn_opts* opts,
-                  double* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_size, cudaStream_t st);
+                  double* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_size, cudaStream_t st,
+                  HostOut* ho = nullptr);
 
 }  // namespace nn

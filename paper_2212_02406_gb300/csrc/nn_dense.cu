@@ -376,8 +376,27 @@ int load_x0(cudaStream_t st, int n, const MixedWs& w, const Common& cm, const X0
   return NN_OK;
 }
 
+}  // namespace
+
+// Host-buffer calls: when a nest is predicted to be the last (s_{k+1} < tol), its new iterate is
+// converted to FP64 and copied to the host on a side stream while the confirming residual runs
+// on the main stream. If the residual confirms the stop, that copy is the result.
+struct HostOut {
+  double* host = nullptr;     // caller's host X (row-major, ld n)
+  double* dev = nullptr;      // device FP64 X (ld n), the conversion target
+  int n = 0;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ready = nullptr, done = nullptr;
+  bool pending = false;       // a side-stream copy was issued and may still run
+  int spec_buf = -1;          // x32 buffer that copy reads
+  int spec_nests = -1;        // nests applied when it was issued
+  bool valid = false;         // set at the end: the copy holds the returned iterate
+};
+
+namespace {
+
 int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const Common& cm, double a_frob,
-              const X0Source& x0src, nn_result* res, int* final_idx) {
+              const X0Source& x0src, nn_result* res, int* final_idx, HostOut* ho) {
   const int np = w.np;
   const double sqrt_n = sqrt(double(n));
   const double n15 = double(n) * sqrt(double(n));
@@ -426,6 +445,10 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
     // errors along eigenvalues of R close to 1, can push rho(R) past 1 nests later. Discard
     // the bulk nest and start again from X_0 at level 2 (once).
     if (k == 1 && level == 1 && !restarted && isfinite(s) && s > 0.85 * res->history[0]) {
+      if (ho != nullptr && ho->pending) {
+        NN_CUDA_TRY(cudaStreamWaitEvent(st, ho->done, 0));
+        ho->spec_nests = -1;
+      }
       restarted = true;
       cur = 0;
       k = 0;
@@ -460,6 +483,7 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
     // large): discard X_k, return to X_{k-1} (still in the other buffer) and continue from
     // there at the top level. NN converges from any X with rho(I - A X) < 1 (Appendix 2).
     if (k >= 1 && level < 4 && rollbacks < 2 && !(s <= res->history[k - 1])) {
+      if (ho != nullptr) ho->spec_nests = -1;  // a copy of the discarded iterate is stale
       ++rollbacks;
       cur ^= 1;
       --k;
@@ -489,14 +513,18 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
     // if it will fall under this level's floor (or under tol), instead of measuring it at the
     // old level first and again at the new one.
     int next_level = level;
-    if (k >= 1 && level < 3 && res->history[k - 1] > 0) {
+    bool likely_final = false;
+    if (k >= 1 && res->history[k - 1] > 0) {
       const double ratio = s / res->history[k - 1];
       if (ratio > 0 && ratio < 1) {
         // s_k / s_{k-1} = rho^(m_{k-1} L_{k-1}) and s_{k+1} / s_k = rho^(m_k L_k), m_k = m_{k-1} (L_{k-1} + 1)
         const double lp = double(nest_depth(o, k - 1)), lk = double(nest_depth(o, k));
         const double s_pred = s * pow(ratio, (lp + 1.0) * lk / lp);
-        while (next_level < 3 && s_pred < 8.0 * level_floor(next_level, c)) ++next_level;
-        if (o.tol > 0 && s_pred < o.tol && next_level < 3) next_level = 3;
+        if (level < 3) {
+          while (next_level < 3 && s_pred < 8.0 * level_floor(next_level, c)) ++next_level;
+          if (o.tol > 0 && s_pred < o.tol && next_level < 3) next_level = 3;
+        }
+        likely_final = o.tol > 0 && s_pred < 0.5 * o.tol && next_level >= 3;
       }
     }
     // Horner: T_1 = R (its column pieces), T_{j+1} = R + R T_j.
@@ -514,6 +542,11 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
       t_cur = w.t_col[j & 1];
     }
     // Update: X_{k+1} = X_k + X_k T, with ||X_{k+1}||_F from the epilogue partials.
+    if (ho != nullptr && ho->pending) {
+      // the side copy must finish reading before x32[cur ^ 1] is rewritten; it is then stale
+      NN_CUDA_TRY(cudaStreamWaitEvent(st, ho->done, 0));
+      if (ho->spec_buf == (cur ^ 1)) ho->spec_nests = -1;
+    }
     {
       TcGemmArgs g;
       g.np = np;
@@ -533,10 +566,23 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
       NN_TRY(reduce_rms(st, cm.partial, grid, 1.0, cm.scal + 1));
       res->launches += 1;
     }
+    if (ho != nullptr && likely_final) {
+      NN_CUDA_TRY(cudaEventRecord(ho->ready, st));
+      NN_CUDA_TRY(cudaStreamWaitEvent(ho->side, ho->ready, 0));
+      NN_TRY(f32_to_f64(ho->side, w.x32[cur ^ 1], np, n, ho->dev, ho->n));
+      NN_CUDA_TRY(cudaMemcpyAsync(ho->host, ho->dev, size_t(ho->n) * size_t(ho->n) * sizeof(double),
+                                  cudaMemcpyDeviceToHost, ho->side));
+      NN_CUDA_TRY(cudaEventRecord(ho->done, ho->side));
+      ho->pending = true;
+      ho->spec_buf = cur ^ 1;
+      ho->spec_nests = k + 1;
+      res->launches += 1;
+    }
     cur ^= 1;
     level = next_level;
   }
   *final_idx = cur;
+  if (ho != nullptr && ho->pending) ho->valid = ho->spec_buf == cur && ho->spec_nests == res->nests;
   if (timer.on) {
     NN_CUDA_TRY(cudaStreamSynchronize(st));
     res->tc_ms = timer.total_ms();
@@ -563,7 +609,8 @@ int check_opts(const nn_opts* o, int64_t n) {
 }
 
 int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int64_t ldx0, const nn_opts* opts,
-                  double* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_size, cudaStream_t st) {
+                  double* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_size, cudaStream_t st,
+                  HostOut* ho) {
   const nn_opts& o = *opts;
   Carver c(workspace, ws_size);
   Common cm;
@@ -610,8 +657,9 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     NN_CUDA_TRY(cudaMemcpyAsync(&a_frob, cm.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
     NN_CUDA_TRY(cudaStreamSynchronize(st));
     res->launches += 4;
-    NN_TRY(run_mixed(st, ni, w, o, cm, a_frob, x0src, res, &fin));
-    NN_TRY(f32_to_f64(st, w.x32[fin], w.np, ni, X, ldx));
+    NN_TRY(run_mixed(st, ni, w, o, cm, a_frob, x0src, res, &fin, ho));
+    if (ho != nullptr && ho->pending) NN_CUDA_TRY(cudaStreamWaitEvent(st, ho->done, 0));
+    if (ho == nullptr || !ho->valid) NN_TRY(f32_to_f64(st, w.x32[fin], w.np, ni, X, ldx));
     res->launches += 3;
   }
   // Algorithmic work of the method: (L+1) GEMMs per nest plus the final residual.
@@ -648,7 +696,9 @@ size_t nn_workspace_bytes(int64_t n, int dtype) {
 size_t nn_workspace_bytes_host(int64_t n, int dtype) {
   size_t b = nn_workspace_bytes(n, dtype);
   if (b == 0) return 0;
-  return b + 3 * align_up(size_t(n) * size_t(n) * sizeof(double), 256) + 256;
+  // A, X_0, X on the device, plus the preconditioner's scratch (8 + 2n doubles)
+  return b + 3 * align_up(size_t(n) * size_t(n) * sizeof(double), 256) +
+         align_up(8 * sizeof(double), 256) + align_up(2 * size_t(n) * sizeof(double), 256) + 256;
 }
 
 int nn_init_precond(const double* A, int64_t n, int64_t lda, int kind, double scalar, double* X0, int64_t ldx,
@@ -681,12 +731,21 @@ int nn_invert(const double* A, int64_t n, int64_t lda, const double* X0, int64_t
   return s;
 }
 
-int nn_invert_host(const double* A_host, int64_t n, const double* X0_host, const nn_opts* opts, double* X_host,
-                   nn_result* res, void* workspace, size_t ws_size, void* stream) {
+}  // extern "C"
+
+namespace nn {
+namespace {
+
+// Shared body of the host-buffer entry points: copy A (and X_0 when given) in, build X_0 on the
+// device otherwise, run the chain, and return X through the speculative side-stream copy when
+// it holds the final iterate.
+int invert_host_impl(const double* A_host, int64_t n, const double* X0_host, int pc_kind, double pc_scalar,
+                     const nn_opts* opts, double* X_host, nn_result* res, void* workspace, size_t ws_size,
+                     void* stream) {
   if (res == nullptr) return NN_ERR_ARG;
   init_result(res);
   NN_TRY(check_opts(opts, n));
-  if (A_host == nullptr || X0_host == nullptr || X_host == nullptr) return NN_ERR_ARG;
+  if (A_host == nullptr || X_host == nullptr) return NN_ERR_ARG;
   const size_t need = nn_workspace_bytes_host(n, opts->dtype);
   if (workspace == nullptr || ws_size < need) return NN_ERR_OOM_BUDGET;
   const size_t inner = nn_workspace_bytes(n, opts->dtype);
@@ -695,15 +754,72 @@ int nn_invert_host(const double* A_host, int64_t n, const double* X0_host, const
   double* dA = c.take<double>(e);
   double* dX0 = c.take<double>(e);
   double* dX = c.take<double>(e);
+  double* pc_scratch = c.take<double>(8);
+  double* pc_vec = c.take<double>(2 * size_t(n));
   if (!c.ok) return NN_ERR_OOM_BUDGET;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   NN_CUDA_TRY(cudaMemcpyAsync(dA, A_host, e * sizeof(double), cudaMemcpyHostToDevice, st));
-  NN_CUDA_TRY(cudaMemcpyAsync(dX0, X0_host, e * sizeof(double), cudaMemcpyHostToDevice, st));
-  int s = invert_device(dA, n, n, dX0, n, opts, dX, n, res, workspace, inner, st);
-  if (s == NN_ERR_CUDA || s == NN_ERR_ARG || s == NN_ERR_UNSUPPORTED || s == NN_ERR_OOM_BUDGET) return s;
-  NN_CUDA_TRY(cudaMemcpyAsync(X_host, dX, e * sizeof(double), cudaMemcpyDeviceToHost, st));
-  NN_CUDA_TRY(cudaStreamSynchronize(st));
-  return s;
+  if (X0_host != nullptr) {
+    NN_CUDA_TRY(cudaMemcpyAsync(dX0, X0_host, e * sizeof(double), cudaMemcpyHostToDevice, st));
+  } else {
+    NN_TRY(precond_fill(st, dA, n, int(n), pc_kind, pc_scalar, dX0, n, pc_scratch, pc_vec));
+    res->launches += 2;
+  }
+  HostOut ho;
+  ho.host = X_host;
+  ho.dev = dX;
+  ho.n = int(n);
+  const bool spec = opts->dtype == NN_MIXED_BF16 && opts->tol > 0;
+  if (spec) {
+    NN_CUDA_TRY(cudaStreamCreateWithFlags(&ho.side, cudaStreamNonBlocking));
+    if (cudaEventCreateWithFlags(&ho.ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ho.done, cudaEventDisableTiming) != cudaSuccess) {
+      if (ho.ready) cudaEventDestroy(ho.ready);
+      cudaStreamDestroy(ho.side);
+      (void)cudaGetLastError();
+      return NN_ERR_CUDA;
+    }
+  }
+  int s = invert_device(dA, n, n, dX0, n, opts, dX, n, res, workspace, inner, st, spec ? &ho : nullptr);
+  int rc = s;
+  if (!(s == NN_ERR_CUDA || s == NN_ERR_ARG || s == NN_ERR_UNSUPPORTED || s == NN_ERR_OOM_BUDGET)) {
+    if (!ho.valid && cudaMemcpyAsync(X_host, dX, e * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      rc = NN_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = NN_ERR_CUDA;
+  }
+  if (spec) {
+    if (cudaStreamSynchronize(ho.side) != cudaSuccess && rc == s) rc = NN_ERR_CUDA;
+    cudaEventDestroy(ho.ready);
+    cudaEventDestroy(ho.done);
+    cudaStreamDestroy(ho.side);
+  }
+  (void)cudaGetLastError();
+  return rc;
+}
+
+}  // namespace
+}  // namespace nn
+
+extern "C" {
+
+int nn_invert_host(const double* A_host, int64_t n, const double* X0_host, const nn_opts* opts, double* X_host,
+                   nn_result* res, void* workspace, size_t ws_size, void* stream) {
+  if (X0_host == nullptr) {
+    if (res != nullptr) init_result(res);
+    return NN_ERR_ARG;
+  }
+  return invert_host_impl(A_host, n, X0_host, 0, 0.0, opts, X_host, res, workspace, ws_size, stream);
+}
+
+int nn_invert_host_pc(const double* A_host, int64_t n, int pc_kind, double pc_scalar, const nn_opts* opts,
+                      double* X_host, nn_result* res, void* workspace, size_t ws_size, void* stream) {
+  if (pc_kind < NN_PC_PAN_SCHREIBER || pc_kind > NN_PC_THETA2 || (pc_kind == NN_PC_SCALAR && !(pc_scalar > 0)) ||
+      (pc_kind == NN_PC_THETA2 && !(pc_scalar >= 1 && pc_scalar <= 1024))) {
+    if (res != nullptr) init_result(res);
+    return NN_ERR_ARG;
+  }
+  if (pc_kind == NN_PC_JACOBI && pc_scalar == 0) pc_scalar = 1.0;
+  return invert_host_impl(A_host, n, nullptr, pc_kind, pc_scalar, opts, X_host, res, workspace, ws_size, stream);
 }
 
 int nn_residual(const double* A, int64_t lda, const double* X, int64_t ldx, int64_t n, int dtype, double* rms_frob,

@@ -241,6 +241,41 @@ def test_host_variant_equals_device_variant(nn):
         assert np.array_equal(x1, xh)
 
 
+@pytest.mark.parametrize("tol", [1e-4, 1e-6, 1e-7])
+@pytest.mark.parametrize("kappa", [1e1, 1e2, 1e3])
+def test_host_pc_variant_and_early_copy_equal_device(nn, tol, kappa):
+    # nn_invert_host_pc builds X_0 on the device; for the mixed chain the likely-final iterate is
+    # copied to the host on a side stream while its residual runs. Either way the host result
+    # must equal the device call's bit for bit, whether or not the prediction held.
+    import torch
+
+    n = 384
+    a, q, lam = synth.spd_spectrum(n, kappa, seed=int(kappa) + 3)
+    alpha = 2.0 / (lam[0] + lam[-1])
+    x0 = dense.precond_scalar(n, alpha)
+    for dtype in ("mixed_bf16", "f64"):
+        st1, res1, x1 = _run(nn, a, x0, 2, tol, 40, dtype)
+        xh = np.full_like(a, np.nan)
+        ws = nn.workspace(n, dtype, host=True)
+        st2, res2 = nn.nn_invert_host_pc(np.ascontiguousarray(a), "scalar", alpha, nn.make_opts(2, tol, 40, dtype),
+                                         xh, ws)
+        torch.cuda.synchronize()
+        assert st1 == st2
+        assert res1["nests"] == res2["nests"] and res1["history"] == res2["history"]
+        assert np.array_equal(x1, xh)
+
+
+def test_host_pc_rejects_bad_preconditioner(nn):
+    n = 8
+    a = np.eye(n)
+    xh = np.empty_like(a)
+    ws = nn.workspace(n, "f64", host=True)
+    st, _ = nn.nn_invert_host_pc(a, "scalar", -1.0, nn.make_opts(2, 1e-8, 10, "f64"), xh, ws)
+    assert st == nn.NN_ERR_ARG
+    st, _ = nn.nn_invert_host_pc(a, "theta2", 0.0, nn.make_opts(2, 1e-8, 10, "f64"), xh, ws)
+    assert st == nn.NN_ERR_ARG
+
+
 @pytest.mark.parametrize("n", [1, 31, 256, 300])
 def test_residual_call(nn, n):
     import torch
