@@ -247,17 +247,21 @@ int nn_solve_normal(const void* A, int64_t n, int64_t lda, int is_complex, const
  *
  * nn_batched_plan (host only): sorts the matrices by size (largest first) and groups equal
  * sizes into work items. sizes_host[count] in 1..64; cfg_by_u (nullable, 65 entries indexed by
- * U, -1 = default) picks the thread tiling per size (0: 8x8 threads per matrix, up to four
- * matrices per CTA; 1: 16x16 threads per matrix); plan_host holds nn_batched_plan_size(count)
+ * U, -1 = default) picks the path per size (0: CUDA cores, 8x8 threads per matrix, up to four
+ * matrices per CTA; 1: CUDA cores, 16x16 threads per matrix; 2: tensor cores, for U in
+ * {16, 32, 48, 64} (other sizes fall back to 0 or 1): the iterates stay in TMEM and each complex
+ * product is one tcgen05 MMA on the real embedding [[Pr, -Pi], [Pi, Pr]] [Qr; Qi] with three
+ * BF16 pieces per operand, FP32-level accuracy); plan_host holds nn_batched_plan_size(count)
  * int32. The caller copies the plan to the device and may reuse it for every launch with the
  * same size list.
  *
  * nn_invert_batched_c64: A and X device complex64 (interleaved re, im) packed back to back,
  * matrix b row-major at element offset offsets[b] (device int64) with size sizes[b] (device
  * int32); plan = the device copy of the plan. residual[b] (device float) = s of the returned
- * X_b; status[b] (device int32) = NN_OK or NN_ERR_DIVERGED. The call only enqueues work on
- * `stream` (a memset and one kernel; no synchronisation, no allocation), so it can be
- * captured in a CUDA graph. Needs nn_batched_workspace_bytes(count) of workspace. */
+ * X_b; status[b] (device int32) = NN_OK, NN_ERR_DIVERGED, or NN_ERR_TIMEOUT (a tensor-core
+ * item whose bounded wait ran out). The call only enqueues work on `stream` (a memset and two
+ * kernels, tensor-core items then CUDA-core items; no synchronisation, no allocation), so it
+ * can be captured in a CUDA graph. Needs nn_batched_workspace_bytes(count) of workspace. */
 int64_t nn_batched_plan_size(int64_t count);
 int nn_batched_plan(const int32_t* sizes_host, int64_t count, const int32_t* cfg_by_u, int32_t* plan_host);
 size_t nn_batched_workspace_bytes(int64_t count);

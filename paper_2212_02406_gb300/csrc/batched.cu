@@ -33,7 +33,7 @@ constexpr int BT_THREADS = 256;
 constexpr int BT_MAX_U = 64;
 constexpr int BT_BUFS = 5;                  // A, X, R, T, W
 constexpr int BT_SMEM = 200 * 1024;         // dynamic shared memory per CTA
-constexpr int PLAN_HDR = 2;                 // [n_items, count]
+constexpr int PLAN_HDR = 3;                 // [n_items, count, n_tc]
 
 enum : int { BM_RESID = 0, BM_ADD = 1 };
 
@@ -145,6 +145,7 @@ struct BatchedParams {
   float* residual;
   int32_t* status;
   int* queue;
+  int* err;     // device error word of the tensor-core path's bounded waits
 };
 
 // Sum over the threads of one group (nthr = TG*TG threads, whole warps), result in red_out[g].
@@ -282,6 +283,316 @@ __device__ void dispatch_tile(const BatchedParams& p, int U, int start, int cnt,
   }
 }
 
+// ---- tensor-core path (plan configuration 2; U in {16, 32, 48, 64}) ------------------------
+//
+// One matrix per CTA at a time, every iterate kept on chip:
+//   * masters (A, X, R, T, W) live in TMEM as the real form [Re; Im] of each U x U complex matrix:
+//     lane i < U holds row i's real parts, lane U + i its imaginary parts, columns 0..U-1;
+//   * a complex product C = P Q runs as one real MMA on the embedding
+//         [Cr; Ci] (2U x U) = [[Pr, -Pi], [Pi, Pr]] (2U x 2U) . [Qr; Qi] (2U x U),
+//     i.e. M = 128 (2U rows used), N = U, K = 2U, with no redundant work. Its left operand is
+//     built from P's master rows, its right operand (K-major: row j = column j of [Qr; Qi]) is
+//     exactly the transpose of Q's master (lane k, column j -> row j, k);
+//   * operands are split into three BF16 pieces (x = p0 + p1 + p2, each the BF16 rounding of the
+//     remainder) and written to shared memory in the SWIZZLE_128B K-major layout; six piece
+//     products (the pairs with i + j <= 2, smallest first) accumulate in FP32 in TMEM, which
+//     matches an FP32 product to about 2^-24 relative;
+//   * the epilogue reads the accumulator, applies I - C or D + C in FP32 and writes the result
+//     master back to TMEM; the residual's sum of squares is reduced across the CTA.
+namespace btc {
+constexpr int M = 128;                         // MMA rows (2U used)
+constexpr int KP = 128;                        // K capacity (2U used): two 64-wide k-blocks
+constexpr int NP = 64;                         // B-operand rows capacity (U used)
+constexpr int A_PIECE = M * KP * 2;            // 32 KB
+constexpr int B_PIECE = NP * KP * 2;           // 16 KB
+constexpr int OPS_BYTES = 3 * A_PIECE + 3 * B_PIECE;
+constexpr uint32_t ACC = 0, MA = 64, MX = 128, MR = 192, MT = 256, MW = 320;
+constexpr uint32_t TMEM_COLS = 512;
+static_assert(OPS_BYTES + 1024 <= BT_SMEM, "operand pieces fit the dynamic shared memory");
+}  // namespace btc
+
+// Shared-memory matrix descriptor of a K-major SWIZZLE_128B tile (8-row atoms 1024 B apart).
+__device__ __forceinline__ uint64_t bt_sw128_desc(uint32_t saddr) {
+  return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
+         (uint64_t(1) << 46) | (uint64_t(2) << 61);
+}
+
+// Byte offset of element (r, k) in a K-major SWIZZLE_128B operand of `rows` rows and 64-wide
+// k-blocks: 16-byte chunk c of row r sits at chunk c ^ (r mod 8) of its 128-byte line.
+__device__ __forceinline__ uint32_t bt_sw128_offset(int r, int k, int rows) {
+  const int kb = k >> 6, c = (k & 63) >> 3, e = k & 7;
+  return uint32_t(kb * rows * 128 + (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4) + (e << 1));
+}
+
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
+  p0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(p0);
+  p1 = __float2bfloat16_rn(r1);
+  p2 = __float2bfloat16_rn(r1 - __bfloat162float(p1));
+}
+
+// Left operand [[Pr, -Pi], [Pi, Pr]] pieces from master P; warp (q, h) owns lanes 32q.. and
+// columns 32h.. of the master.
+template <int U>
+__device__ __forceinline__ void bt_build_left(uint32_t tmem, uint32_t cP, uint8_t* ops, int q, int h, int l) {
+  if (h * 32 >= U) return;
+  uint32_t raw[32];
+  tmem_ld_32x32b_x32(tmem + (uint32_t(q * 32) << 16) + cP + uint32_t(h * 32), raw);
+  tmem_ld_wait();
+  if (l >= 2 * U) return;
+  const bool re = l < U;
+  const int i = re ? l : l - U;
+  // destination 1: row i at K = (re ? 0 : U) + column, sign (re ? + : -); destination 2: row
+  // U + i at K = (re ? U : 0) + column, sign +
+  const int rows[2] = {i, U + i};
+  const int kbase[2] = {re ? 0 : U, re ? U : 0};
+  const float sgn[2] = {re ? 1.0f : -1.0f, 1.0f};
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+      const int j0 = h * 32 + ch * 8;
+      if (j0 >= U) break;
+      uint32_t pk[3][4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+        split3(sgn[d] * __uint_as_float(raw[ch * 8 + 2 * e]), a0, a1, a2);
+        split3(sgn[d] * __uint_as_float(raw[ch * 8 + 2 * e + 1]), b0, b1, b2);
+        pk[0][e] = uint32_t(__bfloat16_as_ushort(a0)) | (uint32_t(__bfloat16_as_ushort(b0)) << 16);
+        pk[1][e] = uint32_t(__bfloat16_as_ushort(a1)) | (uint32_t(__bfloat16_as_ushort(b1)) << 16);
+        pk[2][e] = uint32_t(__bfloat16_as_ushort(a2)) | (uint32_t(__bfloat16_as_ushort(b2)) << 16);
+      }
+      const uint32_t off = bt_sw128_offset(rows[d], kbase[d] + j0, btc::M);
+#pragma unroll
+      for (int pc = 0; pc < 3; ++pc)
+        *reinterpret_cast<uint4*>(ops + pc * btc::A_PIECE + off) = make_uint4(pk[pc][0], pk[pc][1], pk[pc][2], pk[pc][3]);
+    }
+  }
+}
+
+// Right operand pieces: row j, column k = master Q (lane k, column j), k < 2U, j < U. Even lanes
+// store the pair (k, k + 1) received from the odd neighbour.
+template <int U>
+__device__ __forceinline__ void bt_build_right(uint32_t tmem, uint32_t cQ, uint8_t* ops, int q, int h, int l) {
+  if (h * 32 >= U) return;
+  uint32_t raw[32];
+  tmem_ld_32x32b_x32(tmem + (uint32_t(q * 32) << 16) + cQ + uint32_t(h * 32), raw);
+  tmem_ld_wait();
+  uint8_t* bops = ops + 3 * btc::A_PIECE;
+  const bool store = (l & 1) == 0 && l < 2 * U;
+#pragma unroll
+  for (int t = 0; t < 32; ++t) {
+    const float v = __uint_as_float(raw[t]);
+    const float w = __shfl_down_sync(0xffffffffu, v, 1);
+    const int j = h * 32 + t;
+    if (store && j < U) {
+      __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+      split3(v, a0, a1, a2);
+      split3(w, b0, b1, b2);
+      const uint32_t off = bt_sw128_offset(j, l, btc::NP);
+      *reinterpret_cast<uint32_t*>(bops + off) =
+          uint32_t(__bfloat16_as_ushort(a0)) | (uint32_t(__bfloat16_as_ushort(b0)) << 16);
+      *reinterpret_cast<uint32_t*>(bops + btc::B_PIECE + off) =
+          uint32_t(__bfloat16_as_ushort(a1)) | (uint32_t(__bfloat16_as_ushort(b1)) << 16);
+      *reinterpret_cast<uint32_t*>(bops + 2 * btc::B_PIECE + off) =
+          uint32_t(__bfloat16_as_ushort(a2)) | (uint32_t(__bfloat16_as_ushort(b2)) << 16);
+    }
+  }
+}
+
+// out = mode(P Q) for masters at TMEM columns cP, cQ, cD (addend), cOut; returns this thread's
+// sum of squares of the result (residual mode). false if the MMA wait timed out.
+template <int U>
+__device__ bool bt_product(uint32_t tmem, uint8_t* ops, uint64_t* bar, uint32_t& phase, volatile int* abort_flag,
+                           int* err, uint32_t cP, uint32_t cQ, uint32_t cD, uint32_t cOut, int mode, float* ss) {
+  const int w = int(threadIdx.x >> 5), q = w & 3, h = w >> 2, l = q * 32 + int(threadIdx.x & 31);
+  bt_build_left<U>(tmem, cP, ops, q, h, l);
+  bt_build_right<U>(tmem, cQ, ops, q, h, l);
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc_fence_after();
+    constexpr uint32_t idesc =
+        (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(U >> 3) << 17) | (uint32_t(btc::M >> 4) << 24);
+    const uint32_t base = smem_u32(ops);
+    // piece pairs (a, b), smallest terms first: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
+    uint32_t acc = 0;
+#pragma unroll 1
+    for (int pp = 0; pp < 6; ++pp) {
+      const int pa = pp == 0 ? 2 : (pp == 1 || pp == 3) ? 1 : 0;
+      const int pb = pp == 2 ? 2 : (pp == 1 || pp == 4) ? 1 : 0;
+      const uint32_t a0 = base + uint32_t(pa * btc::A_PIECE);
+      const uint32_t b0 = base + uint32_t(3 * btc::A_PIECE + pb * btc::B_PIECE);
+#pragma unroll 1
+      for (int st = 0; st < U / 8; ++st) {
+        const int kb = st >> 2, kk = st & 3;
+        const uint64_t ad = bt_sw128_desc(a0 + uint32_t(kb * btc::M * 128)) + uint64_t(2 * kk);
+        const uint64_t bd = bt_sw128_desc(b0 + uint32_t(kb * btc::NP * 128)) + uint64_t(2 * kk);
+        tc_mma_bf16(tmem + btc::ACC, ad, bd, idesc, acc);
+        acc = 1;
+      }
+    }
+    tc_commit(bar);
+  }
+  // every thread learns the same outcome (a timed-out wait in any thread aborts the item)
+  const bool ok = __syncthreads_and(mbar_wait(bar, phase, abort_flag, err) ? 1 : 0) != 0;
+  phase ^= 1u;
+  tc_fence_after();
+  if (!ok) return false;
+  // epilogue: warp (q, h) owns accumulator lanes 32q.. and columns 32h..
+  float local = 0.f;
+  if (h * 32 < U) {
+    uint32_t c[32], d[32];
+    const uint32_t lane_off = uint32_t(q * 32) << 16;
+    tmem_ld_32x32b_x32(tmem + lane_off + btc::ACC + uint32_t(h * 32), c);
+    if (mode == BM_ADD) tmem_ld_32x32b_x32(tmem + lane_off + cD + uint32_t(h * 32), d);
+    tmem_ld_wait();
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const int j = h * 32 + t;
+      const float cv = __uint_as_float(c[t]);
+      float v;
+      if (mode == BM_RESID) {
+        v = ((l < U && j == l) ? 1.f : 0.f) - cv;
+        if (l < 2 * U && j < U) local = fmaf(v, v, local);
+      } else {
+        v = __uint_as_float(d[t]) + cv;
+      }
+      c[t] = __float_as_uint(v);
+    }
+    tmem_st_32x32b_x32(tmem + lane_off + cOut + uint32_t(h * 32), c);
+    tmem_st_wait();
+  }
+  *ss = local;
+  tc_fence_before();
+  __syncthreads();
+  return true;
+}
+
+// Sum over the CTA (256 threads); result broadcast to every thread.
+__device__ __forceinline__ float bt_block_sum(float v, float* red_warp) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red_warp[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int w = 0; w < BT_THREADS / 32; ++w) t += red_warp[w];
+  __syncthreads();
+  return t;
+}
+
+template <int U>
+__device__ void process_item_tc(const BatchedParams& p, int start, uint8_t* ops, uint32_t tmem, uint64_t* bar,
+                                uint32_t& phase, volatile int* abort_flag, float* red_warp) {
+  const int w = int(threadIdx.x >> 5), q = w & 3, h = w >> 2, l = q * 32 + int(threadIdx.x & 31);
+  const int b = p.plan[PLAN_HDR + start];
+  const int64_t off = p.offsets[b];
+  const float2* A = p.A + off;
+  // masters A and X_0 = c diag(A)^-1 (damped Jacobi) in their real forms
+  if (h * 32 < U) {
+    uint32_t va[32], vx[32];
+    const bool valid_row = l < 2 * U;
+    const bool re = l < U;
+    const int i = re ? l : l - U;
+    float2 aii = make_float2(1.f, 0.f);
+    if (valid_row) aii = A[i * U + i];
+    const float cdamp = 1.f / (1.f + p.damping * float(U));
+    const float den = aii.x * aii.x + aii.y * aii.y;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const int j = h * 32 + t;
+      float av = 0.f, xv = 0.f;
+      if (valid_row && j < U) {
+        const float2 a = A[i * U + j];
+        av = re ? a.x : a.y;
+        if (j == i) xv = re ? cdamp * aii.x / den : -cdamp * aii.y / den;
+      }
+      va[t] = __float_as_uint(av);
+      vx[t] = __float_as_uint(xv);
+    }
+    const uint32_t lane_off = uint32_t(q * 32) << 16;
+    tmem_st_32x32b_x32(tmem + lane_off + btc::MA + uint32_t(h * 32), va);
+    tmem_st_32x32b_x32(tmem + lane_off + btc::MX + uint32_t(h * 32), vx);
+    tmem_st_wait();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  bool frozen = false, timed_out = false;
+  float s_prev = 0.f, s_last = 0.f;
+  int st = NN_OK;
+  uint32_t cX = btc::MX;
+  for (int k = 0; k <= p.nests; ++k) {
+    if (!frozen) {
+      float ss = 0.f;
+      if (!bt_product<U>(tmem, ops, bar, phase, abort_flag, p.err, btc::MA, cX, 0, btc::MR, BM_RESID, &ss)) {
+        timed_out = true;
+        break;
+      }
+      const float s = sqrtf(bt_block_sum(ss, red_warp)) / float(U);
+      s_last = s;
+      if (!isfinite(s) || (k >= 1 && s >= 1.f && s > s_prev)) {
+        st = NN_ERR_DIVERGED;
+        frozen = true;
+      }
+      s_prev = s;
+    }
+    if (k == p.nests || frozen) break;
+    // Horner: T_1 = R, T_{j+1} = R + R T_j (T, W alternate); X_{k+1} = X_k + X_k T
+    uint32_t t_cur = btc::MR;
+    bool ok = true;
+    for (int j = 1; j < p.depth && ok; ++j) {
+      const uint32_t dst = (t_cur == btc::MT) ? btc::MW : btc::MT;
+      float unused = 0.f;
+      ok = bt_product<U>(tmem, ops, bar, phase, abort_flag, p.err, btc::MR, t_cur, btc::MR, dst, BM_ADD, &unused);
+      t_cur = dst;
+    }
+    float unused = 0.f;
+    if (!ok || !bt_product<U>(tmem, ops, bar, phase, abort_flag, p.err, cX, t_cur, cX, cX, BM_ADD, &unused)) {
+      timed_out = true;
+      break;
+    }
+  }
+  if (timed_out) st = NN_ERR_TIMEOUT;
+  // X (complex, row-major) from the X master; 2U is a multiple of 32, so the test is warp-uniform
+  if (h * 32 < U && q * 32 < 2 * U) {
+    uint32_t vx[32];
+    tmem_ld_32x32b_x32(tmem + (uint32_t(q * 32) << 16) + cX + uint32_t(h * 32), vx);
+    tmem_ld_wait();
+    const bool re = l < U;
+    const int i = re ? l : l - U;
+    float* Xf = reinterpret_cast<float*>(p.X + off);
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const int j = h * 32 + t;
+      if (j < U) Xf[2 * (i * U + j) + (re ? 0 : 1)] = __uint_as_float(vx[t]);
+    }
+  }
+  if (threadIdx.x == 0) {
+    p.residual[b] = s_last;
+    p.status[b] = st;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+__device__ void dispatch_tc(const BatchedParams& p, int U, int start, uint8_t* ops, uint32_t tmem, uint64_t* bar,
+                            uint32_t& phase, volatile int* abort_flag, float* red_warp) {
+  switch (U) {
+    case 16: process_item_tc<16>(p, start, ops, tmem, bar, phase, abort_flag, red_warp); break;
+    case 32: process_item_tc<32>(p, start, ops, tmem, bar, phase, abort_flag, red_warp); break;
+    case 48: process_item_tc<48>(p, start, ops, tmem, bar, phase, abort_flag, red_warp); break;
+    default: process_item_tc<64>(p, start, ops, tmem, bar, phase, abort_flag, red_warp); break;
+  }
+}
+
+// TC = true: the plan's tensor-core items [0, n_tc); TC = false: the CUDA-core items
+// [n_tc, n_items). Each kernel pulls items from its own counter.
+template <bool TC>
 __global__ void __launch_bounds__(BT_THREADS, 1) batched_nn_kernel(const BatchedParams p) {
   extern __shared__ float2 smem[];
   __shared__ float red_warp[BT_THREADS / 32];
@@ -289,21 +600,56 @@ __global__ void __launch_bounds__(BT_THREADS, 1) batched_nn_kernel(const Batched
   __shared__ int item;
   const int n_items = p.plan[0];
   const int count = p.plan[1];
+  const int n_tc = p.plan[2];
   const int32_t* items = p.plan + PLAN_HDR + count;
-  while (true) {
-    if (threadIdx.x == 0) item = atomicAdd(p.queue, 1);
+  const int first = TC ? 0 : n_tc, last = TC ? n_tc : n_items;
+  if (TC) {
+    // operand pieces at a 1024-aligned offset of the dynamic shared memory, 512 TMEM columns
+    // (one CTA per SM), one mbarrier for MMA completion
+    __shared__ __align__(8) uint64_t tc_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_word;
+    uint8_t* ops = reinterpret_cast<uint8_t*>(smem);
+    ops += (1024u - (smem_u32(ops) & 1023u)) & 1023u;
+    if (threadIdx.x == 0) {
+      mbar_init(&tc_bar, 1);
+      abort_word = 0;
+      mbar_fence_init();
+    }
+    if (threadIdx.x < 32) tmem_alloc(&tmem_slot, btc::TMEM_COLS);
+    tc_fence_before();
     __syncthreads();
-    const int it = item;
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    uint32_t phase = 0;
+    while (true) {
+      if (threadIdx.x == 0) item = first + atomicAdd(p.queue, 1);
+      __syncthreads();
+      const int it = item;
+      __syncthreads();
+      if (it >= last) break;
+      dispatch_tc(p, items[4 * it + 0], items[4 * it + 1], ops, tmem, &tc_bar, phase, &abort_word, red_warp);
+    }
+    tc_fence_before();
     __syncthreads();
-    if (it >= n_items) break;
-    const int U = items[4 * it + 0];
-    const int start = items[4 * it + 1];
-    const int cnt = items[4 * it + 2];
-    const int cfg = items[4 * it + 3];
-    if (cfg == 0)
-      dispatch_tile<8>(p, U, start, cnt, smem, red_warp, red_grp);
-    else
-      dispatch_tile<16>(p, U, start, cnt, smem, red_warp, red_grp);
+    tc_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(tmem, btc::TMEM_COLS);
+  } else {
+    while (true) {
+      if (threadIdx.x == 0) item = first + atomicAdd(p.queue + 1, 1);
+      __syncthreads();
+      const int it = item;
+      __syncthreads();
+      if (it >= last) break;
+      const int U = items[4 * it + 0];
+      const int start = items[4 * it + 1];
+      const int cnt = items[4 * it + 2];
+      const int cfg = items[4 * it + 3];
+      if (cfg == 0)
+        dispatch_tile<8>(p, U, start, cnt, smem, red_warp, red_grp);
+      else
+        dispatch_tile<16>(p, U, start, cnt, smem, red_warp, red_grp);
+    }
   }
 }
 
@@ -315,13 +661,15 @@ int bt_init() {
   int dev = 0;
   NN_CUDA_TRY(cudaGetDevice(&dev));
   NN_CUDA_TRY(cudaDeviceGetAttribute(&g_bt_sms, cudaDevAttrMultiProcessorCount, dev));
-  NN_CUDA_TRY(cudaFuncSetAttribute(batched_nn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
+  NN_CUDA_TRY(cudaFuncSetAttribute(batched_nn_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
+  NN_CUDA_TRY(cudaFuncSetAttribute(batched_nn_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
   g_bt_init = true;
   return NN_OK;
 }
 
 // Matrices per work item for (U, cfg): thread groups available and shared memory.
 int group_count(int U, int cfg) {
+  if (cfg == 2) return 1;
   const int by_threads = cfg == 0 ? BT_THREADS / 64 : 1;
   const int per = BT_BUFS * U * U * int(sizeof(float2));
   int by_smem = BT_SMEM / per;
@@ -358,7 +706,8 @@ int nn_batched_plan(const int32_t* sizes_host, int64_t count, const int32_t* cfg
   while (pos < count) {
     const int U = sizes_host[order[size_t(pos)]];
     int cfg = (cfg_by_u != nullptr && cfg_by_u[U] >= 0) ? cfg_by_u[U] : (U <= 32 ? 0 : 1);
-    if (cfg != 0 && cfg != 1) return NN_ERR_ARG;
+    if (cfg < 0 || cfg > 2) return NN_ERR_ARG;
+    if (cfg == 2 && (U % 16 != 0 || U > 64)) cfg = U <= 32 ? 0 : 1;
     if (cfg == 1 && (U + 15) / 16 > 4) cfg = 0;
     if (cfg == 0 && (U + 7) / 8 > 8) return NN_ERR_ARG;
     const int gmax = group_count(U, cfg);
@@ -371,7 +720,18 @@ int nn_batched_plan(const int32_t* sizes_host, int64_t count, const int32_t* cfg
     ++n_items;
     pos += cnt;
   }
+  // tensor-core items first (their kernel takes [0, n_tc)), each part still largest first
+  std::vector<int32_t> tmp(items, items + 4 * n_items);
+  int64_t w = 0, n_tc = 0;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int64_t it = 0; it < n_items; ++it)
+      if ((tmp[size_t(4 * it + 3)] == 2) == (pass == 0)) {
+        for (int f = 0; f < 4; ++f) items[4 * w + f] = tmp[size_t(4 * it + f)];
+        ++w;
+        if (pass == 0) ++n_tc;
+      }
   plan_host[0] = int32_t(n_items);
+  plan_host[2] = int32_t(n_tc);
   return NN_OK;
 }
 
@@ -402,8 +762,11 @@ int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* 
   p.residual = residual;
   p.status = status;
   p.queue = static_cast<int*>(workspace);
-  NN_CUDA_TRY(cudaMemsetAsync(p.queue, 0, sizeof(int), st));
-  batched_nn_kernel<<<g_bt_sms, BT_THREADS, BT_SMEM, st>>>(p);
+  p.err = static_cast<int*>(workspace) + 4;
+  NN_CUDA_TRY(cudaMemsetAsync(p.queue, 0, 8 * sizeof(int), st));
+  batched_nn_kernel<true><<<g_bt_sms, BT_THREADS, BT_SMEM, st>>>(p);
+  NN_CUDA_TRY(cudaGetLastError());
+  batched_nn_kernel<false><<<g_bt_sms, BT_THREADS, BT_SMEM, st>>>(p);
   NN_CUDA_TRY(cudaGetLastError());
   return NN_OK;
 }
