@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--max-active", type=int, default=8)
     ap.add_argument("--gemm-variant", type=int, default=0, choices=[0, 1, 2, 3], help="0 auto, 1 single-CTA tiles, 2 CTA pairs with multicast, 3 2-SM MMA")
     ap.add_argument("--spmv-variant", type=int, default=0, choices=[0, 1], help="0 auto (bulk-copy ring), 1 staged loads")
+    ap.add_argument("--batched-tc", action="store_true",
+                    help="batched workload: tensor-core items for U in {16, 32, 48, 64}")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -592,7 +594,11 @@ def run_batched(args, rank, world, local_rank):
     A = torch.from_numpy(bt.data).to(dev)
     offs = torch.from_numpy(bt.offsets.astype(np.int64)).to(dev)
     sizes = torch.from_numpy(bt.sizes.astype(np.int32)).to(dev)
-    plan = torch.from_numpy(abi.nn_batched_plan(bt.sizes, load_batched_tuning())).to(dev)
+    table = load_batched_tuning()
+    if args.batched_tc:
+        table = dict(table or {})
+        table.update({16: 2, 32: 2, 48: 2, 64: 2})
+    plan = torch.from_numpy(abi.nn_batched_plan(bt.sizes, table)).to(dev)
     X = torch.empty_like(A)
     res = torch.empty(count, dtype=torch.float32, device=dev)
     st = torch.empty(count, dtype=torch.int32, device=dev)
@@ -639,11 +645,14 @@ def run_batched(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "c64 (fp32 FMA)", "data": "synthetic",
             "config": {"workload": f"{count} Gram matrices A = H^H H + 0.1 I, H 128 x U CN(0,1), U uniform over "
                                    f"{{8,16,24,32,48,64}}, X0 = diag(A)^-1/(1 + {damping:g} U), depth {depth}, "
-                                   f"{nests} nests, one persistent kernel replayed from a CUDA graph",
-                       "count": count, "damping": damping, "l2": "A + X = 363 MB > L2"},
-            "status_ok_fraction": float(np.mean(stats == 0)), "gpu_launches": args.steps,
+                                   f"{nests} nests, two persistent kernels (tensor-core items, CUDA-core items) "
+                                   f"replayed from a CUDA graph",
+                       "count": count, "damping": damping, "l2": "A + X = 363 MB > L2",
+                       "tensor_core_items": bool(args.batched_tc) or any(v == 2 for v in (table or {}).values())},
+            "status_ok_fraction": float(np.mean(stats == 0)), "gpu_launches": 2 * args.steps,
             "tflops": round(tflops, 2), "gbs": round(byts / (ms / 1e3) / 1e9, 1),
-            "roofline": {"kernel": "nn::batched_nn_kernel", "bound": "alu", "achieved": round(tflops, 2),
+            "roofline": {"kernel": "nn::batched_nn_kernel<false> (CUDA-core items)", "bound": "alu",
+                         "achieved": round(tflops, 2),
                          "peak": round(fma_peak, 1), "unit": "TFLOP/s", "frac": round(tflops / fma_peak, 4),
                          "traffic": None, "peak_source": f"FP32 FMA: {sms} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz",
                          "hbm_frac": round(byts / (ms / 1e3) / 1e9 / float(peaks.get('hbm_gbs', 6800.0)), 4)},
