@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--max-active", type=int, default=8)
-    ap.add_argument("--gemm-variant", type=int, default=0, choices=[0, 1, 2, 3], help="0 auto, 1 single-CTA tiles, 2 CTA pairs with multicast, 3 2-SM MMA")
+    ap.add_argument("--gemm-variant", type=int, default=0, choices=[0, 1, 2, 3, 4], help="0 auto, 1 single-CTA tiles, 2 CTA pairs with multicast, 3 2-SM MMA, 4 2-SM MMA with split last wave")
     ap.add_argument("--spmv-variant", type=int, default=0, choices=[0, 1], help="0 auto (bulk-copy ring), 1 staged loads")
     ap.add_argument("--batched-tc", action="store_true",
                     help="batched workload: tensor-core items for U in {16, 32, 48, 64}")
@@ -273,7 +273,7 @@ def run_dense(args, rank, world, local_rank):
                                                                                  "nn::tc::gemm_tc_2sm_kernel")
         # ncu DRAM bytes per launch (mean over one step) of the profiled default configuration
         traffic = None
-        if (args.gemm_variant in (0, 3) and n == 8192 and args.kappa == 1e2 and args.depth == 2
+        if (args.gemm_variant in (0, 4) and n == 8192 and args.kappa == 1e2 and args.depth == 2
                 and args.tol == 1e-6 and args.seed == 0):
             traffic = profile_traffic("gemm_tc_2sm_dense_n8192.md", ["gemm_tc.cu", "nn_dense.cu"])
         roofline = {"kernel": kernel, "bound": "tensor", "achieved": round(achieved, 2),
@@ -342,8 +342,9 @@ def run_dense(args, rank, world, local_rank):
                                f"depth {args.depth}, eps={args.tol:g}",
                    "n": n, "kappa": args.kappa, "depth": args.depth, "tol": args.tol, "dtype": args.dtype,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "gemm_tiling": {0: "auto (2-SM MMA, cta_group::2)", 1: "single-CTA tiles",
-                                   2: "CTA pairs with TMA multicast", 3: "2-SM MMA (cta_group::2)"}[args.gemm_variant],
+                   "gemm_tiling": {0: "auto (2-SM MMA, cta_group::2, split last wave)", 1: "single-CTA tiles",
+                                   2: "CTA pairs with TMA multicast", 3: "2-SM MMA (cta_group::2)",
+                                   4: "2-SM MMA, last wave split into 256x128 halves"}[args.gemm_variant],
                    "l2": "inputs larger than L2: A fp64 512 MiB, BF16 operands 128 MiB each per GEMM"},
         "status_ok": ok, "nests": last["nests"], "residual": last["residual"], "pieces": last["pieces"],
         "gemms_per_step": last["gemms"], "hw_tflops_per_step": round(last["hw_flops"] / 1e12, 3),

@@ -72,6 +72,11 @@ struct Params {
   int n_col;
   double* partial;
   int* err;
+  // 2-SM kernel: tiles [split_from, num_tiles) run as two 256 x 128 halves each (work units
+  // beyond split_from), which halves the time of a partly filled last wave; map_b_half loads
+  // 64-row halves of those B^T panels.
+  CUtensorMap map_b_half[kTcMaxSeg];
+  int split_from;
   // FP64-emulation epilogue (see TcGemmArgs)
   int emu;
   int emu_first, emu_last;
@@ -415,7 +420,20 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_pair_kernel(const __grid_c
 constexpr int P2_STAGES = 6;
 constexpr int P2_STAGE_BYTES = A_TILE + B_TILE / 2;  // 32 KB
 constexpr int P2_SMEM_BYTES = P2_STAGES * P2_STAGE_BYTES + CTRL_BYTES + 1024;
+constexpr uint32_t IDESC_P2_HALF =
+    (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t((BN / 2) >> 3) << 17) | (uint32_t((2 * BM) >> 4) << 24);
 static_assert((2 * P2_STAGES + 5) * 8 + 8 <= 192 && 192 + 4 * 8 <= CTRL_BYTES, "control block layout");
+
+// Work unit w of the 2-SM schedule: full tiles first, then the split tiles' halves.
+__device__ __forceinline__ void unit_tile(int w, int split_from, int& t, int& half) {
+  if (w < split_from) {
+    t = w;
+    half = -1;
+  } else {
+    t = split_from + ((w - split_from) >> 1);
+    half = (w - split_from) & 1;
+  }
+}
 static_assert(P2_SMEM_BYTES <= 227 * 1024, "shared memory");
 constexpr uint32_t IDESC_P2 =
     (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t((2 * BM) >> 4) << 24);
@@ -460,6 +478,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_2sm_kernel(const __grid_co
     for (int s = 0; s < p.nseg; ++s) {
       tma_prefetch_desc(&p.map_a[s]);
       tma_prefetch_desc(&p.map_b[s]);
+      if (p.split_from < p.tiles_n * (p.tiles_m / 2)) tma_prefetch_desc(&p.map_b_half[s]);
     }
   }
   if (warp == 1) tmem_alloc_pair(tmem_slot, TMEM_COLS);
@@ -469,6 +488,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_2sm_kernel(const __grid_co
   const uint32_t tmem_base = *tmem_slot;
 
   const int num_tiles = unit_rows * p.tiles_n;
+  const int num_units = p.split_from + 2 * (num_tiles - p.split_from);
   const int kblocks = p.np / BK;
   const int total_k = p.nseg * kblocks;
 
@@ -476,8 +496,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_2sm_kernel(const __grid_co
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      for (int t = unit; t < num_tiles && !*abort_flag; t += units) {
-        int tm2, tn;
+      for (int w = unit; w < num_units && !*abort_flag; w += units) {
+        int t, half, tm2, tn;
+        unit_tile(w, p.split_from, t, half);
         tile_coords(t, unit_rows, p.tiles_n, GROUP_M / 2, tm2, tn);
         for (int it = 0; it < total_k; ++it) {
           const int seg = it / kblocks;
@@ -485,10 +506,13 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_2sm_kernel(const __grid_co
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.err)) break;
           uint8_t* sa = tiles + stage * P2_STAGE_BYTES;
           uint8_t* sb = sa + A_TILE;
-          if (leader) mbar_arrive_expect_tx(&full[stage], 2 * P2_STAGE_BYTES);
+          if (leader) mbar_arrive_expect_tx(&full[stage], half < 0 ? 2 * P2_STAGE_BYTES : 2 * (A_TILE + B_TILE / 4));
           const uint32_t bar = cluster_map_shared(&full[stage], 0);
           tma_load_2d_pair(sa, &p.map_a[seg], kb * BK, tm2 * 2 * BM + rank * BM, bar);
-          tma_load_2d_pair(sb, &p.map_b[seg], kb * BK, tn * BN + rank * (BN / 2), bar);
+          if (half < 0)
+            tma_load_2d_pair(sb, &p.map_b[seg], kb * BK, tn * BN + rank * (BN / 2), bar);
+          else
+            tma_load_2d_pair(sb, &p.map_b_half[seg], kb * BK, tn * BN + half * (BN / 2) + rank * (BN / 4), bar);
           if (++stage == P2_STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -501,12 +525,13 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_2sm_kernel(const __grid_co
       int stage = 0;
       uint32_t phase = 0;
       int local = 0;
-      for (int t = unit; t < num_tiles && !*abort_flag; t += units, ++local) {
+      for (int w = unit; w < num_units && !*abort_flag; w += units, ++local) {
         const int acc = local & 1;
         const uint32_t acc_phase = (local >> 1) & 1;
         if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1u, abort_flag, p.err)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + uint32_t(acc * BN);
+        const uint32_t idesc = w < p.split_from ? IDESC_P2 : IDESC_P2_HALF;
         bool ok = true;
         for (int it = 0; it < total_k; ++it) {
           if (!mbar_wait(&full[stage], phase, abort_flag, p.err)) {
@@ -519,7 +544,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_2sm_kernel(const __grid_co
           const uint64_t bdesc = sw128_desc(sa + A_TILE);
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk)
-            tc_mma_bf16_pair(d_tmem, adesc + uint64_t(2 * kk), bdesc + uint64_t(2 * kk), IDESC_P2,
+            tc_mma_bf16_pair(d_tmem, adesc + uint64_t(2 * kk), bdesc + uint64_t(2 * kk), idesc,
                              (it > 0 || kk > 0) ? 1u : 0u);
           tc_commit_pair_multicast(&empty[stage], uint16_t(0x3));
           if (++stage == P2_STAGES) {
@@ -542,16 +567,19 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_2sm_kernel(const __grid_co
                                           cluster_map_shared(&acc_empty[1], 0)};
     double ss = 0.0;
     int local = 0;
-    for (int t = unit; t < num_tiles; t += units, ++local) {
+    for (int w = unit; w < num_units; w += units, ++local) {
       const int acc = local & 1;
       const uint32_t acc_phase = (local >> 1) & 1;
       if (!mbar_wait(&acc_full[acc], acc_phase, abort_flag, p.err)) break;
       tc_fence_after();
-      int tm2, tn;
+      int t, half, tm2, tn;
+      unit_tile(w, p.split_from, t, half);
       tile_coords(t, unit_rows, p.tiles_n, GROUP_M / 2, tm2, tn);
       const int gr = tm2 * 2 * BM + rank * BM + row_in_tile;
-      for (int c = 0; c < BN / 32; ++c) {
-        const int gc0 = tn * BN + c * 32;
+      const int col0 = tn * BN + (half < 0 ? 0 : half * (BN / 2));
+      const int chunks = half < 0 ? BN / 32 : BN / 64;
+      for (int c = 0; c < chunks; ++c) {
+        const int gc0 = col0 + c * 32;
         if (gc0 >= p.np) break;
         uint32_t raw[32];
         tmem_ld_32x32b_x32(tmem_base + uint32_t(acc * BN + c * 32) + (uint32_t(q * 32) << 16), raw);
@@ -586,7 +614,7 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 int g_sms = 0;
 int g_pair_clusters = 0;  // co-resident clusters of the multicast-pair kernel (0: unavailable)
 int g_2sm_clusters = 0;   // co-resident clusters of the 2-SM MMA kernel (0: unavailable)
-int g_variant = 0;        // 0 auto (3 where possible, else 1), 1 single-CTA tiles, 2 CTA pairs with multicast, 3 2-SM MMA
+int g_variant = 0;  // 0 auto (4 where possible, else 1), 1 single-CTA, 2 pairs + multicast, 3 2-SM MMA, 4 3 + split tail
 bool g_tc_ok = false;
 std::once_flag g_once;
 
@@ -666,7 +694,7 @@ bool tc_supported() {
   return g_tc_ok;
 }
 
-void gemm_tc_set_variant(int v) { g_variant = (v >= 0 && v <= 3) ? v : 0; }
+void gemm_tc_set_variant(int v) { g_variant = (v >= 0 && v <= 4) ? v : 0; }
 
 int gemm_tc_max_grid() {
   std::call_once(g_once, init_once);
@@ -722,14 +750,15 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
   p.emu_add = a.emu_add;
   p.emu_ld_add = a.emu_ld_add;
   p.emu_n = a.emu_n;
-  // Variant choice: the 2-SM MMA by default where the size allows it, else single-CTA tiles.
+  // Variant choice: the 2-SM MMA with a split last wave by default where the size allows it, else
+  // single-CTA tiles.
   const bool even = a.np % (2 * tc::BM) == 0;
   int variant = g_variant;
-  if (variant == 0) variant = (even && g_2sm_clusters > 0) ? 3 : 1;
-  if ((variant == 2 && !(even && g_pair_clusters > 0)) || (variant == 3 && !(even && g_2sm_clusters > 0)))
+  if (variant == 0) variant = (even && g_2sm_clusters > 0) ? 4 : 1;
+  if ((variant == 2 && !(even && g_pair_clusters > 0)) || (variant >= 3 && !(even && g_2sm_clusters > 0)))
     return NN_ERR_UNSUPPORTED;
   int grid = 0;
-  if (variant == 2 || variant == 3) {
+  if (variant >= 2) {
     // B^T maps load 128-row halves (one per CTA of the pair)
     for (int s = 0; s < a.nseg; ++s)
       if (!encode_bf16_2d(&p.map_b[s], a.b_seg[s], a.np, tc::BN / 2)) return NN_ERR_CUDA;
@@ -737,6 +766,14 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
     const int avail = variant == 2 ? g_pair_clusters : g_2sm_clusters;
     const int clusters = units < avail ? units : avail;
     grid = 2 * clusters;
+    // 2-SM kernel: a last wave at most half full runs its tiles as 256 x 128 halves
+    p.split_from = units;
+    const int tail = units % clusters;
+    if (variant == 4 && units > clusters && tail > 0 && 2 * tail <= clusters) {
+      p.split_from = units - tail;
+      for (int s = 0; s < a.nseg; ++s)
+        if (!encode_bf16_2d(&p.map_b_half[s], a.b_seg[s], a.np, tc::BN / 4)) return NN_ERR_CUDA;
+    }
     cudaLaunchAttribute attr[1];
     if (variant == 2) {
       cudaLaunchConfig_t cfg = cluster_config(grid, tc::SMEM_BYTES, st, attr);
