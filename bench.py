@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--cond", type=float, default=1e2, help="cond(A) of the normal-equations workload")
     ap.add_argument("--kappa", type=float, default=1e2)
     ap.add_argument("--depth", type=int, default=2)
-    ap.add_argument("--dtype", default="mixed_bf16", choices=["mixed_bf16", "f32", "f64", "f64_df", "f64_emu"])
+    ap.add_argument("--dtype", default="mixed_bf16", choices=["mixed_bf16", "f32", "f64", "f64_df", "f64_emu", "mixed_emu"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--damping", type=float, default=1.0 / 128.0)
@@ -246,7 +246,7 @@ def run_dense(args, rank, world, local_rank):
 
     peaks, peak_src = load_peaks()
     roofline = None
-    if tc_launches > 0 and tc_ms > 0 and args.dtype == "f64_emu":
+    if tc_launches > 0 and tc_ms > 0 and args.dtype in ("f64_emu", "mixed_emu"):
         # tensor-core work of the emulated products over the GEMM calls' time (slicing included)
         hw = sum(r["hw_flops"] for _, r in results)
         achieved = hw / (tc_ms / 1e3) / 1e12
@@ -336,7 +336,8 @@ def run_dense(args, rank, world, local_rank):
         "ms_per_step": round(ms_per_step, 3), "time_to_eps_ms": round(ms_per_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"mixed_bf16": "bf16 (tcgen05, fp32 accumulate; refine with split bf16)", "f32": "f32",
-                  "f64": "f64", "f64_emu": "f64 (emulated: exact bf16 slices on tcgen05)"}[args.dtype],
+                  "f64": "f64", "f64_emu": "f64 (emulated: exact bf16 slices on tcgen05)",
+                  "mixed_emu": "bf16 pieces, then f64 emulated with exact bf16 slices (tcgen05)"}[args.dtype],
         "data": "synthetic",
         "config": {"workload": f"dense SPD N={n}, kappa={args.kappa:g}, log-uniform spectrum, X0=2/(lmin+lmax) I, "
                                f"depth {args.depth}, eps={args.tol:g}",

@@ -57,13 +57,17 @@ typedef enum nn_dtype {
   NN_F64_DF = 3,     /* sparse chain only: FP64 data and results, arithmetic in double-float
                         (hi + lo FP32 pairs, 49-bit significand) on the FP32 pipes; values must
                         lie within the FP32 exponent range                                   */
-  NN_F64_EMU = 4     /* dense chain, nn_residual and nn_solve_normal: FP64 data and results,
+  NN_F64_EMU = 4,    /* dense chain, nn_residual and nn_solve_normal: FP64 data and results,
                         every product emulated on the BF16 tensor cores with exact slices
                         (error-free splitting after Ozaki et al.: per-row / per-column
                         power-of-two scales, signed base-2^beta digits with n 2^(2 beta) <= 2^24,
                         slice products summed exactly in FP32 and the groups in FP64).
                         Accurate to a few units of 2^-53 normwise. Workspace grows by two sets
                         of BF16 slices (about 2.8 GB at N = 8192)                            */
+  NN_MIXED_EMU = 5   /* dense chain: NN_MIXED_BF16 until the iterate nears the BF16 pieces' floor
+                        with tol below it, then NN_F64_EMU nests from that iterate (FP64 copy);
+                        history and status cover both stages, pieces[k] = 0 for the FP64
+                        nests. Reaches FP64-level residuals at a fraction of NN_F64_EMU's cost */
 } nn_dtype;
 
 /* ---- starting matrix X_0 = Theta (Section II-A, Eq. (normalization), Appendix 1) --------- */

@@ -118,11 +118,18 @@ size_t ws_bytes(int64_t n, int dtype) {
   } else {
     MixedWs w;
     carve_mixed(c, n, w);
+    if (dtype == NN_MIXED_EMU) {
+      Simt64Ws w64;
+      carve_f64(c, n, w64);
+      (void)c.take<char>(emu_workspace_bytes(n));
+    }
   }
   return align_up(c.used, 256);
 }
 
-bool valid_dtype(int d) { return d == NN_F64 || d == NN_F32 || d == NN_MIXED_BF16 || d == NN_F64_EMU; }
+bool valid_dtype(int d) {
+  return d == NN_F64 || d == NN_F32 || d == NN_MIXED_BF16 || d == NN_F64_EMU || d == NN_MIXED_EMU;
+}
 
 // Reads s (and the device error word) back to the host; one stream synchronisation.
 int fetch_scalar(cudaStream_t st, const Common& cm, double* s, int* dev_err) {
@@ -502,6 +509,11 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
     if (verdict < 0 && level == 4 && k >= 2 && o.tol > 0 && s > 0.9 * res->history[k - 1] &&
         res->history[k - 1] > 0.9 * res->history[k - 2] && s < 30.0 * level_floor(4, c))
       verdict = NN_ERR_NOT_CONVERGED;
+    // NN_MIXED_EMU: a tolerance below the BF16-piece floors is reached by emulated FP64 nests;
+    // hand the iterate over once the chain is within reach of its own floor.
+    if (verdict < 0 && o.dtype == NN_MIXED_EMU && o.tol > 0 && o.tol < 8.0 * level_floor(3, c) &&
+        s < 64.0 * level_floor(3, c))
+      verdict = NN_ERR_NOT_CONVERGED;
     if (verdict >= 0) {
       res->status = verdict;
       break;
@@ -645,6 +657,14 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     if (!tc_supported()) return NN_ERR_UNSUPPORTED;
     MixedWs w;
     carve_mixed(c, n, w);
+    Simt64Ws w64{};
+    void* ews = nullptr;
+    size_t eb = 0;
+    if (o.dtype == NN_MIXED_EMU) {
+      carve_f64(c, n, w64);
+      eb = emu_workspace_bytes(n);
+      ews = c.take<char>(eb);
+    }
     if (!c.ok) return NN_ERR_OOM_BUDGET;
     // BF16 pieces of A and X_0, with ||A||_F and ||X_0||_F (for the precision-level floors)
     // from the split kernel's per-block sums of squares
@@ -659,7 +679,39 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     res->launches += 4;
     NN_TRY(run_mixed(st, ni, w, o, cm, a_frob, x0src, res, &fin, ho));
     if (ho != nullptr && ho->pending) NN_CUDA_TRY(cudaStreamWaitEvent(st, ho->done, 0));
-    if (ho == nullptr || !ho->valid) NN_TRY(f32_to_f64(st, w.x32[fin], w.np, ni, X, ldx));
+    if (o.dtype == NN_MIXED_EMU && res->status == NN_ERR_NOT_CONVERGED && res->nests < o.max_nests) {
+      // Continue from the mixed chain's last iterate with emulated FP64 nests (NN converges from
+      // any X with rho(I - A X) < 1, Appendix 2): their first residual re-measures s_k exactly.
+      if (ho != nullptr) ho->valid = false;
+      NN_TRY(f32_to_f64(st, w.x32[fin], w.np, ni, w64.X[0], n));
+      nn_opts o2 = o;
+      o2.dtype = NN_F64_EMU;
+      o2.max_nests = o.max_nests - res->nests;
+      o2.depth = nest_depth(o, res->nests);
+      o2.depth_schedule = nullptr;
+      o2.schedule_len = 0;
+      nn_result r2;
+      init_result(&r2);
+      int fin2 = 0;
+      NN_TRY(run_simt<double>(st, ni, A, lda, w64.X, w64.R, w64.T, o2, cm, &r2, &fin2,
+                              EmuGemm{st, ni, ews, eb, cm.err, &res->hw_flops}));
+      const int k0 = res->nests;
+      for (int k = 0; k <= r2.nests && k0 + k < NN_MAX_HISTORY; ++k) {
+        res->history[k0 + k] = r2.history[k];
+        res->pieces[k0 + k] = 0;
+      }
+      res->nests = k0 + r2.nests;
+      res->residual = r2.residual;
+      res->status = r2.status;
+      res->gemms += r2.gemms;
+      res->launches += r2.launches + 1;
+      res->tc_launches += r2.tc_launches;
+      res->tc_ms += r2.tc_ms;
+      res->tc_flops += r2.tc_flops;
+      NN_TRY(copy_f64(st, w64.X[fin2], n, ni, X, ldx));
+    } else if (ho == nullptr || !ho->valid) {
+      NN_TRY(f32_to_f64(st, w.x32[fin], w.np, ni, X, ldx));
+    }
     res->launches += 3;
   }
   // Algorithmic work of the method: (L+1) GEMMs per nest plus the final residual.

@@ -101,3 +101,43 @@ def test_emulated_normal_equations(nn):
     true = np.linalg.solve(a, b)
     err = np.linalg.norm(X.cpu().numpy() - true) / np.linalg.norm(true)
     assert err <= 64 * cond ** 2 * U64 + n * res["residual"]
+
+
+@pytest.mark.parametrize("n,kappa,tol", [(1024, 1e4, 1e-10), (1024, 1e2, 1e-12), (300, 1e3, 1e-11)])
+def test_mixed_then_emulated_reaches_fp64_tolerances(nn, n, kappa, tol):
+    # NN_MIXED_EMU: BF16-piece nests until the iterate nears their floor, then emulated FP64
+    # nests from it; the returned X meets tolerances the mixed chain alone cannot reach
+    import torch
+
+    a, q, lam = synth.spd_spectrum(n, kappa, seed=int(kappa) + n)
+    x0 = dense.precond_scalar(n, 2.0 / (lam[0] + lam[-1]))
+    A, X0 = _dev(a), _dev(x0)
+    X = torch.empty_like(A)
+    ws = nn.workspace(n, "mixed_emu")
+    st, res = nn.nn_invert(A, X0, nn.make_opts(2, tol, 40, "mixed_emu"), X, ws)
+    torch.cuda.synchronize()
+    assert st == nn.NN_OK and res["residual"] < tol
+    assert res["pieces"][0] >= 1 and res["pieces"][res["nests"]] == 0  # both stages ran
+    r = np.eye(n) - a @ X.cpu().numpy()
+    assert np.linalg.norm(r) / n < 2 * tol
+    # the history decreases through the handoff and matches the nest count bookkeeping
+    assert len(res["history"]) == res["nests"] + 1
+
+
+def test_mixed_emu_equals_mixed_when_tol_is_reachable(nn):
+    # a tolerance the BF16 pieces reach: no handoff, bit-for-bit the mixed chain
+    import torch
+
+    n = 512
+    a, q, lam = synth.spd_spectrum(n, 1e2, seed=77)
+    x0 = dense.precond_scalar(n, 2.0 / (lam[0] + lam[-1]))
+    out = {}
+    for dt in ("mixed_bf16", "mixed_emu"):
+        A, X0 = _dev(a), _dev(x0)
+        X = torch.empty_like(A)
+        st, res = nn.nn_invert(A, X0, nn.make_opts(2, 1e-4, 40, dt), X, nn.workspace(n, dt))
+        torch.cuda.synchronize()
+        out[dt] = (st, res, X.cpu().numpy())
+    assert out["mixed_bf16"][0] == out["mixed_emu"][0] == nn.NN_OK
+    assert out["mixed_bf16"][1]["nests"] == out["mixed_emu"][1]["nests"]
+    assert np.array_equal(out["mixed_bf16"][2], out["mixed_emu"][2])
