@@ -17,9 +17,66 @@ constexpr int ROWS = 8;  // 32 x 8 threads per 32 x 32 tile
 // v = hi + lo with hi = fp32(v), lo = fp32(v - hi); p0 = bf16(hi), p1 = bf16((hi - p0) + lo),
 // p2 = bf16(((hi - p0) + lo) - p1). hi - p0 and t - p1 are exact in FP32; the only rounding
 // beyond the pieces themselves is (hi - p0) + lo, at most 2^-24 |hi - p0| <= 2^-33 |v|.
+// hi = fp32(v) and lo = fp32(v - hi), both rounded to nearest even, from the FP64 bit pattern
+// with integer operations only (GB300's FP64 pipe would otherwise bound this kernel). Returns
+// false, leaving the work to FP64 arithmetic, for zeros, |v| outside [2^-90, 2^101) and a
+// subnormal lo; the results are identical to the FP64 conversions.
+__device__ __forceinline__ bool split_hi_lo_int(double v, float& hi, float& lo) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
+  const int e = int((bits >> 52) & 0x7FFull) - 1023;
+  if (e < -90 || e > 100) return false;
+  const unsigned s = unsigned(bits >> 63);
+  const long long M = static_cast<long long>((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+  // hi: M rounded to 24 significant bits
+  long long q = M >> 29;
+  const long long rem = M & ((1ll << 29) - 1);
+  if (rem > (1ll << 28) || (rem == (1ll << 28) && (q & 1))) ++q;
+  const long long r = M - (q << 29);  // v - hi in units of 2^(e-52), |r| <= 2^28
+  int eh = e;
+  long long qh = q;
+  if (q == (1ll << 24)) {
+    qh = 1ll << 23;
+    eh = e + 1;
+  }
+  hi = __uint_as_float((s << 31) | (unsigned(eh + 127) << 23) | unsigned(qh & 0x7FFFFF));
+  if (r == 0) {
+    lo = 0.0f;
+    return true;
+  }
+  // lo: |r| rounded to 24 significant bits, sign of v flipped when hi rounded up
+  const unsigned sl = s ^ (r < 0 ? 1u : 0u);
+  const unsigned long long x = static_cast<unsigned long long>(r < 0 ? -r : r);
+  const int p = 63 - __clzll(static_cast<long long>(x));
+  long long m24;
+  int pe = p;
+  if (p > 23) {
+    const int sh = p - 23;
+    m24 = static_cast<long long>(x >> sh);
+    const unsigned long long rb = x & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rb > half || (rb == half && (m24 & 1))) ++m24;
+    if (m24 == (1ll << 24)) {
+      m24 = 1ll << 23;
+      ++pe;
+    }
+  } else {
+    m24 = static_cast<long long>(x << (23 - p));
+  }
+  const int ef = pe + e - 52 + 127;
+  if (ef < 1) return false;
+  lo = __uint_as_float((sl << 31) | (unsigned(ef) << 23) | unsigned(m24 & 0x7FFFFF));
+  return true;
+}
+
 __device__ __forceinline__ float pieces3(double v, __nv_bfloat16 (&p)[3]) {
-  const float hi = static_cast<float>(v);
-  const float lo = static_cast<float>(v - static_cast<double>(hi));
+  float hi, lo;
+  const unsigned long long vb = static_cast<unsigned long long>(__double_as_longlong(v));
+  if ((vb << 1) == 0) {
+    hi = __uint_as_float(unsigned(vb >> 32) & 0x80000000u);  // +-0
+    lo = 0.0f;
+  } else if (!split_hi_lo_int(v, hi, lo)) {
+    hi = static_cast<float>(v);
+    lo = static_cast<float>(v - static_cast<double>(hi));
+  }
   p[0] = __float2bfloat16_rn(hi);
   const float t = (hi - __bfloat162float(p[0])) + lo;
   p[1] = __float2bfloat16_rn(t);
@@ -31,23 +88,50 @@ struct PiecePtrs {
   __nv_bfloat16* p[3];
 };
 
+// Tile of 32 rows x 128 columns per block of 32 x 8 threads; each thread handles four
+// consecutive columns (32-byte loads, 8-byte piece stores, 16-byte FP32 stores), and the
+// transposed pieces go out through shared memory as 4-byte pairs along the output rows.
+constexpr int SPLIT_R = 32, SPLIT_C = 128;
+
 __global__ void split_kernel(const double* __restrict__ src, int64_t lds, int n, int np, float* __restrict__ f32,
                              PiecePtrs row, int n_row, PiecePtrs col, int n_col, double* __restrict__ sumsq) {
-  __shared__ __nv_bfloat16 tile[3][TILE][TILE + 2];
+  __shared__ __nv_bfloat16 tile[3][SPLIT_R][SPLIT_C + 2];  // odd word pitch: conflict-free columns
   __shared__ float red[ROWS];
-  const int i0 = blockIdx.y * TILE, j0 = blockIdx.x * TILE;
+  const int i0 = blockIdx.y * SPLIT_R, j0 = blockIdx.x * SPLIT_C;
   const int tx = threadIdx.x, ty = threadIdx.y;
+  const int jj = j0 + 4 * tx;
   float ss = 0.f;
-  for (int r = ty; r < TILE; r += ROWS) {
-    const int i = i0 + r, j = j0 + tx;
-    double v = (i < n && j < n) ? src[int64_t(i) * lds + j] : 0.0;
-    const int64_t off = int64_t(i) * np + j;
-    __nv_bfloat16 pc[3];
-    const float hi = pieces3(v, pc);
-    if (f32) f32[off] = hi;
-    ss = fmaf(hi, hi, ss);
-    for (int q = 0; q < n_row; ++q) row.p[q][off] = pc[q];
-    for (int q = 0; q < n_col; ++q) tile[q][r][tx] = pc[q];
+  for (int r = ty; r < SPLIT_R; r += ROWS) {
+    const int i = i0 + r;
+    double v[4];
+    if (i < n && jj + 3 < n && ((lds & 1) | (reinterpret_cast<uintptr_t>(src) & 15)) == 0) {
+      const double2* p2 = reinterpret_cast<const double2*>(src + int64_t(i) * lds + jj);
+      const double2 a = p2[0], b = p2[1];
+      v[0] = a.x;
+      v[1] = a.y;
+      v[2] = b.x;
+      v[3] = b.y;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = (i < n && jj + e < n) ? src[int64_t(i) * lds + jj + e] : 0.0;
+    }
+    __nv_bfloat16 pc[4][3];
+    float hi[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      hi[e] = pieces3(v[e], pc[e]);
+      ss = fmaf(hi[e], hi[e], ss);
+    }
+    const int64_t off = int64_t(i) * np + jj;
+    if (f32) *reinterpret_cast<float4*>(f32 + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+    for (int q = 0; q < n_row; ++q) {
+      const uint32_t lo2 = uint32_t(__bfloat16_as_ushort(pc[0][q])) | (uint32_t(__bfloat16_as_ushort(pc[1][q])) << 16);
+      const uint32_t hi2 = uint32_t(__bfloat16_as_ushort(pc[2][q])) | (uint32_t(__bfloat16_as_ushort(pc[3][q])) << 16);
+      *reinterpret_cast<uint2*>(row.p[q] + off) = make_uint2(lo2, hi2);
+    }
+    for (int q = 0; q < n_col; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) tile[q][r][4 * tx + e] = pc[e][q];
   }
   if (sumsq != nullptr) {
     // per-block sum of squares (FP32 within the block, fixed order), for ||src||_F
@@ -63,10 +147,17 @@ __global__ void split_kernel(const double* __restrict__ src, int64_t lds, int n,
   }
   if (n_col > 0) {
     __syncthreads();
-    for (int r = ty; r < TILE; r += ROWS) {
-      // transposed: output row (j0 + r), column (i0 + tx)
-      const int64_t off = int64_t(j0 + r) * np + (i0 + tx);
-      for (int q = 0; q < n_col; ++q) col.p[q][off] = tile[q][tx][r];
+    // transposed: output row j0 + c (c < 128) holds input column j0 + c, entries i0 .. i0 + 31;
+    // thread (tx, ty) writes the pair of entries 2 (tx % 16), +1 of output rows c = 2 ty' + tx / 16
+    const int t = ty * 32 + tx;
+    for (int c = t / 16; c < SPLIT_C; c += (ROWS * 32) / 16) {
+      const int pr = 2 * (t % 16);
+      const int64_t off = int64_t(j0 + c) * np + i0 + pr;
+      for (int q = 0; q < n_col; ++q) {
+        const uint32_t pair = uint32_t(__bfloat16_as_ushort(tile[q][pr][c])) |
+                              (uint32_t(__bfloat16_as_ushort(tile[q][pr + 1][c])) << 16);
+        *reinterpret_cast<uint32_t*>(col.p[q] + off) = pair;
+      }
     }
   }
 }
@@ -231,17 +322,17 @@ __global__ void fill_diag_kernel(const double* __restrict__ A, int64_t lda, int 
 int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
                  __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
                  double* sumsq_partial) {
-  if (np % TILE != 0 || n > np || n_row < 0 || n_row > 3 || n_col < 0 || n_col > 3) return NN_ERR_ARG;
+  if (np % SPLIT_C != 0 || n > np || n_row < 0 || n_row > 3 || n_col < 0 || n_col > 3) return NN_ERR_ARG;
   PiecePtrs r{}, c{};
   for (int q = 0; q < n_row; ++q) r.p[q] = row_pieces[q];
   for (int q = 0; q < n_col; ++q) c.p[q] = col_pieces[q];
-  dim3 grid(np / TILE, np / TILE), block(TILE, ROWS);
+  dim3 grid(np / SPLIT_C, np / SPLIT_R), block(32, ROWS);
   split_kernel<<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial);
   NN_CUDA_TRY(cudaGetLastError());
   return NN_OK;
 }
 
-int split_blocks(int np) { return (np / TILE) * (np / TILE); }
+int split_blocks(int np) { return (np / SPLIT_C) * (np / SPLIT_R); }
 
 template <typename S, typename D>
 static int convert(cudaStream_t st, const S* src, int64_t lds, int n, D* dst, int64_t ldd) {
