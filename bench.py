@@ -647,13 +647,13 @@ def run_batched(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "c64 (fp32 FMA)", "data": "synthetic",
             "config": {"workload": f"{count} Gram matrices A = H^H H + 0.1 I, H 128 x U CN(0,1), U uniform over "
                                    f"{{8,16,24,32,48,64}}, X0 = diag(A)^-1/(1 + {damping:g} U), depth {depth}, "
-                                   f"{nests} nests, two persistent kernels (tensor-core items, CUDA-core items) "
-                                   f"replayed from a CUDA graph",
+                                   f"{nests} nests, one persistent kernel per tile class, chained by programmatic "
+                                   f"dependent launch, replayed from a CUDA graph",
                        "count": count, "damping": damping, "l2": "A + X = 363 MB > L2",
                        "tensor_core_items": bool(args.batched_tc) or any(v == 2 for v in (table or {}).values())},
-            "status_ok_fraction": float(np.mean(stats == 0)), "gpu_launches": 2 * args.steps,
+            "status_ok_fraction": float(np.mean(stats == 0)), "gpu_launches": abi.NN_BATCHED_KERNELS * args.steps,
             "tflops": round(tflops, 2), "gbs": round(byts / (ms / 1e3) / 1e9, 1),
-            "roofline": {"kernel": "nn::batched_nn_kernel<false> (CUDA-core items)", "bound": "alu",
+            "roofline": {"kernel": "nn::batched_simt_kernel<TG, T, U> (all classes, one batch)", "bound": "alu",
                          "achieved": round(tflops, 2),
                          "peak": round(fma_peak, 1), "unit": "TFLOP/s", "frac": round(tflops / fma_peak, 4),
                          "traffic": None, "peak_source": f"FP32 FMA: {sms} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz",

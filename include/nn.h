@@ -258,15 +258,21 @@ int nn_solve_normal(const void* A, int64_t n, int64_t lda, int is_complex, const
  * product is one tcgen05 MMA on the real embedding [[Pr, -Pi], [Pi, Pr]] [Qr; Qi] with three
  * BF16 pieces per operand, FP32-level accuracy); plan_host holds nn_batched_plan_size(count)
  * int32. The caller copies the plan to the device and may reuse it for every launch with the
- * same size list.
+ * same size list. Layout: [n_items, count, n_tc, class_first[18], order[count],
+ * items[n_items][4]]; order = matrix indices by size, largest first; item = (U, first position
+ * in order, matrices, cfg); items are grouped by tile class (class 0 = tensor cores, 1..16 =
+ * CUDA-core (threads per matrix, tile, exact U) classes), class c spanning items
+ * [class_first[c], class_first[c + 1]).
  *
  * nn_invert_batched_c64: A and X device complex64 (interleaved re, im) packed back to back,
  * matrix b row-major at element offset offsets[b] (device int64) with size sizes[b] (device
  * int32); plan = the device copy of the plan. residual[b] (device float) = s of the returned
  * X_b; status[b] (device int32) = NN_OK, NN_ERR_DIVERGED, or NN_ERR_TIMEOUT (a tensor-core
- * item whose bounded wait ran out). The call only enqueues work on `stream` (a memset and two
- * kernels, tensor-core items then CUDA-core items; no synchronisation, no allocation), so it
- * can be captured in a CUDA graph. Needs nn_batched_workspace_bytes(count) of workspace. */
+ * item whose bounded wait ran out). The call only enqueues work on `stream` (a memset and
+ * NN_BATCHED_KERNELS kernels, one per tile class, chained by programmatic dependent launch;
+ * no synchronisation, no allocation), so it can be captured in a CUDA graph. Needs
+ * nn_batched_workspace_bytes(count) of workspace. */
+#define NN_BATCHED_KERNELS 17
 int64_t nn_batched_plan_size(int64_t count);
 int nn_batched_plan(const int32_t* sizes_host, int64_t count, const int32_t* cfg_by_u, int32_t* plan_host);
 size_t nn_batched_workspace_bytes(int64_t count);

@@ -11,12 +11,16 @@
 // path does.
 //
 // Scheduling: the host plan (nn_batched_plan) sorts the matrices by size, largest first,
-// and cuts them into work items of G equal-size matrices; the grid is one CTA (256 threads)
-// per SM, and each CTA pulls items from a global counter. Inside a CTA, G thread groups run
+// and cuts them into work items of G equal-size matrices. Inside a CTA, G thread groups run
 // G matrices in lock-step (same U, same barriers). Two tile configurations exist per size:
 //   cfg 0: 8 x 8 threads per matrix, each computing a ceil(U/8)^2 tile of every product;
 //   cfg 1: 16 x 16 threads per matrix, tile ceil(U/16)^2, one matrix per CTA.
-// The plan takes a per-size configuration table, which the autotuner fills.
+// The plan takes a per-size configuration table, which the autotuner fills. Items fall into
+// tile classes (tensor cores; or CUDA cores with a given (threads per matrix, tile, exact U)),
+// and each class has its own persistent kernel, compiled alone so that the CUDA-core ones fit
+// 128 registers and run two 256-thread CTAs per SM. The classes' kernels are chained with
+// programmatic dependent launch: the next class's CTAs take the SM slots that the previous
+// class frees at its tail. Each kernel pulls the items of its class from its own counter.
 #include <math.h>
 #include <string.h>
 
@@ -31,23 +35,35 @@ namespace {
 
 constexpr int BT_THREADS = 256;
 constexpr int BT_MAX_U = 64;
-constexpr int BT_BUFS = 5;                  // A, X, R, T, W
-constexpr int BT_SMEM = 200 * 1024;         // dynamic shared memory per CTA
-constexpr int PLAN_HDR = 3;                 // [n_items, count, n_tc]
+constexpr int BT_SMEM = 200 * 1024;         // dynamic shared memory of a tensor-core CTA
+// CUDA-core items: two CTAs per SM at depth <= 2 (three buffers per matrix), one at depth >= 3
+// (four buffers, 4/3 of the same shared memory), so a plan sized for the first fits both.
+constexpr int BT_SMEM_SIMT = 112 * 1024;
+constexpr int BT_SMEM_SIMT_DEEP = BT_SMEM_SIMT / 3 * 4;
+// Tile classes: 0 = tensor-core items; 1..16 = CUDA-core items, ordered by cost: 16x16 threads
+// then 8x8, tile 4 down to 1, exact U (= tile * threads per side) before other sizes.
+constexpr int BT_NCLS = NN_BATCHED_KERNELS;
+constexpr int PLAN_HDR = 3 + BT_NCLS + 1;   // [n_items, count, n_tc, class_first[BT_NCLS + 1]]
+constexpr int BT_QUEUE_ERR = 32;            // workspace: int counters [0, BT_NCLS), error word here
+
+static_assert(BT_NCLS <= BT_QUEUE_ERR && (BT_QUEUE_ERR + 1) * 4 <= 256, "counters fit the workspace");
+
+__host__ __device__ constexpr int bt_class(int cfg, int U) {
+  return cfg == 2 ? 0
+                  : 1 + (cfg == 0 ? 8 : 0) + (4 - (U + (cfg == 0 ? 7 : 15)) / (cfg == 0 ? 8 : 16)) * 2 +
+                        (U % (cfg == 0 ? 8 : 16) == 0 ? 0 : 1);
+}
 
 enum : int { BM_RESID = 0, BM_ADD = 1 };
 
-// out = (mode RESID) I - P Q  or  (mode ADD) D + P Q, for a U x U complex group tile.
-// Thread (ti, tj) of the TG x TG group owns rows ti + a TG and columns tj + b TG.
-// UC > 0 fixes U = UC = T * TG at compile time (no bounds tests, static addressing, unrolled
-// k loop); UC = 0 handles any U <= T * TG.
+// acc = P Q for this thread's part of a U x U complex group tile: thread (ti, tj) of the
+// TG x TG group owns rows ti + a TG and columns tj + b TG. UC > 0 fixes U = UC = T * TG at
+// compile time (no bounds tests, static addressing); UC = 0 handles any U <= T * TG.
 template <int TG, int T, int UC>
-__device__ __forceinline__ float group_gemm(int U_rt, int ti, int tj, const float2* __restrict__ P,
-                                            const float2* __restrict__ Q, float2* __restrict__ out,
-                                            const float2* __restrict__ D, int mode) {
+__device__ __forceinline__ void group_acc(int U_rt, int ti, int tj, const float2* P, const float2* Q,
+                                          float2 (&acc)[T][T]) {
   const int U = UC > 0 ? UC : U_rt;
   constexpr bool exact = UC > 0 && UC == T * TG;
-  float2 acc[T][T];
 #pragma unroll
   for (int a = 0; a < T; ++a)
 #pragma unroll
@@ -55,7 +71,7 @@ __device__ __forceinline__ float group_gemm(int U_rt, int ti, int tj, const floa
   if (exact && (UC % 2) == 0) {
     // P[i, k] and P[i, k + 1] arrive in one 16-byte load (two k steps per P load), which cuts
     // the shared-memory wavefronts of the P operand in half; same FMA order as below.
-#pragma unroll 4
+#pragma unroll 2
     for (int k = 0; k < UC; k += 2) {
       float4 pa2[T];
 #pragma unroll
@@ -86,7 +102,7 @@ __device__ __forceinline__ float group_gemm(int U_rt, int ti, int tj, const floa
         }
     }
   } else {
-#pragma unroll(UC > 0 ? 8 : 1)
+#pragma unroll(UC > 0 ? 2 : 1)
   for (int k = 0; k < U; ++k) {
     float2 pa[T], qb[T];
 #pragma unroll
@@ -110,6 +126,16 @@ __device__ __forceinline__ float group_gemm(int U_rt, int ti, int tj, const floa
       }
   }
   }
+}
+
+// out = (mode RESID) I - acc  or  (mode ADD) D + acc on this thread's elements; returns the
+// thread's sum of |out|^2 (residual mode). out may be D or an operand of the product as long as
+// every thread of the CTA has finished the product (a barrier between group_acc and this).
+template <int TG, int T, int UC>
+__device__ __forceinline__ float group_store(int U_rt, int ti, int tj, const float2 (&acc)[T][T], float2* out,
+                                             const float2* D, int mode) {
+  const int U = UC > 0 ? UC : U_rt;
+  constexpr bool exact = UC > 0 && UC == T * TG;
   float ss = 0.f;
 #pragma unroll
   for (int a = 0; a < T; ++a) {
@@ -163,6 +189,22 @@ __device__ __forceinline__ void group_sum(float v, int g, int lt, int nthr, floa
   __syncthreads();
 }
 
+// One product of the nest: acc = P Q, an optional CTA barrier (when out aliases P, Q or D), then
+// out = mode(acc). Every thread of the CTA calls it (frozen groups skip the arithmetic).
+template <int TG, int T, int UC>
+__device__ __forceinline__ float group_product(int U, int ti, int tj, const float2* P, const float2* Q,
+                                               float2* out, const float2* D, int mode, bool barrier, bool frozen) {
+  float2 acc[T][T];
+  if (!frozen) group_acc<TG, T, UC>(U, ti, tj, P, Q, acc);
+  if (barrier) __syncthreads();
+  return frozen ? 0.f : group_store<TG, T, UC>(U, ti, tj, acc, out, D, mode);
+}
+
+// Buffers per matrix: A, X, R, and T for depth >= 3. Products whose output overwrites one of
+// their own operands (T in place of R at depth 2, T <- R + R T, X <- X + X T) accumulate in
+// registers, wait at a CTA barrier, then store.
+__host__ __device__ constexpr int bt_buffers(int depth) { return depth >= 3 ? 4 : 3; }
+
 template <int TG, int T, int UC>
 __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, float2* smem, float* red_warp,
                              float* red_grp) {
@@ -174,12 +216,11 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
   const bool active = g < groups && g < cnt;
   const int uu = U * U;
   const int b = active ? p.plan[PLAN_HDR + start + g] : -1;
-  float2* base = smem + size_t(g < groups ? g : 0) * BT_BUFS * uu;
+  float2* base = smem + size_t(g < groups ? g : 0) * bt_buffers(p.depth) * uu;
   float2* Ab = base;
   float2* Xb = base + uu;
   float2* Rb = base + 2 * uu;
-  float2* Tb = base + 3 * uu;
-  float2* Wb = base + 4 * uu;
+  float2* Tb = p.depth >= 3 ? base + 3 * uu : Rb;
   const int64_t off = active ? p.offsets[b] : 0;
 
   if (active) {
@@ -205,9 +246,8 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
   float s_prev = 0.f, s_last = 0.f;
   int st = NN_OK;
   for (int k = 0; k <= p.nests; ++k) {
-    float ss = 0.f;
-    if (!frozen) ss = group_gemm<TG, T, UC>(U, ti, tj, Ab, Xb, Rb, nullptr, BM_RESID);
-    group_sum(ss, g < groups ? g : 0, lt, NTHR, red_warp, red_grp);
+    const float ss = group_product<TG, T, UC>(U, ti, tj, Ab, Xb, Rb, nullptr, BM_RESID, false, frozen);
+    group_sum(ss, g < groups ? g : 0, lt, NTHR, red_warp, red_grp);  // includes CTA barriers
     if (!frozen) {
       const float s = sqrtf(red_grp[g]) / float(U);
       s_last = s;
@@ -218,26 +258,16 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
       s_prev = s;
     }
     if (k == p.nests) break;
-    // Horner: T_1 = R, T_{j+1} = R + R T_j; then X_{k+1} = X_k + X_k T.
-    float2* t_cur = Rb;
+    // Horner: T_1 = R, T_{j+1} = R + R T_j (depth 2: T_2 replaces R in place); then
+    // X_{k+1} = X_k + X_k T in place.
+    const float2* t_cur = Rb;
     for (int j = 1; j < p.depth; ++j) {
-      float2* dst = (t_cur == Tb) ? Wb : Tb;
-      if (!frozen) group_gemm<TG, T, UC>(U, ti, tj, Rb, t_cur, dst, Rb, BM_ADD);
+      group_product<TG, T, UC>(U, ti, tj, Rb, t_cur, Tb, Rb, BM_ADD, true, frozen);
       __syncthreads();
-      t_cur = dst;
+      t_cur = Tb;
     }
-    float2* xdst = (t_cur == Wb) ? Tb : Wb;
-    if (!frozen) group_gemm<TG, T, UC>(U, ti, tj, Xb, t_cur, xdst, Xb, BM_ADD);
+    group_product<TG, T, UC>(U, ti, tj, Xb, t_cur, Xb, Xb, BM_ADD, true, frozen);
     __syncthreads();
-    if (!frozen) {
-      // the old X buffer becomes free: keep five distinct buffers for the next nest
-      float2* tmp = Xb;
-      Xb = xdst;
-      if (xdst == Wb)
-        Wb = tmp;
-      else
-        Tb = tmp;
-    }
   }
   if (active) {
     for (int e = lt; e < uu; e += NTHR) p.X[off + e] = Xb[e];
@@ -247,40 +277,6 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
     }
   }
   __syncthreads();
-}
-
-template <int TG>
-__device__ void dispatch_tile(const BatchedParams& p, int U, int start, int cnt, float2* smem, float* rw, float* rg) {
-  // sizes with a compile-time path: the massive-MIMO user counts
-  if (TG == 8) {
-    switch (U) {
-      case 8: process_item<TG, 1, 8>(p, U, start, cnt, smem, rw, rg); return;
-      case 16: process_item<TG, 2, 16>(p, U, start, cnt, smem, rw, rg); return;
-      case 24: process_item<TG, 3, 24>(p, U, start, cnt, smem, rw, rg); return;
-      case 32: process_item<TG, 4, 32>(p, U, start, cnt, smem, rw, rg); return;
-      default: break;
-    }
-  } else {
-    switch (U) {
-      case 16: process_item<TG, 1, 16>(p, U, start, cnt, smem, rw, rg); return;
-      case 32: process_item<TG, 2, 32>(p, U, start, cnt, smem, rw, rg); return;
-      case 48: process_item<TG, 3, 48>(p, U, start, cnt, smem, rw, rg); return;
-      case 64: process_item<TG, 4, 64>(p, U, start, cnt, smem, rw, rg); return;
-      default: break;
-    }
-  }
-  const int t = (U + TG - 1) / TG;
-  switch (t) {
-    case 1: process_item<TG, 1, 0>(p, U, start, cnt, smem, rw, rg); break;
-    case 2: process_item<TG, 2, 0>(p, U, start, cnt, smem, rw, rg); break;
-    case 3: process_item<TG, 3, 0>(p, U, start, cnt, smem, rw, rg); break;
-    case 4: process_item<TG, 4, 0>(p, U, start, cnt, smem, rw, rg); break;
-    case 5: if (TG == 8) process_item<TG, 5, 0>(p, U, start, cnt, smem, rw, rg); break;
-    case 6: if (TG == 8) process_item<TG, 6, 0>(p, U, start, cnt, smem, rw, rg); break;
-    case 7: if (TG == 8) process_item<TG, 7, 0>(p, U, start, cnt, smem, rw, rg); break;
-    case 8: if (TG == 8) process_item<TG, 8, 0>(p, U, start, cnt, smem, rw, rg); break;
-    default: break;
-  }
 }
 
 // ---- tensor-core path (plan configuration 2; U in {16, 32, 48, 64}) ------------------------
@@ -590,25 +586,26 @@ __device__ void dispatch_tc(const BatchedParams& p, int U, int start, uint8_t* o
   }
 }
 
-// TC = true: the plan's tensor-core items [0, n_tc); TC = false: the CUDA-core items
-// [n_tc, n_items). Each kernel pulls items from its own counter.
-template <bool TC>
-__global__ void __launch_bounds__(BT_THREADS, 1) batched_nn_kernel(const BatchedParams p) {
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// Waits for the previous kernel of the chain to complete, so that each kernel's completion
+// implies its predecessors' (stream order for whatever follows the last one).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// The tensor-core items (class 0): one CTA per SM, 512 TMEM columns.
+__global__ void __launch_bounds__(BT_THREADS, 1) batched_tc_kernel(const BatchedParams p) {
   extern __shared__ float2 smem[];
   __shared__ float red_warp[BT_THREADS / 32];
-  __shared__ float red_grp[BT_THREADS / 32];
   __shared__ int item;
-  const int n_items = p.plan[0];
+  __shared__ __align__(8) uint64_t tc_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_word;
+  pdl_launch_dependents();
   const int count = p.plan[1];
-  const int n_tc = p.plan[2];
+  const int first = p.plan[3], last = p.plan[4];
   const int32_t* items = p.plan + PLAN_HDR + count;
-  const int first = TC ? 0 : n_tc, last = TC ? n_tc : n_items;
-  if (TC) {
-    // operand pieces at a 1024-aligned offset of the dynamic shared memory, 512 TMEM columns
-    // (one CTA per SM), one mbarrier for MMA completion
-    __shared__ __align__(8) uint64_t tc_bar;
-    __shared__ uint32_t tmem_slot;
-    __shared__ int abort_word;
+  if (first < last) {
+    // operand pieces at a 1024-aligned offset of the dynamic shared memory, one mbarrier for
+    // MMA completion
     uint8_t* ops = reinterpret_cast<uint8_t*>(smem);
     ops += (1024u - (smem_u32(ops) & 1023u)) & 1023u;
     if (threadIdx.x == 0) {
@@ -634,24 +631,45 @@ __global__ void __launch_bounds__(BT_THREADS, 1) batched_nn_kernel(const Batched
     __syncthreads();
     tc_fence_after();
     if (threadIdx.x < 32) tmem_dealloc(tmem, btc::TMEM_COLS);
-  } else {
+  }
+  pdl_wait();
+}
+
+// The CUDA-core items of one class (TG x TG threads per matrix, T x T tile, UC = exact U or
+// 0): two CTAs per SM at depth <= 2.
+template <int TG, int T, int UC>
+__global__ void __launch_bounds__(BT_THREADS, 2) batched_simt_kernel(const BatchedParams p, int cls) {
+  extern __shared__ float2 smem[];
+  __shared__ float red_warp[BT_THREADS / 32];
+  __shared__ float red_grp[BT_THREADS / 32];
+  __shared__ int item;
+  pdl_launch_dependents();
+  const int count = p.plan[1];
+  const int first = p.plan[3 + cls], last = p.plan[3 + cls + 1];
+  const int32_t* items = p.plan + PLAN_HDR + count;
+  if (first < last) {
     while (true) {
-      if (threadIdx.x == 0) item = first + atomicAdd(p.queue + 1, 1);
+      if (threadIdx.x == 0) item = first + atomicAdd(p.queue + cls, 1);
       __syncthreads();
       const int it = item;
       __syncthreads();
       if (it >= last) break;
-      const int U = items[4 * it + 0];
-      const int start = items[4 * it + 1];
-      const int cnt = items[4 * it + 2];
-      const int cfg = items[4 * it + 3];
-      if (cfg == 0)
-        dispatch_tile<8>(p, U, start, cnt, smem, red_warp, red_grp);
-      else
-        dispatch_tile<16>(p, U, start, cnt, smem, red_warp, red_grp);
+      process_item<TG, T, UC>(p, items[4 * it + 0], items[4 * it + 1], items[4 * it + 2], smem, red_warp, red_grp);
     }
   }
+  pdl_wait();
 }
+
+using SimtKernel = void (*)(const BatchedParams, int);
+
+// Kernel of each CUDA-core class, in class order (bt_class).
+const SimtKernel kSimtKernels[BT_NCLS - 1] = {
+    batched_simt_kernel<16, 4, 64>, batched_simt_kernel<16, 4, 0>, batched_simt_kernel<16, 3, 48>,
+    batched_simt_kernel<16, 3, 0>,  batched_simt_kernel<16, 2, 32>, batched_simt_kernel<16, 2, 0>,
+    batched_simt_kernel<16, 1, 16>, batched_simt_kernel<16, 1, 0>,  batched_simt_kernel<8, 4, 32>,
+    batched_simt_kernel<8, 4, 0>,   batched_simt_kernel<8, 3, 24>,  batched_simt_kernel<8, 3, 0>,
+    batched_simt_kernel<8, 2, 16>,  batched_simt_kernel<8, 2, 0>,   batched_simt_kernel<8, 1, 8>,
+    batched_simt_kernel<8, 1, 0>};
 
 int g_bt_sms = 0;
 bool g_bt_init = false;
@@ -661,8 +679,9 @@ int bt_init() {
   int dev = 0;
   NN_CUDA_TRY(cudaGetDevice(&dev));
   NN_CUDA_TRY(cudaDeviceGetAttribute(&g_bt_sms, cudaDevAttrMultiProcessorCount, dev));
-  NN_CUDA_TRY(cudaFuncSetAttribute(batched_nn_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
-  NN_CUDA_TRY(cudaFuncSetAttribute(batched_nn_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
+  NN_CUDA_TRY(cudaFuncSetAttribute(batched_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
+  for (SimtKernel k : kSimtKernels)
+    NN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM_SIMT_DEEP));
   g_bt_init = true;
   return NN_OK;
 }
@@ -671,8 +690,8 @@ int bt_init() {
 int group_count(int U, int cfg) {
   if (cfg == 2) return 1;
   const int by_threads = cfg == 0 ? BT_THREADS / 64 : 1;
-  const int per = BT_BUFS * U * U * int(sizeof(float2));
-  int by_smem = BT_SMEM / per;
+  const int per = bt_buffers(2) * U * U * int(sizeof(float2));
+  int by_smem = BT_SMEM_SIMT / per;
   return std::max(1, std::min(by_threads, by_smem));
 }
 
@@ -708,8 +727,7 @@ int nn_batched_plan(const int32_t* sizes_host, int64_t count, const int32_t* cfg
     int cfg = (cfg_by_u != nullptr && cfg_by_u[U] >= 0) ? cfg_by_u[U] : (U <= 32 ? 0 : 1);
     if (cfg < 0 || cfg > 2) return NN_ERR_ARG;
     if (cfg == 2 && (U % 16 != 0 || U > 64)) cfg = U <= 32 ? 0 : 1;
-    if (cfg == 1 && (U + 15) / 16 > 4) cfg = 0;
-    if (cfg == 0 && (U + 7) / 8 > 8) return NN_ERR_ARG;
+    if (cfg == 0 && (U + 7) / 8 > 4) cfg = 1;  // 8 x 8 threads with up to 4 x 4 elements each
     const int gmax = group_count(U, cfg);
     int cnt = 0;
     while (pos + cnt < count && cnt < gmax && sizes_host[order[size_t(pos + cnt)]] == U) ++cnt;
@@ -720,18 +738,22 @@ int nn_batched_plan(const int32_t* sizes_host, int64_t count, const int32_t* cfg
     ++n_items;
     pos += cnt;
   }
-  // tensor-core items first (their kernel takes [0, n_tc)), each part still largest first
+  // items grouped by class (each class's kernel takes [class_first[c], class_first[c + 1])),
+  // each class still largest first
   std::vector<int32_t> tmp(items, items + 4 * n_items);
-  int64_t w = 0, n_tc = 0;
-  for (int pass = 0; pass < 2; ++pass)
+  int64_t w = 0;
+  int32_t* class_first = plan_host + 3;
+  for (int c = 0; c < BT_NCLS; ++c) {
+    class_first[c] = int32_t(w);
     for (int64_t it = 0; it < n_items; ++it)
-      if ((tmp[size_t(4 * it + 3)] == 2) == (pass == 0)) {
+      if (bt_class(tmp[size_t(4 * it + 3)], tmp[size_t(4 * it)]) == c) {
         for (int f = 0; f < 4; ++f) items[4 * w + f] = tmp[size_t(4 * it + f)];
         ++w;
-        if (pass == 0) ++n_tc;
       }
+  }
+  class_first[BT_NCLS] = int32_t(w);
   plan_host[0] = int32_t(n_items);
-  plan_host[2] = int32_t(n_tc);
+  plan_host[2] = class_first[1];
   return NN_OK;
 }
 
@@ -762,12 +784,21 @@ int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* 
   p.residual = residual;
   p.status = status;
   p.queue = static_cast<int*>(workspace);
-  p.err = static_cast<int*>(workspace) + 4;
-  NN_CUDA_TRY(cudaMemsetAsync(p.queue, 0, 8 * sizeof(int), st));
-  batched_nn_kernel<true><<<g_bt_sms, BT_THREADS, BT_SMEM, st>>>(p);
+  p.err = static_cast<int*>(workspace) + BT_QUEUE_ERR;
+  NN_CUDA_TRY(cudaMemsetAsync(p.queue, 0, nn_batched_workspace_bytes(count), st));
+  batched_tc_kernel<<<g_bt_sms, BT_THREADS, BT_SMEM, st>>>(p);
   NN_CUDA_TRY(cudaGetLastError());
-  batched_nn_kernel<false><<<g_bt_sms, BT_THREADS, BT_SMEM, st>>>(p);
-  NN_CUDA_TRY(cudaGetLastError());
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(depth <= 2 ? 2 * g_bt_sms : g_bt_sms));
+  cfg.blockDim = dim3(BT_THREADS);
+  cfg.dynamicSmemBytes = size_t(depth <= 2 ? BT_SMEM_SIMT : BT_SMEM_SIMT_DEEP);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  for (int c = 1; c < BT_NCLS; ++c) NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kSimtKernels[c - 1], p, c));
   return NN_OK;
 }
 

@@ -62,3 +62,62 @@ def test_argument_errors_are_status_codes(lib):
     out = ctypes.c_double()
     assert lib.nn_residual(None, 4, None, 4, 4, abi.NN_F64, ctypes.byref(out), None, 0, None) == abi.NN_ERR_ARG
     assert lib.nn_init_precond(None, 4, 4, 0, 0.0, None, 4, None, 0, None) == abi.NN_ERR_ARG
+
+
+def _header_int(name):
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        m = re.search(r"#define\s+" + name + r"\s+(\d+)", open(h).read())
+        if m:
+            return int(m.group(1))
+    raise AssertionError(f"{name} not defined in include/")
+
+
+def _plan_class(cfg, u):
+    """Tile class of an item as the header defines it: 0 = tensor cores; CUDA-core classes
+    ordered by threads per matrix (16 x 16 first), tile (4 down to 1), exact U first."""
+    if cfg == 2:
+        return 0
+    tg = 8 if cfg == 0 else 16
+    t = -(-u // tg)
+    return 1 + (8 if cfg == 0 else 0) + (4 - t) * 2 + (0 if u % tg == 0 else 1)
+
+
+@pytest.mark.parametrize("cfg_by_u", [None, {u: 0 for u in range(1, 33)}, {16: 2, 32: 2, 48: 2, 64: 2, 40: 2}])
+def test_batched_plan_layout(lib, cfg_by_u):
+    """nn_batched_plan (host only): every matrix appears once, sizes within an item are equal,
+    items of a tile class are contiguous and largest first, and the class table brackets them."""
+    import numpy as np
+
+    assert abi.NN_BATCHED_KERNELS == _header_int("NN_BATCHED_KERNELS")
+    ncls = abi.NN_BATCHED_KERNELS
+    rng = np.random.default_rng(7)
+    sizes = rng.integers(1, 65, size=3000).astype(np.int32)
+    sizes[:50] = 64
+    plan = abi.nn_batched_plan(sizes, cfg_by_u)
+    n_items, count, n_tc = int(plan[0]), int(plan[1]), int(plan[2])
+    class_first = plan[3:3 + ncls + 1]
+    hdr = 3 + ncls + 1
+    order = plan[hdr:hdr + count]
+    items = plan[hdr + count:hdr + count + 4 * n_items].reshape(n_items, 4)
+    assert count == len(sizes) and len(plan) == hdr + 5 * count
+    assert sorted(order.tolist()) == list(range(count))
+    assert np.all(np.diff(sizes[order]) <= 0)
+    assert class_first[0] == 0 and class_first[-1] == n_items and n_tc == class_first[1]
+    assert np.all(np.diff(class_first) >= 0)
+    covered = np.zeros(count, dtype=bool)
+    for c in range(ncls):
+        prev_u = 65
+        for it in range(class_first[c], class_first[c + 1]):
+            u, start, cnt, cfg = (int(v) for v in items[it])
+            assert _plan_class(cfg, u) == c
+            assert u <= prev_u
+            prev_u = u
+            assert 1 <= cnt and (cfg != 1 or cnt == 1) and (cfg != 2 or cnt == 1) and cnt <= 4
+            assert cfg != 2 or u in (16, 32, 48, 64)
+            assert cfg != 0 or u <= 32
+            assert np.all(sizes[order[start:start + cnt]] == u)
+            assert not covered[start:start + cnt].any()
+            covered[start:start + cnt] = True
+    assert covered.all()
+    if cfg_by_u and cfg_by_u.get(64) == 2:
+        assert n_tc > 0 and all(int(items[i, 0]) in (16, 32, 48, 64) for i in range(n_tc))
