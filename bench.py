@@ -62,7 +62,7 @@ def parse_args():
     ap.add_argument("--gemm-variant", type=int, default=0, choices=[0, 1, 2, 3, 4], help="0 auto, 1 single-CTA tiles, 2 CTA pairs with multicast, 3 2-SM MMA, 4 2-SM MMA with split last wave")
     ap.add_argument("--spmv-variant", type=int, default=0, choices=[0, 1], help="0 auto (bulk-copy ring), 1 staged loads")
     ap.add_argument("--batched-tc", action="store_true",
-                    help="batched workload: tensor-core items for U in {16, 32, 48, 64}")
+                    help="batched workload: tensor-core items for U in {48, 64}")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -599,7 +599,7 @@ def run_batched(args, rank, world, local_rank):
     table = load_batched_tuning()
     if args.batched_tc:
         table = dict(table or {})
-        table.update({16: 2, 32: 2, 48: 2, 64: 2})
+        table.update({48: 2, 64: 2})
     plan = torch.from_numpy(abi.nn_batched_plan(bt.sizes, table)).to(dev)
     X = torch.empty_like(A)
     res = torch.empty(count, dtype=torch.float32, device=dev)

@@ -35,13 +35,13 @@ namespace {
 
 constexpr int BT_THREADS = 256;
 constexpr int BT_MAX_U = 64;
-constexpr int BT_SMEM = 200 * 1024;         // dynamic shared memory of a tensor-core CTA
+constexpr int BT_SMEM = 193 * 1024;         // dynamic shared memory of a tensor-core CTA
 // CUDA-core items: two CTAs per SM at depth <= 2 (three buffers per matrix), one at depth >= 3
 // (four buffers, 4/3 of the same shared memory), so a plan sized for the first fits both.
 constexpr int BT_SMEM_SIMT = 112 * 1024;
 constexpr int BT_SMEM_SIMT_DEEP = BT_SMEM_SIMT / 3 * 4;
-// Tile classes: 0 = tensor-core items; 1..16 = CUDA-core items, ordered by cost: 16x16 threads
-// then 8x8, tile 4 down to 1, exact U (= tile * threads per side) before other sizes.
+// Tile classes: 0, 1 = tensor-core items of U = 64, 48; 2..17 = CUDA-core items, ordered by
+// cost: 16x16 threads then 8x8, tile 4 down to 1, exact U (= tile * threads per side) first.
 constexpr int BT_NCLS = NN_BATCHED_KERNELS;
 constexpr int PLAN_HDR = 3 + BT_NCLS + 1;   // [n_items, count, n_tc, class_first[BT_NCLS + 1]]
 constexpr int BT_QUEUE_ERR = 32;            // workspace: int counters [0, BT_NCLS), error word here
@@ -49,8 +49,8 @@ constexpr int BT_QUEUE_ERR = 32;            // workspace: int counters [0, BT_NC
 static_assert(BT_NCLS <= BT_QUEUE_ERR && (BT_QUEUE_ERR + 1) * 4 <= 256, "counters fit the workspace");
 
 __host__ __device__ constexpr int bt_class(int cfg, int U) {
-  return cfg == 2 ? 0
-                  : 1 + (cfg == 0 ? 8 : 0) + (4 - (U + (cfg == 0 ? 7 : 15)) / (cfg == 0 ? 8 : 16)) * 2 +
+  return cfg == 2 ? (U == 64 ? 0 : 1)
+                  : 2 + (cfg == 0 ? 8 : 0) + (4 - (U + (cfg == 0 ? 7 : 15)) / (cfg == 0 ? 8 : 16)) * 2 +
                         (U % (cfg == 0 ? 8 : 16) == 0 ? 0 : 1);
 }
 
@@ -279,33 +279,50 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
   __syncthreads();
 }
 
-// ---- tensor-core path (plan configuration 2; U in {16, 32, 48, 64}) ------------------------
+// ---- tensor-core path (plan configuration 2; U in {48, 64}) --------------------------------
 //
-// One matrix per CTA at a time, every iterate kept on chip:
-//   * masters (A, X, R, T, W) live in TMEM as the real form [Re; Im] of each U x U complex matrix:
-//     lane i < U holds row i's real parts, lane U + i its imaginary parts, columns 0..U-1;
-//   * a complex product C = P Q runs as one real MMA on the embedding
+// Two matrices per CTA in a software pipeline, every iterate kept on chip:
+//   * masters (A, X, R; T at depth >= 3) live in TMEM as the real form [Re; Im] of each U x U
+//     complex matrix: lane i < U holds row i's real parts, lane U + i its imaginary parts,
+//     columns 0..U-1; each of the two pipeline slots owns 256 columns (A, X, R, accumulator);
+//   * a complex product C = P Q runs as one real MMA chain on the embedding
 //         [Cr; Ci] (2U x U) = [[Pr, -Pi], [Pi, Pr]] (2U x 2U) . [Qr; Qi] (2U x U),
-//     i.e. M = 128 (2U rows used), N = U, K = 2U, with no redundant work. Its left operand is
-//     built from P's master rows, its right operand (K-major: row j = column j of [Qr; Qi]) is
-//     exactly the transpose of Q's master (lane k, column j -> row j, k);
+//     i.e. M = 128 (2U rows used), N = U, K = 2U. Its left operand is built from P's master
+//     rows, its right operand (K-major: row j = column j of [Qr; Qi]) is the transpose of Q's
+//     master (lane k, column j -> row j, k);
 //   * operands are split into three BF16 pieces (x = p0 + p1 + p2, each the BF16 rounding of the
-//     remainder) and written to shared memory in the SWIZZLE_128B K-major layout; six piece
-//     products (the pairs with i + j <= 2, smallest first) accumulate in FP32 in TMEM, which
-//     matches an FP32 product to about 2^-24 relative;
-//   * the epilogue reads the accumulator, applies I - C or D + C in FP32 and writes the result
-//     master back to TMEM; the residual's sum of squares is reduced across the CTA.
+//     remainder) and written to shared memory in the SWIZZLE_128B K-major layout, one 64-wide
+//     k-block at a time; the six piece products with i + j <= 2 (smallest first) accumulate in
+//     FP32 in TMEM, which matches an FP32 product to about 2^-24 relative;
+//   * pipeline: while the tensor core runs k-block 0 of one slot's product, the CTA stages
+//     k-block 1 of its left operand; while it runs k-block 1, the CTA finishes the other slot's
+//     previous product (reads its accumulator, applies I - C or D + C in FP32, writes the result
+//     master, reduces the residual) and stages k-block 0 of that slot's next product together
+//     with its whole right operand (two right-operand buffers, alternating by product). Each
+//     buffer is reused once the MMAs that read it have completed (one mbarrier per k-block).
 namespace btc {
 constexpr int M = 128;                         // MMA rows (2U used)
-constexpr int KP = 128;                        // K capacity (2U used): two 64-wide k-blocks
+constexpr int CW = 16;                         // master columns per warp (TMEM access: 32 lanes x 16)
+constexpr int WARPS = 4 * (64 / CW);           // warp (q, h): lane quadrant q, column block h
+constexpr int THREADS = 32 * WARPS;
 constexpr int NP = 64;                         // B-operand rows capacity (U used)
-constexpr int A_PIECE = M * KP * 2;            // 32 KB
-constexpr int B_PIECE = NP * KP * 2;           // 16 KB
-constexpr int OPS_BYTES = 3 * A_PIECE + 3 * B_PIECE;
-constexpr uint32_t ACC = 0, MA = 64, MX = 128, MR = 192, MT = 256, MW = 320;
+constexpr int A_KB = M * 128;                  // one 64-wide k-block of one A piece: 16 KB
+constexpr int B_KB = NP * 128;                 // 8 KB
+constexpr int A_BLOCK = 3 * A_KB;              // k-block kb of the three A pieces at kb * A_BLOCK
+constexpr int B_OFF = 2 * A_BLOCK;             // two B buffers (products alternate) after them,
+constexpr int B_BUF = 2 * 3 * B_KB;            // each k-block kb of three pieces at kb * 3 * B_KB
+constexpr int OPS_BYTES = B_OFF + 2 * B_BUF;   // 192 KB
+constexpr uint32_t SLOT_COLS = 256;            // TMEM columns per pipeline slot
+constexpr uint32_t MA = 0, MX = 64, MR = 128, ACC = 192;
+constexpr uint32_t MT = 256;                   // T master (depth >= 3: one slot only)
 constexpr uint32_t TMEM_COLS = 512;
 static_assert(OPS_BYTES + 1024 <= BT_SMEM, "operand pieces fit the dynamic shared memory");
+static_assert(A_KB % 1024 == 0 && B_KB % 1024 == 0, "swizzle atoms stay aligned");
 }  // namespace btc
+
+// TMEM access of a warp's 32 lanes x btc::CW columns.
+__device__ __forceinline__ void tmem_ld_cw(uint32_t taddr, uint32_t (&r)[16]) { tmem_ld_32x32b_x16(taddr, r); }
+__device__ __forceinline__ void tmem_st_cw(uint32_t taddr, const uint32_t (&r)[16]) { tmem_st_32x32b_x16(taddr, r); }
 
 // Shared-memory matrix descriptor of a K-major SWIZZLE_128B tile (8-row atoms 1024 B apart).
 __device__ __forceinline__ uint64_t bt_sw128_desc(uint32_t saddr) {
@@ -313,277 +330,240 @@ __device__ __forceinline__ uint64_t bt_sw128_desc(uint32_t saddr) {
          (uint64_t(1) << 46) | (uint64_t(2) << 61);
 }
 
-// Byte offset of element (r, k) in a K-major SWIZZLE_128B operand of `rows` rows and 64-wide
-// k-blocks: 16-byte chunk c of row r sits at chunk c ^ (r mod 8) of its 128-byte line.
-__device__ __forceinline__ uint32_t bt_sw128_offset(int r, int k, int rows) {
-  const int kb = k >> 6, c = (k & 63) >> 3, e = k & 7;
-  return uint32_t(kb * rows * 128 + (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4) + (e << 1));
+// Byte offset of element (r, kk), kk < 64, in one k-block of a K-major SWIZZLE_128B operand:
+// 16-byte chunk c of row r sits at chunk c ^ (r mod 8) of its 128-byte line.
+__device__ __forceinline__ uint32_t bt_sw128_offset(int r, int kk) {
+  return uint32_t((r >> 3) * 1024 + (r & 7) * 128 + (((kk >> 3) ^ (r & 7)) << 4) + ((kk & 7) << 1));
 }
 
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
-  p0 = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(p0);
-  p1 = __float2bfloat16_rn(r1);
-  p2 = __float2bfloat16_rn(r1 - __bfloat162float(p1));
+// Three BF16 pieces of the pair (a, b) (a in the low halves): each piece is the BF16 rounding
+// of what the previous pieces leave (the remainders are exact in FP32).
+__device__ __forceinline__ void split3x2(float a, float b, uint32_t& w0, uint32_t& w1, uint32_t& w2) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  w0 = *reinterpret_cast<uint32_t*>(&v);
+  a -= __uint_as_float(w0 << 16);
+  b -= __uint_as_float(w0 & 0xffff0000u);
+  v = __floats2bfloat162_rn(a, b);
+  w1 = *reinterpret_cast<uint32_t*>(&v);
+  a -= __uint_as_float(w1 << 16);
+  b -= __uint_as_float(w1 & 0xffff0000u);
+  v = __floats2bfloat162_rn(a, b);
+  w2 = *reinterpret_cast<uint32_t*>(&v);
 }
 
-// Left operand [[Pr, -Pi], [Pi, Pr]] pieces from master P; warp (q, h) owns lanes 32q.. and
-// columns 32h.. of the master.
+// k-block kb of the left operand [[Pr, -Pi], [Pi, Pr]] (three pieces) from master P; warp
+// (q, h) owns lanes 32q.. and columns 32h.. of the master. Row i takes K = column (real part)
+// or U + column (negated imaginary part); row U + i takes K = U + column (real part) or column
+// (imaginary part). An 8-column chunk never straddles a k-block (U is a multiple of 16); the
+// pieces of -x are those of x with the sign bits flipped.
 template <int U>
-__device__ __forceinline__ void bt_build_left(uint32_t tmem, uint32_t cP, uint8_t* ops, int q, int h, int l) {
-  if (h * 32 >= U) return;
-  uint32_t raw[32];
-  tmem_ld_32x32b_x32(tmem + (uint32_t(q * 32) << 16) + cP + uint32_t(h * 32), raw);
+__device__ __forceinline__ void tc_build_left(uint32_t tmem, uint32_t cP, uint8_t* ablk, int kb, int q, int h,
+                                              int l) {
+  if (h * btc::CW >= U) return;
+  uint32_t raw[btc::CW];
+  tmem_ld_cw(tmem + (uint32_t(q * 32) << 16) + cP + uint32_t(h * btc::CW), raw);
   tmem_ld_wait();
   if (l >= 2 * U) return;
   const bool re = l < U;
   const int i = re ? l : l - U;
-  // destination 1: row i at K = (re ? 0 : U) + column, sign (re ? + : -); destination 2: row
-  // U + i at K = (re ? U : 0) + column, sign +
-  const int rows[2] = {i, U + i};
-  const int kbase[2] = {re ? 0 : U, re ? U : 0};
-  const float sgn[2] = {re ? 1.0f : -1.0f, 1.0f};
+  const int kbase0 = re ? 0 : U, kbase1 = re ? U : 0;
+  const uint32_t flip0 = re ? 0u : 0x80008000u;
 #pragma unroll
-  for (int d = 0; d < 2; ++d) {
+  for (int ch = 0; ch < btc::CW / 8; ++ch) {
+    const int j0 = h * btc::CW + ch * 8;
+    if (j0 >= U) break;
+    const int K0 = kbase0 + j0, K1 = kbase1 + j0;
+    const bool n0 = (K0 >> 6) == kb, n1 = (K1 >> 6) == kb;
+    if (!n0 && !n1) continue;
+    uint32_t w[3][4];
 #pragma unroll
-    for (int ch = 0; ch < 4; ++ch) {
-      const int j0 = h * 32 + ch * 8;
-      if (j0 >= U) break;
-      uint32_t pk[3][4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        __nv_bfloat16 a0, a1, a2, b0, b1, b2;
-        split3(sgn[d] * __uint_as_float(raw[ch * 8 + 2 * e]), a0, a1, a2);
-        split3(sgn[d] * __uint_as_float(raw[ch * 8 + 2 * e + 1]), b0, b1, b2);
-        pk[0][e] = uint32_t(__bfloat16_as_ushort(a0)) | (uint32_t(__bfloat16_as_ushort(b0)) << 16);
-        pk[1][e] = uint32_t(__bfloat16_as_ushort(a1)) | (uint32_t(__bfloat16_as_ushort(b1)) << 16);
-        pk[2][e] = uint32_t(__bfloat16_as_ushort(a2)) | (uint32_t(__bfloat16_as_ushort(b2)) << 16);
-      }
-      const uint32_t off = bt_sw128_offset(rows[d], kbase[d] + j0, btc::M);
+    for (int e = 0; e < 4; ++e)
+      split3x2(__uint_as_float(raw[ch * 8 + 2 * e]), __uint_as_float(raw[ch * 8 + 2 * e + 1]), w[0][e], w[1][e],
+               w[2][e]);
+    if (n0) {
+      const uint32_t off = bt_sw128_offset(i, K0 & 63);
 #pragma unroll
       for (int pc = 0; pc < 3; ++pc)
-        *reinterpret_cast<uint4*>(ops + pc * btc::A_PIECE + off) = make_uint4(pk[pc][0], pk[pc][1], pk[pc][2], pk[pc][3]);
+        *reinterpret_cast<uint4*>(ablk + pc * btc::A_KB + off) =
+            make_uint4(w[pc][0] ^ flip0, w[pc][1] ^ flip0, w[pc][2] ^ flip0, w[pc][3] ^ flip0);
+    }
+    if (n1) {
+      const uint32_t off = bt_sw128_offset(U + i, K1 & 63);
+#pragma unroll
+      for (int pc = 0; pc < 3; ++pc)
+        *reinterpret_cast<uint4*>(ablk + pc * btc::A_KB + off) = make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
     }
   }
 }
 
-// Right operand pieces: row j, column k = master Q (lane k, column j), k < 2U, j < U. Even lanes
-// store the pair (k, k + 1) received from the odd neighbour.
+// Both k-blocks of the right operand pieces: row j, column k = master Q (lane k, column j); warp
+// q's lanes fall in k-block q / 2. The pair (k, k + 1) of column j is split and stored by the
+// even lane for the first 16 columns of the warp's block and by the odd lane for the rest.
 template <int U>
-__device__ __forceinline__ void bt_build_right(uint32_t tmem, uint32_t cQ, uint8_t* ops, int q, int h, int l) {
-  if (h * 32 >= U) return;
-  uint32_t raw[32];
-  tmem_ld_32x32b_x32(tmem + (uint32_t(q * 32) << 16) + cQ + uint32_t(h * 32), raw);
+__device__ __forceinline__ void tc_build_right(uint32_t tmem, uint32_t cQ, uint8_t* bbuf, int q, int h, int l) {
+  if (h * btc::CW >= U || q * 32 >= 2 * U) return;
+  uint32_t raw[btc::CW];
+  tmem_ld_cw(tmem + (uint32_t(q * 32) << 16) + cQ + uint32_t(h * btc::CW), raw);
   tmem_ld_wait();
-  uint8_t* bops = ops + 3 * btc::A_PIECE;
-  const bool store = (l & 1) == 0 && l < 2 * U;
+  uint8_t* bops = bbuf + (q >> 1) * 3 * btc::B_KB;
+  const bool odd = (l & 1) != 0;
+  const int kk = (l & 63) & ~1;
 #pragma unroll
-  for (int t = 0; t < 32; ++t) {
-    const float v = __uint_as_float(raw[t]);
-    const float w = __shfl_down_sync(0xffffffffu, v, 1);
-    const int j = h * 32 + t;
-    if (store && j < U) {
-      __nv_bfloat16 a0, a1, a2, b0, b1, b2;
-      split3(v, a0, a1, a2);
-      split3(w, b0, b1, b2);
-      const uint32_t off = bt_sw128_offset(j, l, btc::NP);
-      *reinterpret_cast<uint32_t*>(bops + off) =
-          uint32_t(__bfloat16_as_ushort(a0)) | (uint32_t(__bfloat16_as_ushort(b0)) << 16);
-      *reinterpret_cast<uint32_t*>(bops + btc::B_PIECE + off) =
-          uint32_t(__bfloat16_as_ushort(a1)) | (uint32_t(__bfloat16_as_ushort(b1)) << 16);
-      *reinterpret_cast<uint32_t*>(bops + 2 * btc::B_PIECE + off) =
-          uint32_t(__bfloat16_as_ushort(a2)) | (uint32_t(__bfloat16_as_ushort(b2)) << 16);
+  for (int t = 0; t < btc::CW / 2; ++t) {
+    const float lo_v = __uint_as_float(raw[t]), hi_v = __uint_as_float(raw[btc::CW / 2 + t]);
+    const float from_next = __shfl_down_sync(0xffffffffu, lo_v, 1);  // even lanes: k + 1, column t
+    const float from_prev = __shfl_up_sync(0xffffffffu, hi_v, 1);    // odd lanes: k - 1, column CW/2 + t
+    const int j = h * btc::CW + (odd ? btc::CW / 2 + t : t);
+    if (j < U) {
+      uint32_t w0, w1, w2;
+      if (odd)
+        split3x2(from_prev, hi_v, w0, w1, w2);
+      else
+        split3x2(lo_v, from_next, w0, w1, w2);
+      const uint32_t off = bt_sw128_offset(j, kk);
+      *reinterpret_cast<uint32_t*>(bops + off) = w0;
+      *reinterpret_cast<uint32_t*>(bops + btc::B_KB + off) = w1;
+      *reinterpret_cast<uint32_t*>(bops + 2 * btc::B_KB + off) = w2;
     }
   }
 }
 
-// out = mode(P Q) for masters at TMEM columns cP, cQ, cD (addend), cOut; returns this thread's
-// sum of squares of the result (residual mode). false if the MMA wait timed out.
+// One thread: the MMAs of k-block KB (K = 64, or 2U - 64 for the second block) into d_tmem,
+// piece pairs (a, b) smallest terms first: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0).
+template <int U, int KB>
+__device__ __forceinline__ void tc_issue(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr) {
+  constexpr uint32_t idesc =
+      (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(U >> 3) << 17) | (uint32_t(btc::M >> 4) << 24);
+  constexpr int ksteps = KB == 0 ? 4 : (2 * U - 64) / 16;
+  const uint64_t ad = bt_sw128_desc(a_saddr), bd = bt_sw128_desc(b_saddr);
+#pragma unroll
+  for (int pp = 0; pp < 6; ++pp) {
+    const int pa = pp == 0 ? 2 : (pp == 1 || pp == 3) ? 1 : 0;
+    const int pb = pp == 2 ? 2 : (pp == 1 || pp == 4) ? 1 : 0;
+#pragma unroll
+    for (int st = 0; st < ksteps; ++st)
+      tc_mma_bf16(d_tmem, ad + uint64_t((pa * btc::A_KB) >> 4) + uint64_t(2 * st),
+                  bd + uint64_t((pb * btc::B_KB) >> 4) + uint64_t(2 * st), idesc,
+                  (KB == 0 && pp == 0 && st == 0) ? 0u : 1u);
+  }
+}
+
+// out = mode(accumulator) on this warp's 32 x 32 block of the real form; returns this
+// thread's sum of squares of the result (residual mode, valid lanes and columns only).
 template <int U>
-__device__ bool bt_product(uint32_t tmem, uint8_t* ops, uint64_t* bar, uint32_t& phase, volatile int* abort_flag,
-                           int* err, uint32_t cP, uint32_t cQ, uint32_t cD, uint32_t cOut, int mode, float* ss) {
-  const int w = int(threadIdx.x >> 5), q = w & 3, h = w >> 2, l = q * 32 + int(threadIdx.x & 31);
-  bt_build_left<U>(tmem, cP, ops, q, h, l);
-  bt_build_right<U>(tmem, cQ, ops, q, h, l);
-  fence_proxy_async_smem();
-  tc_fence_before();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    tc_fence_after();
-    constexpr uint32_t idesc =
-        (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(U >> 3) << 17) | (uint32_t(btc::M >> 4) << 24);
-    const uint32_t base = smem_u32(ops);
-    // piece pairs (a, b), smallest terms first: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
-    uint32_t acc = 0;
-#pragma unroll 1
-    for (int pp = 0; pp < 6; ++pp) {
-      const int pa = pp == 0 ? 2 : (pp == 1 || pp == 3) ? 1 : 0;
-      const int pb = pp == 2 ? 2 : (pp == 1 || pp == 4) ? 1 : 0;
-      const uint32_t a0 = base + uint32_t(pa * btc::A_PIECE);
-      const uint32_t b0 = base + uint32_t(3 * btc::A_PIECE + pb * btc::B_PIECE);
-#pragma unroll 1
-      for (int st = 0; st < U / 8; ++st) {
-        const int kb = st >> 2, kk = st & 3;
-        const uint64_t ad = bt_sw128_desc(a0 + uint32_t(kb * btc::M * 128)) + uint64_t(2 * kk);
-        const uint64_t bd = bt_sw128_desc(b0 + uint32_t(kb * btc::NP * 128)) + uint64_t(2 * kk);
-        tc_mma_bf16(tmem + btc::ACC, ad, bd, idesc, acc);
-        acc = 1;
-      }
-    }
-    tc_commit(bar);
-  }
-  // every thread learns the same outcome (a timed-out wait in any thread aborts the item)
-  const bool ok = __syncthreads_and(mbar_wait(bar, phase, abort_flag, err) ? 1 : 0) != 0;
-  phase ^= 1u;
-  tc_fence_after();
-  if (!ok) return false;
-  // epilogue: warp (q, h) owns accumulator lanes 32q.. and columns 32h..
+__device__ __forceinline__ float tc_epilogue(uint32_t tmem, uint32_t cAcc, uint32_t cD, uint32_t cOut, int mode,
+                                             int q, int h, int l) {
   float local = 0.f;
-  if (h * 32 < U) {
-    uint32_t c[32], d[32];
-    const uint32_t lane_off = uint32_t(q * 32) << 16;
-    tmem_ld_32x32b_x32(tmem + lane_off + btc::ACC + uint32_t(h * 32), c);
-    if (mode == BM_ADD) tmem_ld_32x32b_x32(tmem + lane_off + cD + uint32_t(h * 32), d);
-    tmem_ld_wait();
+  if (h * btc::CW >= U) return local;
+  uint32_t c[btc::CW], d[btc::CW];
+  const uint32_t lane_off = uint32_t(q * 32) << 16;
+  tmem_ld_cw(tmem + lane_off + cAcc + uint32_t(h * btc::CW), c);
+  if (mode == BM_ADD) tmem_ld_cw(tmem + lane_off + cD + uint32_t(h * btc::CW), d);
+  tmem_ld_wait();
 #pragma unroll
-    for (int t = 0; t < 32; ++t) {
-      const int j = h * 32 + t;
-      const float cv = __uint_as_float(c[t]);
-      float v;
-      if (mode == BM_RESID) {
-        v = ((l < U && j == l) ? 1.f : 0.f) - cv;
-        if (l < 2 * U && j < U) local = fmaf(v, v, local);
-      } else {
-        v = __uint_as_float(d[t]) + cv;
-      }
-      c[t] = __float_as_uint(v);
+  for (int t = 0; t < btc::CW; ++t) {
+    const int j = h * btc::CW + t;
+    const float cv = __uint_as_float(c[t]);
+    float v;
+    if (mode == BM_RESID) {
+      v = ((l < U && j == l) ? 1.f : 0.f) - cv;
+      if (l < 2 * U && j < U) local = fmaf(v, v, local);
+    } else {
+      v = __uint_as_float(d[t]) + cv;
     }
-    tmem_st_32x32b_x32(tmem + lane_off + cOut + uint32_t(h * 32), c);
-    tmem_st_wait();
+    c[t] = __float_as_uint(v);
   }
-  *ss = local;
-  tc_fence_before();
-  __syncthreads();
-  return true;
+  tmem_st_cw(tmem + lane_off + cOut + uint32_t(h * btc::CW), c);
+  tmem_st_wait();
+  return local;
 }
 
-// Sum over the CTA (256 threads); result broadcast to every thread.
+// Sum over the CTA (btc::THREADS threads); result broadcast to every thread.
 __device__ __forceinline__ float bt_block_sum(float v, float* red_warp) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0) red_warp[threadIdx.x >> 5] = v;
   __syncthreads();
   float t = 0.f;
-  for (int w = 0; w < BT_THREADS / 32; ++w) t += red_warp[w];
+  for (int w = 0; w < btc::WARPS; ++w) t += red_warp[w];
   __syncthreads();
   return t;
 }
 
+// Masters A and X_0 = c diag(A)^-1 (damped Jacobi) of matrix A (device, row-major) in their
+// real forms at slot columns sb + MA, sb + MX; rows >= 2U are zero.
 template <int U>
-__device__ void process_item_tc(const BatchedParams& p, int start, uint8_t* ops, uint32_t tmem, uint64_t* bar,
-                                uint32_t& phase, volatile int* abort_flag, float* red_warp) {
-  const int w = int(threadIdx.x >> 5), q = w & 3, h = w >> 2, l = q * 32 + int(threadIdx.x & 31);
-  const int b = p.plan[PLAN_HDR + start];
-  const int64_t off = p.offsets[b];
-  const float2* A = p.A + off;
-  // masters A and X_0 = c diag(A)^-1 (damped Jacobi) in their real forms
-  if (h * 32 < U) {
-    uint32_t va[32], vx[32];
-    const bool valid_row = l < 2 * U;
-    const bool re = l < U;
-    const int i = re ? l : l - U;
-    float2 aii = make_float2(1.f, 0.f);
-    if (valid_row) aii = A[i * U + i];
-    const float cdamp = 1.f / (1.f + p.damping * float(U));
-    const float den = aii.x * aii.x + aii.y * aii.y;
+__device__ __forceinline__ void tc_load_masters(const float2* A, float damping, uint32_t tmem, uint32_t sb, int q,
+                                                int h, int l) {
+  if (h * btc::CW >= U) return;
+  uint32_t va[btc::CW], vx[btc::CW];
+  const bool valid_row = l < 2 * U;
+  const bool re = l < U;
+  const int i = re ? l : l - U;
+  float2 aii = make_float2(1.f, 0.f);
+  if (valid_row) aii = A[i * U + i];
+  const float cdamp = 1.f / (1.f + damping * float(U));
+  const float den = aii.x * aii.x + aii.y * aii.y;
 #pragma unroll
-    for (int t = 0; t < 32; ++t) {
-      const int j = h * 32 + t;
-      float av = 0.f, xv = 0.f;
-      if (valid_row && j < U) {
-        const float2 a = A[i * U + j];
-        av = re ? a.x : a.y;
-        if (j == i) xv = re ? cdamp * aii.x / den : -cdamp * aii.y / den;
-      }
-      va[t] = __float_as_uint(av);
-      vx[t] = __float_as_uint(xv);
+  for (int t = 0; t < btc::CW; ++t) {
+    const int j = h * btc::CW + t;
+    float av = 0.f, xv = 0.f;
+    if (valid_row && j < U) {
+      const float2 a = A[i * U + j];
+      av = re ? a.x : a.y;
+      if (j == i) xv = re ? cdamp * aii.x / den : -cdamp * aii.y / den;
     }
-    const uint32_t lane_off = uint32_t(q * 32) << 16;
-    tmem_st_32x32b_x32(tmem + lane_off + btc::MA + uint32_t(h * 32), va);
-    tmem_st_32x32b_x32(tmem + lane_off + btc::MX + uint32_t(h * 32), vx);
-    tmem_st_wait();
+    va[t] = __float_as_uint(av);
+    vx[t] = __float_as_uint(xv);
   }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-
-  bool frozen = false, timed_out = false;
-  float s_prev = 0.f, s_last = 0.f;
-  int st = NN_OK;
-  uint32_t cX = btc::MX;
-  for (int k = 0; k <= p.nests; ++k) {
-    if (!frozen) {
-      float ss = 0.f;
-      if (!bt_product<U>(tmem, ops, bar, phase, abort_flag, p.err, btc::MA, cX, 0, btc::MR, BM_RESID, &ss)) {
-        timed_out = true;
-        break;
-      }
-      const float s = sqrtf(bt_block_sum(ss, red_warp)) / float(U);
-      s_last = s;
-      if (!isfinite(s) || (k >= 1 && s >= 1.f && s > s_prev)) {
-        st = NN_ERR_DIVERGED;
-        frozen = true;
-      }
-      s_prev = s;
-    }
-    if (k == p.nests || frozen) break;
-    // Horner: T_1 = R, T_{j+1} = R + R T_j (T, W alternate); X_{k+1} = X_k + X_k T
-    uint32_t t_cur = btc::MR;
-    bool ok = true;
-    for (int j = 1; j < p.depth && ok; ++j) {
-      const uint32_t dst = (t_cur == btc::MT) ? btc::MW : btc::MT;
-      float unused = 0.f;
-      ok = bt_product<U>(tmem, ops, bar, phase, abort_flag, p.err, btc::MR, t_cur, btc::MR, dst, BM_ADD, &unused);
-      t_cur = dst;
-    }
-    float unused = 0.f;
-    if (!ok || !bt_product<U>(tmem, ops, bar, phase, abort_flag, p.err, cX, t_cur, cX, cX, BM_ADD, &unused)) {
-      timed_out = true;
-      break;
-    }
-  }
-  if (timed_out) st = NN_ERR_TIMEOUT;
-  // X (complex, row-major) from the X master; 2U is a multiple of 32, so the test is warp-uniform
-  if (h * 32 < U && q * 32 < 2 * U) {
-    uint32_t vx[32];
-    tmem_ld_32x32b_x32(tmem + (uint32_t(q * 32) << 16) + cX + uint32_t(h * 32), vx);
-    tmem_ld_wait();
-    const bool re = l < U;
-    const int i = re ? l : l - U;
-    float* Xf = reinterpret_cast<float*>(p.X + off);
-#pragma unroll
-    for (int t = 0; t < 32; ++t) {
-      const int j = h * 32 + t;
-      if (j < U) Xf[2 * (i * U + j) + (re ? 0 : 1)] = __uint_as_float(vx[t]);
-    }
-  }
-  if (threadIdx.x == 0) {
-    p.residual[b] = s_last;
-    p.status[b] = st;
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
+  const uint32_t lane_off = uint32_t(q * 32) << 16;
+  tmem_st_cw(tmem + lane_off + sb + btc::MA + uint32_t(h * btc::CW), va);
+  tmem_st_cw(tmem + lane_off + sb + btc::MX + uint32_t(h * btc::CW), vx);
+  tmem_st_wait();
 }
 
-__device__ void dispatch_tc(const BatchedParams& p, int U, int start, uint8_t* ops, uint32_t tmem, uint64_t* bar,
-                            uint32_t& phase, volatile int* abort_flag, float* red_warp) {
-  switch (U) {
-    case 16: process_item_tc<16>(p, start, ops, tmem, bar, phase, abort_flag, red_warp); break;
-    case 32: process_item_tc<32>(p, start, ops, tmem, bar, phase, abort_flag, red_warp); break;
-    case 48: process_item_tc<48>(p, start, ops, tmem, bar, phase, abort_flag, red_warp); break;
-    default: process_item_tc<64>(p, start, ops, tmem, bar, phase, abort_flag, red_warp); break;
+// X (complex, row-major) from the X master at column cX.
+template <int U>
+__device__ __forceinline__ void tc_store_x(float2* X, uint32_t tmem, uint32_t cX, int q, int h, int l) {
+  if (h * btc::CW >= U || q * 32 >= 2 * U) return;  // 2U is a multiple of 32: warp-uniform
+  uint32_t vx[btc::CW];
+  tmem_ld_cw(tmem + (uint32_t(q * 32) << 16) + cX + uint32_t(h * btc::CW), vx);
+  tmem_ld_wait();
+  const bool re = l < U;
+  const int i = re ? l : l - U;
+  float* Xf = reinterpret_cast<float*>(X);
+#pragma unroll
+  for (int t = 0; t < btc::CW; ++t) {
+    const int j = h * btc::CW + t;
+    if (j < U) Xf[2 * (i * U + j) + (re ? 0 : 1)] = __uint_as_float(vx[t]);
   }
+}
+
+// Pipeline slot state (identical in every thread: all updates are CTA-uniform).
+struct TcSlot {
+  int b;          // matrix index, -1 = empty
+  int k, j;       // nest, product within the nest (0 = residual, 1..L-1 Horner, L = update)
+  int st;
+  float s_prev, s_last;
+};
+
+// Columns of the product that slot s at state (k, j) runs next.
+struct TcProd {
+  uint32_t cP, cQ, cD, cOut;
+  int mode;
+};
+
+__device__ __forceinline__ TcProd tc_product(const TcSlot& s, uint32_t sb, int depth) {
+  TcProd r;
+  if (s.j == 0) {
+    r = {sb + btc::MA, sb + btc::MX, 0u, sb + btc::MR, BM_RESID};
+  } else if (s.j < depth) {
+    // Horner T_{j+1} = R + R T_j; at depth 2 it replaces R in place
+    r = {sb + btc::MR, s.j == 1 ? sb + btc::MR : btc::MT, sb + btc::MR, depth == 2 ? sb + btc::MR : btc::MT, BM_ADD};
+  } else {
+    r = {sb + btc::MX, depth <= 2 ? sb + btc::MR : btc::MT, sb + btc::MX, sb + btc::MX, BM_ADD};
+  }
+  return r;
 }
 
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
@@ -591,25 +571,29 @@ __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepc
 // implies its predecessors' (stream order for whatever follows the last one).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-// The tensor-core items (class 0): one CTA per SM, 512 TMEM columns.
-__global__ void __launch_bounds__(BT_THREADS, 1) batched_tc_kernel(const BatchedParams p) {
+// The tensor-core items of size U (classes 0 and 1): one CTA per SM, 512 TMEM columns, two
+// pipeline slots at depth <= 2 (one at depth >= 3, whose T master takes the second slot's
+// columns).
+template <int U>
+__global__ void __launch_bounds__(btc::THREADS, 1) batched_tc_kernel(const BatchedParams p, int cls) {
   extern __shared__ float2 smem[];
-  __shared__ float red_warp[BT_THREADS / 32];
-  __shared__ int item;
-  __shared__ __align__(8) uint64_t tc_bar;
+  __shared__ float red_warp[btc::WARPS];
+  __shared__ int item_sh;
+  __shared__ __align__(8) uint64_t kb_bar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_word;
   pdl_launch_dependents();
   const int count = p.plan[1];
-  const int first = p.plan[3], last = p.plan[4];
+  const int first = p.plan[3 + cls], last = p.plan[3 + cls + 1];
   const int32_t* items = p.plan + PLAN_HDR + count;
   if (first < last) {
-    // operand pieces at a 1024-aligned offset of the dynamic shared memory, one mbarrier for
-    // MMA completion
     uint8_t* ops = reinterpret_cast<uint8_t*>(smem);
     ops += (1024u - (smem_u32(ops) & 1023u)) & 1023u;
+    const uint32_t ops_s = smem_u32(ops);
+    const int w = int(threadIdx.x >> 5), q = w & 3, h = w >> 2, l = q * 32 + int(threadIdx.x & 31);
     if (threadIdx.x == 0) {
-      mbar_init(&tc_bar, 1);
+      mbar_init(&kb_bar[0], 1);
+      mbar_init(&kb_bar[1], 1);
       abort_word = 0;
       mbar_fence_init();
     }
@@ -618,14 +602,151 @@ __global__ void __launch_bounds__(BT_THREADS, 1) batched_tc_kernel(const Batched
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    uint32_t phase = 0;
-    while (true) {
-      if (threadIdx.x == 0) item = first + atomicAdd(p.queue, 1);
+    const int nslots = p.depth <= 2 ? 2 : 1;
+    TcSlot sl[2];
+    uint32_t phase[2] = {0u, 0u};
+    bool outstanding[2] = {false, false};
+    bool ok = true;
+
+    // next item of this class into slot s (masters loaded), or the slot left empty
+    auto fetch = [&](int s) {
+      if (threadIdx.x == 0) item_sh = first + atomicAdd(p.queue + cls, 1);
       __syncthreads();
-      const int it = item;
+      const int it = item_sh;
       __syncthreads();
-      if (it >= last) break;
-      dispatch_tc(p, items[4 * it + 0], items[4 * it + 1], ops, tmem, &tc_bar, phase, &abort_word, red_warp);
+      sl[s].b = -1;
+      if (it < last) {
+        const int b = p.plan[PLAN_HDR + items[4 * it + 1]];
+        sl[s] = {b, 0, 0, NN_OK, 0.f, 0.f};
+        tc_load_masters<U>(p.A + p.offsets[b], p.damping, tmem, uint32_t(s) * btc::SLOT_COLS, q, h, l);
+      }
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+    };
+    // every thread learns the same outcome of a wait on k-block kb's MMAs
+    auto wait_kb = [&](int kb) -> bool {
+      if (!outstanding[kb]) return true;
+      const bool r = __syncthreads_and(mbar_wait(&kb_bar[kb], phase[kb], &abort_word, p.err) ? 1 : 0) != 0;
+      phase[kb] ^= 1u;
+      outstanding[kb] = false;
+      tc_fence_after();
+      return r;
+    };
+    // stage k-block kb of slot s's next product (k-block 0 also writes the whole right operand,
+    // into the B buffer of this product's parity), then one thread issues its MMAs
+    uint32_t bsel = 0;
+    auto stage = [&](int s, int kb) {
+      const uint32_t sb = uint32_t(s) * btc::SLOT_COLS;
+      const TcProd pr = tc_product(sl[s], sb, p.depth);
+      tc_build_left<U>(tmem, pr.cP, ops + kb * btc::A_BLOCK, kb, q, h, l);
+      if (kb == 0) tc_build_right<U>(tmem, pr.cQ, ops + btc::B_OFF + bsel * btc::B_BUF, q, h, l);
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tc_fence_after();
+        const uint32_t b_s = ops_s + uint32_t(btc::B_OFF + bsel * btc::B_BUF);
+        if (kb == 0)
+          tc_issue<U, 0>(tmem + sb + btc::ACC, ops_s, b_s);
+        else
+          tc_issue<U, 1>(tmem + sb + btc::ACC, ops_s + uint32_t(btc::A_BLOCK), b_s + uint32_t(3 * btc::B_KB));
+        tc_commit(&kb_bar[kb]);
+      }
+      outstanding[kb] = true;
+      if (kb == 1) bsel ^= 1u;
+    };
+    // finish slot s's product (its MMAs complete): epilogue, residual test, next state; a
+    // finished matrix is written out and the slot refilled
+    auto finish = [&](int s) {
+      const uint32_t sb = uint32_t(s) * btc::SLOT_COLS;
+      const TcProd pr = tc_product(sl[s], sb, p.depth);
+      const float ss = tc_epilogue<U>(tmem, sb + btc::ACC, pr.cD, pr.cOut, pr.mode, q, h, l);
+      tc_fence_before();
+      bool done = false;
+      TcSlot& t = sl[s];
+      if (pr.mode == BM_RESID) {
+        const float sv = sqrtf(bt_block_sum(ss, red_warp)) / float(U);
+        t.s_last = sv;
+        if (!isfinite(sv) || (t.k >= 1 && sv >= 1.f && sv > t.s_prev)) {
+          t.st = NN_ERR_DIVERGED;
+          done = true;
+        }
+        t.s_prev = sv;
+        if (t.k == p.nests) done = true;
+      }
+      __syncthreads();
+      tc_fence_after();
+      if (!done) {
+        if (++t.j > p.depth) {
+          t.j = 0;
+          ++t.k;
+        }
+        return;
+      }
+      const int64_t off = p.offsets[t.b];
+      tc_store_x<U>(p.X + off, tmem, sb + btc::MX, q, h, l);
+      if (threadIdx.x == 0) {
+        p.residual[t.b] = t.s_last;
+        p.status[t.b] = t.st;
+      }
+      fetch(s);
+    };
+
+    for (int s = 0; s < nslots; ++s) fetch(s);
+    int pending = -1;  // slot whose product's MMAs are issued and whose epilogue is not done
+    while (ok) {
+      int m = -1;
+      if (pending >= 0)
+        m = (nslots == 2 && sl[1 - pending].b >= 0) ? 1 - pending : pending;
+      else if (sl[0].b >= 0)
+        m = 0;
+      else if (nslots == 2 && sl[1].b >= 0)
+        m = 1;
+      if (m < 0) break;
+      if (m == pending) {
+        // one slot in flight: its product completes before the next is staged
+        ok = wait_kb(1);
+        if (!ok) break;
+        finish(m);
+        pending = -1;
+        continue;
+      }
+      ok = wait_kb(0);
+      if (!ok) break;
+      stage(m, 0);
+      ok = wait_kb(1);
+      if (!ok) break;
+      stage(m, 1);
+      if (pending >= 0) finish(pending);
+      pending = m;
+    }
+    if (ok) ok = wait_kb(0) && wait_kb(1);
+    if (!ok) {
+      // a bounded wait ran out: the slots' matrices and every item not yet taken report
+      // NN_ERR_TIMEOUT (X unspecified); wait (bounded) for the issued MMAs before freeing TMEM
+      for (int s = 0; s < nslots; ++s)
+        if (sl[s].b >= 0 && threadIdx.x == 0) {
+          p.residual[sl[s].b] = sl[s].s_last;
+          p.status[sl[s].b] = NN_ERR_TIMEOUT;
+        }
+      while (true) {
+        if (threadIdx.x == 0) item_sh = first + atomicAdd(p.queue + cls, 1);
+        __syncthreads();
+        const int it = item_sh;
+        __syncthreads();
+        if (it >= last) break;
+        if (threadIdx.x == 0) {
+          const int b = p.plan[PLAN_HDR + items[4 * it + 1]];
+          p.residual[b] = 0.f;
+          p.status[b] = NN_ERR_TIMEOUT;
+        }
+      }
+      for (int kb = 0; kb < 2; ++kb)
+        if (outstanding[kb]) {
+          volatile int drain_flag = 0;
+          mbar_wait(&kb_bar[kb], phase[kb], &drain_flag, p.err);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -663,7 +784,7 @@ __global__ void __launch_bounds__(BT_THREADS, 2) batched_simt_kernel(const Batch
 using SimtKernel = void (*)(const BatchedParams, int);
 
 // Kernel of each CUDA-core class, in class order (bt_class).
-const SimtKernel kSimtKernels[BT_NCLS - 1] = {
+const SimtKernel kSimtKernels[BT_NCLS - 2] = {
     batched_simt_kernel<16, 4, 64>, batched_simt_kernel<16, 4, 0>, batched_simt_kernel<16, 3, 48>,
     batched_simt_kernel<16, 3, 0>,  batched_simt_kernel<16, 2, 32>, batched_simt_kernel<16, 2, 0>,
     batched_simt_kernel<16, 1, 16>, batched_simt_kernel<16, 1, 0>,  batched_simt_kernel<8, 4, 32>,
@@ -679,7 +800,8 @@ int bt_init() {
   int dev = 0;
   NN_CUDA_TRY(cudaGetDevice(&dev));
   NN_CUDA_TRY(cudaDeviceGetAttribute(&g_bt_sms, cudaDevAttrMultiProcessorCount, dev));
-  NN_CUDA_TRY(cudaFuncSetAttribute(batched_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
+  NN_CUDA_TRY(cudaFuncSetAttribute(batched_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
+  NN_CUDA_TRY(cudaFuncSetAttribute(batched_tc_kernel<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
   for (SimtKernel k : kSimtKernels)
     NN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM_SIMT_DEEP));
   g_bt_init = true;
@@ -726,7 +848,7 @@ int nn_batched_plan(const int32_t* sizes_host, int64_t count, const int32_t* cfg
     const int U = sizes_host[order[size_t(pos)]];
     int cfg = (cfg_by_u != nullptr && cfg_by_u[U] >= 0) ? cfg_by_u[U] : (U <= 32 ? 0 : 1);
     if (cfg < 0 || cfg > 2) return NN_ERR_ARG;
-    if (cfg == 2 && (U % 16 != 0 || U > 64)) cfg = U <= 32 ? 0 : 1;
+    if (cfg == 2 && U != 48 && U != 64) cfg = U <= 32 ? 0 : 1;
     if (cfg == 0 && (U + 7) / 8 > 4) cfg = 1;  // 8 x 8 threads with up to 4 x 4 elements each
     const int gmax = group_count(U, cfg);
     int cnt = 0;
@@ -753,7 +875,7 @@ int nn_batched_plan(const int32_t* sizes_host, int64_t count, const int32_t* cfg
   }
   class_first[BT_NCLS] = int32_t(w);
   plan_host[0] = int32_t(n_items);
-  plan_host[2] = class_first[1];
+  plan_host[2] = class_first[2];
   return NN_OK;
 }
 
@@ -786,19 +908,23 @@ int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* 
   p.queue = static_cast<int*>(workspace);
   p.err = static_cast<int*>(workspace) + BT_QUEUE_ERR;
   NN_CUDA_TRY(cudaMemsetAsync(p.queue, 0, nn_batched_workspace_bytes(count), st));
-  batched_tc_kernel<<<g_bt_sms, BT_THREADS, BT_SMEM, st>>>(p);
+  batched_tc_kernel<64><<<g_bt_sms, btc::THREADS, BT_SMEM, st>>>(p, 0);
   NN_CUDA_TRY(cudaGetLastError());
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(depth <= 2 ? 2 * g_bt_sms : g_bt_sms));
-  cfg.blockDim = dim3(BT_THREADS);
-  cfg.dynamicSmemBytes = size_t(depth <= 2 ? BT_SMEM_SIMT : BT_SMEM_SIMT_DEEP);
+  cfg.gridDim = dim3(unsigned(g_bt_sms));
+  cfg.blockDim = dim3(btc::THREADS);
+  cfg.dynamicSmemBytes = size_t(BT_SMEM);
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  for (int c = 1; c < BT_NCLS; ++c) NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kSimtKernels[c - 1], p, c));
+  NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, batched_tc_kernel<48>, p, 1));
+  cfg.gridDim = dim3(unsigned(depth <= 2 ? 2 * g_bt_sms : g_bt_sms));
+  cfg.blockDim = dim3(BT_THREADS);
+  cfg.dynamicSmemBytes = size_t(depth <= 2 ? BT_SMEM_SIMT : BT_SMEM_SIMT_DEEP);
+  for (int c = 2; c < BT_NCLS; ++c) NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kSimtKernels[c - 2], p, c));
   return NN_OK;
 }
 

@@ -73,13 +73,14 @@ def _header_int(name):
 
 
 def _plan_class(cfg, u):
-    """Tile class of an item as the header defines it: 0 = tensor cores; CUDA-core classes
-    ordered by threads per matrix (16 x 16 first), tile (4 down to 1), exact U first."""
+    """Tile class of an item as the header defines it: 0, 1 = tensor cores for U = 64, 48;
+    CUDA-core classes ordered by threads per matrix (16 x 16 first), tile (4 down to 1), exact
+    U first."""
     if cfg == 2:
-        return 0
+        return 0 if u == 64 else 1
     tg = 8 if cfg == 0 else 16
     t = -(-u // tg)
-    return 1 + (8 if cfg == 0 else 0) + (4 - t) * 2 + (0 if u % tg == 0 else 1)
+    return 2 + (8 if cfg == 0 else 0) + (4 - t) * 2 + (0 if u % tg == 0 else 1)
 
 
 @pytest.mark.parametrize("cfg_by_u", [None, {u: 0 for u in range(1, 33)}, {16: 2, 32: 2, 48: 2, 64: 2, 40: 2}])
@@ -102,7 +103,7 @@ def test_batched_plan_layout(lib, cfg_by_u):
     assert count == len(sizes) and len(plan) == hdr + 5 * count
     assert sorted(order.tolist()) == list(range(count))
     assert np.all(np.diff(sizes[order]) <= 0)
-    assert class_first[0] == 0 and class_first[-1] == n_items and n_tc == class_first[1]
+    assert class_first[0] == 0 and class_first[-1] == n_items and n_tc == class_first[2]
     assert np.all(np.diff(class_first) >= 0)
     covered = np.zeros(count, dtype=bool)
     for c in range(ncls):
@@ -113,11 +114,11 @@ def test_batched_plan_layout(lib, cfg_by_u):
             assert u <= prev_u
             prev_u = u
             assert 1 <= cnt and (cfg != 1 or cnt == 1) and (cfg != 2 or cnt == 1) and cnt <= 4
-            assert cfg != 2 or u in (16, 32, 48, 64)
+            assert cfg != 2 or u in (48, 64)
             assert cfg != 0 or u <= 32
             assert np.all(sizes[order[start:start + cnt]] == u)
             assert not covered[start:start + cnt].any()
             covered[start:start + cnt] = True
     assert covered.all()
     if cfg_by_u and cfg_by_u.get(64) == 2:
-        assert n_tc > 0 and all(int(items[i, 0]) in (16, 32, 48, 64) for i in range(n_tc))
+        assert n_tc > 0 and all(int(items[i, 0]) in (48, 64) for i in range(n_tc))
