@@ -35,7 +35,7 @@ namespace {
 
 constexpr int BT_THREADS = 256;
 constexpr int BT_MAX_U = 64;
-constexpr int BT_SMEM = 193 * 1024;         // dynamic shared memory of a tensor-core CTA
+constexpr int BT_SMEM = 212 * 1024;         // dynamic shared memory of a tensor-core CTA
 // CUDA-core items: two CTAs per SM at depth <= 2 (three buffers per matrix), one at depth >= 3
 // (four buffers, 4/3 of the same shared memory), so a plan sized for the first fits both.
 constexpr int BT_SMEM_SIMT = 112 * 1024;
@@ -281,43 +281,48 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
 
 // ---- tensor-core path (plan configuration 2; U in {48, 64}) --------------------------------
 //
-// Two matrices per CTA in a software pipeline, every iterate kept on chip:
-//   * masters (A, X, R; T at depth >= 3) live in TMEM as the real form [Re; Im] of each U x U
+// Two matrices per CTA, every iterate kept on chip:
+//   * masters (X, R; T at depth >= 3) live in TMEM as the real form [Re; Im] of each U x U
 //     complex matrix: lane i < U holds row i's real parts, lane U + i its imaginary parts,
-//     columns 0..U-1; each of the two pipeline slots owns 256 columns (A, X, R, accumulator);
-//   * a complex product C = P Q runs as one real MMA chain on the embedding
-//         [Cr; Ci] (2U x U) = [[Pr, -Pi], [Pi, Pr]] (2U x 2U) . [Qr; Qi] (2U x U),
-//     i.e. M = 128 (2U rows used), N = U, K = 2U. Its left operand is built from P's master
-//     rows, its right operand (K-major: row j = column j of [Qr; Qi]) is the transpose of Q's
-//     master (lane k, column j -> row j, k);
+//     columns 0..U-1; each of the two slots owns 256 columns (X, R, a 2U-column accumulator);
+//   * a complex product C = P Q is one real MMA chain
+//         D (2U x 2U) = [Pr; Pi] (2U x U) . [Qr | Qi] (U x 2U)
+//           = [[Pr Qr, Pr Qi], [Pi Qr, Pi Qi]],   Cr = Pr Qr - Pi Qi,  Ci = Pi Qr + Pr Qi,
+//     i.e. M = 128 (2U rows used), N = 2U, K = U. The left operand's rows are P's master lanes;
+//     the right operand (K-major: row n < U = column n of Qr, row U + n = column n of Qi) is the
+//     transpose of Q's master. A's left operand is split once per matrix and kept in shared
+//     memory (one copy per slot);
 //   * operands are split into three BF16 pieces (x = p0 + p1 + p2, each the BF16 rounding of the
-//     remainder) and written to shared memory in the SWIZZLE_128B K-major layout, one 64-wide
-//     k-block at a time; the six piece products with i + j <= 2 (smallest first) accumulate in
-//     FP32 in TMEM, which matches an FP32 product to about 2^-24 relative;
-//   * pipeline: while the tensor core runs k-block 0 of one slot's product, the CTA stages
-//     k-block 1 of its left operand; while it runs k-block 1, the CTA finishes the other slot's
-//     previous product (reads its accumulator, applies I - C or D + C in FP32, writes the result
-//     master, reduces the residual) and stages k-block 0 of that slot's next product together
-//     with its whole right operand (two right-operand buffers, alternating by product). Each
-//     buffer is reused once the MMAs that read it have completed (one mbarrier per k-block).
+//     remainder) and written in the SWIZZLE_128B K-major layout; the six piece products with
+//     i + j <= 2 (smallest first) accumulate in FP32 in TMEM, which matches an FP32 product to
+//     about 2^-24 relative;
+//   * epilogue: the real-part lanes need Pi Qi from the imaginary-part lanes and those need
+//     Pr Qi from the real-part lanes (other warps): the cross terms pass through shared memory,
+//     then I - C or D + C is applied in FP32 and written to the result master, and the residual's
+//     sum of squares is reduced across the CTA;
+//   * the two slots alternate: while the tensor core runs one slot's product, the CTA finishes
+//     the other slot's previous product; then it stages the other slot's next product once the
+//     MMAs (which read the single staging buffers) have completed.
 namespace btc {
 constexpr int M = 128;                         // MMA rows (2U used)
 constexpr int CW = 16;                         // master columns per warp (TMEM access: 32 lanes x 16)
 constexpr int WARPS = 4 * (64 / CW);           // warp (q, h): lane quadrant q, column block h
 constexpr int THREADS = 32 * WARPS;
-constexpr int NP = 64;                         // B-operand rows capacity (U used)
-constexpr int A_KB = M * 128;                  // one 64-wide k-block of one A piece: 16 KB
-constexpr int B_KB = NP * 128;                 // 8 KB
-constexpr int A_BLOCK = 3 * A_KB;              // k-block kb of the three A pieces at kb * A_BLOCK
-constexpr int B_OFF = 2 * A_BLOCK;             // two B buffers (products alternate) after them,
-constexpr int B_BUF = 2 * 3 * B_KB;            // each k-block kb of three pieces at kb * 3 * B_KB
-constexpr int OPS_BYTES = B_OFF + 2 * B_BUF;   // 192 KB
-constexpr uint32_t SLOT_COLS = 256;            // TMEM columns per pipeline slot
-constexpr uint32_t MA = 0, MX = 64, MR = 128, ACC = 192;
+constexpr int PIECE = 128 * 128;               // one piece: 128 rows x 64 BF16 (one SW128 k-block)
+constexpr int OPND = 3 * PIECE;                // an operand's three pieces: 48 KB
+constexpr int A_CACHE = 0;                     // the slots' left operands of A: 2 x 48 KB
+constexpr int L_STAGE = 2 * OPND;              // staged left operand
+constexpr int B_STAGE = 3 * OPND;              // staged right operand
+constexpr int EX = 4 * OPND;                   // cross-term exchange, per direction: U rows x EX_PITCH
+constexpr int EX_PITCH = 32 + 4;               // floats: half of each row per phase (float4, no conflicts)
+constexpr int EX_DIR = 64 * EX_PITCH;          // floats per direction
+constexpr int OPS_BYTES = EX + 2 * EX_DIR * 4;
+constexpr uint32_t SLOT_COLS = 256;            // TMEM columns per slot
+constexpr uint32_t MX = 0, MR = 64, ACC = 128;
 constexpr uint32_t MT = 256;                   // T master (depth >= 3: one slot only)
 constexpr uint32_t TMEM_COLS = 512;
-static_assert(OPS_BYTES + 1024 <= BT_SMEM, "operand pieces fit the dynamic shared memory");
-static_assert(A_KB % 1024 == 0 && B_KB % 1024 == 0, "swizzle atoms stay aligned");
+static_assert(OPS_BYTES + 1024 <= BT_SMEM, "operands fit the dynamic shared memory");
+static_assert(PIECE % 1024 == 0 && EX % 16 == 0, "swizzle atoms and float4 rows stay aligned");
 }  // namespace btc
 
 // TMEM access of a warp's 32 lanes x btc::CW columns.
@@ -351,129 +356,155 @@ __device__ __forceinline__ void split3x2(float a, float b, uint32_t& w0, uint32_
   w2 = *reinterpret_cast<uint32_t*>(&v);
 }
 
-// k-block kb of the left operand [[Pr, -Pi], [Pi, Pr]] (three pieces) from master P; warp
-// (q, h) owns lanes 32q.. and columns 32h.. of the master. Row i takes K = column (real part)
-// or U + column (negated imaginary part); row U + i takes K = U + column (real part) or column
-// (imaginary part). An 8-column chunk never straddles a k-block (U is a multiple of 16); the
-// pieces of -x are those of x with the sign bits flipped.
+// Pieces of CW consecutive values of one left-operand row (K = col0 .. col0 + CW - 1, col0 a
+// multiple of 8; values at K >= U are not written).
 template <int U>
-__device__ __forceinline__ void tc_build_left(uint32_t tmem, uint32_t cP, uint8_t* ablk, int kb, int q, int h,
-                                              int l) {
-  if (h * btc::CW >= U) return;
-  uint32_t raw[btc::CW];
-  tmem_ld_cw(tmem + (uint32_t(q * 32) << 16) + cP + uint32_t(h * btc::CW), raw);
-  tmem_ld_wait();
-  if (l >= 2 * U) return;
-  const bool re = l < U;
-  const int i = re ? l : l - U;
-  const int kbase0 = re ? 0 : U, kbase1 = re ? U : 0;
-  const uint32_t flip0 = re ? 0u : 0x80008000u;
+__device__ __forceinline__ void tc_row_pieces(const uint32_t (&v)[btc::CW], uint8_t* dst, int row, int col0) {
 #pragma unroll
   for (int ch = 0; ch < btc::CW / 8; ++ch) {
-    const int j0 = h * btc::CW + ch * 8;
+    const int j0 = col0 + ch * 8;
     if (j0 >= U) break;
-    const int K0 = kbase0 + j0, K1 = kbase1 + j0;
-    const bool n0 = (K0 >> 6) == kb, n1 = (K1 >> 6) == kb;
-    if (!n0 && !n1) continue;
     uint32_t w[3][4];
 #pragma unroll
     for (int e = 0; e < 4; ++e)
-      split3x2(__uint_as_float(raw[ch * 8 + 2 * e]), __uint_as_float(raw[ch * 8 + 2 * e + 1]), w[0][e], w[1][e],
-               w[2][e]);
-    if (n0) {
-      const uint32_t off = bt_sw128_offset(i, K0 & 63);
+      split3x2(__uint_as_float(v[ch * 8 + 2 * e]), __uint_as_float(v[ch * 8 + 2 * e + 1]), w[0][e], w[1][e], w[2][e]);
+    const uint32_t off = bt_sw128_offset(row, j0);
 #pragma unroll
-      for (int pc = 0; pc < 3; ++pc)
-        *reinterpret_cast<uint4*>(ablk + pc * btc::A_KB + off) =
-            make_uint4(w[pc][0] ^ flip0, w[pc][1] ^ flip0, w[pc][2] ^ flip0, w[pc][3] ^ flip0);
-    }
-    if (n1) {
-      const uint32_t off = bt_sw128_offset(U + i, K1 & 63);
-#pragma unroll
-      for (int pc = 0; pc < 3; ++pc)
-        *reinterpret_cast<uint4*>(ablk + pc * btc::A_KB + off) = make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
-    }
+    for (int pc = 0; pc < 3; ++pc)
+      *reinterpret_cast<uint4*>(dst + pc * btc::PIECE + off) = make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
   }
 }
 
-// Both k-blocks of the right operand pieces: row j, column k = master Q (lane k, column j); warp
-// q's lanes fall in k-block q / 2. The pair (k, k + 1) of column j is split and stored by the
-// even lane for the first 16 columns of the warp's block and by the odd lane for the rest.
+// Right operand [Qr | Qi] (K-major) from master Q values raw (this thread's lane l, columns
+// h CW ..): master lane r, column c goes to row c (+ U for r >= U), column k = r mod U. The pair
+// (k, k + 1) of a column is split and stored by the even lane for the first CW/2 columns of the
+// warp's block and by the odd lane for the rest (U is even, so a pair never straddles the real
+// and imaginary lanes). Every lane of the warp calls it (shuffles).
 template <int U>
-__device__ __forceinline__ void tc_build_right(uint32_t tmem, uint32_t cQ, uint8_t* bbuf, int q, int h, int l) {
-  if (h * btc::CW >= U || q * 32 >= 2 * U) return;
-  uint32_t raw[btc::CW];
-  tmem_ld_cw(tmem + (uint32_t(q * 32) << 16) + cQ + uint32_t(h * btc::CW), raw);
-  tmem_ld_wait();
-  uint8_t* bops = bbuf + (q >> 1) * 3 * btc::B_KB;
+__device__ __forceinline__ void tc_right_pieces(const uint32_t (&raw)[btc::CW], uint8_t* dst, int h, int l) {
   const bool odd = (l & 1) != 0;
-  const int kk = (l & 63) & ~1;
+  const bool re = l < U;
+  const int kk = (re ? l : l - U) & ~1;
+  // rows (re ? 0 : U) + h CW + (odd ? CW/2 : 0) + t: a multiple of 8 plus t < 8
+  const int row8 = ((re ? 0 : U) + h * btc::CW + (odd ? btc::CW / 2 : 0)) >> 3;
+  uint8_t* base = dst + row8 * 1024 + ((kk & 7) << 1);
+  const int kc = kk >> 3;
+  const bool store = l < 2 * U;
 #pragma unroll
   for (int t = 0; t < btc::CW / 2; ++t) {
     const float lo_v = __uint_as_float(raw[t]), hi_v = __uint_as_float(raw[btc::CW / 2 + t]);
-    const float from_next = __shfl_down_sync(0xffffffffu, lo_v, 1);  // even lanes: k + 1, column t
-    const float from_prev = __shfl_up_sync(0xffffffffu, hi_v, 1);    // odd lanes: k - 1, column CW/2 + t
-    const int j = h * btc::CW + (odd ? btc::CW / 2 + t : t);
-    if (j < U) {
+    const float from_next = __shfl_down_sync(0xffffffffu, lo_v, 1);  // even lanes: k + 1
+    const float from_prev = __shfl_up_sync(0xffffffffu, hi_v, 1);    // odd lanes: k - 1
+    if (store) {
       uint32_t w0, w1, w2;
-      if (odd)
-        split3x2(from_prev, hi_v, w0, w1, w2);
-      else
-        split3x2(lo_v, from_next, w0, w1, w2);
-      const uint32_t off = bt_sw128_offset(j, kk);
-      *reinterpret_cast<uint32_t*>(bops + off) = w0;
-      *reinterpret_cast<uint32_t*>(bops + btc::B_KB + off) = w1;
-      *reinterpret_cast<uint32_t*>(bops + 2 * btc::B_KB + off) = w2;
+      split3x2(odd ? from_prev : lo_v, odd ? hi_v : from_next, w0, w1, w2);
+      uint8_t* at = base + t * 128 + ((kc ^ t) << 4);
+      *reinterpret_cast<uint32_t*>(at) = w0;
+      *reinterpret_cast<uint32_t*>(at + btc::PIECE) = w1;
+      *reinterpret_cast<uint32_t*>(at + 2 * btc::PIECE) = w2;
     }
   }
 }
 
-// One thread: the MMAs of k-block KB (K = 64, or 2U - 64 for the second block) into d_tmem,
-// piece pairs (a, b) smallest terms first: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0).
-template <int U, int KB>
-__device__ __forceinline__ void tc_issue(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr) {
+// Stages one product: the left operand [Pr; Pi] from master P (row r = master lane r; not for
+// the residual, whose left operand is A's cached pieces) and the right operand from master Q;
+// warp (q, h) owns lanes 32q.. and columns h CW...
+template <int U>
+__device__ __forceinline__ void tc_stage(uint32_t tmem, bool left, uint32_t cP, uint32_t cQ, uint8_t* ldst,
+                                         uint8_t* bdst, int q, int h, int l) {
+  if (h * btc::CW >= U) return;
+  const uint32_t lane_off = uint32_t(q * 32) << 16;
+  uint32_t rp[btc::CW], rq[btc::CW];
+  if (left) tmem_ld_cw(tmem + lane_off + cP + uint32_t(h * btc::CW), rp);
+  tmem_ld_cw(tmem + lane_off + cQ + uint32_t(h * btc::CW), rq);
+  tmem_ld_wait();
+  if (q * 32 >= 2 * U) return;  // warp-uniform: 2U is a multiple of 32
+  if (left && l < 2 * U) tc_row_pieces<U>(rp, ldst, l, h * btc::CW);
+  tc_right_pieces<U>(rq, bdst, h, l);
+}
+
+// One thread: the MMA chain D = L B^T (K = U) into d_tmem, piece pairs (a, b) smallest terms
+// first: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0).
+template <int U>
+__device__ __forceinline__ void tc_issue(uint32_t d_tmem, uint32_t l_saddr, uint32_t b_saddr) {
   constexpr uint32_t idesc =
-      (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(U >> 3) << 17) | (uint32_t(btc::M >> 4) << 24);
-  constexpr int ksteps = KB == 0 ? 4 : (2 * U - 64) / 16;
-  const uint64_t ad = bt_sw128_desc(a_saddr), bd = bt_sw128_desc(b_saddr);
+      (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t((2 * U) >> 3) << 17) | (uint32_t(btc::M >> 4) << 24);
+  const uint64_t ld = bt_sw128_desc(l_saddr), bd = bt_sw128_desc(b_saddr);
 #pragma unroll
   for (int pp = 0; pp < 6; ++pp) {
     const int pa = pp == 0 ? 2 : (pp == 1 || pp == 3) ? 1 : 0;
     const int pb = pp == 2 ? 2 : (pp == 1 || pp == 4) ? 1 : 0;
 #pragma unroll
-    for (int st = 0; st < ksteps; ++st)
-      tc_mma_bf16(d_tmem, ad + uint64_t((pa * btc::A_KB) >> 4) + uint64_t(2 * st),
-                  bd + uint64_t((pb * btc::B_KB) >> 4) + uint64_t(2 * st), idesc,
-                  (KB == 0 && pp == 0 && st == 0) ? 0u : 1u);
+    for (int st = 0; st < U / 16; ++st)
+      tc_mma_bf16(d_tmem, ld + uint64_t((pa * btc::PIECE) >> 4) + uint64_t(2 * st),
+                  bd + uint64_t((pb * btc::PIECE) >> 4) + uint64_t(2 * st), idesc, (pp | st) != 0 ? 1u : 0u);
   }
 }
 
-// out = mode(accumulator) on this warp's 32 x 32 block of the real form; returns this
-// thread's sum of squares of the result (residual mode, valid lanes and columns only).
+// out = mode(C) from the accumulator D of a product (see above) on this warp's 32 x CW block
+// of the real form; returns this thread's sum of squares of the result (residual mode, valid
+// lanes only). Every thread of the CTA calls it (three CTA barriers inside).
 template <int U>
 __device__ __forceinline__ float tc_epilogue(uint32_t tmem, uint32_t cAcc, uint32_t cD, uint32_t cOut, int mode,
-                                             int q, int h, int l) {
-  float local = 0.f;
-  if (h * btc::CW >= U) return local;
-  uint32_t c[btc::CW], d[btc::CW];
+                                             float* ex, int q, int h, int l) {
+  // Every warp reads and writes its block, also a block of columns >= U (U = 48): those lie
+  // inside the accumulator's 2U and the masters' 64 columns and carry no data (zeros written).
+  const bool valid = h * btc::CW < U && l < 2 * U;
+  const bool re = l < U;
+  const int i = re ? l : l - U;
   const uint32_t lane_off = uint32_t(q * 32) << 16;
-  tmem_ld_cw(tmem + lane_off + cAcc + uint32_t(h * btc::CW), c);
-  if (mode == BM_ADD) tmem_ld_cw(tmem + lane_off + cD + uint32_t(h * btc::CW), d);
+  uint32_t dd[btc::CW], dx[btc::CW], dm[btc::CW];
+  tmem_ld_cw(tmem + lane_off + cAcc + uint32_t(h * btc::CW), dd);
+  tmem_ld_cw(tmem + lane_off + cAcc + uint32_t(U + h * btc::CW), dx);
+  if (mode == BM_ADD) tmem_ld_cw(tmem + lane_off + cD + uint32_t(h * btc::CW), dm);
   tmem_ld_wait();
+  // cross terms: real-part lanes need Pi Qi (Cr = Pr Qr - Pi Qi), imaginary-part lanes need
+  // Pr Qi (Ci = Pi Qr + Pr Qi); each lane publishes its own cross term (dx) in direction re / im
+  // and reads its partner's, half of its columns per phase so that every warp works each phase
+  float* mine = ex + (re ? 0 : btc::EX_DIR) + i * btc::EX_PITCH + h * (btc::CW / 2);
+  const float* theirs = ex + (re ? btc::EX_DIR : 0) + i * btc::EX_PITCH + h * (btc::CW / 2);
+  const float sgn = re ? -1.f : 1.f;
+#pragma unroll
+  for (int ph = 0; ph < 2; ++ph) {
+    if (valid) {
+#pragma unroll
+      for (int t = 0; t < btc::CW / 8; ++t) {
+        const int c0 = ph * (btc::CW / 2) + 4 * t;
+        reinterpret_cast<float4*>(mine)[t] = make_float4(__uint_as_float(dx[c0]), __uint_as_float(dx[c0 + 1]),
+                                                         __uint_as_float(dx[c0 + 2]), __uint_as_float(dx[c0 + 3]));
+      }
+    }
+    __syncthreads();
+    if (valid) {
+#pragma unroll
+      for (int t = 0; t < btc::CW / 8; ++t) {
+        const int c0 = ph * (btc::CW / 2) + 4 * t;
+        const float4 x = reinterpret_cast<const float4*>(theirs)[t];
+        dd[c0] = __float_as_uint(fmaf(sgn, x.x, __uint_as_float(dd[c0])));
+        dd[c0 + 1] = __float_as_uint(fmaf(sgn, x.y, __uint_as_float(dd[c0 + 1])));
+        dd[c0 + 2] = __float_as_uint(fmaf(sgn, x.z, __uint_as_float(dd[c0 + 2])));
+        dd[c0 + 3] = __float_as_uint(fmaf(sgn, x.w, __uint_as_float(dd[c0 + 3])));
+      }
+    }
+    if (ph == 0) __syncthreads();
+  }
+  float local = 0.f;
 #pragma unroll
   for (int t = 0; t < btc::CW; ++t) {
     const int j = h * btc::CW + t;
-    const float cv = __uint_as_float(c[t]);
-    float v;
-    if (mode == BM_RESID) {
-      v = ((l < U && j == l) ? 1.f : 0.f) - cv;
-      if (l < 2 * U && j < U) local = fmaf(v, v, local);
-    } else {
-      v = __uint_as_float(d[t]) + cv;
+    const float cv = __uint_as_float(dd[t]);
+    float v = 0.f;
+    if (valid) {
+      if (mode == BM_RESID) {
+        v = ((re && j == i) ? 1.f : 0.f) - cv;
+        local = fmaf(v, v, local);
+      } else {
+        v = __uint_as_float(dm[t]) + cv;
+      }
     }
-    c[t] = __float_as_uint(v);
+    dd[t] = __float_as_uint(v);
   }
-  tmem_st_cw(tmem + lane_off + cOut + uint32_t(h * btc::CW), c);
+  tmem_st_cw(tmem + lane_off + cOut + uint32_t(h * btc::CW), dd);
   tmem_st_wait();
   return local;
 }
@@ -490,56 +521,78 @@ __device__ __forceinline__ float bt_block_sum(float v, float* red_warp) {
   return t;
 }
 
-// Masters A and X_0 = c diag(A)^-1 (damped Jacobi) of matrix A (device, row-major) in their
-// real forms at slot columns sb + MA, sb + MX; rows >= 2U are zero.
+// A new matrix into a slot: A (U x U complex, row-major) is read coalesced into the slot's
+// cache area (free: its previous matrix is done), each thread takes its row part, and after a
+// CTA barrier the pieces of A's left operand [Ar; Ai] overwrite the area; X_0 = c diag(A)^-1
+// (damped Jacobi) goes to the X master at column cX (rows >= 2U zero). Every thread calls it.
 template <int U>
-__device__ __forceinline__ void tc_load_masters(const float2* A, float damping, uint32_t tmem, uint32_t sb, int q,
-                                                int h, int l) {
-  if (h * btc::CW >= U) return;
-  uint32_t va[btc::CW], vx[btc::CW];
-  const bool valid_row = l < 2 * U;
+__device__ __forceinline__ void tc_load_matrix(const float2* A, float damping, uint8_t* acache, uint32_t tmem,
+                                               uint32_t cX, int q, int h, int l) {
+  // matrices of any size are packed back to back, so A is 8- but not always 16-byte aligned
+  if ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) {
+    const float4* src = reinterpret_cast<const float4*>(A);
+    for (int e = threadIdx.x; e < U * U / 2; e += btc::THREADS) reinterpret_cast<float4*>(acache)[e] = __ldg(src + e);
+  } else {
+    for (int e = threadIdx.x; e < U * U; e += btc::THREADS) reinterpret_cast<float2*>(acache)[e] = __ldg(A + e);
+  }
+  __syncthreads();
+  const bool active = h * btc::CW < U;
+  const bool valid_row = active && l < 2 * U;
   const bool re = l < U;
   const int i = re ? l : l - U;
+  uint32_t va[btc::CW], vx[btc::CW];
+  const float* Af = reinterpret_cast<const float*>(acache);
   float2 aii = make_float2(1.f, 0.f);
-  if (valid_row) aii = A[i * U + i];
+  if (valid_row) aii = reinterpret_cast<const float2*>(acache)[i * U + i];
   const float cdamp = 1.f / (1.f + damping * float(U));
   const float den = aii.x * aii.x + aii.y * aii.y;
 #pragma unroll
   for (int t = 0; t < btc::CW; ++t) {
     const int j = h * btc::CW + t;
     float av = 0.f, xv = 0.f;
-    if (valid_row && j < U) {
-      const float2 a = A[i * U + j];
-      av = re ? a.x : a.y;
+    if (valid_row) {
+      av = Af[2 * (i * U + j) + (re ? 0 : 1)];
       if (j == i) xv = re ? cdamp * aii.x / den : -cdamp * aii.y / den;
     }
     va[t] = __float_as_uint(av);
     vx[t] = __float_as_uint(xv);
   }
-  const uint32_t lane_off = uint32_t(q * 32) << 16;
-  tmem_st_cw(tmem + lane_off + sb + btc::MA + uint32_t(h * btc::CW), va);
-  tmem_st_cw(tmem + lane_off + sb + btc::MX + uint32_t(h * btc::CW), vx);
-  tmem_st_wait();
-}
-
-// X (complex, row-major) from the X master at column cX.
-template <int U>
-__device__ __forceinline__ void tc_store_x(float2* X, uint32_t tmem, uint32_t cX, int q, int h, int l) {
-  if (h * btc::CW >= U || q * 32 >= 2 * U) return;  // 2U is a multiple of 32: warp-uniform
-  uint32_t vx[btc::CW];
-  tmem_ld_cw(tmem + (uint32_t(q * 32) << 16) + cX + uint32_t(h * btc::CW), vx);
-  tmem_ld_wait();
-  const bool re = l < U;
-  const int i = re ? l : l - U;
-  float* Xf = reinterpret_cast<float*>(X);
-#pragma unroll
-  for (int t = 0; t < btc::CW; ++t) {
-    const int j = h * btc::CW + t;
-    if (j < U) Xf[2 * (i * U + j) + (re ? 0 : 1)] = __uint_as_float(vx[t]);
+  __syncthreads();
+  if (valid_row) tc_row_pieces<U>(va, acache, l, h * btc::CW);
+  if (active) {
+    tmem_st_cw(tmem + (uint32_t(q * 32) << 16) + cX + uint32_t(h * btc::CW), vx);
+    tmem_st_wait();
   }
 }
 
-// Pipeline slot state (identical in every thread: all updates are CTA-uniform).
+// X (complex, row-major) from the X master at column cX, through the slot's cache area (free:
+// its matrix is done) so that the global writes are coalesced. Every thread calls it.
+template <int U>
+__device__ __forceinline__ void tc_store_x(float2* X, uint32_t tmem, uint32_t cX, uint8_t* acache, int q, int h,
+                                           int l) {
+  float* xs = reinterpret_cast<float*>(acache);
+  if (h * btc::CW < U) {
+    uint32_t vx[btc::CW];
+    tmem_ld_cw(tmem + (uint32_t(q * 32) << 16) + cX + uint32_t(h * btc::CW), vx);
+    tmem_ld_wait();
+    if (l < 2 * U) {
+      const bool re = l < U;
+      const int i = re ? l : l - U;
+#pragma unroll
+      for (int t = 0; t < btc::CW; ++t) xs[2 * (i * U + h * btc::CW + t) + (re ? 0 : 1)] = __uint_as_float(vx[t]);
+    }
+  }
+  __syncthreads();
+  if ((reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
+    for (int e = threadIdx.x; e < U * U / 2; e += btc::THREADS)
+      reinterpret_cast<float4*>(X)[e] = reinterpret_cast<const float4*>(xs)[e];
+  } else {
+    for (int e = threadIdx.x; e < U * U; e += btc::THREADS) X[e] = reinterpret_cast<const float2*>(xs)[e];
+  }
+  __syncthreads();
+}
+
+// Slot state (identical in every thread: all updates are CTA-uniform).
 struct TcSlot {
   int b;          // matrix index, -1 = empty
   int k, j;       // nest, product within the nest (0 = residual, 1..L-1 Horner, L = update)
@@ -547,7 +600,8 @@ struct TcSlot {
   float s_prev, s_last;
 };
 
-// Columns of the product that slot s at state (k, j) runs next.
+// Masters of the product that a slot at state (k, j) runs next (the residual's left operand is
+// A's cached pieces).
 struct TcProd {
   uint32_t cP, cQ, cD, cOut;
   int mode;
@@ -556,7 +610,7 @@ struct TcProd {
 __device__ __forceinline__ TcProd tc_product(const TcSlot& s, uint32_t sb, int depth) {
   TcProd r;
   if (s.j == 0) {
-    r = {sb + btc::MA, sb + btc::MX, 0u, sb + btc::MR, BM_RESID};
+    r = {0u, sb + btc::MX, 0u, sb + btc::MR, BM_RESID};
   } else if (s.j < depth) {
     // Horner T_{j+1} = R + R T_j; at depth 2 it replaces R in place
     r = {sb + btc::MR, s.j == 1 ? sb + btc::MR : btc::MT, sb + btc::MR, depth == 2 ? sb + btc::MR : btc::MT, BM_ADD};
@@ -572,14 +626,13 @@ __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepc
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // The tensor-core items of size U (classes 0 and 1): one CTA per SM, 512 TMEM columns, two
-// pipeline slots at depth <= 2 (one at depth >= 3, whose T master takes the second slot's
-// columns).
+// slots at depth <= 2 (one at depth >= 3, whose T master takes the second slot's columns).
 template <int U>
 __global__ void __launch_bounds__(btc::THREADS, 1) batched_tc_kernel(const BatchedParams p, int cls) {
   extern __shared__ float2 smem[];
   __shared__ float red_warp[btc::WARPS];
   __shared__ int item_sh;
-  __shared__ __align__(8) uint64_t kb_bar[2];
+  __shared__ __align__(8) uint64_t mma_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_word;
   pdl_launch_dependents();
@@ -590,10 +643,10 @@ __global__ void __launch_bounds__(btc::THREADS, 1) batched_tc_kernel(const Batch
     uint8_t* ops = reinterpret_cast<uint8_t*>(smem);
     ops += (1024u - (smem_u32(ops) & 1023u)) & 1023u;
     const uint32_t ops_s = smem_u32(ops);
+    float* ex = reinterpret_cast<float*>(ops + btc::EX);
     const int w = int(threadIdx.x >> 5), q = w & 3, h = w >> 2, l = q * 32 + int(threadIdx.x & 31);
     if (threadIdx.x == 0) {
-      mbar_init(&kb_bar[0], 1);
-      mbar_init(&kb_bar[1], 1);
+      mbar_init(&mma_bar, 1);
       abort_word = 0;
       mbar_fence_init();
     }
@@ -603,68 +656,66 @@ __global__ void __launch_bounds__(btc::THREADS, 1) batched_tc_kernel(const Batch
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     const int nslots = p.depth <= 2 ? 2 : 1;
-    TcSlot sl[2];
-    uint32_t phase[2] = {0u, 0u};
-    bool outstanding[2] = {false, false};
+    TcSlot sl0 = {-1, 0, 0, NN_OK, 0.f, 0.f}, sl1 = sl0;  // two named slots: no local memory
+    uint32_t phase = 0;
+    bool outstanding = false;
     bool ok = true;
 
-    // next item of this class into slot s (masters loaded), or the slot left empty
+    // next item of this class into slot s, or the slot left empty
     auto fetch = [&](int s) {
       if (threadIdx.x == 0) item_sh = first + atomicAdd(p.queue + cls, 1);
       __syncthreads();
       const int it = item_sh;
       __syncthreads();
-      sl[s].b = -1;
+      TcSlot t = {-1, 0, 0, NN_OK, 0.f, 0.f};
       if (it < last) {
-        const int b = p.plan[PLAN_HDR + items[4 * it + 1]];
-        sl[s] = {b, 0, 0, NN_OK, 0.f, 0.f};
-        tc_load_masters<U>(p.A + p.offsets[b], p.damping, tmem, uint32_t(s) * btc::SLOT_COLS, q, h, l);
+        t.b = p.plan[PLAN_HDR + items[4 * it + 1]];
+        tc_load_matrix<U>(p.A + p.offsets[t.b], p.damping, ops + btc::A_CACHE + s * btc::OPND, tmem,
+                          uint32_t(s) * btc::SLOT_COLS + btc::MX, q, h, l);
       }
+      if (s == 0)
+        sl0 = t;
+      else
+        sl1 = t;
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
     };
-    // every thread learns the same outcome of a wait on k-block kb's MMAs
-    auto wait_kb = [&](int kb) -> bool {
-      if (!outstanding[kb]) return true;
-      const bool r = __syncthreads_and(mbar_wait(&kb_bar[kb], phase[kb], &abort_word, p.err) ? 1 : 0) != 0;
-      phase[kb] ^= 1u;
-      outstanding[kb] = false;
+    // every thread learns the same outcome of the wait on the last issued MMA chain
+    auto wait_mma = [&]() -> bool {
+      if (!outstanding) return true;
+      const bool r = __syncthreads_and(mbar_wait(&mma_bar, phase, &abort_word, p.err) ? 1 : 0) != 0;
+      phase ^= 1u;
+      outstanding = false;
       tc_fence_after();
       return r;
     };
-    // stage k-block kb of slot s's next product (k-block 0 also writes the whole right operand,
-    // into the B buffer of this product's parity), then one thread issues its MMAs
-    uint32_t bsel = 0;
-    auto stage = [&](int s, int kb) {
+    // stage slot s's next product, then one thread issues its MMA chain
+    auto stage = [&](int s) {
       const uint32_t sb = uint32_t(s) * btc::SLOT_COLS;
-      const TcProd pr = tc_product(sl[s], sb, p.depth);
-      tc_build_left<U>(tmem, pr.cP, ops + kb * btc::A_BLOCK, kb, q, h, l);
-      if (kb == 0) tc_build_right<U>(tmem, pr.cQ, ops + btc::B_OFF + bsel * btc::B_BUF, q, h, l);
+      const TcProd pr = tc_product(s == 0 ? sl0 : sl1, sb, p.depth);
+      tc_stage<U>(tmem, pr.mode != BM_RESID, pr.cP, pr.cQ, ops + btc::L_STAGE, ops + btc::B_STAGE, q, h, l);
       fence_proxy_async_smem();
       tc_fence_before();
       __syncthreads();
       if (threadIdx.x == 0) {
         tc_fence_after();
-        const uint32_t b_s = ops_s + uint32_t(btc::B_OFF + bsel * btc::B_BUF);
-        if (kb == 0)
-          tc_issue<U, 0>(tmem + sb + btc::ACC, ops_s, b_s);
-        else
-          tc_issue<U, 1>(tmem + sb + btc::ACC, ops_s + uint32_t(btc::A_BLOCK), b_s + uint32_t(3 * btc::B_KB));
-        tc_commit(&kb_bar[kb]);
+        const uint32_t lop = pr.mode == BM_RESID ? ops_s + uint32_t(btc::A_CACHE + s * btc::OPND)
+                                                 : ops_s + uint32_t(btc::L_STAGE);
+        tc_issue<U>(tmem + sb + btc::ACC, lop, ops_s + uint32_t(btc::B_STAGE));
+        tc_commit(&mma_bar);
       }
-      outstanding[kb] = true;
-      if (kb == 1) bsel ^= 1u;
+      outstanding = true;
     };
     // finish slot s's product (its MMAs complete): epilogue, residual test, next state; a
     // finished matrix is written out and the slot refilled
     auto finish = [&](int s) {
       const uint32_t sb = uint32_t(s) * btc::SLOT_COLS;
-      const TcProd pr = tc_product(sl[s], sb, p.depth);
-      const float ss = tc_epilogue<U>(tmem, sb + btc::ACC, pr.cD, pr.cOut, pr.mode, q, h, l);
+      TcSlot t = s == 0 ? sl0 : sl1;
+      const TcProd pr = tc_product(t, sb, p.depth);
+      const float ss = tc_epilogue<U>(tmem, sb + btc::ACC, pr.cD, pr.cOut, pr.mode, ex, q, h, l);
       tc_fence_before();
       bool done = false;
-      TcSlot& t = sl[s];
       if (pr.mode == BM_RESID) {
         const float sv = sqrtf(bt_block_sum(ss, red_warp)) / float(U);
         t.s_last = sv;
@@ -682,10 +733,13 @@ __global__ void __launch_bounds__(btc::THREADS, 1) batched_tc_kernel(const Batch
           t.j = 0;
           ++t.k;
         }
+        if (s == 0)
+          sl0 = t;
+        else
+          sl1 = t;
         return;
       }
-      const int64_t off = p.offsets[t.b];
-      tc_store_x<U>(p.X + off, tmem, sb + btc::MX, q, h, l);
+      tc_store_x<U>(p.X + p.offsets[t.b], tmem, sb + btc::MX, ops + btc::A_CACHE + s * btc::OPND, q, h, l);
       if (threadIdx.x == 0) {
         p.residual[t.b] = t.s_last;
         p.status[t.b] = t.st;
@@ -698,38 +752,38 @@ __global__ void __launch_bounds__(btc::THREADS, 1) batched_tc_kernel(const Batch
     while (ok) {
       int m = -1;
       if (pending >= 0)
-        m = (nslots == 2 && sl[1 - pending].b >= 0) ? 1 - pending : pending;
-      else if (sl[0].b >= 0)
+        m = (nslots == 2 && (pending == 0 ? sl1 : sl0).b >= 0) ? 1 - pending : pending;
+      else if (sl0.b >= 0)
         m = 0;
-      else if (nslots == 2 && sl[1].b >= 0)
+      else if (nslots == 2 && sl1.b >= 0)
         m = 1;
       if (m < 0) break;
+      ok = wait_mma();  // staging buffers free, the pending product's accumulator final
+      if (!ok) break;
       if (m == pending) {
         // one slot in flight: its product completes before the next is staged
-        ok = wait_kb(1);
-        if (!ok) break;
         finish(m);
         pending = -1;
         continue;
       }
-      ok = wait_kb(0);
-      if (!ok) break;
-      stage(m, 0);
-      ok = wait_kb(1);
-      if (!ok) break;
-      stage(m, 1);
+      stage(m);
       if (pending >= 0) finish(pending);
       pending = m;
     }
-    if (ok) ok = wait_kb(0) && wait_kb(1);
+    if (ok) ok = wait_mma();
     if (!ok) {
       // a bounded wait ran out: the slots' matrices and every item not yet taken report
       // NN_ERR_TIMEOUT (X unspecified); wait (bounded) for the issued MMAs before freeing TMEM
-      for (int s = 0; s < nslots; ++s)
-        if (sl[s].b >= 0 && threadIdx.x == 0) {
-          p.residual[sl[s].b] = sl[s].s_last;
-          p.status[sl[s].b] = NN_ERR_TIMEOUT;
+      if (threadIdx.x == 0) {
+        if (sl0.b >= 0) {
+          p.residual[sl0.b] = sl0.s_last;
+          p.status[sl0.b] = NN_ERR_TIMEOUT;
         }
+        if (nslots == 2 && sl1.b >= 0) {
+          p.residual[sl1.b] = sl1.s_last;
+          p.status[sl1.b] = NN_ERR_TIMEOUT;
+        }
+      }
       while (true) {
         if (threadIdx.x == 0) item_sh = first + atomicAdd(p.queue + cls, 1);
         __syncthreads();
@@ -742,11 +796,10 @@ __global__ void __launch_bounds__(btc::THREADS, 1) batched_tc_kernel(const Batch
           p.status[b] = NN_ERR_TIMEOUT;
         }
       }
-      for (int kb = 0; kb < 2; ++kb)
-        if (outstanding[kb]) {
-          volatile int drain_flag = 0;
-          mbar_wait(&kb_bar[kb], phase[kb], &drain_flag, p.err);
-        }
+      if (outstanding) {
+        volatile int drain_flag = 0;
+        mbar_wait(&mma_bar, phase, &drain_flag, p.err);
+      }
     }
     tc_fence_before();
     __syncthreads();

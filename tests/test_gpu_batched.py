@@ -105,6 +105,15 @@ def test_tensor_core_items_match_oracle(nn, depth, damping):
     assert n_conv > 0
 
 
+def test_tensor_core_items_unaligned_offsets(nn):
+    # odd sizes before the tensor-core sizes leave their matrices 8- but not 16-byte aligned
+    bt = synth.mimo_gram_batch(24, seed=31, sizes=(5, 64, 17, 48, 1, 63))
+    x, res, st = _run(nn, bt, 2, 3, 1.0 / 128.0, cfg_by_u={48: 2, 64: 2})
+    assert any(int(bt.offsets[b]) % 2 == 1 and int(bt.sizes[b]) in (48, 64) for b in range(bt.count))
+    n_conv = _check(bt, x, res, st, 2, 3, 1.0 / 128.0)
+    assert n_conv > 0
+
+
 def test_single_and_tiny(nn):
     bt = synth.mimo_gram_batch(1, seed=2, sizes=(1,))
     x, res, st = _run(nn, bt, 2, 2, 0.0)
