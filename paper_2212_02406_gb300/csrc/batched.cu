@@ -307,7 +307,7 @@ namespace btc {
 constexpr int M = 128;                         // MMA rows (2U used)
 constexpr int CW = 16;                         // master columns per warp (TMEM access: 32 lanes x 16)
 constexpr int WARPS = 4 * (64 / CW);           // warp (q, h): lane quadrant q, column block h
-constexpr int THREADS = 32 * WARPS;
+constexpr int THREADS = 32 * WARPS;            // worker threads; one more warp issues the MMAs
 constexpr int PIECE = 128 * 128;               // one piece: 128 rows x 64 BF16 (one SW128 k-block)
 constexpr int OPND = 3 * PIECE;                // an operand's three pieces: 48 KB
 constexpr int A_CACHE = 0;                     // the slots' left operands of A: 2 x 48 KB
@@ -324,6 +324,26 @@ constexpr uint32_t TMEM_COLS = 512;
 static_assert(OPS_BYTES + 1024 <= BT_SMEM, "operands fit the dynamic shared memory");
 static_assert(PIECE % 1024 == 0 && EX % 16 == 0, "swizzle atoms and float4 rows stay aligned");
 }  // namespace btc
+
+// Named barriers of the tensor-core kernel: the btc::THREADS worker threads synchronise among
+// themselves on barrier 1; a staged product is handed to the MMA warp on barrier 2 (the workers
+// arrive without waiting, the MMA warp waits), so the MMA warp, which stalls while the tensor
+// core drains its queue, never holds the workers up.
+__device__ __forceinline__ void tc_wsync() { asm volatile("bar.sync 1, %0;" ::"n"(btc::THREADS) : "memory"); }
+__device__ __forceinline__ bool tc_wsync_and(bool v) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.and.pred po, 1, %2, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}"
+      : "=r"(out)
+      : "r"(v ? 1u : 0u), "n"(btc::THREADS)
+      : "memory");
+  return out != 0;
+}
+__device__ __forceinline__ void tc_handoff_arrive() {
+  asm volatile("bar.arrive 2, %0;" ::"n"(btc::THREADS + 32) : "memory");
+}
+__device__ __forceinline__ void tc_handoff_wait() { asm volatile("bar.sync 2, %0;" ::"n"(btc::THREADS + 32) : "memory"); }
 
 // TMEM access of a warp's 32 lanes x btc::CW columns.
 __device__ __forceinline__ void tmem_ld_cw(uint32_t taddr, uint32_t (&r)[16]) { tmem_ld_32x32b_x16(taddr, r); }
@@ -443,7 +463,7 @@ __device__ __forceinline__ void tc_issue(uint32_t d_tmem, uint32_t l_saddr, uint
 
 // out = mode(C) from the accumulator D of a product (see above) on this warp's 32 x CW block
 // of the real form; returns this thread's sum of squares of the result (residual mode, valid
-// lanes only). Every thread of the CTA calls it (three CTA barriers inside).
+// lanes only). Every worker thread calls it (three worker barriers inside).
 template <int U>
 __device__ __forceinline__ float tc_epilogue(uint32_t tmem, uint32_t cAcc, uint32_t cD, uint32_t cOut, int mode,
                                              float* ex, int q, int h, int l) {
@@ -453,97 +473,96 @@ __device__ __forceinline__ float tc_epilogue(uint32_t tmem, uint32_t cAcc, uint3
   const bool re = l < U;
   const int i = re ? l : l - U;
   const uint32_t lane_off = uint32_t(q * 32) << 16;
-  uint32_t dd[btc::CW], dx[btc::CW], dm[btc::CW];
-  tmem_ld_cw(tmem + lane_off + cAcc + uint32_t(h * btc::CW), dd);
-  tmem_ld_cw(tmem + lane_off + cAcc + uint32_t(U + h * btc::CW), dx);
-  if (mode == BM_ADD) tmem_ld_cw(tmem + lane_off + cD + uint32_t(h * btc::CW), dm);
-  tmem_ld_wait();
   // cross terms: real-part lanes need Pi Qi (Cr = Pr Qr - Pi Qi), imaginary-part lanes need
-  // Pr Qi (Ci = Pi Qr + Pr Qi); each lane publishes its own cross term (dx) in direction re / im
-  // and reads its partner's, half of its columns per phase so that every warp works each phase
+  // Pr Qi (Ci = Pi Qr + Pr Qi); each lane publishes its own cross term in direction re / im and
+  // reads its partner's, half of its columns per phase so that every warp works each phase
   float* mine = ex + (re ? 0 : btc::EX_DIR) + i * btc::EX_PITCH + h * (btc::CW / 2);
   const float* theirs = ex + (re ? btc::EX_DIR : 0) + i * btc::EX_PITCH + h * (btc::CW / 2);
   const float sgn = re ? -1.f : 1.f;
-#pragma unroll
-  for (int ph = 0; ph < 2; ++ph) {
-    if (valid) {
-#pragma unroll
-      for (int t = 0; t < btc::CW / 8; ++t) {
-        const int c0 = ph * (btc::CW / 2) + 4 * t;
-        reinterpret_cast<float4*>(mine)[t] = make_float4(__uint_as_float(dx[c0]), __uint_as_float(dx[c0 + 1]),
-                                                         __uint_as_float(dx[c0 + 2]), __uint_as_float(dx[c0 + 3]));
-      }
-    }
-    __syncthreads();
-    if (valid) {
-#pragma unroll
-      for (int t = 0; t < btc::CW / 8; ++t) {
-        const int c0 = ph * (btc::CW / 2) + 4 * t;
-        const float4 x = reinterpret_cast<const float4*>(theirs)[t];
-        dd[c0] = __float_as_uint(fmaf(sgn, x.x, __uint_as_float(dd[c0])));
-        dd[c0 + 1] = __float_as_uint(fmaf(sgn, x.y, __uint_as_float(dd[c0 + 1])));
-        dd[c0 + 2] = __float_as_uint(fmaf(sgn, x.z, __uint_as_float(dd[c0 + 2])));
-        dd[c0 + 3] = __float_as_uint(fmaf(sgn, x.w, __uint_as_float(dd[c0 + 3])));
-      }
-    }
-    if (ph == 0) __syncthreads();
-  }
   float local = 0.f;
 #pragma unroll
-  for (int t = 0; t < btc::CW; ++t) {
-    const int j = h * btc::CW + t;
-    const float cv = __uint_as_float(dd[t]);
-    float v = 0.f;
+  for (int ph = 0; ph < 2; ++ph) {
+    const uint32_t col = uint32_t(h * btc::CW + ph * (btc::CW / 2));
+    uint32_t dd[8], dx[8], dm[8];
+    tmem_ld_32x32b_x8(tmem + lane_off + cAcc + col, dd);
+    tmem_ld_32x32b_x8(tmem + lane_off + cAcc + uint32_t(U) + col, dx);
+    if (mode == BM_ADD) tmem_ld_32x32b_x8(tmem + lane_off + cD + col, dm);
+    tmem_ld_wait();
+    if (ph == 1) tc_wsync();  // the partner has read phase 0's cross terms
     if (valid) {
-      if (mode == BM_RESID) {
-        v = ((re && j == i) ? 1.f : 0.f) - cv;
-        local = fmaf(v, v, local);
-      } else {
-        v = __uint_as_float(dm[t]) + cv;
-      }
+      reinterpret_cast<float4*>(mine)[0] = make_float4(__uint_as_float(dx[0]), __uint_as_float(dx[1]),
+                                                       __uint_as_float(dx[2]), __uint_as_float(dx[3]));
+      reinterpret_cast<float4*>(mine)[1] = make_float4(__uint_as_float(dx[4]), __uint_as_float(dx[5]),
+                                                       __uint_as_float(dx[6]), __uint_as_float(dx[7]));
     }
-    dd[t] = __float_as_uint(v);
+    tc_wsync();
+    if (valid) {
+      const float4 x0 = reinterpret_cast<const float4*>(theirs)[0];
+      const float4 x1 = reinterpret_cast<const float4*>(theirs)[1];
+      const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int j = int(col) + t;
+        const float cv = fmaf(sgn, xs[t], __uint_as_float(dd[t]));
+        float v;
+        if (mode == BM_RESID) {
+          v = ((re && j == i) ? 1.f : 0.f) - cv;
+          local = fmaf(v, v, local);
+        } else {
+          v = __uint_as_float(dm[t]) + cv;
+        }
+        dd[t] = __float_as_uint(v);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 8; ++t) dd[t] = 0u;
+    }
+    tmem_st_32x32b_x8(tmem + lane_off + cOut + col, dd);
   }
-  tmem_st_cw(tmem + lane_off + cOut + uint32_t(h * btc::CW), dd);
   tmem_st_wait();
   return local;
 }
 
-// Sum over the CTA (btc::THREADS threads); result broadcast to every thread.
+// Sum over the worker threads; result broadcast to each of them.
 __device__ __forceinline__ float bt_block_sum(float v, float* red_warp) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0) red_warp[threadIdx.x >> 5] = v;
-  __syncthreads();
+  tc_wsync();
   float t = 0.f;
   for (int w = 0; w < btc::WARPS; ++w) t += red_warp[w];
-  __syncthreads();
+  tc_wsync();
   return t;
 }
 
 // A new matrix into a slot: A (U x U complex, row-major) is read coalesced into the slot's
-// cache area (free: its previous matrix is done), each thread takes its row part, and after a
-// CTA barrier the pieces of A's left operand [Ar; Ai] overwrite the area; X_0 = c diag(A)^-1
-// (damped Jacobi) goes to the X master at column cX (rows >= 2U zero). Every thread calls it.
+// cache area (free: its previous matrix is done) with rows padded to 2U + 1 floats, so that the
+// threads of a warp (consecutive rows) read their row parts without bank conflicts; after a CTA
+// barrier the pieces of A's left operand [Ar; Ai] overwrite the area; X_0 = c diag(A)^-1
+// (damped Jacobi) goes to the X master at column cX (rows >= 2U zero). Every worker thread calls it.
 template <int U>
 __device__ __forceinline__ void tc_load_matrix(const float2* A, float damping, uint8_t* acache, uint32_t tmem,
                                                uint32_t cX, int q, int h, int l) {
-  // matrices of any size are packed back to back, so A is 8- but not always 16-byte aligned
-  if ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) {
-    const float4* src = reinterpret_cast<const float4*>(A);
-    for (int e = threadIdx.x; e < U * U / 2; e += btc::THREADS) reinterpret_cast<float4*>(acache)[e] = __ldg(src + e);
-  } else {
-    for (int e = threadIdx.x; e < U * U; e += btc::THREADS) reinterpret_cast<float2*>(acache)[e] = __ldg(A + e);
+  constexpr int XP = 2 * U + 1;
+  float* st = reinterpret_cast<float*>(acache);
+  const float* src = reinterpret_cast<const float*>(A);
+  static_assert((2 * U * U) % btc::THREADS == 0, "whole rounds of the worker threads");
+  float v[2 * U * U / btc::THREADS];
+#pragma unroll
+  for (int k = 0; k < 2 * U * U / btc::THREADS; ++k) v[k] = __ldg(src + threadIdx.x + k * btc::THREADS);
+#pragma unroll
+  for (int k = 0; k < 2 * U * U / btc::THREADS; ++k) {
+    const int e = threadIdx.x + k * btc::THREADS;
+    st[(e / (2 * U)) * XP + e % (2 * U)] = v[k];
   }
-  __syncthreads();
+  tc_wsync();
   const bool active = h * btc::CW < U;
   const bool valid_row = active && l < 2 * U;
   const bool re = l < U;
   const int i = re ? l : l - U;
   uint32_t va[btc::CW], vx[btc::CW];
-  const float* Af = reinterpret_cast<const float*>(acache);
   float2 aii = make_float2(1.f, 0.f);
-  if (valid_row) aii = reinterpret_cast<const float2*>(acache)[i * U + i];
+  if (valid_row) aii = make_float2(st[i * XP + 2 * i], st[i * XP + 2 * i + 1]);
   const float cdamp = 1.f / (1.f + damping * float(U));
   const float den = aii.x * aii.x + aii.y * aii.y;
 #pragma unroll
@@ -551,13 +570,13 @@ __device__ __forceinline__ void tc_load_matrix(const float2* A, float damping, u
     const int j = h * btc::CW + t;
     float av = 0.f, xv = 0.f;
     if (valid_row) {
-      av = Af[2 * (i * U + j) + (re ? 0 : 1)];
+      av = st[i * XP + 2 * j + (re ? 0 : 1)];
       if (j == i) xv = re ? cdamp * aii.x / den : -cdamp * aii.y / den;
     }
     va[t] = __float_as_uint(av);
     vx[t] = __float_as_uint(xv);
   }
-  __syncthreads();
+  tc_wsync();
   if (valid_row) tc_row_pieces<U>(va, acache, l, h * btc::CW);
   if (active) {
     tmem_st_cw(tmem + (uint32_t(q * 32) << 16) + cX + uint32_t(h * btc::CW), vx);
@@ -566,10 +585,12 @@ __device__ __forceinline__ void tc_load_matrix(const float2* A, float damping, u
 }
 
 // X (complex, row-major) from the X master at column cX, through the slot's cache area (free:
-// its matrix is done) so that the global writes are coalesced. Every thread calls it.
+// its matrix is done; rows padded as above) so that the global writes are coalesced. Every
+// worker thread calls it.
 template <int U>
 __device__ __forceinline__ void tc_store_x(float2* X, uint32_t tmem, uint32_t cX, uint8_t* acache, int q, int h,
                                            int l) {
+  constexpr int XP = 2 * U + 1;
   float* xs = reinterpret_cast<float*>(acache);
   if (h * btc::CW < U) {
     uint32_t vx[btc::CW];
@@ -579,17 +600,17 @@ __device__ __forceinline__ void tc_store_x(float2* X, uint32_t tmem, uint32_t cX
       const bool re = l < U;
       const int i = re ? l : l - U;
 #pragma unroll
-      for (int t = 0; t < btc::CW; ++t) xs[2 * (i * U + h * btc::CW + t) + (re ? 0 : 1)] = __uint_as_float(vx[t]);
+      for (int t = 0; t < btc::CW; ++t) xs[i * XP + 2 * (h * btc::CW + t) + (re ? 0 : 1)] = __uint_as_float(vx[t]);
     }
   }
-  __syncthreads();
-  if ((reinterpret_cast<uintptr_t>(X) & 15u) == 0) {
-    for (int e = threadIdx.x; e < U * U / 2; e += btc::THREADS)
-      reinterpret_cast<float4*>(X)[e] = reinterpret_cast<const float4*>(xs)[e];
-  } else {
-    for (int e = threadIdx.x; e < U * U; e += btc::THREADS) X[e] = reinterpret_cast<const float2*>(xs)[e];
+  tc_wsync();
+  float* dst = reinterpret_cast<float*>(X);
+#pragma unroll
+  for (int k = 0; k < 2 * U * U / btc::THREADS; ++k) {
+    const int e = threadIdx.x + k * btc::THREADS;
+    dst[e] = xs[(e / (2 * U)) * XP + e % (2 * U)];
   }
-  __syncthreads();
+  tc_wsync();
 }
 
 // Slot state (identical in every thread: all updates are CTA-uniform).
@@ -626,15 +647,183 @@ __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepc
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // The tensor-core items of size U (classes 0 and 1): one CTA per SM, 512 TMEM columns, two
-// slots at depth <= 2 (one at depth >= 3, whose T master takes the second slot's columns).
+// slots at depth <= 2 (one at depth >= 3, whose T master takes the second slot's columns);
+// btc::THREADS worker threads stage, finish and move matrices, one more warp issues the MMAs.
+struct TcCmd {
+  uint32_t d_tmem, l_saddr, b_saddr;
+  int exit;
+};
+
+// The worker threads of batched_tc_kernel: pull matrices, stage products, hand them to the MMA
+// warp, finish them; see the tensor-core notes above.
 template <int U>
-__global__ void __launch_bounds__(btc::THREADS, 1) batched_tc_kernel(const BatchedParams p, int cls) {
+__device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls, int first, int last,
+                                                const int32_t* items, uint8_t* ops, uint32_t ops_s, uint32_t tmem,
+                                                uint64_t* mma_bar, int* abort_word, int* item_sh, float* red_warp,
+                                                TcCmd* cmd) {
+  float* ex = reinterpret_cast<float*>(ops + btc::EX);
+  const int w = int(threadIdx.x >> 5), q = w & 3, h = w >> 2, l = q * 32 + int(threadIdx.x & 31);
+  const int nslots = p.depth <= 2 ? 2 : 1;
+  TcSlot sl0 = {-1, 0, 0, NN_OK, 0.f, 0.f}, sl1 = sl0;  // two named slots: no local memory
+  uint32_t phase = 0;
+  bool outstanding = false;
+  bool ok = true;
+
+  // next item of this class into slot s, or the slot left empty
+  auto fetch = [&](int s) {
+    if (threadIdx.x == 0) *item_sh = first + atomicAdd(p.queue + cls, 1);
+    tc_wsync();
+    const int it = *item_sh;
+    tc_wsync();
+    TcSlot t = {-1, 0, 0, NN_OK, 0.f, 0.f};
+    if (it < last) {
+      t.b = p.plan[PLAN_HDR + items[4 * it + 1]];
+      tc_load_matrix<U>(p.A + p.offsets[t.b], p.damping, ops + btc::A_CACHE + s * btc::OPND, tmem,
+                        uint32_t(s) * btc::SLOT_COLS + btc::MX, q, h, l);
+    }
+    if (s == 0)
+      sl0 = t;
+    else
+      sl1 = t;
+    tc_fence_before();
+    tc_wsync();
+    tc_fence_after();
+  };
+  // every thread learns the same outcome of the wait on the last issued MMA chain
+  auto wait_mma = [&]() -> bool {
+    if (!outstanding) return true;
+    const bool r = tc_wsync_and(mbar_wait(mma_bar, phase, abort_word, p.err));
+    phase ^= 1u;
+    outstanding = false;
+    tc_fence_after();
+    return r;
+  };
+  // stage slot s's next product, then one thread issues its MMA chain
+  auto stage = [&](int s) {
+    const uint32_t sb = uint32_t(s) * btc::SLOT_COLS;
+    const TcProd pr = tc_product(s == 0 ? sl0 : sl1, sb, p.depth);
+    tc_stage<U>(tmem, pr.mode != BM_RESID, pr.cP, pr.cQ, ops + btc::L_STAGE, ops + btc::B_STAGE, q, h, l);
+    fence_proxy_async_smem();
+    tc_fence_before();
+    if (threadIdx.x == 0) {
+      cmd->d_tmem = tmem + sb + btc::ACC;
+      cmd->l_saddr = pr.mode == BM_RESID ? ops_s + uint32_t(btc::A_CACHE + s * btc::OPND) : ops_s + uint32_t(btc::L_STAGE);
+      cmd->b_saddr = ops_s + uint32_t(btc::B_STAGE);
+      cmd->exit = 0;
+    }
+    tc_handoff_arrive();
+    outstanding = true;
+  };
+  // finish slot s's product (its MMAs complete): epilogue, residual test, next state; a
+  // finished matrix is written out and the slot refilled
+  auto finish = [&](int s) {
+    const uint32_t sb = uint32_t(s) * btc::SLOT_COLS;
+    TcSlot t = s == 0 ? sl0 : sl1;
+    const TcProd pr = tc_product(t, sb, p.depth);
+    const float ss = tc_epilogue<U>(tmem, sb + btc::ACC, pr.cD, pr.cOut, pr.mode, ex, q, h, l);
+    tc_fence_before();
+    bool done = false;
+    if (pr.mode == BM_RESID) {
+      const float sv = sqrtf(bt_block_sum(ss, red_warp)) / float(U);
+      t.s_last = sv;
+      if (!isfinite(sv) || (t.k >= 1 && sv >= 1.f && sv > t.s_prev)) {
+        t.st = NN_ERR_DIVERGED;
+        done = true;
+      }
+      t.s_prev = sv;
+      if (t.k == p.nests) done = true;
+    }
+    tc_wsync();
+    tc_fence_after();
+    if (!done) {
+      if (++t.j > p.depth) {
+        t.j = 0;
+        ++t.k;
+      }
+      if (s == 0)
+        sl0 = t;
+      else
+        sl1 = t;
+      return;
+    }
+    tc_store_x<U>(p.X + p.offsets[t.b], tmem, sb + btc::MX, ops + btc::A_CACHE + s * btc::OPND, q, h, l);
+    if (threadIdx.x == 0) {
+      p.residual[t.b] = t.s_last;
+      p.status[t.b] = t.st;
+    }
+    fetch(s);
+  };
+
+  for (int s = 0; s < nslots; ++s) fetch(s);
+  int pending = -1;  // slot whose product's MMAs are issued and whose epilogue is not done
+  while (ok) {
+    int m = -1;
+    if (pending >= 0)
+      m = (nslots == 2 && (pending == 0 ? sl1 : sl0).b >= 0) ? 1 - pending : pending;
+    else if (sl0.b >= 0)
+      m = 0;
+    else if (nslots == 2 && sl1.b >= 0)
+      m = 1;
+    if (m < 0) break;
+    ok = wait_mma();  // staging buffers free, the pending product's accumulator final
+    if (!ok) break;
+    if (m == pending) {
+      // one slot in flight: its product completes before the next is staged
+      finish(m);
+      pending = -1;
+      continue;
+    }
+    stage(m);
+    if (pending >= 0) finish(pending);
+    pending = m;
+  }
+  if (ok) ok = wait_mma();
+  // release the MMA warp (after a timeout too; its last chain, if any, was issued)
+  if (threadIdx.x == 0) cmd->exit = 1;
+  tc_handoff_arrive();
+  if (!ok) {
+    // a bounded wait ran out: the slots' matrices and every item not yet taken report
+    // NN_ERR_TIMEOUT (X unspecified); wait (bounded) for the issued MMAs before freeing TMEM
+    if (threadIdx.x == 0) {
+      if (sl0.b >= 0) {
+        p.residual[sl0.b] = sl0.s_last;
+        p.status[sl0.b] = NN_ERR_TIMEOUT;
+      }
+      if (nslots == 2 && sl1.b >= 0) {
+        p.residual[sl1.b] = sl1.s_last;
+        p.status[sl1.b] = NN_ERR_TIMEOUT;
+      }
+    }
+    while (true) {
+      if (threadIdx.x == 0) *item_sh = first + atomicAdd(p.queue + cls, 1);
+      tc_wsync();
+      const int it = *item_sh;
+      tc_wsync();
+      if (it >= last) break;
+      if (threadIdx.x == 0) {
+        const int b = p.plan[PLAN_HDR + items[4 * it + 1]];
+        p.residual[b] = 0.f;
+        p.status[b] = NN_ERR_TIMEOUT;
+      }
+    }
+    if (outstanding) {
+      volatile int drain_flag = 0;
+      mbar_wait(mma_bar, phase, &drain_flag, p.err);
+    }
+  }
+}
+
+// 17 warps: at most 96 registers a thread (five warps share one scheduler's quarter of the
+// register file)
+template <int U>
+__global__ void __launch_bounds__(btc::THREADS + 32, 1) batched_tc_kernel(const BatchedParams p, int cls) {
   extern __shared__ float2 smem[];
   __shared__ float red_warp[btc::WARPS];
   __shared__ int item_sh;
   __shared__ __align__(8) uint64_t mma_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_word;
+  __shared__ TcCmd cmd;
   pdl_launch_dependents();
   const int count = p.plan[1];
   const int first = p.plan[3 + cls], last = p.plan[3 + cls + 1];
@@ -643,8 +832,6 @@ __global__ void __launch_bounds__(btc::THREADS, 1) batched_tc_kernel(const Batch
     uint8_t* ops = reinterpret_cast<uint8_t*>(smem);
     ops += (1024u - (smem_u32(ops) & 1023u)) & 1023u;
     const uint32_t ops_s = smem_u32(ops);
-    float* ex = reinterpret_cast<float*>(ops + btc::EX);
-    const int w = int(threadIdx.x >> 5), q = w & 3, h = w >> 2, l = q * 32 + int(threadIdx.x & 31);
     if (threadIdx.x == 0) {
       mbar_init(&mma_bar, 1);
       abort_word = 0;
@@ -655,151 +842,22 @@ __global__ void __launch_bounds__(btc::THREADS, 1) batched_tc_kernel(const Batch
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const int nslots = p.depth <= 2 ? 2 : 1;
-    TcSlot sl0 = {-1, 0, 0, NN_OK, 0.f, 0.f}, sl1 = sl0;  // two named slots: no local memory
-    uint32_t phase = 0;
-    bool outstanding = false;
-    bool ok = true;
-
-    // next item of this class into slot s, or the slot left empty
-    auto fetch = [&](int s) {
-      if (threadIdx.x == 0) item_sh = first + atomicAdd(p.queue + cls, 1);
-      __syncthreads();
-      const int it = item_sh;
-      __syncthreads();
-      TcSlot t = {-1, 0, 0, NN_OK, 0.f, 0.f};
-      if (it < last) {
-        t.b = p.plan[PLAN_HDR + items[4 * it + 1]];
-        tc_load_matrix<U>(p.A + p.offsets[t.b], p.damping, ops + btc::A_CACHE + s * btc::OPND, tmem,
-                          uint32_t(s) * btc::SLOT_COLS + btc::MX, q, h, l);
-      }
-      if (s == 0)
-        sl0 = t;
-      else
-        sl1 = t;
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-    };
-    // every thread learns the same outcome of the wait on the last issued MMA chain
-    auto wait_mma = [&]() -> bool {
-      if (!outstanding) return true;
-      const bool r = __syncthreads_and(mbar_wait(&mma_bar, phase, &abort_word, p.err) ? 1 : 0) != 0;
-      phase ^= 1u;
-      outstanding = false;
-      tc_fence_after();
-      return r;
-    };
-    // stage slot s's next product, then one thread issues its MMA chain
-    auto stage = [&](int s) {
-      const uint32_t sb = uint32_t(s) * btc::SLOT_COLS;
-      const TcProd pr = tc_product(s == 0 ? sl0 : sl1, sb, p.depth);
-      tc_stage<U>(tmem, pr.mode != BM_RESID, pr.cP, pr.cQ, ops + btc::L_STAGE, ops + btc::B_STAGE, q, h, l);
-      fence_proxy_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        tc_fence_after();
-        const uint32_t lop = pr.mode == BM_RESID ? ops_s + uint32_t(btc::A_CACHE + s * btc::OPND)
-                                                 : ops_s + uint32_t(btc::L_STAGE);
-        tc_issue<U>(tmem + sb + btc::ACC, lop, ops_s + uint32_t(btc::B_STAGE));
-        tc_commit(&mma_bar);
-      }
-      outstanding = true;
-    };
-    // finish slot s's product (its MMAs complete): epilogue, residual test, next state; a
-    // finished matrix is written out and the slot refilled
-    auto finish = [&](int s) {
-      const uint32_t sb = uint32_t(s) * btc::SLOT_COLS;
-      TcSlot t = s == 0 ? sl0 : sl1;
-      const TcProd pr = tc_product(t, sb, p.depth);
-      const float ss = tc_epilogue<U>(tmem, sb + btc::ACC, pr.cD, pr.cOut, pr.mode, ex, q, h, l);
-      tc_fence_before();
-      bool done = false;
-      if (pr.mode == BM_RESID) {
-        const float sv = sqrtf(bt_block_sum(ss, red_warp)) / float(U);
-        t.s_last = sv;
-        if (!isfinite(sv) || (t.k >= 1 && sv >= 1.f && sv > t.s_prev)) {
-          t.st = NN_ERR_DIVERGED;
-          done = true;
-        }
-        t.s_prev = sv;
-        if (t.k == p.nests) done = true;
-      }
-      __syncthreads();
-      tc_fence_after();
-      if (!done) {
-        if (++t.j > p.depth) {
-          t.j = 0;
-          ++t.k;
-        }
-        if (s == 0)
-          sl0 = t;
-        else
-          sl1 = t;
-        return;
-      }
-      tc_store_x<U>(p.X + p.offsets[t.b], tmem, sb + btc::MX, ops + btc::A_CACHE + s * btc::OPND, q, h, l);
-      if (threadIdx.x == 0) {
-        p.residual[t.b] = t.s_last;
-        p.status[t.b] = t.st;
-      }
-      fetch(s);
-    };
-
-    for (int s = 0; s < nslots; ++s) fetch(s);
-    int pending = -1;  // slot whose product's MMAs are issued and whose epilogue is not done
-    while (ok) {
-      int m = -1;
-      if (pending >= 0)
-        m = (nslots == 2 && (pending == 0 ? sl1 : sl0).b >= 0) ? 1 - pending : pending;
-      else if (sl0.b >= 0)
-        m = 0;
-      else if (nslots == 2 && sl1.b >= 0)
-        m = 1;
-      if (m < 0) break;
-      ok = wait_mma();  // staging buffers free, the pending product's accumulator final
-      if (!ok) break;
-      if (m == pending) {
-        // one slot in flight: its product completes before the next is staged
-        finish(m);
-        pending = -1;
-        continue;
-      }
-      stage(m);
-      if (pending >= 0) finish(pending);
-      pending = m;
-    }
-    if (ok) ok = wait_mma();
-    if (!ok) {
-      // a bounded wait ran out: the slots' matrices and every item not yet taken report
-      // NN_ERR_TIMEOUT (X unspecified); wait (bounded) for the issued MMAs before freeing TMEM
-      if (threadIdx.x == 0) {
-        if (sl0.b >= 0) {
-          p.residual[sl0.b] = sl0.s_last;
-          p.status[sl0.b] = NN_ERR_TIMEOUT;
-        }
-        if (nslots == 2 && sl1.b >= 0) {
-          p.residual[sl1.b] = sl1.s_last;
-          p.status[sl1.b] = NN_ERR_TIMEOUT;
-        }
-      }
+    if (threadIdx.x >= btc::THREADS) {
+      // the MMA warp: one chain per handed-over product until the workers send exit
       while (true) {
-        if (threadIdx.x == 0) item_sh = first + atomicAdd(p.queue + cls, 1);
-        __syncthreads();
-        const int it = item_sh;
-        __syncthreads();
-        if (it >= last) break;
-        if (threadIdx.x == 0) {
-          const int b = p.plan[PLAN_HDR + items[4 * it + 1]];
-          p.residual[b] = 0.f;
-          p.status[b] = NN_ERR_TIMEOUT;
+        tc_handoff_wait();
+        const TcCmd c = cmd;
+        if (c.exit) break;
+        if (threadIdx.x == btc::THREADS) {
+          tc_fence_after();
+          tc_issue<U>(c.d_tmem, c.l_saddr, c.b_saddr);
+          tc_commit(&mma_bar);
         }
+        __syncwarp();
       }
-      if (outstanding) {
-        volatile int drain_flag = 0;
-        mbar_wait(&mma_bar, phase, &drain_flag, p.err);
-      }
+    } else {
+      batched_tc_work<U>(p, cls, first, last, items, ops, ops_s, tmem, &mma_bar, &abort_word, &item_sh, red_warp,
+                         &cmd);
     }
     tc_fence_before();
     __syncthreads();
@@ -855,6 +913,11 @@ int bt_init() {
   NN_CUDA_TRY(cudaDeviceGetAttribute(&g_bt_sms, cudaDevAttrMultiProcessorCount, dev));
   NN_CUDA_TRY(cudaFuncSetAttribute(batched_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
   NN_CUDA_TRY(cudaFuncSetAttribute(batched_tc_kernel<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM));
+  for (auto k : {batched_tc_kernel<64>, batched_tc_kernel<48>}) {
+    cudaFuncAttributes fa;
+    NN_CUDA_TRY(cudaFuncGetAttributes(&fa, k));
+    if (fa.maxThreadsPerBlock < btc::THREADS + 32) return NN_ERR_UNSUPPORTED;  // registers do not fit
+  }
   for (SimtKernel k : kSimtKernels)
     NN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM_SIMT_DEEP));
   g_bt_init = true;
@@ -961,14 +1024,14 @@ int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* 
   p.queue = static_cast<int*>(workspace);
   p.err = static_cast<int*>(workspace) + BT_QUEUE_ERR;
   NN_CUDA_TRY(cudaMemsetAsync(p.queue, 0, nn_batched_workspace_bytes(count), st));
-  batched_tc_kernel<64><<<g_bt_sms, btc::THREADS, BT_SMEM, st>>>(p, 0);
+  batched_tc_kernel<64><<<g_bt_sms, btc::THREADS + 32, BT_SMEM, st>>>(p, 0);
   NN_CUDA_TRY(cudaGetLastError());
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(g_bt_sms));
-  cfg.blockDim = dim3(btc::THREADS);
+  cfg.blockDim = dim3(btc::THREADS + 32);
   cfg.dynamicSmemBytes = size_t(BT_SMEM);
   cfg.stream = st;
   cfg.attrs = attr;
