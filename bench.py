@@ -653,7 +653,7 @@ def run_batched(args, rank, world, local_rank):
                        "tensor_core_items": bool(args.batched_tc) or any(v == 2 for v in (table or {}).values())},
             "status_ok_fraction": float(np.mean(stats == 0)), "gpu_launches": abi.NN_BATCHED_KERNELS * args.steps,
             "tflops": round(tflops, 2), "gbs": round(byts / (ms / 1e3) / 1e9, 1),
-            "roofline": {"kernel": "nn::batched_simt_kernel<TG, T, U> (all classes, one batch)", "bound": "alu",
+            "roofline": {"kernel": "the batch: batched_tc_kernel<U> (tuned sizes, tensor cores) + batched_simt_kernel<TG, T, U> (CUDA cores), useful complex FLOPs", "bound": "alu",
                          "achieved": round(tflops, 2),
                          "peak": round(fma_peak, 1), "unit": "TFLOP/s", "frac": round(tflops / fma_peak, 4),
                          "traffic": None, "peak_source": f"FP32 FMA: {sms} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz",

@@ -283,12 +283,14 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
 //
 // Two matrices per CTA, every iterate kept on chip:
 //   * masters (X, R; T at depth >= 3) live in TMEM as the real form [Re; Im] of each U x U
-//     complex matrix: lane i < U holds row i's real parts, lane U + i its imaginary parts,
-//     columns 0..U-1; each of the two slots owns 256 columns (X, R, a 2U-column accumulator);
+//     complex matrix: one lane holds row i's real parts and lane + 64 its imaginary parts,
+//     columns 0..U-1 (tc_lane_row gives the row of each lane); each of the two slots owns 256
+//     columns (X, R, a 2U-column accumulator);
 //   * a complex product C = P Q is one real MMA chain
 //         D (2U x 2U) = [Pr; Pi] (2U x U) . [Qr | Qi] (U x 2U)
 //           = [[Pr Qr, Pr Qi], [Pi Qr, Pi Qi]],   Cr = Pr Qr - Pi Qi,  Ci = Pi Qr + Pr Qi,
-//     i.e. M = 128 (2U rows used), N = 2U, K = U. The left operand's rows are P's master lanes;
+//     i.e. M = 128 (2U rows used, in the lanes' order), N = 2U, K = U. The left operand's rows
+//     are P's master lanes;
 //     the right operand (K-major: row n < U = column n of Qr, row U + n = column n of Qi) is the
 //     transpose of Q's master. A's left operand is split once per matrix and kept in shared
 //     memory (one copy per slot);
@@ -376,6 +378,23 @@ __device__ __forceinline__ void split3x2(float a, float b, uint32_t& w0, uint32_
   w2 = *reinterpret_cast<uint32_t*>(&v);
 }
 
+// Row of the real form held by master lane l: row i's real part (im = false) or imaginary part.
+// U = 64: lanes i and 64 + i. U = 48: the 48 rows of each part fill the first 24 lanes of two
+// 32-lane quadrants (lanes 24..31 of every quadrant are padding), so that all four quadrants,
+// and with them all four schedulers' warps, share the work. Returns false for padding lanes.
+template <int U>
+__device__ __forceinline__ bool tc_lane_row(int l, int& i, bool& im) {
+  static_assert(U == 48 || U == 64, "tensor-core sizes");
+  im = l >= 64;
+  const int r = l & 63;
+  if (U == 64) {
+    i = r;
+    return true;
+  }
+  i = (r >> 5) * 24 + (r & 31);
+  return (r & 31) < 24;
+}
+
 // Pieces of CW consecutive values of one left-operand row (K = col0 .. col0 + CW - 1, col0 a
 // multiple of 8; values at K >= U are not written).
 template <int U>
@@ -396,20 +415,22 @@ __device__ __forceinline__ void tc_row_pieces(const uint32_t (&v)[btc::CW], uint
 }
 
 // Right operand [Qr | Qi] (K-major) from master Q values raw (this thread's lane l, columns
-// h CW ..): master lane r, column c goes to row c (+ U for r >= U), column k = r mod U. The pair
+// h CW ..): row i's real part, column c goes to row c, column k = i; its imaginary part to row
+// U + c, column k = i. The pair
 // (k, k + 1) of a column is split and stored by the even lane for the first CW/2 columns of the
 // warp's block and by the odd lane for the rest (U is even, so a pair never straddles the real
 // and imaginary lanes). Every lane of the warp calls it (shuffles).
 template <int U>
 __device__ __forceinline__ void tc_right_pieces(const uint32_t (&raw)[btc::CW], uint8_t* dst, int h, int l) {
+  int i;
+  bool im;
+  const bool store = tc_lane_row<U>(l, i, im);  // row pairs (i, i + 1) sit in lanes (l, l + 1)
   const bool odd = (l & 1) != 0;
-  const bool re = l < U;
-  const int kk = (re ? l : l - U) & ~1;
-  // rows (re ? 0 : U) + h CW + (odd ? CW/2 : 0) + t: a multiple of 8 plus t < 8
-  const int row8 = ((re ? 0 : U) + h * btc::CW + (odd ? btc::CW / 2 : 0)) >> 3;
+  const int kk = i & ~1;
+  // rows (im ? U : 0) + h CW + (odd ? CW/2 : 0) + t: a multiple of 8 plus t < 8
+  const int row8 = ((im ? U : 0) + h * btc::CW + (odd ? btc::CW / 2 : 0)) >> 3;
   uint8_t* base = dst + row8 * 1024 + ((kk & 7) << 1);
   const int kc = kk >> 3;
-  const bool store = l < 2 * U;
 #pragma unroll
   for (int t = 0; t < btc::CW / 2; ++t) {
     const float lo_v = __uint_as_float(raw[t]), hi_v = __uint_as_float(raw[btc::CW / 2 + t]);
@@ -426,7 +447,7 @@ __device__ __forceinline__ void tc_right_pieces(const uint32_t (&raw)[btc::CW], 
   }
 }
 
-// Stages one product: the left operand [Pr; Pi] from master P (row r = master lane r; not for
+// Stages one product: the left operand [Pr; Pi] from master P (operand row = master lane; not for
 // the residual, whose left operand is A's cached pieces) and the right operand from master Q;
 // warp (q, h) owns lanes 32q.. and columns h CW...
 template <int U>
@@ -438,8 +459,9 @@ __device__ __forceinline__ void tc_stage(uint32_t tmem, bool left, uint32_t cP, 
   if (left) tmem_ld_cw(tmem + lane_off + cP + uint32_t(h * btc::CW), rp);
   tmem_ld_cw(tmem + lane_off + cQ + uint32_t(h * btc::CW), rq);
   tmem_ld_wait();
-  if (q * 32 >= 2 * U) return;  // warp-uniform: 2U is a multiple of 32
-  if (left && l < 2 * U) tc_row_pieces<U>(rp, ldst, l, h * btc::CW);
+  int i;
+  bool im;
+  if (left && tc_lane_row<U>(l, i, im)) tc_row_pieces<U>(rp, ldst, l, h * btc::CW);
   tc_right_pieces<U>(rq, bdst, h, l);
 }
 
@@ -469,9 +491,10 @@ __device__ __forceinline__ float tc_epilogue(uint32_t tmem, uint32_t cAcc, uint3
                                              float* ex, int q, int h, int l) {
   // Every warp reads and writes its block, also a block of columns >= U (U = 48): those lie
   // inside the accumulator's 2U and the masters' 64 columns and carry no data (zeros written).
-  const bool valid = h * btc::CW < U && l < 2 * U;
-  const bool re = l < U;
-  const int i = re ? l : l - U;
+  int i;
+  bool im;
+  const bool valid = tc_lane_row<U>(l, i, im) && h * btc::CW < U;
+  const bool re = !im;
   const uint32_t lane_off = uint32_t(q * 32) << 16;
   // cross terms: real-part lanes need Pi Qi (Cr = Pr Qr - Pi Qi), imaginary-part lanes need
   // Pr Qi (Ci = Pi Qr + Pr Qi); each lane publishes its own cross term in direction re / im and
@@ -539,7 +562,8 @@ __device__ __forceinline__ float bt_block_sum(float v, float* red_warp) {
 // cache area (free: its previous matrix is done) with rows padded to 2U + 1 floats, so that the
 // threads of a warp (consecutive rows) read their row parts without bank conflicts; after a CTA
 // barrier the pieces of A's left operand [Ar; Ai] overwrite the area; X_0 = c diag(A)^-1
-// (damped Jacobi) goes to the X master at column cX (rows >= 2U zero). Every worker thread calls it.
+// (damped Jacobi) goes to the X master at column cX (padding lanes zero). Every worker thread
+// calls it.
 template <int U>
 __device__ __forceinline__ void tc_load_matrix(const float2* A, float damping, uint8_t* acache, uint32_t tmem,
                                                uint32_t cX, int q, int h, int l) {
@@ -557,9 +581,10 @@ __device__ __forceinline__ void tc_load_matrix(const float2* A, float damping, u
   }
   tc_wsync();
   const bool active = h * btc::CW < U;
-  const bool valid_row = active && l < 2 * U;
-  const bool re = l < U;
-  const int i = re ? l : l - U;
+  int i;
+  bool im;
+  const bool valid_row = tc_lane_row<U>(l, i, im) && active;
+  const bool re = !im;
   uint32_t va[btc::CW], vx[btc::CW];
   float2 aii = make_float2(1.f, 0.f);
   if (valid_row) aii = make_float2(st[i * XP + 2 * i], st[i * XP + 2 * i + 1]);
@@ -596,9 +621,10 @@ __device__ __forceinline__ void tc_store_x(float2* X, uint32_t tmem, uint32_t cX
     uint32_t vx[btc::CW];
     tmem_ld_cw(tmem + (uint32_t(q * 32) << 16) + cX + uint32_t(h * btc::CW), vx);
     tmem_ld_wait();
-    if (l < 2 * U) {
-      const bool re = l < U;
-      const int i = re ? l : l - U;
+    int i;
+    bool im;
+    if (tc_lane_row<U>(l, i, im)) {
+      const bool re = !im;
 #pragma unroll
       for (int t = 0; t < btc::CW; ++t) xs[i * XP + 2 * (h * btc::CW + t) + (re ? 0 : 1)] = __uint_as_float(vx[t]);
     }
