@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--max-active", type=int, default=8)
     ap.add_argument("--gemm-variant", type=int, default=0, choices=[0, 1, 2, 3, 4], help="0 auto, 1 single-CTA tiles, 2 CTA pairs with multicast, 3 2-SM MMA, 4 2-SM MMA with split last wave")
     ap.add_argument("--spmv-variant", type=int, default=0, choices=[0, 1], help="0 auto (bulk-copy ring), 1 staged loads")
+    ap.add_argument("--batched-simt", action="store_true",
+                    help="batched workload: CUDA-core items for every size (ignore tensor-core entries of the table)")
     ap.add_argument("--batched-tc", action="store_true",
                     help="batched workload: tensor-core items for U in {48, 64}")
     ap.add_argument("--no-e2e", action="store_true")
@@ -597,6 +599,8 @@ def run_batched(args, rank, world, local_rank):
     offs = torch.from_numpy(bt.offsets.astype(np.int64)).to(dev)
     sizes = torch.from_numpy(bt.sizes.astype(np.int32)).to(dev)
     table = load_batched_tuning()
+    if args.batched_simt:
+        table = {u: c for u, c in (table or {}).items() if c != 2}
     if args.batched_tc:
         table = dict(table or {})
         table.update({48: 2, 64: 2})
