@@ -35,7 +35,7 @@ namespace {
 
 constexpr int BT_THREADS = 256;
 constexpr int BT_MAX_U = 64;
-constexpr int BT_SMEM = 212 * 1024;         // dynamic shared memory of a tensor-core CTA
+constexpr int BT_SMEM = 193 * 1024;         // dynamic shared memory of a tensor-core CTA
 // CUDA-core items: two CTAs per SM at depth <= 2 (three buffers per matrix), one at depth >= 3
 // (four buffers, 4/3 of the same shared memory), so a plan sized for the first fits both.
 constexpr int BT_SMEM_SIMT = 112 * 1024;
@@ -283,9 +283,9 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
 //
 // Two matrices per CTA, every iterate kept on chip:
 //   * masters (X, R; T at depth >= 3) live in TMEM as the real form [Re; Im] of each U x U
-//     complex matrix: one lane holds row i's real parts and lane + 64 its imaginary parts,
-//     columns 0..U-1 (tc_lane_row gives the row of each lane); each of the two slots owns 256
-//     columns (X, R, a 2U-column accumulator);
+//     complex matrix: adjacent lanes hold row i's real and imaginary parts, columns 0..U-1
+//     (tc_lane_row gives the row of each lane); each of the two slots owns 256 columns (X, R,
+//     a 2U-column accumulator);
 //   * a complex product C = P Q is one real MMA chain
 //         D (2U x 2U) = [Pr; Pi] (2U x U) . [Qr | Qi] (U x 2U)
 //           = [[Pr Qr, Pr Qi], [Pi Qr, Pi Qi]],   Cr = Pr Qr - Pi Qi,  Ci = Pi Qr + Pr Qi,
@@ -298,10 +298,10 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
 //     remainder) and written in the SWIZZLE_128B K-major layout; the six piece products with
 //     i + j <= 2 (smallest first) accumulate in FP32 in TMEM, which matches an FP32 product to
 //     about 2^-24 relative;
-//   * epilogue: the real-part lanes need Pi Qi from the imaginary-part lanes and those need
-//     Pr Qi from the real-part lanes (other warps): the cross terms pass through shared memory,
-//     then I - C or D + C is applied in FP32 and written to the result master, and the residual's
-//     sum of squares is reduced across the CTA;
+//   * epilogue: the real-part lane of a row needs Pi Qi and the imaginary-part lane Pr Qi, each
+//     the other lane's own cross term, exchanged with one lane shuffle; then I - C or D + C is
+//     applied in FP32 and written to the result master, and the residual's sum of squares is
+//     reduced across the workers;
 //   * the two slots alternate: while the tensor core runs one slot's product, the CTA finishes
 //     the other slot's previous product; then it stages the other slot's next product once the
 //     MMAs (which read the single staging buffers) have completed.
@@ -315,16 +315,13 @@ constexpr int OPND = 3 * PIECE;                // an operand's three pieces: 48 
 constexpr int A_CACHE = 0;                     // the slots' left operands of A: 2 x 48 KB
 constexpr int L_STAGE = 2 * OPND;              // staged left operand
 constexpr int B_STAGE = 3 * OPND;              // staged right operand
-constexpr int EX = 4 * OPND;                   // cross-term exchange, per direction: U rows x EX_PITCH
-constexpr int EX_PITCH = 32 + 4;               // floats: half of each row per phase (float4, no conflicts)
-constexpr int EX_DIR = 64 * EX_PITCH;          // floats per direction
-constexpr int OPS_BYTES = EX + 2 * EX_DIR * 4;
+constexpr int OPS_BYTES = 4 * OPND;
 constexpr uint32_t SLOT_COLS = 256;            // TMEM columns per slot
 constexpr uint32_t MX = 0, MR = 64, ACC = 128;
 constexpr uint32_t MT = 256;                   // T master (depth >= 3: one slot only)
 constexpr uint32_t TMEM_COLS = 512;
 static_assert(OPS_BYTES + 1024 <= BT_SMEM, "operands fit the dynamic shared memory");
-static_assert(PIECE % 1024 == 0 && EX % 16 == 0, "swizzle atoms and float4 rows stay aligned");
+static_assert(PIECE % 1024 == 0, "swizzle atoms stay aligned");
 }  // namespace btc
 
 // Named barriers of the tensor-core kernel: the btc::THREADS worker threads synchronise among
@@ -378,21 +375,15 @@ __device__ __forceinline__ void split3x2(float a, float b, uint32_t& w0, uint32_
   w2 = *reinterpret_cast<uint32_t*>(&v);
 }
 
-// Row of the real form held by master lane l: row i's real part (im = false) or imaginary part.
-// U = 64: lanes i and 64 + i. U = 48: the 48 rows of each part fill the first 24 lanes of two
-// 32-lane quadrants (lanes 24..31 of every quadrant are padding), so that all four quadrants,
-// and with them all four schedulers' warps, share the work. Returns false for padding lanes.
+// Row of the real form held by master lane l: row i's real part (im = false) in lane 2i, its
+// imaginary part in lane 2i + 1, so that the two parts of a row sit in one warp and the epilogue
+// combines the cross terms with a lane shuffle. Returns false for the padding lanes >= 2U.
 template <int U>
 __device__ __forceinline__ bool tc_lane_row(int l, int& i, bool& im) {
   static_assert(U == 48 || U == 64, "tensor-core sizes");
-  im = l >= 64;
-  const int r = l & 63;
-  if (U == 64) {
-    i = r;
-    return true;
-  }
-  i = (r >> 5) * 24 + (r & 31);
-  return (r & 31) < 24;
+  im = (l & 1) != 0;
+  i = l >> 1;
+  return l < 2 * U;
 }
 
 // Pieces of CW consecutive values of one left-operand row (K = col0 .. col0 + CW - 1, col0 a
@@ -416,30 +407,35 @@ __device__ __forceinline__ void tc_row_pieces(const uint32_t (&v)[btc::CW], uint
 
 // Right operand [Qr | Qi] (K-major) from master Q values raw (this thread's lane l, columns
 // h CW ..): row i's real part, column c goes to row c, column k = i; its imaginary part to row
-// U + c, column k = i. The pair
-// (k, k + 1) of a column is split and stored by the even lane for the first CW/2 columns of the
-// warp's block and by the odd lane for the rest (U is even, so a pair never straddles the real
-// and imaginary lanes). Every lane of the warp calls it (shuffles).
+// U + c, column k = i. The pair (k, k + 1) (k even; lanes l and l + 2) of a column is split and
+// stored by row k's lane for the first CW/2 columns of the warp's block and by row k + 1's lane
+// for the rest. The four kinds of lanes (real / imaginary part, row k / k + 1) take their
+// columns in rotated orders so that the four rows one store instruction writes fall in four
+// different swizzle phases (no bank conflicts). Every lane of the warp calls it (shuffles).
 template <int U>
 __device__ __forceinline__ void tc_right_pieces(const uint32_t (&raw)[btc::CW], uint8_t* dst, int h, int l) {
   int i;
   bool im;
-  const bool store = tc_lane_row<U>(l, i, im);  // row pairs (i, i + 1) sit in lanes (l, l + 1)
-  const bool odd = (l & 1) != 0;
+  const bool store = tc_lane_row<U>(l, i, im);  // rows (i, i + 1) of one part sit in lanes (l, l + 2)
+  const bool upper = (i & 1) != 0;
   const int kk = i & ~1;
-  // rows (im ? U : 0) + h CW + (odd ? CW/2 : 0) + t: a multiple of 8 plus t < 8
-  const int row8 = ((im ? U : 0) + h * btc::CW + (odd ? btc::CW / 2 : 0)) >> 3;
+  const int row8 = ((im ? U : 0) + h * btc::CW + (upper ? btc::CW / 2 : 0)) >> 3;
   uint8_t* base = dst + row8 * 1024 + ((kk & 7) << 1);
   const int kc = kk >> 3;
 #pragma unroll
   for (int t = 0; t < btc::CW / 2; ++t) {
-    const float lo_v = __uint_as_float(raw[t]), hi_v = __uint_as_float(raw[btc::CW / 2 + t]);
-    const float from_next = __shfl_down_sync(0xffffffffu, lo_v, 1);  // even lanes: k + 1
-    const float from_prev = __shfl_up_sync(0xffffffffu, hi_v, 1);    // odd lanes: k - 1
+    // column offsets within the half: real rows k: t, imaginary rows k: t + 4, real rows k + 1:
+    // t + 2, imaginary rows k + 1: t + 6 (mod 8)
+    const int lo_re = t, lo_im = (t + 4) & 7, up_re = (t + 2) & 7, up_im = (t + 6) & 7;
+    const float x1 = __uint_as_float(im ? raw[lo_im] : raw[lo_re]);
+    const float x2 = __uint_as_float(im ? raw[btc::CW / 2 + up_im] : raw[btc::CW / 2 + up_re]);
+    const float from_upper = __shfl_down_sync(0xffffffffu, x1, 2);  // row k + 1, the column of row k
+    const float from_lower = __shfl_up_sync(0xffffffffu, x2, 2);    // row k, the column of row k + 1
     if (store) {
       uint32_t w0, w1, w2;
-      split3x2(odd ? from_prev : lo_v, odd ? hi_v : from_next, w0, w1, w2);
-      uint8_t* at = base + t * 128 + ((kc ^ t) << 4);
+      split3x2(upper ? from_lower : x1, upper ? x2 : from_upper, w0, w1, w2);
+      const int c = upper ? (im ? up_im : up_re) : (im ? lo_im : lo_re);  // row8 * 8 + c, c < 8
+      uint8_t* at = base + c * 128 + ((kc ^ c) << 4);
       *reinterpret_cast<uint32_t*>(at) = w0;
       *reinterpret_cast<uint32_t*>(at + btc::PIECE) = w1;
       *reinterpret_cast<uint32_t*>(at + 2 * btc::PIECE) = w2;
@@ -485,22 +481,20 @@ __device__ __forceinline__ void tc_issue(uint32_t d_tmem, uint32_t l_saddr, uint
 
 // out = mode(C) from the accumulator D of a product (see above) on this warp's 32 x CW block
 // of the real form; returns this thread's sum of squares of the result (residual mode, valid
-// lanes only). Every worker thread calls it (three worker barriers inside).
+// lanes only). Every lane of the warp calls it (shuffles).
 template <int U>
 __device__ __forceinline__ float tc_epilogue(uint32_t tmem, uint32_t cAcc, uint32_t cD, uint32_t cOut, int mode,
-                                             float* ex, int q, int h, int l) {
-  // Every warp reads and writes its block, also a block of columns >= U (U = 48): those lie
-  // inside the accumulator's 2U and the masters' 64 columns and carry no data (zeros written).
+                                             int q, int h, int l) {
+  // Every warp reads and writes its block, also padding lanes and a block of columns >= U
+  // (U = 48): those lie inside the accumulator's 2U and the masters' 64 columns, carry no data
+  // and feed only padding rows and columns (the residual sum skips them).
   int i;
   bool im;
   const bool valid = tc_lane_row<U>(l, i, im) && h * btc::CW < U;
   const bool re = !im;
   const uint32_t lane_off = uint32_t(q * 32) << 16;
-  // cross terms: real-part lanes need Pi Qi (Cr = Pr Qr - Pi Qi), imaginary-part lanes need
-  // Pr Qi (Ci = Pi Qr + Pr Qi); each lane publishes its own cross term in direction re / im and
-  // reads its partner's, half of its columns per phase so that every warp works each phase
-  float* mine = ex + (re ? 0 : btc::EX_DIR) + i * btc::EX_PITCH + h * (btc::CW / 2);
-  const float* theirs = ex + (re ? btc::EX_DIR : 0) + i * btc::EX_PITCH + h * (btc::CW / 2);
+  // cross terms: the real-part lane needs Pi Qi (Cr = Pr Qr - Pi Qi) and the imaginary-part
+  // lane Pr Qi (Ci = Pi Qr + Pr Qi): each is the other lane's own cross term (lanes l, l ^ 1)
   const float sgn = re ? -1.f : 1.f;
   float local = 0.f;
 #pragma unroll
@@ -511,34 +505,19 @@ __device__ __forceinline__ float tc_epilogue(uint32_t tmem, uint32_t cAcc, uint3
     tmem_ld_32x32b_x8(tmem + lane_off + cAcc + uint32_t(U) + col, dx);
     if (mode == BM_ADD) tmem_ld_32x32b_x8(tmem + lane_off + cD + col, dm);
     tmem_ld_wait();
-    if (ph == 1) tc_wsync();  // the partner has read phase 0's cross terms
-    if (valid) {
-      reinterpret_cast<float4*>(mine)[0] = make_float4(__uint_as_float(dx[0]), __uint_as_float(dx[1]),
-                                                       __uint_as_float(dx[2]), __uint_as_float(dx[3]));
-      reinterpret_cast<float4*>(mine)[1] = make_float4(__uint_as_float(dx[4]), __uint_as_float(dx[5]),
-                                                       __uint_as_float(dx[6]), __uint_as_float(dx[7]));
-    }
-    tc_wsync();
-    if (valid) {
-      const float4 x0 = reinterpret_cast<const float4*>(theirs)[0];
-      const float4 x1 = reinterpret_cast<const float4*>(theirs)[1];
-      const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int j = int(col) + t;
-        const float cv = fmaf(sgn, xs[t], __uint_as_float(dd[t]));
-        float v;
-        if (mode == BM_RESID) {
-          v = ((re && j == i) ? 1.f : 0.f) - cv;
-          local = fmaf(v, v, local);
-        } else {
-          v = __uint_as_float(dm[t]) + cv;
-        }
-        dd[t] = __float_as_uint(v);
+    for (int t = 0; t < 8; ++t) {
+      const float x = __shfl_xor_sync(0xffffffffu, __uint_as_float(dx[t]), 1);
+      const int j = int(col) + t;
+      const float cv = fmaf(sgn, x, __uint_as_float(dd[t]));
+      float v;
+      if (mode == BM_RESID) {
+        v = ((re && j == i) ? 1.f : 0.f) - cv;
+        if (valid) local = fmaf(v, v, local);
+      } else {
+        v = __uint_as_float(dm[t]) + cv;
       }
-    } else {
-#pragma unroll
-      for (int t = 0; t < 8; ++t) dd[t] = 0u;
+      dd[t] = __float_as_uint(v);
     }
     tmem_st_32x32b_x8(tmem + lane_off + cOut + col, dd);
   }
@@ -687,7 +666,6 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
                                                 const int32_t* items, uint8_t* ops, uint32_t ops_s, uint32_t tmem,
                                                 uint64_t* mma_bar, int* abort_word, int* item_sh, float* red_warp,
                                                 TcCmd* cmd) {
-  float* ex = reinterpret_cast<float*>(ops + btc::EX);
   const int w = int(threadIdx.x >> 5), q = w & 3, h = w >> 2, l = q * 32 + int(threadIdx.x & 31);
   const int nslots = p.depth <= 2 ? 2 : 1;
   TcSlot sl0 = {-1, 0, 0, NN_OK, 0.f, 0.f}, sl1 = sl0;  // two named slots: no local memory
@@ -746,7 +724,7 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
     const uint32_t sb = uint32_t(s) * btc::SLOT_COLS;
     TcSlot t = s == 0 ? sl0 : sl1;
     const TcProd pr = tc_product(t, sb, p.depth);
-    const float ss = tc_epilogue<U>(tmem, sb + btc::ACC, pr.cD, pr.cOut, pr.mode, ex, q, h, l);
+    const float ss = tc_epilogue<U>(tmem, sb + btc::ACC, pr.cD, pr.cOut, pr.mode, q, h, l);
     tc_fence_before();
     bool done = false;
     if (pr.mode == BM_RESID) {
