@@ -253,16 +253,18 @@ int nn_solve_normal(const void* A, int64_t n, int64_t lda, int is_complex, const
  * nn_batched_plan (host only): sorts the matrices by size (largest first) and groups equal
  * sizes into work items. sizes_host[count] in 1..64; cfg_by_u (nullable, 65 entries indexed by
  * U, -1 = default) picks the path per size (0: CUDA cores, 8x8 threads per matrix, up to four
- * matrices per CTA; 1: CUDA cores, 16x16 threads per matrix; 2: tensor cores, for U in
+ * matrices per CTA; 1: CUDA cores, 16x16 threads per matrix; 3: CUDA cores, one warp per
+ * matrix, for U in {8, 16, 24, 32} (other sizes fall back to 0 or 1); 2: tensor cores, for U in
  * {48, 64} (other sizes fall back to 0 or 1): the iterates stay in TMEM, each complex product
  * is a tcgen05 MMA chain on the real embedding [[Pr, -Pi], [Pi, Pr]] [Qr; Qi] with three BF16
  * pieces per operand, FP32-level accuracy, two matrices per SM in a software pipeline);
  * plan_host holds nn_batched_plan_size(count)
  * int32. The caller copies the plan to the device and may reuse it for every launch with the
- * same size list. Layout: [n_items, count, n_tc, class_first[19], order[count],
+ * same size list. Layout: [n_items, count, n_tc, class_first[23], order[count],
  * items[n_items][4]]; order = matrix indices by size, largest first; item = (U, first position
  * in order, matrices, cfg); items are grouped by tile class (classes 0, 1 = tensor cores for
- * U = 64, 48; 2..17 = CUDA-core (threads per matrix, tile, exact U) classes), class c spanning items
+ * U = 64, 48; 2..17 = CUDA-core (threads per matrix, tile, exact U) classes; 18..21 = one warp
+ * per matrix, U = 32, 24, 16, 8), class c spanning items
  * [class_first[c], class_first[c + 1]).
  *
  * nn_invert_batched_c64: A and X device complex64 (interleaved re, im) packed back to back,
@@ -273,7 +275,7 @@ int nn_solve_normal(const void* A, int64_t n, int64_t lda, int is_complex, const
  * NN_BATCHED_KERNELS kernels, one per tile class, chained by programmatic dependent launch;
  * no synchronisation, no allocation), so it can be captured in a CUDA graph. Needs
  * nn_batched_workspace_bytes(count) of workspace. */
-#define NN_BATCHED_KERNELS 18
+#define NN_BATCHED_KERNELS 22
 int64_t nn_batched_plan_size(int64_t count);
 int nn_batched_plan(const int32_t* sizes_host, int64_t count, const int32_t* cfg_by_u, int32_t* plan_host);
 size_t nn_batched_workspace_bytes(int64_t count);

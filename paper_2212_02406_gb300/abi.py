@@ -26,7 +26,7 @@ NN_ERR_TOO_LARGE = 8
 STATUS_NAMES = {0: "ok", 1: "arg", 2: "diverged", 3: "not_converged", 4: "oom_budget", 5: "timeout",
                 6: "cuda", 7: "unsupported", 8: "too_large"}
 NN_RESIDUAL_NOALLOC_MAX_N = 1440
-NN_BATCHED_KERNELS = 18
+NN_BATCHED_KERNELS = 22
 
 NN_F64, NN_F32, NN_MIXED_BF16, NN_F64_DF, NN_F64_EMU, NN_MIXED_EMU = 0, 1, 2, 3, 4, 5
 DTYPES = {"f64": NN_F64, "f32": NN_F32, "mixed_bf16": NN_MIXED_BF16, "f64_df": NN_F64_DF,

@@ -41,7 +41,8 @@ constexpr int BT_SMEM = 193 * 1024;         // dynamic shared memory of a tensor
 constexpr int BT_SMEM_SIMT = 112 * 1024;
 constexpr int BT_SMEM_SIMT_DEEP = BT_SMEM_SIMT / 3 * 4;
 // Tile classes: 0, 1 = tensor-core items of U = 64, 48; 2..17 = CUDA-core items, ordered by
-// cost: 16x16 threads then 8x8, tile 4 down to 1, exact U (= tile * threads per side) first.
+// cost: 16x16 threads then 8x8, tile 4 down to 1, exact U (= tile * threads per side) first;
+// 18..21 = warp-per-matrix CUDA-core items of U = 32, 24, 16, 8.
 constexpr int BT_NCLS = NN_BATCHED_KERNELS;
 constexpr int PLAN_HDR = 3 + BT_NCLS + 1;   // [n_items, count, n_tc, class_first[BT_NCLS + 1]]
 constexpr int BT_QUEUE_ERR = 32;            // workspace: int counters [0, BT_NCLS), error word here
@@ -49,8 +50,9 @@ constexpr int BT_QUEUE_ERR = 32;            // workspace: int counters [0, BT_NC
 static_assert(BT_NCLS <= BT_QUEUE_ERR && (BT_QUEUE_ERR + 1) * 4 <= 256, "counters fit the workspace");
 
 __host__ __device__ constexpr int bt_class(int cfg, int U) {
-  return cfg == 2 ? (U == 64 ? 0 : 1)
-                  : 2 + (cfg == 0 ? 8 : 0) + (4 - (U + (cfg == 0 ? 7 : 15)) / (cfg == 0 ? 8 : 16)) * 2 +
+  return cfg == 3   ? 18 + (4 - U / 8)
+         : cfg == 2 ? (U == 64 ? 0 : 1)
+                    : 2 + (cfg == 0 ? 8 : 0) + (4 - (U + (cfg == 0 ? 7 : 15)) / (cfg == 0 ? 8 : 16)) * 2 +
                         (U % (cfg == 0 ? 8 : 16) == 0 ? 0 : 1);
 }
 
@@ -871,6 +873,156 @@ __global__ void __launch_bounds__(btc::THREADS + 32, 1) batched_tc_kernel(const 
   pdl_wait();
 }
 
+// ---- warp-per-matrix CUDA-core path (plan configuration 3; U in {8, 16, 24, 32}) ----------
+//
+// One warp runs one matrix's whole loop; its products need only warp synchronisation, so the
+// warps of an SM never wait for each other. Thread (ti, tj) of the 8 x 4 warp grid owns rows
+// ti + 8a (a < U/8) and columns tj + 4b (b < U/4) of every product. Matrices live in shared
+// memory with rows padded to U + 1 complex (the eight rows a k step reads fall in different
+// banks); three buffers per matrix (A, X, R), four at depth >= 3 (T).
+namespace bw {
+template <int U>
+struct Shape {
+  static constexpr int TR = U / 8, TC = U / 4, PITCH = U + 1;
+  static constexpr int MAT = U * PITCH;  // float2 per buffer
+};
+// warps per CTA for (U, buffers): shared memory up to about 200 KB, at most 32 warps
+__host__ __device__ constexpr int warps_per_cta(int U, int bufs) {
+  return (200 * 1024) / (bufs * U * (U + 1) * 8) < 32 ? (200 * 1024) / (bufs * U * (U + 1) * 8) : 32;
+}
+}  // namespace bw
+
+// acc = P Q for this thread's tile (all U k steps).
+template <int U>
+__device__ __forceinline__ void warp_acc(const float2* P, const float2* Q, int ti, int tj,
+                                         float2 (&acc)[bw::Shape<U>::TR][bw::Shape<U>::TC]) {
+  using S = bw::Shape<U>;
+#pragma unroll
+  for (int a = 0; a < S::TR; ++a)
+#pragma unroll
+    for (int b = 0; b < S::TC; ++b) acc[a][b] = make_float2(0.f, 0.f);
+#pragma unroll 4
+  for (int k = 0; k < U; ++k) {
+    float2 pa[S::TR], qb[S::TC];
+#pragma unroll
+    for (int a = 0; a < S::TR; ++a) pa[a] = P[(ti + 8 * a) * S::PITCH + k];
+#pragma unroll
+    for (int b = 0; b < S::TC; ++b) qb[b] = Q[k * S::PITCH + tj + 4 * b];
+#pragma unroll
+    for (int a = 0; a < S::TR; ++a)
+#pragma unroll
+      for (int b = 0; b < S::TC; ++b) {
+        acc[a][b].x = fmaf(pa[a].x, qb[b].x, acc[a][b].x);
+        acc[a][b].x = fmaf(-pa[a].y, qb[b].y, acc[a][b].x);
+        acc[a][b].y = fmaf(pa[a].x, qb[b].y, acc[a][b].y);
+        acc[a][b].y = fmaf(pa[a].y, qb[b].x, acc[a][b].y);
+      }
+  }
+}
+
+// out = I - P Q (mode RESID, returns this thread's sum of |out|^2) or D + P Q (mode ADD); out
+// may alias P, Q or D (the warp synchronises between the product and the stores).
+template <int U>
+__device__ __forceinline__ float warp_product(const float2* P, const float2* Q, const float2* D, float2* out,
+                                              int mode, int ti, int tj) {
+  using S = bw::Shape<U>;
+  float2 acc[S::TR][S::TC];
+  warp_acc<U>(P, Q, ti, tj, acc);
+  __syncwarp();
+  float ss = 0.f;
+#pragma unroll
+  for (int a = 0; a < S::TR; ++a)
+#pragma unroll
+    for (int b = 0; b < S::TC; ++b) {
+      const int i = ti + 8 * a, j = tj + 4 * b;
+      float2 v;
+      if (mode == BM_RESID) {
+        v = make_float2((i == j ? 1.f : 0.f) - acc[a][b].x, -acc[a][b].y);
+        ss = fmaf(v.x, v.x, fmaf(v.y, v.y, ss));
+      } else {
+        const float2 d = D[i * S::PITCH + j];
+        v = make_float2(d.x + acc[a][b].x, d.y + acc[a][b].y);
+      }
+      out[i * S::PITCH + j] = v;
+    }
+  __syncwarp();
+  return ss;
+}
+
+// One matrix, the whole NN loop, by one warp (lane = threadIdx.x % 32).
+template <int U>
+__device__ void warp_item(const BatchedParams& p, int b, float2* buf, int lane) {
+  using S = bw::Shape<U>;
+  const int ti = lane >> 2, tj = lane & 3;
+  float2* Ab = buf;
+  float2* Xb = buf + S::MAT;
+  float2* Rb = buf + 2 * S::MAT;
+  float2* Tb = p.depth >= 3 ? buf + 3 * S::MAT : Rb;
+  const int64_t off = p.offsets[b];
+  for (int e = lane; e < U * U; e += 32) Ab[(e / U) * S::PITCH + e % U] = p.A[off + e];
+  __syncwarp();
+  const float c = 1.f / (1.f + p.damping * float(U));
+  for (int e = lane; e < U * U; e += 32) {
+    const int i = e / U, j = e % U;
+    float2 v = make_float2(0.f, 0.f);
+    if (i == j) {
+      const float2 a = Ab[i * S::PITCH + i];
+      const float den = a.x * a.x + a.y * a.y;
+      v = make_float2(c * a.x / den, -c * a.y / den);
+    }
+    Xb[i * S::PITCH + j] = v;
+  }
+  __syncwarp();
+  float s_prev = 0.f, s_last = 0.f;
+  int st = NN_OK;
+  for (int k = 0; k <= p.nests; ++k) {
+    float ss = warp_product<U>(Ab, Xb, nullptr, Rb, BM_RESID, ti, tj);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const float s = sqrtf(ss) / float(U);
+    s_last = s;
+    if (!isfinite(s) || (k >= 1 && s >= 1.f && s > s_prev)) {
+      st = NN_ERR_DIVERGED;
+      break;
+    }
+    s_prev = s;
+    if (k == p.nests) break;
+    // Horner: T_1 = R, T_{j+1} = R + R T_j (depth 2: in place of R); X_{k+1} = X_k + X_k T
+    const float2* t_cur = Rb;
+    for (int j = 1; j < p.depth; ++j) {
+      warp_product<U>(Rb, t_cur, Rb, Tb, BM_ADD, ti, tj);
+      t_cur = Tb;
+    }
+    warp_product<U>(Xb, t_cur, Xb, Xb, BM_ADD, ti, tj);
+  }
+  for (int e = lane; e < U * U; e += 32) p.X[off + e] = Xb[(e / U) * S::PITCH + e % U];
+  if (lane == 0) {
+    p.residual[b] = s_last;
+    p.status[b] = st;
+  }
+  __syncwarp();
+}
+
+// The configuration-3 items of size U (classes 18..21): each warp pulls single matrices.
+template <int U>
+__global__ void __launch_bounds__(32 * bw::warps_per_cta(U, 3)) batched_warp_kernel(const BatchedParams p, int cls) {
+  extern __shared__ float2 smem[];
+  pdl_launch_dependents();
+  const int count = p.plan[1];
+  const int first = p.plan[3 + cls], last = p.plan[3 + cls + 1];
+  const int32_t* items = p.plan + PLAN_HDR + count;
+  const int lane = int(threadIdx.x & 31), w = int(threadIdx.x >> 5);
+  float2* buf = smem + size_t(w) * (p.depth >= 3 ? 4 : 3) * bw::Shape<U>::MAT;
+  while (first < last) {
+    int it = 0;
+    if (lane == 0) it = first + atomicAdd(p.queue + cls, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= last) break;
+    warp_item<U>(p, p.plan[PLAN_HDR + items[4 * it + 1]], buf, lane);
+  }
+  pdl_wait();
+}
+
 // The CUDA-core items of one class (TG x TG threads per matrix, T x T tile, UC = exact U or
 // 0): two CTAs per SM at depth <= 2.
 template <int TG, int T, int UC>
@@ -899,13 +1051,16 @@ __global__ void __launch_bounds__(BT_THREADS, 2) batched_simt_kernel(const Batch
 using SimtKernel = void (*)(const BatchedParams, int);
 
 // Kernel of each CUDA-core class, in class order (bt_class).
-const SimtKernel kSimtKernels[BT_NCLS - 2] = {
+const SimtKernel kSimtKernels[16] = {
     batched_simt_kernel<16, 4, 64>, batched_simt_kernel<16, 4, 0>, batched_simt_kernel<16, 3, 48>,
     batched_simt_kernel<16, 3, 0>,  batched_simt_kernel<16, 2, 32>, batched_simt_kernel<16, 2, 0>,
     batched_simt_kernel<16, 1, 16>, batched_simt_kernel<16, 1, 0>,  batched_simt_kernel<8, 4, 32>,
     batched_simt_kernel<8, 4, 0>,   batched_simt_kernel<8, 3, 24>,  batched_simt_kernel<8, 3, 0>,
     batched_simt_kernel<8, 2, 16>,  batched_simt_kernel<8, 2, 0>,   batched_simt_kernel<8, 1, 8>,
     batched_simt_kernel<8, 1, 0>};
+
+// Dynamic shared memory of a warp-per-matrix CTA (U, buffers per matrix).
+int warp_smem(int U, int bufs) { return bw::warps_per_cta(U, bufs) * bufs * U * (U + 1) * int(sizeof(float2)); }
 
 int g_bt_sms = 0;
 bool g_bt_init = false;
@@ -924,13 +1079,20 @@ int bt_init() {
   }
   for (SimtKernel k : kSimtKernels)
     NN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM_SIMT_DEEP));
+  const SimtKernel warp_kernels[4] = {batched_warp_kernel<32>, batched_warp_kernel<24>, batched_warp_kernel<16>,
+                                      batched_warp_kernel<8>};
+  for (int c = 0; c < 4; ++c) {
+    const int U = 32 - 8 * c;
+    NN_CUDA_TRY(cudaFuncSetAttribute(warp_kernels[c], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     std::max(warp_smem(U, 3), warp_smem(U, 4))));
+  }
   g_bt_init = true;
   return NN_OK;
 }
 
 // Matrices per work item for (U, cfg): thread groups available and shared memory.
 int group_count(int U, int cfg) {
-  if (cfg == 2) return 1;
+  if (cfg >= 2) return 1;
   const int by_threads = cfg == 0 ? BT_THREADS / 64 : 1;
   const int per = bt_buffers(2) * U * U * int(sizeof(float2));
   int by_smem = BT_SMEM_SIMT / per;
@@ -967,8 +1129,9 @@ int nn_batched_plan(const int32_t* sizes_host, int64_t count, const int32_t* cfg
   while (pos < count) {
     const int U = sizes_host[order[size_t(pos)]];
     int cfg = (cfg_by_u != nullptr && cfg_by_u[U] >= 0) ? cfg_by_u[U] : (U <= 32 ? 0 : 1);
-    if (cfg < 0 || cfg > 2) return NN_ERR_ARG;
+    if (cfg < 0 || cfg > 3) return NN_ERR_ARG;
     if (cfg == 2 && U != 48 && U != 64) cfg = U <= 32 ? 0 : 1;
+    if (cfg == 3 && (U % 8 != 0 || U > 32)) cfg = U <= 32 ? 0 : 1;
     if (cfg == 0 && (U + 7) / 8 > 4) cfg = 1;  // 8 x 8 threads with up to 4 x 4 elements each
     const int gmax = group_count(U, cfg);
     int cnt = 0;
@@ -1044,7 +1207,18 @@ int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* 
   cfg.gridDim = dim3(unsigned(depth <= 2 ? 2 * g_bt_sms : g_bt_sms));
   cfg.blockDim = dim3(BT_THREADS);
   cfg.dynamicSmemBytes = size_t(depth <= 2 ? BT_SMEM_SIMT : BT_SMEM_SIMT_DEEP);
-  for (int c = 2; c < BT_NCLS; ++c) NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kSimtKernels[c - 2], p, c));
+  for (int c = 2; c < 18; ++c) NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kSimtKernels[c - 2], p, c));
+  const int bufs = depth >= 3 ? 4 : 3;
+  const SimtKernel warp_kernels[4] = {batched_warp_kernel<32>, batched_warp_kernel<24>, batched_warp_kernel<16>,
+                                      batched_warp_kernel<8>};
+  for (int c = 18; c < BT_NCLS; ++c) {
+    const int U = 8 * (4 - (c - 18));
+    const int warps = bw::warps_per_cta(U, bufs);
+    cfg.gridDim = dim3(unsigned(g_bt_sms));
+    cfg.blockDim = dim3(unsigned(32 * warps));
+    cfg.dynamicSmemBytes = size_t(warp_smem(U, bufs));
+    NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, warp_kernels[c - 18], p, c));
+  }
   return NN_OK;
 }
 

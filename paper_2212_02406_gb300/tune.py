@@ -2,7 +2,8 @@
 
 For every matrix size U it times nn_invert_batched_c64 on a homogeneous batch under each
 configuration (0: CUDA cores, 8 x 8 threads per matrix, up to four matrices per CTA; 1: CUDA
-cores, 16 x 16 threads per matrix; 2: tensor cores, U in {48, 64}) and keeps the
+cores, 16 x 16 threads per matrix; 2: tensor cores, U in {48, 64}; 3: CUDA cores, one warp
+per matrix, U in {8, 16, 24, 32}) and keeps the
 fastest. The result is a table U -> configuration, written
 as JSON and passed to nn_batched_plan by callers (bench.py reads
 ``paper_2212_02406_gb300/batched_tuning.json``).
@@ -56,10 +57,12 @@ def tune(sizes=(8, 16, 24, 32, 48, 64), count=4096, depth=2, nests=3, reps=5):
     table, timings = {}, {}
     for u in sizes:
         best = None
-        for cfg in (0, 1, 2):
+        for cfg in (0, 1, 2, 3):
             if cfg == 1 and (u + 15) // 16 > 4:
                 continue
             if cfg == 2 and u not in (48, 64):
+                continue
+            if cfg == 3 and u not in (8, 16, 24, 32):
                 continue
             ms = time_config(abi, torch, u, cfg, count, depth, nests, reps, seed=u)
             timings[f"{u}:{cfg}"] = ms

@@ -76,6 +76,8 @@ def _plan_class(cfg, u):
     """Tile class of an item as the header defines it: 0, 1 = tensor cores for U = 64, 48;
     CUDA-core classes ordered by threads per matrix (16 x 16 first), tile (4 down to 1), exact
     U first."""
+    if cfg == 3:
+        return 18 + (4 - u // 8)
     if cfg == 2:
         return 0 if u == 64 else 1
     tg = 8 if cfg == 0 else 16
@@ -83,7 +85,8 @@ def _plan_class(cfg, u):
     return 2 + (8 if cfg == 0 else 0) + (4 - t) * 2 + (0 if u % tg == 0 else 1)
 
 
-@pytest.mark.parametrize("cfg_by_u", [None, {u: 0 for u in range(1, 33)}, {16: 2, 32: 2, 48: 2, 64: 2, 40: 2}])
+@pytest.mark.parametrize("cfg_by_u", [None, {u: 0 for u in range(1, 33)}, {16: 2, 32: 2, 48: 2, 64: 2, 40: 2},
+                                      {u: 3 for u in range(1, 65)}])
 def test_batched_plan_layout(lib, cfg_by_u):
     """nn_batched_plan (host only): every matrix appears once, sizes within an item are equal,
     items of a tile class are contiguous and largest first, and the class table brackets them."""
@@ -113,8 +116,9 @@ def test_batched_plan_layout(lib, cfg_by_u):
             assert _plan_class(cfg, u) == c
             assert u <= prev_u
             prev_u = u
-            assert 1 <= cnt and (cfg != 1 or cnt == 1) and (cfg != 2 or cnt == 1) and cnt <= 4
+            assert 1 <= cnt and (cfg == 0 or cnt == 1) and cnt <= 4
             assert cfg != 2 or u in (48, 64)
+            assert cfg != 3 or u in (8, 16, 24, 32)
             assert cfg != 0 or u <= 32
             assert np.all(sizes[order[start:start + cnt]] == u)
             assert not covered[start:start + cnt].any()

@@ -86,7 +86,7 @@ def test_mixed_sizes_match_oracle(nn, depth, damping):
     assert n_conv > 0
 
 
-@pytest.mark.parametrize("cfg", [0, 1])
+@pytest.mark.parametrize("cfg", [0, 1, 3])
 def test_tile_configs_agree(nn, cfg):
     bt = synth.mimo_gram_batch(48, seed=11, sizes=(8, 24, 40, 64, 5, 17, 33, 63, 1))
     x, res, st = _run(nn, bt, 2, 4, 1.0 / 128.0, cfg_by_u={u: cfg for u in range(1, 65)})
@@ -102,6 +102,16 @@ def test_tensor_core_items_match_oracle(nn, depth, damping):
     bt = synth.mimo_gram_batch(60, seed=20 + depth, sizes=(16, 32, 48, 64, 8, 24, 40))
     x, res, st = _run(nn, bt, depth, 3, damping, cfg_by_u={u: 2 for u in range(1, 65)})
     n_conv = _check(bt, x, res, st, depth, 3, damping)
+    assert n_conv > 0
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_warp_items_match_oracle(nn, depth):
+    # plan configuration 3 (U in {8, 16, 24, 32}): one warp per matrix, warp synchronisation
+    # only; other sizes fall back to the CTA-wide CUDA-core classes
+    bt = synth.mimo_gram_batch(80, seed=40 + depth, sizes=(8, 16, 24, 32, 5, 40, 64))
+    x, res, st = _run(nn, bt, depth, 3, 1.0 / 128.0, cfg_by_u={u: 3 for u in range(1, 65)})
+    n_conv = _check(bt, x, res, st, depth, 3, 1.0 / 128.0)
     assert n_conv > 0
 
 
