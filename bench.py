@@ -604,7 +604,9 @@ def run_batched(args, rank, world, local_rank):
     if args.batched_tc:
         table = dict(table or {})
         table.update({48: 2, 64: 2})
-    plan = torch.from_numpy(abi.nn_batched_plan(bt.sizes, table)).to(dev)
+    plan_host = abi.nn_batched_plan(bt.sizes, table)
+    classes = abi.nn_batched_plan_classes(plan_host)
+    plan = torch.from_numpy(plan_host).to(dev)
     X = torch.empty_like(A)
     res = torch.empty(count, dtype=torch.float32, device=dev)
     st = torch.empty(count, dtype=torch.int32, device=dev)
@@ -613,11 +615,13 @@ def run_batched(args, rank, world, local_rank):
     s.wait_stream(torch.cuda.current_stream(dev))
     with torch.cuda.stream(s):
         for _ in range(2):
-            assert abi.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws, s) == 0
+            assert abi.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws, s,
+                                             classes=classes) == 0
     torch.cuda.current_stream(dev).wait_stream(s)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
-        assert abi.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws) == 0
+        assert abi.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws,
+                                         classes=classes) == 0
     for _ in range(args.warmup):
         g.replay()
     stream = torch.cuda.current_stream(dev)
@@ -655,7 +659,7 @@ def run_batched(args, rank, world, local_rank):
                                    f"dependent launch, replayed from a CUDA graph",
                        "count": count, "damping": damping, "l2": "A + X = 363 MB > L2",
                        "tensor_core_items": bool(args.batched_tc) or any(v == 2 for v in (table or {}).values())},
-            "status_ok_fraction": float(np.mean(stats == 0)), "gpu_launches": abi.NN_BATCHED_KERNELS * args.steps,
+            "status_ok_fraction": float(np.mean(stats == 0)), "gpu_launches": bin(classes).count("1") * args.steps,
             "tflops": round(tflops, 2), "gbs": round(byts / (ms / 1e3) / 1e9, 1),
             "roofline": {"kernel": "the batch: batched_tc_kernel<U> (tuned sizes, tensor cores) + batched_simt_kernel<TG, T, U> (CUDA cores), useful complex FLOPs", "bound": "alu",
                          "achieved": round(tflops, 2),

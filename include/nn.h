@@ -265,22 +265,27 @@ int nn_solve_normal(const void* A, int64_t n, int64_t lda, int is_complex, const
  * in order, matrices, cfg); items are grouped by tile class (classes 0, 1 = tensor cores for
  * U = 64, 48; 2..17 = CUDA-core (threads per matrix, tile, exact U) classes; 18..21 = one warp
  * per matrix, U = 32, 24, 16, 8), class c spanning items
- * [class_first[c], class_first[c + 1]).
+ * [class_first[c], class_first[c + 1]). nn_batched_plan_classes (host only) returns the mask of
+ * the classes that hold items (bit c for class c; 0 for a null plan).
  *
  * nn_invert_batched_c64: A and X device complex64 (interleaved re, im) packed back to back,
  * matrix b row-major at element offset offsets[b] (device int64) with size sizes[b] (device
- * int32); plan = the device copy of the plan. residual[b] (device float) = s of the returned
- * X_b; status[b] (device int32) = NN_OK, NN_ERR_DIVERGED, or NN_ERR_TIMEOUT (a tensor-core
- * item whose bounded wait ran out). The call only enqueues work on `stream` (a memset and
- * NN_BATCHED_KERNELS kernels, one per tile class, chained by programmatic dependent launch;
- * no synchronisation, no allocation), so it can be captured in a CUDA graph. Needs
- * nn_batched_workspace_bytes(count) of workspace. */
+ * int32); plan = the device copy of the plan; classes = nn_batched_plan_classes of its host
+ * copy (or any superset, e.g. 0xFFFFFFFF: a class without items costs one empty launch; a
+ * class with items left out is not computed); NN_ERR_ARG if no class bit is set.
+ * residual[b] (device float) = s of the returned X_b; status[b] (device int32) = NN_OK,
+ * NN_ERR_DIVERGED, or NN_ERR_TIMEOUT (a tensor-core item whose bounded wait ran out). The call
+ * only enqueues work on `stream` (a memset and one kernel per selected tile class, at most
+ * NN_BATCHED_KERNELS, chained by programmatic dependent launch; no synchronisation, no
+ * allocation), so it can be captured in a CUDA graph. Needs nn_batched_workspace_bytes(count)
+ * of workspace. */
 #define NN_BATCHED_KERNELS 22
 int64_t nn_batched_plan_size(int64_t count);
 int nn_batched_plan(const int32_t* sizes_host, int64_t count, const int32_t* cfg_by_u, int32_t* plan_host);
+uint32_t nn_batched_plan_classes(const int32_t* plan_host);
 size_t nn_batched_workspace_bytes(int64_t count);
 int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* sizes, int64_t count,
-                          const int32_t* plan, int depth, int nests, double damping, void* X,
+                          const int32_t* plan, uint32_t classes, int depth, int nests, double damping, void* X,
                           float* residual, int32_t* status, void* workspace, size_t ws_bytes,
                           void* stream);
 

@@ -13,6 +13,7 @@ from .abi import (  # noqa: F401
     nn_csr_workspace_bytes,
     nn_solve_csr,
     nn_batched_plan,
+    nn_batched_plan_classes,
     nn_invert_batched_c64,
     nn_workspace_bytes,
     nn_workspace_bytes_host,

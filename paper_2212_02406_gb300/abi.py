@@ -107,9 +107,10 @@ _SIGNATURES = {
     "nn_server_destroy": (c_int, [c_void_p]),
     "nn_batched_plan_size": (c_int64, [c_int64]),
     "nn_batched_plan": (c_int, [c_void_p, c_int64, c_void_p, c_void_p]),
+    "nn_batched_plan_classes": (ctypes.c_uint32, [c_void_p]),
     "nn_batched_workspace_bytes": (c_size_t, [c_int64]),
-    "nn_invert_batched_c64": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int, c_int, c_double,
-                                      c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "nn_invert_batched_c64": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, ctypes.c_uint32, c_int, c_int,
+                                      c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "nn_solve_csr": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int, c_void_p, c_int64, c_int64, c_int,
                              c_int, c_double, c_void_p, c_int64, POINTER(NNResult), c_void_p, c_size_t, c_void_p]),
 }
@@ -413,14 +414,23 @@ def nn_batched_plan(sizes, cfg_by_u=None):
     return plan
 
 
+def nn_batched_plan_classes(plan) -> int:
+    """Mask of the tile classes that hold items, from a host plan (NumPy int32 array)."""
+    import numpy as np
+
+    plan = np.ascontiguousarray(plan, dtype=np.int32)
+    return int(lib().nn_batched_plan_classes(c_void_p(plan.ctypes.data)))
+
+
 def nn_batched_workspace_bytes(count: int) -> int:
     return int(lib().nn_batched_workspace_bytes(int(count)))
 
 
 def nn_invert_batched_c64(A, offsets, sizes, plan, depth, nests, damping, X, residual, status, workspace,
-                          stream=None) -> int:
+                          stream=None, classes=0xFFFFFFFF) -> int:
     """A, X: complex64 CUDA tensors (packed); offsets int64, sizes int32, plan int32, residual float32,
-    status int32 CUDA tensors. Enqueues only (graph-capturable); returns the status code."""
+    status int32 CUDA tensors; classes = nn_batched_plan_classes of the host plan (default: all).
+    Enqueues only (graph-capturable); returns the status code."""
     import torch
 
     if A.dtype != torch.complex64 or X.dtype != torch.complex64 or not (A.is_cuda and X.is_cuda):
@@ -433,7 +443,8 @@ def nn_invert_batched_c64(A, offsets, sizes, plan, depth, nests, damping, X, res
     pw, nw = _ws(workspace)
     return lib().nn_invert_batched_c64(c_void_p(A.data_ptr()), c_void_p(offsets.data_ptr()),
                                        c_void_p(sizes.data_ptr()), sizes.numel(), c_void_p(plan.data_ptr()),
-                                       int(depth), int(nests), float(damping), c_void_p(X.data_ptr()),
+                                       int(classes) & 0xFFFFFFFF, int(depth), int(nests), float(damping),
+                                       c_void_p(X.data_ptr()),
                                        c_void_p(residual.data_ptr()), c_void_p(status.data_ptr()), pw, nw,
                                        _stream_ptr(stream))
 

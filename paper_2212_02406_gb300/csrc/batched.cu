@@ -1167,12 +1167,22 @@ size_t nn_batched_workspace_bytes(int64_t count) {
   return 256;
 }
 
+uint32_t nn_batched_plan_classes(const int32_t* plan_host) {
+  if (plan_host == nullptr) return 0;
+  uint32_t mask = 0;
+  for (int c = 0; c < BT_NCLS; ++c)
+    if (plan_host[3 + c + 1] > plan_host[3 + c]) mask |= 1u << c;
+  return mask;
+}
+
 int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* sizes, int64_t count,
-                          const int32_t* plan, int depth, int nests, double damping, void* X, float* residual,
-                          int32_t* status, void* workspace, size_t ws_bytes, void* stream) {
+                          const int32_t* plan, uint32_t classes, int depth, int nests, double damping, void* X,
+                          float* residual, int32_t* status, void* workspace, size_t ws_bytes, void* stream) {
   if (A == nullptr || offsets == nullptr || sizes == nullptr || plan == nullptr || X == nullptr ||
       residual == nullptr || status == nullptr || count < 1)
     return NN_ERR_ARG;
+  classes &= (1u << BT_NCLS) - 1u;
+  if (classes == 0) return NN_ERR_ARG;
   if (depth < 1 || depth > 16 || nests < 0 || nests > NN_MAX_HISTORY - 1 || !(damping >= 0)) return NN_ERR_ARG;
   if (workspace == nullptr || ws_bytes < nn_batched_workspace_bytes(count)) return NN_ERR_OOM_BUDGET;
   NN_TRY(bt_init());
@@ -1191,33 +1201,40 @@ int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* 
   p.queue = static_cast<int*>(workspace);
   p.err = static_cast<int*>(workspace) + BT_QUEUE_ERR;
   NN_CUDA_TRY(cudaMemsetAsync(p.queue, 0, nn_batched_workspace_bytes(count), st));
-  batched_tc_kernel<64><<<g_bt_sms, btc::THREADS + 32, BT_SMEM, st>>>(p, 0);
-  NN_CUDA_TRY(cudaGetLastError());
+  // the classes' kernels in class order; each after the first may start as the previous
+  // one's CTAs retire (programmatic dependent launch)
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(g_bt_sms));
-  cfg.blockDim = dim3(btc::THREADS + 32);
-  cfg.dynamicSmemBytes = size_t(BT_SMEM);
   cfg.stream = st;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, batched_tc_kernel<48>, p, 1));
-  cfg.gridDim = dim3(unsigned(depth <= 2 ? 2 * g_bt_sms : g_bt_sms));
-  cfg.blockDim = dim3(BT_THREADS);
-  cfg.dynamicSmemBytes = size_t(depth <= 2 ? BT_SMEM_SIMT : BT_SMEM_SIMT_DEEP);
-  for (int c = 2; c < 18; ++c) NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kSimtKernels[c - 2], p, c));
+  cfg.numAttrs = 0;
   const int bufs = depth >= 3 ? 4 : 3;
   const SimtKernel warp_kernels[4] = {batched_warp_kernel<32>, batched_warp_kernel<24>, batched_warp_kernel<16>,
                                       batched_warp_kernel<8>};
-  for (int c = 18; c < BT_NCLS; ++c) {
-    const int U = 8 * (4 - (c - 18));
-    const int warps = bw::warps_per_cta(U, bufs);
-    cfg.gridDim = dim3(unsigned(g_bt_sms));
-    cfg.blockDim = dim3(unsigned(32 * warps));
-    cfg.dynamicSmemBytes = size_t(warp_smem(U, bufs));
-    NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, warp_kernels[c - 18], p, c));
+  for (int c = 0; c < BT_NCLS; ++c) {
+    if (((classes >> c) & 1u) == 0) continue;
+    SimtKernel k;
+    if (c < 2) {
+      k = c == 0 ? batched_tc_kernel<64> : batched_tc_kernel<48>;
+      cfg.gridDim = dim3(unsigned(g_bt_sms));
+      cfg.blockDim = dim3(btc::THREADS + 32);
+      cfg.dynamicSmemBytes = size_t(BT_SMEM);
+    } else if (c < 18) {
+      k = kSimtKernels[c - 2];
+      cfg.gridDim = dim3(unsigned(depth <= 2 ? 2 * g_bt_sms : g_bt_sms));
+      cfg.blockDim = dim3(BT_THREADS);
+      cfg.dynamicSmemBytes = size_t(depth <= 2 ? BT_SMEM_SIMT : BT_SMEM_SIMT_DEEP);
+    } else {
+      const int U = 8 * (4 - (c - 18));
+      k = warp_kernels[c - 18];
+      cfg.gridDim = dim3(unsigned(g_bt_sms));
+      cfg.blockDim = dim3(unsigned(32 * bw::warps_per_cta(U, bufs)));
+      cfg.dynamicSmemBytes = size_t(warp_smem(U, bufs));
+    }
+    NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, p, c));
+    cfg.numAttrs = 1;
   }
   return NN_OK;
 }

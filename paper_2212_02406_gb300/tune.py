@@ -31,17 +31,19 @@ def time_config(abi, torch, u: int, cfg: int, count: int, depth: int, nests: int
     X = torch.empty_like(A)
     offs = torch.from_numpy(offsets).cuda()
     sz = torch.from_numpy(sizes).cuda()
-    plan = torch.from_numpy(abi.nn_batched_plan(sizes, {u: cfg})).cuda()
+    plan_host = abi.nn_batched_plan(sizes, {u: cfg})
+    classes = abi.nn_batched_plan_classes(plan_host)
+    plan = torch.from_numpy(plan_host).cuda()
     res = torch.empty(count, dtype=torch.float32, device="cuda")
     st = torch.empty(count, dtype=torch.int32, device="cuda")
     ws = torch.empty(abi.nn_batched_workspace_bytes(count), dtype=torch.uint8, device="cuda")
     for _ in range(2):
-        abi.nn_invert_batched_c64(A, offs, sz, plan, depth, nests, 1.0 / 128, X, res, st, ws)
+        abi.nn_invert_batched_c64(A, offs, sz, plan, depth, nests, 1.0 / 128, X, res, st, ws, classes=classes)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
-        abi.nn_invert_batched_c64(A, offs, sz, plan, depth, nests, 1.0 / 128, X, res, st, ws)
+        abi.nn_invert_batched_c64(A, offs, sz, plan, depth, nests, 1.0 / 128, X, res, st, ws, classes=classes)
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps

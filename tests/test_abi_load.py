@@ -124,5 +124,7 @@ def test_batched_plan_layout(lib, cfg_by_u):
             assert not covered[start:start + cnt].any()
             covered[start:start + cnt] = True
     assert covered.all()
+    mask = abi.nn_batched_plan_classes(plan)
+    assert mask == sum(1 << c for c in range(ncls) if class_first[c + 1] > class_first[c])
     if cfg_by_u and cfg_by_u.get(64) == 2:
         assert n_tc > 0 and all(int(items[i, 0]) in (48, 64) for i in range(n_tc))

@@ -32,7 +32,9 @@ def _run(nn, bt, depth, nests, damping, cfg_by_u=None, graph=False):
     A = torch.from_numpy(bt.data.astype(np.complex64)).cuda()
     offs = torch.from_numpy(bt.offsets.astype(np.int64)).cuda()
     sizes = torch.from_numpy(bt.sizes.astype(np.int32)).cuda()
-    plan = torch.from_numpy(nn.nn_batched_plan(bt.sizes, cfg_by_u)).cuda()
+    plan_host = nn.nn_batched_plan(bt.sizes, cfg_by_u)
+    classes = nn.nn_batched_plan_classes(plan_host)
+    plan = torch.from_numpy(plan_host).cuda()
     X = torch.empty_like(A)
     res = torch.empty(bt.count, dtype=torch.float32, device="cuda")
     st = torch.empty(bt.count, dtype=torch.int32, device="cuda")
@@ -41,17 +43,19 @@ def _run(nn, bt, depth, nests, damping, cfg_by_u=None, graph=False):
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
-            assert nn.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws, s) == 0
+            assert nn.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws, s,
+                                            classes=classes) == 0
         torch.cuda.current_stream().wait_stream(s)
         g = torch.cuda.CUDAGraph()
         X.zero_()
         with torch.cuda.graph(g):
-            rc = nn.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws)
+            rc = nn.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws, classes=classes)
         assert rc == 0
         g.replay()
         g.replay()
     else:
-        assert nn.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws) == 0
+        assert nn.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws,
+                                        classes=classes) == 0
     torch.cuda.synchronize()
     return X.cpu().numpy(), res.cpu().numpy(), st.cpu().numpy()
 
@@ -129,6 +133,27 @@ def test_single_and_tiny(nn):
     x, res, st = _run(nn, bt, 2, 2, 0.0)
     a = bt.matrix(0)
     assert st[0] == 0 and abs(x[0] - 1.0 / a[0, 0]) <= 1e-6 * abs(1.0 / a[0, 0])
+
+
+def test_all_classes_mask_matches_plan_mask(nn):
+    # launching every class (empty ones exit at once) gives the same bits as the plan's mask
+    import torch
+
+    bt = synth.mimo_gram_batch(40, seed=6)
+    x1, r1, s1 = _run(nn, bt, 2, 3, 1.0 / 128.0)
+    A = torch.from_numpy(bt.data.astype(np.complex64)).cuda()
+    offs = torch.from_numpy(bt.offsets.astype(np.int64)).cuda()
+    sizes = torch.from_numpy(bt.sizes.astype(np.int32)).cuda()
+    plan = torch.from_numpy(nn.nn_batched_plan(bt.sizes)).cuda()
+    X = torch.empty_like(A)
+    res = torch.empty(bt.count, dtype=torch.float32, device="cuda")
+    st = torch.empty(bt.count, dtype=torch.int32, device="cuda")
+    ws = torch.empty(nn.nn_batched_workspace_bytes(bt.count), dtype=torch.uint8, device="cuda")
+    assert nn.nn_invert_batched_c64(A, offs, sizes, plan, 2, 3, 1.0 / 128.0, X, res, st, ws) == 0
+    assert nn.nn_invert_batched_c64(A, offs, sizes, plan, 2, 3, 1.0 / 128.0, X, res, st, ws, classes=0) == nn.NN_ERR_ARG
+    torch.cuda.synchronize()
+    assert np.array_equal(X.cpu().numpy(), x1) and np.array_equal(res.cpu().numpy(), r1)
+    assert np.array_equal(st.cpu().numpy(), s1)
 
 
 def test_graph_capture_replay(nn):
