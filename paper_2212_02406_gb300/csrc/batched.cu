@@ -1,26 +1,29 @@
 // Batched NN inversion of many small complex matrices (massive-MIMO Gram matrices,
-// U x U with U <= 64) in one persistent kernel.
+// U x U with U <= 64) in persistent kernels.
 //
 // Each matrix runs the right-multiplied NN loop of the dense path (Theorem, Eq.
-// (nestedneumann); L = 1 Newton, L = 2 Chebyshev as in Corollary 4) entirely in shared
-// memory, from the damped Jacobi start X_0 = diag(A)^-1 / (1 + damping U) (a diagonal Theta,
-// Appendix 1), for a fixed number of nests:
+// (nestedneumann); L = 1 Newton, L = 2 Chebyshev as in Corollary 4) entirely on chip (shared
+// memory, or TMEM on the tensor-core path), from the damped Jacobi start
+// X_0 = diag(A)^-1 / (1 + damping U) (a diagonal Theta, Appendix 1), for a fixed number of
+// nests:
 //     k = 0..nests:  R = I - A X_k, s_k = ||R||_F / U;  stop if diverged or k = nests;
 //                    T = R, L-1 times T = R + R T;  X_{k+1} = X_k + X_k T.
 // Divergence (s_k non-finite, or s_k >= 1 and s_k > s_{k-1}) freezes X at X_k, as the dense
 // path does.
 //
 // Scheduling: the host plan (nn_batched_plan) sorts the matrices by size, largest first,
-// and cuts them into work items of G equal-size matrices. Inside a CTA, G thread groups run
-// G matrices in lock-step (same U, same barriers). Two tile configurations exist per size:
-//   cfg 0: 8 x 8 threads per matrix, each computing a ceil(U/8)^2 tile of every product;
-//   cfg 1: 16 x 16 threads per matrix, tile ceil(U/16)^2, one matrix per CTA.
-// The plan takes a per-size configuration table, which the autotuner fills. Items fall into
-// tile classes (tensor cores; or CUDA cores with a given (threads per matrix, tile, exact U)),
-// and each class has its own persistent kernel, compiled alone so that the CUDA-core ones fit
-// 128 registers and run two 256-thread CTAs per SM. The classes' kernels are chained with
-// programmatic dependent launch: the next class's CTAs take the SM slots that the previous
-// class frees at its tail. Each kernel pulls the items of its class from its own counter.
+// and cuts them into work items of equal-size matrices, each with a configuration taken from a
+// per-size table (the autotuner fills it):
+//   cfg 0: CUDA cores, 8 x 8 threads per matrix, each computing a ceil(U/8)^2 tile of every
+//          product, up to four matrices per CTA in lock-step;
+//   cfg 1: CUDA cores, 16 x 16 threads per matrix, tile ceil(U/16)^2, one matrix per CTA;
+//   cfg 2: tensor cores, U in {48, 64} (see the tensor-core notes below);
+//   cfg 3: CUDA cores, one warp per matrix, U in {8, 16, 24, 32}.
+// Items fall into tile classes, and each class has its own persistent kernel, compiled alone
+// so that the CTA-wide CUDA-core ones fit 128 registers and run two 256-thread CTAs per SM.
+// Only the classes that hold items are launched, chained with programmatic dependent launch:
+// the next class's CTAs take the SM slots that the previous class frees at its tail. Each
+// kernel pulls the items of its class from its own counter.
 #include <math.h>
 #include <string.h>
 
