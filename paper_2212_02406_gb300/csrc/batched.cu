@@ -295,10 +295,9 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
 //         D (2U x 2U) = [Pr; Pi] (2U x U) . [Qr | Qi] (U x 2U)
 //           = [[Pr Qr, Pr Qi], [Pi Qr, Pi Qi]],   Cr = Pr Qr - Pi Qi,  Ci = Pi Qr + Pr Qi,
 //     i.e. M = 128 (2U rows used, in the lanes' order), N = 2U, K = U. The left operand's rows
-//     are P's master lanes;
-//     the right operand (K-major: row n < U = column n of Qr, row U + n = column n of Qi) is the
-//     transpose of Q's master. A's left operand is split once per matrix and kept in shared
-//     memory (one copy per slot);
+//     are P's master lanes; the right operand (K-major: row n < U = column n of Qr, row U + n =
+//     column n of Qi) is the transpose of Q's master. A's left operand is split once per matrix
+//     and kept in shared memory (one copy per slot);
 //   * operands are split into three BF16 pieces (x = p0 + p1 + p2, each the BF16 rounding of the
 //     remainder) and written in the SWIZZLE_128B K-major layout; the six piece products with
 //     i + j <= 2 (smallest first) accumulate in FP32 in TMEM, which matches an FP32 product to
@@ -307,9 +306,10 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
 //     the other lane's own cross term, exchanged with one lane shuffle; then I - C or D + C is
 //     applied in FP32 and written to the result master, and the residual's sum of squares is
 //     reduced across the workers;
-//   * the two slots alternate: while the tensor core runs one slot's product, the CTA finishes
-//     the other slot's previous product; then it stages the other slot's next product once the
-//     MMAs (which read the single staging buffers) have completed.
+//   * the two slots alternate: 16 worker warps stage one slot's product and hand it to a 17th
+//     warp that only issues its MMA chain; while the tensor core runs it, the workers finish
+//     the other slot's previous product, then stage that slot's next product once the MMAs
+//     (which read the single staging buffers) have completed.
 namespace btc {
 constexpr int M = 128;                         // MMA rows (2U used)
 constexpr int CW = 16;                         // master columns per warp (TMEM access: 32 lanes x 16)
