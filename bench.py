@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--batched-tc", action="store_true",
                     help="batched workload: tensor-core items for U in {48, 64}")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-scalar-x0", action="store_true",
+                    help="dense workload: run the first nest's residual and update as GEMMs (no X_0 = alpha I hint)")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.n is None:
@@ -202,7 +204,9 @@ def run_dense(args, rank, world, local_rank):
     st = abi.nn_init_precond(A, "scalar", alpha, X0, ws)
     assert st == abi.NN_OK, st
     X = torch.empty_like(A)
-    opts = abi.make_opts(args.depth, args.tol, 64, args.dtype, flags=abi.NN_FLAG_TIME_KERNELS)
+    # X_0 = alpha I: the mixed chain runs the first nest's residual and update element-wise
+    opts = abi.make_opts(args.depth, args.tol, 64, args.dtype, flags=abi.NN_FLAG_TIME_KERNELS,
+                         x0_scalar=0.0 if args.no_scalar_x0 else alpha)
     stream = torch.cuda.current_stream(dev)
 
     for _ in range(args.warmup):

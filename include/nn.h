@@ -101,6 +101,11 @@ typedef struct nn_opts {
                           (CNS) construction of Corollary 4 / Corollary 6; after nests of depths
                           L_0..L_{k-1} X_k is the Neumann series of order prod(L_j + 1) - 1    */
   int schedule_len;    /* entries of depth_schedule, 0 .. NN_MAX_HISTORY (0: every nest `depth`) */
+  double x0_scalar;    /* > 0: the caller asserts X_0 = x0_scalar * I (X0 must still be passed).
+                          NN_MIXED_BF16 / NN_MIXED_EMU then run the first nest's residual
+                          R_0 = I - x0_scalar A and update X_1 = x0_scalar (I + T) element-wise
+                          (no GEMM, no pieces of X_0); the other dtypes read X0 as usual.
+                          nn_result.flops still counts the method's 2 N^3 for both products. */
 } nn_opts;
 
 /* nn_opts.flags: time every GEMM launch of the chain with CUDA events on the call's stream

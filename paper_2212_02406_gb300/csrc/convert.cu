@@ -93,8 +93,39 @@ struct PiecePtrs {
 // transposed pieces go out through shared memory as 4-byte pairs along the output rows.
 constexpr int SPLIT_R = 32, SPLIT_C = 128;
 
-__global__ void split_kernel(const double* __restrict__ src, int64_t lds, int n, int np, float* __restrict__ f32,
-                             PiecePtrs row, int n_row, PiecePtrs col, int n_col, double* __restrict__ sumsq) {
+// Four consecutive source values of row i from column jj (zeros past n), as FP64.
+__device__ __forceinline__ void split_load4(const double* src, int64_t lds, int n, int i, int jj, double (&v)[4]) {
+  if (i < n && jj + 3 < n && ((lds & 1) | (reinterpret_cast<uintptr_t>(src) & 15)) == 0) {
+    const double2* p2 = reinterpret_cast<const double2*>(src + int64_t(i) * lds + jj);
+    const double2 a = p2[0], b = p2[1];
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = (i < n && jj + e < n) ? src[int64_t(i) * lds + jj + e] : 0.0;
+  }
+}
+__device__ __forceinline__ void split_load4(const float* src, int64_t lds, int n, int i, int jj, double (&v)[4]) {
+  if (i < n && jj + 3 < n && ((lds & 3) | (reinterpret_cast<uintptr_t>(src) & 15)) == 0) {
+    const float4 a = *reinterpret_cast<const float4*>(src + int64_t(i) * lds + jj);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = (i < n && jj + e < n) ? double(src[int64_t(i) * lds + jj + e]) : 0.0;
+  }
+}
+
+// Splits the n x n matrix scale * src + diag * I (FP64 arithmetic; AFFINE = false: src as is)
+// into its FP32 rounding and BF16 pieces.
+template <typename S, bool AFFINE>
+__global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int np, float* __restrict__ f32,
+                             PiecePtrs row, int n_row, PiecePtrs col, int n_col, double* __restrict__ sumsq,
+                             double scale, double diag) {
   __shared__ __nv_bfloat16 tile[3][SPLIT_R][SPLIT_C + 2];  // odd word pitch: conflict-free columns
   __shared__ float red[ROWS];
   const int i0 = blockIdx.y * SPLIT_R, j0 = blockIdx.x * SPLIT_C;
@@ -104,16 +135,11 @@ __global__ void split_kernel(const double* __restrict__ src, int64_t lds, int n,
   for (int r = ty; r < SPLIT_R; r += ROWS) {
     const int i = i0 + r;
     double v[4];
-    if (i < n && jj + 3 < n && ((lds & 1) | (reinterpret_cast<uintptr_t>(src) & 15)) == 0) {
-      const double2* p2 = reinterpret_cast<const double2*>(src + int64_t(i) * lds + jj);
-      const double2 a = p2[0], b = p2[1];
-      v[0] = a.x;
-      v[1] = a.y;
-      v[2] = b.x;
-      v[3] = b.y;
-    } else {
+    split_load4(src, lds, n, i, jj, v);
+    if (AFFINE) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) v[e] = (i < n && jj + e < n) ? src[int64_t(i) * lds + jj + e] : 0.0;
+      for (int e = 0; e < 4; ++e)
+        if (i < n && jj + e < n) v[e] = scale * v[e] + (i == jj + e ? diag : 0.0);
     }
     __nv_bfloat16 pc[4][3];
     float hi[4];
@@ -327,9 +353,36 @@ int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np,
   for (int q = 0; q < n_row; ++q) r.p[q] = row_pieces[q];
   for (int q = 0; q < n_col; ++q) c.p[q] = col_pieces[q];
   dim3 grid(np / SPLIT_C, np / SPLIT_R), block(32, ROWS);
-  split_kernel<<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial);
+  split_kernel<double, false><<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial, 1.0,
+                                                      0.0);
   NN_CUDA_TRY(cudaGetLastError());
   return NN_OK;
+}
+
+template <typename S>
+static int split_affine(cudaStream_t st, const S* src, int64_t lds, int n, int np, float* f32,
+                        __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
+                        double* sumsq_partial, double scale, double diag) {
+  if (np % SPLIT_C != 0 || n > np || n_row < 0 || n_row > 3 || n_col < 0 || n_col > 3) return NN_ERR_ARG;
+  PiecePtrs r{}, c{};
+  for (int q = 0; q < n_row; ++q) r.p[q] = row_pieces[q];
+  for (int q = 0; q < n_col; ++q) c.p[q] = col_pieces[q];
+  dim3 grid(np / SPLIT_C, np / SPLIT_R), block(32, ROWS);
+  split_kernel<S, true><<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial, scale, diag);
+  NN_CUDA_TRY(cudaGetLastError());
+  return NN_OK;
+}
+
+int split_matrix_affine(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
+                        __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
+                        double* sumsq_partial, double scale, double diag) {
+  return split_affine(st, src, lds, n, np, f32, row_pieces, n_row, col_pieces, n_col, sumsq_partial, scale, diag);
+}
+
+int split_matrix_affine(cudaStream_t st, const float* src, int64_t lds, int n, int np, float* f32,
+                        __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
+                        double* sumsq_partial, double scale, double diag) {
+  return split_affine(st, src, lds, n, np, f32, row_pieces, n_row, col_pieces, n_col, sumsq_partial, scale, diag);
 }
 
 int split_blocks(int np) { return (np / SPLIT_C) * (np / SPLIT_R); }

@@ -88,6 +88,14 @@ bool tc_supported();
 int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
                  __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
                  double* sumsq_partial);
+// The same for scale * src + diag * I (FP64 arithmetic on the FP64 or FP32 source): element-wise
+// products with a scalar X_0 (R_0 = I - a A, X_1 = a (I + T)).
+int split_matrix_affine(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
+                        __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
+                        double* sumsq_partial, double scale, double diag);
+int split_matrix_affine(cudaStream_t st, const float* src, int64_t lds, int n, int np, float* f32,
+                        __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
+                        double* sumsq_partial, double scale, double diag);
 int split_blocks(int np);
 // dst (FP64, ldd) = src (FP32, lds), n x n.
 int f32_to_f64(cudaStream_t st, const float* src, int64_t lds, int n, double* dst, int64_t ldd);

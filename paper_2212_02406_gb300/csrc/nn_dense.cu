@@ -402,9 +402,15 @@ struct HostOut {
 
 namespace {
 
-int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const Common& cm, double a_frob,
-              const X0Source& x0src, nn_result* res, int* final_idx, HostOut* ho) {
+int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedWs& w, const nn_opts& o,
+              const Common& cm, double a_frob, const X0Source& x0src, nn_result* res, int* final_idx, HostOut* ho) {
   const int np = w.np;
+  // X_0 = alpha I (the caller's assertion): the first nest's residual R_0 = I - alpha A and update
+  // X_1 = alpha (I + T) are element-wise, split straight into the chain's layouts from FP64 A
+  // and the FP32 T; the chain's other products are unchanged.
+  const bool scalar_x0 = o.x0_scalar > 0;
+  const double alpha = o.x0_scalar;
+  const int sb = split_blocks(np);
   const double sqrt_n = sqrt(double(n));
   const double n15 = double(n) * sqrt(double(n));
   int level = (o.bulk_pieces >= 1 && o.bulk_pieces <= 4) ? o.bulk_pieces : 1;
@@ -440,13 +446,33 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
     x_frob = vals[1];
     return NN_OK;
   };
+  auto residual0 = [&](int L, double* s_out) -> int {
+    const int hp = level_upd_pieces(L);
+    const bool rows = max_depth(o) >= 2;
+    NN_TRY(split_matrix_affine(st, A, lda, n, np, rows ? w.r32 : nullptr, w.r_row, rows ? hp : 0, w.r_col, hp,
+                               w.split_partial, -alpha, 1.0));
+    NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0 / double(n), cm.scal));
+    res->launches += 2;
+    int dev_err = 0;
+    double vals[2];
+    NN_TRY(fetch_scalars(st, cm, vals, 2, &dev_err));
+    if (dev_err != DEV_OK) return NN_ERR_TIMEOUT;
+    *s_out = vals[0];
+    x_frob = alpha * sqrt(double(n));  // ||X_0||_F
+    return NN_OK;
+  };
 
   int rollbacks = 0;
   bool restarted = false;
   double x_frob_prev = 0;  // ||X_{k-1}||_F, kept for a rollback
-  for (int k = 0;; ++k) {
+  int k = 0;
+  // the residual of X_k at level L (element-wise for k = 0 with a scalar X_0)
+  auto measure = [&](int L, double* s_out) -> int {
+    return (scalar_x0 && k == 0) ? residual0(L, s_out) : residual(L, s_out);
+  };
+  for (;; ++k) {
     double s = 0;
-    NN_TRY(residual(level, &s));
+    NN_TRY(measure(level, &s));
     // Slow first contraction (s_1 > 0.85 s_0) marks a residual spectrum crowded near 1, i.e.
     // large kappa: there the rounding of BF16 bulk nests, amplified by the (L+1)-fold growth of
     // errors along eigenvalues of R close to 1, can push rho(R) past 1 nests later. Discard
@@ -460,9 +486,11 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
       cur = 0;
       k = 0;
       level = 2;
-      NN_TRY(load_x0(st, n, w, cm, x0src));
-      res->launches += 2;
-      NN_TRY(residual(level, &s));
+      if (!scalar_x0) {
+        NN_TRY(load_x0(st, n, w, cm, x0src));
+        res->launches += 2;
+      }
+      NN_TRY(measure(level, &s));
     }
     const double c = a_frob * x_frob / n15;
     {
@@ -482,7 +510,7 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
         const bool remeasure = level_res_pieces(target) != level_res_pieces(level) ||
                                level_upd_pieces(target) != level_upd_pieces(level);
         level = target;
-        if (remeasure) NN_TRY(residual(level, &s));
+        if (remeasure) NN_TRY(measure(level, &s));
       }
     }
     // A nest that made the residual grow below the top level was spoiled by rounding
@@ -496,7 +524,7 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
       --k;
       x_frob = x_frob_prev;
       level = 4;
-      NN_TRY(residual(level, &s));
+      NN_TRY(measure(level, &s));
       x_frob = x_frob_prev;
     }
     res->history[k] = s;
@@ -539,7 +567,10 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
         likely_final = o.tol > 0 && s_pred < 0.5 * o.tol && next_level >= 3;
       }
     }
-    // Horner: T_1 = R (its column pieces), T_{j+1} = R + R T_j.
+    // Horner: T_1 = R (its column pieces), T_{j+1} = R + R T_j. With a scalar X_0 the first
+    // nest's last Horner product also leaves T in FP32 over R's FP32 copy (each element read as
+    // the addend, then written), for the element-wise update below.
+    const bool update0 = scalar_x0 && k == 0;
     __nv_bfloat16* const* t_cur = w.r_col;
     for (int j = 1; j < nest_depth(o, k); ++j) {
       TcGemmArgs g;
@@ -548,6 +579,7 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
       g.mode = EPI_ADD;
       g.add = w.r32;
       g.n_col = hp;
+      if (update0 && j == nest_depth(o, k) - 1) g.out_f32 = w.r32;
       for (int i = 0; i < 3; ++i) g.col_pieces[i] = w.t_col[j & 1][i];
       int grid = 0;
       NN_TRY(tc_product(st, g, hp, w.r_row, t_cur, cm, res, &grid, &timer));
@@ -559,7 +591,18 @@ int run_mixed(cudaStream_t st, int n, const MixedWs& w, const nn_opts& o, const 
       NN_CUDA_TRY(cudaStreamWaitEvent(st, ho->done, 0));
       if (ho->spec_buf == (cur ^ 1)) ho->spec_nests = -1;
     }
-    {
+    if (update0) {
+      // X_1 = alpha I + alpha T: T = R_0 = I - alpha A at depth 1 (X_1 = 2 alpha I - alpha^2 A
+      // from FP64 A), else T in FP32 from the last Horner product
+      if (nest_depth(o, k) == 1)
+        NN_TRY(split_matrix_affine(st, A, lda, n, np, w.x32[cur ^ 1], w.x_row[cur ^ 1], 3, w.x_col[cur ^ 1], 3,
+                                   w.split_partial, -alpha * alpha, 2.0 * alpha));
+      else
+        NN_TRY(split_matrix_affine(st, w.r32, np, n, np, w.x32[cur ^ 1], w.x_row[cur ^ 1], 3, w.x_col[cur ^ 1], 3,
+                                   w.split_partial, alpha, alpha));
+      NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0, cm.scal + 1));
+      res->launches += 2;
+    } else {
       TcGemmArgs g;
       g.np = np;
       g.n_id = n;
@@ -617,6 +660,7 @@ int check_opts(const nn_opts* o, int64_t n) {
   if (!valid_dtype(o->dtype)) return NN_ERR_ARG;
   if (n < 1 || n > 32768) return NN_ERR_ARG;
   if (isnan(o->tol)) return NN_ERR_ARG;
+  if (!(o->x0_scalar >= 0.0) || !isfinite(o->x0_scalar)) return NN_ERR_ARG;
   return NN_OK;
 }
 
@@ -672,12 +716,12 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     NN_TRY(split_matrix(st, A, lda, ni, w.np, nullptr, w.a_row, 3, nullptr, 0, w.split_partial));
     NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0, cm.scal + 2));
     const X0Source x0src{X0, ldx0};
-    NN_TRY(load_x0(st, ni, w, cm, x0src));
+    if (o.x0_scalar <= 0) NN_TRY(load_x0(st, ni, w, cm, x0src));  // a scalar X_0 needs no pieces
     double a_frob = 0;
     NN_CUDA_TRY(cudaMemcpyAsync(&a_frob, cm.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
     NN_CUDA_TRY(cudaStreamSynchronize(st));
     res->launches += 4;
-    NN_TRY(run_mixed(st, ni, w, o, cm, a_frob, x0src, res, &fin, ho));
+    NN_TRY(run_mixed(st, ni, A, lda, w, o, cm, a_frob, x0src, res, &fin, ho));
     if (ho != nullptr && ho->pending) NN_CUDA_TRY(cudaStreamWaitEvent(st, ho->done, 0));
     if (o.dtype == NN_MIXED_EMU && res->status == NN_ERR_NOT_CONVERGED && res->nests < o.max_nests) {
       // Continue from the mixed chain's last iterate with emulated FP64 nests (NN converges from
@@ -811,9 +855,13 @@ int invert_host_impl(const double* A_host, int64_t n, const double* X0_host, int
   if (!c.ok) return NN_ERR_OOM_BUDGET;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   NN_CUDA_TRY(cudaMemcpyAsync(dA, A_host, e * sizeof(double), cudaMemcpyHostToDevice, st));
+  // a scalar preconditioner on the mixed chain: X_0 = pc_scalar I is never materialised
+  nn_opts oh = *opts;
+  const bool mixed = opts->dtype == NN_MIXED_BF16 || opts->dtype == NN_MIXED_EMU;
+  if (X0_host == nullptr && pc_kind == NN_PC_SCALAR && mixed && pc_scalar > 0) oh.x0_scalar = pc_scalar;
   if (X0_host != nullptr) {
     NN_CUDA_TRY(cudaMemcpyAsync(dX0, X0_host, e * sizeof(double), cudaMemcpyHostToDevice, st));
-  } else {
+  } else if (!(mixed && oh.x0_scalar > 0 && pc_kind == NN_PC_SCALAR)) {
     NN_TRY(precond_fill(st, dA, n, int(n), pc_kind, pc_scalar, dX0, n, pc_scratch, pc_vec));
     res->launches += 2;
   }
@@ -832,7 +880,7 @@ int invert_host_impl(const double* A_host, int64_t n, const double* X0_host, int
       return NN_ERR_CUDA;
     }
   }
-  int s = invert_device(dA, n, n, dX0, n, opts, dX, n, res, workspace, inner, st, spec ? &ho : nullptr);
+  int s = invert_device(dA, n, n, dX0, n, &oh, dX, n, res, workspace, inner, st, spec ? &ho : nullptr);
   int rc = s;
   if (!(s == NN_ERR_CUDA || s == NN_ERR_ARG || s == NN_ERR_UNSUPPORTED || s == NN_ERR_OOM_BUDGET)) {
     if (!ho.valid && cudaMemcpyAsync(X_host, dX, e * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)

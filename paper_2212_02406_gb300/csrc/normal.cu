@@ -201,6 +201,7 @@ int nn_solve_normal(const void* A, int64_t n, int64_t lda, int is_complex, const
   // Complex: the embedding's s_k is the complex residual / sqrt(2), so the stop test runs on
   // tol / sqrt(2) and the reported history is scaled back to the complex ||R_k||_F / n.
   nn_opts o = *opts;
+  o.x0_scalar = 0.0;  // X_0 of W is built here, whatever the caller asserted about its own
   const double rs = is_complex ? sqrt(2.0) : 1.0;
   if (is_complex && o.tol > 0) o.tol /= rs;
   const int s = invert_device(w.W, m, m, w.X0, m, &o, w.Xw, m, res, workspace, inner, st);

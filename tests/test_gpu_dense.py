@@ -254,7 +254,8 @@ def test_host_pc_variant_and_early_copy_equal_device(nn, tol, kappa):
     alpha = 2.0 / (lam[0] + lam[-1])
     x0 = dense.precond_scalar(n, alpha)
     for dtype in ("mixed_bf16", "f64"):
-        st1, res1, x1 = _run(nn, a, x0, 2, tol, 40, dtype)
+        # the host call passes the scalar preconditioner to the chain as the X_0 = alpha I hint
+        st1, res1, x1 = _run(nn, a, x0, 2, tol, 40, dtype, x0_scalar=alpha)
         xh = np.full_like(a, np.nan)
         ws = nn.workspace(n, dtype, host=True)
         st2, res2 = nn.nn_invert_host_pc(np.ascontiguousarray(a), "scalar", alpha, nn.make_opts(2, tol, 40, dtype),
@@ -263,6 +264,35 @@ def test_host_pc_variant_and_early_copy_equal_device(nn, tol, kappa):
         assert st1 == st2
         assert res1["nests"] == res2["nests"] and res1["history"] == res2["history"]
         assert np.array_equal(x1, xh)
+
+
+@pytest.mark.parametrize("n", [300, 1024])
+@pytest.mark.parametrize("sched", [[1], [2], [3], [1, 2]])
+@pytest.mark.parametrize("kappa", [1e2, 1e4])
+def test_scalar_x0_hint_matches_explicit_x0(nn, n, sched, kappa):
+    # With x0_scalar the mixed chain forms R_0 = I - alpha A and X_1 = alpha (I + T) element-wise
+    # instead of by GEMMs. The iteration is the same; only rounding in the first nest differs
+    # (the element-wise forms are the more accurate), so both runs must end in the same status,
+    # within one nest, and each must meet the forward-error bound of the module docstring.
+    a, q, lam = synth.spd_spectrum(n, kappa, seed=int(n + kappa) % 997)
+    alpha = 2.0 / (lam[0] + lam[-1])
+    x0 = dense.precond_scalar(n, alpha)
+    tol = 1e-6
+    kw = dict(depth_schedule=sched)
+    st1, res1, x1 = _run(nn, a, x0, sched[-1], tol, 40, "mixed_bf16", **kw)
+    st2, res2, x2 = _run(nn, a, x0, sched[-1], tol, 40, "mixed_bf16", x0_scalar=alpha, **kw)
+    assert st1 == st2, (res1["history"], res2["history"])
+    assert abs(res1["nests"] - res2["nests"]) <= 1
+    assert res2["gemms"] < res1["gemms"]
+    ainv = (q / lam) @ q.T
+    for x, res in ((x1, res1), (x2, res2)):
+        s64 = dense.rms_frob(dense.residual(a, x))
+        assert abs(s64 - res["residual"]) <= e_acc(n) * max(1.0, kappa / 1e2)
+        if st2 == nn.NN_OK:
+            assert _rel(x, ainv) <= 2 * math.sqrt(n) * s64 + 16 * kappa * U32
+    # the first residual of the hinted run is the element-wise I - alpha A
+    s0 = dense.rms_frob(np.eye(n) - alpha * a)
+    assert abs(res2["history"][0] - s0) <= 1e-6 * s0
 
 
 def test_host_pc_rejects_bad_preconditioner(nn):
