@@ -150,14 +150,20 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
     }
     const int64_t off = int64_t(i) * np + jj;
     if (f32) *reinterpret_cast<float4*>(f32 + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-    for (int q = 0; q < n_row; ++q) {
+    // static piece indices (q unrolled) keep pc in registers
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (q >= n_row) break;
       const uint32_t lo2 = uint32_t(__bfloat16_as_ushort(pc[0][q])) | (uint32_t(__bfloat16_as_ushort(pc[1][q])) << 16);
       const uint32_t hi2 = uint32_t(__bfloat16_as_ushort(pc[2][q])) | (uint32_t(__bfloat16_as_ushort(pc[3][q])) << 16);
       *reinterpret_cast<uint2*>(row.p[q] + off) = make_uint2(lo2, hi2);
     }
-    for (int q = 0; q < n_col; ++q)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (q >= n_col) break;
 #pragma unroll
       for (int e = 0; e < 4; ++e) tile[q][r][4 * tx + e] = pc[e][q];
+    }
   }
   if (sumsq != nullptr) {
     // per-block sum of squares (FP32 within the block, fixed order), for ||src||_F
@@ -174,15 +180,20 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
   if (n_col > 0) {
     __syncthreads();
     // transposed: output row j0 + c (c < 128) holds input column j0 + c, entries i0 .. i0 + 31;
-    // thread (tx, ty) writes the pair of entries 2 (tx % 16), +1 of output rows c = 2 ty' + tx / 16
+    // thread t writes entries 8 (t % 4) .. + 7 of output row c = t / 4 (+ 64) as one 16-byte store
     const int t = ty * 32 + tx;
-    for (int c = t / 16; c < SPLIT_C; c += (ROWS * 32) / 16) {
-      const int pr = 2 * (t % 16);
-      const int64_t off = int64_t(j0 + c) * np + i0 + pr;
-      for (int q = 0; q < n_col; ++q) {
-        const uint32_t pair = uint32_t(__bfloat16_as_ushort(tile[q][pr][c])) |
-                              (uint32_t(__bfloat16_as_ushort(tile[q][pr + 1][c])) << 16);
-        *reinterpret_cast<uint32_t*>(col.p[q] + off) = pair;
+    const int r0 = 8 * (t % 4);
+    for (int c = t / 4; c < SPLIT_C; c += (ROWS * 32) / 4) {
+      const int64_t off = int64_t(j0 + c) * np + i0 + r0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q >= n_col) break;
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          w[e] = uint32_t(__bfloat16_as_ushort(tile[q][r0 + 2 * e][c])) |
+                 (uint32_t(__bfloat16_as_ushort(tile[q][r0 + 2 * e + 1][c])) << 16);
+        *reinterpret_cast<uint4*>(col.p[q] + off) = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
   }
