@@ -341,8 +341,8 @@ int tc_product(cudaStream_t st, TcGemmArgs& g, int pieces, __nv_bfloat16* const*
 
 // Precision levels of the mixed chain (BF16 pieces per operand):
 //   level 1: residual 1 piece,  Horner/update 1 piece   (bulk)
-//   level 2: residual 2 pieces, Horner/update 2 pieces
-//   level 3: residual 3 pieces, Horner/update 2 pieces   (FP32-level residual)
+//   level 2: residual 2 pieces, Horner product 1 piece, update 2 pieces
+//   level 3: residual 3 pieces, Horner product 1 piece, update 2 pieces   (FP32-level residual)
 //   level 4: residual 3 pieces, Horner/update 3 pieces
 // A piece-p product has relative error about 2^-(8p+1); the residual error floor of level L
 // is e(L) ~ 2^-b(L) ||A||_F ||X_k||_F / N^1.5, the rms of the rounding of sum_k a_ik x_kj
@@ -569,8 +569,12 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     }
     // Horner: T_1 = R (its column pieces), T_{j+1} = R + R T_j. With a scalar X_0 the first
     // nest's last Horner product also leaves T in FP32 over R's FP32 copy (each element read as
-    // the addend, then written), for the element-wise update below.
+    // the addend, then written), for the element-wise update below. R T_j is second order in
+    // the residual (|R T_j| <= s_k |T_j|), so at levels 2 and 3 one piece less (one pass
+    // instead of three) perturbs the next residual by about 2^-9 s_k^2, far under the floors
+    // those levels serve; its output T keeps the update's pieces.
     const bool update0 = scalar_x0 && k == 0;
+    const int hh = (level == 2 || level == 3) ? hp - 1 : hp;
     __nv_bfloat16* const* t_cur = w.r_col;
     for (int j = 1; j < nest_depth(o, k); ++j) {
       TcGemmArgs g;
@@ -582,7 +586,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       if (update0 && j == nest_depth(o, k) - 1) g.out_f32 = w.r32;
       for (int i = 0; i < 3; ++i) g.col_pieces[i] = w.t_col[j & 1][i];
       int grid = 0;
-      NN_TRY(tc_product(st, g, hp, w.r_row, t_cur, cm, res, &grid, &timer));
+      NN_TRY(tc_product(st, g, hh, w.r_row, t_cur, cm, res, &grid, &timer));
       t_cur = w.t_col[j & 1];
     }
     // Update: X_{k+1} = X_k + X_k T, with ||X_{k+1}||_F from the epilogue partials.
