@@ -157,13 +157,26 @@ int run_job(nn_server* s, const Job& j, cudaStream_t st, nn_completion* c) {
   NN_CUDA_TRY(cudaMemcpyAsync(dA, r.A, e * sizeof(double), cudaMemcpyHostToDevice, st));
   if (nrhs > 0)
     NN_CUDA_TRY(cudaMemcpyAsync(dB, r.B, size_t(n) * size_t(nrhs) * sizeof(double), cudaMemcpyHostToDevice, st));
-  NN_TRY(nn_init_precond(dA, n, n, r.precond, r.pc_scalar, dX0, n, ws, wsb, st));
+  // A scalar X_0 on the mixed chain (the scalar preconditioner, or Theta_1 = I / Tr(A) from the
+  // host copy of A) is passed as the x0_scalar hint and never materialised.
+  double alpha = 0.0;
+  if (r.dtype == NN_MIXED_BF16 && r.precond == NN_PC_SCALAR) alpha = r.pc_scalar;
+  if (r.dtype == NN_MIXED_BF16 && r.precond == NN_PC_TRACE) {
+    double tr = 0.0;
+    for (int64_t i = 0; i < n; ++i) tr += r.A[i * n + i];
+    alpha = tr > 0.0 ? 1.0 / tr : 0.0;
+  }
+  if (!(alpha > 0.0 && std::isfinite(alpha))) {
+    alpha = 0.0;
+    NN_TRY(nn_init_precond(dA, n, n, r.precond, r.pc_scalar, dX0, n, ws, wsb, st));
+  }
   nn_opts o;
   memset(&o, 0, sizeof(o));
   o.depth = s->opts.depth;
   o.tol = s->opts.tol;
   o.max_nests = s->opts.max_nests;
   o.dtype = r.dtype;
+  o.x0_scalar = alpha;
   nn_result res;
   memset(&res, 0, sizeof(res));
   const int st_inv = invert_device(dA, n, n, dX0, n, &o, dX, n, &res, ws, wsb, st);
@@ -171,7 +184,8 @@ int run_job(nn_server* s, const Job& j, cudaStream_t st, nn_completion* c) {
   c->nests = res.nests;
   c->residual = res.residual;
   // X_0: one reduction for the scalar (trace / Theta_2 power steps / none) and the fill
-  const int pc_launches = r.precond == NN_PC_PAN_SCHREIBER ? 3
+  const int pc_launches = alpha > 0.0                         ? 0
+                          : r.precond == NN_PC_PAN_SCHREIBER ? 3
                           : r.precond == NN_PC_TRACE         ? 2
                           : r.precond == NN_PC_THETA2        ? 3 + int(r.pc_scalar)
                                                              : 1;
