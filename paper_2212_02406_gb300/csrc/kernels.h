@@ -76,9 +76,10 @@ void gemm_tc_set_variant(int v);
 // tensor-core kernel's bounded waits.
 size_t emu_workspace_bytes(int64_t n);
 // *hw_flops (nullable) is increased by the tensor-core FLOPs issued (2 Np^3 per slice product).
+// min_bits > 0 truncates the slice products to a relative error of about 2^-min_bits.
 int gemm_f64_emu(cudaStream_t st, int n, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
                  int64_t ldc, int mode, const double* D, int64_t ldd, int n_id, double* partial, int* partials,
-                 void* ws, size_t ws_bytes, int* err, double* hw_flops = nullptr);
+                 void* ws, size_t ws_bytes, int* err, double* hw_flops = nullptr, int min_bits = 0);
 bool tc_supported();
 
 // ---- conversion / preconditioner / reduction kernels (convert.cu) -----------------------

@@ -226,7 +226,7 @@ struct SimtGemm {
   cudaStream_t st;
   int n;
   int operator()(const T* A, int64_t lda, const T* B, int64_t ldb, T* C, int64_t ldc, int mode, const T* D,
-                 int64_t ldd, double* partial, int* nparts) const {
+                 int64_t ldd, double* partial, int* nparts, bool /*second_order*/ = false) const {
     if (nparts) *nparts = gemm_simt_partials<T>(n, n);
     return gemm_simt<T>(st, n, n, n, A, lda, B, ldb, C, ldc, mode, D, ldd, n, partial);
   }
@@ -240,10 +240,13 @@ struct EmuGemm {
   size_t ws_bytes;
   int* err;
   double* hw_flops;
+  // second_order: the Horner product R T_j, which enters the next residual multiplied by the
+  // residual again (about 2^-40 s_k^2 from 40-bit products), runs on the slice products of a
+  // 40-bit result instead of FP64's.
   int operator()(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int mode,
-                 const double* D, int64_t ldd, double* partial, int* nparts) const {
+                 const double* D, int64_t ldd, double* partial, int* nparts, bool second_order = false) const {
     return gemm_f64_emu(st, n, A, lda, B, ldb, C, ldc, mode, D, ldd, n, partial, nparts, ws, ws_bytes, err,
-                        hw_flops);
+                        hw_flops, second_order ? 40 : 0);
   }
 };
 
@@ -284,7 +287,7 @@ int run_simt(cudaStream_t st, int n, const T* A, int64_t lda, T* const X[2], T* 
     const T* t_cur = R;
     for (int j = 1; j < nest_depth(o, k); ++j) {
       T* t_nxt = Tb[j & 1];
-      NN_TRY(timed([&] { return gemm(R, n, t_cur, n, t_nxt, n, EPI_ADD, R, n, nullptr, nullptr); }));
+      NN_TRY(timed([&] { return gemm(R, n, t_cur, n, t_nxt, n, EPI_ADD, R, n, nullptr, nullptr, true); }));
       t_cur = t_nxt;
       res->gemms += 1;
       res->launches += 1;

@@ -215,7 +215,7 @@ size_t emu_workspace_bytes(int64_t n) {
 
 int gemm_f64_emu(cudaStream_t st, int n, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
                  int64_t ldc, int mode, const double* D, int64_t ldd, int n_id, double* partial, int* partials,
-                 void* ws, size_t ws_bytes, int* err, double* hw_flops) {
+                 void* ws, size_t ws_bytes, int* err, double* hw_flops, int min_bits) {
   if (n < 1 || A == nullptr || B == nullptr || C == nullptr || err == nullptr) return NN_ERR_ARG;
   if (mode == EPI_ADD && D == nullptr) return NN_ERR_ARG;
   if (!tc_supported()) return NN_ERR_UNSUPPORTED;
@@ -225,7 +225,10 @@ int gemm_f64_emu(cudaStream_t st, int n, const double* A, int64_t lda, const dou
   if (!c.ok) return NN_ERR_OOM_BUDGET;
   const int np = int(emu_np(n));
   const int beta = emu_beta(n);
-  const int S = emu_slices(beta);
+  // min_bits > 0: only the slice products with s + t < ceil(min_bits / beta) (relative error
+  // about 2^-min_bits instead of FP64's 2^-53)
+  int S = emu_slices(beta);
+  if (min_bits > 0) S = std::min(S, (min_bits + beta - 1) / beta);
 
   init_exps_kernel<<<1, 32, 0, st>>>(w.gexp);
   NN_CUDA_TRY(cudaGetLastError());
