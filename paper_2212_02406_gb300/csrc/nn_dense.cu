@@ -19,8 +19,6 @@
 namespace nn {
 namespace {
 
-constexpr double kDefaultRefineBelow = 0.1;
-
 struct Simt64Ws {
   double* X[2];
   double* R;

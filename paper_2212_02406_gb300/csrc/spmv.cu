@@ -42,9 +42,7 @@ struct ArithF64 {
   using In = double;
   static constexpr bool kBranchTail = true;
   __device__ static V zero() { return 0.0; }
-  __device__ static V mad(V a, V x, V acc) { return fma(a, x, acc); }
   __device__ static V nmad(V a, V x, V acc) { return fma(-a, x, acc); }
-  __device__ static V sub(V a, V b) { return a - b; }
   __device__ static V add(V a, V b) { return a + b; }
   __device__ static double to_d(V a) { return a; }
   __device__ static V from_d(double a) { return a; }
@@ -55,9 +53,7 @@ struct ArithF32 {
   using In = float;
   static constexpr bool kBranchTail = false;
   __device__ static V zero() { return 0.f; }
-  __device__ static V mad(V a, V x, V acc) { return fmaf(a, x, acc); }
   __device__ static V nmad(V a, V x, V acc) { return fmaf(-a, x, acc); }
-  __device__ static V sub(V a, V b) { return a - b; }
   __device__ static V add(V a, V b) { return a + b; }
   __device__ static double to_d(V a) { return double(a); }
   __device__ static V from_d(double a) { return float(a); }
@@ -90,7 +86,6 @@ struct ArithDF {
     quick_two_sum(s1, s2, s1, s2);
     return make_float2(s1, s2);
   }
-  __device__ static V sub(V a, V b) { return add(a, make_float2(-b.x, -b.y)); }
   // a * x: exact high product from FMA, cross terms into the low part
   __device__ static V mul(V a, V x) {
     const float p = __fmul_rn(a.x, x.x);
@@ -101,7 +96,6 @@ struct ArithDF {
     quick_two_sum(p, e, s, t);
     return make_float2(s, t);
   }
-  __device__ static V mad(V a, V x, V acc) { return add(acc, mul(a, x)); }
   __device__ static V nmad(V a, V x, V acc) { return add(acc, mul(make_float2(-a.x, -a.y), x)); }
   __device__ static double to_d(V a) { return double(a.x) + double(a.y); }
   __device__ static V from_d(double a) {
