@@ -37,6 +37,15 @@ def test_every_declared_symbol_is_exported_and_bound(lib):
     assert declared == set(abi.exported_symbols())
 
 
+def test_opts_struct_matches_header(lib):
+    # NNOpts mirrors nn_opts field for field (the C struct gained x0_scalar at the end)
+    text = open(os.path.join(ROOT, "include", "nn.h")).read()
+    body = re.search(r"typedef struct nn_opts \{(.*?)\} nn_opts;", text, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(\w+)\s*;", body)
+    assert fields == [f for f, _ in abi.NNOpts._fields_]
+
+
 def test_workspace_sizes(lib):
     assert abi.nn_workspace_bytes(0, "f64") == 0
     assert abi.nn_workspace_bytes(16, 99) == 0
@@ -59,6 +68,10 @@ def test_argument_errors_are_status_codes(lib):
                          None) == abi.NN_ERR_ARG
     opts = abi.make_opts(depth=2)
     assert lib.nn_invert(None, 16, 16, None, 16, ctypes.byref(opts), None, 16, None, None, 0, None) == abi.NN_ERR_ARG
+    for bad in (-1.0, float("nan"), float("inf")):  # the X_0 = x0_scalar I hint must be >= 0 and finite
+        opts = abi.make_opts(depth=2, dtype="mixed_bf16", x0_scalar=bad)
+        assert lib.nn_invert(None, 16, 16, None, 16, ctypes.byref(opts), None, 16, ctypes.byref(res), None, 0,
+                             None) == abi.NN_ERR_ARG
     out = ctypes.c_double()
     assert lib.nn_residual(None, 4, None, 4, 4, abi.NN_F64, ctypes.byref(out), None, 0, None) == abi.NN_ERR_ARG
     assert lib.nn_init_precond(None, 4, 4, 0, 0.0, None, 4, None, 0, None) == abi.NN_ERR_ARG
