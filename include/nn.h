@@ -152,8 +152,11 @@ int nn_init_precond(const double* A, int64_t n, int64_t lda, int kind, double sc
 
 /* Dense NN inversion (Algorithm 1, right-multiplied form). A, X0, X are device FP64
  * row-major with leading dimensions lda, ldx0, ldx (>= n). X receives the last iterate
- * X_nests (also on failure statuses, so the caller can inspect it). res (host) receives
- * the run record. The call synchronises `stream` once per nest to read s_k. */
+ * X_nests (also on failure statuses, so the caller can inspect it); X must not overlap A or
+ * X0, and for the mixed dtypes it may be written before the last nest is confirmed (the
+ * iterate predicted to be returned is widened to FP64 by the confirming residual's epilogue).
+ * res (host) receives the run record. The call synchronises `stream` once per nest to read
+ * s_k. */
 int nn_invert(const double* A, int64_t n, int64_t lda, const double* X0, int64_t ldx0,
               const nn_opts* opts, double* X, int64_t ldx, nn_result* res,
               void* workspace, size_t ws_bytes, void* stream);

@@ -107,18 +107,6 @@ __device__ __forceinline__ void split_load4(const double* src, int64_t lds, int 
     for (int e = 0; e < 4; ++e) v[e] = (i < n && jj + e < n) ? src[int64_t(i) * lds + jj + e] : 0.0;
   }
 }
-__device__ __forceinline__ void split_load4(const float* src, int64_t lds, int n, int i, int jj, double (&v)[4]) {
-  if (i < n && jj + 3 < n && ((lds & 3) | (reinterpret_cast<uintptr_t>(src) & 15)) == 0) {
-    const float4 a = *reinterpret_cast<const float4*>(src + int64_t(i) * lds + jj);
-    v[0] = a.x;
-    v[1] = a.y;
-    v[2] = a.z;
-    v[3] = a.w;
-  } else {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = (i < n && jj + e < n) ? double(src[int64_t(i) * lds + jj + e]) : 0.0;
-  }
-}
 
 // Splits the n x n matrix scale * src + diag * I (FP64 arithmetic; AFFINE = false: src as is)
 // into its FP32 rounding and BF16 pieces.
@@ -132,10 +120,19 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int jj = j0 + 4 * tx;
   float ss = 0.f;
-  for (int r = ty; r < SPLIT_R; r += ROWS) {
+  // all of the thread's source rows are loaded before any is processed: four 32-byte loads
+  // in flight per thread instead of one
+  constexpr int RPT = SPLIT_R / ROWS;
+  double vin[RPT][4];
+#pragma unroll
+  for (int rr = 0; rr < RPT; ++rr) split_load4(src, lds, n, i0 + ty + rr * ROWS, jj, vin[rr]);
+#pragma unroll
+  for (int rr = 0; rr < RPT; ++rr) {
+    const int r = ty + rr * ROWS;
     const int i = i0 + r;
     double v[4];
-    split_load4(src, lds, n, i, jj, v);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = vin[rr][e];
     if (AFFINE) {
 #pragma unroll
       for (int e = 0; e < 4; ++e)
@@ -204,6 +201,24 @@ __global__ void convert_kernel(const S* __restrict__ src, int64_t lds, int n, D*
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y;
   if (i < n && j < n) dst[int64_t(i) * ldd + j] = static_cast<D>(src[int64_t(i) * lds + j]);
+}
+
+// FP32 -> FP64 with 16-byte loads and stores: four consecutive elements of row blockIdx.y per
+// thread (src rows 16-byte aligned, dst rows 16-byte aligned).
+__global__ void f32_to_f64_vec_kernel(const float* __restrict__ src, int64_t lds, int n, double* __restrict__ dst,
+                                      int64_t ldd) {
+  const int j = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int i = blockIdx.y;
+  if (j >= n) return;
+  const float* s = src + int64_t(i) * lds + j;
+  double* d = dst + int64_t(i) * ldd + j;
+  if (j + 4 <= n) {
+    const float4 f = *reinterpret_cast<const float4*>(s);
+    reinterpret_cast<double2*>(d)[0] = make_double2(double(f.x), double(f.y));
+    reinterpret_cast<double2*>(d)[1] = make_double2(double(f.z), double(f.w));
+  } else {
+    for (int e = 0; j + e < n; ++e) d[e] = double(s[e]);
+  }
 }
 
 __global__ void reduce_rms_kernel(const double* __restrict__ partial, int count, double scale, double* out) {
@@ -370,8 +385,7 @@ int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np,
   return NN_OK;
 }
 
-template <typename S>
-static int split_affine(cudaStream_t st, const S* src, int64_t lds, int n, int np, float* f32,
+static int split_affine(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
                         __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
                         double* sumsq_partial, double scale, double diag) {
   if (np % SPLIT_C != 0 || n > np || n_row < 0 || n_row > 3 || n_col < 0 || n_col > 3) return NN_ERR_ARG;
@@ -379,18 +393,12 @@ static int split_affine(cudaStream_t st, const S* src, int64_t lds, int n, int n
   for (int q = 0; q < n_row; ++q) r.p[q] = row_pieces[q];
   for (int q = 0; q < n_col; ++q) c.p[q] = col_pieces[q];
   dim3 grid(np / SPLIT_C, np / SPLIT_R), block(32, ROWS);
-  split_kernel<S, true><<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial, scale, diag);
+  split_kernel<double, true><<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial, scale, diag);
   NN_CUDA_TRY(cudaGetLastError());
   return NN_OK;
 }
 
 int split_matrix_affine(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
-                        __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
-                        double* sumsq_partial, double scale, double diag) {
-  return split_affine(st, src, lds, n, np, f32, row_pieces, n_row, col_pieces, n_col, sumsq_partial, scale, diag);
-}
-
-int split_matrix_affine(cudaStream_t st, const float* src, int64_t lds, int n, int np, float* f32,
                         __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
                         double* sumsq_partial, double scale, double diag) {
   return split_affine(st, src, lds, n, np, f32, row_pieces, n_row, col_pieces, n_col, sumsq_partial, scale, diag);
@@ -408,6 +416,13 @@ static int convert(cudaStream_t st, const S* src, int64_t lds, int n, D* dst, in
 }
 
 int f32_to_f64(cudaStream_t st, const float* src, int64_t lds, int n, double* dst, int64_t ldd) {
+  if (n > 0 && lds % 4 == 0 && ldd % 2 == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0 &&
+      (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+    dim3 grid((n + 1023) / 1024, n), block(256);
+    f32_to_f64_vec_kernel<<<grid, block, 0, st>>>(src, lds, n, dst, ldd);
+    NN_CUDA_TRY(cudaGetLastError());
+    return NN_OK;
+  }
   return convert(st, src, lds, n, dst, ldd);
 }
 int copy_f64(cudaStream_t st, const double* src, int64_t lds, int n, double* dst, int64_t ldd) {

@@ -87,6 +87,16 @@ struct Params {
   const double* emu_add;
   int64_t emu_ld_add;
   int emu_n;
+  // Affine epilogue (affine != 0): C' = aff_scale * C + aff_diag * I_{n_id}, after the mode.
+  int affine;
+  float aff_scale, aff_diag;
+  // Side copy: cvt_dst (FP64, ld cvt_ld) = cvt_src (FP32, ld Np) over this launch's tiles,
+  // rows and columns < cvt_n; cvt_vec: cvt_dst rows are 16-byte aligned.
+  const float* cvt_src;
+  double* cvt_dst;
+  int64_t cvt_ld;
+  int cvt_n;
+  int cvt_vec;
 };
 
 // Shared-memory matrix descriptor for a K-major tile written by TMA with SWIZZLE_128B:
@@ -192,8 +202,29 @@ __device__ __forceinline__ void epilogue_chunk(const Params& p, const uint32_t (
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(raw[j]);
   }
+  if (p.affine) {
 #pragma unroll
-  for (int j = 0; j < 32; ++j) ss = fma(double(v[j]), double(v[j]), ss);
+    for (int j = 0; j < 32; ++j) v[j] = fmaf(p.aff_scale, v[j], (gr == gc0 + j && gr < p.n_id) ? p.aff_diag : 0.0f);
+  }
+  {
+    // The chunk's 32 squares in FP32 (four interleaved sums, fixed order; relative error
+    // ~2^-21), accumulated in FP64 across chunks: FP64 work once per chunk, not per element
+    // (GB300's FP64 pipe is narrow). A chunk sum outside [2^-100, 2^100] (zeros, values whose
+    // squares underflow or overflow FP32, NaN) is redone in FP64, so the result stays
+    // scale-invariant.
+    float c4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < 32; ++j) c4[j & 3] = fmaf(v[j], v[j], c4[j & 3]);
+    const float cs = (c4[0] + c4[1]) + (c4[2] + c4[3]);
+    if (cs >= 0x1p-100f && cs <= 0x1p100f) {
+      ss += double(cs);
+    } else {
+      double d = 0.0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) d = fma(double(v[j]), double(v[j]), d);
+      ss += d;
+    }
+  }
   if (p.out_f32 != nullptr) {
     float4* dst = reinterpret_cast<float4*>(p.out_f32 + off);
 #pragma unroll
@@ -212,6 +243,21 @@ __device__ __forceinline__ void epilogue_chunk(const Params& p, const uint32_t (
         rem[j] -= __bfloat162float(b);
         dst[int64_t(gc0 + j) * ld] = b;  // lanes write consecutive rows: 64-byte runs
       }
+    }
+  }
+  if (p.cvt_dst != nullptr && gr < p.cvt_n && gc0 < p.cvt_n) {
+    const float4* src = reinterpret_cast<const float4*>(p.cvt_src + off);
+    double* dst = p.cvt_dst + int64_t(gr) * p.cvt_ld + gc0;
+    if (p.cvt_vec && gc0 + 32 <= p.cvt_n) {
+#pragma unroll
+      for (int j4 = 0; j4 < 8; ++j4) {
+        const float4 f = src[j4];
+        reinterpret_cast<double2*>(dst)[2 * j4] = make_double2(double(f.x), double(f.y));
+        reinterpret_cast<double2*>(dst)[2 * j4 + 1] = make_double2(double(f.z), double(f.w));
+      }
+    } else {
+      const int jn = min(32, p.cvt_n - gc0);
+      for (int j = 0; j < jn; ++j) dst[j] = double(p.cvt_src[off + j]);
     }
   }
 }
@@ -707,6 +753,9 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
       a.n_col < 0 || a.n_col > 3 || a.err == nullptr)
     return NN_ERR_ARG;
   if (!a.emu && a.mode == EPI_ADD && a.add == nullptr) return NN_ERR_ARG;
+  if (a.cvt_dst != nullptr && (a.emu || a.cvt_src == nullptr || a.cvt_n < 1 || a.cvt_n > a.np || a.cvt_ld < a.cvt_n))
+    return NN_ERR_ARG;
+  if (a.emu && a.affine) return NN_ERR_ARG;
   if (a.emu && (a.emu_acc == nullptr || a.emu_gexp == nullptr || (a.emu_last && a.emu_out == nullptr) ||
                 (a.emu_last && a.mode == EPI_ADD && a.emu_add == nullptr) || a.n_row != 0 || a.n_col != 0 ||
                 a.out_f32 != nullptr || a.emu_n < 1 || a.emu_n > a.np))
@@ -750,6 +799,14 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
   p.emu_add = a.emu_add;
   p.emu_ld_add = a.emu_ld_add;
   p.emu_n = a.emu_n;
+  p.affine = a.affine ? 1 : 0;
+  p.aff_scale = a.aff_scale;
+  p.aff_diag = a.aff_diag;
+  p.cvt_src = a.cvt_src;
+  p.cvt_dst = a.cvt_dst;
+  p.cvt_ld = a.cvt_ld;
+  p.cvt_n = a.cvt_n;
+  p.cvt_vec = (a.cvt_ld % 2 == 0 && (reinterpret_cast<uintptr_t>(a.cvt_dst) & 15) == 0) ? 1 : 0;
   // Variant choice: the 2-SM MMA with a split last wave by default where the size allows it, else
   // single-CTA tiles.
   const bool even = a.np % (2 * tc::BM) == 0;

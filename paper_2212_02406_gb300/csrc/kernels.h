@@ -61,6 +61,17 @@ struct TcGemmArgs {
   const double* emu_add = nullptr;
   int64_t emu_ld_add = 0;
   int emu_n = 0;
+  // Affine epilogue: C' = aff_scale * C + aff_diag * I_{n_id} (FP32), applied after `mode`, before
+  // the squares and the outputs.
+  bool affine = false;
+  float aff_scale = 1.0f, aff_diag = 0.0f;
+  // Side copy riding on the epilogue: cvt_dst (FP64, ld cvt_ld) receives cvt_src (FP32, ld Np)
+  // widened, for rows and columns < cvt_n (a final FP32 -> FP64 conversion overlapped with a
+  // tensor-bound product).
+  const float* cvt_src = nullptr;
+  double* cvt_dst = nullptr;
+  int64_t cvt_ld = 0;
+  int cvt_n = 0;
 };
 int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used);
 int gemm_tc_max_grid();
@@ -89,12 +100,9 @@ bool tc_supported();
 int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
                  __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
                  double* sumsq_partial);
-// The same for scale * src + diag * I (FP64 arithmetic on the FP64 or FP32 source): element-wise
-// products with a scalar X_0 (R_0 = I - a A, X_1 = a (I + T)).
+// The same for scale * src + diag * I (FP64 arithmetic): element-wise products with a scalar
+// X_0 (R_0 = I - a A; at depth 1, X_1 = 2 a I - a^2 A).
 int split_matrix_affine(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
-                        __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
-                        double* sumsq_partial, double scale, double diag);
-int split_matrix_affine(cudaStream_t st, const float* src, int64_t lds, int n, int np, float* f32,
                         __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
                         double* sumsq_partial, double scale, double diag);
 int split_blocks(int np);

@@ -401,10 +401,20 @@ struct HostOut {
   bool valid = false;         // set at the end: the copy holds the returned iterate
 };
 
+// The caller's device X (FP64), written by the epilogue of a residual product whose iterate is
+// predicted to be the last one; buf / nests record which iterate the copy holds (-1: none).
+struct DevOut {
+  double* X = nullptr;
+  int64_t ldx = 0;
+  int buf = -1;
+  int nests = -1;
+};
+
 namespace {
 
 int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedWs& w, const nn_opts& o,
-              const Common& cm, double a_frob, const X0Source& x0src, nn_result* res, int* final_idx, HostOut* ho) {
+              const Common& cm, double a_frob, const X0Source& x0src, nn_result* res, int* final_idx, HostOut* ho,
+              DevOut* dout) {
   const int np = w.np;
   // X_0 = alpha I (the caller's assertion): the first nest's residual R_0 = I - alpha A and update
   // X_1 = alpha (I + T) are element-wise, split straight into the chain's layouts from FP64 A
@@ -416,6 +426,8 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
   const double n15 = double(n) * sqrt(double(n));
   int level = (o.bulk_pieces >= 1 && o.bulk_pieces <= 4) ? o.bulk_pieces : 1;
   int cur = 0;
+  int k = 0;
+  bool copy_next = false;  // the next residual's iterate is predicted to be returned
   double x_frob = 0;  // ||X_k||_F, read back with s_k
   LaunchTimer timer;
   timer.on = (o.flags & NN_FLAG_TIME_KERNELS) != 0;
@@ -435,6 +447,16 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       g.col_pieces[i] = w.r_col[i];
     }
     g.partial = cm.partial;
+    if (dout != nullptr && copy_next) {
+      // the predicted final residual (a multi-pass, tensor-bound product) also widens X_k into
+      // the caller's FP64 X from its epilogue
+      g.cvt_src = w.x32[cur];
+      g.cvt_dst = dout->X;
+      g.cvt_ld = dout->ldx;
+      g.cvt_n = n;
+      dout->buf = cur;
+      dout->nests = k;
+    }
     int grid = 0;
     NN_TRY(tc_product(st, g, level_res_pieces(L), w.a_row, w.x_col[cur], cm, res, &grid, &timer));
     NN_TRY(reduce_rms(st, cm.partial, grid, 1.0 / double(n), cm.scal));
@@ -466,7 +488,6 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
   int rollbacks = 0;
   bool restarted = false;
   double x_frob_prev = 0;  // ||X_{k-1}||_F, kept for a rollback
-  int k = 0;
   // the residual of X_k at level L (element-wise for k = 0 with a scalar X_0)
   auto measure = [&](int L, double* s_out) -> int {
     return (scalar_x0 && k == 0) ? residual0(L, s_out) : residual(L, s_out);
@@ -576,6 +597,16 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     // those levels serve; its output T keeps the update's pieces.
     const bool update0 = scalar_x0 && k == 0;
     const int hh = (level == 2 || level == 3) ? hp - 1 : hp;
+    // Before a write to x32[cur ^ 1]: a host side copy must finish reading it, and a copy of
+    // it is stale from then on.
+    auto before_x_write = [&]() -> int {
+      if (ho != nullptr && ho->pending) {
+        NN_CUDA_TRY(cudaStreamWaitEvent(st, ho->done, 0));
+        if (ho->spec_buf == (cur ^ 1)) ho->spec_nests = -1;
+      }
+      if (dout != nullptr && dout->buf == (cur ^ 1)) dout->nests = -1;
+      return NN_OK;
+    };
     __nv_bfloat16* const* t_cur = w.r_col;
     for (int j = 1; j < nest_depth(o, k); ++j) {
       TcGemmArgs g;
@@ -584,30 +615,43 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       g.mode = EPI_ADD;
       g.add = w.r32;
       g.n_col = hp;
-      if (update0 && j == nest_depth(o, k) - 1) g.out_f32 = w.r32;
       for (int i = 0; i < 3; ++i) g.col_pieces[i] = w.t_col[j & 1][i];
       int grid = 0;
+      if (update0 && j == nest_depth(o, k) - 1) {
+        // the first nest's last Horner product writes X_1 = alpha (I + T) straight from its
+        // epilogue (FP32 master, row and column pieces, ||X_1||_F): no T, no separate pass
+        g.affine = true;
+        g.aff_scale = float(alpha);
+        g.aff_diag = float(alpha);
+        g.out_f32 = w.x32[cur ^ 1];
+        g.n_row = 3;
+        g.n_col = 3;
+        for (int i = 0; i < 3; ++i) {
+          g.row_pieces[i] = w.x_row[cur ^ 1][i];
+          g.col_pieces[i] = w.x_col[cur ^ 1][i];
+        }
+        g.partial = cm.partial;
+        NN_TRY(before_x_write());
+        NN_TRY(tc_product(st, g, hh, w.r_row, t_cur, cm, res, &grid, &timer));
+        NN_TRY(reduce_rms(st, cm.partial, grid, 1.0, cm.scal + 1));
+        res->launches += 1;
+        break;
+      }
       NN_TRY(tc_product(st, g, hh, w.r_row, t_cur, cm, res, &grid, &timer));
       t_cur = w.t_col[j & 1];
     }
     // Update: X_{k+1} = X_k + X_k T, with ||X_{k+1}||_F from the epilogue partials.
-    if (ho != nullptr && ho->pending) {
-      // the side copy must finish reading before x32[cur ^ 1] is rewritten; it is then stale
-      NN_CUDA_TRY(cudaStreamWaitEvent(st, ho->done, 0));
-      if (ho->spec_buf == (cur ^ 1)) ho->spec_nests = -1;
-    }
     if (update0) {
-      // X_1 = alpha I + alpha T: T = R_0 = I - alpha A at depth 1 (X_1 = 2 alpha I - alpha^2 A
-      // from FP64 A), else T in FP32 from the last Horner product
-      if (nest_depth(o, k) == 1)
+      // depth 1: T = R_0 = I - alpha A, X_1 = 2 alpha I - alpha^2 A element-wise from FP64 A
+      if (nest_depth(o, k) == 1) {
+        NN_TRY(before_x_write());
         NN_TRY(split_matrix_affine(st, A, lda, n, np, w.x32[cur ^ 1], w.x_row[cur ^ 1], 3, w.x_col[cur ^ 1], 3,
                                    w.split_partial, -alpha * alpha, 2.0 * alpha));
-      else
-        NN_TRY(split_matrix_affine(st, w.r32, np, n, np, w.x32[cur ^ 1], w.x_row[cur ^ 1], 3, w.x_col[cur ^ 1], 3,
-                                   w.split_partial, alpha, alpha));
-      NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0, cm.scal + 1));
-      res->launches += 2;
+        NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0, cm.scal + 1));
+        res->launches += 2;
+      }
     } else {
+      NN_TRY(before_x_write());
       TcGemmArgs g;
       g.np = np;
       g.n_id = n;
@@ -640,6 +684,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     }
     cur ^= 1;
     level = next_level;
+    copy_next = likely_final;
   }
   *final_idx = cur;
   if (ho != nullptr && ho->pending) ho->valid = ho->spec_buf == cur && ho->spec_nests == res->nests;
@@ -726,7 +771,21 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     NN_CUDA_TRY(cudaMemcpyAsync(&a_frob, cm.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
     NN_CUDA_TRY(cudaStreamSynchronize(st));
     res->launches += 4;
-    NN_TRY(run_mixed(st, ni, A, lda, w, o, cm, a_frob, x0src, res, &fin, ho));
+    // X written before the run ends must not be read by it (X overlapping A or X_0: no early copy)
+    auto span = [&](const double* p, int64_t ld) {
+      return std::make_pair(reinterpret_cast<uintptr_t>(p),
+                            reinterpret_cast<uintptr_t>(p + (n - 1) * ld + n));
+    };
+    auto overlaps = [&](std::pair<uintptr_t, uintptr_t> a, std::pair<uintptr_t, uintptr_t> b) {
+      return a.first < b.second && b.first < a.second;
+    };
+    const bool early_ok = !overlaps(span(X, ldx), span(A, lda)) &&
+                          (X0 == nullptr || !overlaps(span(X, ldx), span(X0, ldx0)));
+    DevOut dout;
+    dout.X = X;
+    dout.ldx = ldx;
+    NN_TRY(run_mixed(st, ni, A, lda, w, o, cm, a_frob, x0src, res, &fin, ho,
+                     (ho == nullptr && early_ok) ? &dout : nullptr));
     if (ho != nullptr && ho->pending) NN_CUDA_TRY(cudaStreamWaitEvent(st, ho->done, 0));
     if (o.dtype == NN_MIXED_EMU && res->status == NN_ERR_NOT_CONVERGED && res->nests < o.max_nests) {
       // Continue from the mixed chain's last iterate with emulated FP64 nests (NN converges from
@@ -758,7 +817,7 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
       res->tc_ms += r2.tc_ms;
       res->tc_flops += r2.tc_flops;
       NN_TRY(copy_f64(st, w64.X[fin2], n, ni, X, ldx));
-    } else if (ho == nullptr || !ho->valid) {
+    } else if (ho != nullptr ? !ho->valid : !(dout.buf == fin && dout.nests == res->nests)) {
       NN_TRY(f32_to_f64(st, w.x32[fin], w.np, ni, X, ldx));
     }
     res->launches += 3;

@@ -266,14 +266,41 @@ def test_host_pc_variant_and_early_copy_equal_device(nn, tol, kappa):
         assert np.array_equal(x1, xh)
 
 
+@pytest.mark.parametrize("n,pad", [(300, 0), (300, 1), (517, 3), (1024, 0)])
+@pytest.mark.parametrize("tol", [1e-5, 1e-7])
+def test_device_early_copy_strided_output(nn, n, pad, tol):
+    # For the mixed chain the iterate predicted to be returned is widened into the caller's X by
+    # the confirming residual's epilogue (16-byte stores for an even leading dimension, element
+    # stores otherwise, ragged last chunk). X must equal the host call's result bit for bit,
+    # whether or not the prediction held, and the columns past n stay untouched.
+    import torch
+
+    a, q, lam = synth.spd_spectrum(n, 1e2, seed=n + pad)
+    x0 = dense.precond_scalar(n, 2.0 / (lam[0] + lam[-1]))
+    xf_dev = torch.full((n, n + pad), 7.0, dtype=torch.float64, device="cuda")
+    X = xf_dev[:, :n]
+    ws = nn.workspace(n, "mixed_bf16")
+    st1, res1 = nn.nn_invert(_dev(a), _dev(x0), nn.make_opts(2, tol, 40, "mixed_bf16"), X, ws)
+    torch.cuda.synchronize()
+    xh = np.full_like(a, np.nan)
+    st2, res2 = nn.nn_invert_host(np.ascontiguousarray(a), np.ascontiguousarray(x0),
+                                  nn.make_opts(2, tol, 40, "mixed_bf16"), xh, nn.workspace(n, "mixed_bf16", host=True))
+    assert st1 == st2 == nn.NN_OK
+    assert res1["history"] == res2["history"]
+    xf = xf_dev.cpu().numpy()
+    assert np.array_equal(xf[:, :n], xh)
+    assert np.all(xf[:, n:] == 7.0)
+
+
 @pytest.mark.parametrize("n", [300, 1024])
 @pytest.mark.parametrize("sched", [[1], [2], [3], [1, 2]])
 @pytest.mark.parametrize("kappa", [1e2, 1e4])
 def test_scalar_x0_hint_matches_explicit_x0(nn, n, sched, kappa):
-    # With x0_scalar the mixed chain forms R_0 = I - alpha A and X_1 = alpha (I + T) element-wise
-    # instead of by GEMMs. The iteration is the same; only rounding in the first nest differs
-    # (the element-wise forms are the more accurate), so both runs must end in the same status,
-    # within one nest, and each must meet the forward-error bound of the module docstring.
+    # With x0_scalar the mixed chain forms R_0 = I - alpha A element-wise (FP64) and X_1 =
+    # alpha (I + T) in the epilogue of the first nest's last Horner product (depth 1: element-wise)
+    # instead of by GEMMs. The iteration is the same; only rounding in the first nest differs, so
+    # both runs must end in the same status, within one nest, and each must meet the
+    # forward-error bound of the module docstring.
     a, q, lam = synth.spd_spectrum(n, kappa, seed=int(n + kappa) % 997)
     alpha = 2.0 / (lam[0] + lam[-1])
     x0 = dense.precond_scalar(n, alpha)
