@@ -17,53 +17,24 @@ constexpr int ROWS = 8;  // 32 x 8 threads per 32 x 32 tile
 // v = hi + lo with hi = fp32(v), lo = fp32(v - hi); p0 = bf16(hi), p1 = bf16((hi - p0) + lo),
 // p2 = bf16(((hi - p0) + lo) - p1). hi - p0 and t - p1 are exact in FP32; the only rounding
 // beyond the pieces themselves is (hi - p0) + lo, at most 2^-24 |hi - p0| <= 2^-33 |v|.
-// hi = fp32(v) and lo = fp32(v - hi), both rounded to nearest even, from the FP64 bit pattern
-// with integer operations only (GB300's FP64 pipe would otherwise bound this kernel). Returns
-// false, leaving the work to FP64 arithmetic, for zeros, |v| outside [2^-90, 2^101) and a
-// subnormal lo; the results are identical to the FP64 conversions.
+// hi and lo, both rounded to nearest even, come from the FP64 bit pattern without FP64
+// arithmetic: hi by rounding the significand's top 24 bits (a carry into the exponent field is
+// the correct rounding), lo as the 29-bit remainder (an integer, |r| <= 2^28) converted with
+// one int -> float rounding and scaled by the exact power of two 2^(e-52). Returns false,
+// leaving the work to FP64 arithmetic, for |v| outside [2^-60, 2^101) (zeros, subnormals, inf
+// and NaN included); the results are identical to the FP64 conversions.
 __device__ __forceinline__ bool split_hi_lo_int(double v, float& hi, float& lo) {
-  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
-  const int e = int((bits >> 52) & 0x7FFull) - 1023;
-  if (e < -90 || e > 100) return false;
-  const unsigned s = unsigned(bits >> 63);
-  const long long M = static_cast<long long>((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52));
-  // hi: M rounded to 24 significant bits
-  long long q = M >> 29;
-  const long long rem = M & ((1ll << 29) - 1);
-  if (rem > (1ll << 28) || (rem == (1ll << 28) && (q & 1))) ++q;
-  const long long r = M - (q << 29);  // v - hi in units of 2^(e-52), |r| <= 2^28
-  int eh = e;
-  long long qh = q;
-  if (q == (1ll << 24)) {
-    qh = 1ll << 23;
-    eh = e + 1;
-  }
-  hi = __uint_as_float((s << 31) | (unsigned(eh + 127) << 23) | unsigned(qh & 0x7FFFFF));
-  if (r == 0) {
-    lo = 0.0f;
-    return true;
-  }
-  // lo: |r| rounded to 24 significant bits, sign of v flipped when hi rounded up
-  const unsigned sl = s ^ (r < 0 ? 1u : 0u);
-  const unsigned long long x = static_cast<unsigned long long>(r < 0 ? -r : r);
-  const int p = 63 - __clzll(static_cast<long long>(x));
-  long long m24;
-  int pe = p;
-  if (p > 23) {
-    const int sh = p - 23;
-    m24 = static_cast<long long>(x >> sh);
-    const unsigned long long rb = x & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-    if (rb > half || (rb == half && (m24 & 1))) ++m24;
-    if (m24 == (1ll << 24)) {
-      m24 = 1ll << 23;
-      ++pe;
-    }
-  } else {
-    m24 = static_cast<long long>(x << (23 - p));
-  }
-  const int ef = pe + e - 52 + 127;
-  if (ef < 1) return false;
-  lo = __uint_as_float((sl << 31) | (unsigned(ef) << 23) | unsigned(m24 & 0x7FFFFF));
+  const unsigned hw = unsigned(__double2hiint(v)), lw = unsigned(__double2loint(v));
+  const int e = int((hw >> 20) & 0x7FFu) - 1023;
+  if (e < -60 || e > 100) return false;
+  const unsigned sign = hw & 0x80000000u;
+  const unsigned mtop = ((hw & 0xFFFFFu) << 3) | (lw >> 29);  // the 23 fraction bits FP32 keeps
+  const unsigned rest = lw & 0x1FFFFFFFu;                     // the 29 bits below them
+  const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (mtop & 1u))) ? 1u : 0u;
+  hi = __uint_as_float(sign | ((unsigned(e + 127) << 23) + mtop + up));
+  const int r = int(rest) - int(up << 29);  // (v - hi) / 2^(e-52), sign of v factored out
+  const float mag = __int2float_rn(r) * __uint_as_float(unsigned(e - 52 + 127) << 23);
+  lo = sign ? -mag : mag;
   return true;
 }
 
