@@ -55,6 +55,21 @@ __device__ __forceinline__ float pieces3(double v, __nv_bfloat16 (&p)[3]) {
   return hi;
 }
 
+// Four consecutive FP32 source values of row i from column jj (zeros past n), widened to FP64
+// (exact).
+__device__ __forceinline__ void split_load4(const float* src, int64_t lds, int n, int i, int jj, double (&v)[4]) {
+  if (i < n && jj + 3 < n && ((lds & 3) | (reinterpret_cast<uintptr_t>(src) & 15)) == 0) {
+    const float4 a = *reinterpret_cast<const float4*>(src + int64_t(i) * lds + jj);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = (i < n && jj + e < n) ? double(src[int64_t(i) * lds + jj + e]) : 0.0;
+  }
+}
+
 struct PiecePtrs {
   __nv_bfloat16* p[3];
 };
@@ -352,6 +367,18 @@ int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np,
   dim3 grid(np / SPLIT_C, np / SPLIT_R), block(32, ROWS);
   split_kernel<double, false><<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial, 1.0,
                                                       0.0);
+  NN_CUDA_TRY(cudaGetLastError());
+  return NN_OK;
+}
+
+int split_matrix_f32(cudaStream_t st, const float* src, int64_t lds, int n, int np, __nv_bfloat16* const* row_pieces,
+                     int n_row, __nv_bfloat16* const* col_pieces, int n_col) {
+  if (np % SPLIT_C != 0 || n > np || n_row < 0 || n_row > 3 || n_col < 0 || n_col > 3) return NN_ERR_ARG;
+  PiecePtrs r{}, c{};
+  for (int q = 0; q < n_row; ++q) r.p[q] = row_pieces[q];
+  for (int q = 0; q < n_col; ++q) c.p[q] = col_pieces[q];
+  dim3 grid(np / SPLIT_C, np / SPLIT_R), block(32, ROWS);
+  split_kernel<float, false><<<grid, block, 0, st>>>(src, lds, n, np, nullptr, r, n_row, c, n_col, nullptr, 1.0, 0.0);
   NN_CUDA_TRY(cudaGetLastError());
   return NN_OK;
 }

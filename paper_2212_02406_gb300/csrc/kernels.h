@@ -105,6 +105,9 @@ int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np,
 int split_matrix_affine(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
                         __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
                         double* sumsq_partial, double scale, double diag);
+// BF16 pieces of an FP32 matrix (the same pieces the GEMM epilogue writes for it).
+int split_matrix_f32(cudaStream_t st, const float* src, int64_t lds, int n, int np, __nv_bfloat16* const* row_pieces,
+                     int n_row, __nv_bfloat16* const* col_pieces, int n_col);
 int split_blocks(int np);
 // dst (FP64, ldd) = src (FP32, lds), n x n.
 int f32_to_f64(cudaStream_t st, const float* src, int64_t lds, int n, double* dst, int64_t ldd);

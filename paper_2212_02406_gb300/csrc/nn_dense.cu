@@ -428,6 +428,18 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
   int cur = 0;
   int k = 0;
   bool copy_next = false;  // the next residual's iterate is predicted to be returned
+  // BF16 pieces of x32[b] present in x_row[b] / x_col[b]: an update writes only what the next
+  // nest's predicted level reads; a later level rise or a rollback regenerates them from the
+  // FP32 master (the same pieces).
+  int xr[2] = {0, 0}, xc[2] = {0, 0};
+  if (!scalar_x0) xr[0] = xc[0] = 3;
+  auto ensure_pieces = [&](int b, int need_r, int need_c) -> int {
+    if (xr[b] >= need_r && xc[b] >= need_c) return NN_OK;
+    NN_TRY(split_matrix_f32(st, w.x32[b], np, n, np, w.x_row[b], 3, w.x_col[b], 3));
+    xr[b] = xc[b] = 3;
+    res->launches += 1;
+    return NN_OK;
+  };
   double x_frob = 0;  // ||X_k||_F, read back with s_k
   LaunchTimer timer;
   timer.on = (o.flags & NN_FLAG_TIME_KERNELS) != 0;
@@ -457,6 +469,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       dout->buf = cur;
       dout->nests = k;
     }
+    NN_TRY(ensure_pieces(cur, 0, level_res_pieces(L)));
     int grid = 0;
     NN_TRY(tc_product(st, g, level_res_pieces(L), w.a_row, w.x_col[cur], cm, res, &grid, &timer));
     NN_TRY(reduce_rms(st, cm.partial, grid, 1.0 / double(n), cm.scal));
@@ -510,6 +523,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       level = 2;
       if (!scalar_x0) {
         NN_TRY(load_x0(st, n, w, cm, x0src));
+        xr[0] = xc[0] = 3;
         res->launches += 2;
       }
       NN_TRY(measure(level, &s));
@@ -597,6 +611,8 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     // those levels serve; its output T keeps the update's pieces.
     const bool update0 = scalar_x0 && k == 0;
     const int hh = (level == 2 || level == 3) ? hp - 1 : hp;
+    // pieces of X_{k+1} that the next nest reads at its predicted level
+    const int wr = level_upd_pieces(next_level), wc = level_res_pieces(next_level);
     // Before a write to x32[cur ^ 1]: a host side copy must finish reading it, and a copy of
     // it is stale from then on.
     auto before_x_write = [&]() -> int {
@@ -624,14 +640,16 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
         g.aff_scale = float(alpha);
         g.aff_diag = float(alpha);
         g.out_f32 = w.x32[cur ^ 1];
-        g.n_row = 3;
-        g.n_col = 3;
+        g.n_row = wr;
+        g.n_col = wc;
         for (int i = 0; i < 3; ++i) {
           g.row_pieces[i] = w.x_row[cur ^ 1][i];
           g.col_pieces[i] = w.x_col[cur ^ 1][i];
         }
         g.partial = cm.partial;
         NN_TRY(before_x_write());
+        xr[cur ^ 1] = wr;
+        xc[cur ^ 1] = wc;
         NN_TRY(tc_product(st, g, hh, w.r_row, t_cur, cm, res, &grid, &timer));
         NN_TRY(reduce_rms(st, cm.partial, grid, 1.0, cm.scal + 1));
         res->launches += 1;
@@ -645,21 +663,25 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       // depth 1: T = R_0 = I - alpha A, X_1 = 2 alpha I - alpha^2 A element-wise from FP64 A
       if (nest_depth(o, k) == 1) {
         NN_TRY(before_x_write());
+        xr[cur ^ 1] = xc[cur ^ 1] = 3;
         NN_TRY(split_matrix_affine(st, A, lda, n, np, w.x32[cur ^ 1], w.x_row[cur ^ 1], 3, w.x_col[cur ^ 1], 3,
                                    w.split_partial, -alpha * alpha, 2.0 * alpha));
         NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0, cm.scal + 1));
         res->launches += 2;
       }
     } else {
+      NN_TRY(ensure_pieces(cur, hp, 0));
       NN_TRY(before_x_write());
+      xr[cur ^ 1] = wr;
+      xc[cur ^ 1] = wc;
       TcGemmArgs g;
       g.np = np;
       g.n_id = n;
       g.mode = EPI_ADD;
       g.add = w.x32[cur];
       g.out_f32 = w.x32[cur ^ 1];
-      g.n_row = 3;
-      g.n_col = 3;
+      g.n_row = wr;
+      g.n_col = wc;
       for (int i = 0; i < 3; ++i) {
         g.row_pieces[i] = w.x_row[cur ^ 1][i];
         g.col_pieces[i] = w.x_col[cur ^ 1][i];
