@@ -77,6 +77,77 @@ def parse_args():
 
 # ---- clocks ------------------------------------------------------------------------------
 
+class NvmlClockSampler:
+    """SM clock, its maximum and the clock-event reasons of the benchmark's GPU, polled through NVML
+    (read-only queries) every few milliseconds from begin() to stop(), so that a timed region of a
+    few hundred milliseconds still gets tens of samples and none from the idle time around it."""
+    NVML_CLOCK_SM = 1
+    REASONS = ((0x8, "hw_slowdown"), (0x40, "hw_thermal_slowdown"), (0x20, "sw_thermal_slowdown"),
+               (0x4, "sw_power_cap"), (0x80, "hw_power_brake_slowdown"))
+
+    def __init__(self, device, period_s=0.005):
+        import ctypes
+        import threading
+
+        import torch
+
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        props = torch.cuda.get_device_properties(device)
+        bus = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0".encode()
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle for the device")
+        mx = ctypes.c_uint()
+        self.max_mhz = float(mx.value) if self.lib.nvmlDeviceGetMaxClockInfo(
+            self.h, self.NVML_CLOCK_SM, ctypes.byref(mx)) == 0 else None
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.period = period_s
+        self.samples = []
+        self.window = threading.Event()
+        self.done = threading.Event()
+        self.thread = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        ct = self.ct
+        mhz, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self.done.is_set():
+            if self.window.is_set():
+                ok = self.lib.nvmlDeviceGetClockInfo(self.h, self.NVML_CLOCK_SM, ct.byref(mhz)) == 0
+                ok = ok and self.reasons_fn(self.h, ct.byref(rs)) == 0
+                if ok:
+                    self.samples.append((float(mhz.value), int(rs.value)))
+            time.sleep(self.period)
+
+    def start(self):
+        self.thread.start()
+
+    def begin(self):
+        self.window.set()
+
+    def stop(self):
+        self.window.clear()
+        self.done.set()
+        self.thread.join(timeout=5)
+        if not self.samples:
+            return None
+        reasons = sorted({name for _, r in self.samples for bit, name in self.REASONS if r & bit})
+        return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(self.samples), "source": "nvml, every 5 ms of the timed region"}
+
+
+def clock_sampler(gpu_index):
+    """NVML polling where the library and the device's PCI location are available, else
+    nvidia-smi."""
+    try:
+        return NvmlClockSampler(gpu_index)
+    except Exception:
+        return ClockSampler(gpu_index)
+
+
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -96,6 +167,9 @@ class ClockSampler:
                  "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def begin(self):
+        pass
 
     def stop(self):
         if self.proc is None:
@@ -220,10 +294,11 @@ def run_dense(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    sampler = ClockSampler(local_rank)
+    sampler = clock_sampler(local_rank)
     barrier()
     sampler.start()
     time.sleep(0.3)
+    sampler.begin()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     results = []
@@ -396,9 +471,10 @@ def run_normal(args, rank, world, local_rank):
         st, res = abi.nn_solve_normal(A, B, opts, X, ws, stream)
         assert st == abi.NN_OK, (st, res)
     torch.cuda.synchronize(dev)
-    sampler = ClockSampler(local_rank)
+    sampler = clock_sampler(local_rank)
     sampler.start()
     time.sleep(0.3)
+    sampler.begin()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     results = []
@@ -544,9 +620,10 @@ def run_sparse(args, rank, world, local_rank):
         st, res = abi.nn_solve_csr(rp, col, val, B, depth, nests, 0.0, X, ws, stream, double_float=dfl)
         assert st == abi.NN_OK, (st, res)
     torch.cuda.synchronize(dev)
-    sampler = ClockSampler(local_rank)
+    sampler = clock_sampler(local_rank)
     sampler.start()
     time.sleep(0.3)
+    sampler.begin()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -630,9 +707,10 @@ def run_batched(args, rank, world, local_rank):
         g.replay()
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize(dev)
-    sampler = ClockSampler(local_rank)
+    sampler = clock_sampler(local_rank)
     sampler.start()
     time.sleep(0.3)
+    sampler.begin()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ev[0].record(stream)
     for i in range(args.steps):

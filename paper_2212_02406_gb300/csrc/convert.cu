@@ -96,16 +96,19 @@ __device__ __forceinline__ void split_load4(const double* src, int64_t lds, int 
 
 // Splits the n x n matrix scale * src + diag * I (FP64 arithmetic; AFFINE = false: src as is)
 // into its FP32 rounding and BF16 pieces.
-template <typename S, bool AFFINE>
+// DUAL (with AFFINE): the same pass also writes the three row-major pieces of src itself to
+// dual_row, with its per-block sums of squares in dual_sumsq (one read of src for both).
+template <typename S, bool AFFINE, bool DUAL = false>
 __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int np, float* __restrict__ f32,
                              PiecePtrs row, int n_row, PiecePtrs col, int n_col, double* __restrict__ sumsq,
-                             double scale, double diag) {
+                             double scale, double diag, PiecePtrs dual_row = PiecePtrs{},
+                             double* __restrict__ dual_sumsq = nullptr) {
   __shared__ __nv_bfloat16 tile[3][SPLIT_R][SPLIT_C + 2];  // odd word pitch: conflict-free columns
   __shared__ float red[ROWS];
   const int i0 = blockIdx.y * SPLIT_R, j0 = blockIdx.x * SPLIT_C;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int jj = j0 + 4 * tx;
-  float ss = 0.f;
+  float ss = 0.f, ss_src = 0.f;
   // all of the thread's source rows are loaded before any is processed: four 32-byte loads
   // in flight per thread instead of one
   constexpr int RPT = SPLIT_R / ROWS;
@@ -119,6 +122,21 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
     double v[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) v[e] = vin[rr][e];
+    if (DUAL) {
+      __nv_bfloat16 pd[4][3];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float h = pieces3(v[e], pd[e]);
+        ss_src = fmaf(h, h, ss_src);
+      }
+      const int64_t off = int64_t(i) * np + jj;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const uint32_t lo2 = uint32_t(__bfloat16_as_ushort(pd[0][q])) | (uint32_t(__bfloat16_as_ushort(pd[1][q])) << 16);
+        const uint32_t hi2 = uint32_t(__bfloat16_as_ushort(pd[2][q])) | (uint32_t(__bfloat16_as_ushort(pd[3][q])) << 16);
+        *reinterpret_cast<uint2*>(dual_row.p[q] + off) = make_uint2(lo2, hi2);
+      }
+    }
     if (AFFINE) {
 #pragma unroll
       for (int e = 0; e < 4; ++e)
@@ -158,6 +176,19 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
       float t = 0.f;
       for (int w = 0; w < ROWS; ++w) t += red[w];
       sumsq[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = double(t);
+    }
+  }
+  if (DUAL) {
+    // the same for src itself (the affine output's sums above)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss_src += __shfl_down_sync(0xffffffffu, ss_src, o);
+    __syncthreads();
+    if (tx == 0) red[ty] = ss_src;
+    __syncthreads();
+    if (tx == 0 && ty == 0) {
+      float t = 0.f;
+      for (int w = 0; w < ROWS; ++w) t += red[w];
+      dual_sumsq[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = double(t);
     }
   }
   if (n_col > 0) {
@@ -392,6 +423,27 @@ static int split_affine(cudaStream_t st, const double* src, int64_t lds, int n, 
   for (int q = 0; q < n_col; ++q) c.p[q] = col_pieces[q];
   dim3 grid(np / SPLIT_C, np / SPLIT_R), block(32, ROWS);
   split_kernel<double, true><<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial, scale, diag);
+  NN_CUDA_TRY(cudaGetLastError());
+  return NN_OK;
+}
+
+int split_matrix_dual(cudaStream_t st, const double* src, int64_t lds, int n, int np,
+                      __nv_bfloat16* const* src_row_pieces, double* src_sumsq_partial, float* f32,
+                      __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
+                      double* sumsq_partial, double scale, double diag) {
+  if (np % SPLIT_C != 0 || n > np || n_row < 0 || n_row > 3 || n_col < 0 || n_col > 3 || sumsq_partial == nullptr ||
+      src_sumsq_partial == nullptr)
+    return NN_ERR_ARG;
+  PiecePtrs r{}, c{}, d{};
+  for (int q = 0; q < n_row; ++q) r.p[q] = row_pieces[q];
+  for (int q = 0; q < n_col; ++q) c.p[q] = col_pieces[q];
+  for (int q = 0; q < 3; ++q) {
+    if (src_row_pieces[q] == nullptr) return NN_ERR_ARG;
+    d.p[q] = src_row_pieces[q];
+  }
+  dim3 grid(np / SPLIT_C, np / SPLIT_R), block(32, ROWS);
+  split_kernel<double, true, true><<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial,
+                                                           scale, diag, d, src_sumsq_partial);
   NN_CUDA_TRY(cudaGetLastError());
   return NN_OK;
 }

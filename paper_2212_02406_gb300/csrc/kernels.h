@@ -105,6 +105,12 @@ int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np,
 int split_matrix_affine(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
                         __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
                         double* sumsq_partial, double scale, double diag);
+// One pass over src for both: the three row-major pieces of src with its per-block sums of squares
+// (as split_matrix), and the outputs of split_matrix_affine for scale * src + diag * I.
+int split_matrix_dual(cudaStream_t st, const double* src, int64_t lds, int n, int np,
+                      __nv_bfloat16* const* src_row_pieces, double* src_sumsq_partial, float* f32,
+                      __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
+                      double* sumsq_partial, double scale, double diag);
 // BF16 pieces of an FP32 matrix (the same pieces the GEMM epilogue writes for it).
 int split_matrix_f32(cudaStream_t st, const float* src, int64_t lds, int n, int np, __nv_bfloat16* const* row_pieces,
                      int n_row, __nv_bfloat16* const* col_pieces, int n_col);

@@ -33,6 +33,7 @@ struct Simt32Ws {
 struct MixedWs {
   int np;
   double* split_partial;  // one per 32 x 32 block of the split kernel
+  double* split_partial2;  // the second set of a two-output split
   __nv_bfloat16* a_row[3];
   float* x32[2];
   __nv_bfloat16* x_row[2][3];
@@ -42,6 +43,7 @@ struct MixedWs {
   __nv_bfloat16* r_col[3];
   __nv_bfloat16* t_col[2][3];
 };
+constexpr size_t kErrOffset = 256, kScalBlock = 512;
 struct Common {
   double* partial;
   int n_partial;
@@ -60,8 +62,9 @@ int partial_capacity(int64_t n, int dtype) {
 void carve_common(Carver& c, int64_t n, int dtype, Common& cm) {
   cm.n_partial = partial_capacity(n, dtype);
   cm.partial = c.take<double>(size_t(cm.n_partial));
-  cm.scal = c.take<double>(8);
-  cm.err = c.take<int>(8);
+  // scal[0..8) and the error word 256 bytes further in one block: one read-back per nest
+  cm.scal = c.take<double>(kScalBlock / sizeof(double));
+  cm.err = cm.scal == nullptr ? nullptr : reinterpret_cast<int*>(cm.scal + kErrOffset / sizeof(double));
 }
 
 void carve_f64(Carver& c, int64_t n, Simt64Ws& w) {
@@ -87,6 +90,7 @@ void carve_mixed(Carver& c, int64_t n, MixedWs& w) {
   w.np = int((n + 127) / 128 * 128);
   const size_t e = size_t(w.np) * size_t(w.np);
   w.split_partial = c.take<double>(size_t(split_blocks(w.np)));
+  w.split_partial2 = c.take<double>(size_t(split_blocks(w.np)));
   for (int i = 0; i < 3; ++i) w.a_row[i] = c.take<__nv_bfloat16>(e);
   for (int b = 0; b < 2; ++b) {
     w.x32[b] = c.take<float>(e);
@@ -129,20 +133,21 @@ bool valid_dtype(int d) {
   return d == NN_F64 || d == NN_F32 || d == NN_MIXED_BF16 || d == NN_F64_EMU || d == NN_MIXED_EMU;
 }
 
-// Reads s (and the device error word) back to the host; one stream synchronisation.
-int fetch_scalar(cudaStream_t st, const Common& cm, double* s, int* dev_err) {
-  NN_CUDA_TRY(cudaMemcpyAsync(s, cm.scal, sizeof(double), cudaMemcpyDeviceToHost, st));
-  NN_CUDA_TRY(cudaMemcpyAsync(dev_err, cm.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+// Reads count (<= 8) doubles from cm.scal and the device error word with one copy (they share
+// one block) and one stream synchronisation.
+int fetch_scalars(cudaStream_t st, const Common& cm, double* vals, int count, int* dev_err) {
+  if (count < 1 || count > 8) return NN_ERR_ARG;
+  double blk[kErrOffset / sizeof(double) + 1];
+  NN_CUDA_TRY(cudaMemcpyAsync(blk, cm.scal, kErrOffset + sizeof(int), cudaMemcpyDeviceToHost, st));
   NN_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < count; ++i) vals[i] = blk[i];
+  memcpy(dev_err, reinterpret_cast<const char*>(blk) + kErrOffset, sizeof(int));
   return NN_OK;
 }
 
-// Reads count doubles from cm.scal and the device error word; one stream synchronisation.
-int fetch_scalars(cudaStream_t st, const Common& cm, double* vals, int count, int* dev_err) {
-  NN_CUDA_TRY(cudaMemcpyAsync(vals, cm.scal, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
-  NN_CUDA_TRY(cudaMemcpyAsync(dev_err, cm.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  NN_CUDA_TRY(cudaStreamSynchronize(st));
-  return NN_OK;
+// Reads s (and the device error word) back to the host; one stream synchronisation.
+int fetch_scalar(cudaStream_t st, const Common& cm, double* s, int* dev_err) {
+  return fetch_scalars(st, cm, s, 1, dev_err);
 }
 
 // Applies the stop and divergence rules to s_k. Returns -1 to continue, else a status.
@@ -412,9 +417,13 @@ struct DevOut {
 
 namespace {
 
+int initial_level(const nn_opts& o) { return (o.bulk_pieces >= 1 && o.bulk_pieces <= 4) ? o.bulk_pieces : 1; }
+
+// r0_pre: R_0 = I - alpha A for the initial level is already in the residual layouts, its
+// per-block sums of squares in w.split_partial2 (written by the pass that split A).
 int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedWs& w, const nn_opts& o,
               const Common& cm, double a_frob, const X0Source& x0src, nn_result* res, int* final_idx, HostOut* ho,
-              DevOut* dout) {
+              DevOut* dout, bool r0_pre) {
   const int np = w.np;
   // X_0 = alpha I (the caller's assertion): the first nest's residual R_0 = I - alpha A and update
   // X_1 = alpha (I + T) are element-wise, split straight into the chain's layouts from FP64 A
@@ -424,7 +433,8 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
   const int sb = split_blocks(np);
   const double sqrt_n = sqrt(double(n));
   const double n15 = double(n) * sqrt(double(n));
-  int level = (o.bulk_pieces >= 1 && o.bulk_pieces <= 4) ? o.bulk_pieces : 1;
+  int level = initial_level(o);
+  const int r0_pre_hp = level_upd_pieces(level);
   int cur = 0;
   int k = 0;
   bool copy_next = false;  // the next residual's iterate is predicted to be returned
@@ -485,10 +495,16 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
   auto residual0 = [&](int L, double* s_out) -> int {
     const int hp = level_upd_pieces(L);
     const bool rows = max_depth(o) >= 2;
-    NN_TRY(split_matrix_affine(st, A, lda, n, np, rows ? w.r32 : nullptr, w.r_row, rows ? hp : 0, w.r_col, hp,
-                               w.split_partial, -alpha, 1.0));
-    NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0 / double(n), cm.scal));
-    res->launches += 2;
+    if (r0_pre && hp == r0_pre_hp) {
+      NN_TRY(reduce_rms(st, w.split_partial2, sb, 1.0 / double(n), cm.scal));
+      res->launches += 1;
+    } else {
+      NN_TRY(split_matrix_affine(st, A, lda, n, np, rows ? w.r32 : nullptr, w.r_row, rows ? hp : 0, w.r_col, hp,
+                                 w.split_partial, -alpha, 1.0));
+      NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0 / double(n), cm.scal));
+      res->launches += 2;
+    }
+    r0_pre = false;  // R's buffers are rewritten from here on
     int dev_err = 0;
     double vals[2];
     NN_TRY(fetch_scalars(st, cm, vals, 2, &dev_err));
@@ -785,7 +801,16 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     // BF16 pieces of A and X_0, with ||A||_F and ||X_0||_F (for the precision-level floors)
     // from the split kernel's per-block sums of squares
     const int sb = split_blocks(w.np);
-    NN_TRY(split_matrix(st, A, lda, ni, w.np, nullptr, w.a_row, 3, nullptr, 0, w.split_partial));
+    // with X_0 = alpha I the same pass over A also writes R_0 = I - alpha A for the first residual
+    const bool r0_pre = o.x0_scalar > 0;
+    if (r0_pre) {
+      const int hp = level_upd_pieces(initial_level(o));
+      const bool rows = max_depth(o) >= 2;
+      NN_TRY(split_matrix_dual(st, A, lda, ni, w.np, w.a_row, w.split_partial, rows ? w.r32 : nullptr, w.r_row,
+                               rows ? hp : 0, w.r_col, hp, w.split_partial2, -o.x0_scalar, 1.0));
+    } else {
+      NN_TRY(split_matrix(st, A, lda, ni, w.np, nullptr, w.a_row, 3, nullptr, 0, w.split_partial));
+    }
     NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0, cm.scal + 2));
     const X0Source x0src{X0, ldx0};
     if (o.x0_scalar <= 0) NN_TRY(load_x0(st, ni, w, cm, x0src));  // a scalar X_0 needs no pieces
@@ -807,7 +832,7 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     dout.X = X;
     dout.ldx = ldx;
     NN_TRY(run_mixed(st, ni, A, lda, w, o, cm, a_frob, x0src, res, &fin, ho,
-                     (ho == nullptr && early_ok) ? &dout : nullptr));
+                     (ho == nullptr && early_ok) ? &dout : nullptr, r0_pre));
     if (ho != nullptr && ho->pending) NN_CUDA_TRY(cudaStreamWaitEvent(st, ho->done, 0));
     if (o.dtype == NN_MIXED_EMU && res->status == NN_ERR_NOT_CONVERGED && res->nests < o.max_nests) {
       // Continue from the mixed chain's last iterate with emulated FP64 nests (NN converges from

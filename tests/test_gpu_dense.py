@@ -322,6 +322,25 @@ def test_scalar_x0_hint_matches_explicit_x0(nn, n, sched, kappa):
     assert abs(res2["history"][0] - s0) <= 1e-6 * s0
 
 
+@pytest.mark.parametrize("bulk", [1, 2, 3, 4])
+@pytest.mark.parametrize("depth", [1, 2])
+def test_scalar_x0_first_residual_any_start_level(nn, bulk, depth):
+    # With X_0 = alpha I the pass that splits A also writes R_0 = I - alpha A at the starting
+    # level's piece count (opts.bulk_pieces); every starting level must give the element-wise s_0
+    # and agree with the explicit-X_0 run's status.
+    n = 300
+    a, q, lam = synth.spd_spectrum(n, 1e2, seed=17)
+    alpha = 2.0 / (lam[0] + lam[-1])
+    x0 = dense.precond_scalar(n, alpha)
+    st1, res1, x1 = _run(nn, a, x0, depth, 1e-6, 40, "mixed_bf16", bulk_pieces=bulk)
+    st2, res2, x2 = _run(nn, a, x0, depth, 1e-6, 40, "mixed_bf16", bulk_pieces=bulk, x0_scalar=alpha)
+    assert st1 == st2 == nn.NN_OK
+    s0 = dense.rms_frob(np.eye(n) - alpha * a)
+    assert abs(res2["history"][0] - s0) <= 1e-6 * s0
+    s64 = dense.rms_frob(dense.residual(a, x2))
+    assert s64 < 1e-6 + e_acc(n)
+
+
 def test_host_pc_rejects_bad_preconditioner(nn):
     n = 8
     a = np.eye(n)
