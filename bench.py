@@ -44,7 +44,9 @@ def load_peaks():
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: dense and sparse 20, batched 200, otherwise 5; long enough "
+                         "for several clock samples inside the timed region)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dense", choices=["dense", "sparse", "batched", "serve", "normal"])
@@ -72,91 +74,43 @@ def parse_args():
     args = ap.parse_args()
     if args.n is None:
         args.n = 2048 if args.workload == "normal" else 8192
+    if args.steps is None:
+        args.steps = {"dense": 20, "sparse": 20, "batched": 200}.get(args.workload, 5) if args.impl == "ours" else 5
     return args
 
 
 # ---- clocks ------------------------------------------------------------------------------
 
-class NvmlClockSampler:
-    """SM clock, its maximum and the clock-event reasons of the benchmark's GPU, polled through NVML
-    (read-only queries) every few milliseconds from begin() to stop(), so that a timed region of a
-    few hundred milliseconds still gets tens of samples and none from the idle time around it."""
-    NVML_CLOCK_SM = 1
-    REASONS = ((0x8, "hw_slowdown"), (0x40, "hw_thermal_slowdown"), (0x20, "sw_thermal_slowdown"),
-               (0x4, "sw_power_cap"), (0x80, "hw_power_brake_slowdown"))
-
-    def __init__(self, device, period_s=0.005):
-        import ctypes
-        import threading
-
-        import torch
-
-        self.ct = ctypes
-        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
-        if self.lib.nvmlInit_v2() != 0:
-            raise RuntimeError("nvmlInit failed")
-        props = torch.cuda.get_device_properties(device)
-        bus = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0".encode()
-        self.h = ctypes.c_void_p()
-        if self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(self.h)) != 0:
-            raise RuntimeError("no NVML handle for the device")
-        mx = ctypes.c_uint()
-        self.max_mhz = float(mx.value) if self.lib.nvmlDeviceGetMaxClockInfo(
-            self.h, self.NVML_CLOCK_SM, ctypes.byref(mx)) == 0 else None
-        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
-        self.period = period_s
-        self.samples = []
-        self.window = threading.Event()
-        self.done = threading.Event()
-        self.thread = threading.Thread(target=self._run, daemon=True)
-
-    def _run(self):
-        ct = self.ct
-        mhz, rs = ct.c_uint(), ct.c_ulonglong()
-        while not self.done.is_set():
-            if self.window.is_set():
-                ok = self.lib.nvmlDeviceGetClockInfo(self.h, self.NVML_CLOCK_SM, ct.byref(mhz)) == 0
-                ok = ok and self.reasons_fn(self.h, ct.byref(rs)) == 0
-                if ok:
-                    self.samples.append((float(mhz.value), int(rs.value)))
-            time.sleep(self.period)
-
-    def start(self):
-        self.thread.start()
-
-    def begin(self):
-        self.window.set()
-
-    def stop(self):
-        self.window.clear()
-        self.done.set()
-        self.thread.join(timeout=5)
-        if not self.samples:
-            return None
-        reasons = sorted({name for _, r in self.samples for bit, name in self.REASONS if r & bit})
-        return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
-                "reasons": reasons, "samples": len(self.samples), "source": "nvml, every 5 ms of the timed region"}
-
-
 def clock_sampler(gpu_index):
-    """NVML polling where the library and the device's PCI location are available, else
-    nvidia-smi."""
-    try:
-        return NvmlClockSampler(gpu_index)
-    except Exception:
-        return ClockSampler(gpu_index)
+    return ClockSampler(gpu_index)
+
+
+def bf16_peak(peaks, peak_src, clocks):
+    """The measured cuBLAS BF16 peak that matches the timed region's regime: the sustained figure
+    (seconds of back-to-back GEMMs under the power cap) when the GPU reported sw_power_cap during
+    the region, else the burst figure. Returns (peak, label, burst peak)."""
+    burst = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+    if clocks and "sw_power_cap" in clocks.get("reasons", []):
+        sus = float(peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))
+        return sus, f"{peak_src} bf16 sustained (sw_power_cap active in the timed region)", burst
+    return burst, f"{peak_src} bf16 burst", burst
 
 
 class ClockSampler:
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi in its own process, sampling every 100 ms from start() (before the warm-up, so
+    that it is running when the timed region begins); stop() keeps the samples whose timestamps
+    fall between begin() and stop() (the timed region), or, when the region is shorter than the
+    sampling period, the samples nearest to it."""
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 100
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.t_begin = None
 
     def start(self):
         try:
@@ -164,16 +118,22 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", str(self.PERIOD_MS)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
     def begin(self):
-        pass
+        import datetime
+
+        self.t_begin = datetime.datetime.now()
 
     def stop(self):
+        import datetime
+
+        t_end = datetime.datetime.now()
         if self.proc is None:
             return None
+        time.sleep(self.PERIOD_MS / 1000.0)  # the sample after the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -183,17 +143,32 @@ class ClockSampler:
         with open(self.path) as f:
             for line in f:
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                except ValueError:
+                    continue
+                rows.append((ts, parts))
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        t0 = self.t_begin or t_end
+        inside = [r for ts, r in rows if t0 <= ts <= t_end]
+        if inside:
+            kept, where = inside, "timed region"
+        else:
+            # region shorter than the period: the last sample before it and the first after it
+            before = [r for ts, r in rows if ts < t0][-1:]
+            after = [r for ts, r in rows if ts > t_end][:1]
+            kept, where = before + after, "nearest to the timed region"
+        sm = [float(r[2]) for r in kept if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in kept if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        reasons = sorted({names[i] for r in kept for i in range(4) if r[6 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(kept), "window": where,
+                "source": f"nvidia-smi every {self.PERIOD_MS} ms"}
 
 
 # ---- CPU baseline: the oracle as it stands -------------------------------------------------
@@ -283,6 +258,9 @@ def run_dense(args, rank, world, local_rank):
                          x0_scalar=0.0 if args.no_scalar_x0 else alpha)
     stream = torch.cuda.current_stream(dev)
 
+    sampler = clock_sampler(local_rank)
+    sampler.start()  # running (it takes a moment to start) before the warm-up heats the GPU
+    time.sleep(0.3)
     for _ in range(args.warmup):
         st, res = abi.nn_invert(A, X0, opts, X, ws, stream)
         assert st == abi.NN_OK, (st, res)
@@ -294,10 +272,7 @@ def run_dense(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    sampler = clock_sampler(local_rank)
     barrier()
-    sampler.start()
-    time.sleep(0.3)
     sampler.begin()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -331,10 +306,11 @@ def run_dense(args, rank, world, local_rank):
         # tensor-core work of the emulated products over the GEMM calls' time (slicing included)
         hw = sum(r["hw_flops"] for _, r in results)
         achieved = hw / (tc_ms / 1e3) / 1e12
-        peak = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+        peak, label, burst = bf16_peak(peaks, peak_src, clocks)
         roofline = {"kernel": "nn::tc::gemm_tc_2sm_kernel (FP64 emulation: exact BF16 slice products)",
                     "bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
-                    "frac": round(achieved / peak, 4), "traffic": None, "peak_source": f"{peak_src} bf16 burst",
+                    "frac": round(achieved / peak, 4), "frac_of_burst": round(achieved / burst, 4),
+                    "traffic": None, "peak_source": label,
                     "launches": tc_launches, "avg_launch_ms": round(tc_ms / tc_launches, 4),
                     "fp64_equivalent_tflops": round(tc_flops / (tc_ms / 1e3) / 1e12, 3),
                     "flops_per_launch": "2 Np^3 per BF16 slice product, all products of one emulated FP64 GEMM"}
@@ -349,7 +325,7 @@ def run_dense(args, rank, world, local_rank):
                     "launches": tc_launches, "avg_launch_ms": round(tc_ms / tc_launches, 4)}
     elif tc_launches > 0 and tc_ms > 0:
         achieved = tc_flops / (tc_ms / 1e3) / 1e12
-        peak = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+        peak, label, burst = bf16_peak(peaks, peak_src, clocks)
         kernel = {1: "nn::tc::gemm_tc_kernel", 2: "nn::tc::gemm_tc_pair_kernel"}.get(args.gemm_variant,
                                                                                  "nn::tc::gemm_tc_2sm_kernel")
         # ncu DRAM bytes per launch (mean over one step) of the profiled default configuration
@@ -358,8 +334,9 @@ def run_dense(args, rank, world, local_rank):
                 and args.tol == 1e-6 and args.seed == 0):
             traffic = profile_traffic("gemm_tc_2sm_dense_n8192.md", ["gemm_tc.cu", "nn_dense.cu"])
         roofline = {"kernel": kernel, "bound": "tensor", "achieved": round(achieved, 2),
-                    "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                    "peak_source": f"{peak_src} bf16 burst", "launches": tc_launches,
+                    "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                    "frac_of_burst": round(achieved / burst, 4), "traffic": traffic,
+                    "peak_source": label, "launches": tc_launches,
                     "avg_launch_ms": round(tc_ms / tc_launches, 4),
                     "flops_per_launch": "2 Np^3 per BF16 product pass (split passes are real tensor work)"}
 
@@ -467,13 +444,13 @@ def run_normal(args, rank, world, local_rank):
     ws = abi.normal_workspace(n, 1, False, dtype, device=dev)
     opts = abi.make_opts(depth, tol, 64, dtype, flags=abi.NN_FLAG_TIME_KERNELS)
     stream = torch.cuda.current_stream(dev)
+    sampler = clock_sampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
     for _ in range(args.warmup):
         st, res = abi.nn_solve_normal(A, B, opts, X, ws, stream)
         assert st == abi.NN_OK, (st, res)
     torch.cuda.synchronize(dev)
-    sampler = clock_sampler(local_rank)
-    sampler.start()
-    time.sleep(0.3)
     sampler.begin()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -494,13 +471,14 @@ def run_normal(args, rank, world, local_rank):
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     if dtype == "f64_emu":
         peaks, peak_src = load_peaks()
-        peak = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+        peak, label, burst = bf16_peak(peaks, peak_src, clocks)
         hw = sum(r["hw_flops"] for _, r in results)
         achieved = hw / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
         roofline = {"kernel": "nn::tc::gemm_tc_2sm_kernel (FP64 emulation: exact BF16 slice products)",
                     "bound": "tensor", "achieved": round(achieved, 2) if achieved else None, "peak": peak,
-                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
-                    "peak_source": f"{peak_src} bf16 burst", "launches": gemm_launches,
+                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if achieved else None,
+                    "frac_of_burst": round(achieved / burst, 4) if achieved else None, "traffic": None,
+                    "peak_source": label, "launches": gemm_launches,
                     "avg_launch_ms": round(gemm_ms / max(gemm_launches, 1), 4),
                     "fp64_equivalent_tflops": round(gemm_flops / (gemm_ms / 1e3) / 1e12, 3) if gemm_ms > 0 else None}
     else:
@@ -616,13 +594,13 @@ def run_sparse(args, rank, world, local_rank):
     ws = abi.csr_workspace(m.n, m.nnz, 1, kind, device=dev)
     stream = torch.cuda.current_stream(dev)
     dfl = kind == "f64_df"
+    sampler = clock_sampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
     for _ in range(args.warmup):
         st, res = abi.nn_solve_csr(rp, col, val, B, depth, nests, 0.0, X, ws, stream, double_float=dfl)
         assert st == abi.NN_OK, (st, res)
     torch.cuda.synchronize(dev)
-    sampler = clock_sampler(local_rank)
-    sampler.start()
-    time.sleep(0.3)
     sampler.begin()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -703,13 +681,13 @@ def run_batched(args, rank, world, local_rank):
     with torch.cuda.graph(g):
         assert abi.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws,
                                          classes=classes) == 0
+    sampler = clock_sampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
     for _ in range(args.warmup):
         g.replay()
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize(dev)
-    sampler = clock_sampler(local_rank)
-    sampler.start()
-    time.sleep(0.3)
     sampler.begin()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ev[0].record(stream)
