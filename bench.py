@@ -104,7 +104,7 @@ class ClockSampler:
     QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-    PERIOD_MS = 100
+    PERIOD_MS = 200
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index

@@ -832,6 +832,7 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
         if (!encode_bf16_2d(&p.map_b_half[s], a.b_seg[s], a.np, tc::BN / 4)) return NN_ERR_CUDA;
     }
     cudaLaunchAttribute attr[1];
+    if (a.ev_before) NN_CUDA_TRY(cudaEventRecord(a.ev_before, st));
     if (variant == 2) {
       cudaLaunchConfig_t cfg = cluster_config(grid, tc::SMEM_BYTES, st, attr);
       NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc::gemm_tc_pair_kernel, p));
@@ -842,9 +843,11 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
   } else {
     const int tiles = p.tiles_m * p.tiles_n;
     grid = tiles < g_sms ? tiles : g_sms;
+    if (a.ev_before) NN_CUDA_TRY(cudaEventRecord(a.ev_before, st));
     tc::gemm_tc_kernel<<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(p);
     NN_CUDA_TRY(cudaGetLastError());
   }
+  if (a.ev_after) NN_CUDA_TRY(cudaEventRecord(a.ev_after, st));
   if (grid_used) *grid_used = grid;
   return NN_OK;
 }

@@ -72,6 +72,9 @@ struct TcGemmArgs {
   double* cvt_dst = nullptr;
   int64_t cvt_ld = 0;
   int cvt_n = 0;
+  // Optional events recorded on the stream immediately before and after the kernel launch (after
+  // the host has prepared it), so that their interval is the kernel's device time.
+  cudaEvent_t ev_before = nullptr, ev_after = nullptr;
 };
 int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used);
 int gemm_tc_max_grid();

@@ -190,6 +190,7 @@ struct LaunchTimer {
       cudaEventDestroy(e.second);
     }
   }
+  // Events around a whole product (several launches: CUDA-core and emulated FP64 products).
   int begin(cudaStream_t st) {
     if (!on) return NN_OK;
     cudaEvent_t a, b;
@@ -206,6 +207,21 @@ struct LaunchTimer {
   int end(cudaStream_t st) {
     if (!on) return NN_OK;
     NN_CUDA_TRY(cudaEventRecord(ev.back().second, st));
+    return NN_OK;
+  }
+  // A pair of events for the next tensor-core GEMM, recorded by gemm_tc around the launch itself.
+  int arm(TcGemmArgs& g) {
+    if (!on) return NN_OK;
+    cudaEvent_t a, b;
+    NN_CUDA_TRY(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      (void)cudaGetLastError();
+      return NN_ERR_CUDA;
+    }
+    ev.emplace_back(a, b);
+    g.ev_before = a;
+    g.ev_after = b;
     return NN_OK;
   }
   // After the stream has been synchronised.
@@ -333,9 +349,8 @@ int tc_product(cudaStream_t st, TcGemmArgs& g, int pieces, __nv_bfloat16* const*
     g.b_seg[s] = b_pieces[pairs[s][1]];
   }
   g.err = cm.err;
-  NN_TRY(tm->begin(st));
+  NN_TRY(tm->arm(g));
   NN_TRY(gemm_tc(st, g, grid));
-  NN_TRY(tm->end(st));
   const double np3 = double(g.np) * double(g.np) * double(g.np);
   res->gemms += 1;
   res->launches += 1;
