@@ -341,6 +341,27 @@ def test_scalar_x0_first_residual_any_start_level(nn, bulk, depth):
     assert s64 < 1e-6 + e_acc(n)
 
 
+@pytest.mark.parametrize("refine", [1e-1, 1e-3])
+@pytest.mark.parametrize("hint", [False, True])
+def test_level_rise_at_measurement_regenerates_pieces(nn, refine, hint):
+    # opts.refine_below raises the level to 3 once s sqrt(N) falls below it, a rise that the
+    # per-nest prediction does not foresee: the iterate's BF16 pieces (written for the predicted
+    # level only) are split again from its FP32 master before the residual reads them. The run
+    # must converge, reach level 3, and report a residual that an FP64 re-evaluation confirms.
+    n = 384
+    a, q, lam = synth.spd_spectrum(n, 1e2, seed=23)
+    alpha = 2.0 / (lam[0] + lam[-1])
+    x0 = dense.precond_scalar(n, alpha)
+    kw = dict(refine_below=refine, x0_scalar=alpha if hint else 0.0)
+    st, res, x = _run(nn, a, x0, 2, 1e-6, 40, "mixed_bf16", **kw)
+    assert st == nn.NN_OK, res
+    assert 3 in res["pieces"]
+    s64 = dense.rms_frob(dense.residual(a, x))
+    assert abs(s64 - res["residual"]) <= e_acc(n)
+    ainv = (q / lam) @ q.T
+    assert _rel(x, ainv) <= 2 * math.sqrt(n) * s64 + 16 * 1e2 * U32
+
+
 def test_host_pc_rejects_bad_preconditioner(nn):
     n = 8
     a = np.eye(n)
