@@ -250,8 +250,27 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
   bool frozen = !active;
   float s_prev = 0.f, s_last = 0.f;
   int st = NN_OK;
+  // X_0 is diagonal, so with at least one nest the first nest's residual R_0 = I - A X_0 (a
+  // column scaling) and update X_1 = X_0 (I + T) (a row scaling) are element-wise; x0 is
+  // recomputed from A's diagonal exactly as X_0 was, so X is never read while it is rewritten.
+  const float cdamp = 1.f / (1.f + p.damping * float(U));
   for (int k = 0; k <= p.nests; ++k) {
-    const float ss = group_product<TG, T, UC>(U, ti, tj, Ab, Xb, Rb, nullptr, BM_RESID, false, frozen);
+    const bool diag0 = k == 0;
+    float ss = 0.f;
+    if (diag0) {
+      if (!frozen) {
+        for (int e = lt; e < uu; e += NTHR) {
+          const int i = e / U, j = e % U;
+          const float2 a = Ab[e];
+          const float2 xj = Xb[j * U + j];
+          const float2 r = make_float2((i == j ? 1.f : 0.f) - (a.x * xj.x - a.y * xj.y), -(a.x * xj.y + a.y * xj.x));
+          Rb[e] = r;
+          ss = fmaf(r.x, r.x, fmaf(r.y, r.y, ss));
+        }
+      }
+    } else {
+      ss = group_product<TG, T, UC>(U, ti, tj, Ab, Xb, Rb, nullptr, BM_RESID, false, frozen);
+    }
     group_sum(ss, g < groups ? g : 0, lt, NTHR, red_warp, red_grp);  // includes CTA barriers
     if (!frozen) {
       const float s = sqrtf(red_grp[g]) / float(U);
@@ -271,7 +290,20 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
       __syncthreads();
       t_cur = Tb;
     }
-    group_product<TG, T, UC>(U, ti, tj, Xb, t_cur, Xb, Xb, BM_ADD, true, frozen);
+    if (diag0) {
+      if (!frozen) {
+        for (int e = lt; e < uu; e += NTHR) {
+          const int i = e / U, j = e % U;
+          const float2 a = Ab[i * U + i];
+          const float den = a.x * a.x + a.y * a.y;
+          const float2 xi = make_float2(cdamp * a.x / den, -cdamp * a.y / den);
+          const float2 t = make_float2(t_cur[e].x + (i == j ? 1.f : 0.f), t_cur[e].y);
+          Xb[e] = make_float2(xi.x * t.x - xi.y * t.y, xi.x * t.y + xi.y * t.x);
+        }
+      }
+    } else {
+      group_product<TG, T, UC>(U, ti, tj, Xb, t_cur, Xb, Xb, BM_ADD, true, frozen);
+    }
     __syncthreads();
   }
   if (active) {
@@ -548,9 +580,15 @@ __device__ __forceinline__ float bt_block_sum(float v, float* red_warp) {
 // barrier the pieces of A's left operand [Ar; Ai] overwrite the area; X_0 = c diag(A)^-1
 // (damped Jacobi) goes to the X master at column cX (padding lanes zero). Every worker thread
 // calls it.
+// first_nest: X_0 is diagonal, so the first nest's residual R_0 = I - A X_0 is the column
+// scaling R_0[i][j] = delta_ij - A[i][j] x0[j]; it is formed here in FP32 (the x0[j] in x0s,
+// R_0 into the R master at column cR; depth 1 (one_step): X_1 = X_0 (I + R_0), the row scaling
+// x0[i] (delta_ij + R_0[i][j]), into the X master instead of X_0). Returns this thread's sum
+// of squares of R_0 (valid lanes and columns).
 template <int U>
-__device__ __forceinline__ void tc_load_matrix(const float2* A, float damping, uint8_t* acache, uint32_t tmem,
-                                               uint32_t cX, int q, int h, int l) {
+__device__ __forceinline__ float tc_load_matrix(const float2* A, float damping, uint8_t* acache, uint32_t tmem,
+                                                uint32_t cX, uint32_t cR, float2* x0s, bool first_nest, bool one_step,
+                                                int q, int h, int l) {
   constexpr int XP = 2 * U + 1;
   float* st = reinterpret_cast<float*>(acache);
   const float* src = reinterpret_cast<const float*>(A);
@@ -564,33 +602,99 @@ __device__ __forceinline__ void tc_load_matrix(const float2* A, float damping, u
     st[(e / (2 * U)) * XP + e % (2 * U)] = v[k];
   }
   tc_wsync();
+  const float cdamp = 1.f / (1.f + damping * float(U));
+  if (threadIdx.x < U) {
+    // x0[t] = c / A[t][t]
+    const float ar = st[threadIdx.x * XP + 2 * threadIdx.x], ai = st[threadIdx.x * XP + 2 * threadIdx.x + 1];
+    const float den = ar * ar + ai * ai;
+    x0s[threadIdx.x] = make_float2(cdamp * ar / den, -cdamp * ai / den);
+  }
+  tc_wsync();
   const bool active = h * btc::CW < U;
   int i;
   bool im;
   const bool valid_row = tc_lane_row<U>(l, i, im) && active;
   const bool re = !im;
-  uint32_t va[btc::CW], vx[btc::CW];
-  float2 aii = make_float2(1.f, 0.f);
-  if (valid_row) aii = make_float2(st[i * XP + 2 * i], st[i * XP + 2 * i + 1]);
-  const float cdamp = 1.f / (1.f + damping * float(U));
-  const float den = aii.x * aii.x + aii.y * aii.y;
+  const uint32_t lane_off = uint32_t(q * 32) << 16;
+  const float2 xi = valid_row ? x0s[i] : make_float2(0.f, 0.f);
+  float local = 0.f;
+  {
+    // the X master (X_0, or X_1 at depth 1 with the first nest element-wise) and R_0 go to TMEM
+    // before A's pieces are formed, so that their registers are free again
+    uint32_t vx[btc::CW], vr[btc::CW];
+#pragma unroll
+    for (int t = 0; t < btc::CW; ++t) {
+      const int j = h * btc::CW + t;
+      float xv = 0.f, rv = 0.f;
+      if (valid_row && j < U) {
+        if (j == i) xv = re ? xi.x : xi.y;
+        if (first_nest) {
+          const float ar = st[i * XP + 2 * j], ai = st[i * XP + 2 * j + 1];
+          const float2 xj = x0s[j];
+          const float d = (re && j == i) ? 1.f : 0.f;
+          rv = re ? d - (ar * xj.x - ai * xj.y) : -(ar * xj.y + ai * xj.x);
+          local = fmaf(rv, rv, local);
+        }
+      }
+      vx[t] = __float_as_uint(xv);
+      vr[t] = __float_as_uint(rv);
+    }
+    if (first_nest && one_step) {
+      // X_1[i][j] = x0[i] (delta_ij + R_0[i][j]); the row's other part from the partner lane
+#pragma unroll
+      for (int t = 0; t < btc::CW; ++t) {
+        const int j = h * btc::CW + t;
+        const float own = __uint_as_float(vr[t]) + ((re && j == i) ? 1.f : 0.f);
+        const float other = __shfl_xor_sync(0xffffffffu, own, 1);
+        const float pr = re ? own : other, pi = re ? other : own;
+        const float xv = re ? xi.x * pr - xi.y * pi : xi.x * pi + xi.y * pr;
+        vx[t] = __float_as_uint(valid_row ? xv : 0.f);
+      }
+    }
+    if (active) {
+      tmem_st_cw(tmem + lane_off + cX + uint32_t(h * btc::CW), vx);
+      if (first_nest) tmem_st_cw(tmem + lane_off + cR + uint32_t(h * btc::CW), vr);
+      tmem_st_wait();
+    }
+  }
+  uint32_t va[btc::CW];
 #pragma unroll
   for (int t = 0; t < btc::CW; ++t) {
     const int j = h * btc::CW + t;
-    float av = 0.f, xv = 0.f;
-    if (valid_row) {
-      av = st[i * XP + 2 * j + (re ? 0 : 1)];
-      if (j == i) xv = re ? cdamp * aii.x / den : -cdamp * aii.y / den;
-    }
-    va[t] = __float_as_uint(av);
-    vx[t] = __float_as_uint(xv);
+    va[t] = __float_as_uint((valid_row && j < U) ? st[i * XP + 2 * j + (re ? 0 : 1)] : 0.f);
   }
   tc_wsync();
   if (valid_row) tc_row_pieces<U>(va, acache, l, h * btc::CW);
-  if (active) {
-    tmem_st_cw(tmem + (uint32_t(q * 32) << 16) + cX + uint32_t(h * btc::CW), vx);
-    tmem_st_wait();
+  return local;
+}
+
+// X_1 = X_0 (I + T) for a diagonal X_0 (the first nest's update): the row scaling
+// x0[i] (delta_ij + T[i][j]) from the T master at column cT into the X master at column cX.
+// Every lane of an active warp calls it (shuffles).
+template <int U>
+__device__ __forceinline__ void tc_diag_update(uint32_t tmem, uint32_t cT, uint32_t cX, const float2* x0s, int q,
+                                               int h, int l) {
+  if (h * btc::CW >= U) return;
+  int i;
+  bool im;
+  const bool valid = tc_lane_row<U>(l, i, im);
+  const bool re = !im;
+  const float2 xi = valid ? x0s[i] : make_float2(0.f, 0.f);
+  const uint32_t lane_off = uint32_t(q * 32) << 16;
+  uint32_t tv[btc::CW];
+  tmem_ld_cw(tmem + lane_off + cT + uint32_t(h * btc::CW), tv);
+  tmem_ld_wait();
+#pragma unroll
+  for (int t = 0; t < btc::CW; ++t) {
+    const int j = h * btc::CW + t;
+    const float own = __uint_as_float(tv[t]) + ((re && j == i) ? 1.f : 0.f);
+    const float other = __shfl_xor_sync(0xffffffffu, own, 1);
+    const float pr = re ? own : other, pi = re ? other : own;
+    const float xv = re ? xi.x * pr - xi.y * pi : xi.x * pi + xi.y * pr;
+    tv[t] = __float_as_uint((valid && j < U) ? xv : 0.f);
   }
+  tmem_st_cw(tmem + lane_off + cX + uint32_t(h * btc::CW), tv);
+  tmem_st_wait();
 }
 
 // X (complex, row-major) from the X master at column cX, through the slot's cache area (free:
@@ -629,6 +733,7 @@ struct TcSlot {
   int k, j;       // nest, product within the nest (0 = residual, 1..L-1 Horner, L = update)
   int st;
   float s_prev, s_last;
+  int diag;       // the first nest runs element-wise (R_0 formed at load, X_1 by row scaling)
 };
 
 // Masters of the product that a slot at state (k, j) runs next (the residual's left operand is
@@ -670,10 +775,13 @@ template <int U>
 __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls, int first, int last,
                                                 const int32_t* items, uint8_t* ops, uint32_t ops_s, uint32_t tmem,
                                                 uint64_t* mma_bar, int* abort_word, int* item_sh, float* red_warp,
-                                                TcCmd* cmd) {
+                                                TcCmd* cmd, float2 (*x0s)[64]) {
   const int w = int(threadIdx.x >> 5), q = w & 3, h = w >> 2, l = q * 32 + int(threadIdx.x & 31);
   const int nslots = p.depth <= 2 ? 2 : 1;
-  TcSlot sl0 = {-1, 0, 0, NN_OK, 0.f, 0.f}, sl1 = sl0;  // two named slots: no local memory
+  TcSlot sl0 = {-1, 0, 0, NN_OK, 0.f, 0.f, 0}, sl1 = sl0;  // two named slots: no local memory
+  // With at least one nest the first nest's residual and update are element-wise (X_0 is
+  // diagonal); with none the residual of X_0 runs as a product.
+  const bool first_nest = p.nests >= 1;
   uint32_t phase = 0;
   bool outstanding = false;
   bool ok = true;
@@ -684,11 +792,29 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
     tc_wsync();
     const int it = *item_sh;
     tc_wsync();
-    TcSlot t = {-1, 0, 0, NN_OK, 0.f, 0.f};
+    TcSlot t = {-1, 0, 0, NN_OK, 0.f, 0.f, 0};
     if (it < last) {
       t.b = p.plan[PLAN_HDR + items[4 * it + 1]];
-      tc_load_matrix<U>(p.A + p.offsets[t.b], p.damping, ops + btc::A_CACHE + s * btc::OPND, tmem,
-                        uint32_t(s) * btc::SLOT_COLS + btc::MX, q, h, l);
+      const uint32_t sb = uint32_t(s) * btc::SLOT_COLS;
+      const float ss = tc_load_matrix<U>(p.A + p.offsets[t.b], p.damping, ops + btc::A_CACHE + s * btc::OPND, tmem,
+                                         sb + btc::MX, sb + btc::MR, x0s[s], first_nest, p.depth == 1, q, h, l);
+      if (first_nest) {
+        const float s0 = sqrtf(bt_block_sum(ss, red_warp)) / float(U);
+        if (isfinite(s0)) {
+          // nest 0's residual is done; next: its first Horner product, or (depth 1, X_1 already
+          // formed) nest 1's residual
+          t.s_prev = t.s_last = s0;
+          t.diag = 1;
+          if (p.depth == 1) {
+            t.k = 1;
+            t.j = 0;
+          } else {
+            t.j = 1;
+          }
+        }
+        // a non-finite s_0 (a zero or non-finite diagonal): the residual runs as a product and
+        // reports the matrix as diverged
+      }
     }
     if (s == 0)
       sl0 = t;
@@ -730,6 +856,10 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
     TcSlot t = s == 0 ? sl0 : sl1;
     const TcProd pr = tc_product(t, sb, p.depth);
     const float ss = tc_epilogue<U>(tmem, sb + btc::ACC, pr.cD, pr.cOut, pr.mode, q, h, l);
+    // the first nest's update X_1 = X_0 (I + T) is a row scaling: right after its last Horner
+    // product (each thread reads back what it wrote)
+    const bool diag_update = t.diag && t.k == 0 && t.j + 1 == p.depth;
+    if (diag_update) tc_diag_update<U>(tmem, pr.cOut, sb + btc::MX, x0s[s], q, h, l);
     tc_fence_before();
     bool done = false;
     if (pr.mode == BM_RESID) {
@@ -745,7 +875,7 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
     tc_wsync();
     tc_fence_after();
     if (!done) {
-      if (++t.j > p.depth) {
+      if (diag_update || ++t.j > p.depth) {
         t.j = 0;
         ++t.k;
       }
@@ -833,6 +963,7 @@ __global__ void __launch_bounds__(btc::THREADS + 32, 1) batched_tc_kernel(const 
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_word;
   __shared__ TcCmd cmd;
+  __shared__ float2 x0s[2][64];  // per slot: the diagonal of X_0
   pdl_launch_dependents();
   const int count = p.plan[1];
   const int first = p.plan[3 + cls], last = p.plan[3 + cls + 1];
@@ -866,7 +997,7 @@ __global__ void __launch_bounds__(btc::THREADS + 32, 1) batched_tc_kernel(const 
       }
     } else {
       batched_tc_work<U>(p, cls, first, last, items, ops, ops_s, tmem, &mma_bar, &abort_word, &item_sh, red_warp,
-                         &cmd);
+                         &cmd, x0s);
     }
     tc_fence_before();
     __syncthreads();
@@ -978,8 +1109,24 @@ __device__ void warp_item(const BatchedParams& p, int b, float2* buf, int lane) 
   __syncwarp();
   float s_prev = 0.f, s_last = 0.f;
   int st = NN_OK;
+  // the first nest element-wise (X_0 diagonal): R_0 = I - A X_0, X_1 = X_0 (I + T), x0
+  // recomputed from A's diagonal exactly as above
   for (int k = 0; k <= p.nests; ++k) {
-    float ss = warp_product<U>(Ab, Xb, nullptr, Rb, BM_RESID, ti, tj);
+    const bool diag0 = k == 0;
+    float ss = 0.f;
+    if (diag0) {
+      for (int e = lane; e < U * U; e += 32) {
+        const int i = e / U, j = e % U;
+        const float2 a = Ab[i * S::PITCH + j];
+        const float2 xj = Xb[j * S::PITCH + j];
+        const float2 r = make_float2((i == j ? 1.f : 0.f) - (a.x * xj.x - a.y * xj.y), -(a.x * xj.y + a.y * xj.x));
+        Rb[i * S::PITCH + j] = r;
+        ss = fmaf(r.x, r.x, fmaf(r.y, r.y, ss));
+      }
+      __syncwarp();
+    } else {
+      ss = warp_product<U>(Ab, Xb, nullptr, Rb, BM_RESID, ti, tj);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     const float s = sqrtf(ss) / float(U);
@@ -996,7 +1143,20 @@ __device__ void warp_item(const BatchedParams& p, int b, float2* buf, int lane) 
       warp_product<U>(Rb, t_cur, Rb, Tb, BM_ADD, ti, tj);
       t_cur = Tb;
     }
-    warp_product<U>(Xb, t_cur, Xb, Xb, BM_ADD, ti, tj);
+    if (diag0) {
+      for (int e = lane; e < U * U; e += 32) {
+        const int i = e / U, j = e % U;
+        const float2 a = Ab[i * S::PITCH + i];
+        const float den = a.x * a.x + a.y * a.y;
+        const float2 xi = make_float2(c * a.x / den, -c * a.y / den);
+        const float2 tv = t_cur[i * S::PITCH + j];
+        const float2 t = make_float2(tv.x + (i == j ? 1.f : 0.f), tv.y);
+        Xb[i * S::PITCH + j] = make_float2(xi.x * t.x - xi.y * t.y, xi.x * t.y + xi.y * t.x);
+      }
+      __syncwarp();
+    } else {
+      warp_product<U>(Xb, t_cur, Xb, Xb, BM_ADD, ti, tj);
+    }
   }
   for (int e = lane; e < U * U; e += 32) p.X[off + e] = Xb[(e / U) * S::PITCH + e % U];
   if (lane == 0) {
