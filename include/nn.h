@@ -253,10 +253,12 @@ int nn_solve_normal(const void* A, int64_t n, int64_t lda, int is_complex, const
 
 /* ---- batched small complex inversions ---------------------------------------------------
  * Many independent U x U complex64 matrices (U <= 64; massive-MIMO Gram matrices, the use the
- * paper names in Corollary 4) inverted by the right-multiplied NN loop in one persistent
- * kernel: X_0 = diag(A)^-1 / (1 + damping * U) (Jacobi start, a diagonal Theta of Appendix 1;
- * damping = 0 is plain Jacobi), then `nests` nests of depth L, with s_k = ||I - A X_k||_F / U
- * and the divergence rule of nn_invert (a diverged matrix keeps the X_k at which it diverged).
+ * paper names in Corollary 4) inverted by the right-multiplied NN loop in persistent kernels
+ * (one per tile class): X_0 = diag(A)^-1 / (1 + damping * U) (Jacobi start, a diagonal Theta of
+ * Appendix 1; damping = 0 is plain Jacobi), then `nests` nests of depth L, with s_k =
+ * ||I - A X_k||_F / U and the divergence rule of nn_invert (a diverged matrix keeps the X_k at
+ * which it diverged). X_0 being diagonal, the first nest's residual I - A X_0 and update
+ * X_0 (I + T) are computed element-wise (column and row scalings) rather than as products.
  *
  * nn_batched_plan (host only): sorts the matrices by size (largest first) and groups equal
  * sizes into work items. sizes_host[count] in 1..64; cfg_by_u (nullable, 65 entries indexed by
@@ -264,8 +266,9 @@ int nn_solve_normal(const void* A, int64_t n, int64_t lda, int is_complex, const
  * matrices per CTA; 1: CUDA cores, 16x16 threads per matrix; 3: CUDA cores, one warp per
  * matrix, for U in {8, 16, 24, 32} (other sizes fall back to 0 or 1); 2: tensor cores, for U in
  * {48, 64} (other sizes fall back to 0 or 1): the iterates stay in TMEM, each complex product
- * is a tcgen05 MMA chain on the real embedding [[Pr, -Pi], [Pi, Pr]] [Qr; Qi] with three BF16
- * pieces per operand, FP32-level accuracy, two matrices per SM in a software pipeline);
+ * P Q is one tcgen05 MMA chain [Pr; Pi] [Qr | Qi] whose cross terms combine in the epilogue,
+ * with three BF16 pieces per operand, FP32-level accuracy, two matrices per SM in a software
+ * pipeline);
  * plan_host holds nn_batched_plan_size(count)
  * int32. The caller copies the plan to the device and may reuse it for every launch with the
  * same size list. Layout: [n_items, count, n_tc, class_first[23], order[count],
