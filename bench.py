@@ -235,6 +235,18 @@ def make_dense_inputs(n, kappa, seed, device):
     return a.contiguous(), alpha
 
 
+def dense_config(args, n, world):
+    """The dense workload's config (shared by both arms of the bench)."""
+    return {"workload": f"dense SPD N={n}, kappa={args.kappa:g}, log-uniform spectrum, X0=2/(lmin+lmax) I, "
+                        f"depth {args.depth}, eps={args.tol:g}",
+            "n": n, "kappa": args.kappa, "depth": args.depth, "tol": args.tol, "dtype": args.dtype,
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "gemm_tiling": {0: "auto (2-SM MMA, cta_group::2, split last wave)", 1: "single-CTA tiles",
+                            2: "CTA pairs with TMA multicast", 3: "2-SM MMA (cta_group::2)",
+                            4: "2-SM MMA, last wave split into 256x128 halves"}[args.gemm_variant],
+            "l2": "inputs larger than L2: A fp64 512 MiB, BF16 operands 128 MiB each per GEMM"}
+
+
 def run_dense(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -397,14 +409,7 @@ def run_dense(args, rank, world, local_rank):
                   "f64": "f64", "f64_emu": "f64 (emulated: exact bf16 slices on tcgen05)",
                   "mixed_emu": "bf16 pieces, then f64 emulated with exact bf16 slices (tcgen05)"}[args.dtype],
         "data": "synthetic",
-        "config": {"workload": f"dense SPD N={n}, kappa={args.kappa:g}, log-uniform spectrum, X0=2/(lmin+lmax) I, "
-                               f"depth {args.depth}, eps={args.tol:g}",
-                   "n": n, "kappa": args.kappa, "depth": args.depth, "tol": args.tol, "dtype": args.dtype,
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "gemm_tiling": {0: "auto (2-SM MMA, cta_group::2, split last wave)", 1: "single-CTA tiles",
-                                   2: "CTA pairs with TMA multicast", 3: "2-SM MMA (cta_group::2)",
-                                   4: "2-SM MMA, last wave split into 256x128 halves"}[args.gemm_variant],
-                   "l2": "inputs larger than L2: A fp64 512 MiB, BF16 operands 128 MiB each per GEMM"},
+        "config": dense_config(args, n, world),
         "status_ok": ok, "nests": last["nests"], "residual": last["residual"], "pieces": last["pieces"],
         "gemms_per_step": last["gemms"], "hw_tflops_per_step": round(last["hw_flops"] / 1e12, 3),
         "gpu_launches": launches,
@@ -864,7 +869,7 @@ def run_reference(args):
             "value": round(value, 5), "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"dense SPD N={n}, kappa={args.kappa:g}, depth {args.depth}", "n": n},
+            "config": dense_config(args, n, args.gpus),
             "cpu_baseline": cpu,
             "e2e": {"value": round(value, 5), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
