@@ -102,10 +102,12 @@ template <typename S, bool AFFINE, bool DUAL = false>
 __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int np, float* __restrict__ f32,
                              PiecePtrs row, int n_row, PiecePtrs col, int n_col, double* __restrict__ sumsq,
                              double scale, double diag, PiecePtrs dual_row = PiecePtrs{},
-                             double* __restrict__ dual_sumsq = nullptr) {
+                             double* __restrict__ dual_sumsq = nullptr, int yb0 = 0) {
   __shared__ __nv_bfloat16 tile[3][SPLIT_R][SPLIT_C + 2];  // odd word pitch: conflict-free columns
   __shared__ float red[ROWS];
-  const int i0 = blockIdx.y * SPLIT_R, j0 = blockIdx.x * SPLIT_C;
+  // yb0: first block row (a launch may cover a panel of rows; partial sums keep global indices)
+  const int yb = int(blockIdx.y) + yb0;
+  const int i0 = yb * SPLIT_R, j0 = blockIdx.x * SPLIT_C;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int jj = j0 + 4 * tx;
   float ss = 0.f, ss_src = 0.f;
@@ -175,7 +177,7 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
     if (tx == 0 && ty == 0) {
       float t = 0.f;
       for (int w = 0; w < ROWS; ++w) t += red[w];
-      sumsq[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = double(t);
+      sumsq[int64_t(yb) * gridDim.x + blockIdx.x] = double(t);
     }
   }
   if (DUAL) {
@@ -188,7 +190,7 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
     if (tx == 0 && ty == 0) {
       float t = 0.f;
       for (int w = 0; w < ROWS; ++w) t += red[w];
-      dual_sumsq[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = double(t);
+      dual_sumsq[int64_t(yb) * gridDim.x + blockIdx.x] = double(t);
     }
   }
   if (n_col > 0) {
@@ -388,16 +390,23 @@ __global__ void fill_diag_kernel(const double* __restrict__ A, int64_t lda, int 
 
 }  // namespace
 
+// Rows [row0, row1) of the padded matrix (row1 < 0: to np); both multiples of the block height.
+static bool split_rows(int np, int& row0, int& row1) {
+  if (row1 < 0) row1 = np;
+  return row0 >= 0 && row0 < row1 && row1 <= np && row0 % SPLIT_R == 0 && row1 % SPLIT_R == 0;
+}
+
 int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
                  __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
-                 double* sumsq_partial) {
+                 double* sumsq_partial, int row0, int row1) {
   if (np % SPLIT_C != 0 || n > np || n_row < 0 || n_row > 3 || n_col < 0 || n_col > 3) return NN_ERR_ARG;
+  if (!split_rows(np, row0, row1)) return NN_ERR_ARG;
   PiecePtrs r{}, c{};
   for (int q = 0; q < n_row; ++q) r.p[q] = row_pieces[q];
   for (int q = 0; q < n_col; ++q) c.p[q] = col_pieces[q];
-  dim3 grid(np / SPLIT_C, np / SPLIT_R), block(32, ROWS);
+  dim3 grid(np / SPLIT_C, (row1 - row0) / SPLIT_R), block(32, ROWS);
   split_kernel<double, false><<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial, 1.0,
-                                                      0.0);
+                                                      0.0, PiecePtrs{}, nullptr, row0 / SPLIT_R);
   NN_CUDA_TRY(cudaGetLastError());
   return NN_OK;
 }
@@ -430,10 +439,11 @@ static int split_affine(cudaStream_t st, const double* src, int64_t lds, int n, 
 int split_matrix_dual(cudaStream_t st, const double* src, int64_t lds, int n, int np,
                       __nv_bfloat16* const* src_row_pieces, double* src_sumsq_partial, float* f32,
                       __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
-                      double* sumsq_partial, double scale, double diag) {
+                      double* sumsq_partial, double scale, double diag, int row0, int row1) {
   if (np % SPLIT_C != 0 || n > np || n_row < 0 || n_row > 3 || n_col < 0 || n_col > 3 || sumsq_partial == nullptr ||
       src_sumsq_partial == nullptr)
     return NN_ERR_ARG;
+  if (!split_rows(np, row0, row1)) return NN_ERR_ARG;
   PiecePtrs r{}, c{}, d{};
   for (int q = 0; q < n_row; ++q) r.p[q] = row_pieces[q];
   for (int q = 0; q < n_col; ++q) c.p[q] = col_pieces[q];
@@ -441,9 +451,9 @@ int split_matrix_dual(cudaStream_t st, const double* src, int64_t lds, int n, in
     if (src_row_pieces[q] == nullptr) return NN_ERR_ARG;
     d.p[q] = src_row_pieces[q];
   }
-  dim3 grid(np / SPLIT_C, np / SPLIT_R), block(32, ROWS);
+  dim3 grid(np / SPLIT_C, (row1 - row0) / SPLIT_R), block(32, ROWS);
   split_kernel<double, true, true><<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial,
-                                                           scale, diag, d, src_sumsq_partial);
+                                                           scale, diag, d, src_sumsq_partial, row0 / SPLIT_R);
   NN_CUDA_TRY(cudaGetLastError());
   return NN_OK;
 }

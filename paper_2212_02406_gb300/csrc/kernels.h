@@ -100,9 +100,11 @@ bool tc_supported();
 // Splits an n x n FP64 matrix (leading dim lds) into an Np-padded FP32 copy and BF16
 // pieces (row-major and/or transposed). Any output may be null. Padding is zero.
 // sumsq_partial (nullable) receives one sum of squares per 32 x 32 block (split_blocks(np) entries).
+// row0, row1: only the padded rows [row0, row1) (multiples of 32; row1 < 0: to Np), e.g. a panel
+// of A whose host copy has arrived; the partial sums keep their global positions.
 int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
                  __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
-                 double* sumsq_partial);
+                 double* sumsq_partial, int row0 = 0, int row1 = -1);
 // The same for scale * src + diag * I (FP64 arithmetic): element-wise products with a scalar
 // X_0 (R_0 = I - a A; at depth 1, X_1 = 2 a I - a^2 A).
 int split_matrix_affine(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
@@ -113,7 +115,7 @@ int split_matrix_affine(cudaStream_t st, const double* src, int64_t lds, int n, 
 int split_matrix_dual(cudaStream_t st, const double* src, int64_t lds, int n, int np,
                       __nv_bfloat16* const* src_row_pieces, double* src_sumsq_partial, float* f32,
                       __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
-                      double* sumsq_partial, double scale, double diag);
+                      double* sumsq_partial, double scale, double diag, int row0 = 0, int row1 = -1);
 // BF16 pieces of an FP32 matrix (the same pieces the GEMM epilogue writes for it).
 int split_matrix_f32(cudaStream_t st, const float* src, int64_t lds, int n, int np, __nv_bfloat16* const* row_pieces,
                      int n_row, __nv_bfloat16* const* col_pieces, int n_col);
@@ -137,6 +139,6 @@ int check_opts(const nn_opts* o, int64_t n);
 struct HostOut;  // speculative copy of the likely-final iterate to host memory (nn_dense.cu)
 int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int64_t ldx0, const nn_opts* opts,
                   double* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_size, cudaStream_t st,
-                  HostOut* ho = nullptr);
+                  HostOut* ho = nullptr, bool a_presplit = false);
 
 }  // namespace nn

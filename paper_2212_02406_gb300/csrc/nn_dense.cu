@@ -750,6 +750,19 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
 
 }  // namespace
 
+// A's BF16 pieces with their per-block sums of squares, for the padded rows [row0, row1) (row1 < 0:
+// to Np); with X_0 = alpha I the same pass also writes R_0 = I - alpha A at the starting level.
+int split_a_panels(cudaStream_t st, const double* A, int64_t lda, int n, const MixedWs& w, const nn_opts& o, int row0,
+                   int row1) {
+  if (o.x0_scalar > 0) {
+    const int hp = level_upd_pieces(initial_level(o));
+    const bool rows = max_depth(o) >= 2;
+    return split_matrix_dual(st, A, lda, n, w.np, w.a_row, w.split_partial, rows ? w.r32 : nullptr, w.r_row,
+                             rows ? hp : 0, w.r_col, hp, w.split_partial2, -o.x0_scalar, 1.0, row0, row1);
+  }
+  return split_matrix(st, A, lda, n, w.np, nullptr, w.a_row, 3, nullptr, 0, w.split_partial, row0, row1);
+}
+
 int check_opts(const nn_opts* o, int64_t n) {
   if (o == nullptr) return NN_ERR_ARG;
   if (o->depth < 1 || o->depth > 16) return NN_ERR_ARG;
@@ -767,9 +780,11 @@ int check_opts(const nn_opts* o, int64_t n) {
   return NN_OK;
 }
 
+// a_presplit (mixed dtypes): the caller already wrote A's pieces (and, with x0_scalar, R_0) into
+// the workspace with split_a_panels, panel by panel as A arrived.
 int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int64_t ldx0, const nn_opts* opts,
                   double* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_size, cudaStream_t st,
-                  HostOut* ho) {
+                  HostOut* ho, bool a_presplit) {
   const nn_opts& o = *opts;
   Carver c(workspace, ws_size);
   Common cm;
@@ -818,14 +833,7 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     const int sb = split_blocks(w.np);
     // with X_0 = alpha I the same pass over A also writes R_0 = I - alpha A for the first residual
     const bool r0_pre = o.x0_scalar > 0;
-    if (r0_pre) {
-      const int hp = level_upd_pieces(initial_level(o));
-      const bool rows = max_depth(o) >= 2;
-      NN_TRY(split_matrix_dual(st, A, lda, ni, w.np, w.a_row, w.split_partial, rows ? w.r32 : nullptr, w.r_row,
-                               rows ? hp : 0, w.r_col, hp, w.split_partial2, -o.x0_scalar, 1.0));
-    } else {
-      NN_TRY(split_matrix(st, A, lda, ni, w.np, nullptr, w.a_row, 3, nullptr, 0, w.split_partial));
-    }
+    if (!a_presplit) NN_TRY(split_a_panels(st, A, lda, ni, w, o, 0, -1));
     NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0, cm.scal + 2));
     const X0Source x0src{X0, ldx0};
     if (o.x0_scalar <= 0) NN_TRY(load_x0(st, ni, w, cm, x0src));  // a scalar X_0 needs no pieces
@@ -980,11 +988,54 @@ int invert_host_impl(const double* A_host, int64_t n, const double* X0_host, int
   double* pc_vec = c.take<double>(2 * size_t(n));
   if (!c.ok) return NN_ERR_OOM_BUDGET;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  NN_CUDA_TRY(cudaMemcpyAsync(dA, A_host, e * sizeof(double), cudaMemcpyHostToDevice, st));
   // a scalar preconditioner on the mixed chain: X_0 = pc_scalar I is never materialised
   nn_opts oh = *opts;
   const bool mixed = opts->dtype == NN_MIXED_BF16 || opts->dtype == NN_MIXED_EMU;
   if (X0_host == nullptr && pc_kind == NN_PC_SCALAR && mixed && pc_scalar > 0) oh.x0_scalar = pc_scalar;
+  // Mixed chain, large N: A travels in row panels on a copy stream, and each panel is split into
+  // its BF16 pieces (and R_0) as soon as it has arrived, so the split overlaps the copy.
+  bool presplit = false;
+  if (mixed && n >= 2048 && tc_supported()) {
+    Carver cw(workspace, inner);
+    Common cmw;
+    carve_common(cw, n, oh.dtype, cmw);
+    MixedWs ww;
+    carve_mixed(cw, n, ww);  // the same carving as invert_device's
+    if (!cw.ok) return NN_ERR_OOM_BUDGET;
+    constexpr int kPanels = 8;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t start = nullptr, ev[kPanels] = {};
+    bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&start, cudaEventDisableTiming) == cudaSuccess;
+    // the copies start after the work already queued on the caller's stream
+    ok = ok && cudaEventRecord(start, st) == cudaSuccess && cudaStreamWaitEvent(cs, start, 0) == cudaSuccess;
+    const int rb = ((ww.np / kPanels + 31) / 32) * 32;
+    int p = 0;
+    for (int r0 = 0; ok && r0 < ww.np && p < kPanels; r0 += rb, ++p) {
+      const int r1 = (p == kPanels - 1) ? ww.np : std::min(r0 + rb, ww.np);
+      const int64_t h0 = std::min<int64_t>(r0, n), h1 = std::min<int64_t>(r1, n);
+      ok = cudaEventCreateWithFlags(&ev[p], cudaEventDisableTiming) == cudaSuccess;
+      if (ok && h1 > h0)
+        ok = cudaMemcpyAsync(dA + h0 * n, A_host + h0 * n, size_t(h1 - h0) * size_t(n) * sizeof(double),
+                             cudaMemcpyHostToDevice, cs) == cudaSuccess;
+      ok = ok && cudaEventRecord(ev[p], cs) == cudaSuccess && cudaStreamWaitEvent(st, ev[p], 0) == cudaSuccess;
+      ok = ok && split_a_panels(st, dA, n, int(n), ww, oh, r0, r1) == NN_OK;
+      res->launches += 1;
+      if (r1 == ww.np) break;
+    }
+    // (destroying a stream or event with work pending releases it once that work is done)
+    for (auto& x : ev)
+      if (x) cudaEventDestroy(x);
+    if (start) cudaEventDestroy(start);
+    if (cs) cudaStreamDestroy(cs);
+    if (!ok) {
+      (void)cudaGetLastError();
+      return NN_ERR_CUDA;
+    }
+    presplit = true;
+  } else {
+    NN_CUDA_TRY(cudaMemcpyAsync(dA, A_host, e * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
   if (X0_host != nullptr) {
     NN_CUDA_TRY(cudaMemcpyAsync(dX0, X0_host, e * sizeof(double), cudaMemcpyHostToDevice, st));
   } else if (!(mixed && oh.x0_scalar > 0 && pc_kind == NN_PC_SCALAR)) {
@@ -1006,7 +1057,7 @@ int invert_host_impl(const double* A_host, int64_t n, const double* X0_host, int
       return NN_ERR_CUDA;
     }
   }
-  int s = invert_device(dA, n, n, dX0, n, &oh, dX, n, res, workspace, inner, st, spec ? &ho : nullptr);
+  int s = invert_device(dA, n, n, dX0, n, &oh, dX, n, res, workspace, inner, st, spec ? &ho : nullptr, presplit);
   int rc = s;
   if (!(s == NN_ERR_CUDA || s == NN_ERR_ARG || s == NN_ERR_UNSUPPORTED || s == NN_ERR_OOM_BUDGET)) {
     if (!ho.valid && cudaMemcpyAsync(X_host, dX, e * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)

@@ -266,6 +266,35 @@ def test_host_pc_variant_and_early_copy_equal_device(nn, tol, kappa):
         assert np.array_equal(x1, xh)
 
 
+@pytest.mark.parametrize("n", [2048, 2100])
+def test_host_panel_split_equals_device(nn, n):
+    # From N = 2048 the host-buffer calls copy A in row panels on a copy stream and split each
+    # panel as soon as it has arrived (the last panel includes the padding rows); the results
+    # must equal the device calls bit for bit, with the scalar-X_0 hint and with an explicit X_0.
+    import torch
+
+    a, q, lam = synth.spd_spectrum(n, 1e2, seed=n)
+    alpha = 2.0 / (lam[0] + lam[-1])
+    x0 = dense.precond_scalar(n, alpha)
+    ws = nn.workspace(n, "mixed_bf16", host=True)
+    st1, res1, x1 = _run(nn, a, x0, 2, 1e-6, 40, "mixed_bf16", x0_scalar=alpha)
+    xh = np.full_like(a, np.nan)
+    st2, res2 = nn.nn_invert_host_pc(np.ascontiguousarray(a), "scalar", alpha, nn.make_opts(2, 1e-6, 40, "mixed_bf16"),
+                                     xh, ws)
+    torch.cuda.synchronize()
+    assert st1 == st2 == nn.NN_OK
+    assert res1["history"] == res2["history"]
+    assert np.array_equal(x1, xh)
+    st3, res3, x3 = _run(nn, a, x0, 2, 1e-6, 40, "mixed_bf16")
+    xh3 = np.full_like(a, np.nan)
+    st4, res4 = nn.nn_invert_host(np.ascontiguousarray(a), np.ascontiguousarray(x0),
+                                  nn.make_opts(2, 1e-6, 40, "mixed_bf16"), xh3, ws)
+    torch.cuda.synchronize()
+    assert st3 == st4 == nn.NN_OK
+    assert res3["history"] == res4["history"]
+    assert np.array_equal(x3, xh3)
+
+
 @pytest.mark.parametrize("n,pad", [(300, 0), (300, 1), (517, 3), (1024, 0)])
 @pytest.mark.parametrize("tol", [1e-5, 1e-7])
 def test_device_early_copy_strided_output(nn, n, pad, tol):
