@@ -61,7 +61,7 @@ def parse_args():
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--max-active", type=int, default=8)
-    ap.add_argument("--gemm-variant", type=int, default=0, choices=[0, 1, 2, 3, 4], help="0 auto, 1 single-CTA tiles, 2 CTA pairs with multicast, 3 2-SM MMA, 4 2-SM MMA with split last wave")
+    ap.add_argument("--gemm-variant", type=int, default=0, choices=[0, 1, 3, 4], help="0 auto, 1 single-CTA tiles, 3 2-SM MMA, 4 2-SM MMA with split last wave")
     ap.add_argument("--spmv-variant", type=int, default=0, choices=[0, 1], help="0 auto (bulk-copy ring), 1 staged loads")
     ap.add_argument("--batched-simt", action="store_true",
                     help="batched workload: CUDA-core items for every size (ignore tensor-core entries of the table)")
@@ -242,7 +242,7 @@ def dense_config(args, n, world):
             "n": n, "kappa": args.kappa, "depth": args.depth, "tol": args.tol, "dtype": args.dtype,
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             "gemm_tiling": {0: "auto (2-SM MMA, cta_group::2, split last wave)", 1: "single-CTA tiles",
-                            2: "CTA pairs with TMA multicast", 3: "2-SM MMA (cta_group::2)",
+                            3: "2-SM MMA (cta_group::2)",
                             4: "2-SM MMA, last wave split into 256x128 halves"}[args.gemm_variant],
             "l2": "inputs larger than L2: A fp64 512 MiB, BF16 operands 128 MiB each per GEMM"}
 
@@ -338,8 +338,7 @@ def run_dense(args, rank, world, local_rank):
     elif tc_launches > 0 and tc_ms > 0:
         achieved = tc_flops / (tc_ms / 1e3) / 1e12
         peak, label, burst = bf16_peak(peaks, peak_src, clocks)
-        kernel = {1: "nn::tc::gemm_tc_kernel", 2: "nn::tc::gemm_tc_pair_kernel"}.get(args.gemm_variant,
-                                                                                 "nn::tc::gemm_tc_2sm_kernel")
+        kernel = "nn::tc::gemm_tc_kernel" if args.gemm_variant == 1 else "nn::tc::gemm_tc_2sm_kernel"
         # ncu DRAM bytes per launch (mean over one step) of the profiled default configuration
         traffic = None
         if (args.gemm_variant in (0, 4) and n == 8192 and args.kappa == 1e2 and args.depth == 2

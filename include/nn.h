@@ -131,12 +131,12 @@ typedef struct nn_result {
 /* Tensor-core GEMM tiling for the NN_MIXED_BF16 chain (a process-wide tuning knob; the
  * element-wise outputs of every variant are bitwise identical, only the per-CTA grouping of the
  * residual's sum of squares differs): 0 = automatic (variant 4 when the padded size is a
- * multiple of 256, else 1), 1 = single-CTA 128 x 256 tiles, 2 = CTA pairs in clusters of two
- * sharing each B^T tile through TMA multicast, 3 = CTA pairs issuing one 256 x 256 MMA over
- * both SMs' shared memory and TMEM (tcgen05 cta_group::2), 4 = variant 3 with a last wave
- * that is at most half full run as 256 x 128 halves. Variants 2-4 need a padded size that is a
- * multiple of 256; calls that cannot use the chosen one return NN_ERR_UNSUPPORTED.
- * Returns NN_ERR_ARG for other values. Not thread-safe against concurrent inversions. */
+ * multiple of 256, else 1), 1 = single-CTA 128 x 256 tiles, 3 = CTA pairs issuing one
+ * 256 x 256 MMA over both SMs' shared memory and TMEM (tcgen05 cta_group::2), 4 = variant 3
+ * with a last wave that is at most half full run as 256 x 128 halves. Variants 3 and 4 need a
+ * padded size that is a multiple of 256; calls that cannot use the chosen one return
+ * NN_ERR_UNSUPPORTED. Returns NN_ERR_ARG for other values (2 included). Not thread-safe
+ * against concurrent inversions. */
 int nn_set_gemm_variant(int variant);
 
 /* Bytes of device workspace nn_invert / nn_residual need for an N x N problem of `dtype`

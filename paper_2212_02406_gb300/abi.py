@@ -196,8 +196,8 @@ def workspace(n: int, dtype="f64", host=False, device=None):
 # ---- entry points (same names as the C ABI) -------------------------------------------
 
 def nn_set_gemm_variant(variant: int) -> int:
-    """0 automatic, 1 single-CTA tiles, 2 CTA pairs with multicast, 3 2-SM MMA, 4 2-SM MMA with the last
-    wave split into halves (tensor-core GEMM tiling)."""
+    """0 automatic, 1 single-CTA tiles, 3 2-SM MMA, 4 2-SM MMA with the last wave split into halves
+    (tensor-core GEMM tiling)."""
     return int(lib().nn_set_gemm_variant(int(variant)))
 
 

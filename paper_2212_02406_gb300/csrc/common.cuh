@@ -132,17 +132,6 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* desc, in
       : "memory");
 }
 
-// Same load, delivered to the same shared-memory offset (and completing tx bytes on the same
-// mbarrier offset) in every CTA of the cluster whose bit is set in cta_mask.
-__device__ __forceinline__ void tma_load_2d_multicast(void* smem_dst, const void* desc, int x, int y, uint64_t* bar,
-                                                      uint16_t cta_mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
-      "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(smem_dst)),
-      "l"(reinterpret_cast<uint64_t>(desc)), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(cta_mask)
-      : "memory");
-}
-
 // L2 policy that marks lines as first to evict (for data streamed once).
 __device__ __forceinline__ uint64_t l2_evict_first_policy() {
   uint64_t pol;
@@ -260,16 +249,6 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uin
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
-}
-
-// Arrive once on the mbarrier at bar's offset in every CTA of cta_mask when this thread's
-// tcgen05 operations so far have completed.
-__device__ __forceinline__ void tc_commit_multicast(uint64_t* bar, uint16_t cta_mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(cta_mask)
-      : "memory");
 }
 
 // Warp-wide load of 32 lanes x 32 consecutive 32-bit columns (lane i of the warp receives

@@ -11,10 +11,8 @@
 //               piece stores (row-major and transposed), and sum(C^2) partials.
 // The two accumulators let the epilogue of tile i overlap the main loop of tile i+1.
 //
-// Three tilings of the same schedule (bitwise identical element-wise results):
+// Two tilings of the same schedule (bitwise identical element-wise results):
 //   gemm_tc_kernel       one CTA per 128 x 256 tile, as above (any padded size, multiple of 128);
-//   gemm_tc_pair_kernel  clusters of two CTAs on vertically adjacent tiles sharing each B^T
-//                        tile through TMA multicast (halves the L2 -> SM traffic for B);
 //   gemm_tc_2sm_kernel   clusters of two CTAs computing one 256 x 256 tile with
 //                        tcgen05.mma.cta_group::2: each SM stages 32 KB per K step instead of
 //                        48 KB for the same tensor work, which lifts the per-SM shared-memory
@@ -262,14 +260,8 @@ __device__ __forceinline__ void epilogue_chunk(const Params& p, const uint32_t (
   }
 }
 
-// PAIR = false: one CTA per 128 x 256 tile. PAIR = true: CTAs run in clusters of two on
-// vertically adjacent 128 x 256 tiles that share the same 256-row B^T panel; each CTA loads its
-// own A tile and one 128-row half of the B^T tile with TMA multicast into both CTAs, so every
-// B byte crosses L2 once per pair. Each CTA's MMA thread then releases a stage on both CTAs'
-// empty barriers (multicast commit), because the stage's B half in a CTA was written by the
-// peer too.
-template <bool PAIR>
-__device__ __forceinline__ void gemm_tc_body(const Params& p) {
+// One CTA per 128 x 256 tile.
+__global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ Params p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
@@ -286,15 +278,14 @@ __device__ __forceinline__ void gemm_tc_body(const Params& p) {
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
 
-  const int rank = PAIR ? int(cluster_ctarank()) : 0;
-  const int unit = PAIR ? int(blockIdx.x >> 1) : int(blockIdx.x);
-  const int units = PAIR ? int(gridDim.x >> 1) : int(gridDim.x);
-  const int unit_rows = PAIR ? p.tiles_m / 2 : p.tiles_m;  // tile rows per scheduling unit row
+  const int unit = int(blockIdx.x);
+  const int units = int(gridDim.x);
+  const int unit_rows = p.tiles_m;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], PAIR ? 2 : 1);
+      mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
@@ -312,12 +303,7 @@ __device__ __forceinline__ void gemm_tc_body(const Params& p) {
   }
   if (warp == 1) tmem_alloc(tmem_slot, TMEM_COLS);
   tc_fence_before();
-  // PAIR: the peer's multicast loads and commits target this CTA's barriers, so both CTAs
-  // must have initialised them before either starts.
-  if (PAIR)
-    cluster_sync_all();
-  else
-    __syncthreads();
+  __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
@@ -331,23 +317,16 @@ __device__ __forceinline__ void gemm_tc_body(const Params& p) {
       uint32_t phase = 0;
       for (int t = unit; t < num_tiles && !*abort_flag; t += units) {
         int tm, tn;
-        tile_coords(t, unit_rows, p.tiles_n, PAIR ? GROUP_M / 2 : GROUP_M, tm, tn);
-        if (PAIR) tm = 2 * tm + rank;
+        tile_coords(t, unit_rows, p.tiles_n, GROUP_M, tm, tn);
         for (int it = 0; it < total_k; ++it) {
           const int seg = it / kblocks;
           const int kb = it - seg * kblocks;
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.err)) break;
           uint8_t* sa = tiles + stage * STAGE_BYTES;
           uint8_t* sb = sa + A_TILE;
-          // PAIR: this CTA's A tile, plus its own 128-row half of B^T arriving in both CTAs;
-          // the other half arrives from the peer. Either way 48 KB land per stage.
           mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
           tma_load_2d(sa, &p.map_a[seg], kb * BK, tm * BM, &full[stage]);
-          if (PAIR)
-            tma_load_2d_multicast(sb + rank * (B_TILE / 2), &p.map_b[seg], kb * BK, tn * BN + rank * (BN / 2),
-                                  &full[stage], uint16_t(0x3));
-          else
-            tma_load_2d(sb, &p.map_b[seg], kb * BK, tn * BN, &full[stage]);
+          tma_load_2d(sb, &p.map_b[seg], kb * BK, tn * BN, &full[stage]);
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -382,10 +361,7 @@ __device__ __forceinline__ void gemm_tc_body(const Params& p) {
             tc_mma_bf16(d_tmem, adesc + uint64_t(2 * kk), bdesc + uint64_t(2 * kk), IDESC,
                         (it > 0 || kk > 0) ? 1u : 0u);
           }
-          if (PAIR)
-            tc_commit_multicast(&empty[stage], uint16_t(0x3));
-          else
-            tc_commit(&empty[stage]);
+          tc_commit(&empty[stage]);
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -412,8 +388,7 @@ __device__ __forceinline__ void gemm_tc_body(const Params& p) {
       if (!mbar_wait(&acc_full[acc], acc_phase, abort_flag, p.err)) break;
       tc_fence_after();
       int tm, tn;
-      tile_coords(t, unit_rows, p.tiles_n, PAIR ? GROUP_M / 2 : GROUP_M, tm, tn);
-      if (PAIR) tm = 2 * tm + rank;
+      tile_coords(t, unit_rows, p.tiles_n, GROUP_M, tm, tn);
       const int gr = tm * BM + row_in_tile;
       for (int c = 0; c < BN / 32; ++c) {
         const int gc0 = tn * BN + c * 32;
@@ -436,22 +411,9 @@ __device__ __forceinline__ void gemm_tc_body(const Params& p) {
   }
 
   tc_fence_before();
-  // PAIR: the peer's last multicast commits land on this CTA's barriers; both CTAs leave
-  // together once every MMA of both has completed (each MMA thread drained its commits above).
-  if (PAIR)
-    cluster_sync_all();
-  else
-    __syncthreads();
+  __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem_base, TMEM_COLS);
-}
-
-__global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_constant__ Params p) {
-  gemm_tc_body<false>(p);
-}
-
-__global__ void __launch_bounds__(THREADS, 1) gemm_tc_pair_kernel(const __grid_constant__ Params p) {
-  gemm_tc_body<true>(p);
 }
 
 
@@ -658,9 +620,8 @@ namespace {
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 int g_sms = 0;
-int g_pair_clusters = 0;  // co-resident clusters of the multicast-pair kernel (0: unavailable)
 int g_2sm_clusters = 0;   // co-resident clusters of the 2-SM MMA kernel (0: unavailable)
-int g_variant = 0;  // 0 auto (4 where possible, else 1), 1 single-CTA, 2 pairs + multicast, 3 2-SM MMA, 4 3 + split tail
+int g_variant = 0;  // 0 auto (4 where possible, else 1), 1 single-CTA, 3 2-SM MMA, 4 3 + split tail
 bool g_tc_ok = false;
 std::once_flag g_once;
 
@@ -717,7 +678,6 @@ void init_once() {
     return;
   }
   g_tc_ok = true;
-  g_pair_clusters = max_clusters(tc::gemm_tc_pair_kernel, tc::SMEM_BYTES);
   g_2sm_clusters = max_clusters(tc::gemm_tc_2sm_kernel, tc::P2_SMEM_BYTES);
   (void)cudaGetLastError();
 }
@@ -740,7 +700,7 @@ bool tc_supported() {
   return g_tc_ok;
 }
 
-void gemm_tc_set_variant(int v) { g_variant = (v >= 0 && v <= 4) ? v : 0; }
+void gemm_tc_set_variant(int v) { g_variant = (v == 1 || v == 3 || v == 4) ? v : 0; }
 
 int gemm_tc_max_grid() {
   std::call_once(g_once, init_once);
@@ -812,15 +772,14 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
   const bool even = a.np % (2 * tc::BM) == 0;
   int variant = g_variant;
   if (variant == 0) variant = (even && g_2sm_clusters > 0) ? 4 : 1;
-  if ((variant == 2 && !(even && g_pair_clusters > 0)) || (variant >= 3 && !(even && g_2sm_clusters > 0)))
-    return NN_ERR_UNSUPPORTED;
+  if (variant >= 3 && !(even && g_2sm_clusters > 0)) return NN_ERR_UNSUPPORTED;
   int grid = 0;
-  if (variant >= 2) {
+  if (variant >= 3) {
     // B^T maps load 128-row halves (one per CTA of the pair)
     for (int s = 0; s < a.nseg; ++s)
       if (!encode_bf16_2d(&p.map_b[s], a.b_seg[s], a.np, tc::BN / 2)) return NN_ERR_CUDA;
     const int units = (p.tiles_m / 2) * p.tiles_n;
-    const int avail = variant == 2 ? g_pair_clusters : g_2sm_clusters;
+    const int avail = g_2sm_clusters;
     const int clusters = units < avail ? units : avail;
     grid = 2 * clusters;
     // 2-SM kernel: a last wave at most half full runs its tiles as 256 x 128 halves
@@ -833,13 +792,8 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
     }
     cudaLaunchAttribute attr[1];
     if (a.ev_before) NN_CUDA_TRY(cudaEventRecord(a.ev_before, st));
-    if (variant == 2) {
-      cudaLaunchConfig_t cfg = cluster_config(grid, tc::SMEM_BYTES, st, attr);
-      NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc::gemm_tc_pair_kernel, p));
-    } else {
-      cudaLaunchConfig_t cfg = cluster_config(grid, tc::P2_SMEM_BYTES, st, attr);
-      NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc::gemm_tc_2sm_kernel, p));
-    }
+    cudaLaunchConfig_t cfg = cluster_config(grid, tc::P2_SMEM_BYTES, st, attr);
+    NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc::gemm_tc_2sm_kernel, p));
   } else {
     const int tiles = p.tiles_m * p.tiles_n;
     grid = tiles < g_sms ? tiles : g_sms;

@@ -79,8 +79,8 @@ struct TcGemmArgs {
 int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used);
 int gemm_tc_max_grid();
 // 0: automatic (4 when Np is a multiple of 256, else single-CTA tiles), 1: single-CTA
-// tiles, 2: CTA pairs with multicast, 3: 2-SM MMA, 4: 2-SM MMA with a split last wave (2-4:
-// NN_ERR_UNSUPPORTED where they do not apply).
+// tiles, 3: 2-SM MMA, 4: 2-SM MMA with a split last wave (3, 4: NN_ERR_UNSUPPORTED where they
+// do not apply).
 void gemm_tc_set_variant(int v);
 
 // ---- FP64 GEMM emulated with exact BF16 slices on the tensor cores (ozaki.cu) -------------

@@ -913,7 +913,7 @@ using namespace nn;
 extern "C" {
 
 int nn_set_gemm_variant(int variant) {
-  if (variant < 0 || variant > 4) return NN_ERR_ARG;
+  if (variant != 0 && variant != 1 && variant != 3 && variant != 4) return NN_ERR_ARG;
   gemm_tc_set_variant(variant);
   return NN_OK;
 }
