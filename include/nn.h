@@ -358,17 +358,19 @@ int nn_server_destroy(nn_server* s);
 
 /* ---- residual without any allocation ---------------------------------------------------
  * The paper has no counterpart: this is a deployment variant of nn_residual for callers that
- * cannot allocate device memory (inside a CUDA graph capture, in services that forbid
- * allocation after start-up, or when another framework owns and budgets all device memory and
- * hands out only the operands). It computes s = ||I - A X||_F / N in FP64 from device A and X
+ * cannot allocate device memory: real-time services that forbid allocation after start-up, and
+ * plug-ins whose host framework owns and budgets all device memory and hands them only the
+ * operands. It computes s = ||I - A X||_F / N in FP64 from device A and X
  * (row-major, leading dimensions lda, ldx >= n) into *rms_frob (host), using the same kernels
  * as nn_residual, with its scratch in a fixed 16 MiB array that the library reserves in device
  * memory on every GPU that loads it, until the process exits.
  * Limits: n <= NN_RESIDUAL_NOALLOC_MAX_N, larger n returns NN_ERR_TOO_LARGE before any device
  * work. The array is shared by all calls on a device: calls whose work overlaps on the GPU race
  * on it; each call overwrites all the scratch it reads, so nothing carries over between calls.
- * The first call on each device resolves the array's address (cudaGetSymbolAddress); make it
- * before any stream capture on that device. Synchronises `stream` before returning. */
+ * The first call on each device resolves the array's address (cudaGetSymbolAddress) and keeps
+ * it for that device's context (a call after cudaDeviceReset resolves it again); make the first
+ * call before any stream capture on that device. Calls no allocating routine. Synchronises
+ * `stream` before returning. */
 #define NN_RESIDUAL_NOALLOC_MAX_N 1440
 int nn_residual_noalloc(const double* A, int64_t lda, const double* X, int64_t ldx, int64_t n,
                         double* rms_frob, void* stream);

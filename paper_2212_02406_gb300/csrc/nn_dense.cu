@@ -1023,6 +1023,13 @@ int invert_host_impl(const double* A_host, int64_t n, const double* X0_host, int
       res->launches += 1;
       if (r1 == ww.np) break;
     }
+    // On failure, queued copies and splits may still read the caller's A and write the
+    // workspace: wait for them (statuses ignored) so that nothing references caller memory after
+    // the error returns.
+    if (!ok) {
+      if (cs) (void)cudaStreamSynchronize(cs);
+      (void)cudaStreamSynchronize(st);
+    }
     // (destroying a stream or event with work pending releases it once that work is done)
     for (auto& x : ev)
       if (x) cudaEventDestroy(x);

@@ -1,12 +1,12 @@
 // nn_residual_noalloc: the FP64 residual s = ||I - A X||_F / N without any device allocation.
 //
-// Some callers cannot allocate device memory: code that runs inside a CUDA graph being
-// captured, where an allocation would break the capture; real-time or embedded services
-// that forbid allocation after start-up; and hosts whose device memory is owned and
-// budgeted by another framework that hands out only the operands. This entry point serves
-// them. Its scratch (the N x N residual matrix, the per-block partial sums and the result
-// scalar) lives in one file-scope __device__ array of fixed size, so the caller passes
-// only the inputs A and X and receives s on the host.
+// Some callers cannot allocate device memory: real-time or embedded services that forbid any
+// allocation after start-up (an allocation can block or fail at an arbitrary moment), and
+// plug-ins whose host framework owns and budgets all device memory and hands them only the
+// operands, with no allocator and no workspace to draw on. This entry point serves them. Its
+// scratch (the N x N residual matrix, the per-block partial sums and the result scalar) lives
+// in one file-scope __device__ array of fixed size, so the caller passes only the inputs A
+// and X and receives s on the host.
 //
 // Limits and sharing:
 // * N <= NN_RESIDUAL_NOALLOC_MAX_N (1440): the array holds 16 MiB, and every GPU that loads
@@ -17,8 +17,12 @@
 //   overwrites all the scratch it reads (R, every partial, the scalar), so no state carries
 //   over from the previous call and nothing needs clearing.
 // * The first call on a device resolves the array's device address with
-//   cudaGetSymbolAddress (host code cannot use the symbol itself as a pointer). Make that
-//   first call before any stream capture on the device.
+//   cudaGetSymbolAddress (in host code the symbol names a host-side stand-in, not device
+//   memory) and keeps it for the device's context; a call after cudaDeviceReset, which ends
+//   that context, resolves it again. Make the first call on each device before any stream
+//   capture on that device.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -34,18 +38,52 @@ static __device__ __align__(256) unsigned char g_residual_scratch[kNoallocScratc
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kMaxDevices] = {};  // context the address belongs to
 
-// Device address of g_residual_scratch on the current device (resolved once per device).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique id of the current device's context (0 if the driver cannot tell): a device reset
+// ends the context, and the id of the next one differs, so a cached address is re-resolved.
+unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+    (void)cudaGetLastError();
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur == nullptr || get_id == nullptr || get_cur(&ctx) != CUDA_SUCCESS || ctx == nullptr ||
+      get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of g_residual_scratch on the current device: resolved at the first call on
+// the device (the set-up step), again only when the device's context has changed.
 int noalloc_scratch(void** out) {
   int dev = 0;
   NN_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return NN_ERR_UNSUPPORTED;
+  // (0 when this thread has no current context yet: the set-up below makes it current)
+  const unsigned long long ctx = current_ctx_id();
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (g_noalloc_ptr[dev] == nullptr) {
+  if (g_noalloc_ptr[dev] == nullptr || ctx == 0 || g_noalloc_ctx[dev] != ctx) {
     void* p = nullptr;
     NN_CUDA_TRY(cudaGetSymbolAddress(&p, g_residual_scratch));
     if (p == nullptr) return NN_ERR_CUDA;
     g_noalloc_ptr[dev] = p;
+    g_noalloc_ctx[dev] = current_ctx_id();
   }
   *out = g_noalloc_ptr[dev];
   return NN_OK;
