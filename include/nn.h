@@ -218,6 +218,18 @@ int nn_solve_csr_sched(const int32_t* row_ptr, const int32_t* col, const void* v
                        double tol, void* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_bytes,
                        void* stream);
 
+/* nn_solve: the sparse chain with the argument order of the library's solve interface
+ * (A, B, depth, tol, options, X, result, stream): the problem statement A X = B solved by the
+ * explicit NN form of Corollary 1 (Eq. (NNexplicit)) and Algorithm 2. A is the CSR triple
+ * (row_ptr, col, val) of size n with nnz nonzeros; B and X as in nn_solve_csr. From opts it
+ * reads dtype (NN_F64, NN_F64_DF or NN_F32), max_nests (the number of factors) and, when
+ * schedule_len > 0, depth_schedule (a depth per factor, as nn_solve_csr_sched; `depth` is then
+ * unused); its other fields are ignored. Same workspace (nn_csr_workspace_bytes), result and
+ * errors as nn_solve_csr; a null opts or a bad schedule returns NN_ERR_ARG. */
+int nn_solve(const int32_t* row_ptr, const int32_t* col, const void* val, int64_t n, int64_t nnz, const void* B,
+             int64_t ldb, int64_t nrhs, int depth, double tol, const nn_opts* opts, void* X, int64_t ldx,
+             nn_result* res, void* workspace, size_t ws_bytes, void* stream);
+
 /* Sparse-product kernel for one right-hand side (a process-wide tuning knob; both variants
  * sum each row's terms in the same order, so results are bitwise identical): 0 = automatic
  * (a persistent kernel that streams (val, col, row_ptr) through a ring of shared-memory stages
@@ -299,6 +311,15 @@ int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* 
                           const int32_t* plan, uint32_t classes, int depth, int nests, double damping, void* X,
                           float* residual, int32_t* status, void* workspace, size_t ws_bytes,
                           void* stream);
+
+/* nn_invert_batched: nn_invert_batched_c64 with the argument order of the library's batched
+ * interface (batch A, depth, nests, X, residuals, stream; Corollary 4's mMIMO use, each matrix
+ * run as Algorithm 1): A (complex64 batch: data, offsets, sizes, count), depth, nests, damping
+ * of the Jacobi start, the device plan and its class mask, then X, residual, status, workspace
+ * and stream. Same semantics, workspace and errors as nn_invert_batched_c64. */
+int nn_invert_batched(const void* A, const int64_t* offsets, const int32_t* sizes, int64_t count, int depth, int nests,
+                      double damping, const int32_t* plan, uint32_t classes, void* X, float* residual,
+                      int32_t* status, void* workspace, size_t ws_bytes, void* stream);
 
 /* ---- serving: continuous batching of inversions and solves -----------------------------
  * A request inverts one dense N x N matrix A (host FP64, row-major) with the NN loop of

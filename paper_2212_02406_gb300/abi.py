@@ -111,6 +111,10 @@ _SIGNATURES = {
     "nn_batched_workspace_bytes": (c_size_t, [c_int64]),
     "nn_invert_batched_c64": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, ctypes.c_uint32, c_int, c_int,
                                       c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "nn_invert_batched": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int, c_double, c_void_p,
+                                  ctypes.c_uint32, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "nn_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_int64, c_int64, c_int, c_double,
+                         POINTER(NNOpts), c_void_p, c_int64, POINTER(NNResult), c_void_p, c_size_t, c_void_p]),
     "nn_solve_csr": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int, c_void_p, c_int64, c_int64, c_int,
                              c_int, c_double, c_void_p, c_int64, POINTER(NNResult), c_void_p, c_size_t, c_void_p]),
 }
@@ -396,6 +400,21 @@ def nn_solve_csr_sched(row_ptr, col, val, B, depths, tol, X, workspace, stream=N
     return st, res.as_dict()
 
 
+def nn_solve(row_ptr, col, val, B, depth, tol, opts, X, workspace, stream=None):
+    """The sparse chain with the solve interface's argument order: opts (make_opts) supplies the
+    dtype ("f64", "f64_df" or "f32"), max_nests (factors) and an optional per-factor depth
+    schedule. Tensors as nn_solve_csr. Returns (status, result)."""
+    d, n, nrhs, ldb, ldx = _csr_args(row_ptr, col, val, B, X, opts.dtype == NN_F64_DF)
+    if opts.dtype != d:
+        raise TypeError("opts.dtype does not match the value tensor")
+    pw, nw = _ws(workspace)
+    res = NNResult()
+    st = lib().nn_solve(c_void_p(row_ptr.data_ptr()), c_void_p(col.data_ptr()), c_void_p(val.data_ptr()), n,
+                        val.numel(), c_void_p(B.data_ptr()), ldb, nrhs, int(depth), float(tol), ctypes.byref(opts),
+                        c_void_p(X.data_ptr()), ldx, ctypes.byref(res), pw, nw, _stream_ptr(stream))
+    return st, res.as_dict()
+
+
 # ---- batched small complex inversions -------------------------------------------------------
 
 def nn_batched_plan(sizes, cfg_by_u=None):
@@ -450,6 +469,25 @@ def nn_invert_batched_c64(A, offsets, sizes, plan, depth, nests, damping, X, res
                                        c_void_p(X.data_ptr()),
                                        c_void_p(residual.data_ptr()), c_void_p(status.data_ptr()), pw, nw,
                                        _stream_ptr(stream))
+
+
+def nn_invert_batched(A, offsets, sizes, depth, nests, damping, plan, X, residual, status, workspace,
+                      stream=None, classes=0xFFFFFFFF) -> int:
+    """nn_invert_batched_c64 with the batched interface's argument order (same tensors)."""
+    import torch
+
+    if A.dtype != torch.complex64 or X.dtype != torch.complex64 or not (A.is_cuda and X.is_cuda):
+        raise TypeError("A and X must be complex64 CUDA tensors")
+    checks = ((offsets, torch.int64), (sizes, torch.int32), (plan, torch.int32), (residual, torch.float32),
+              (status, torch.int32))
+    for t, dt in checks:
+        if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError(f"expected contiguous CUDA {dt}")
+    pw, nw = _ws(workspace)
+    return lib().nn_invert_batched(c_void_p(A.data_ptr()), c_void_p(offsets.data_ptr()), c_void_p(sizes.data_ptr()),
+                                   sizes.numel(), int(depth), int(nests), float(damping), c_void_p(plan.data_ptr()),
+                                   int(classes) & 0xFFFFFFFF, c_void_p(X.data_ptr()), c_void_p(residual.data_ptr()),
+                                   c_void_p(status.data_ptr()), pw, nw, _stream_ptr(stream))
 
 
 # ---- residual without allocation ---------------------------------------------------------

@@ -1402,4 +1402,11 @@ int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* 
   return NN_OK;
 }
 
+int nn_invert_batched(const void* A, const int64_t* offsets, const int32_t* sizes, int64_t count, int depth, int nests,
+                      double damping, const int32_t* plan, uint32_t classes, void* X, float* residual,
+                      int32_t* status, void* workspace, size_t ws_bytes, void* stream) {
+  return nn_invert_batched_c64(A, offsets, sizes, count, plan, classes, depth, nests, damping, X, residual, status,
+                               workspace, ws_bytes, stream);
+}
+
 }  // extern "C"

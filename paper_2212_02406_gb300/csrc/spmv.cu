@@ -891,4 +891,22 @@ int nn_solve_csr_sched(const int32_t* row_ptr, const int32_t* col, const void* v
                        ws_bytes, stream);
 }
 
+int nn_solve(const int32_t* row_ptr, const int32_t* col, const void* val, int64_t n, int64_t nnz, const void* B,
+             int64_t ldb, int64_t nrhs, int depth, double tol, const nn_opts* opts, void* X, int64_t ldx,
+             nn_result* res, void* workspace, size_t ws_bytes, void* stream) {
+  if (opts == nullptr || opts->schedule_len < 0 || opts->schedule_len > NN_MAX_HISTORY ||
+      (opts->schedule_len > 0 && opts->depth_schedule == nullptr)) {
+    if (res != nullptr) {
+      memset(res, 0, sizeof(*res));
+      res->status = NN_ERR_ARG;
+    }
+    return NN_ERR_ARG;
+  }
+  if (opts->schedule_len > 0)
+    return solve_csr_any(row_ptr, col, val, n, nnz, opts->dtype, B, ldb, nrhs, opts->depth_schedule,
+                         opts->schedule_len, tol, X, ldx, res, workspace, ws_bytes, stream);
+  return nn_solve_csr(row_ptr, col, val, n, nnz, opts->dtype, B, ldb, nrhs, depth, opts->max_nests, tol, X, ldx, res,
+                      workspace, ws_bytes, stream);
+}
+
 }  // extern "C"

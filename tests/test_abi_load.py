@@ -77,6 +77,27 @@ def test_argument_errors_are_status_codes(lib):
     assert lib.nn_init_precond(None, 4, 4, 0, 0.0, None, 4, None, 0, None) == abi.NN_ERR_ARG
 
 
+def test_solve_and_batched_interface_names(lib):
+    # The solve (A X = B, the problem statement; Algorithm 2) and batched (Corollary 4's mMIMO use)
+    # entry points in the interface's argument order: each is called through ctypes and answers a
+    # bad argument with NN_ERR_ARG before any device work.
+    res = abi.NNResult()
+    opts = abi.make_opts(depth=2, max_nests=3, dtype="f64")
+    assert lib.nn_solve(None, None, None, 16, 48, None, 16, 1, 2, 0.0, ctypes.byref(opts), None, 16,
+                        ctypes.byref(res), None, 0, None) == abi.NN_ERR_ARG
+    assert res.status == abi.NN_ERR_ARG
+    assert lib.nn_solve(None, None, None, 16, 48, None, 16, 1, 2, 0.0, None, None, 16, ctypes.byref(res), None, 0,
+                        None) == abi.NN_ERR_ARG
+    sched = abi.make_opts(depth=2, max_nests=3, dtype="f64", depth_schedule=[2, 0])  # depth 0 is invalid
+    assert lib.nn_solve(None, None, None, 16, 48, None, 16, 1, 2, 0.0, ctypes.byref(sched), None, 16,
+                        ctypes.byref(res), None, 0, None) == abi.NN_ERR_ARG
+    assert lib.nn_invert_batched(None, None, None, 4, 2, 3, 0.0, None, 1, None, None, None, None, 0,
+                                 None) == abi.NN_ERR_ARG
+    # the normal-equation solve of Corollary 3, too
+    assert lib.nn_solve_normal(None, 4, 4, 0, None, 4, 1, ctypes.byref(opts), None, 1, ctypes.byref(res), None, 0,
+                               None) == abi.NN_ERR_ARG
+
+
 def _header_int(name):
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         m = re.search(r"#define\s+" + name + r"\s+(\d+)", open(h).read())

@@ -173,3 +173,26 @@ def test_full_batch_16384(nn, cfg_tc):
     x, res, st = _run(nn, bt, 2, 3, 1.0 / 128.0, cfg_by_u=table)
     n_conv = _check(bt, x, res, st, 2, 3, 1.0 / 128.0)
     assert n_conv == bt.count
+
+
+def test_batched_interface_equals_c64_entry(nn):
+    # nn_invert_batched (batch, depth, nests, X, residuals, stream order) runs the same kernels
+    # as nn_invert_batched_c64: bitwise the same X, residuals and statuses (Corollary 4's use)
+    import torch
+
+    bt = synth.mimo_gram_batch(64, seed=21)
+    x, res, st = _run(nn, bt, 2, 3, 1.0 / 128.0)
+    A = torch.from_numpy(bt.data.astype(np.complex64)).cuda()
+    offs = torch.from_numpy(bt.offsets.astype(np.int64)).cuda()
+    sizes = torch.from_numpy(bt.sizes.astype(np.int32)).cuda()
+    plan_host = nn.nn_batched_plan(bt.sizes, None)
+    plan = torch.from_numpy(plan_host).cuda()
+    X = torch.empty_like(A)
+    r2 = torch.empty(bt.count, dtype=torch.float32, device="cuda")
+    s2 = torch.empty(bt.count, dtype=torch.int32, device="cuda")
+    ws = torch.empty(nn.nn_batched_workspace_bytes(bt.count), dtype=torch.uint8, device="cuda")
+    assert nn.nn_invert_batched(A, offs, sizes, 2, 3, 1.0 / 128.0, plan, X, r2, s2, ws,
+                                classes=nn.nn_batched_plan_classes(plan_host)) == nn.NN_OK
+    torch.cuda.synchronize()
+    assert np.array_equal(X.cpu().numpy(), x)
+    assert np.array_equal(r2.cpu().numpy(), res) and np.array_equal(s2.cpu().numpy(), st)

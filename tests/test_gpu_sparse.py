@@ -169,3 +169,41 @@ def test_schedule_matches_oracle(nn, dtype, depths):
     nnz_row = int(np.max(np.diff(m.row_ptr)))
     tol = max(8 * terms * U[dtype] * (nnz_row + 1), 1e-13 if dtype == "f64" else 0)
     assert np.linalg.norm(x - want) / np.linalg.norm(want) <= tol
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("sched", [None, [2, 2, 1]])
+def test_solve_interface_equals_csr_entry_and_oracle(nn, dtype, sched):
+    # nn_solve (A, B, depth, tol, opts, X, result, stream) runs the same chain as nn_solve_csr /
+    # nn_solve_csr_sched: bitwise the same X, and the oracle's factor product within the chain
+    # tolerance (problem statement; Corollary 1, Eq. (NNexplicit); Algorithm 2)
+    import torch
+
+    m = synth.laplacian_5pt(37, 31, shift=0.5)
+    b = synth.gaussian_rhs(m.n, 2, seed=5)
+    npd = NP[dtype]
+    rp = torch.from_numpy(m.row_ptr.astype(np.int32)).cuda()
+    col = torch.from_numpy(m.col.astype(np.int32)).cuda()
+    val = torch.from_numpy(m.val.astype(npd)).cuda()
+    B = torch.from_numpy(np.ascontiguousarray(b.T.astype(npd))).cuda()
+    X = torch.empty_like(B)
+    ws = nn.csr_workspace(m.n, m.nnz, B.shape[0], dtype)
+    opts = nn.make_opts(depth=2, max_nests=3, dtype=dtype, depth_schedule=sched)
+    st, res = nn.nn_solve(rp, col, val, B, 2, 0.0, opts, X, ws)
+    torch.cuda.synchronize()
+    assert st == nn.NN_OK
+    X2 = torch.empty_like(B)
+    if sched is None:
+        st2, res2 = nn.nn_solve_csr(rp, col, val, B, 2, 3, 0.0, X2, ws)
+        depths = [2, 2, 2]
+    else:
+        st2, res2 = nn.nn_solve_csr_sched(rp, col, val, B, sched, 0.0, X2, ws)
+        depths = sched
+    torch.cuda.synchronize()
+    assert st2 == nn.NN_OK and res["nests"] == res2["nests"] == len(depths)
+    assert torch.equal(X, X2)
+    want = sparse.nn_sparse_solve_sched(m.to_scipy(), b, depths)
+    err = np.linalg.norm(X.cpu().numpy().T - want) / np.linalg.norm(want)
+    terms = int(np.prod([d + 1 for d in depths])) - 1
+    nnz_row = int(np.max(np.diff(m.row_ptr)))
+    assert err <= max(8 * terms * U[dtype] * (nnz_row + 1), 1e-13), err
