@@ -105,7 +105,7 @@ typedef struct nn_opts {
                           NN_MIXED_BF16 / NN_MIXED_EMU then run the first nest's residual
                           R_0 = I - x0_scalar A and update X_1 = x0_scalar (I + T) element-wise
                           (no GEMM, no pieces of X_0); the other dtypes read X0 as usual.
-                          nn_result.flops still counts the method's 2 N^3 for both products. */
+                          nn_result.flops then leaves those two products out. */
 } nn_opts;
 
 /* nn_opts.flags: time every GEMM launch of the chain with CUDA events on the call's stream
@@ -119,7 +119,10 @@ typedef struct nn_result {
   double history[NN_MAX_HISTORY];  /* s_0 .. s_nests                                               */
   int pieces[NN_MAX_HISTORY];      /* BF16 pieces used for residual k (0 for FP64/FP32 paths)      */
   int gemms;                       /* GEMM launches issued                                         */
-  double flops;                    /* algorithmic FLOPs: 2 N^3 per GEMM (split passes not counted) */
+  double flops;                    /* algorithmic FLOPs: 2 N^3 per product of the method that ran as a
+                                      GEMM ((L+1) per nest + the final residual, less products run
+                                      element-wise); precision passes and re-measured residuals are
+                                      not counted                                                  */
   double hw_flops;                 /* tensor-core FLOPs issued, split passes included              */
   int launches;                    /* kernel launches issued by the call                           */
   int tc_launches;                 /* GEMM launches of the chain: tcgen05 for NN_MIXED_BF16,       */

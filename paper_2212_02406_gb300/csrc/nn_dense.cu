@@ -892,9 +892,12 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     }
     res->launches += 3;
   }
-  // Algorithmic work of the method: (L+1) GEMMs per nest plus the final residual.
+  // Algorithmic work of the method: (L+1) GEMMs per nest plus the final residual, less the
+  // products that ran element-wise (X_0 = alpha I on the mixed chains: the first nest's residual
+  // and update). Precision passes, re-measured residuals and rolled-back nests are not counted.
   double gemms = 1.0;
   for (int k = 0; k < res->nests; ++k) gemms += double(nest_depth(o, k) + 1);
+  if ((o.dtype == NN_MIXED_BF16 || o.dtype == NN_MIXED_EMU) && o.x0_scalar > 0) gemms -= res->nests >= 1 ? 2.0 : 1.0;
   res->flops = 2.0 * double(n) * double(n) * double(n) * gemms;
   NN_CUDA_TRY(cudaStreamSynchronize(st));
   int dev_err = 0;
