@@ -106,6 +106,13 @@ typedef struct nn_opts {
                           R_0 = I - x0_scalar A and update X_1 = x0_scalar (I + T) element-wise
                           (no GEMM, no pieces of X_0); the other dtypes read X0 as usual.
                           nn_result.flops then leaves those two products out. */
+  double fwd_tol;      /* > 0: forward-error target. X_k - A^-1 = -A^-1 R_k and ||A^-1||_2 <= ||A^-1||_F give
+                          ||X_k - A^-1||_F / ||A^-1||_F <= ||R_k||_F = N s_k, so the chain stops at the
+                          first k with s_k < fwd_tol / N (or < tol, when tol > 0 is smaller): the
+                          returned X is then within fwd_tol of the inverse, relatively, in the
+                          Frobenius norm. With NN_MIXED_EMU the BF16-piece nests run until the next
+                          residual is predicted to lie near their floor, then emulated FP64 nests
+                          whose products carry only the bits the target needs finish the job. 0: off */
 } nn_opts;
 
 /* nn_opts.flags: time every GEMM launch of the chain with CUDA events on the call's stream

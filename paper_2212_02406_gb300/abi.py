@@ -39,7 +39,8 @@ NN_MAX_HISTORY = 65
 class NNOpts(ctypes.Structure):
     _fields_ = [("depth", c_int), ("tol", c_double), ("max_nests", c_int), ("dtype", c_int),
                 ("refine_below", c_double), ("bulk_pieces", c_int), ("flags", c_int),
-                ("depth_schedule", POINTER(c_int32)), ("schedule_len", c_int), ("x0_scalar", c_double)]
+                ("depth_schedule", POINTER(c_int32)), ("schedule_len", c_int), ("x0_scalar", c_double),
+                ("fwd_tol", c_double)]
 
 
 class NNResult(ctypes.Structure):
@@ -171,13 +172,15 @@ NN_FLAG_TIME_KERNELS = 1
 
 
 def make_opts(depth=2, tol=1e-6, max_nests=64, dtype="f64", refine_below=0.0, bulk_pieces=1,
-              flags=0, depth_schedule=None, x0_scalar=0.0) -> NNOpts:
+              flags=0, depth_schedule=None, x0_scalar=0.0, fwd_tol=0.0) -> NNOpts:
     """depth_schedule: optional per-nest depths (the last one repeats), e.g. [2, 2, 1].
     x0_scalar > 0: the caller asserts X_0 = x0_scalar * I (the mixed dtypes then run the first
-    nest's residual and update element-wise)."""
+    nest's residual and update element-wise). fwd_tol > 0: stop once N s_k < fwd_tol, which bounds
+    the relative Frobenius error of X against the inverse."""
     d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
     o = NNOpts(int(depth), float(tol), int(max_nests), d, float(refine_below), int(bulk_pieces), int(flags))
     o.x0_scalar = float(x0_scalar)
+    o.fwd_tol = float(fwd_tol)
     if depth_schedule:
         arr = (c_int32 * len(depth_schedule))(*[int(x) for x in depth_schedule])
         o.depth_schedule = ctypes.cast(arr, POINTER(c_int32))

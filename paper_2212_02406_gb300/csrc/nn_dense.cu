@@ -240,12 +240,16 @@ struct LaunchTimer {
 // CUDA-core chains (FP64 / FP32).
 
 // The GEMM of a CUDA-core-style chain: C = mode(A B) with Σ C^2 partials (count in *nparts).
+// Role of a product in the nest, for arithmetics whose precision can follow it.
+enum ProductRole { ROLE_RESIDUAL = 0, ROLE_HORNER = 1, ROLE_UPDATE = 2 };
+
 template <typename T>
 struct SimtGemm {
   cudaStream_t st;
   int n;
   int operator()(const T* A, int64_t lda, const T* B, int64_t ldb, T* C, int64_t ldc, int mode, const T* D,
-                 int64_t ldd, double* partial, int* nparts, bool /*second_order*/ = false) const {
+                 int64_t ldd, double* partial, int* nparts, int /*role*/ = ROLE_RESIDUAL, double /*s_k*/ = 0,
+                 double /*need*/ = 0) const {
     if (nparts) *nparts = gemm_simt_partials<T>(n, n);
     return gemm_simt<T>(st, n, n, n, A, lda, B, ldb, C, ldc, mode, D, ldd, n, partial);
   }
@@ -259,13 +263,31 @@ struct EmuGemm {
   size_t ws_bytes;
   int* err;
   double* hw_flops;
-  // second_order: the Horner product R T_j, which enters the next residual multiplied by the
-  // residual again (about 2^-40 s_k^2 from 40-bit products), runs on the slice products of a
-  // 40-bit result instead of FP64's.
+  // adaptive: the products' precision follows the nest's needs (the continuation of
+  // NN_MIXED_EMU); otherwise every product is FP64-accurate but the Horner products.
+  bool adaptive = false;
+  // The Horner product R T_j enters the next residual multiplied by the residual again (about
+  // 2^-40 s_k^2 from 40-bit products), so it runs on the slice products of a 40-bit result
+  // instead of FP64's. With `adaptive`, `need` is the rms error the nest may add to the next
+  // residual (s_k the current one); dropping slice products past b bits perturbs
+  //   the Horner product by about 2^-b sqrt(N) s_k^2,
+  //   the update X T (T ~ R) by about 2^-b K s_k in the next residual, K = ||A|| ||X|| / N <= 1024,
+  // and 8 more bits cover the slices' fixed point relative to row / column maxima.
   int operator()(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int mode,
-                 const double* D, int64_t ldd, double* partial, int* nparts, bool second_order = false) const {
+                 const double* D, int64_t ldd, double* partial, int* nparts, int role = ROLE_RESIDUAL,
+                 double s_k = 0, double need = 0) const {
+    int bits = role == ROLE_HORNER ? 40 : 0;
+    if (adaptive && need > 0 && s_k > 0 && isfinite(s_k)) {
+      if (role == ROLE_HORNER) {
+        const double b = ceil(log2(16.0 * sqrt(double(n)) * s_k * s_k / need)) + 8.0;
+        bits = b < 16 ? 16 : (b > 40 ? 40 : int(b));
+      } else if (role == ROLE_UPDATE) {
+        const double b = ceil(log2(1024.0 * s_k / need)) + 8.0;
+        bits = b < 24 ? 24 : (b >= 54 ? 0 : int(b));
+      }
+    }
     return gemm_f64_emu(st, n, A, lda, B, ldb, C, ldc, mode, D, ldd, n, partial, nparts, ws, ws_bytes, err,
-                        hw_flops, second_order ? 40 : 0);
+                        hw_flops, bits);
   }
 };
 
@@ -303,15 +325,23 @@ int run_simt(cudaStream_t st, int n, const T* A, int64_t lda, T* const X[2], T* 
       res->status = verdict;
       break;
     }
+    // rms error this nest may add to the next residual: under tol / 16 for the final nest, and
+    // under s_{k+1} / 16 ~ s_k^(L+1) / 16 before it (the nests after correct what it adds)
+    const int lk = nest_depth(o, k);
+    const double need = o.tol > 0 ? fmax(o.tol, pow(s, double(lk + 1))) / 16.0 : 0.0;
     const T* t_cur = R;
-    for (int j = 1; j < nest_depth(o, k); ++j) {
+    for (int j = 1; j < lk; ++j) {
       T* t_nxt = Tb[j & 1];
-      NN_TRY(timed([&] { return gemm(R, n, t_cur, n, t_nxt, n, EPI_ADD, R, n, nullptr, nullptr, true); }));
+      NN_TRY(timed([&] {
+        return gemm(R, n, t_cur, n, t_nxt, n, EPI_ADD, R, n, nullptr, nullptr, ROLE_HORNER, s, need);
+      }));
       t_cur = t_nxt;
       res->gemms += 1;
       res->launches += 1;
     }
-    NN_TRY(timed([&] { return gemm(X[cur], n, t_cur, n, X[cur ^ 1], n, EPI_ADD, X[cur], n, nullptr, nullptr); }));
+    NN_TRY(timed([&] {
+      return gemm(X[cur], n, t_cur, n, X[cur ^ 1], n, EPI_ADD, X[cur], n, nullptr, nullptr, ROLE_UPDATE, s, need);
+    }));
     res->gemms += 1;
     res->launches += 1;
     cur ^= 1;
@@ -621,12 +651,13 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     // old level first and again at the new one.
     int next_level = level;
     bool likely_final = false;
+    double s_pred = -1.0;
     if (k >= 1 && res->history[k - 1] > 0) {
       const double ratio = s / res->history[k - 1];
       if (ratio > 0 && ratio < 1) {
         // s_k / s_{k-1} = rho^(m_{k-1} L_{k-1}) and s_{k+1} / s_k = rho^(m_k L_k), m_k = m_{k-1} (L_{k-1} + 1)
         const double lp = double(nest_depth(o, k - 1)), lk = double(nest_depth(o, k));
-        const double s_pred = s * pow(ratio, (lp + 1.0) * lk / lp);
+        s_pred = s * pow(ratio, (lp + 1.0) * lk / lp);
         if (level < 3) {
           while (next_level < 3 && s_pred < 8.0 * level_floor(next_level, c)) ++next_level;
           if (o.tol > 0 && s_pred < o.tol && next_level < 3) next_level = 3;
@@ -634,6 +665,12 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
         likely_final = o.tol > 0 && s_pred < 0.5 * o.tol && next_level >= 3;
       }
     }
+    // NN_MIXED_EMU with tol below the BF16 pieces' floor: once X_{k+1} is predicted to lie within
+    // 64 floors of it, the emulated FP64 nests take X_{k+1} over and measure its residual
+    // themselves (no piece residual first): one nest of order L+1 from there reaches tol.
+    const bool handover = o.dtype == NN_MIXED_EMU && o.tol > 0 && o.tol < 8.0 * level_floor(3, c) &&
+                          s_pred >= 0 && s_pred < 64.0 * level_floor(3, c) && k + 1 < o.max_nests;
+    if (handover) likely_final = false;
     // Horner: T_1 = R (its column pieces), T_{j+1} = R + R T_j. With a scalar X_0 the first
     // nest's last Horner product also leaves T in FP32 over R's FP32 copy (each element read as
     // the addend, then written), for the element-wise update below. R T_j is second order in
@@ -642,8 +679,9 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     // those levels serve; its output T keeps the update's pieces.
     const bool update0 = scalar_x0 && k == 0;
     const int hh = (level == 2 || level == 3) ? hp - 1 : hp;
-    // pieces of X_{k+1} that the next nest reads at its predicted level
-    const int wr = level_upd_pieces(next_level), wc = level_res_pieces(next_level);
+    // pieces of X_{k+1} that the next nest reads at its predicted level (none after a handover:
+    // the emulated nests read the FP32 master)
+    const int wr = handover ? 0 : level_upd_pieces(next_level), wc = handover ? 0 : level_res_pieces(next_level);
     // Before a write to x32[cur ^ 1]: a host side copy must finish reading it, and a copy of
     // it is stale from then on.
     auto before_x_write = [&]() -> int {
@@ -738,6 +776,12 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     cur ^= 1;
     level = next_level;
     copy_next = likely_final;
+    if (handover) {
+      xr[cur] = xc[cur] = 0;
+      res->nests = k + 1;
+      res->status = NN_ERR_NOT_CONVERGED;
+      break;
+    }
   }
   *final_idx = cur;
   if (ho != nullptr && ho->pending) ho->valid = ho->spec_buf == cur && ho->spec_nests == res->nests;
@@ -777,6 +821,7 @@ int check_opts(const nn_opts* o, int64_t n) {
   if (n < 1 || n > 32768) return NN_ERR_ARG;
   if (isnan(o->tol)) return NN_ERR_ARG;
   if (!(o->x0_scalar >= 0.0) || !isfinite(o->x0_scalar)) return NN_ERR_ARG;
+  if (!(o->fwd_tol >= 0.0) || !isfinite(o->fwd_tol)) return NN_ERR_ARG;
   return NN_OK;
 }
 
@@ -785,7 +830,12 @@ int check_opts(const nn_opts* o, int64_t n) {
 int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int64_t ldx0, const nn_opts* opts,
                   double* X, int64_t ldx, nn_result* res, void* workspace, size_t ws_size, cudaStream_t st,
                   HostOut* ho, bool a_presplit) {
-  const nn_opts& o = *opts;
+  // the stop threshold with the forward-error target folded in: N s_k bounds the relative error
+  nn_opts o = *opts;
+  if (o.fwd_tol > 0) {
+    const double t = o.fwd_tol / double(n);
+    o.tol = (o.tol > 0 && o.tol < t) ? o.tol : t;
+  }
   Carver c(workspace, ws_size);
   Common cm;
   carve_common(c, n, o.dtype, cm);
@@ -871,8 +921,9 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
       nn_result r2;
       init_result(&r2);
       int fin2 = 0;
-      NN_TRY(run_simt<double>(st, ni, A, lda, w64.X, w64.R, w64.T, o2, cm, &r2, &fin2,
-                              EmuGemm{st, ni, ews, eb, cm.err, &res->hw_flops}));
+      EmuGemm eg{st, ni, ews, eb, cm.err, &res->hw_flops};
+      eg.adaptive = true;
+      NN_TRY(run_simt<double>(st, ni, A, lda, w64.X, w64.R, w64.T, o2, cm, &r2, &fin2, eg));
       const int k0 = res->nests;
       for (int k = 0; k <= r2.nests && k0 + k < NN_MAX_HISTORY; ++k) {
         res->history[k0 + k] = r2.history[k];
@@ -1056,7 +1107,7 @@ int invert_host_impl(const double* A_host, int64_t n, const double* X0_host, int
   ho.host = X_host;
   ho.dev = dX;
   ho.n = int(n);
-  const bool spec = opts->dtype == NN_MIXED_BF16 && opts->tol > 0;
+  const bool spec = opts->dtype == NN_MIXED_BF16 && (opts->tol > 0 || opts->fwd_tol > 0);
   if (spec) {
     NN_CUDA_TRY(cudaStreamCreateWithFlags(&ho.side, cudaStreamNonBlocking));
     if (cudaEventCreateWithFlags(&ho.ready, cudaEventDisableTiming) != cudaSuccess ||

@@ -72,6 +72,10 @@ def test_argument_errors_are_status_codes(lib):
         opts = abi.make_opts(depth=2, dtype="mixed_bf16", x0_scalar=bad)
         assert lib.nn_invert(None, 16, 16, None, 16, ctypes.byref(opts), None, 16, ctypes.byref(res), None, 0,
                              None) == abi.NN_ERR_ARG
+    for bad in (-1e-6, float("nan"), float("inf")):  # the forward-error target must be >= 0 and finite
+        opts = abi.make_opts(depth=2, dtype="mixed_emu", fwd_tol=bad)
+        assert lib.nn_invert(None, 16, 16, None, 16, ctypes.byref(opts), None, 16, ctypes.byref(res), None, 0,
+                             None) == abi.NN_ERR_ARG
     out = ctypes.c_double()
     assert lib.nn_residual(None, 4, None, 4, 4, abi.NN_F64, ctypes.byref(out), None, 0, None) == abi.NN_ERR_ARG
     assert lib.nn_init_precond(None, 4, 4, 0, 0.0, None, 4, None, 0, None) == abi.NN_ERR_ARG

@@ -141,3 +141,33 @@ def test_mixed_emu_equals_mixed_when_tol_is_reachable(nn):
     assert out["mixed_bf16"][0] == out["mixed_emu"][0] == nn.NN_OK
     assert out["mixed_bf16"][1]["nests"] == out["mixed_emu"][1]["nests"]
     assert np.array_equal(out["mixed_bf16"][2], out["mixed_emu"][2])
+
+
+@pytest.mark.parametrize("n,kappa", [(1024, 1e2), (2048, 1e2), (1024, 1e4), (2048, 1e4)])
+def test_refined_result_within_1e6_of_oracle(nn, n, kappa):
+    # The refined mode (NN_MIXED_EMU with a forward-error target): BF16-piece nests, then
+    # emulated FP64 nests, stopping at N s_k < fwd_tol, which bounds ||X - A^-1||_F / ||A^-1||_F
+    # (X - A^-1 = -A^-1 R and ||A^-1||_2 <= ||A^-1||_F). The FP64 oracle runs the same NN
+    # (Algorithm 1, depth 2, same X_0) to its own floor; the returned X must lie within 1e-6 of
+    # it, relatively, in the Frobenius norm (Section II's error measure against the solution).
+    import torch
+
+    a, q, lam = synth.spd_spectrum(n, kappa, seed=n + int(kappa))
+    alpha = 2.0 / (lam[0] + lam[-1])
+    x0 = dense.precond_scalar(n, alpha)
+    ora = dense.nn_invert(a, x0, 2, tol=1e-13, max_nests=40)
+    A, X0 = _dev(a), _dev(x0)
+    X = torch.empty_like(A)
+    ws = nn.workspace(n, "mixed_emu")
+    opts = nn.make_opts(2, 0.0, 40, "mixed_emu", x0_scalar=alpha, fwd_tol=1e-6)
+    st, res = nn.nn_invert(A, X0, opts, X, ws)
+    torch.cuda.synchronize()
+    assert st == nn.NN_OK, res
+    assert n * res["residual"] < 1e-6
+    assert res["pieces"][0] >= 1 and res["pieces"][res["nests"]] == 0  # both stages ran
+    x = X.cpu().numpy()
+    err = np.linalg.norm(x - ora.x) / np.linalg.norm(ora.x)
+    assert err <= 1e-6, err
+    # the residual the call reports is the FP64 residual of the returned X
+    s64 = dense.rms_frob(dense.residual(a, x))
+    assert abs(res["residual"] - s64) <= 1e-3 * s64 + 64 * U64 * math.sqrt(n), (res["residual"], s64)
