@@ -48,7 +48,10 @@ constexpr int THREADS = 192;
 constexpr int TMEM_COLS = 512;                 // two 128x256 FP32 accumulators
 constexpr int CTRL_BYTES = 256;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + CTRL_BYTES + 1024;
-constexpr int GROUP_M = 16;                    // tile raster: bands of 16 row tiles
+#ifndef NN_TC_GROUP_M
+#define NN_TC_GROUP_M 16
+#endif
+constexpr int GROUP_M = NN_TC_GROUP_M;         // tile raster: bands of 16 row tiles
 
 // Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A BF16 (bits 7-9 = 1),
 // B BF16 (bits 10-12 = 1), both K-major (bits 15, 16 = 0), N>>3 at bit 17, M>>4 at bit 24.
@@ -425,7 +428,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
 // CTAs' loads complete on the even CTA's full barrier; its commits release both CTAs'
 // stages and accumulators; both CTAs' epilogue warps free an accumulator on the even CTA's
 // barrier (count 8).
-constexpr int P2_STAGES = 6;
+#ifndef NN_TC_P2_STAGES
+#define NN_TC_P2_STAGES 6
+#endif
+constexpr int P2_STAGES = NN_TC_P2_STAGES;
 constexpr int P2_STAGE_BYTES = A_TILE + B_TILE / 2;  // 32 KB
 constexpr int P2_SMEM_BYTES = P2_STAGES * P2_STAGE_BYTES + CTRL_BYTES + 1024;
 constexpr uint32_t IDESC_P2_HALF =

@@ -355,25 +355,29 @@ int run_simt(cudaStream_t st, int n, const T* A, int64_t lda, T* const X[2], T* 
 // ---------------------------------------------------------------------------------------
 // Tensor-core mixed chain.
 
-// Operand-piece pairs for a split product with p pieces per operand, smallest terms first:
-// p = 1: hh;  p = 2: lh, hl, hh;  p = 3: (2,0) (1,1) (0,2) (1,0) (0,1) (0,0).
-int seg_pairs(int p, int (*pairs)[2]) {
-  static const int p1[1][2] = {{0, 0}};
-  static const int p2[3][2] = {{1, 0}, {0, 1}, {0, 0}};
-  static const int p3[6][2] = {{2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}, {0, 0}};
-  const int(*src)[2] = p == 1 ? p1 : (p == 2 ? p2 : p3);
-  const int cnt = p == 1 ? 1 : (p == 2 ? 3 : 6);
-  for (int i = 0; i < cnt; ++i) {
-    pairs[i][0] = src[i][0];
-    pairs[i][1] = src[i][1];
-  }
+// Operand-piece pairs (i, j) of a split product with pa pieces of the left operand and pb of
+// the right: every pair with i < pa, j < pb and i + j < max(pa, pb) (the terms of the product's
+// precision), smallest terms first: (3, 3): (2,0) (1,1) (0,2) (1,0) (0,1) (0,0); (2, 2): (1,0)
+// (0,1) (0,0); (2, 1): (1,0) (0,0); (1, 1): (0,0).
+int seg_pairs(int pa, int pb, int (*pairs)[2]) {
+  const int top = pa > pb ? pa : pb;
+  int cnt = 0;
+  for (int d = top - 1; d >= 0; --d)
+    for (int i = d; i >= 0; --i) {
+      const int j = d - i;
+      if (i < pa && j < pb && cnt < kTcMaxSeg) {
+        pairs[cnt][0] = i;
+        pairs[cnt][1] = j;
+        ++cnt;
+      }
+    }
   return cnt;
 }
 
-int tc_product(cudaStream_t st, TcGemmArgs& g, int pieces, __nv_bfloat16* const* a_pieces,
+int tc_product(cudaStream_t st, TcGemmArgs& g, int pa, int pb, __nv_bfloat16* const* a_pieces,
                __nv_bfloat16* const* b_pieces, const Common& cm, nn_result* res, int* grid, LaunchTimer* tm) {
-  int pairs[6][2];
-  g.nseg = seg_pairs(pieces, pairs);
+  int pairs[kTcMaxSeg][2];
+  g.nseg = seg_pairs(pa, pb, pairs);
   for (int s = 0; s < g.nseg; ++s) {
     g.a_seg[s] = a_pieces[pairs[s][0]];
     g.b_seg[s] = b_pieces[pairs[s][1]];
@@ -408,12 +412,38 @@ int tc_product(cudaStream_t st, TcGemmArgs& g, int pieces, __nv_bfloat16* const*
 // level must keep 2^-(8p+1) K * 64 <= 1 (64 covers ||T||_2 <= L+1 and the Frobenius-to-spectral
 // gap of the spectra this path is built for).
 // Levels never go down. The residual accepted for the stop test is always level >= 3.
+//
+// The update X_k T reads X_k with the level's pieces and T with its own count: T ~ R_k, and
+// A X_k ~ I, so T's rounding reaches the next residual unamplified (about 2^-(8p+1) s_k),
+// while X_k's is amplified by K; one piece of T (one pass less at levels 2 and 3) stays under
+// the next residual wherever s_k is small enough for those levels.
+// Compile-time tuning of the schedule (defaults as described above).
+#ifndef NN_POLICY_RISE
+#define NN_POLICY_RISE 8.0
+#endif
+#ifndef NN_POLICY_T_MID
+#define NN_POLICY_T_MID 2
+#endif
+#ifndef NN_POLICY_FINAL_LEVEL
+#define NN_POLICY_FINAL_LEVEL 3
+#endif
+#ifndef NN_POLICY_STABLE
+#define NN_POLICY_STABLE 64.0
+#endif
+constexpr double kRise = NN_POLICY_RISE;        // level L < 3 rises once s_k < kRise e(L)
+constexpr int kFinalLevel = NN_POLICY_FINAL_LEVEL;  // lowest level accepted for a stop
+constexpr double kStable = NN_POLICY_STABLE;    // 2^-(8p+1) K kStable <= 1 for the X pieces p
 static int level_res_pieces(int L) { return L <= 1 ? 1 : (L == 2 ? 2 : 3); }
-static int level_upd_pieces(int L) { return L <= 1 ? 1 : (L <= 3 ? 2 : 3); }
+// pieces of X_k in the update
+static int level_x_pieces(int L) { return L <= 1 ? 1 : (L <= 3 ? 2 : 3); }
+// pieces of T (and of R as T_1) that the update reads
+static int level_t_pieces(int L) { return L <= 1 ? 1 : (L <= 3 ? NN_POLICY_T_MID : 3); }
+// pieces of both operands of the Horner products R T_j (second order in the residual)
+static int level_h_pieces(int L) { return (L == 2 || L == 3) ? 1 : level_x_pieces(L); }
 static int stable_level(double kest) {
   for (int L = 1; L <= 3; ++L) {
-    const int p = level_upd_pieces(L);
-    if (ldexp(kest, -(8 * p + 1)) * 64.0 <= 1.0) return L;
+    const int p = level_x_pieces(L);
+    if (ldexp(kest, -(8 * p + 1)) * kStable <= 1.0) return L;
   }
   return 4;
 }
@@ -479,7 +509,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
   const double sqrt_n = sqrt(double(n));
   const double n15 = double(n) * sqrt(double(n));
   int level = initial_level(o);
-  const int r0_pre_hp = level_upd_pieces(level);
+  const int r0_pre_hp = level_t_pieces(level);
   int cur = 0;
   int k = 0;
   bool copy_next = false;  // the next residual's iterate is predicted to be returned
@@ -500,7 +530,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
   timer.on = (o.flags & NN_FLAG_TIME_KERNELS) != 0;
 
   auto residual = [&](int L, double* s_out) -> int {
-    const int hp = level_upd_pieces(L);
+    const int hp = level_t_pieces(L);
     TcGemmArgs g;
     g.np = np;
     g.n_id = n;
@@ -526,7 +556,8 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     }
     NN_TRY(ensure_pieces(cur, 0, level_res_pieces(L)));
     int grid = 0;
-    NN_TRY(tc_product(st, g, level_res_pieces(L), w.a_row, w.x_col[cur], cm, res, &grid, &timer));
+    NN_TRY(tc_product(st, g, level_res_pieces(L), level_res_pieces(L), w.a_row, w.x_col[cur], cm, res, &grid,
+                      &timer));
     NN_TRY(reduce_rms(st, cm.partial, grid, 1.0 / double(n), cm.scal));
     res->launches += 1;
     int dev_err = 0;
@@ -538,7 +569,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     return NN_OK;
   };
   auto residual0 = [&](int L, double* s_out) -> int {
-    const int hp = level_upd_pieces(L);
+    const int hp = level_t_pieces(L);
     const bool rows = max_depth(o) >= 2;
     if (r0_pre && hp == r0_pre_hp) {
       NN_TRY(reduce_rms(st, w.split_partial2, sb, 1.0 / double(n), cm.scal));
@@ -595,17 +626,17 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       if (isfinite(s)) {
         const int ls = stable_level(a_frob * x_frob / double(n));
         if (target < ls) target = ls;
-        while (target < 3 && s < 8.0 * level_floor(target, c)) ++target;
+        while (target < 3 && s < kRise * level_floor(target, c)) ++target;
         if (k >= 1 && s > 0.9 * res->history[k - 1] && s < 30.0 * level_floor(level, c) && level < 4)
           target = target > (level <= 2 ? 3 : 4) ? target : (level <= 2 ? 3 : 4);
         if (o.refine_below > 0 && s * sqrt_n < o.refine_below && target < 3) target = 3;
-        if (o.tol > 0 && s < o.tol && target < 3) target = 3;
+        if (o.tol > 0 && s < o.tol && target < kFinalLevel) target = kFinalLevel;
       }
       if (target != level) {
         // The residual epilogue writes R's pieces for the Horner/update GEMMs at the level's
-        // update count, so a change in either count needs a new residual.
+        // count of T pieces, so a change in either count needs a new residual.
         const bool remeasure = level_res_pieces(target) != level_res_pieces(level) ||
-                               level_upd_pieces(target) != level_upd_pieces(level);
+                               level_t_pieces(target) != level_t_pieces(level);
         level = target;
         if (remeasure) NN_TRY(measure(level, &s));
       }
@@ -635,15 +666,16 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
         res->history[k - 1] > 0.9 * res->history[k - 2] && s < 30.0 * level_floor(4, c))
       verdict = NN_ERR_NOT_CONVERGED;
     // NN_MIXED_EMU: a tolerance below the BF16-piece floors is reached by emulated FP64 nests;
-    // hand the iterate over once the chain is within reach of its own floor.
+    // hand the iterate over once the pieces can no longer bring s down (within 4 level-2 floors:
+    // level 3 only gains the tensor core's FP32 accumulation floor at twice the passes).
     if (verdict < 0 && o.dtype == NN_MIXED_EMU && o.tol > 0 && o.tol < 8.0 * level_floor(3, c) &&
-        s < 64.0 * level_floor(3, c))
+        s < 4.0 * level_floor(2, c))
       verdict = NN_ERR_NOT_CONVERGED;
     if (verdict >= 0) {
       res->status = verdict;
       break;
     }
-    const int hp = level_upd_pieces(level);
+    const int hp = level_x_pieces(level), ht = level_t_pieces(level), hh = level_h_pieces(level);
     x_frob_prev = x_frob;
     // Predict s_{k+1} from the observed order-(L+1) contraction,
     // log(s_{k+1}/s_k) ~ (L+1) log(s_k/s_{k-1}), and raise the level of the next residual now
@@ -659,17 +691,25 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
         const double lp = double(nest_depth(o, k - 1)), lk = double(nest_depth(o, k));
         s_pred = s * pow(ratio, (lp + 1.0) * lk / lp);
         if (level < 3) {
-          while (next_level < 3 && s_pred < 8.0 * level_floor(next_level, c)) ++next_level;
-          if (o.tol > 0 && s_pred < o.tol && next_level < 3) next_level = 3;
+          while (next_level < 3 && s_pred < kRise * level_floor(next_level, c)) ++next_level;
+          if (o.tol > 0 && s_pred < o.tol && next_level < kFinalLevel) next_level = kFinalLevel;
         }
-        likely_final = o.tol > 0 && s_pred < 0.5 * o.tol && next_level >= 3;
+        likely_final = o.tol > 0 && s_pred < 0.5 * o.tol && next_level >= kFinalLevel;
       }
     }
     // NN_MIXED_EMU with tol below the BF16 pieces' floor: once X_{k+1} is predicted to lie within
-    // 64 floors of it, the emulated FP64 nests take X_{k+1} over and measure its residual
-    // themselves (no piece residual first): one nest of order L+1 from there reaches tol.
+    // 4 level-2 floors, the emulated FP64 nests take X_{k+1} over and measure its residual
+    // themselves (no piece residual first). The prediction here is the cautious one: near the
+    // ends of a continuous spectrum s_k ~ rho^(m_k) m_k^(-1/2) (m_k the Neumann order + 1), so
+    // the geometric extrapolation above is multiplied by
+    // exp((ln(L_{k-1} + 1) (L_{k-1} + 1) L_k / L_{k-1} - ln(L_k + 1)) / 2) (3 at depth 2).
+    double s_slow = -1.0;
+    if (s_pred >= 0) {
+      const double lp = double(nest_depth(o, k - 1)), lk = double(nest_depth(o, k));
+      s_slow = s_pred * exp(0.5 * (log(lp + 1.0) * (lp + 1.0) * lk / lp - log(lk + 1.0)));
+    }
     const bool handover = o.dtype == NN_MIXED_EMU && o.tol > 0 && o.tol < 8.0 * level_floor(3, c) &&
-                          s_pred >= 0 && s_pred < 64.0 * level_floor(3, c) && k + 1 < o.max_nests;
+                          s_slow >= 0 && s_slow < 4.0 * level_floor(2, c) && k + 1 < o.max_nests;
     if (handover) likely_final = false;
     // Horner: T_1 = R (its column pieces), T_{j+1} = R + R T_j. With a scalar X_0 the first
     // nest's last Horner product also leaves T in FP32 over R's FP32 copy (each element read as
@@ -678,10 +718,9 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     // instead of three) perturbs the next residual by about 2^-9 s_k^2, far under the floors
     // those levels serve; its output T keeps the update's pieces.
     const bool update0 = scalar_x0 && k == 0;
-    const int hh = (level == 2 || level == 3) ? hp - 1 : hp;
     // pieces of X_{k+1} that the next nest reads at its predicted level (none after a handover:
     // the emulated nests read the FP32 master)
-    const int wr = handover ? 0 : level_upd_pieces(next_level), wc = handover ? 0 : level_res_pieces(next_level);
+    const int wr = handover ? 0 : level_x_pieces(next_level), wc = handover ? 0 : level_res_pieces(next_level);
     // Before a write to x32[cur ^ 1]: a host side copy must finish reading it, and a copy of
     // it is stale from then on.
     auto before_x_write = [&]() -> int {
@@ -699,7 +738,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       g.n_id = n;
       g.mode = EPI_ADD;
       g.add = w.r32;
-      g.n_col = hp;
+      g.n_col = ht;
       for (int i = 0; i < 3; ++i) g.col_pieces[i] = w.t_col[j & 1][i];
       int grid = 0;
       if (update0 && j == nest_depth(o, k) - 1) {
@@ -719,12 +758,12 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
         NN_TRY(before_x_write());
         xr[cur ^ 1] = wr;
         xc[cur ^ 1] = wc;
-        NN_TRY(tc_product(st, g, hh, w.r_row, t_cur, cm, res, &grid, &timer));
+        NN_TRY(tc_product(st, g, hh, hh, w.r_row, t_cur, cm, res, &grid, &timer));
         NN_TRY(reduce_rms(st, cm.partial, grid, 1.0, cm.scal + 1));
         res->launches += 1;
         break;
       }
-      NN_TRY(tc_product(st, g, hh, w.r_row, t_cur, cm, res, &grid, &timer));
+      NN_TRY(tc_product(st, g, hh, hh, w.r_row, t_cur, cm, res, &grid, &timer));
       t_cur = w.t_col[j & 1];
     }
     // Update: X_{k+1} = X_k + X_k T, with ||X_{k+1}||_F from the epilogue partials.
@@ -757,7 +796,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       }
       g.partial = cm.partial;
       int grid = 0;
-      NN_TRY(tc_product(st, g, hp, w.x_row[cur], t_cur, cm, res, &grid, &timer));
+      NN_TRY(tc_product(st, g, hp, ht, w.x_row[cur], t_cur, cm, res, &grid, &timer));
       NN_TRY(reduce_rms(st, cm.partial, grid, 1.0, cm.scal + 1));
       res->launches += 1;
     }
@@ -799,7 +838,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
 int split_a_panels(cudaStream_t st, const double* A, int64_t lda, int n, const MixedWs& w, const nn_opts& o, int row0,
                    int row1) {
   if (o.x0_scalar > 0) {
-    const int hp = level_upd_pieces(initial_level(o));
+    const int hp = level_t_pieces(initial_level(o));
     const bool rows = max_depth(o) >= 2;
     return split_matrix_dual(st, A, lda, n, w.np, w.a_row, w.split_partial, rows ? w.r32 : nullptr, w.r_row,
                              rows ? hp : 0, w.r_col, hp, w.split_partial2, -o.x0_scalar, 1.0, row0, row1);
