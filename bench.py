@@ -71,6 +71,10 @@ def parse_args():
     ap.add_argument("--no-scalar-x0", action="store_true",
                     help="dense workload: run the first nest's residual and update as GEMMs (no X_0 = alpha I hint)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-refined", action="store_true",
+                    help="dense workload: skip the refined line (forward error <= 1e-6 against the inverse)")
+    ap.add_argument("--no-baselines", action="store_true",
+                    help="dense workload: skip the plain FP32 / FP64 CUDA-core chains timed beside the mixed one")
     args = ap.parse_args()
     if args.n is None:
         args.n = 2048 if args.workload == "normal" else 8192
@@ -247,6 +251,79 @@ def dense_config(args, n, world):
             "l2": "inputs larger than L2: A fp64 512 MiB, BF16 operands 128 MiB each per GEMM"}
 
 
+def time_dense_call(abi, A, X0, opts, dtype, stream, steps, warmup=1):
+    """Device time of nn_invert (CUDA events on the call's stream, median of `steps` calls after
+    `warmup`); returns (ms, status, result, X)."""
+    import torch
+
+    n = A.shape[0]
+    ws = abi.workspace(n, dtype, device=A.device)
+    X = torch.empty_like(A)
+    for _ in range(warmup):
+        abi.nn_invert(A, X0, opts, X, ws, stream)
+    times = []
+    st, res = None, None
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, res = abi.nn_invert(A, X0, opts, X, ws, stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    del ws
+    return statistics.median(times), st, res, X
+
+
+def sampled_fp64_residual(A, X, rows=64, seed=123):
+    """FP64 rms of sampled rows of I - A X (device), scaled to ||I - A X||_F / N."""
+    import numpy as np
+    import torch
+
+    n = A.shape[0]
+    r = np.random.Generator(np.random.PCG64(seed))
+    idx = torch.from_numpy(np.sort(r.choice(n, size=min(rows, n), replace=False))).to(A.device)
+    rr = -(A[idx] @ X)
+    rr[torch.arange(len(idx), device=A.device), idx] += 1.0
+    return float(torch.linalg.norm(rr)) / math.sqrt(len(idx) * n)
+
+
+def dense_refined(args, abi, A, X0, alpha, stream):
+    """Time to a result within 1e-6 of the inverse (relative Frobenius error): NN_MIXED_EMU with
+    the forward-error target, BF16-piece nests then emulated FP64 nests; the call stops at
+    N s < 1e-6, which bounds ||X - A^-1||_F / ||A^-1||_F."""
+    n = A.shape[0]
+    opts = abi.make_opts(args.depth, 0.0, 40, "mixed_emu", x0_scalar=alpha, fwd_tol=1e-6)
+    ms, st, res, X = time_dense_call(abi, A, X0, opts, "mixed_emu", stream, steps=3)
+    return {"fwd_tol": 1e-6, "dtype": "mixed_emu", "time_to_result_ms": round(ms, 3), "status_ok": st == abi.NN_OK,
+            "nests": res["nests"], "pieces": res["pieces"], "residual": res["residual"],
+            "fwd_bound": n * res["residual"], "residual_fp64_sampled": sampled_fp64_residual(A, X),
+            "stop": "N s < fwd_tol (X - A^-1 = -A^-1 R and ||A^-1||_2 <= ||A^-1||_F)"}
+
+
+def dense_baselines(args, abi, n_main, A_main, X0_main, alpha_main, stream, dev):
+    """The plain CUDA-core chains (FP32, FP64) to the same tol, beside the mixed one: at the main
+    size for FP32, at N = 2048 for FP64, FP32 and the mixed chain (FP64 at N = 8192 takes ~17 s)."""
+    out = {}
+    o32 = abi.make_opts(args.depth, args.tol, 64, "f32")
+    ms, st, res, _ = time_dense_call(abi, A_main, X0_main, o32, "f32", stream, steps=1)
+    out[f"f32_n{n_main}"] = {"ms": round(ms, 2), "status_ok": st == abi.NN_OK, "nests": res["nests"],
+                             "residual": res["residual"]}
+    A2, alpha2 = make_dense_inputs(2048, args.kappa, args.seed + 1, dev)
+    X02 = torch_scalar_x0(A2, alpha2)
+    for dt, x0s in (("f64", 0.0), ("f32", 0.0), ("mixed_bf16", alpha2)):
+        o = abi.make_opts(args.depth, args.tol, 64, dt, x0_scalar=x0s)
+        ms, st, res, _ = time_dense_call(abi, A2, X02, o, dt, stream, steps=3)
+        out[f"{dt}_n2048"] = {"ms": round(ms, 3), "status_ok": st == abi.NN_OK, "nests": res["nests"],
+                              "residual": res["residual"]}
+    return out
+
+
+def torch_scalar_x0(A, alpha):
+    import torch
+
+    return torch.eye(A.shape[0], dtype=A.dtype, device=A.device) * alpha
+
+
 def run_dense(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -399,6 +476,13 @@ def run_dense(args, rank, world, local_rank):
         check = {"rows": len(rows), "s_fp64_sampled": float(np.sqrt(np.mean(np.sum(rr ** 2, axis=1)) / n))}
         del x_host
 
+    refined = None
+    baselines = None
+    if args.dtype == "mixed_bf16" and not args.no_refined:
+        refined = dense_refined(args, abi, A, X0, alpha, stream)
+    if args.dtype == "mixed_bf16" and not args.no_baselines:
+        baselines = dense_baselines(args, abi, n, A, X0, alpha, stream, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         a_host = A.cpu().numpy()
@@ -416,10 +500,11 @@ def run_dense(args, rank, world, local_rank):
                   "mixed_emu": "bf16 pieces, then f64 emulated with exact bf16 slices (tcgen05)"}[args.dtype],
         "data": "synthetic",
         "config": dense_config(args, n, world),
-        "status_ok": ok, "nests": last["nests"], "residual": last["residual"], "pieces": last["pieces"],
+        "status_ok": ok, "nests": last["nests"], "residual": last["residual"],
+        "residual_certified": last["residual_est"], "pieces": last["pieces"],
         "gemms_per_step": last["gemms"], "hw_tflops_per_step": round(last["hw_flops"] / 1e12, 3),
         "gpu_launches": launches,
-        "residual_check": check,
+        "residual_check": check, "refined": refined, "gpu_baselines": baselines,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
     }
     return line

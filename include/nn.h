@@ -136,6 +136,14 @@ typedef struct nn_result {
                                    /* CUDA-core for NN_F64 / NN_F32                                */
   double tc_ms;                    /* summed CUDA-event time of those launches (NN_FLAG_TIME_KERNELS) */
   double tc_flops;                 /* 2 Np^3 per BF16 product pass (mixed) or 2 N^3 per GEMM (F64/F32) */
+  double residual_est;             /* the residual the returned X has, as certified by the stop test:
+                                      equal to `residual` for FP64, FP32 and emulated residuals; for
+                                      BF16-piece residuals sqrt(residual^2 + e^2), e the error floor
+                                      of the residual that produced X (the pieces' rounding and the
+                                      tensor core's FP32 accumulation: the chain converges to the X
+                                      whose measured residual vanishes, so the measured value lies
+                                      under the truth by about e). A stop requires residual_est < tol;
+                                      a tol under the arithmetic's floor ends NN_ERR_NOT_CONVERGED */
 } nn_result;
 
 /* Tensor-core GEMM tiling for the NN_MIXED_BF16 chain (a process-wide tuning knob; the
@@ -374,7 +382,7 @@ typedef struct nn_completion {
   int64_t id;
   int status;
   int nests;
-  double residual;
+  double residual;      /* certified residual of the returned X (nn_result.residual_est)         */
   double t_submit, t_start, t_done;
   int launches;         /* kernels the request launched (X_0, the NN loop, the solve)          */
 } nn_completion;

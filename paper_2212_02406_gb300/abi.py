@@ -47,7 +47,8 @@ class NNResult(ctypes.Structure):
     _fields_ = [("status", c_int), ("nests", c_int), ("residual", c_double),
                 ("history", c_double * NN_MAX_HISTORY), ("pieces", c_int * NN_MAX_HISTORY),
                 ("gemms", c_int), ("flops", c_double), ("hw_flops", c_double), ("launches", c_int),
-                ("tc_launches", c_int), ("tc_ms", c_double), ("tc_flops", c_double)]
+                ("tc_launches", c_int), ("tc_ms", c_double), ("tc_flops", c_double),
+                ("residual_est", c_double)]
 
     def as_dict(self) -> dict:
         k = self.nests
@@ -55,7 +56,8 @@ class NNResult(ctypes.Structure):
                 "residual": self.residual, "history": [self.history[i] for i in range(k + 1)],
                 "pieces": [self.pieces[i] for i in range(k + 1)], "gemms": self.gemms,
                 "flops": self.flops, "hw_flops": self.hw_flops, "launches": self.launches,
-                "tc_launches": self.tc_launches, "tc_ms": self.tc_ms, "tc_flops": self.tc_flops}
+                "tc_launches": self.tc_launches, "tc_ms": self.tc_ms, "tc_flops": self.tc_flops,
+                "residual_est": self.residual_est}
 
 
 class NNServerOpts(ctypes.Structure):

@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
 // stages and accumulators; both CTAs' epilogue warps free an accumulator on the even CTA's
 // barrier (count 8).
 #ifndef NN_TC_P2_STAGES
-#define NN_TC_P2_STAGES 6
+#define NN_TC_P2_STAGES 7
 #endif
 constexpr int P2_STAGES = NN_TC_P2_STAGES;
 constexpr int P2_STAGE_BYTES = A_TILE + B_TILE / 2;  // 32 KB
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_2sm_kernel(const __grid_co
   uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  // 17 barriers + TMEM slot + abort flag take the first 144 bytes of the control block
+  // 2 P2_STAGES + 5 barriers, the TMEM slot and the abort flag fit in the first 192 bytes of the control block
   double* red = reinterpret_cast<double*>(smem + P2_STAGES * P2_STAGE_BYTES + 192);
 
   const int warp = threadIdx.x >> 5;

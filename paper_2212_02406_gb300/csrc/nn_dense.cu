@@ -320,6 +320,7 @@ int run_simt(cudaStream_t st, int n, const T* A, int64_t lda, T* const X[2], T* 
     res->pieces[k] = 0;
     res->nests = k;
     res->residual = s;
+    res->residual_est = s;
     const int verdict = judge(o, k, res->history);
     if (verdict >= 0) {
       res->status = verdict;
@@ -396,42 +397,45 @@ int tc_product(cudaStream_t st, TcGemmArgs& g, int pa, int pb, __nv_bfloat16* co
 
 // Precision levels of the mixed chain (BF16 pieces per operand):
 //   level 1: residual 1 piece,  Horner/update 1 piece   (bulk)
-//   level 2: residual 2 pieces, Horner product 1 piece, update 2 pieces
-//   level 3: residual 3 pieces, Horner product 1 piece, update 2 pieces   (FP32-level residual)
+//   level 2: residual 2 pieces, Horner product 1 piece, update 2 pieces of X
+//   level 3: residual 3 pieces, Horner product 1 piece, update 2 pieces of X
 //   level 4: residual 3 pieces, Horner/update 3 pieces
-// A piece-p product has relative error about 2^-(8p+1); the residual error floor of level L
-// is e(L) ~ 2^-b(L) ||A||_F ||X_k||_F / N^1.5, the rms of the rounding of sum_k a_ik x_kj
-// (N terms of typical size |a_i| |x_j| / N with random signs, |a_i| ~ ||A||_F / sqrt(N)),
-// with b = 9, 17, 19, 19 (levels 3 and 4 are bounded by the tensor core's FP32
-// accumulation, not by the pieces). The chain moves up a level once s_k < 8 e(L), when it
-// stalls (s_k > 0.9 s_{k-1}) within 30 e(L) of the floor, and before accepting s_k < tol.
+// Error floors (rms error of a residual measured at the level, with c = ||A||_F ||X_k||_F / N^1.5):
+// the pieces leave about 2^-8.8 c (1 piece), 2^-17.9 c (2 pieces), 2^-25 c (3 pieces) -- the
+// rounding of N terms of size ~|a_i| |x_j| / N with random signs -- and the tensor core's FP32
+// accumulation over K = N adds about 5.4e-10 c N, growing with N (both constants measured on
+// GB300 by comparing residuals of an FP64 inverse with FP64 ones, N = 1024..8192, kappa = 1e2
+// and 1e4). At N = 8192 the accumulation floor of level 3 equals the piece floor of level 2.
+// These floors are systematic for a given A: the chain converges to the X whose measured
+// residual vanishes, so a measured s_k falls below the truth, which is about
+// sqrt(s_k^2 + e(L')^2) with L' the level of the residual that produced X_k. That estimate
+// is what a stop must pass (the certified residual). The top level of a run is the lowest one
+// whose floor lies under 0.8 tol; levels above it gain nothing for this tol.
+// The chain moves up a level (not past the top one) once s_k < 8 e(L), and when it stalls
+// (s_k > 0.9 s_{k-1}) within 30 e(L) of the floor.
 // Stability: a product with p pieces perturbs the next residual by about
 // 2^-(8p+1) ||A||_2 ||X_k||_2 ||T||_2; once that nears 1 the perturbed residual can reach
 // spectral radius 1 in a slowly converging direction and the chain diverges later even though
 // s_k still falls. K = ||A||_F ||X_k||_F / N estimates ||A||_2 ||X_k||_2 from below, so the
 // level must keep 2^-(8p+1) K * 64 <= 1 (64 covers ||T||_2 <= L+1 and the Frobenius-to-spectral
 // gap of the spectra this path is built for).
-// Levels never go down. The residual accepted for the stop test is always level >= 3.
+// Levels never go down.
 //
 // The update X_k T reads X_k with the level's pieces and T with its own count: T ~ R_k, and
-// A X_k ~ I, so T's rounding reaches the next residual unamplified (about 2^-(8p+1) s_k),
-// while X_k's is amplified by K; one piece of T (one pass less at levels 2 and 3) stays under
-// the next residual wherever s_k is small enough for those levels.
+// A X_k ~ I, so T's rounding reaches the next residual unamplified (about 2^-9 s_k for one
+// piece), while X_k's is amplified by K; one piece of T (one pass less at levels 2 and 3) stays
+// under the next residual wherever s_k is small enough for those levels.
 // Compile-time tuning of the schedule (defaults as described above).
 #ifndef NN_POLICY_RISE
 #define NN_POLICY_RISE 8.0
 #endif
 #ifndef NN_POLICY_T_MID
-#define NN_POLICY_T_MID 2
-#endif
-#ifndef NN_POLICY_FINAL_LEVEL
-#define NN_POLICY_FINAL_LEVEL 3
+#define NN_POLICY_T_MID 1
 #endif
 #ifndef NN_POLICY_STABLE
 #define NN_POLICY_STABLE 64.0
 #endif
 constexpr double kRise = NN_POLICY_RISE;        // level L < 3 rises once s_k < kRise e(L)
-constexpr int kFinalLevel = NN_POLICY_FINAL_LEVEL;  // lowest level accepted for a stop
 constexpr double kStable = NN_POLICY_STABLE;    // 2^-(8p+1) K kStable <= 1 for the X pieces p
 static int level_res_pieces(int L) { return L <= 1 ? 1 : (L == 2 ? 2 : 3); }
 // pieces of X_k in the update
@@ -447,9 +451,19 @@ static int stable_level(double kest) {
   }
   return 4;
 }
-static double level_floor(int L, double c) {
-  const double b = L <= 1 ? 9.0 : (L == 2 ? 17.0 : 19.0);
-  return ldexp(c, -int(b));
+// rms error floor of a residual measured at level L (0: exact, the element-wise R_0)
+static double level_floor(int L, double c, double n) {
+  if (L <= 0) return 0.0;
+  const double pieces = c * (L == 1 ? 0x1.27p-9 : (L == 2 ? 0x1.15p-18 : 0x1p-25));
+  const double acc = 5.4e-10 * c * n;
+  return sqrt(pieces * pieces + acc * acc);
+}
+// lowest level whose floor lies under 0.8 tol (3 if none does, 1 for tol <= 0)
+static int top_level(double tol, double c, double n) {
+  if (!(tol > 0)) return 3;
+  for (int L = 1; L <= 3; ++L)
+    if (level_floor(L, c, n) < 0.8 * tol) return L;
+  return 3;
 }
 
 // Re-splits X_0 into buffer set 0 (pieces, FP32 master) and its norm into cm.scal[1].
@@ -518,6 +532,8 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
   // FP32 master (the same pieces).
   int xr[2] = {0, 0}, xc[2] = {0, 0};
   if (!scalar_x0) xr[0] = xc[0] = 3;
+  // level of the residual that produced each buffer's iterate (0: X_0, exact)
+  int xlev[2] = {0, 0};
   auto ensure_pieces = [&](int b, int need_r, int need_c) -> int {
     if (xr[b] >= need_r && xc[b] >= need_c) return NN_OK;
     NN_TRY(split_matrix_f32(st, w.x32[b], np, n, np, w.x_row[b], 3, w.x_col[b], 3));
@@ -613,6 +629,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       cur = 0;
       k = 0;
       level = 2;
+      xlev[0] = 0;
       if (!scalar_x0) {
         NN_TRY(load_x0(st, n, w, cm, x0src));
         xr[0] = xc[0] = 3;
@@ -621,16 +638,20 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       NN_TRY(measure(level, &s));
     }
     const double c = a_frob * x_frob / n15;
+    const double dn = double(n);
+    const int l_top = top_level(o.tol, c, dn);
+    // false: tol lies under what BF16 pieces can certify (the level-3 floor is above 0.8 tol)
+    const bool certifiable = !(o.tol > 0) || level_floor(3, c, dn) < 0.8 * o.tol;
     {
       int target = level;
       if (isfinite(s)) {
-        const int ls = stable_level(a_frob * x_frob / double(n));
+        const int ls = stable_level(a_frob * x_frob / dn);
         if (target < ls) target = ls;
-        while (target < 3 && s < kRise * level_floor(target, c)) ++target;
-        if (k >= 1 && s > 0.9 * res->history[k - 1] && s < 30.0 * level_floor(level, c) && level < 4)
+        while (target < l_top && s < kRise * level_floor(target, c, dn)) ++target;
+        if (k >= 1 && s > 0.9 * res->history[k - 1] && s < 30.0 * level_floor(level, c, dn) && level < 4)
           target = target > (level <= 2 ? 3 : 4) ? target : (level <= 2 ? 3 : 4);
         if (o.refine_below > 0 && s * sqrt_n < o.refine_below && target < 3) target = 3;
-        if (o.tol > 0 && s < o.tol && target < kFinalLevel) target = kFinalLevel;
+        if (o.tol > 0 && s < o.tol && target < l_top) target = l_top;
       }
       if (target != level) {
         // The residual epilogue writes R's pieces for the Horner/update GEMMs at the level's
@@ -659,17 +680,24 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     res->pieces[k] = level_res_pieces(level);
     res->nests = k;
     res->residual = s;
+    // the residual X_k has, with the floor of the residual that produced it (certified estimate)
+    const double e_fix = level_floor(xlev[cur], c, dn);
+    const double s_cert = sqrt(s * s + e_fix * e_fix);
+    res->residual_est = s_cert;
     int verdict = judge(o, k, res->history);
+    if (verdict == NN_OK && o.tol > 0 && !(s_cert < o.tol))
+      // measured under tol but not certified: a nest from a residual at the top level certifies
+      // it where the top level's floor allows, otherwise the floor blocks
+      verdict = (certifiable && k < o.max_nests) ? -1 : NN_ERR_NOT_CONVERGED;
     // At the top level, two nests in a row within 30 floors without a 10% gain: the residual
     // has reached the arithmetic floor, so more nests cannot reach tol.
     if (verdict < 0 && level == 4 && k >= 2 && o.tol > 0 && s > 0.9 * res->history[k - 1] &&
-        res->history[k - 1] > 0.9 * res->history[k - 2] && s < 30.0 * level_floor(4, c))
+        res->history[k - 1] > 0.9 * res->history[k - 2] && s < 30.0 * level_floor(4, c, dn))
       verdict = NN_ERR_NOT_CONVERGED;
     // NN_MIXED_EMU: a tolerance below the BF16-piece floors is reached by emulated FP64 nests;
     // hand the iterate over once the pieces can no longer bring s down (within 4 level-2 floors:
     // level 3 only gains the tensor core's FP32 accumulation floor at twice the passes).
-    if (verdict < 0 && o.dtype == NN_MIXED_EMU && o.tol > 0 && o.tol < 8.0 * level_floor(3, c) &&
-        s < 4.0 * level_floor(2, c))
+    if (verdict < 0 && o.dtype == NN_MIXED_EMU && !certifiable && s < 4.0 * level_floor(2, c, dn))
       verdict = NN_ERR_NOT_CONVERGED;
     if (verdict >= 0) {
       res->status = verdict;
@@ -691,10 +719,11 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
         const double lp = double(nest_depth(o, k - 1)), lk = double(nest_depth(o, k));
         s_pred = s * pow(ratio, (lp + 1.0) * lk / lp);
         if (level < 3) {
-          while (next_level < 3 && s_pred < kRise * level_floor(next_level, c)) ++next_level;
-          if (o.tol > 0 && s_pred < o.tol && next_level < kFinalLevel) next_level = kFinalLevel;
+          while (next_level < l_top && s_pred < kRise * level_floor(next_level, c, dn)) ++next_level;
+          if (o.tol > 0 && s_pred < o.tol && next_level < l_top) next_level = l_top;
         }
-        likely_final = o.tol > 0 && s_pred < 0.5 * o.tol && next_level >= kFinalLevel;
+        likely_final = o.tol > 0 && s_pred < 0.5 * o.tol && next_level >= l_top &&
+                       hypot(s_pred, level_floor(level, c, dn)) < 0.9 * o.tol;
       }
     }
     // NN_MIXED_EMU with tol below the BF16 pieces' floor: once X_{k+1} is predicted to lie within
@@ -708,8 +737,8 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       const double lp = double(nest_depth(o, k - 1)), lk = double(nest_depth(o, k));
       s_slow = s_pred * exp(0.5 * (log(lp + 1.0) * (lp + 1.0) * lk / lp - log(lk + 1.0)));
     }
-    const bool handover = o.dtype == NN_MIXED_EMU && o.tol > 0 && o.tol < 8.0 * level_floor(3, c) &&
-                          s_slow >= 0 && s_slow < 4.0 * level_floor(2, c) && k + 1 < o.max_nests;
+    const bool handover = o.dtype == NN_MIXED_EMU && !certifiable && s_slow >= 0 &&
+                          s_slow < 4.0 * level_floor(2, c, dn) && k + 1 < o.max_nests;
     if (handover) likely_final = false;
     // Horner: T_1 = R (its column pieces), T_{j+1} = R + R T_j. With a scalar X_0 the first
     // nest's last Horner product also leaves T in FP32 over R's FP32 copy (each element read as
@@ -756,6 +785,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
         }
         g.partial = cm.partial;
         NN_TRY(before_x_write());
+        xlev[cur ^ 1] = level;
         xr[cur ^ 1] = wr;
         xc[cur ^ 1] = wc;
         NN_TRY(tc_product(st, g, hh, hh, w.r_row, t_cur, cm, res, &grid, &timer));
@@ -771,6 +801,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       // depth 1: T = R_0 = I - alpha A, X_1 = 2 alpha I - alpha^2 A element-wise from FP64 A
       if (nest_depth(o, k) == 1) {
         NN_TRY(before_x_write());
+        xlev[cur ^ 1] = level;
         xr[cur ^ 1] = xc[cur ^ 1] = 3;
         NN_TRY(split_matrix_affine(st, A, lda, n, np, w.x32[cur ^ 1], w.x_row[cur ^ 1], 3, w.x_col[cur ^ 1], 3,
                                    w.split_partial, -alpha * alpha, 2.0 * alpha));
@@ -780,6 +811,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     } else {
       NN_TRY(ensure_pieces(cur, hp, 0));
       NN_TRY(before_x_write());
+      xlev[cur ^ 1] = level;
       xr[cur ^ 1] = wr;
       xc[cur ^ 1] = wc;
       TcGemmArgs g;
@@ -970,6 +1002,7 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
       }
       res->nests = k0 + r2.nests;
       res->residual = r2.residual;
+      res->residual_est = r2.residual_est;
       res->status = r2.status;
       res->gemms += r2.gemms;
       res->launches += r2.launches + 1;

@@ -182,7 +182,7 @@ int run_job(nn_server* s, const Job& j, cudaStream_t st, nn_completion* c) {
   const int st_inv = invert_device(dA, n, n, dX0, n, &o, dX, n, &res, ws, wsb, st);
   c->status = st_inv;
   c->nests = res.nests;
-  c->residual = res.residual;
+  c->residual = res.residual_est;
   // X_0: one reduction for the scalar (trace / Theta_2 power steps / none) and the fill
   const int pc_launches = alpha > 0.0                         ? 0
                           : r.precond == NN_PC_PAN_SCHREIBER ? 3

@@ -46,6 +46,15 @@ def test_opts_struct_matches_header(lib):
     assert fields == [f for f, _ in abi.NNOpts._fields_]
 
 
+def test_result_struct_matches_header(lib):
+    # NNResult mirrors nn_result field for field (array members included)
+    text = open(os.path.join(ROOT, "include", "nn.h")).read()
+    body = re.search(r"typedef struct nn_result \{(.*?)\} nn_result;", text, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(\w+)\s*(?:\[\w+\])?\s*;", body)
+    assert fields == [f for f, _ in abi.NNResult._fields_]
+
+
 def test_workspace_sizes(lib):
     assert abi.nn_workspace_bytes(0, "f64") == 0
     assert abi.nn_workspace_bytes(16, 99) == 0

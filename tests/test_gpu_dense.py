@@ -189,6 +189,8 @@ def test_mixed_bf16_converges_and_matches(nn, n, depth):
     s64 = dense.rms_frob(dense.residual(a, x))
     assert abs(s64 - res["residual"]) <= e_acc(n)
     assert s64 < 1e-6
+    # the certified residual (measured value with the arithmetic's floor) covers the truth
+    assert res["residual_est"] < 1e-6 and s64 <= 1.5 * res["residual_est"]
     # forward error against the library inverse: residual floor + FP32 rounding of A
     inv = np.linalg.inv(a)
     assert _rel(x, inv) <= 2 * math.sqrt(n) * s64 + 16 * kappa * U32
@@ -208,6 +210,27 @@ def test_mixed_matches_oracle_within_1e6(nn, n):
     assert st in (nn.NN_OK, nn.NN_ERR_NOT_CONVERGED), res
     ora = dense.nn_invert(a, x0, depth, tol=1e-13, max_nests=40)
     assert _rel(x, ora.x) <= 1e-6
+
+
+@pytest.mark.parametrize("n,kappa", [(1024, 1e3), (2048, 1e2), (2048, 1e3)])
+def test_mixed_stop_is_certified(nn, n, kappa):
+    # The chain converges to the X whose measured (BF16-piece, FP32-accumulated) residual
+    # vanishes, so a measured s falls below the truth by about the arithmetic's floor. A stop
+    # must pass the certified estimate, residual_est = sqrt(s^2 + e^2): whenever the call reports
+    # NN_OK the FP64 residual of the returned X meets tol, and a tol under the floor ends
+    # NN_ERR_NOT_CONVERGED with an honest estimate.
+    a, q, lam = synth.spd_spectrum(n, kappa, seed=n + int(kappa) + 5)
+    alpha = 2.0 / (lam[0] + lam[-1])
+    x0 = dense.precond_scalar(n, alpha)
+    for tol in (1e-5, 1e-6, 3e-7):
+        st, res, x = _run(nn, a, x0, 2, tol, 40, "mixed_bf16", x0_scalar=alpha)
+        s64 = dense.rms_frob(dense.residual(a, x))
+        assert st in (nn.NN_OK, nn.NN_ERR_NOT_CONVERGED), res
+        assert s64 <= 1.5 * res["residual_est"], (tol, s64, res["residual_est"])
+        if st == nn.NN_OK:
+            assert res["residual_est"] < tol and s64 < tol, (tol, s64, res)
+        else:
+            assert res["residual_est"] >= 0.5 * tol, (tol, res)
 
 
 def test_mixed_kappa_1e4_does_not_diverge(nn):
