@@ -157,6 +157,15 @@ typedef struct nn_result {
  * against concurrent inversions. */
 int nn_set_gemm_variant(int variant);
 
+/* Failure-detection test hook (the paper has no counterpart). on != 0 arms it for the next
+ * tensor-core GEMM launch of the process: that launch's MMA issuer withholds its first
+ * "accumulator ready" signal, a signal nothing else sets, so the epilogue's bounded device wait
+ * (about one second) runs out; every role of the kernel then leaves its loop, in-flight tensor
+ * work is drained and TMEM freed, the kernel returns, and the calling entry point reports
+ * NN_ERR_TIMEOUT with the CUDA context still usable. The hook disarms itself when that launch
+ * takes it; on = 0 disarms it. No fault, trap or endless wait is involved. Returns NN_OK. */
+int nn_debug_withhold_signal(int on);
+
 /* Bytes of device workspace nn_invert / nn_residual need for an N x N problem of `dtype`
  * (256-byte aligned internally). Returns 0 for invalid arguments. */
 size_t nn_workspace_bytes(int64_t n, int dtype);
@@ -374,7 +383,8 @@ typedef struct nn_request {
   const double* B;
   double* Y;
   double* X;
-  int dtype;            /* NN_F64, NN_F32 or NN_MIXED_BF16                                     */
+  int dtype;            /* NN_F64, NN_F32, NN_MIXED_BF16 or NN_MIXED_EMU (BF16-piece nests, then
+                           emulated FP64 nests where tol lies under what the pieces certify)   */
   int precond;          /* nn_pc                                                               */
   double pc_scalar;
 } nn_request;

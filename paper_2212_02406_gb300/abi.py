@@ -80,6 +80,7 @@ _LIB = None
 # Every symbol include/nn.h declares, with its ctypes signature.
 _SIGNATURES = {
     "nn_set_gemm_variant": (c_int, [c_int]),
+    "nn_debug_withhold_signal": (c_int, [c_int]),
     "nn_workspace_bytes": (c_size_t, [c_int64, c_int]),
     "nn_workspace_bytes_host": (c_size_t, [c_int64, c_int]),
     "nn_init_precond": (c_int, [c_void_p, c_int64, c_int64, c_int, c_double, c_void_p, c_int64, c_void_p, c_size_t,
@@ -203,6 +204,12 @@ def workspace(n: int, dtype="f64", host=False, device=None):
 
 
 # ---- entry points (same names as the C ABI) -------------------------------------------
+
+def nn_debug_withhold_signal(on: bool = True) -> int:
+    """Arms the failure-detection hook for the next tensor-core GEMM launch (its bounded wait runs
+    out and the call reports NN_ERR_TIMEOUT)."""
+    return int(lib().nn_debug_withhold_signal(1 if on else 0))
+
 
 def nn_set_gemm_variant(variant: int) -> int:
     """0 automatic, 1 single-CTA tiles, 3 2-SM MMA, 4 2-SM MMA with the last wave split into halves

@@ -28,6 +28,7 @@
 #include <cudaTypedefs.h>
 #include <cuda.h>
 
+#include <atomic>
 #include <mutex>
 #include <string.h>
 
@@ -98,6 +99,9 @@ struct Params {
   int64_t cvt_ld;
   int cvt_n;
   int cvt_vec;
+  // Failure-detection test hook: the MMA issuer withholds the first accumulator-ready signal, so
+  // the epilogue's bounded wait runs out (nn_debug_withhold_signal).
+  int withhold;
 };
 
 // Shared-memory matrix descriptor for a K-major tile written by TMA with SWIZZLE_128B:
@@ -371,7 +375,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
           }
         }
         if (!ok) break;
-        tc_commit(&acc_full[acc]);
+        if (!(p.withhold && local == 0)) tc_commit(&acc_full[acc]);
       }
       // Wait for every MMA this thread issued before TMEM can be released.
       tc_commit(drain);
@@ -567,7 +571,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_2sm_kernel(const __grid_co
           }
         }
         if (!ok) break;
-        tc_commit_pair_multicast(&acc_full[acc], uint16_t(0x3));
+        if (!(p.withhold && local == 0)) tc_commit_pair_multicast(&acc_full[acc], uint16_t(0x3));
       }
       tc_commit_pair(drain);
       volatile int no_abort = 0;
@@ -630,6 +634,7 @@ int g_2sm_clusters = 0;   // co-resident clusters of the 2-SM MMA kernel (0: una
 int g_variant = 0;  // 0 auto (4 where possible, else 1), 1 single-CTA, 3 2-SM MMA, 4 3 + split tail
 bool g_tc_ok = false;
 std::once_flag g_once;
+std::atomic<int> g_withhold{0};  // armed by nn_debug_withhold_signal, consumed by the next launch
 
 cudaLaunchConfig_t cluster_config(int grid, int smem, cudaStream_t st, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
@@ -706,6 +711,8 @@ bool tc_supported() {
   return g_tc_ok;
 }
 
+void gemm_tc_withhold_next(int on) { g_withhold.store(on ? 1 : 0); }
+
 void gemm_tc_set_variant(int v) { g_variant = (v == 1 || v == 3 || v == 4) ? v : 0; }
 
 int gemm_tc_max_grid() {
@@ -773,6 +780,7 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
   p.cvt_ld = a.cvt_ld;
   p.cvt_n = a.cvt_n;
   p.cvt_vec = (a.cvt_ld % 2 == 0 && (reinterpret_cast<uintptr_t>(a.cvt_dst) & 15) == 0) ? 1 : 0;
+  p.withhold = g_withhold.exchange(0);
   // Variant choice: the 2-SM MMA with a split last wave by default where the size allows it, else
   // single-CTA tiles.
   const bool even = a.np % (2 * tc::BM) == 0;

@@ -639,9 +639,10 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     }
     const double c = a_frob * x_frob / n15;
     const double dn = double(n);
-    const int l_top = top_level(o.tol, c, dn);
     // false: tol lies under what BF16 pieces can certify (the level-3 floor is above 0.8 tol)
     const bool certifiable = !(o.tol > 0) || level_floor(3, c, dn) < 0.8 * o.tol;
+    // NN_MIXED_EMU hands an uncertifiable tol to emulated nests: level 3 would gain nothing
+    const int l_top = (o.dtype == NN_MIXED_EMU && !certifiable) ? 2 : top_level(o.tol, c, dn);
     {
       int target = level;
       if (isfinite(s)) {
@@ -699,6 +700,10 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     // level 3 only gains the tensor core's FP32 accumulation floor at twice the passes).
     if (verdict < 0 && o.dtype == NN_MIXED_EMU && !certifiable && s < 4.0 * level_floor(2, c, dn))
       verdict = NN_ERR_NOT_CONVERGED;
+    // NN_MIXED_BF16 with a tol it cannot certify: once s is under the level-3 floor, more nests
+    // lower the measured residual but not the true one (about the floor), so the run ends there.
+    if (verdict < 0 && o.dtype == NN_MIXED_BF16 && !certifiable && level >= 3 && s < level_floor(3, c, dn))
+      verdict = NN_ERR_NOT_CONVERGED;
     if (verdict >= 0) {
       res->status = verdict;
       break;
@@ -732,10 +737,21 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     // ends of a continuous spectrum s_k ~ rho^(m_k) m_k^(-1/2) (m_k the Neumann order + 1), so
     // the geometric extrapolation above is multiplied by
     // exp((ln(L_{k-1} + 1) (L_{k-1} + 1) L_k / L_{k-1} - ln(L_k + 1)) / 2) (3 at depth 2).
+    auto predict_slow = [](double s_cur, double s_prev, double lp, double lk) {
+      const double ratio = s_cur / s_prev;
+      return s_cur * pow(ratio, (lp + 1.0) * lk / lp) *
+             exp(0.5 * (log(lp + 1.0) * (lp + 1.0) * lk / lp - log(lk + 1.0)));
+    };
     double s_slow = -1.0;
     if (s_pred >= 0) {
       const double lp = double(nest_depth(o, k - 1)), lk = double(nest_depth(o, k));
-      s_slow = s_pred * exp(0.5 * (log(lp + 1.0) * (lp + 1.0) * lk / lp - log(lk + 1.0)));
+      s_slow = predict_slow(s, res->history[k - 1], lp, lk);
+      // Nest k+1 predicted to be the last one (its iterate X_{k+2} under tol): X_{k+2} is only
+      // certified if R_{k+1}, which produces it, runs at the top level.
+      if (o.tol > 0 && next_level < l_top && s_slow < s) {
+        const double s2 = predict_slow(s_slow, s, lk, double(nest_depth(o, k + 1)));
+        if (s2 < 0.5 * o.tol) next_level = l_top;
+      }
     }
     const bool handover = o.dtype == NN_MIXED_EMU && !certifiable && s_slow >= 0 &&
                           s_slow < 4.0 * level_floor(2, c, dn) && k + 1 < o.max_nests;
@@ -1037,6 +1053,11 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
 using namespace nn;
 
 extern "C" {
+
+int nn_debug_withhold_signal(int on) {
+  gemm_tc_withhold_next(on);
+  return NN_OK;
+}
 
 int nn_set_gemm_variant(int variant) {
   if (variant != 0 && variant != 1 && variant != 3 && variant != 4) return NN_ERR_ARG;

@@ -160,8 +160,9 @@ int run_job(nn_server* s, const Job& j, cudaStream_t st, nn_completion* c) {
   // A scalar X_0 on the mixed chain (the scalar preconditioner, or Theta_1 = I / Tr(A) from the
   // host copy of A) is passed as the x0_scalar hint and never materialised.
   double alpha = 0.0;
-  if (r.dtype == NN_MIXED_BF16 && r.precond == NN_PC_SCALAR) alpha = r.pc_scalar;
-  if (r.dtype == NN_MIXED_BF16 && r.precond == NN_PC_TRACE) {
+  const bool mixed = r.dtype == NN_MIXED_BF16 || r.dtype == NN_MIXED_EMU;
+  if (mixed && r.precond == NN_PC_SCALAR) alpha = r.pc_scalar;
+  if (mixed && r.precond == NN_PC_TRACE) {
     double tr = 0.0;
     for (int64_t i = 0; i < n; ++i) tr += r.A[i * n + i];
     alpha = tr > 0.0 ? 1.0 / tr : 0.0;
@@ -290,7 +291,8 @@ int nn_server_create(const nn_server_opts* opts, nn_server** out) {
 int nn_server_submit(nn_server* s, const nn_request* r) {
   if (s == nullptr || r == nullptr || r->A == nullptr || r->n < 1 || r->nrhs < 0) return NN_ERR_ARG;
   if (r->nrhs > 0 && r->B == nullptr) return NN_ERR_ARG;
-  if (r->dtype != NN_F64 && r->dtype != NN_F32 && r->dtype != NN_MIXED_BF16) return NN_ERR_ARG;
+  if (r->dtype != NN_F64 && r->dtype != NN_F32 && r->dtype != NN_MIXED_BF16 && r->dtype != NN_MIXED_EMU)
+    return NN_ERR_ARG;
   if (r->precond < NN_PC_PAN_SCHREIBER || r->precond > NN_PC_THETA2) return NN_ERR_ARG;
   const size_t bytes = request_bytes(r->n, r->nrhs, r->dtype);
   if (bytes == 0) return NN_ERR_ARG;

@@ -319,7 +319,7 @@ def test_host_panel_split_equals_device(nn, n):
 
 
 @pytest.mark.parametrize("n,pad", [(300, 0), (300, 1), (517, 3), (1024, 0)])
-@pytest.mark.parametrize("tol", [1e-5, 1e-7])
+@pytest.mark.parametrize("tol", [1e-5, 3e-7])
 def test_device_early_copy_strided_output(nn, n, pad, tol):
     # For the mixed chain the iterate predicted to be returned is widened into the caller's X by
     # the confirming residual's epilogue (16-byte stores for an even leading dimension, element
