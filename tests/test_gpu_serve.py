@@ -112,8 +112,7 @@ def test_budget_respected_and_oversize_refused(nn):
     import torch
 
     reqs = _requests(6, seed=3, n_max=300)
-    sizes = [nn.nn_server_request_bytes(r.n, r.nrhs, "f32" if r.dtype == "f32" else "mixed_bf16")
-             for r, _, _ in reqs]
+    sizes = [nn.nn_server_request_bytes(r.n, r.nrhs, _dt(r)) for r, _, _ in reqs]
     budget = int(max(sizes) * 1.5)
     outs, comps, stats, cap = _run(nn, reqs, max_active=4, arena_bytes=budget)
     assert len(comps) == len(reqs)
