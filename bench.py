@@ -663,6 +663,87 @@ def sparse_chain_bytes(n, nnz, depth, nests, val_bytes):
     return total, products, resid
 
 
+def run_sparse_sharded(args, rank, world, local_rank):
+    """The sparse chain over row strips, one per GPU (weak scaling: a 2048 x 2048 block of grid rows
+    per rank, the global grid 2048 wide and 2048 x world high): each product exchanges one grid
+    row with each neighbour (NCCL point-to-point), the residual all-reduces two sums."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2212_02406_gb300 import abi, build, shard
+
+    build.build()
+    abi.lib()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    grid, depth, nests = 2048, 2, 5
+    if args.dtype not in ("mixed_bf16", "f64", "f32"):
+        raise SystemExit("the sharded sparse chain runs FP64 or FP32")
+    dtype = np.float32 if args.dtype == "f32" else np.float64
+    m = synth.laplacian_5pt(grid, grid * world, shift=0.5, dtype=dtype)
+    plans = shard.build_halo_plans(m.row_ptr, m.col, shard.partition_rows(m.n, world))
+    p = plans[rank]
+    strip = shard.CudaStrip(p, m.row_ptr, m.val, dev)
+    ex = shard.DistExchange(p, dev)
+    shard.setup_strips([strip], ex)
+    nnz_local = int(m.row_ptr[p.r1] - m.row_ptr[p.r0])
+    b = synth.gaussian_rhs(p.r1 - p.r0, 1, seed=args.seed + rank, dtype=dtype)[:, 0]
+    b_dev = torch.from_numpy(np.ascontiguousarray(b)).to(dev)
+    del m
+
+    def allreduce(vals):
+        t = torch.tensor(vals, dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return t.tolist()
+
+    depths = [depth] * nests
+    stream = torch.cuda.current_stream(dev)
+    sampler = clock_sampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    for _ in range(args.warmup):
+        xs, rel = shard.sharded_sparse_chain([strip], ex, [b_dev], depths, allreduce=allreduce)
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    sampler.begin()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        xs, rel = shard.sharded_sparse_chain([strip], ex, [b_dev], depths, allreduce=allreduce)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    clocks = sampler.stop()
+    t = torch.tensor([ev0.elapsed_time(ev1) / args.steps], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    vb = 8 if dtype == np.float64 else 4
+    chain, products, resid = sparse_chain_bytes(p.r1 - p.r0, nnz_local, depth, nests, vb)
+    tot = torch.tensor([float(chain + resid)], dtype=torch.float64, device=dev)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    gbs = float(tot.item()) / (ms / 1e3) / 1e9
+    peaks, src = load_peaks()
+    peak = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
+    return {"metric": "HBM GB/s of the sparse NN chain (5-point Laplacian 2048^2, depth 2)",
+            "value": round(gbs, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if dtype == np.float64 else "f32", "data": "synthetic",
+            "config": {"workload": f"2-D 5-point Laplacian {grid} x {grid * world} + 0.5 I in row strips of "
+                                   f"{grid} x {grid} per GPU, CSR, b ~ N(0,1), Jacobi X0, depth {depth}, {nests} "
+                                   f"factors ({products} sparse products)",
+                       "parallelism": f"row strips over {world} GPUs, one halo grid row per neighbour per product "
+                                      "(NCCL point-to-point), residual sums all-reduced",
+                       "l2": "matrix larger than L2 (streams every product)"},
+            "residual": rel, "gpu_launches": (products + 3) * args.steps,
+            "roofline": {"kernel": "nn::spmv_ring_kernel through nn_csr_strip_product (whole chain timed, halo "
+                                   "exchanges included)", "bound": "hbm", "achieved": round(gbs / world, 1),
+                         "peak": peak, "unit": "GB/s per GPU", "frac": round(gbs / world / peak, 4), "traffic": None,
+                         "peak_source": f"{src} copy bandwidth"},
+            "clocks": clocks}
+
+
 def run_sparse(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -670,6 +751,8 @@ def run_sparse(args, rank, world, local_rank):
     import synth
     from paper_2212_02406_gb300 import abi, build
 
+    if world > 1:
+        return run_sparse_sharded(args, rank, world, local_rank)
     build.build()
     abi.lib()
     abi.nn_set_spmv_variant(args.spmv_variant)
@@ -749,7 +832,17 @@ def run_batched(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     count, depth, nests = 16384, 2, 3
     damping = args.damping
-    bt = synth.mimo_gram_batch(count, seed=args.seed + rank)
+    if world > 1:
+        # one global batch of count x world matrices, sharded by matrices (balanced sum of U^3);
+        # each rank generates only its share (per-matrix streams): no data-path collective
+        from paper_2212_02406_gb300 import shard
+
+        sizes_all = synth.mimo_sizes(count * world, seed=args.seed)
+        mine = shard.shard_batch(sizes_all, world)[rank]
+        bt = synth.mimo_gram_indexed(mine, sizes_all, seed=args.seed)
+        count = bt.count
+    else:
+        bt = synth.mimo_gram_batch(count, seed=args.seed + rank)
     A = torch.from_numpy(bt.data).to(dev)
     offs = torch.from_numpy(bt.offsets.astype(np.int64)).to(dev)
     sizes = torch.from_numpy(bt.sizes.astype(np.int32)).to(dev)
@@ -784,6 +877,10 @@ def run_batched(args, rank, world, local_rank):
         g.replay()
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize(dev)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
     sampler.begin()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ev[0].record(stream)
@@ -791,9 +888,19 @@ def run_batched(args, rank, world, local_rank):
         g.replay()
         ev[i + 1].record(stream)
     torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
     clocks = sampler.stop()
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     ms = sum(per) / len(per)
+    total = count
+    if world > 1:
+        t = torch.tensor([ms, float(count)], device=dev, dtype=torch.float64)
+        tmax = t[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t[1:].clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms, total = float(tmax.item()), int(tsum.item())
     u = bt.sizes.astype(np.float64)
     gemms = (depth + 1) * nests + 1
     flops = float(np.sum(8.0 * u ** 3)) * gemms
@@ -809,7 +916,7 @@ def run_batched(args, rank, world, local_rank):
     tflops = flops / (ms / 1e3) / 1e12
     tflops_exec = flops_exec / (ms / 1e3) / 1e12
     return {"metric": "batched inversions/s (16,384 complex64 Gram matrices, U in {8..64}, depth 2, 3 nests)",
-            "value": round(count * world / (ms / 1e3), 1), "unit": "inversions/s", "n_gpus": world,
+            "value": round(total / (ms / 1e3), 1), "unit": "inversions/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
             "p99_ms": round(float(np.percentile(per, 99)), 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64 (fp32 FMA)", "data": "synthetic",
@@ -818,6 +925,8 @@ def run_batched(args, rank, world, local_rank):
                                    f"{nests} nests, one persistent kernel per tile class, chained by programmatic "
                                    f"dependent launch, replayed from a CUDA graph",
                        "count": count, "damping": damping, "l2": "A + X = 363 MB > L2",
+                       "parallelism": (f"batch sharded by matrices over {world} GPUs (balanced sum of U^3), "
+                                       "no data-path collective") if world > 1 else "single GPU",
                        "tensor_core_items": bool(args.batched_tc) or any(v == 2 for v in (table or {}).values())},
             "status_ok_fraction": float(np.mean(stats == 0)), "gpu_launches": bin(classes).count("1") * args.steps,
             "tflops": round(tflops, 2), "gbs": round(byts / (ms / 1e3) / 1e9, 1),

@@ -265,6 +265,47 @@ int nn_solve(const int32_t* row_ptr, const int32_t* col, const void* val, int64_
  * against concurrent solves. */
 int nn_set_spmv_variant(int variant);
 
+/* ---- row strips of the sparse chain (one rank's share of a sharded solve) ----------------
+ * Corollary 1 applied per row strip: with the rows of A cut into contiguous strips, one per
+ * rank, each sparse product P v = v - A D^-1 v of the chain needs, besides the strip's own
+ * entries of v, the values of v on the strip's halo columns (owned by other strips), and each
+ * residual check needs two sums reduced over the strips. These calls run one strip's share on
+ * this GPU; the caller exchanges the halo values (NCCL or any transport) and reduces the sums.
+ * One right-hand side.
+ *
+ * Local numbering: the strip holds rows [r0, r1) of A, n_local = r1 - r0, in CSR with
+ * row_ptr[n_local + 1] (from 0) and col_local[nnz] in an extended numbering: a column c owned
+ * by the strip is c - r0, a halo column takes a position >= n_local (n_ext = n_local + number of
+ * halo columns). An extended vector v_ext[n_ext] holds the strip's values first, then the halo
+ * values in that order. All arrays are device memory owned by the caller; values of dtype
+ * NN_F64 or NN_F32 (else NN_ERR_ARG). Every call needs nn_csr_strip_workspace_bytes(n_local) of
+ * workspace; nn_csr_strip_diag_inv clears its error word, so call it first with the workspace.
+ *
+ * nn_csr_strip_diag_inv: dinv_local[i] = 1 / A_ii for the strip's rows (the entries with
+ *   col_local == i); NN_ERR_ARG if a row has no or a zero diagonal. Synchronises `stream`.
+ * nn_csr_strip_scale: val_scaled[e] = val[e] * dinv_ext[col_local[e]] (A' = A D^-1; dinv_ext is
+ *   dinv_local extended with the halo rows' values, exchanged like a vector).
+ * nn_csr_strip_product: y_i = v_ext[i] - sum_e val_scaled[e] v_ext[col_local[e]] for i < n_local
+ *   (the strip of P v); with acc_out, also acc_out = acc_in + y (acc_in may equal acc_out; y may
+ *   then be NULL), the factor accumulation of the chain. Only enqueues work.
+ * nn_csr_strip_residual: sums[0] = sum_i (b_i - (A' z)_i)^2, sums[1] = sum_i b_i^2 over the
+ *   strip (host array of two doubles; A x = A' z for x = D^-1 z); NN_ERR_TIMEOUT if a bounded
+ *   device wait of an earlier product or of this one ran past its limit. Synchronises `stream`.
+ * nn_csr_strip_finish: x_local = dinv_local * z_local. Only enqueues work. */
+size_t nn_csr_strip_workspace_bytes(int64_t n_local);
+int nn_csr_strip_diag_inv(const int32_t* row_ptr, const int32_t* col_local, const void* val, int64_t n_local,
+                          int64_t nnz, int dtype, void* dinv_local, void* workspace, size_t ws_bytes, void* stream);
+int nn_csr_strip_scale(const int32_t* col_local, const void* val, int64_t nnz, int dtype, const void* dinv_ext,
+                       void* val_scaled, void* stream);
+int nn_csr_strip_product(const int32_t* row_ptr, const int32_t* col_local, const void* val_scaled, int64_t n_local,
+                         int64_t nnz, int dtype, const void* v_ext, void* y, const void* acc_in, void* acc_out,
+                         void* workspace, size_t ws_bytes, void* stream);
+int nn_csr_strip_residual(const int32_t* row_ptr, const int32_t* col_local, const void* val_scaled, int64_t n_local,
+                          int64_t nnz, int dtype, const void* z_ext, const void* b_local, double* sums,
+                          void* workspace, size_t ws_bytes, void* stream);
+int nn_csr_strip_finish(const void* z_local, const void* dinv_local, int64_t n_local, int dtype, void* x_local,
+                        void* stream);
+
 /* ---- general systems through the normal equations ----------------------------------------
  * Corollary 3 (Eq. (linearsystemfinal), Eq. (nnlinearsystem)): A X = B for any nonsingular A,
  * real or complex, solved as X = (A^H A)^-1 A^H B. W = A^H A is Hermitian positive definite;

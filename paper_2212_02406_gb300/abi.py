@@ -117,6 +117,15 @@ _SIGNATURES = {
                                       c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "nn_invert_batched": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int, c_int, c_double, c_void_p,
                                   ctypes.c_uint32, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "nn_csr_strip_workspace_bytes": (c_size_t, [c_int64]),
+    "nn_csr_strip_diag_inv": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int, c_void_p, c_void_p,
+                                      c_size_t, c_void_p]),
+    "nn_csr_strip_scale": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_void_p, c_void_p, c_void_p]),
+    "nn_csr_strip_product": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int, c_void_p, c_void_p,
+                                     c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "nn_csr_strip_residual": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int, c_void_p, c_void_p,
+                                      POINTER(c_double), c_void_p, c_size_t, c_void_p]),
+    "nn_csr_strip_finish": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_void_p, c_void_p]),
     "nn_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_void_p, c_int64, c_int64, c_int, c_double,
                          POINTER(NNOpts), c_void_p, c_int64, POINTER(NNResult), c_void_p, c_size_t, c_void_p]),
     "nn_solve_csr": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int, c_void_p, c_int64, c_int64, c_int,
@@ -425,6 +434,53 @@ def nn_solve(row_ptr, col, val, B, depth, tol, opts, X, workspace, stream=None):
                         val.numel(), c_void_p(B.data_ptr()), ldb, nrhs, int(depth), float(tol), ctypes.byref(opts),
                         c_void_p(X.data_ptr()), ldx, ctypes.byref(res), pw, nw, _stream_ptr(stream))
     return st, res.as_dict()
+
+
+# ---- row strips of the sparse chain --------------------------------------------------------
+
+def _ptr(t):
+    return None if t is None else c_void_p(t.data_ptr())
+
+
+def nn_csr_strip_workspace_bytes(n_local: int) -> int:
+    return int(lib().nn_csr_strip_workspace_bytes(int(n_local)))
+
+
+def nn_csr_strip_diag_inv(row_ptr, col_local, val, dinv_local, workspace, stream=None) -> int:
+    """dinv_local = 1 / diag of the strip's rows (device tensors; val float64 or float32)."""
+    pw, nw = _ws(workspace)
+    return int(lib().nn_csr_strip_diag_inv(_ptr(row_ptr), _ptr(col_local), _ptr(val), row_ptr.numel() - 1,
+                                           val.numel(), _vec_dtype(val), _ptr(dinv_local), pw, nw,
+                                           _stream_ptr(stream)))
+
+
+def nn_csr_strip_scale(col_local, val, dinv_ext, val_scaled, stream=None) -> int:
+    return int(lib().nn_csr_strip_scale(_ptr(col_local), _ptr(val), val.numel(), _vec_dtype(val), _ptr(dinv_ext),
+                                        _ptr(val_scaled), _stream_ptr(stream)))
+
+
+def nn_csr_strip_product(row_ptr, col_local, val_scaled, v_ext, y, workspace, acc_in=None, acc_out=None,
+                         stream=None) -> int:
+    """y = v_ext[:n_local] - A'_strip v_ext (and acc_out = acc_in + y when acc_out is given)."""
+    pw, nw = _ws(workspace)
+    return int(lib().nn_csr_strip_product(_ptr(row_ptr), _ptr(col_local), _ptr(val_scaled), row_ptr.numel() - 1,
+                                          val_scaled.numel(), _vec_dtype(val_scaled), _ptr(v_ext), _ptr(y),
+                                          _ptr(acc_in), _ptr(acc_out), pw, nw, _stream_ptr(stream)))
+
+
+def nn_csr_strip_residual(row_ptr, col_local, val_scaled, z_ext, b_local, workspace, stream=None):
+    """(status, [sum r^2, sum b^2]) over the strip, r = b - A' z."""
+    pw, nw = _ws(workspace)
+    out = (c_double * 2)()
+    st = lib().nn_csr_strip_residual(_ptr(row_ptr), _ptr(col_local), _ptr(val_scaled), row_ptr.numel() - 1,
+                                     val_scaled.numel(), _vec_dtype(val_scaled), _ptr(z_ext), _ptr(b_local), out, pw,
+                                     nw, _stream_ptr(stream))
+    return int(st), [out[0], out[1]]
+
+
+def nn_csr_strip_finish(z_local, dinv_local, x_local, stream=None) -> int:
+    return int(lib().nn_csr_strip_finish(_ptr(z_local), _ptr(dinv_local), z_local.numel(), _vec_dtype(z_local),
+                                         _ptr(x_local), _stream_ptr(stream)))
 
 
 # ---- batched small complex inversions -------------------------------------------------------

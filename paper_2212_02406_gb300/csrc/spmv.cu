@@ -798,6 +798,48 @@ int solve_csr(const int* rp, const int* col, const typename P::In* val, int64_t 
   return res->status;
 }
 
+// Both sums of the residual partials (sum r^2, sum b^2), for an all-reduce across row strips.
+__global__ void reduce_pair_sums_kernel(const double* __restrict__ partial, int count, double* out) {
+  __shared__ double a[256], c[256];
+  double x = 0, y = 0;
+  for (int i = threadIdx.x; i < count; i += 256) {
+    x += partial[2 * i];
+    y += partial[2 * i + 1];
+  }
+  a[threadIdx.x] = x;
+  c[threadIdx.x] = y;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      a[threadIdx.x] += a[threadIdx.x + w];
+      c[threadIdx.x] += c[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = a[0];
+    out[1] = c[0];
+  }
+}
+
+// Workspace of the row-strip entry points: residual partials, two sums, the error word.
+struct StripWs {
+  double* partial;
+  double* sums;
+  int* err;
+};
+void carve_strip(Carver& c, int64_t n_local, StripWs& w) {
+  w.partial = c.take<double>(size_t(2 * ((n_local + SP_ROWS - 1) / SP_ROWS)));
+  w.sums = c.take<double>(2);
+  w.err = c.take<int>(8);
+}
+
+bool strip_args_ok(const int32_t* row_ptr, const int32_t* col, const void* val, int64_t n_local, int64_t nnz,
+                   int dtype) {
+  return row_ptr != nullptr && col != nullptr && val != nullptr && n_local >= 1 && n_local <= (int64_t(1) << 30) &&
+         nnz >= 0 && nnz <= (int64_t(1) << 31) - 1 && (dtype == NN_F64 || dtype == NN_F32);
+}
+
 size_t csr_ws_bytes(int64_t n, int64_t nnz, int64_t nrhs, int dtype) {
   Carver c(nullptr, 0);
   CsrWs w;
@@ -889,6 +931,128 @@ int nn_solve_csr_sched(const int32_t* row_ptr, const int32_t* col, const void* v
                        void* stream) {
   return solve_csr_any(row_ptr, col, val, n, nnz, dtype, B, ldb, nrhs, depths, nfactors, tol, X, ldx, res, workspace,
                        ws_bytes, stream);
+}
+
+size_t nn_csr_strip_workspace_bytes(int64_t n_local) {
+  if (n_local < 1 || n_local > (int64_t(1) << 30)) return 0;
+  Carver c(nullptr, 0);
+  StripWs w;
+  carve_strip(c, n_local, w);
+  return align_up(c.used, 256);
+}
+
+int nn_csr_strip_diag_inv(const int32_t* row_ptr, const int32_t* col_local, const void* val, int64_t n_local,
+                          int64_t nnz, int dtype, void* dinv_local, void* workspace, size_t ws_bytes, void* stream) {
+  if (!strip_args_ok(row_ptr, col_local, val, n_local, nnz, dtype) || dinv_local == nullptr) return NN_ERR_ARG;
+  Carver c(workspace, ws_bytes);
+  StripWs w;
+  carve_strip(c, n_local, w);
+  if (workspace == nullptr || !c.ok) return NN_ERR_OOM_BUDGET;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int n = int(n_local);
+  NN_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  if (dtype == NN_F64)
+    diag_inv_kernel<double><<<(n + 255) / 256, 256, 0, st>>>(n, row_ptr, col_local, static_cast<const double*>(val),
+                                                              static_cast<double*>(dinv_local), w.err);
+  else
+    diag_inv_kernel<float><<<(n + 255) / 256, 256, 0, st>>>(n, row_ptr, col_local, static_cast<const float*>(val),
+                                                             static_cast<float*>(dinv_local), w.err);
+  NN_CUDA_TRY(cudaGetLastError());
+  int e = DEV_OK;
+  NN_CUDA_TRY(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NN_CUDA_TRY(cudaStreamSynchronize(st));
+  return e == DEV_OK ? NN_OK : NN_ERR_ARG;
+}
+
+int nn_csr_strip_scale(const int32_t* col_local, const void* val, int64_t nnz, int dtype, const void* dinv_ext,
+                       void* val_scaled, void* stream) {
+  if (col_local == nullptr || val == nullptr || dinv_ext == nullptr || val_scaled == nullptr || nnz < 0 ||
+      nnz > (int64_t(1) << 31) - 1 || (dtype != NN_F64 && dtype != NN_F32))
+    return NN_ERR_ARG;
+  if (nnz == 0) return NN_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const unsigned blocks = unsigned((nnz + 255) / 256);
+  if (dtype == NN_F64)
+    scale_cols_kernel<ArithF64><<<blocks, 256, 0, st>>>(nnz, col_local, static_cast<const double*>(val),
+                                                        static_cast<const double*>(dinv_ext),
+                                                        static_cast<double*>(val_scaled));
+  else
+    scale_cols_kernel<ArithF32><<<blocks, 256, 0, st>>>(nnz, col_local, static_cast<const float*>(val),
+                                                        static_cast<const float*>(dinv_ext),
+                                                        static_cast<float*>(val_scaled));
+  NN_CUDA_TRY(cudaGetLastError());
+  return NN_OK;
+}
+
+int nn_csr_strip_product(const int32_t* row_ptr, const int32_t* col_local, const void* val_scaled, int64_t n_local,
+                         int64_t nnz, int dtype, const void* v_ext, void* y, const void* acc_in, void* acc_out,
+                         void* workspace, size_t ws_bytes, void* stream) {
+  if (!strip_args_ok(row_ptr, col_local, val_scaled, n_local, nnz, dtype) || v_ext == nullptr) return NN_ERR_ARG;
+  if (y == nullptr && acc_out == nullptr) return NN_ERR_ARG;
+  if (acc_out != nullptr && acc_in == nullptr) return NN_ERR_ARG;
+  Carver c(workspace, ws_bytes);
+  StripWs w;
+  carve_strip(c, n_local, w);
+  if (workspace == nullptr || !c.ok) return NN_ERR_OOM_BUDGET;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int mode = acc_out == nullptr ? SP_Y : (y == nullptr ? SP_ACC : SP_Y_ACC);
+  if (dtype == NN_F64)
+    return spmv<ArithF64>(st, int(n_local), int(nnz), row_ptr, col_local, static_cast<const double*>(val_scaled),
+                          static_cast<const double*>(v_ext), static_cast<double*>(y),
+                          static_cast<const double*>(acc_in), static_cast<double*>(acc_out), nullptr, 0, 1, mode,
+                          nullptr, w.err);
+  return spmv<ArithF32>(st, int(n_local), int(nnz), row_ptr, col_local, static_cast<const float*>(val_scaled),
+                        static_cast<const float*>(v_ext), static_cast<float*>(y), static_cast<const float*>(acc_in),
+                        static_cast<float*>(acc_out), nullptr, 0, 1, mode, nullptr, w.err);
+}
+
+int nn_csr_strip_residual(const int32_t* row_ptr, const int32_t* col_local, const void* val_scaled, int64_t n_local,
+                          int64_t nnz, int dtype, const void* z_ext, const void* b_local, double* sums,
+                          void* workspace, size_t ws_bytes, void* stream) {
+  if (!strip_args_ok(row_ptr, col_local, val_scaled, n_local, nnz, dtype) || z_ext == nullptr ||
+      b_local == nullptr || sums == nullptr)
+    return NN_ERR_ARG;
+  Carver c(workspace, ws_bytes);
+  StripWs w;
+  carve_strip(c, n_local, w);
+  if (workspace == nullptr || !c.ok) return NN_ERR_OOM_BUDGET;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int n = int(n_local);
+  const int blocks = (n + SP_ROWS - 1) / SP_ROWS;
+  if (dtype == NN_F64)
+    NN_TRY(spmv<ArithF64>(st, n, int(nnz), row_ptr, col_local, static_cast<const double*>(val_scaled),
+                          static_cast<const double*>(z_ext), nullptr, nullptr, nullptr,
+                          static_cast<const double*>(b_local), n, 1, SP_RESID, w.partial, w.err));
+  else
+    NN_TRY(spmv<ArithF32>(st, n, int(nnz), row_ptr, col_local, static_cast<const float*>(val_scaled),
+                          static_cast<const float*>(z_ext), nullptr, nullptr, nullptr,
+                          static_cast<const float*>(b_local), n, 1, SP_RESID, w.partial, w.err));
+  reduce_pair_sums_kernel<<<1, 256, 0, st>>>(w.partial, blocks, w.sums);
+  NN_CUDA_TRY(cudaGetLastError());
+  int e = DEV_OK;
+  NN_CUDA_TRY(cudaMemcpyAsync(sums, w.sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  NN_CUDA_TRY(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  NN_CUDA_TRY(cudaStreamSynchronize(st));
+  return e == DEV_OK ? NN_OK : NN_ERR_TIMEOUT;
+}
+
+int nn_csr_strip_finish(const void* z_local, const void* dinv_local, int64_t n_local, int dtype, void* x_local,
+                        void* stream) {
+  if (z_local == nullptr || dinv_local == nullptr || x_local == nullptr || n_local < 1 ||
+      n_local > (int64_t(1) << 30) || (dtype != NN_F64 && dtype != NN_F32))
+    return NN_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int n = int(n_local);
+  if (dtype == NN_F64)
+    store_cols_kernel<ArithF64><<<dim3((n + 255) / 256, 1), 256, 0, st>>>(
+        n, 1, static_cast<const double*>(z_local), static_cast<const double*>(dinv_local),
+        static_cast<double*>(x_local), n);
+  else
+    store_cols_kernel<ArithF32><<<dim3((n + 255) / 256, 1), 256, 0, st>>>(
+        n, 1, static_cast<const float*>(z_local), static_cast<const float*>(dinv_local), static_cast<float*>(x_local),
+        n);
+  NN_CUDA_TRY(cudaGetLastError());
+  return NN_OK;
 }
 
 int nn_solve(const int32_t* row_ptr, const int32_t* col, const void* val, int64_t n, int64_t nnz, const void* B,

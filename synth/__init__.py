@@ -172,6 +172,34 @@ def mimo_gram_batch(count: int, seed: int = 0, sigma2: float = 0.1,
     return MimoBatch(out, offs, us)
 
 
+def mimo_sizes(count: int, seed: int = 0, sizes=MIMO_SIZES) -> np.ndarray:
+    """The U_b of a batch of ``count`` matrices drawn uniformly over ``sizes`` (first draw of the
+    indexed recipe below)."""
+    return rng(seed).choice(np.asarray(sizes, dtype=np.int64), size=count)
+
+
+def mimo_gram_indexed(indices, sizes_all: np.ndarray, seed: int = 0, sigma2: float = 0.1,
+                      antennas: int = MIMO_ANTENNAS, dtype=np.complex64) -> MimoBatch:
+    """The matrices ``indices`` of a batch whose sizes are ``sizes_all``, each from its own stream
+    PCG64([seed, b]) (so any subset is generated alone, e.g. one rank's share of a sharded batch):
+    H_b with CN(0,1) entries, A_b = H_b^H H_b + sigma2 I in complex128, rounded once."""
+    idx = np.asarray(indices, dtype=np.int64)
+    us = np.asarray(sizes_all)[idx].astype(np.int64)
+    offs = np.zeros(len(idx), dtype=np.int64)
+    if len(idx) > 1:
+        offs[1:] = np.cumsum(us[:-1] * us[:-1])
+    out = np.empty(int(np.sum(us * us)), dtype=dtype)
+    for k, b in enumerate(idx):
+        u = int(us[k])
+        r = np.random.Generator(np.random.PCG64([seed, int(b)]))
+        h = (r.standard_normal((antennas, u)) + 1j * r.standard_normal((antennas, u))) / math.sqrt(2.0)
+        a = h.conj().T @ h
+        a = 0.5 * (a + a.conj().T)
+        a[np.diag_indices(u)] = a[np.diag_indices(u)].real + sigma2
+        out[offs[k]:offs[k] + u * u] = a.astype(dtype).reshape(-1)
+    return MimoBatch(out, offs, us)
+
+
 @dataclass
 class Csr:
     """Compressed sparse row matrix with int32 indices (n rows, n columns)."""

@@ -207,3 +207,53 @@ def test_solve_interface_equals_csr_entry_and_oracle(nn, dtype, sched):
     terms = int(np.prod([d + 1 for d in depths])) - 1
     nnz_row = int(np.max(np.diff(m.row_ptr)))
     assert err <= max(8 * terms * U[dtype] * (nnz_row + 1), 1e-13), err
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("world", [2, 3])
+def test_row_strips_equal_single_chain_bitwise(nn, dtype, world):
+    # The row-strip entry points (nn_csr_strip_*) driven by the sharded host loop, with the halos
+    # copied in-process between strips on this GPU: each strip row sums its terms in the order of
+    # the single-GPU chain's row, and the loop applies the same products and accumulations, so
+    # X must equal nn_solve_csr_sched's bit for bit (Corollary 1 applied per strip).
+    import torch
+
+    from paper_2212_02406_gb300 import shard
+
+    npd = NP[dtype]
+    m = synth.laplacian_5pt(41, 37, shift=0.5)
+    b = synth.gaussian_rhs(m.n, 1, seed=12)[:, 0].astype(npd)
+    depths = [2, 2, 1]
+    plans = shard.build_halo_plans(m.row_ptr, m.col, shard.partition_rows_by_nnz(m.row_ptr, world))
+    strips = [shard.CudaStrip(p, m.row_ptr, m.val.astype(npd), "cuda") for p in plans]
+    ex = shard.LocalExchange(plans, "cuda")
+    shard.setup_strips(strips, ex)
+    xs, rel = shard.sharded_sparse_chain(strips, ex, [torch.from_numpy(b[p.r0:p.r1].copy()).cuda() for p in plans],
+                                         depths)
+    torch.cuda.synchronize()
+    x = torch.cat(xs).cpu().numpy()
+    rp = torch.from_numpy(m.row_ptr.astype(np.int32)).cuda()
+    col = torch.from_numpy(m.col.astype(np.int32)).cuda()
+    val = torch.from_numpy(m.val.astype(npd)).cuda()
+    B = torch.from_numpy(b[None, :].copy()).cuda()
+    X = torch.empty_like(B)
+    st, res = nn.nn_solve_csr_sched(rp, col, val, B, depths, 0.0, X, nn.csr_workspace(m.n, m.nnz, 1, dtype))
+    torch.cuda.synchronize()
+    assert st == nn.NN_OK
+    assert np.array_equal(x, X.cpu().numpy()[0])
+    assert abs(rel - res["residual"]) <= 1e-8 * res["residual"] + {"f64": 1e-14, "f32": 1e-6}[dtype]
+
+
+def test_row_strip_entry_points_reject_bad_arguments(nn):
+    import torch
+
+    ws = torch.empty(nn.nn_csr_strip_workspace_bytes(8), dtype=torch.uint8, device="cuda")
+    rp = torch.zeros(9, dtype=torch.int32, device="cuda")
+    col = torch.zeros(0, dtype=torch.int32, device="cuda")
+    val = torch.zeros(0, dtype=torch.float64, device="cuda")
+    dinv = torch.empty(8, dtype=torch.float64, device="cuda")
+    # rows without a diagonal entry
+    assert nn.nn_csr_strip_diag_inv(rp, col, val, dinv, ws) == nn.NN_ERR_ARG
+    v = torch.zeros(8, dtype=torch.float64, device="cuda")
+    # neither y nor an accumulator to write
+    assert nn.nn_csr_strip_product(rp, col, val, v, None, ws) == nn.NN_ERR_ARG

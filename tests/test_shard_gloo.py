@@ -143,3 +143,61 @@ def test_sharded_batch_gathers_full_result():
     for part, vals in zip(parts, gathered):
         for i, v in zip(part, vals):
             assert abs(v - full[i].history[-1]) <= 1e-15 * max(1.0, abs(v))
+
+
+def _strip_chain_worker(rank, world, port, out):
+    # the host loop of the strip-sharded chain (sharded_sparse_chain) with the host stand-in of
+    # the library's strip calls, halos exchanged between gloo ranks (DistExchange)
+    import torch
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        m = synth.laplacian_5pt(23, 17, shift=0.5)
+        b = synth.gaussian_rhs(m.n, 1, seed=6)[:, 0]
+        ranges = shard.partition_rows_by_nnz(m.row_ptr, world)
+        plans = shard.build_halo_plans(m.row_ptr, m.col, ranges)
+        p = plans[rank]
+        strip = shard.HostStrip(p, m.row_ptr, m.val)
+        ex = shard.DistExchange(p, "cpu")
+        shard.setup_strips([strip], ex)
+        xs, rel = shard.sharded_sparse_chain([strip], ex, [torch.from_numpy(b[p.r0:p.r1].copy())], [2, 2, 1],
+                                             allreduce=shard.allreduce_sum)
+        out[rank] = (p.r0, p.r1, xs[0].numpy(), rel)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_strip_sharded_chain_two_ranks_matches_oracle():
+    out = _spawn(_strip_chain_worker, world=2)
+    m = synth.laplacian_5pt(23, 17, shift=0.5)
+    b = synth.gaussian_rhs(m.n, 1, seed=6)[:, 0]
+    x = np.empty(m.n)
+    rels = set()
+    for r0, r1, xl, rel in out.values():
+        x[r0:r1] = xl
+        rels.add(round(rel, 12))
+    want = sparse.nn_sparse_solve_sched(m.to_scipy(), b[:, None], [2, 2, 1])[:, 0]
+    assert np.linalg.norm(x - want) <= 1e-13 * np.linalg.norm(want)
+    assert len(rels) == 1  # one all-reduced residual on both ranks
+    assert abs(rels.pop() - sparse.relative_residual(m.to_scipy(), want[:, None], b[:, None])) <= 1e-10
+
+
+@pytest.mark.parametrize("world", [1, 3, 4])
+def test_strip_chain_in_one_process_matches_oracle(world):
+    # several strips held by one process, halos copied in-process (LocalExchange): the same loop
+    import torch
+
+    m = synth.random_sparse_spd(300, 6, seed=9)
+    b = synth.gaussian_rhs(m.n, 1, seed=4)[:, 0]
+    plans = shard.build_halo_plans(m.row_ptr, m.col, shard.partition_rows_by_nnz(m.row_ptr, world))
+    strips = [shard.HostStrip(p, m.row_ptr, m.val) for p in plans]
+    ex = shard.LocalExchange(plans, "cpu")
+    shard.setup_strips(strips, ex)
+    xs, rel = shard.sharded_sparse_chain(strips, ex, [torch.from_numpy(b[p.r0:p.r1].copy()) for p in plans], [2, 2])
+    x = np.concatenate([t.numpy() for t in xs])
+    want = sparse.nn_sparse_solve(m.to_scipy(), b[:, None], 2, 2)[:, 0]
+    assert np.linalg.norm(x - want) <= 1e-13 * np.linalg.norm(want)
+    assert abs(rel - sparse.relative_residual(m.to_scipy(), want[:, None], b[:, None])) <= 1e-10
