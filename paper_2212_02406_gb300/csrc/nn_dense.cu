@@ -10,6 +10,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -181,26 +182,65 @@ void init_result(nn_result* r) {
 }
 
 // CUDA events around each GEMM launch of a chain (NN_FLAG_TIME_KERNELS).
+// Timing events are reused across calls (per device): creating two per GEMM in every call
+// cost host time between the launches of a nest.
+std::mutex g_ev_mu;
+std::vector<std::pair<int, cudaEvent_t>> g_ev_pool;  // (device, event)
+
+int event_take(cudaEvent_t* e) {
+  int dev = 0;
+  NN_CUDA_TRY(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lock(g_ev_mu);
+    for (size_t i = g_ev_pool.size(); i-- > 0;) {
+      if (g_ev_pool[i].first == dev) {
+        *e = g_ev_pool[i].second;
+        g_ev_pool.erase(g_ev_pool.begin() + ptrdiff_t(i));
+        return NN_OK;
+      }
+    }
+  }
+  NN_CUDA_TRY(cudaEventCreate(e));
+  return NN_OK;
+}
+
+void event_give(cudaEvent_t e) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    cudaEventDestroy(e);
+    return;
+  }
+  std::lock_guard<std::mutex> lock(g_ev_mu);
+  if (g_ev_pool.size() < 4096)
+    g_ev_pool.emplace_back(dev, e);
+  else
+    cudaEventDestroy(e);
+}
+
 struct LaunchTimer {
   bool on = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   ~LaunchTimer() {
     for (auto& e : ev) {
-      cudaEventDestroy(e.first);
-      cudaEventDestroy(e.second);
+      event_give(e.first);
+      event_give(e.second);
     }
+  }
+  int pair(cudaEvent_t* a, cudaEvent_t* b) {
+    NN_TRY(event_take(a));
+    if (event_take(b) != NN_OK) {
+      event_give(*a);
+      return NN_ERR_CUDA;
+    }
+    ev.emplace_back(*a, *b);
+    return NN_OK;
   }
   // Events around a whole product (several launches: CUDA-core and emulated FP64 products).
   int begin(cudaStream_t st) {
     if (!on) return NN_OK;
     cudaEvent_t a, b;
-    NN_CUDA_TRY(cudaEventCreate(&a));
-    if (cudaEventCreate(&b) != cudaSuccess) {
-      cudaEventDestroy(a);
-      (void)cudaGetLastError();
-      return NN_ERR_CUDA;
-    }
-    ev.emplace_back(a, b);
+    NN_TRY(pair(&a, &b));
     NN_CUDA_TRY(cudaEventRecord(a, st));
     return NN_OK;
   }
@@ -213,13 +253,7 @@ struct LaunchTimer {
   int arm(TcGemmArgs& g) {
     if (!on) return NN_OK;
     cudaEvent_t a, b;
-    NN_CUDA_TRY(cudaEventCreate(&a));
-    if (cudaEventCreate(&b) != cudaSuccess) {
-      cudaEventDestroy(a);
-      (void)cudaGetLastError();
-      return NN_ERR_CUDA;
-    }
-    ev.emplace_back(a, b);
+    NN_TRY(pair(&a, &b));
     g.ev_before = a;
     g.ev_after = b;
     return NN_OK;
@@ -239,10 +273,10 @@ struct LaunchTimer {
 // ---------------------------------------------------------------------------------------
 // CUDA-core chains (FP64 / FP32).
 
-// The GEMM of a CUDA-core-style chain: C = mode(A B) with Σ C^2 partials (count in *nparts).
 // Role of a product in the nest, for arithmetics whose precision can follow it.
 enum ProductRole { ROLE_RESIDUAL = 0, ROLE_HORNER = 1, ROLE_UPDATE = 2 };
 
+// The GEMM of a CUDA-core-style chain: C = mode(A B) with Σ C^2 partials (count in *nparts).
 template <typename T>
 struct SimtGemm {
   cudaStream_t st;
