@@ -327,11 +327,11 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
 //         D (2U x 2U) = [Pr; Pi] (2U x U) . [Qr | Qi] (U x 2U)
 //           = [[Pr Qr, Pr Qi], [Pi Qr, Pi Qi]],   Cr = Pr Qr - Pi Qi,  Ci = Pi Qr + Pr Qi,
 //     i.e. M = 128 (2U rows used, in the lanes' order), N = 2U, K = U. The left operand's rows
-//     are P's master lanes; the right operand (K-major: row n < U = column n of Qr, row U + n =
-//     column n of Qi) is the transpose of Q's master. A's left operand is split once per matrix
-//     and kept in shared memory (one copy per slot);
+//     are P's master lanes (K-major); the right operand is MN-major, its row k being master row
+//     k of Q (real part at N < U, imaginary part at N >= U), so each lane stages its own values.
+//     A's left operand is split once per matrix and kept in shared memory (one copy per slot);
 //   * operands are split into three BF16 pieces (x = p0 + p1 + p2, each the BF16 rounding of the
-//     remainder) and written in the SWIZZLE_128B K-major layout; the six piece products with
+//     remainder) and written in SWIZZLE_128B layouts; the six piece products with
 //     i + j <= 2 (smallest first) accumulate in FP32 in TMEM, which matches an FP32 product to
 //     about 2^-24 relative;
 //   * epilogue: the real-part lane of a row needs Pi Qi and the imaginary-part lane Pr Qi, each
@@ -341,7 +341,10 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
 //   * the two slots alternate: 16 worker warps stage one slot's product and hand it to a 17th
 //     warp that only issues its MMA chain; while the tensor core runs it, the workers finish
 //     the other slot's previous product, then stage that slot's next product once the MMAs
-//     (which read the single staging buffers) have completed.
+//     (which read the single staging buffers) have completed;
+//   * an 18th warp claims each slot's next matrix ahead of time (the item queue's atomic and the
+//     plan's dependent reads) and pulls it toward L2, handing it over through a mailbox in
+//     shared memory; the workers read a new matrix in coalesced row segments.
 namespace btc {
 constexpr int M = 128;                         // MMA rows (2U used)
 constexpr int CW = 16;                         // master columns per warp (TMEM access: 32 lanes x 16)
@@ -353,6 +356,7 @@ constexpr int A_CACHE = 0;                     // the slots' left operands of A:
 constexpr int L_STAGE = 2 * OPND;              // staged left operand
 constexpr int B_STAGE = 3 * OPND;              // staged right operand
 constexpr int OPS_BYTES = 4 * OPND;
+constexpr int BLOCK = THREADS + 64;            // workers, the MMA warp, the claimer warp
 constexpr uint32_t SLOT_COLS = 256;            // TMEM columns per slot
 constexpr uint32_t MX = 0, MR = 64, ACC = 128;
 constexpr uint32_t MT = 256;                   // T master (depth >= 3: one slot only)
@@ -395,6 +399,24 @@ __device__ __forceinline__ uint64_t bt_sw128_desc(uint32_t saddr) {
 // 16-byte chunk c of row r sits at chunk c ^ (r mod 8) of its 128-byte line.
 __device__ __forceinline__ uint32_t bt_sw128_offset(int r, int kk) {
   return uint32_t((r >> 3) * 1024 + (r & 7) * 128 + (((kk >> 3) ^ (r & 7)) << 4) + ((kk & 7) << 1));
+}
+
+// The right operand B = [Qr | Qi] (K = U rows, N = 2U columns) is staged MN-major: B's row k is
+// master row k of Q (its real part in columns 0..U-1, its imaginary part in U..2U-1), so each lane
+// writes its own master values with no transposition. SWIZZLE_128B MN-major atoms hold 8 rows (K)
+// x 64 elements (N); atoms along N sit BT_MN_LBO apart (the leading byte offset), along K
+// BT_MN_SBO apart (the stride byte offset), so one piece (K <= 64, N <= 128) spans 16 KB. Were
+// the two offsets read the other way round, every access would still stay inside the piece.
+constexpr uint32_t BT_MN_LBO = 1024, BT_MN_SBO = 2048;
+__device__ __forceinline__ uint64_t bt_sw128_mn_desc(uint32_t saddr) {
+  return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t(BT_MN_LBO >> 4) << 16) | (uint64_t(BT_MN_SBO >> 4) << 32) |
+         (uint64_t(1) << 46) | (uint64_t(2) << 61);
+}
+// Byte offset of element (k, n) of an MN-major SWIZZLE_128B operand: 16-byte chunk c of a row's
+// 64-element span sits at chunk c ^ (k mod 8).
+__device__ __forceinline__ uint32_t bt_mn_offset(int k, int n) {
+  return uint32_t((k >> 3) * int(BT_MN_SBO) + (n >> 6) * int(BT_MN_LBO) + (k & 7) * 128 +
+                  ((((n >> 3) & 7) ^ (k & 7)) << 4) + ((n & 7) << 1));
 }
 
 // Three BF16 pieces of the pair (a, b) (a in the low halves): each piece is the BF16 rounding
@@ -442,60 +464,64 @@ __device__ __forceinline__ void tc_row_pieces(const uint32_t (&v)[btc::CW], uint
   }
 }
 
-// Right operand [Qr | Qi] (K-major) from master Q values raw (this thread's lane l, columns
-// h CW ..): row i's real part, column c goes to row c, column k = i; its imaginary part to row
-// U + c, column k = i. The pair (k, k + 1) (k even; lanes l and l + 2) of a column is split and
-// stored by row k's lane for the first CW/2 columns of the warp's block and by row k + 1's lane
-// for the rest. The four kinds of lanes (real / imaginary part, row k / k + 1) take their
-// columns in rotated orders so that the four rows one store instruction writes fall in four
-// different swizzle phases (no bank conflicts). Every lane of the warp calls it (shuffles).
+// N position of column j of Qi in the right operand, minus U: for U = 64 the 32-column halves
+// are swapped (j ^ 32), which puts the real- and imaginary-part chunks that the two lanes of a
+// row store at the same time into different swizzle phases (no bank conflicts); for U = 48 the
+// imaginary-part lanes take their chunks in the other order instead.
 template <int U>
-__device__ __forceinline__ void tc_right_pieces(const uint32_t (&raw)[btc::CW], uint8_t* dst, int h, int l) {
-  int i;
-  bool im;
-  const bool store = tc_lane_row<U>(l, i, im);  // rows (i, i + 1) of one part sit in lanes (l, l + 2)
-  const bool upper = (i & 1) != 0;
-  const int kk = i & ~1;
-  const int row8 = ((im ? U : 0) + h * btc::CW + (upper ? btc::CW / 2 : 0)) >> 3;
-  uint8_t* base = dst + row8 * 1024 + ((kk & 7) << 1);
-  const int kc = kk >> 3;
-#pragma unroll
-  for (int t = 0; t < btc::CW / 2; ++t) {
-    // column offsets within the half: real rows k: t, imaginary rows k: t + 4, real rows k + 1:
-    // t + 2, imaginary rows k + 1: t + 6 (mod 8)
-    const int lo_re = t, lo_im = (t + 4) & 7, up_re = (t + 2) & 7, up_im = (t + 6) & 7;
-    const float x1 = __uint_as_float(im ? raw[lo_im] : raw[lo_re]);
-    const float x2 = __uint_as_float(im ? raw[btc::CW / 2 + up_im] : raw[btc::CW / 2 + up_re]);
-    const float from_upper = __shfl_down_sync(0xffffffffu, x1, 2);  // row k + 1, the column of row k
-    const float from_lower = __shfl_up_sync(0xffffffffu, x2, 2);    // row k, the column of row k + 1
-    if (store) {
-      uint32_t w0, w1, w2;
-      split3x2(upper ? from_lower : x1, upper ? x2 : from_upper, w0, w1, w2);
-      const int c = upper ? (im ? up_im : up_re) : (im ? lo_im : lo_re);  // row8 * 8 + c, c < 8
-      uint8_t* at = base + c * 128 + ((kc ^ c) << 4);
-      *reinterpret_cast<uint32_t*>(at) = w0;
-      *reinterpret_cast<uint32_t*>(at + btc::PIECE) = w1;
-      *reinterpret_cast<uint32_t*>(at + 2 * btc::PIECE) = w2;
-    }
-  }
+__device__ __forceinline__ int tc_imag_col(int j) {
+  return U == 64 ? (j ^ 32) : j;
 }
 
-// Stages one product: the left operand [Pr; Pi] from master P (operand row = master lane; not for
-// the residual, whose left operand is A's cached pieces) and the right operand from master Q;
-// warp (q, h) owns lanes 32q.. and columns h CW...
+// Stages one product: the right operand [Qr | Qi] (MN-major, see above) from master Q and, unless
+// the product is the residual (whose left operand is A's cached pieces), the left operand
+// [Pr; Pi] (K-major, operand row = master lane) from master P. Warp (q, h) owns lanes 32q.. and
+// master columns h CW..: lane (i, part) holds row i of one part of each master, which is B's
+// row i at N = h CW.. (real part) or U + tc_imag_col(h CW..) (imaginary part). When P and Q
+// are the same master (the first Horner product, T_1 = R), each value is split once for both.
 template <int U>
 __device__ __forceinline__ void tc_stage(uint32_t tmem, bool left, uint32_t cP, uint32_t cQ, uint8_t* ldst,
                                          uint8_t* bdst, int q, int h, int l) {
+  static_assert(U % btc::CW == 0 && btc::CW == 16, "whole 16-column blocks, two 8-column chunks each");
   if (h * btc::CW >= U) return;
   const uint32_t lane_off = uint32_t(q * 32) << 16;
-  uint32_t rp[btc::CW], rq[btc::CW];
-  if (left) tmem_ld_cw(tmem + lane_off + cP + uint32_t(h * btc::CW), rp);
-  tmem_ld_cw(tmem + lane_off + cQ + uint32_t(h * btc::CW), rq);
-  tmem_ld_wait();
+  const bool same = left && cP == cQ;
   int i;
   bool im;
-  if (left && tc_lane_row<U>(l, i, im)) tc_row_pieces<U>(rp, ldst, l, h * btc::CW);
-  tc_right_pieces<U>(rq, bdst, h, l);
+  const bool valid = tc_lane_row<U>(l, i, im);
+  const bool rev = U == 48 && im;
+  uint32_t r[btc::CW];
+  // the right operand (and, for P = Q, the left one from the same pieces), then the left one
+  tmem_ld_cw(tmem + lane_off + cQ + uint32_t(h * btc::CW), r);
+  tmem_ld_wait();
+  if (valid) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int j0 = h * btc::CW + (rev ? 1 - t : t) * 8;  // master columns j0 .. j0 + 7
+      uint32_t w[3][4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const uint32_t a = rev ? r[(1 - t) * 8 + 2 * e] : r[t * 8 + 2 * e];
+        const uint32_t b = rev ? r[(1 - t) * 8 + 2 * e + 1] : r[t * 8 + 2 * e + 1];
+        split3x2(__uint_as_float(a), __uint_as_float(b), w[0][e], w[1][e], w[2][e]);
+      }
+      const uint32_t boff = bt_mn_offset(i, im ? U + tc_imag_col<U>(j0) : j0);
+#pragma unroll
+      for (int pc = 0; pc < 3; ++pc)
+        *reinterpret_cast<uint4*>(bdst + pc * btc::PIECE + boff) = make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
+      if (same) {
+        const uint32_t loff = bt_sw128_offset(l, j0);
+#pragma unroll
+        for (int pc = 0; pc < 3; ++pc)
+          *reinterpret_cast<uint4*>(ldst + pc * btc::PIECE + loff) = make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
+      }
+    }
+  }
+  if (left && !same) {
+    tmem_ld_cw(tmem + lane_off + cP + uint32_t(h * btc::CW), r);
+    tmem_ld_wait();
+    if (valid) tc_row_pieces<U>(r, ldst, l, h * btc::CW);
+  }
 }
 
 // One thread: the MMA chain D = L B^T (K = U) into d_tmem, piece pairs (a, b) smallest terms
@@ -504,7 +530,12 @@ template <int U>
 __device__ __forceinline__ void tc_issue(uint32_t d_tmem, uint32_t l_saddr, uint32_t b_saddr) {
   constexpr uint32_t idesc =
       (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t((2 * U) >> 3) << 17) | (uint32_t(btc::M >> 4) << 24);
-  const uint64_t ld = bt_sw128_desc(l_saddr), bd = bt_sw128_desc(b_saddr);
+  // bit 16: B is MN-major; a K = 16 step advances A by 32 bytes within its 128-byte lines and
+  // B by two 8-row K-atoms
+  constexpr uint32_t idesc_b = idesc | (1u << 16);
+  constexpr uint64_t b_step = (2 * BT_MN_SBO) >> 4;
+  const uint64_t ld = bt_sw128_desc(l_saddr);
+  const uint64_t bd = bt_sw128_mn_desc(b_saddr);
 #pragma unroll
   for (int pp = 0; pp < 6; ++pp) {
     const int pa = pp == 0 ? 2 : (pp == 1 || pp == 3) ? 1 : 0;
@@ -512,7 +543,7 @@ __device__ __forceinline__ void tc_issue(uint32_t d_tmem, uint32_t l_saddr, uint
 #pragma unroll
     for (int st = 0; st < U / 16; ++st)
       tc_mma_bf16(d_tmem, ld + uint64_t((pa * btc::PIECE) >> 4) + uint64_t(2 * st),
-                  bd + uint64_t((pb * btc::PIECE) >> 4) + uint64_t(2 * st), idesc, (pp | st) != 0 ? 1u : 0u);
+                  bd + uint64_t((pb * btc::PIECE) >> 4) + b_step * uint64_t(st), idesc_b, (pp | st) != 0 ? 1u : 0u);
   }
 }
 
@@ -539,7 +570,7 @@ __device__ __forceinline__ float tc_epilogue(uint32_t tmem, uint32_t cAcc, uint3
     const uint32_t col = uint32_t(h * btc::CW + ph * (btc::CW / 2));
     uint32_t dd[8], dx[8], dm[8];
     tmem_ld_32x32b_x8(tmem + lane_off + cAcc + col, dd);
-    tmem_ld_32x32b_x8(tmem + lane_off + cAcc + uint32_t(U) + col, dx);
+    tmem_ld_32x32b_x8(tmem + lane_off + cAcc + uint32_t(U + tc_imag_col<U>(int(col))), dx);
     if (mode == BM_ADD) tmem_ld_32x32b_x8(tmem + lane_off + cD + col, dm);
     tmem_ld_wait();
 #pragma unroll
@@ -574,62 +605,194 @@ __device__ __forceinline__ float bt_block_sum(float v, float* red_warp) {
   return t;
 }
 
-// A new matrix into a slot: A (U x U complex, row-major) is read coalesced into the slot's
-// cache area (free: its previous matrix is done) with rows padded to 2U + 1 floats, so that the
-// threads of a warp (consecutive rows) read their row parts without bank conflicts; after a CTA
-// barrier the pieces of A's left operand [Ar; Ai] overwrite the area; X_0 = c diag(A)^-1
-// (damped Jacobi) goes to the X master at column cX (padding lanes zero). Every worker thread
-// calls it.
+// The claimer warp hands the workers their next item through a one-entry mailbox in shared
+// memory: full = 1 once it has claimed an item (it, its matrix index b and offset off; b = -1
+// for it >= last) and pulled the item's matrix toward L2; the workers set full = 0 once they have
+// taken it. exit = 1 (set by the workers) ends the claimer.
+struct TcMailbox {
+  long long off;
+  int full, it, b, exit;
+};
+__device__ __forceinline__ int ld_acquire_shared(const int* a) {
+  int v;
+  asm volatile("ld.acquire.cta.shared.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32(a)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_shared(int* a, int v) {
+  asm volatile("st.release.cta.shared.b32 [%0], %1;" ::"r"(smem_u32(a)), "r"(v) : "memory");
+}
+// Bounded wait (one thread) for a full mailbox; false (a timeout recorded as by mbar_wait) if it
+// stayed empty past the wait limit or another role gave up.
+__device__ __forceinline__ bool tc_wait_full(TcMailbox* mb, int* abort_word, int* err) {
+  if (ld_acquire_shared(&mb->full)) return true;
+  const unsigned long long t0 = global_ns();
+  uint32_t spins = 0;
+  while (true) {
+    if (ld_acquire_shared(&mb->full)) return true;
+    if ((++spins & 15u) == 0) {
+      if (*reinterpret_cast<volatile int*>(abort_word)) return false;
+      if (global_ns() - t0 > kWaitLimitNs) {
+        *reinterpret_cast<volatile int*>(abort_word) = 1;
+        atomicExch(err, DEV_TIMEOUT);
+        return false;
+      }
+    }
+    __nanosleep(32);
+  }
+}
+
+// The claimer warp: claims the next item of this class whenever the mailbox is empty and
+// prefetches its matrix into L2 (one prefetch per 128-byte line, every address inside the
+// matrix), so that the dependent reads of the plan and most of the matrix's global latency stay
+// off the workers' path. Items it claims are always delivered (the workers take every full
+// mailbox). Returns when the workers set exit, or (recording a timeout) when nothing empties the
+// mailbox within the wait limit.
+template <int U>
+__device__ __forceinline__ void tc_claimer(const BatchedParams& p, int cls, int first, int last,
+                                           const int32_t* items, TcMailbox* mb, int* abort_word) {
+  const int lane = int(threadIdx.x & 31);
+  while (true) {
+    int state = 0;  // 0: empty (claim), 1: exit, 2: gave up
+    if (lane == 0) {
+      unsigned long long t0 = 0;
+      uint32_t spins = 0;
+      while (true) {
+        if (*reinterpret_cast<volatile int*>(&mb->exit)) {
+          state = 1;
+          break;
+        }
+        if (ld_acquire_shared(&mb->full) == 0) break;
+        if (spins++ == 0) t0 = global_ns();
+        if ((spins & 15u) == 0) {
+          if (*reinterpret_cast<volatile int*>(abort_word)) {
+            state = 2;
+            break;
+          }
+          if (global_ns() - t0 > kWaitLimitNs) {
+            *reinterpret_cast<volatile int*>(abort_word) = 1;
+            atomicExch(p.err, DEV_TIMEOUT);
+            state = 2;
+            break;
+          }
+        }
+        __nanosleep(1024);
+      }
+    }
+    state = __shfl_sync(0xffffffffu, state, 0);
+    if (state == 1) return;
+    if (state == 2) {
+      // the workers learn of it through abort_word; wait (bounded) for their exit
+      if (lane == 0) {
+        const unsigned long long t0 = global_ns();
+        while (!*reinterpret_cast<volatile int*>(&mb->exit) && global_ns() - t0 < kWaitLimitNs) __nanosleep(1024);
+      }
+      __syncwarp();
+      return;
+    }
+    int it = 0, b = -1;
+    long long off = 0;
+    if (lane == 0) {
+      it = first + atomicAdd(p.queue + cls, 1);
+      if (it < last) {
+        b = p.plan[PLAN_HDR + items[4 * it + 1]];
+        off = p.offsets[b];
+      }
+    }
+    it = __shfl_sync(0xffffffffu, it, 0);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    off = __shfl_sync(0xffffffffu, off, 0);
+    if (b >= 0) {
+      constexpr int bytes = U * U * int(sizeof(float2));
+      const char* base = reinterpret_cast<const char*>(p.A + off);
+      for (int k = lane * 128; k <= bytes; k += 32 * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (k < bytes ? k : bytes - 1)));
+    }
+    __syncwarp();
+    if (lane == 0) {
+      mb->it = it;
+      mb->b = b;
+      mb->off = off;
+      st_release_shared(&mb->full, 1);
+    }
+    __syncwarp();
+  }
+}
+
+// A new matrix into a slot, straight from global memory (the claimer pulled it toward L2) into
+// registers: lane (i, part) reads its part of A[i][h CW .. h CW + CW - 1] (the row's two lanes
+// together read whole complex values) and takes the other part from its partner lane where a
+// complex product needs it. The real-part lane of row j in its diagonal block (warp h = j / CW)
+// forms x0[j] = c / A[j][j] (damped Jacobi, c = 1 / (1 + damping U)) into x0s; after a worker
+// barrier X_0 goes to the X master at column cX (padding lanes zero) and the pieces of A's left
+// operand [Ar; Ai] to the slot's cache area (free: its previous matrix is done). Every worker
+// thread calls it (shuffles).
 // first_nest: X_0 is diagonal, so the first nest's residual R_0 = I - A X_0 is the column
-// scaling R_0[i][j] = delta_ij - A[i][j] x0[j]; it is formed here in FP32 (the x0[j] in x0s,
-// R_0 into the R master at column cR; depth 1 (one_step): X_1 = X_0 (I + R_0), the row scaling
-// x0[i] (delta_ij + R_0[i][j]), into the X master instead of X_0). Returns this thread's sum
-// of squares of R_0 (valid lanes and columns).
+// scaling R_0[i][j] = delta_ij - A[i][j] x0[j]; it is formed here in FP32 (R_0 into the R master
+// at column cR; depth 1 (one_step): X_1 = X_0 (I + R_0), the row scaling x0[i] (delta_ij +
+// R_0[i][j]), into the X master instead of X_0). Returns this thread's sum of squares of R_0
+// (valid lanes and columns).
 template <int U>
 __device__ __forceinline__ float tc_load_matrix(const float2* A, float damping, uint8_t* acache, uint32_t tmem,
                                                 uint32_t cX, uint32_t cR, float2* x0s, bool first_nest, bool one_step,
                                                 int q, int h, int l) {
-  constexpr int XP = 2 * U + 1;
-  float* st = reinterpret_cast<float*>(acache);
-  const float* src = reinterpret_cast<const float*>(A);
-  static_assert((2 * U * U) % btc::THREADS == 0, "whole rounds of the worker threads");
-  float v[2 * U * U / btc::THREADS];
-#pragma unroll
-  for (int k = 0; k < 2 * U * U / btc::THREADS; ++k) v[k] = __ldg(src + threadIdx.x + k * btc::THREADS);
-#pragma unroll
-  for (int k = 0; k < 2 * U * U / btc::THREADS; ++k) {
-    const int e = threadIdx.x + k * btc::THREADS;
-    st[(e / (2 * U)) * XP + e % (2 * U)] = v[k];
-  }
-  tc_wsync();
-  const float cdamp = 1.f / (1.f + damping * float(U));
-  if (threadIdx.x < U) {
-    // x0[t] = c / A[t][t]
-    const float ar = st[threadIdx.x * XP + 2 * threadIdx.x], ai = st[threadIdx.x * XP + 2 * threadIdx.x + 1];
-    const float den = ar * ar + ai * ai;
-    x0s[threadIdx.x] = make_float2(cdamp * ar / den, -cdamp * ai / den);
-  }
-  tc_wsync();
+  static_assert(U % btc::CW == 0, "an active warp's columns all lie inside the matrix");
   const bool active = h * btc::CW < U;
   int i;
   bool im;
   const bool valid_row = tc_lane_row<U>(l, i, im) && active;
   const bool re = !im;
+  // the warp's 16 x 16 block of A (rows 16q.., columns h CW..) in coalesced row segments (a
+  // half-warp reads one row's 128 bytes), turned to the lanes' layout through a scratch block in
+  // the slot's cache area (rows padded to 17 complex values: no bank conflicts either way)
+  float av[btc::CW];
+  {
+    static_assert(btc::CW == 16 && btc::WARPS * 16 * 17 * 8 <= btc::OPND, "scratch blocks fit the cache area");
+    float2* sc = reinterpret_cast<float2*>(acache) + (threadIdx.x >> 5) * (16 * 17);
+    const int lw = int(threadIdx.x & 31);
+    if (active) {
+      float2 v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int r = q * 16 + 2 * k + (lw >> 4);
+        v[k] = r < U ? __ldg(A + size_t(r) * U + h * btc::CW + (lw & 15)) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sc[(2 * k + (lw >> 4)) * 17 + (lw & 15)] = v[k];
+      __syncwarp();
+      const float* own = reinterpret_cast<const float*>(sc + (lw >> 1) * 17) + (im ? 1 : 0);
+#pragma unroll
+      for (int t = 0; t < btc::CW; ++t) av[t] = own[2 * t];
+      if (valid_row && re && i / btc::CW == h) {
+        const float2 d = sc[(lw >> 1) * 17 + (i - h * btc::CW)];
+        const float r = (1.f / (1.f + damping * float(U))) / (d.x * d.x + d.y * d.y);
+        x0s[i] = make_float2(d.x * r, -d.y * r);
+      }
+    }
+  }
+  // (after this barrier every warp has read its scratch block: the pieces may overwrite it)
+  tc_wsync();
+  if (!active) return 0.f;
+  // the diagonal lanes' division (and its slow path) can leave the warp diverged past the
+  // barrier; every shuffle of the loops below would then run once per half of the warp
+  __syncwarp();
   const uint32_t lane_off = uint32_t(q * 32) << 16;
   const float2 xi = valid_row ? x0s[i] : make_float2(0.f, 0.f);
   float local = 0.f;
-  {
-    // the X master (X_0, or X_1 at depth 1 with the first nest element-wise) and R_0 go to TMEM
-    // before A's pieces are formed, so that their registers are free again
-    uint32_t vx[btc::CW], vr[btc::CW];
+  // per 8-column half: the X master (X_0, or X_1 at depth 1 with the first nest element-wise)
+  // and R_0 to TMEM, then the half's pieces of A's left operand
 #pragma unroll
-    for (int t = 0; t < btc::CW; ++t) {
-      const int j = h * btc::CW + t;
+  for (int hf = 0; hf < 2; ++hf) {
+    uint32_t vx[8], vr[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int j = h * btc::CW + hf * 8 + t;
+      const float mine = av[hf * 8 + t];
+      const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
       float xv = 0.f, rv = 0.f;
-      if (valid_row && j < U) {
+      if (valid_row) {
         if (j == i) xv = re ? xi.x : xi.y;
         if (first_nest) {
-          const float ar = st[i * XP + 2 * j], ai = st[i * XP + 2 * j + 1];
+          const float ar = re ? mine : other, ai = re ? other : mine;
           const float2 xj = x0s[j];
           const float d = (re && j == i) ? 1.f : 0.f;
           rv = re ? d - (ar * xj.x - ai * xj.y) : -(ar * xj.y + ai * xj.x);
@@ -642,29 +805,29 @@ __device__ __forceinline__ float tc_load_matrix(const float2* A, float damping, 
     if (first_nest && one_step) {
       // X_1[i][j] = x0[i] (delta_ij + R_0[i][j]); the row's other part from the partner lane
 #pragma unroll
-      for (int t = 0; t < btc::CW; ++t) {
-        const int j = h * btc::CW + t;
-        const float own = __uint_as_float(vr[t]) + ((re && j == i) ? 1.f : 0.f);
-        const float other = __shfl_xor_sync(0xffffffffu, own, 1);
-        const float pr = re ? own : other, pi = re ? other : own;
+      for (int t = 0; t < 8; ++t) {
+        const int j = h * btc::CW + hf * 8 + t;
+        const float mine = __uint_as_float(vr[t]) + ((re && j == i) ? 1.f : 0.f);
+        const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+        const float pr = re ? mine : other, pi = re ? other : mine;
         const float xv = re ? xi.x * pr - xi.y * pi : xi.x * pi + xi.y * pr;
         vx[t] = __float_as_uint(valid_row ? xv : 0.f);
       }
     }
-    if (active) {
-      tmem_st_cw(tmem + lane_off + cX + uint32_t(h * btc::CW), vx);
-      if (first_nest) tmem_st_cw(tmem + lane_off + cR + uint32_t(h * btc::CW), vr);
-      tmem_st_wait();
+    const uint32_t col = uint32_t(h * btc::CW + hf * 8);
+    tmem_st_32x32b_x8(tmem + lane_off + cX + col, vx);
+    if (first_nest) tmem_st_32x32b_x8(tmem + lane_off + cR + col, vr);
+    if (valid_row) {
+      uint32_t w[3][4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) split3x2(av[hf * 8 + 2 * e], av[hf * 8 + 2 * e + 1], w[0][e], w[1][e], w[2][e]);
+      const uint32_t off = bt_sw128_offset(l, int(col));
+#pragma unroll
+      for (int pc = 0; pc < 3; ++pc)
+        *reinterpret_cast<uint4*>(acache + pc * btc::PIECE + off) = make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
     }
   }
-  uint32_t va[btc::CW];
-#pragma unroll
-  for (int t = 0; t < btc::CW; ++t) {
-    const int j = h * btc::CW + t;
-    va[t] = __float_as_uint((valid_row && j < U) ? st[i * XP + 2 * j + (re ? 0 : 1)] : 0.f);
-  }
-  tc_wsync();
-  if (valid_row) tc_row_pieces<U>(va, acache, l, h * btc::CW);
+  tmem_st_wait();
   return local;
 }
 
@@ -719,7 +882,7 @@ __device__ __forceinline__ void tc_store_x(float2* X, uint32_t tmem, uint32_t cX
   }
   tc_wsync();
   float* dst = reinterpret_cast<float*>(X);
-#pragma unroll
+#pragma unroll 4
   for (int k = 0; k < 2 * U * U / btc::THREADS; ++k) {
     const int e = threadIdx.x + k * btc::THREADS;
     dst[e] = xs[(e / (2 * U)) * XP + e % (2 * U)];
@@ -763,7 +926,8 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 
 // The tensor-core items of size U (classes 0 and 1): one CTA per SM, 512 TMEM columns, two
 // slots at depth <= 2 (one at depth >= 3, whose T master takes the second slot's columns);
-// btc::THREADS worker threads stage, finish and move matrices, one more warp issues the MMAs.
+// btc::THREADS worker threads stage, finish and move matrices, one more warp issues the MMAs
+// and another claims the next items.
 struct TcCmd {
   uint32_t d_tmem, l_saddr, b_saddr;
   int exit;
@@ -775,7 +939,7 @@ template <int U>
 __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls, int first, int last,
                                                 const int32_t* items, uint8_t* ops, uint32_t ops_s, uint32_t tmem,
                                                 uint64_t* mma_bar, int* abort_word, int* item_sh, float* red_warp,
-                                                TcCmd* cmd, float2 (*x0s)[64]) {
+                                                TcCmd* cmd, float2 (*x0s)[64], TcMailbox* mb, long long* slot_off) {
   const int w = int(threadIdx.x >> 5), q = w & 3, h = w >> 2, l = q * 32 + int(threadIdx.x & 31);
   const int nslots = p.depth <= 2 ? 2 : 1;
   TcSlot sl0 = {-1, 0, 0, NN_OK, 0.f, 0.f, 0}, sl1 = sl0;  // two named slots: no local memory
@@ -786,17 +950,27 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
   bool outstanding = false;
   bool ok = true;
 
-  // next item of this class into slot s, or the slot left empty
+  // the claimer's next item into slot s, or the slot left empty (no item left, or the wait for
+  // the mailbox ran out: ok = false)
   auto fetch = [&](int s) {
-    if (threadIdx.x == 0) *item_sh = first + atomicAdd(p.queue + cls, 1);
+    if (threadIdx.x == 0) {
+      const bool got = tc_wait_full(mb, abort_word, p.err);
+      item_sh[0] = got ? mb->it : -1;
+      item_sh[1] = mb->b;
+      if (got) {
+        if (mb->b >= 0) slot_off[s] = mb->off;
+        st_release_shared(&mb->full, 0);  // taken: the claimer claims the next one
+      }
+    }
+    __syncwarp();
     tc_wsync();
-    const int it = *item_sh;
-    tc_wsync();
+    const int it = item_sh[0], b = item_sh[1];
+    if (it < 0) ok = false;
     TcSlot t = {-1, 0, 0, NN_OK, 0.f, 0.f, 0};
-    if (it < last) {
-      t.b = p.plan[PLAN_HDR + items[4 * it + 1]];
+    if (it >= 0 && b >= 0) {
+      t.b = b;
       const uint32_t sb = uint32_t(s) * btc::SLOT_COLS;
-      const float ss = tc_load_matrix<U>(p.A + p.offsets[t.b], p.damping, ops + btc::A_CACHE + s * btc::OPND, tmem,
+      const float ss = tc_load_matrix<U>(p.A + slot_off[s], p.damping, ops + btc::A_CACHE + s * btc::OPND, tmem,
                                          sb + btc::MX, sb + btc::MR, x0s[s], first_nest, p.depth == 1, q, h, l);
       if (first_nest) {
         const float s0 = sqrtf(bt_block_sum(ss, red_warp)) / float(U);
@@ -827,7 +1001,10 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
   // every thread learns the same outcome of the wait on the last issued MMA chain
   auto wait_mma = [&]() -> bool {
     if (!outstanding) return true;
-    const bool r = tc_wsync_and(mbar_wait(mma_bar, phase, abort_word, p.err));
+    // (the lanes leave the polling loop at different times: reconverge before the TMEM loads)
+    const bool got = mbar_wait(mma_bar, phase, abort_word, p.err);
+    __syncwarp();
+    const bool r = tc_wsync_and(got);
     phase ^= 1u;
     outstanding = false;
     tc_fence_after();
@@ -871,9 +1048,12 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
       }
       t.s_prev = sv;
       if (t.k == p.nests) done = true;
+      tc_wsync();
+      tc_fence_after();
     }
-    tc_wsync();
-    tc_fence_after();
+    // (other products need no worker barrier here: each warp reads back only the TMEM columns
+    // and lanes it wrote itself, and the next MMA into this slot's accumulator is ordered after
+    // every warp's epilogue by the next wait and hand-over)
     if (!done) {
       if (diag_update || ++t.j > p.depth) {
         t.j = 0;
@@ -885,7 +1065,7 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
         sl1 = t;
       return;
     }
-    tc_store_x<U>(p.X + p.offsets[t.b], tmem, sb + btc::MX, ops + btc::A_CACHE + s * btc::OPND, q, h, l);
+    tc_store_x<U>(p.X + slot_off[s], tmem, sb + btc::MX, ops + btc::A_CACHE + s * btc::OPND, q, h, l);
     if (threadIdx.x == 0) {
       p.residual[t.b] = t.s_last;
       p.status[t.b] = t.st;
@@ -917,12 +1097,17 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
     pending = m;
   }
   if (ok) ok = wait_mma();
-  // release the MMA warp (after a timeout too; its last chain, if any, was issued)
-  if (threadIdx.x == 0) cmd->exit = 1;
+  // release the MMA warp (after a timeout too; its last chain, if any, was issued) and the
+  // claimer
+  if (threadIdx.x == 0) {
+    cmd->exit = 1;
+    *reinterpret_cast<volatile int*>(&mb->exit) = 1;
+  }
   tc_handoff_arrive();
   if (!ok) {
     // a bounded wait ran out: the slots' matrices and every item not yet taken report
-    // NN_ERR_TIMEOUT (X unspecified); wait (bounded) for the issued MMAs before freeing TMEM
+    // NN_ERR_TIMEOUT (X unspecified; an item left in the mailbox is reported once the claimer
+    // has returned); wait (bounded) for the issued MMAs before freeing TMEM
     if (threadIdx.x == 0) {
       if (sl0.b >= 0) {
         p.residual[sl0.b] = sl0.s_last;
@@ -934,9 +1119,9 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
       }
     }
     while (true) {
-      if (threadIdx.x == 0) *item_sh = first + atomicAdd(p.queue + cls, 1);
+      if (threadIdx.x == 0) item_sh[0] = first + atomicAdd(p.queue + cls, 1);
       tc_wsync();
-      const int it = *item_sh;
+      const int it = item_sh[0];
       tc_wsync();
       if (it >= last) break;
       if (threadIdx.x == 0) {
@@ -952,13 +1137,15 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
   }
 }
 
-// 17 warps: at most 96 registers a thread (five warps share one scheduler's quarter of the
-// register file)
+// 18 warps (16 workers, the MMA warp, the claimer warp): at most 96 registers a thread (five
+// warps share one scheduler's quarter of the register file)
 template <int U>
-__global__ void __launch_bounds__(btc::THREADS + 32, 1) batched_tc_kernel(const BatchedParams p, int cls) {
+__global__ void __launch_bounds__(btc::BLOCK, 1) batched_tc_kernel(const BatchedParams p, int cls) {
   extern __shared__ float2 smem[];
   __shared__ float red_warp[btc::WARPS];
-  __shared__ int item_sh;
+  __shared__ int item_sh[2];
+  __shared__ long long slot_off[2];  // per slot: the matrix's offset in A and X
+  __shared__ TcMailbox mb;
   __shared__ __align__(8) uint64_t mma_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_word;
@@ -975,6 +1162,8 @@ __global__ void __launch_bounds__(btc::THREADS + 32, 1) batched_tc_kernel(const 
     if (threadIdx.x == 0) {
       mbar_init(&mma_bar, 1);
       abort_word = 0;
+      mb.full = 0;
+      mb.exit = 0;
       mbar_fence_init();
     }
     if (threadIdx.x < 32) tmem_alloc(&tmem_slot, btc::TMEM_COLS);
@@ -982,7 +1171,9 @@ __global__ void __launch_bounds__(btc::THREADS + 32, 1) batched_tc_kernel(const 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    if (threadIdx.x >= btc::THREADS) {
+    if (threadIdx.x >= btc::THREADS + 32) {
+      tc_claimer<U>(p, cls, first, last, items, &mb, &abort_word);
+    } else if (threadIdx.x >= btc::THREADS) {
       // the MMA warp: one chain per handed-over product until the workers send exit
       while (true) {
         tc_handoff_wait();
@@ -996,12 +1187,17 @@ __global__ void __launch_bounds__(btc::THREADS + 32, 1) batched_tc_kernel(const 
         __syncwarp();
       }
     } else {
-      batched_tc_work<U>(p, cls, first, last, items, ops, ops_s, tmem, &mma_bar, &abort_word, &item_sh, red_warp,
-                         &cmd, x0s);
+      batched_tc_work<U>(p, cls, first, last, items, ops, ops_s, tmem, &mma_bar, &abort_word, item_sh, red_warp,
+                         &cmd, x0s, &mb, slot_off);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // an item the claimer delivered after a timeout ended the workers
+    if (threadIdx.x == 0 && mb.full && mb.b >= 0) {
+      p.residual[mb.b] = 0.f;
+      p.status[mb.b] = NN_ERR_TIMEOUT;
+    }
     if (threadIdx.x < 32) tmem_dealloc(tmem, btc::TMEM_COLS);
   }
   pdl_wait();
@@ -1238,7 +1434,7 @@ int bt_init() {
   for (auto k : {batched_tc_kernel<64>, batched_tc_kernel<48>}) {
     cudaFuncAttributes fa;
     NN_CUDA_TRY(cudaFuncGetAttributes(&fa, k));
-    if (fa.maxThreadsPerBlock < btc::THREADS + 32) return NN_ERR_UNSUPPORTED;  // registers do not fit
+    if (fa.maxThreadsPerBlock < btc::BLOCK) return NN_ERR_UNSUPPORTED;  // registers do not fit
   }
   for (SimtKernel k : kSimtKernels)
     NN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM_SIMT_DEEP));
@@ -1382,7 +1578,7 @@ int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* 
     if (c < 2) {
       k = c == 0 ? batched_tc_kernel<64> : batched_tc_kernel<48>;
       cfg.gridDim = dim3(unsigned(g_bt_sms));
-      cfg.blockDim = dim3(btc::THREADS + 32);
+      cfg.blockDim = dim3(btc::BLOCK);
       cfg.dynamicSmemBytes = size_t(BT_SMEM);
     } else if (c < 18) {
       k = kSimtKernels[c - 2];
