@@ -28,6 +28,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -347,8 +348,7 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
 //     shared memory; the workers read a new matrix in coalesced row segments.
 namespace btc {
 constexpr int M = 128;                         // MMA rows (2U used)
-constexpr int CW = 16;                         // master columns per warp (TMEM access: 32 lanes x 16)
-constexpr int WARPS = 4 * (64 / CW);           // warp (q, h): lane quadrant q, column block h
+constexpr int WARPS = 16;                      // warp (q, h): lane quadrant q, column block h (U / 4 columns)
 constexpr int THREADS = 32 * WARPS;            // worker threads; one more warp issues the MMAs
 constexpr int PIECE = 128 * 128;               // one piece: 128 rows x 64 BF16 (one SW128 k-block)
 constexpr int OPND = 3 * PIECE;                // an operand's three pieces: 48 KB
@@ -385,9 +385,53 @@ __device__ __forceinline__ void tc_handoff_arrive() {
 }
 __device__ __forceinline__ void tc_handoff_wait() { asm volatile("bar.sync 2, %0;" ::"n"(btc::THREADS + 32) : "memory"); }
 
-// TMEM access of a warp's 32 lanes x btc::CW columns.
-__device__ __forceinline__ void tmem_ld_cw(uint32_t taddr, uint32_t (&r)[16]) { tmem_ld_32x32b_x16(taddr, r); }
-__device__ __forceinline__ void tmem_st_cw(uint32_t taddr, const uint32_t (&r)[16]) { tmem_st_32x32b_x16(taddr, r); }
+// The master columns one worker warp owns: the four warps of a lane quadrant split the U
+// columns evenly (CW = U / 4: 16 for U = 64, 12 for U = 48), so every worker warp carries data.
+// G is the column group of one shared-memory store of a piece: 8 values (16 bytes) for 16-column
+// blocks, 4 values (8 bytes) for 12-column blocks, which start at multiples of 4 only.
+template <int U>
+struct TcCols {
+  static_assert(U == 48 || U == 64, "tensor-core sizes");
+  static constexpr int CW = U / 4;
+  static constexpr int G = U == 64 ? 8 : 4;
+  static constexpr int NG = CW / G;
+};
+
+// TMEM access of a warp's 32 lanes x n consecutive columns, n = 4, 8, 12 or 16.
+template <int n>
+__device__ __forceinline__ void tmem_ld_n(uint32_t taddr, uint32_t (&r)[n]) {
+  static_assert(n == 4 || n == 8 || n == 12 || n == 16, "widths");
+  if constexpr (n == 16) {
+    tmem_ld_32x32b_x16(taddr, r);
+  } else {
+    if constexpr (n >= 8)
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                   : "r"(taddr)
+                   : "memory");
+    if constexpr (n == 4 || n == 12)
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                   : "=r"(r[n - 4]), "=r"(r[n - 3]), "=r"(r[n - 2]), "=r"(r[n - 1])
+                   : "r"(taddr + uint32_t(n - 4))
+                   : "memory");
+  }
+}
+template <int n>
+__device__ __forceinline__ void tmem_st_n(uint32_t taddr, const uint32_t (&r)[n]) {
+  static_assert(n == 4 || n == 8 || n == 12 || n == 16, "widths");
+  if constexpr (n == 16) {
+    tmem_st_32x32b_x16(taddr, r);
+  } else {
+    if constexpr (n >= 8)
+      asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+                   "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                   : "memory");
+    if constexpr (n == 4 || n == 12)
+      asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr + uint32_t(n - 4)),
+                   "r"(r[n - 4]), "r"(r[n - 3]), "r"(r[n - 2]), "r"(r[n - 1])
+                   : "memory");
+  }
+}
 
 // Shared-memory matrix descriptor of a K-major SWIZZLE_128B tile (8-row atoms 1024 B apart).
 __device__ __forceinline__ uint64_t bt_sw128_desc(uint32_t saddr) {
@@ -445,22 +489,42 @@ __device__ __forceinline__ bool tc_lane_row(int l, int& i, bool& im) {
   return l < 2 * U;
 }
 
-// Pieces of CW consecutive values of one left-operand row (K = col0 .. col0 + CW - 1, col0 a
-// multiple of 8; values at K >= U are not written).
+// Splits G consecutive values v[0..G-1] (FP32 bits) into three BF16 pieces and stores piece pc
+// at dst + pc PIECE + off (and, DUAL, at dst2 + pc PIECE + off2): one 16-byte store a piece for
+// G = 8, one 8-byte store for G = 4.
+template <int G, bool DUAL>
+__device__ __forceinline__ void tc_put_group(const uint32_t (&v)[G], uint8_t* dst, uint32_t off, uint8_t* dst2,
+                                             uint32_t off2) {
+  static_assert(G == 4 || G == 8, "groups of 4 or 8 values");
+  uint32_t w[3][G / 2];
+#pragma unroll
+  for (int e = 0; e < G / 2; ++e)
+    split3x2(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]), w[0][e], w[1][e], w[2][e]);
+#pragma unroll
+  for (int pc = 0; pc < 3; ++pc) {
+    if constexpr (G == 8) {
+      const uint4 x = make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
+      *reinterpret_cast<uint4*>(dst + pc * btc::PIECE + off) = x;
+      if constexpr (DUAL) *reinterpret_cast<uint4*>(dst2 + pc * btc::PIECE + off2) = x;
+    } else {
+      const uint2 x = make_uint2(w[pc][0], w[pc][1]);
+      *reinterpret_cast<uint2*>(dst + pc * btc::PIECE + off) = x;
+      if constexpr (DUAL) *reinterpret_cast<uint2*>(dst2 + pc * btc::PIECE + off2) = x;
+    }
+  }
+}
+
+// v = r[g G .. g G + G - 1] (g a compile-time constant after unrolling).
 template <int U>
-__device__ __forceinline__ void tc_row_pieces(const uint32_t (&v)[btc::CW], uint8_t* dst, int row, int col0) {
+__device__ __forceinline__ void tc_take_group(const uint32_t (&r)[TcCols<U>::CW], int g,
+                                              uint32_t (&v)[TcCols<U>::G]) {
+  constexpr int G = TcCols<U>::G;
 #pragma unroll
-  for (int ch = 0; ch < btc::CW / 8; ++ch) {
-    const int j0 = col0 + ch * 8;
-    if (j0 >= U) break;
-    uint32_t w[3][4];
+  for (int e = 0; e < G; ++e) {
+    uint32_t x = r[e];
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
-      split3x2(__uint_as_float(v[ch * 8 + 2 * e]), __uint_as_float(v[ch * 8 + 2 * e + 1]), w[0][e], w[1][e], w[2][e]);
-    const uint32_t off = bt_sw128_offset(row, j0);
-#pragma unroll
-    for (int pc = 0; pc < 3; ++pc)
-      *reinterpret_cast<uint4*>(dst + pc * btc::PIECE + off) = make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
+    for (int gg = 1; gg < TcCols<U>::NG; ++gg) x = g == gg ? r[gg * G + e] : x;
+    v[e] = x;
   }
 }
 
@@ -482,45 +546,42 @@ __device__ __forceinline__ int tc_imag_col(int j) {
 template <int U>
 __device__ __forceinline__ void tc_stage(uint32_t tmem, bool left, uint32_t cP, uint32_t cQ, uint8_t* ldst,
                                          uint8_t* bdst, int q, int h, int l) {
-  static_assert(U % btc::CW == 0 && btc::CW == 16, "whole 16-column blocks, two 8-column chunks each");
-  if (h * btc::CW >= U) return;
+  constexpr int CW = TcCols<U>::CW, G = TcCols<U>::G, NG = TcCols<U>::NG;
   const uint32_t lane_off = uint32_t(q * 32) << 16;
   const bool same = left && cP == cQ;
   int i;
   bool im;
   const bool valid = tc_lane_row<U>(l, i, im);
-  const bool rev = U == 48 && im;
-  uint32_t r[btc::CW];
+  uint32_t r[CW];
   // the right operand (and, for P = Q, the left one from the same pieces), then the left one
-  tmem_ld_cw(tmem + lane_off + cQ + uint32_t(h * btc::CW), r);
+  tmem_ld_n<CW>(tmem + lane_off + cQ + uint32_t(h * CW), r);
   tmem_ld_wait();
   if (valid) {
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int j0 = h * btc::CW + (rev ? 1 - t : t) * 8;  // master columns j0 .. j0 + 7
-      uint32_t w[3][4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const uint32_t a = rev ? r[(1 - t) * 8 + 2 * e] : r[t * 8 + 2 * e];
-        const uint32_t b = rev ? r[(1 - t) * 8 + 2 * e + 1] : r[t * 8 + 2 * e + 1];
-        split3x2(__uint_as_float(a), __uint_as_float(b), w[0][e], w[1][e], w[2][e]);
-      }
+    for (int t = 0; t < NG; ++t) {
+      const int g = t;
+      const int j0 = h * CW + g * G;  // master columns j0 .. j0 + G - 1
+      uint32_t v[G];
+      tc_take_group<U>(r, g, v);
       const uint32_t boff = bt_mn_offset(i, im ? U + tc_imag_col<U>(j0) : j0);
-#pragma unroll
-      for (int pc = 0; pc < 3; ++pc)
-        *reinterpret_cast<uint4*>(bdst + pc * btc::PIECE + boff) = make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
-      if (same) {
-        const uint32_t loff = bt_sw128_offset(l, j0);
-#pragma unroll
-        for (int pc = 0; pc < 3; ++pc)
-          *reinterpret_cast<uint4*>(ldst + pc * btc::PIECE + loff) = make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
-      }
+      if (same)
+        tc_put_group<G, true>(v, bdst, boff, ldst, bt_sw128_offset(l, j0));
+      else
+        tc_put_group<G, false>(v, bdst, boff, nullptr, 0);
     }
   }
   if (left && !same) {
-    tmem_ld_cw(tmem + lane_off + cP + uint32_t(h * btc::CW), r);
+    tmem_ld_n<CW>(tmem + lane_off + cP + uint32_t(h * CW), r);
     tmem_ld_wait();
-    if (valid) tc_row_pieces<U>(r, ldst, l, h * btc::CW);
+    if (valid) {
+#pragma unroll
+      for (int t = 0; t < NG; ++t) {
+        const int g = t;
+        uint32_t v[G];
+        tc_take_group<U>(r, g, v);
+        tc_put_group<G, false>(v, ldst, bt_sw128_offset(l, h * CW + g * G), nullptr, 0);
+      }
+    }
   }
 }
 
@@ -547,48 +608,56 @@ __device__ __forceinline__ void tc_issue(uint32_t d_tmem, uint32_t l_saddr, uint
   }
 }
 
+// Columns col .. col + W - 1 of the epilogue below (W = 8 or 4).
+template <int U, int W>
+__device__ __forceinline__ void tc_epilogue_part(uint32_t tmem, uint32_t lane_off, uint32_t cAcc, uint32_t cD,
+                                                 uint32_t cOut, int mode, uint32_t col, int i, bool re, bool valid,
+                                                 float& local) {
+  // cross terms: the real-part lane needs Pi Qi (Cr = Pr Qr - Pi Qi) and the imaginary-part
+  // lane Pr Qi (Ci = Pi Qr + Pr Qi): each is the other lane's own cross term (lanes l, l ^ 1)
+  uint32_t dd[W], dx[W], dm[W];
+  tmem_ld_n<W>(tmem + lane_off + cAcc + col, dd);
+  tmem_ld_n<W>(tmem + lane_off + cAcc + uint32_t(U + tc_imag_col<U>(int(col))), dx);
+  if (mode == BM_ADD) tmem_ld_n<W>(tmem + lane_off + cD + col, dm);
+  tmem_ld_wait();
+  const float sgn = re ? -1.f : 1.f;
+#pragma unroll
+  for (int t = 0; t < W; ++t) {
+    const float x = __shfl_xor_sync(0xffffffffu, __uint_as_float(dx[t]), 1);
+    const int j = int(col) + t;
+    const float cv = fmaf(sgn, x, __uint_as_float(dd[t]));
+    float v;
+    if (mode == BM_RESID) {
+      v = ((re && j == i) ? 1.f : 0.f) - cv;
+      if (valid) local = fmaf(v, v, local);
+    } else {
+      v = __uint_as_float(dm[t]) + cv;
+    }
+    dd[t] = __float_as_uint(v);
+  }
+  tmem_st_n<W>(tmem + lane_off + cOut + col, dd);
+}
+
 // out = mode(C) from the accumulator D of a product (see above) on this warp's 32 x CW block
 // of the real form; returns this thread's sum of squares of the result (residual mode, valid
-// lanes only). Every lane of the warp calls it (shuffles).
+// lanes only). Every lane of the warp calls it (shuffles); padding lanes (rows >= U) carry no
+// data and feed only padding rows of later products (the residual sum skips them).
 template <int U>
 __device__ __forceinline__ float tc_epilogue(uint32_t tmem, uint32_t cAcc, uint32_t cD, uint32_t cOut, int mode,
                                              int q, int h, int l) {
-  // Every warp reads and writes its block, also padding lanes and a block of columns >= U
-  // (U = 48): those lie inside the accumulator's 2U and the masters' 64 columns, carry no data
-  // and feed only padding rows and columns (the residual sum skips them).
+  constexpr int CW = TcCols<U>::CW;
   int i;
   bool im;
-  const bool valid = tc_lane_row<U>(l, i, im) && h * btc::CW < U;
-  const bool re = !im;
+  const bool valid = tc_lane_row<U>(l, i, im);
   const uint32_t lane_off = uint32_t(q * 32) << 16;
-  // cross terms: the real-part lane needs Pi Qi (Cr = Pr Qr - Pi Qi) and the imaginary-part
-  // lane Pr Qi (Ci = Pi Qr + Pr Qi): each is the other lane's own cross term (lanes l, l ^ 1)
-  const float sgn = re ? -1.f : 1.f;
   float local = 0.f;
+  const uint32_t col0 = uint32_t(h * CW);
 #pragma unroll
-  for (int ph = 0; ph < 2; ++ph) {
-    const uint32_t col = uint32_t(h * btc::CW + ph * (btc::CW / 2));
-    uint32_t dd[8], dx[8], dm[8];
-    tmem_ld_32x32b_x8(tmem + lane_off + cAcc + col, dd);
-    tmem_ld_32x32b_x8(tmem + lane_off + cAcc + uint32_t(U + tc_imag_col<U>(int(col))), dx);
-    if (mode == BM_ADD) tmem_ld_32x32b_x8(tmem + lane_off + cD + col, dm);
-    tmem_ld_wait();
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const float x = __shfl_xor_sync(0xffffffffu, __uint_as_float(dx[t]), 1);
-      const int j = int(col) + t;
-      const float cv = fmaf(sgn, x, __uint_as_float(dd[t]));
-      float v;
-      if (mode == BM_RESID) {
-        v = ((re && j == i) ? 1.f : 0.f) - cv;
-        if (valid) local = fmaf(v, v, local);
-      } else {
-        v = __uint_as_float(dm[t]) + cv;
-      }
-      dd[t] = __float_as_uint(v);
-    }
-    tmem_st_32x32b_x8(tmem + lane_off + cOut + col, dd);
-  }
+  for (int ph = 0; ph < CW / 8; ++ph)
+    tc_epilogue_part<U, 8>(tmem, lane_off, cAcc, cD, cOut, mode, col0 + uint32_t(8 * ph), i, !im, valid, local);
+  if constexpr (CW % 8 != 0)
+    tc_epilogue_part<U, CW % 8>(tmem, lane_off, cAcc, cD, cOut, mode, col0 + uint32_t(CW - CW % 8), i, !im, valid,
+                                local);
   tmem_st_wait();
   return local;
 }
@@ -735,58 +804,56 @@ template <int U>
 __device__ __forceinline__ float tc_load_matrix(const float2* A, float damping, uint8_t* acache, uint32_t tmem,
                                                 uint32_t cX, uint32_t cR, float2* x0s, bool first_nest, bool one_step,
                                                 int q, int h, int l) {
-  static_assert(U % btc::CW == 0, "an active warp's columns all lie inside the matrix");
-  const bool active = h * btc::CW < U;
+  constexpr int CW = TcCols<U>::CW, G = TcCols<U>::G, NG = TcCols<U>::NG, SP = CW + 1;
   int i;
   bool im;
-  const bool valid_row = tc_lane_row<U>(l, i, im) && active;
+  const bool valid_row = tc_lane_row<U>(l, i, im);
   const bool re = !im;
-  // the warp's 16 x 16 block of A (rows 16q.., columns h CW..) in coalesced row segments (a
-  // half-warp reads one row's 128 bytes), turned to the lanes' layout through a scratch block in
-  // the slot's cache area (rows padded to 17 complex values: no bank conflicts either way)
-  float av[btc::CW];
+  // the warp's 16 x CW block of A (rows 16q.., columns h CW..) in coalesced row segments (a
+  // half-warp reads one row's CW values), turned to the lanes' layout through a scratch block in
+  // the slot's cache area (rows padded to CW + 1 complex values: no bank conflicts either way)
+  float av[CW];
   {
-    static_assert(btc::CW == 16 && btc::WARPS * 16 * 17 * 8 <= btc::OPND, "scratch blocks fit the cache area");
-    float2* sc = reinterpret_cast<float2*>(acache) + (threadIdx.x >> 5) * (16 * 17);
-    const int lw = int(threadIdx.x & 31);
-    if (active) {
-      float2 v[8];
+    static_assert(btc::WARPS * 16 * SP * 8 <= btc::OPND, "scratch blocks fit the cache area");
+    float2* sc = reinterpret_cast<float2*>(acache) + (threadIdx.x >> 5) * (16 * SP);
+    const int lw = int(threadIdx.x & 31), c = lw & 15;
+    float2 v[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int r = q * 16 + 2 * k + (lw >> 4);
-        v[k] = r < U ? __ldg(A + size_t(r) * U + h * btc::CW + (lw & 15)) : make_float2(0.f, 0.f);
-      }
+    for (int k = 0; k < 8; ++k) {
+      const int r = q * 16 + 2 * k + (lw >> 4);
+      v[k] = (r < U && c < CW) ? __ldg(A + size_t(r) * U + h * CW + c) : make_float2(0.f, 0.f);
+    }
+    if (c < CW) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) sc[(2 * k + (lw >> 4)) * 17 + (lw & 15)] = v[k];
-      __syncwarp();
-      const float* own = reinterpret_cast<const float*>(sc + (lw >> 1) * 17) + (im ? 1 : 0);
+      for (int k = 0; k < 8; ++k) sc[(2 * k + (lw >> 4)) * SP + c] = v[k];
+    }
+    __syncwarp();
+    const float* own = reinterpret_cast<const float*>(sc + (lw >> 1) * SP) + (im ? 1 : 0);
 #pragma unroll
-      for (int t = 0; t < btc::CW; ++t) av[t] = own[2 * t];
-      if (valid_row && re && i / btc::CW == h) {
-        const float2 d = sc[(lw >> 1) * 17 + (i - h * btc::CW)];
-        const float r = (1.f / (1.f + damping * float(U))) / (d.x * d.x + d.y * d.y);
-        x0s[i] = make_float2(d.x * r, -d.y * r);
-      }
+    for (int t = 0; t < CW; ++t) av[t] = own[2 * t];
+    if (valid_row && re && i / CW == h) {
+      const float2 d = sc[(lw >> 1) * SP + (i - h * CW)];
+      const float r = (1.f / (1.f + damping * float(U))) / (d.x * d.x + d.y * d.y);
+      x0s[i] = make_float2(d.x * r, -d.y * r);
     }
   }
   // (after this barrier every warp has read its scratch block: the pieces may overwrite it)
   tc_wsync();
-  if (!active) return 0.f;
   // the diagonal lanes' division (and its slow path) can leave the warp diverged past the
   // barrier; every shuffle of the loops below would then run once per half of the warp
   __syncwarp();
   const uint32_t lane_off = uint32_t(q * 32) << 16;
   const float2 xi = valid_row ? x0s[i] : make_float2(0.f, 0.f);
   float local = 0.f;
-  // per 8-column half: the X master (X_0, or X_1 at depth 1 with the first nest element-wise)
-  // and R_0 to TMEM, then the half's pieces of A's left operand
+  // the X master (X_0, or X_1 at depth 1 with the first nest element-wise) and R_0 to TMEM, in
+  // parts of 8 and CW - 8 columns
+  auto part = [&](auto width, int c0) {
+    constexpr int W = decltype(width)::value;
+    uint32_t vx[W], vr[W];
 #pragma unroll
-  for (int hf = 0; hf < 2; ++hf) {
-    uint32_t vx[8], vr[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int j = h * btc::CW + hf * 8 + t;
-      const float mine = av[hf * 8 + t];
+    for (int t = 0; t < W; ++t) {
+      const int j = h * CW + c0 + t;
+      const float mine = av[c0 + t];
       const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
       float xv = 0.f, rv = 0.f;
       if (valid_row) {
@@ -805,8 +872,8 @@ __device__ __forceinline__ float tc_load_matrix(const float2* A, float damping, 
     if (first_nest && one_step) {
       // X_1[i][j] = x0[i] (delta_ij + R_0[i][j]); the row's other part from the partner lane
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int j = h * btc::CW + hf * 8 + t;
+      for (int t = 0; t < W; ++t) {
+        const int j = h * CW + c0 + t;
         const float mine = __uint_as_float(vr[t]) + ((re && j == i) ? 1.f : 0.f);
         const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
         const float pr = re ? mine : other, pi = re ? other : mine;
@@ -814,17 +881,23 @@ __device__ __forceinline__ float tc_load_matrix(const float2* A, float damping, 
         vx[t] = __float_as_uint(valid_row ? xv : 0.f);
       }
     }
-    const uint32_t col = uint32_t(h * btc::CW + hf * 8);
-    tmem_st_32x32b_x8(tmem + lane_off + cX + col, vx);
-    if (first_nest) tmem_st_32x32b_x8(tmem + lane_off + cR + col, vr);
-    if (valid_row) {
-      uint32_t w[3][4];
+    const uint32_t col = uint32_t(h * CW + c0);
+    tmem_st_n<W>(tmem + lane_off + cX + col, vx);
+    if (first_nest) tmem_st_n<W>(tmem + lane_off + cR + col, vr);
+  };
+  part(std::integral_constant<int, 8>(), 0);
+  part(std::integral_constant<int, CW - 8>(), 8);
+  // the pieces of A's left operand
+  if (valid_row) {
+    uint32_t ab[CW];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) split3x2(av[hf * 8 + 2 * e], av[hf * 8 + 2 * e + 1], w[0][e], w[1][e], w[2][e]);
-      const uint32_t off = bt_sw128_offset(l, int(col));
+    for (int t = 0; t < CW; ++t) ab[t] = __float_as_uint(av[t]);
 #pragma unroll
-      for (int pc = 0; pc < 3; ++pc)
-        *reinterpret_cast<uint4*>(acache + pc * btc::PIECE + off) = make_uint4(w[pc][0], w[pc][1], w[pc][2], w[pc][3]);
+    for (int t = 0; t < NG; ++t) {
+      const int g = t;
+      uint32_t v[G];
+      tc_take_group<U>(ab, g, v);
+      tc_put_group<G, false>(v, acache, bt_sw128_offset(l, h * CW + g * G), nullptr, 0);
     }
   }
   tmem_st_wait();
@@ -833,51 +906,51 @@ __device__ __forceinline__ float tc_load_matrix(const float2* A, float damping, 
 
 // X_1 = X_0 (I + T) for a diagonal X_0 (the first nest's update): the row scaling
 // x0[i] (delta_ij + T[i][j]) from the T master at column cT into the X master at column cX.
-// Every lane of an active warp calls it (shuffles).
+// Every lane of the warp calls it (shuffles).
 template <int U>
 __device__ __forceinline__ void tc_diag_update(uint32_t tmem, uint32_t cT, uint32_t cX, const float2* x0s, int q,
                                                int h, int l) {
-  if (h * btc::CW >= U) return;
+  constexpr int CW = TcCols<U>::CW;
   int i;
   bool im;
   const bool valid = tc_lane_row<U>(l, i, im);
   const bool re = !im;
   const float2 xi = valid ? x0s[i] : make_float2(0.f, 0.f);
   const uint32_t lane_off = uint32_t(q * 32) << 16;
-  uint32_t tv[btc::CW];
-  tmem_ld_cw(tmem + lane_off + cT + uint32_t(h * btc::CW), tv);
+  uint32_t tv[CW];
+  tmem_ld_n<CW>(tmem + lane_off + cT + uint32_t(h * CW), tv);
   tmem_ld_wait();
 #pragma unroll
-  for (int t = 0; t < btc::CW; ++t) {
-    const int j = h * btc::CW + t;
+  for (int t = 0; t < CW; ++t) {
+    const int j = h * CW + t;
     const float own = __uint_as_float(tv[t]) + ((re && j == i) ? 1.f : 0.f);
     const float other = __shfl_xor_sync(0xffffffffu, own, 1);
     const float pr = re ? own : other, pi = re ? other : own;
     const float xv = re ? xi.x * pr - xi.y * pi : xi.x * pi + xi.y * pr;
-    tv[t] = __float_as_uint((valid && j < U) ? xv : 0.f);
+    tv[t] = __float_as_uint(valid ? xv : 0.f);
   }
-  tmem_st_cw(tmem + lane_off + cX + uint32_t(h * btc::CW), tv);
+  tmem_st_n<CW>(tmem + lane_off + cX + uint32_t(h * CW), tv);
   tmem_st_wait();
 }
 
 // X (complex, row-major) from the X master at column cX, through the slot's cache area (free:
-// its matrix is done; rows padded as above) so that the global writes are coalesced. Every
-// worker thread calls it.
+// its matrix is done; rows padded to 2U + 1 floats) so that the global writes are coalesced.
+// Every worker thread calls it.
 template <int U>
 __device__ __forceinline__ void tc_store_x(float2* X, uint32_t tmem, uint32_t cX, uint8_t* acache, int q, int h,
                                            int l) {
-  constexpr int XP = 2 * U + 1;
+  constexpr int CW = TcCols<U>::CW, XP = 2 * U + 1;
   float* xs = reinterpret_cast<float*>(acache);
-  if (h * btc::CW < U) {
-    uint32_t vx[btc::CW];
-    tmem_ld_cw(tmem + (uint32_t(q * 32) << 16) + cX + uint32_t(h * btc::CW), vx);
+  {
+    uint32_t vx[CW];
+    tmem_ld_n<CW>(tmem + (uint32_t(q * 32) << 16) + cX + uint32_t(h * CW), vx);
     tmem_ld_wait();
     int i;
     bool im;
     if (tc_lane_row<U>(l, i, im)) {
       const bool re = !im;
 #pragma unroll
-      for (int t = 0; t < btc::CW; ++t) xs[i * XP + 2 * (h * btc::CW + t) + (re ? 0 : 1)] = __uint_as_float(vx[t]);
+      for (int t = 0; t < CW; ++t) xs[i * XP + 2 * (h * CW + t) + (re ? 0 : 1)] = __uint_as_float(vx[t]);
     }
   }
   tc_wsync();
@@ -890,12 +963,12 @@ __device__ __forceinline__ void tc_store_x(float2* X, uint32_t tmem, uint32_t cX
   tc_wsync();
 }
 
-// Slot state (identical in every thread: all updates are CTA-uniform).
+// Slot state (identical in every thread: all updates are CTA-uniform). The slot's last two
+// residuals live in shared memory (slot_s[s] = (s_prev, s_last), written by thread 0 after a
+// worker barrier), which keeps the loop's registers down.
 struct TcSlot {
   int b;          // matrix index, -1 = empty
   int k, j;       // nest, product within the nest (0 = residual, 1..L-1 Horner, L = update)
-  int st;
-  float s_prev, s_last;
   int diag;       // the first nest runs element-wise (R_0 formed at load, X_1 by row scaling)
 };
 
@@ -939,10 +1012,11 @@ template <int U>
 __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls, int first, int last,
                                                 const int32_t* items, uint8_t* ops, uint32_t ops_s, uint32_t tmem,
                                                 uint64_t* mma_bar, int* abort_word, int* item_sh, float* red_warp,
-                                                TcCmd* cmd, float2 (*x0s)[64], TcMailbox* mb, long long* slot_off) {
+                                                TcCmd* cmd, float2 (*x0s)[64], TcMailbox* mb, long long* slot_off,
+                                                float2* slot_s) {
   const int w = int(threadIdx.x >> 5), q = w & 3, h = w >> 2, l = q * 32 + int(threadIdx.x & 31);
   const int nslots = p.depth <= 2 ? 2 : 1;
-  TcSlot sl0 = {-1, 0, 0, NN_OK, 0.f, 0.f, 0}, sl1 = sl0;  // two named slots: no local memory
+  TcSlot sl0 = {-1, 0, 0, 0}, sl1 = sl0;  // two named slots: no local memory
   // With at least one nest the first nest's residual and update are element-wise (X_0 is
   // diagonal); with none the residual of X_0 runs as a product.
   const bool first_nest = p.nests >= 1;
@@ -966,18 +1040,18 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
     tc_wsync();
     const int it = item_sh[0], b = item_sh[1];
     if (it < 0) ok = false;
-    TcSlot t = {-1, 0, 0, NN_OK, 0.f, 0.f, 0};
+    TcSlot t = {-1, 0, 0, 0};
     if (it >= 0 && b >= 0) {
       t.b = b;
       const uint32_t sb = uint32_t(s) * btc::SLOT_COLS;
       const float ss = tc_load_matrix<U>(p.A + slot_off[s], p.damping, ops + btc::A_CACHE + s * btc::OPND, tmem,
                                          sb + btc::MX, sb + btc::MR, x0s[s], first_nest, p.depth == 1, q, h, l);
+      float s0 = 0.f;
       if (first_nest) {
-        const float s0 = sqrtf(bt_block_sum(ss, red_warp)) / float(U);
+        s0 = sqrtf(bt_block_sum(ss, red_warp)) / float(U);
         if (isfinite(s0)) {
           // nest 0's residual is done; next: its first Horner product, or (depth 1, X_1 already
           // formed) nest 1's residual
-          t.s_prev = t.s_last = s0;
           t.diag = 1;
           if (p.depth == 1) {
             t.k = 1;
@@ -988,7 +1062,9 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
         }
         // a non-finite s_0 (a zero or non-finite diagonal): the residual runs as a product and
         // reports the matrix as diverged
+        if (!isfinite(s0)) s0 = 0.f;
       }
+      if (threadIdx.x == 0) slot_s[s] = make_float2(s0, s0);  // read after later barriers only
     }
     if (s == 0)
       sl0 = t;
@@ -1038,18 +1114,14 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
     const bool diag_update = t.diag && t.k == 0 && t.j + 1 == p.depth;
     if (diag_update) tc_diag_update<U>(tmem, pr.cOut, sb + btc::MX, x0s[s], q, h, l);
     tc_fence_before();
-    bool done = false;
+    bool done = false, diverged = false;
     if (pr.mode == BM_RESID) {
       const float sv = sqrtf(bt_block_sum(ss, red_warp)) / float(U);
-      t.s_last = sv;
-      if (!isfinite(sv) || (t.k >= 1 && sv >= 1.f && sv > t.s_prev)) {
-        t.st = NN_ERR_DIVERGED;
-        done = true;
-      }
-      t.s_prev = sv;
+      if (!isfinite(sv) || (t.k >= 1 && sv >= 1.f && sv > slot_s[s].x)) diverged = done = true;
       if (t.k == p.nests) done = true;
-      tc_wsync();
+      tc_wsync();  // every thread has read s_prev
       tc_fence_after();
+      if (threadIdx.x == 0) slot_s[s] = make_float2(sv, sv);
     }
     // (other products need no worker barrier here: each warp reads back only the TMEM columns
     // and lanes it wrote itself, and the next MMA into this slot's accumulator is ordered after
@@ -1067,8 +1139,8 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
     }
     tc_store_x<U>(p.X + slot_off[s], tmem, sb + btc::MX, ops + btc::A_CACHE + s * btc::OPND, q, h, l);
     if (threadIdx.x == 0) {
-      p.residual[t.b] = t.s_last;
-      p.status[t.b] = t.st;
+      p.residual[t.b] = slot_s[s].y;
+      p.status[t.b] = diverged ? NN_ERR_DIVERGED : NN_OK;
     }
     fetch(s);
   };
@@ -1110,11 +1182,11 @@ __device__ __forceinline__ void batched_tc_work(const BatchedParams& p, int cls,
     // has returned); wait (bounded) for the issued MMAs before freeing TMEM
     if (threadIdx.x == 0) {
       if (sl0.b >= 0) {
-        p.residual[sl0.b] = sl0.s_last;
+        p.residual[sl0.b] = slot_s[0].y;
         p.status[sl0.b] = NN_ERR_TIMEOUT;
       }
       if (nslots == 2 && sl1.b >= 0) {
-        p.residual[sl1.b] = sl1.s_last;
+        p.residual[sl1.b] = slot_s[1].y;
         p.status[sl1.b] = NN_ERR_TIMEOUT;
       }
     }
@@ -1145,6 +1217,7 @@ __global__ void __launch_bounds__(btc::BLOCK, 1) batched_tc_kernel(const Batched
   __shared__ float red_warp[btc::WARPS];
   __shared__ int item_sh[2];
   __shared__ long long slot_off[2];  // per slot: the matrix's offset in A and X
+  __shared__ float2 slot_s[2];       // per slot: (s_prev, s_last)
   __shared__ TcMailbox mb;
   __shared__ __align__(8) uint64_t mma_bar;
   __shared__ uint32_t tmem_slot;
@@ -1188,7 +1261,7 @@ __global__ void __launch_bounds__(btc::BLOCK, 1) batched_tc_kernel(const Batched
       }
     } else {
       batched_tc_work<U>(p, cls, first, last, items, ops, ops_s, tmem, &mma_bar, &abort_word, item_sh, red_warp,
-                         &cmd, x0s, &mb, slot_off);
+                         &cmd, x0s, &mb, slot_off, slot_s);
     }
     tc_fence_before();
     __syncthreads();
