@@ -893,6 +893,24 @@ def run_batched(args, rank, world, local_rank):
     clocks = sampler.stop()
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     ms = sum(per) / len(per)
+    # the dominant kernel alone: the U = 64 tensor-core class (class 0), launched on its own
+    # (class mask 1) on the same plan and workspace, CUDA events on the launching stream
+    tc64 = None
+    n64 = int(np.sum(bt.sizes == 64))
+    if (table or {}).get(64) == 2 and (classes & 1) and n64 > 0:
+        reps = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(3):
+            abi.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws, classes=1)
+        e0.record(stream)
+        for _ in range(reps):
+            abi.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws, classes=1)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        tc64 = (e0.elapsed_time(e1) / reps, n64)
+        # restore the whole batch's results (the class-0 runs rewrote only its own items)
+        g.replay()
+        torch.cuda.synchronize(dev)
     total = count
     if world > 1:
         t = torch.tensor([ms, float(count)], device=dev, dtype=torch.float64)
@@ -915,6 +933,33 @@ def run_batched(args, rank, world, local_rank):
     fma_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
     tflops = flops / (ms / 1e3) / 1e12
     tflops_exec = flops_exec / (ms / 1e3) / 1e12
+    batch_alu = {"achieved": round(tflops_exec, 2), "peak": round(fma_peak, 1),
+                 "frac": round(tflops_exec / fma_peak, 4),
+                 "note": "complex products executed by every class over the whole batch, against the CUDA-core "
+                         "FP32 FMA peak; above 1 because the U = 48 and 64 classes run on the tensor cores"}
+    if tc64 is not None:
+        # batched_tc_kernel<64>: per executed complex product 6 BF16 piece products of
+        # M = 128, N = 2U, K = U (the tensor pipe's work); (L+1) nests - 1 products a matrix
+        # (the first nest's residual and update are element-wise)
+        kms, n64 = tc64
+        prods = n64 * ((depth + 1) * nests - (1 if nests >= 1 else 0))
+        exec_fl = prods * 6 * 2.0 * 128 * 128 * 64
+        alg_fl = n64 * 8.0 * 64 ** 3 * gemms
+        peak = float(peaks.get("bf16_tflops", 1900.0))
+        traffic = profile_traffic("batched_nn_mimo16384.md", ["batched.cu"])
+        roof = {"kernel": f"nn::batched_tc_kernel<64> ({n64} matrices of U = 64, timed alone: {kms:.4f} ms per "
+                          "launch)", "bound": "tensor",
+                "achieved": round(exec_fl / (kms / 1e3) / 1e12, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(exec_fl / (kms / 1e3) / 1e12 / peak, 4),
+                "algorithmic_tflops": round(alg_fl / (kms / 1e3) / 1e12, 2),
+                "traffic": traffic,
+                "peak_source": f"BF16 tensor, burst, {src} (MEASURED_PEAKS.json bf16_tflops)",
+                "count": "achieved = 6 BF16 piece products x 2 x 128 x 2U x U per executed complex product; "
+                         "algorithmic_tflops = 8U^3 per product of the method",
+                "batch_alu": batch_alu}
+    else:
+        roof = dict({"kernel": "the batch (CUDA-core classes only)", "bound": "alu", "unit": "TFLOP/s",
+                     "traffic": None}, **{k: v for k, v in batch_alu.items() if k != "note"})
     return {"metric": "batched inversions/s (16,384 complex64 Gram matrices, U in {8..64}, depth 2, 3 nests)",
             "value": round(total / (ms / 1e3), 1), "unit": "inversions/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -930,12 +975,8 @@ def run_batched(args, rank, world, local_rank):
                        "tensor_core_items": bool(args.batched_tc) or any(v == 2 for v in (table or {}).values())},
             "status_ok_fraction": float(np.mean(stats == 0)), "gpu_launches": bin(classes).count("1") * args.steps,
             "tflops": round(tflops, 2), "gbs": round(byts / (ms / 1e3) / 1e9, 1),
-            "roofline": {"kernel": "the batch: batched_tc_kernel<U> (tuned sizes, tensor cores) + batched_simt_kernel<TG, T, U> / batched_warp_kernel<U> (CUDA cores), complex products executed (8 U^3 FLOP each)", "bound": "alu",
-                         "achieved": round(tflops_exec, 2),
-                         "peak": round(fma_peak, 1), "unit": "TFLOP/s", "frac": round(tflops_exec / fma_peak, 4),
-                         "method_tflops": round(tflops, 2),
-                         "traffic": None, "peak_source": f"FP32 FMA: {sms} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz",
-                         "hbm_frac": round(byts / (ms / 1e3) / 1e9 / float(peaks.get('hbm_gbs', 6800.0)), 4)},
+            "roofline": dict(roof, method_tflops=round(tflops, 2),
+                             hbm_frac=round(byts / (ms / 1e3) / 1e9 / float(peaks.get('hbm_gbs', 6800.0)), 4)),
             "clocks": clocks}
 
 

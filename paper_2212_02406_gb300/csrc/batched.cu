@@ -387,14 +387,10 @@ __device__ __forceinline__ void tc_handoff_wait() { asm volatile("bar.sync 2, %0
 
 // The master columns one worker warp owns: the four warps of a lane quadrant split the U
 // columns evenly (CW = U / 4: 16 for U = 64, 12 for U = 48), so every worker warp carries data.
-// G is the column group of one shared-memory store of a piece: 8 values (16 bytes) for 16-column
-// blocks, 4 values (8 bytes) for 12-column blocks, which start at multiples of 4 only.
 template <int U>
 struct TcCols {
   static_assert(U == 48 || U == 64, "tensor-core sizes");
   static constexpr int CW = U / 4;
-  static constexpr int G = U == 64 ? 8 : 4;
-  static constexpr int NG = CW / G;
 };
 
 // TMEM access of a warp's 32 lanes x n consecutive columns, n = 4, 8, 12 or 16.
@@ -514,17 +510,35 @@ __device__ __forceinline__ void tc_put_group(const uint32_t (&v)[G], uint8_t* ds
   }
 }
 
-// v = r[g G .. g G + G - 1] (g a compile-time constant after unrolling).
-template <int U>
-__device__ __forceinline__ void tc_take_group(const uint32_t (&r)[TcCols<U>::CW], int g,
-                                              uint32_t (&v)[TcCols<U>::G]) {
-  constexpr int G = TcCols<U>::G;
+// v = r[8 g .. 8 g + 7] for 16-column blocks (g a compile-time constant after unrolling).
+__device__ __forceinline__ void tc_take8(const uint32_t (&r)[16], int g, uint32_t (&v)[8]) {
 #pragma unroll
-  for (int e = 0; e < G; ++e) {
+  for (int e = 0; e < 8; ++e) {
     uint32_t x = r[e];
-#pragma unroll
-    for (int gg = 1; gg < TcCols<U>::NG; ++gg) x = g == gg ? r[gg * G + e] : x;
+    x = g == 1 ? r[8 + e] : x;
     v[e] = x;
+  }
+}
+
+// Calls f(width, first) for the store groups of this warp's CW master columns, as compile-time
+// constants: 8-value groups (16-byte stores) at multiples of 8 and, for 12-column blocks, one
+// 4-value group (8-byte stores) at the odd multiple of 4: h even (8 at 0, 4 at 8), h odd (4 at
+// 0, 8 at 4). Fewer, wider stores than 4-value groups, and the 16-byte ones are free of bank
+// conflicts (8-lane phases: eight rows of distinct swizzle phases, or a row's two part lanes).
+template <int U, typename F>
+__device__ __forceinline__ void tc_for_groups(int h, F&& f) {
+  using I0 = std::integral_constant<int, 0>;
+  using I4 = std::integral_constant<int, 4>;
+  using I8 = std::integral_constant<int, 8>;
+  static_assert(TcCols<U>::CW == 12, "16-column blocks use plain 8-value groups");
+  {
+    if (h & 1) {
+      f(I4(), I0());
+      f(I8(), I4());
+    } else {
+      f(I8(), I0());
+      f(I4(), I8());
+    }
   }
 }
 
@@ -546,7 +560,7 @@ __device__ __forceinline__ int tc_imag_col(int j) {
 template <int U>
 __device__ __forceinline__ void tc_stage(uint32_t tmem, bool left, uint32_t cP, uint32_t cQ, uint8_t* ldst,
                                          uint8_t* bdst, int q, int h, int l) {
-  constexpr int CW = TcCols<U>::CW, G = TcCols<U>::G, NG = TcCols<U>::NG;
+  constexpr int CW = TcCols<U>::CW;
   const uint32_t lane_off = uint32_t(q * 32) << 16;
   const bool same = left && cP == cQ;
   int i;
@@ -556,31 +570,54 @@ __device__ __forceinline__ void tc_stage(uint32_t tmem, bool left, uint32_t cP, 
   // the right operand (and, for P = Q, the left one from the same pieces), then the left one
   tmem_ld_n<CW>(tmem + lane_off + cQ + uint32_t(h * CW), r);
   tmem_ld_wait();
-  if (valid) {
+  if constexpr (CW == 16) {
+    if (valid) {
 #pragma unroll
-    for (int t = 0; t < NG; ++t) {
-      const int g = t;
-      const int j0 = h * CW + g * G;  // master columns j0 .. j0 + G - 1
-      uint32_t v[G];
-      tc_take_group<U>(r, g, v);
+      for (int g = 0; g < 2; ++g) {
+        const int j0 = h * CW + 8 * g;  // master columns j0 .. j0 + 7
+        uint32_t v[8];
+        tc_take8(r, g, v);
+        const uint32_t boff = bt_mn_offset(i, im ? U + tc_imag_col<U>(j0) : j0);
+        if (same)
+          tc_put_group<8, true>(v, bdst, boff, ldst, bt_sw128_offset(l, j0));
+        else
+          tc_put_group<8, false>(v, bdst, boff, nullptr, 0);
+      }
+    }
+  } else if (valid) {
+    tc_for_groups<U>(h, [&](auto width, auto first) {
+      constexpr int W = decltype(width)::value, S = decltype(first)::value;
+      const int j0 = h * CW + S;  // master columns j0 .. j0 + W - 1
+      uint32_t v[W];
+#pragma unroll
+      for (int e = 0; e < W; ++e) v[e] = r[S + e];
       const uint32_t boff = bt_mn_offset(i, im ? U + tc_imag_col<U>(j0) : j0);
       if (same)
-        tc_put_group<G, true>(v, bdst, boff, ldst, bt_sw128_offset(l, j0));
+        tc_put_group<W, true>(v, bdst, boff, ldst, bt_sw128_offset(l, j0));
       else
-        tc_put_group<G, false>(v, bdst, boff, nullptr, 0);
-    }
+        tc_put_group<W, false>(v, bdst, boff, nullptr, 0);
+    });
   }
   if (left && !same) {
     tmem_ld_n<CW>(tmem + lane_off + cP + uint32_t(h * CW), r);
     tmem_ld_wait();
-    if (valid) {
+    if constexpr (CW == 16) {
+      if (valid) {
 #pragma unroll
-      for (int t = 0; t < NG; ++t) {
-        const int g = t;
-        uint32_t v[G];
-        tc_take_group<U>(r, g, v);
-        tc_put_group<G, false>(v, ldst, bt_sw128_offset(l, h * CW + g * G), nullptr, 0);
+        for (int g = 0; g < 2; ++g) {
+          uint32_t v[8];
+          tc_take8(r, g, v);
+          tc_put_group<8, false>(v, ldst, bt_sw128_offset(l, h * CW + 8 * g), nullptr, 0);
+        }
       }
+    } else if (valid) {
+      tc_for_groups<U>(h, [&](auto width, auto first) {
+        constexpr int W = decltype(width)::value, S = decltype(first)::value;
+        uint32_t v[W];
+#pragma unroll
+        for (int e = 0; e < W; ++e) v[e] = r[S + e];
+        tc_put_group<W, false>(v, ldst, bt_sw128_offset(l, h * CW + S), nullptr, 0);
+      });
     }
   }
 }
@@ -804,7 +841,7 @@ template <int U>
 __device__ __forceinline__ float tc_load_matrix(const float2* A, float damping, uint8_t* acache, uint32_t tmem,
                                                 uint32_t cX, uint32_t cR, float2* x0s, bool first_nest, bool one_step,
                                                 int q, int h, int l) {
-  constexpr int CW = TcCols<U>::CW, G = TcCols<U>::G, NG = TcCols<U>::NG, SP = CW + 1;
+  constexpr int CW = TcCols<U>::CW, SP = CW + 1;
   int i;
   bool im;
   const bool valid_row = tc_lane_row<U>(l, i, im);
@@ -892,12 +929,21 @@ __device__ __forceinline__ float tc_load_matrix(const float2* A, float damping, 
     uint32_t ab[CW];
 #pragma unroll
     for (int t = 0; t < CW; ++t) ab[t] = __float_as_uint(av[t]);
+    if constexpr (CW == 16) {
 #pragma unroll
-    for (int t = 0; t < NG; ++t) {
-      const int g = t;
-      uint32_t v[G];
-      tc_take_group<U>(ab, g, v);
-      tc_put_group<G, false>(v, acache, bt_sw128_offset(l, h * CW + g * G), nullptr, 0);
+      for (int g = 0; g < 2; ++g) {
+        uint32_t v[8];
+        tc_take8(ab, g, v);
+        tc_put_group<8, false>(v, acache, bt_sw128_offset(l, h * CW + 8 * g), nullptr, 0);
+      }
+    } else {
+      tc_for_groups<U>(h, [&](auto width, auto first) {
+        constexpr int W = decltype(width)::value, S = decltype(first)::value;
+        uint32_t v[W];
+#pragma unroll
+        for (int e = 0; e < W; ++e) v[e] = ab[S + e];
+        tc_put_group<W, false>(v, acache, bt_sw128_offset(l, h * CW + S), nullptr, 0);
+      });
     }
   }
   tmem_st_wait();
