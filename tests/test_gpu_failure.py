@@ -7,7 +7,7 @@
 * Non-finite input: NaN or Inf in A (dense chains, every dtype), in one matrix of a batch, or in
   a right-hand side of the sparse chain must be reported as NN_ERR_DIVERGED (the residual is not
   finite, the divergence rule of Algorithm 1's stop test); the other matrices of a batch are
-  unaffected.
+  unaffected, bit for bit.
 """
 import time
 
@@ -130,6 +130,44 @@ def test_non_finite_batch_member_diverges_alone(nn):
             assert sb[k] == nn.NN_ERR_DIVERGED, (k, sb[k])
         else:
             assert sb[k] == sc[k]
+            assert np.array_equal(xb[o:o + u * u], xc[o:o + u * u]), k
+
+
+@pytest.mark.parametrize("u,cfg", [(64, 2), (48, 2), (32, 0), (16, 3)])
+def test_non_finite_member_of_a_size_class(nn, u, cfg):
+    """One size, one path: NaN or Inf on the diagonal of some matrices (each ends as diverged)
+    leaves every other matrix bitwise as in a clean run."""
+    import torch
+
+    count = 25
+    bt = synth.mimo_gram_batch(count, seed=40 + u, sizes=(u,))
+    data_bad = bt.data.copy()
+    k_bad = [0, 5, 12, 24]
+    for j, k in enumerate(k_bad):
+        data_bad[int(bt.offsets[k]) + (j % 3) * (u + 1)] = (np.nan, np.inf, -np.inf, np.nan)[j]
+    plan_h = nn.nn_batched_plan(bt.sizes, {u: cfg})
+    out = {}
+    for label, data in (("clean", bt.data), ("bad", data_bad)):
+        A = torch.from_numpy(data.astype(np.complex64)).cuda()
+        X = torch.empty_like(A)
+        res = torch.empty(bt.count, dtype=torch.float32, device="cuda")
+        st = torch.empty(bt.count, dtype=torch.int32, device="cuda")
+        ws = torch.empty(nn.nn_batched_workspace_bytes(bt.count), dtype=torch.uint8, device="cuda")
+        assert nn.nn_invert_batched(A, torch.from_numpy(bt.offsets.astype(np.int64)).cuda(),
+                                    torch.from_numpy(bt.sizes.astype(np.int32)).cuda(), 2, 3, 1.0 / 128.0,
+                                    torch.from_numpy(plan_h).cuda(), X, res, st, ws,
+                                    classes=nn.nn_batched_plan_classes(plan_h)) == nn.NN_OK
+        torch.cuda.synchronize()
+        out[label] = (X.cpu().numpy(), st.cpu().numpy(), res.cpu().numpy())
+    xc, sc, rc = out["clean"]
+    xb, sb, rb = out["bad"]
+    assert np.all(sc == nn.NN_OK)
+    for k in range(bt.count):
+        o = int(bt.offsets[k])
+        if k in k_bad:
+            assert sb[k] == nn.NN_ERR_DIVERGED, (k, sb[k])
+        else:
+            assert sb[k] == nn.NN_OK and rb[k] == rc[k], k
             assert np.array_equal(xb[o:o + u * u], xc[o:o + u * u]), k
 
 
