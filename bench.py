@@ -795,6 +795,44 @@ def run_sparse(args, rank, world, local_rank):
     vb = 8 if dtype == np.float64 else 4
     chain, products, resid = sparse_chain_bytes(m.n, m.nnz, depth, nests, vb)
     gbs = (chain + resid) / (ms / 1e3) / 1e9
+    # end to end through the public call: per step the right-hand side from pinned host memory,
+    # the solve, and x back to pinned host memory (the matrix stays resident: the operator)
+    e2e = None
+    if not args.no_e2e:
+        B_h = torch.from_numpy(np.ascontiguousarray(b.T)).pin_memory()
+        X_h = torch.empty_like(B_h).pin_memory()
+        e_steps = 10
+        for i in range(e_steps + 2):
+            if i == 2:
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            B.copy_(B_h, non_blocking=True)
+            st_e, _ = abi.nn_solve_csr(rp, col, val, B, depth, nests, 0.0, X, ws, stream, double_float=dfl)
+            X_h.copy_(X, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e_ms = e0.elapsed_time(e1) / e_steps
+        e2e = {"value": round((chain + resid) / (e_ms / 1e3) / 1e9, 1), "unit": "GB/s",
+               "ms_per_step": round(e_ms, 3), "h2d_bytes_per_step": int(B_h.numel() * B_h.element_size()),
+               "d2h_bytes_per_step": int(X_h.numel() * X_h.element_size()), "steps": e_steps,
+               "ok": st_e == abi.NN_OK, "call": "nn_solve_csr (b in, x out, pinned host buffers)"}
+    # the CPU oracle as it stands (SciPy CSR products) on a bounded sample: its first two factors
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        import scipy.sparse as sps
+
+        from oracle import sparse as osparse
+
+        a = sps.csr_matrix((m.val.astype(np.float64), m.col, m.row_ptr), shape=(m.n, m.n))
+        sample_nests = 2
+        t0 = time.perf_counter()
+        osparse.nn_sparse_solve(a, b[:, :1].astype(np.float64), depth, sample_nests)
+        t = time.perf_counter() - t0
+        s_chain, s_products, _ = sparse_chain_bytes(m.n, m.nnz, depth, sample_nests, 8)
+        cpu = {"value": round(s_chain / t / 1e9, 2), "unit": "GB/s", "cores": host_cores(), "kind": "oracle",
+               "sample": f"the chain's first {sample_nests} factors ({s_products} sparse products) of the FP64 "
+                         f"SciPy oracle on the same matrix and b, {t:.2f} s"}
     peaks, src = load_peaks()
     peak = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
     return {"metric": "HBM GB/s of the sparse NN chain (5-point Laplacian 2048^2, depth 2)",
@@ -807,6 +845,7 @@ def run_sparse(args, rank, world, local_rank):
                                    f"depth {depth}, {nests} factors ({products} sparse products)",
                        "n": m.n, "nnz": m.nnz, "l2": "matrix larger than L2 (streams every product)"},
             "status_ok": st == abi.NN_OK, "residual": res["residual"], "gpu_launches": launches,
+            "e2e": e2e, "cpu_baseline": cpu,
             "roofline": {"kernel": ("nn::spmv_ring_kernel" if args.spmv_variant == 0 else "nn::spmv_p_kernel")
                          + " (whole chain timed, residual products and reductions included)", "bound": "hbm", "achieved": round(gbs, 1),
                          "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
@@ -911,6 +950,52 @@ def run_batched(args, rank, world, local_rank):
         # restore the whole batch's results (the class-0 runs rewrote only its own items)
         g.replay()
         torch.cuda.synchronize(dev)
+    # end to end through the public call: per step the batch's A from pinned host memory, the
+    # call, and X, residual and status back to pinned host memory
+    e2e = None
+    if not args.no_e2e and world == 1:
+        A_h = torch.from_numpy(bt.data).pin_memory()
+        X_h = torch.empty_like(A_h).pin_memory()
+        res_h = torch.empty(count, dtype=torch.float32).pin_memory()
+        st_h = torch.empty(count, dtype=torch.int32).pin_memory()
+        e_steps = 20
+
+        def e2e_step():
+            A.copy_(A_h, non_blocking=True)
+            assert abi.nn_invert_batched_c64(A, offs, sizes, plan, depth, nests, damping, X, res, st, ws,
+                                             classes=classes) == 0
+            X_h.copy_(X, non_blocking=True)
+            res_h.copy_(res, non_blocking=True)
+            st_h.copy_(st, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e_ms = e0.elapsed_time(e1) / e_steps
+        e2e = {"value": round(count / (e_ms / 1e3), 1), "unit": "inversions/s", "ms_per_step": round(e_ms, 4),
+               "h2d_bytes_per_step": int(A_h.numel() * A_h.element_size()),
+               "d2h_bytes_per_step": int(X_h.numel() * X_h.element_size() + 4 * count + 4 * count),
+               "steps": e_steps, "ok": bool(np.all(st_h.numpy() == 0)),
+               "call": "nn_invert_batched_c64 (A in, X, residual and status out, pinned host buffers)"}
+    # the CPU oracle as it stands (complex128 loop) on a bounded sample of the same batch
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        from oracle import batched as obatched
+
+        sample = min(count, 1024)
+        mats = [bt.matrix(k).astype(np.complex128) for k in range(sample)]
+        t0 = time.perf_counter()
+        obatched.nn_batched(mats, depth, nests, damping=lambda n: 1.0 / (1.0 + damping * n))
+        t = time.perf_counter() - t0
+        cpu = {"value": round(sample / t, 1), "unit": "inversions/s", "cores": host_cores(), "kind": "oracle",
+               "sample": f"the first {sample} matrices of the batch (same sizes mix), complex128 NumPy loop, "
+                         f"{t:.2f} s"}
     total = count
     if world > 1:
         t = torch.tensor([ms, float(count)], device=dev, dtype=torch.float64)
@@ -974,6 +1059,7 @@ def run_batched(args, rank, world, local_rank):
                                        "no data-path collective") if world > 1 else "single GPU",
                        "tensor_core_items": bool(args.batched_tc) or any(v == 2 for v in (table or {}).values())},
             "status_ok_fraction": float(np.mean(stats == 0)), "gpu_launches": bin(classes).count("1") * args.steps,
+            "e2e": e2e, "cpu_baseline": cpu,
             "tflops": round(tflops, 2), "gbs": round(byts / (ms / 1e3) / 1e9, 1),
             "roofline": dict(roof, method_tflops=round(tflops, 2),
                              hbm_frac=round(byts / (ms / 1e3) / 1e9 / float(peaks.get('hbm_gbs', 6800.0)), 4)),
