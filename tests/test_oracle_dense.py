@@ -155,6 +155,28 @@ def test_preconditioners_satisfy_norm_condition():
     assert np.max(np.abs(np.linalg.eigvals(np.eye(30) - dd @ dense.precond_jacobi(dd)))) < 1.0
 
 
+def test_pan_schreiber_complex_start():
+    # Section II allows W in C^{N x N}: X_0 = W^H / (||W||_1 ||W||_inf) makes W X_0 Hermitian
+    # positive definite with eigenvalues sigma_i^2 / (||W||_1 ||W||_inf) in (0, 1] (sigma_max^2 <=
+    # ||W||_1 ||W||_inf), so I - W X_0 has its spectrum in [0, 1) and the NN loop converges to
+    # W^-1. A dropped conjugate (W^T) breaks the Hermitian property and the convergence.
+    r = synth.rng(6)
+    n = 24
+    w = r.standard_normal((n, n)) + 1j * r.standard_normal((n, n))
+    x0 = dense.precond_pan_schreiber(w)
+    m = w @ x0
+    assert np.allclose(m, m.conj().T, rtol=0, atol=1e-14)
+    ev = np.linalg.eigvalsh(m)
+    assert ev.min() > 0 and ev.max() <= 1 + 1e-12
+    assert np.linalg.norm(np.eye(n) - m, 2) < 1.0
+    run = dense.nn_invert(w, x0, 2, tol=1e-12, max_nests=40)
+    assert run.status == dense.STATUS_OK
+    assert np.linalg.norm(run.x @ w - np.eye(n)) < 1e-9
+    # the transpose without conjugation is not a convergent start for this W
+    bad = w.T / (np.max(np.sum(np.abs(w), axis=0)) * np.max(np.sum(np.abs(w), axis=1)))
+    assert np.max(np.abs(np.linalg.eigvals(np.eye(n) - w @ bad))) >= 1.0
+
+
 # --- the paper's only printed numeric claim (Corollary 3) ---------------------------
 
 def test_corollary3_normal_equations_claim():
