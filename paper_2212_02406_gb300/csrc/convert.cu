@@ -38,8 +38,8 @@ __device__ __forceinline__ bool split_hi_lo_int(double v, float& hi, float& lo) 
   return true;
 }
 
-__device__ __forceinline__ float pieces3(double v, __nv_bfloat16 (&p)[3]) {
-  float hi, lo;
+// v = hi + lo (hi = fp32(v), lo = fp32(v - hi)), by split_hi_lo_int where it applies.
+__device__ __forceinline__ void split_hi_lo(double v, float& hi, float& lo) {
   const unsigned long long vb = static_cast<unsigned long long>(__double_as_longlong(v));
   if ((vb << 1) == 0) {
     hi = __uint_as_float(unsigned(vb >> 32) & 0x80000000u);  // +-0
@@ -48,11 +48,40 @@ __device__ __forceinline__ float pieces3(double v, __nv_bfloat16 (&p)[3]) {
     hi = static_cast<float>(v);
     lo = static_cast<float>(v - static_cast<double>(hi));
   }
+}
+
+// The three pieces of hi + lo (|lo| at most half an FP32 ulp of hi); returns hi.
+__device__ __forceinline__ float pieces3_hl(float hi, float lo, __nv_bfloat16 (&p)[3]) {
   p[0] = __float2bfloat16_rn(hi);
   const float t = (hi - __bfloat162float(p[0])) + lo;
   p[1] = __float2bfloat16_rn(t);
   p[2] = __float2bfloat16_rn(t - __bfloat162float(p[1]));
   return hi;
+}
+
+__device__ __forceinline__ float pieces3(double v, __nv_bfloat16 (&p)[3]) {
+  float hi, lo;
+  split_hi_lo(v, hi, lo);
+  return pieces3_hl(hi, lo, p);
+}
+
+// scale v + d as an unevaluated FP32 pair (hi, lo), hi the FP32 rounding of the pair's sum, from
+// v = vh + vl, scale = sh + sl and d = dh + dl without FP64 arithmetic (the FP64 pipe is
+// narrow): the product sh vh exactly as p + pe (FMA), the cross terms sh vl + sl vh rounded in
+// FP32 (they are below 2^-23 |scale v|; sl vl, below 2^-46, is dropped), p + dh exactly as a
+// two-sum, then one renormalisation. The pair carries scale v + d to about 2^-45
+// max(|scale v|, |d|), far below the 2^-24 of the three BF16 pieces made from it.
+__device__ __forceinline__ void affine_hi_lo(float vh, float vl, float sh, float sl, float dh, float dl, float& hi,
+                                             float& lo) {
+  const float p = sh * vh;
+  const float pe = fmaf(sh, vh, -p);
+  const float cross = fmaf(sh, vl, sl * vh) + pe;
+  const float s = p + dh;
+  const float bp = s - p;
+  const float se = (p - (s - bp)) + (dh - bp);
+  const float t = (se + cross) + dl;
+  hi = s + t;
+  lo = t - (hi - s);
 }
 
 // Four consecutive FP32 source values of row i from column jj (zeros past n), widened to FP64
@@ -124,11 +153,17 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
     double v[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) v[e] = vin[rr][e];
+    // AFFINE: the source's FP32 pairs, shared by its own pieces (DUAL) and the affine output
+    float vh[4], vl[4];
+    if (AFFINE) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) split_hi_lo(v[e], vh[e], vl[e]);
+    }
     if (DUAL) {
       __nv_bfloat16 pd[4][3];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float h = pieces3(v[e], pd[e]);
+        const float h = pieces3_hl(vh[e], vl[e], pd[e]);
         ss_src = fmaf(h, h, ss_src);
       }
       const int64_t off = int64_t(i) * np + jj;
@@ -139,17 +174,28 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
         *reinterpret_cast<uint2*>(dual_row.p[q] + off) = make_uint2(lo2, hi2);
       }
     }
-    if (AFFINE) {
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (i < n && jj + e < n) v[e] = scale * v[e] + (i == jj + e ? diag : 0.0);
-    }
     __nv_bfloat16 pc[4][3];
     float hi[4];
+    if (AFFINE) {
+      // scale v + diag I in FP32 pairs (padding rows and columns stay zero)
+      const float sh = static_cast<float>(scale), sl = static_cast<float>(scale - static_cast<double>(sh));
+      const float dh = static_cast<float>(diag), dl = static_cast<float>(diag - static_cast<double>(dh));
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      hi[e] = pieces3(v[e], pc[e]);
-      ss = fmaf(hi[e], hi[e], ss);
+      for (int e = 0; e < 4; ++e) {
+        float h = 0.f, l = 0.f;
+        if (i < n && jj + e < n) {
+          const bool on = i == jj + e;
+          affine_hi_lo(vh[e], vl[e], sh, sl, on ? dh : 0.f, on ? dl : 0.f, h, l);
+        }
+        hi[e] = pieces3_hl(h, l, pc[e]);
+        ss = fmaf(hi[e], hi[e], ss);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        hi[e] = pieces3(v[e], pc[e]);
+        ss = fmaf(hi[e], hi[e], ss);
+      }
     }
     const int64_t off = int64_t(i) * np + jj;
     if (f32) *reinterpret_cast<float4*>(f32 + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
