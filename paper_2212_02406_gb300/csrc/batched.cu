@@ -178,6 +178,7 @@ struct BatchedParams {
   int32_t* status;
   int* queue;
   int* err;     // device error word of the tensor-core path's bounded waits
+  int withhold;  // failure-detection test hook: each CTA's MMA warp withholds its first commit
 };
 
 // Sum over the threads of one group (nthr = TG*TG threads, whole warps), result in red_out[g].
@@ -1293,7 +1294,9 @@ __global__ void __launch_bounds__(btc::BLOCK, 1) batched_tc_kernel(const Batched
     if (threadIdx.x >= btc::THREADS + 32) {
       tc_claimer<U>(p, cls, first, last, items, &mb, &abort_word);
     } else if (threadIdx.x >= btc::THREADS) {
-      // the MMA warp: one chain per handed-over product until the workers send exit
+      // the MMA warp: one chain per handed-over product until the workers send exit (test hook:
+      // the first chain's completion is never signalled, so the workers' bounded wait runs out)
+      bool first_chain = true;
       while (true) {
         tc_handoff_wait();
         const TcCmd c = cmd;
@@ -1301,8 +1304,9 @@ __global__ void __launch_bounds__(btc::BLOCK, 1) batched_tc_kernel(const Batched
         if (threadIdx.x == btc::THREADS) {
           tc_fence_after();
           tc_issue<U>(c.d_tmem, c.l_saddr, c.b_saddr);
-          tc_commit(&mma_bar);
+          if (!(p.withhold && first_chain)) tc_commit(&mma_bar);
         }
+        first_chain = false;
         __syncwarp();
       }
     } else {
@@ -1678,6 +1682,7 @@ int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* 
   p.status = status;
   p.queue = static_cast<int*>(workspace);
   p.err = static_cast<int*>(workspace) + BT_QUEUE_ERR;
+  p.withhold = 0;
   NN_CUDA_TRY(cudaMemsetAsync(p.queue, 0, nn_batched_workspace_bytes(count), st));
   // the classes' kernels in class order; each after the first may start as the previous
   // one's CTAs retire (programmatic dependent launch)
@@ -1711,7 +1716,9 @@ int nn_invert_batched_c64(const void* A, const int64_t* offsets, const int32_t* 
       cfg.blockDim = dim3(unsigned(32 * bw::warps_per_cta(U, bufs)));
       cfg.dynamicSmemBytes = size_t(warp_smem(U, bufs));
     }
-    NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, p, c));
+    BatchedParams pc = p;
+    if (c < 2) pc.withhold = tc_take_withhold();  // the test hook goes to the first tensor-core class
+    NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, pc, c));
     cfg.numAttrs = 1;
   }
   return NN_OK;

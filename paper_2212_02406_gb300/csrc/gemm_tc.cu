@@ -712,6 +712,7 @@ bool tc_supported() {
 }
 
 void gemm_tc_withhold_next(int on) { g_withhold.store(on ? 1 : 0); }
+int tc_take_withhold() { return g_withhold.exchange(0); }
 
 void gemm_tc_set_variant(int v) { g_variant = (v == 1 || v == 3 || v == 4) ? v : 0; }
 
@@ -780,7 +781,7 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
   p.cvt_ld = a.cvt_ld;
   p.cvt_n = a.cvt_n;
   p.cvt_vec = (a.cvt_ld % 2 == 0 && (reinterpret_cast<uintptr_t>(a.cvt_dst) & 15) == 0) ? 1 : 0;
-  p.withhold = g_withhold.exchange(0);
+  p.withhold = tc_take_withhold();
   // Variant choice: the 2-SM MMA with a split last wave by default where the size allows it, else
   // single-CTA tiles.
   const bool even = a.np % (2 * tc::BM) == 0;

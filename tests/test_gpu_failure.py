@@ -3,7 +3,8 @@
 * A device wait that runs out: nn_debug_withhold_signal makes the next tensor-core GEMM's MMA
   issuer withhold one "accumulator ready" signal that nothing else sets. The epilogue's bounded
   wait (about one second) runs out, the kernel returns, and the call reports NN_ERR_TIMEOUT; the
-  context stays usable, and the next call returns the same X as a clean run, bit for bit.
+  context stays usable, and the next call returns the same X as a clean run, bit for bit. The
+  same for the batched tensor-core class: every matrix of the class reports NN_ERR_TIMEOUT.
 * Non-finite input: NaN or Inf in A (dense chains, every dtype), in one matrix of a batch, or in
   a right-hand side of the sparse chain must be reported as NN_ERR_DIVERGED (the residual is not
   finite, the divergence rule of Algorithm 1's stop test); the other matrices of a batch are
@@ -62,6 +63,46 @@ def test_withheld_signal_times_out_and_context_recovers(nn, n, hint):
     st2, res2, x2 = _invert(nn, a, x0, "mixed_bf16", **kw)
     assert st2 == nn.NN_OK and res2["history"] == res0["history"]
     assert np.array_equal(x2, x_clean)
+
+
+def _batched(nn, bt, cfg_by_u):
+    import torch
+
+    plan_h = nn.nn_batched_plan(bt.sizes, cfg_by_u)
+    A = torch.from_numpy(bt.data.astype(np.complex64)).cuda()
+    X = torch.empty_like(A)
+    res = torch.empty(bt.count, dtype=torch.float32, device="cuda")
+    st = torch.empty(bt.count, dtype=torch.int32, device="cuda")
+    ws = torch.empty(nn.nn_batched_workspace_bytes(bt.count), dtype=torch.uint8, device="cuda")
+    assert nn.nn_invert_batched(A, torch.from_numpy(bt.offsets.astype(np.int64)).cuda(),
+                                torch.from_numpy(bt.sizes.astype(np.int32)).cuda(), 2, 3, 1.0 / 128.0,
+                                torch.from_numpy(plan_h).cuda(), X, res, st, ws,
+                                classes=nn.nn_batched_plan_classes(plan_h)) == nn.NN_OK
+    torch.cuda.synchronize()
+    return X.cpu().numpy(), st.cpu().numpy()
+
+
+def test_batched_withheld_signal_times_out_and_recovers(nn):
+    # the hook goes to the first tensor-core class (U = 64): every CTA's first MMA chain never
+    # signals completion, the workers' bounded wait runs out, and every matrix of that class
+    # (those in the slots, the one claimed ahead, the ones still queued) reports NN_ERR_TIMEOUT;
+    # the U = 48 class runs untouched, and the next call equals a clean run bit for bit
+    bt = synth.mimo_gram_batch(400, seed=61, sizes=(64, 48))
+    cfg = {48: 2, 64: 2}
+    x_clean, st_clean = _batched(nn, bt, cfg)
+    assert np.all(st_clean == nn.NN_OK)
+    assert nn.nn_debug_withhold_signal(True) == nn.NN_OK
+    t0 = time.time()
+    x_bad, st_bad = _batched(nn, bt, cfg)
+    assert time.time() - t0 < 30.0
+    big = bt.sizes == 64
+    assert np.all(st_bad[big] == nn.NN_ERR_TIMEOUT), np.unique(st_bad[big])
+    assert np.all(st_bad[~big] == nn.NN_OK)
+    for k in np.flatnonzero(~big):
+        o, u = int(bt.offsets[k]), int(bt.sizes[k])
+        assert np.array_equal(x_bad[o:o + u * u], x_clean[o:o + u * u]), k
+    x2, st2 = _batched(nn, bt, cfg)
+    assert np.array_equal(st2, st_clean) and np.array_equal(x2, x_clean)
 
 
 def test_disarmed_hook_changes_nothing(nn):
