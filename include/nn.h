@@ -158,15 +158,16 @@ typedef struct nn_result {
 int nn_set_gemm_variant(int variant);
 
 /* Failure-detection test hook (the paper has no counterpart). on != 0 arms it for the next
- * tensor-core launch of the process (a GEMM of the dense chains, or the first tensor-core class
- * of an nn_invert_batched_c64 call): that launch's MMA issuer withholds its first "accumulator
- * ready" signal (in a batched class: every CTA's first chain's completion signal), a signal
- * nothing else sets, so the bounded device wait on it (about one second) runs out; every role
- * of the kernel then leaves its loop, in-flight tensor work is drained and TMEM freed, the
- * kernel returns, and the calling entry point reports NN_ERR_TIMEOUT (the batched call: as the
- * status of every matrix of that class) with the CUDA context still usable. The hook disarms
- * itself when that launch takes it; on = 0 disarms it. No fault, trap or endless wait is
- * involved. Returns NN_OK. */
+ * launch of a kernel with bounded device waits (a tensor-core GEMM of the dense chains, the
+ * first tensor-core class of an nn_invert_batched_c64 call, or a sparse product on the
+ * bulk-copy ring): that launch withholds one signal nothing else sets — the MMA issuer's first
+ * "accumulator ready" (in a batched class: every CTA's first chain's completion), or the ring's
+ * first stage in its first block — so the bounded device wait on it (about one second) runs
+ * out; every role of the kernel then leaves its loop, in-flight copies and tensor work are
+ * drained and TMEM freed, the kernel returns, and the calling entry point reports
+ * NN_ERR_TIMEOUT (the batched call: as the status of every matrix of that class) with the CUDA
+ * context still usable. The hook disarms itself when that launch takes it; on = 0 disarms it.
+ * No fault, trap or endless wait is involved. Returns NN_OK. */
 int nn_debug_withhold_signal(int on);
 
 /* Bytes of device workspace nn_invert / nn_residual need for an N x N problem of `dtype`

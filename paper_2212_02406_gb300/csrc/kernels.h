@@ -82,8 +82,9 @@ int gemm_tc_max_grid();
 // tiles, 3: 2-SM MMA, 4: 2-SM MMA with a split last wave (3, 4: NN_ERR_UNSUPPORTED where they
 // do not apply).
 void gemm_tc_set_variant(int v);
-// Arms (on != 0) or disarms the failure-detection test hook for the next tensor-core launch (a
-// GEMM or a batched tensor-core class); tc_take_withhold returns the armed state and disarms it.
+// Arms (on != 0) or disarms the failure-detection test hook for the next launch of an
+// instrumented kernel (a tensor-core GEMM, a batched tensor-core class, a sparse ring product);
+// tc_take_withhold returns the armed state and disarms it.
 void gemm_tc_withhold_next(int on);
 int tc_take_withhold();
 

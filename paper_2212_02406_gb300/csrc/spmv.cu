@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4)
 spmv_ring_kernel(int n, int nnz, const int* __restrict__ row_ptr, const int* __restrict__ col,
                  const typename P::V* __restrict__ val, const typename P::V* v, typename P::V* y,
                  const typename P::V* acc_in, typename P::V* acc_out, const typename P::In* b, int mode,
-                 double* __restrict__ partial, int* err) {
+                 double* __restrict__ partial, int* err, int withhold) {
   using V = typename P::V;
   using L = StLayout<P>;
   extern __shared__ __align__(128) uint8_t st_smem[];
@@ -320,6 +320,9 @@ spmv_ring_kernel(int n, int nnz, const int* __restrict__ row_ptr, const int* __r
     int stage = 0;
     uint32_t phase = 0;
     bool stop = false;
+    // failure-detection test hook: block 0 never fills its first stage, so its consumers'
+    // bounded wait on it runs out (the later stages' copies land long before)
+    bool skip_first = withhold != 0 && blockIdx.x == 0;
     for (int t0 = blockIdx.x; t0 < tiles && !stop; t0 += 32 * int(gridDim.x)) {
       // lane j fetches the nonzero range of the block's j-th next tile
       const int tj = t0 + lane * int(gridDim.x);
@@ -338,7 +341,9 @@ spmv_ring_kernel(int n, int nnz, const int* __restrict__ row_ptr, const int* __r
         bool first = true;
         while (true) {
           const int end = min(base + ST_CAP, e1);
-          if (lane == 0) {
+          if (lane == 0 && skip_first) {
+            skip_first = false;
+          } else if (lane == 0) {
             if (mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err)) {
               const int copy_end = max(base, min((end + 3) & ~3, nnz4));
               const int rows = first ? max(0, min(ST_ROWBUF, rows4 - r0)) : 0;
@@ -647,7 +652,7 @@ int spmv(cudaStream_t st, int n, int nnz, const int* rp, const int* col, const t
       NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, spmv_ring_kernel<P>, n, nnz, rp, col, vals, v + off,
                                      y ? y + off : nullptr, acc_in ? acc_in + off : nullptr,
                                      acc_out ? acc_out + off : nullptr, b ? b + int64_t(r0) * ldb : nullptr, mode,
-                                     part, err));
+                                     part, err, tc_take_withhold()));
     } else if (nr == 1) {
       spmv_p_kernel<P, 1><<<blocks, SP_ROWS, 0, st>>>(n, rp, col, vals, v + off, n, y ? y + off : nullptr, n,
                                                       acc_in ? acc_in + off : nullptr, acc_out ? acc_out + off : nullptr,

@@ -4,7 +4,8 @@
   issuer withhold one "accumulator ready" signal that nothing else sets. The epilogue's bounded
   wait (about one second) runs out, the kernel returns, and the call reports NN_ERR_TIMEOUT; the
   context stays usable, and the next call returns the same X as a clean run, bit for bit. The
-  same for the batched tensor-core class: every matrix of the class reports NN_ERR_TIMEOUT.
+  same for the batched tensor-core class (every matrix of the class reports NN_ERR_TIMEOUT) and
+  for the sparse chain's bulk-copy ring (its first block never fills its first stage).
 * Non-finite input: NaN or Inf in A (dense chains, every dtype), in one matrix of a batch, or in
   a right-hand side of the sparse chain must be reported as NN_ERR_DIVERGED (the residual is not
   finite, the divergence rule of Algorithm 1's stop test); the other matrices of a batch are
@@ -103,6 +104,37 @@ def test_batched_withheld_signal_times_out_and_recovers(nn):
         assert np.array_equal(x_bad[o:o + u * u], x_clean[o:o + u * u]), k
     x2, st2 = _batched(nn, bt, cfg)
     assert np.array_equal(st2, st_clean) and np.array_equal(x2, x_clean)
+
+
+def test_sparse_ring_withheld_stage_times_out_and_recovers(nn):
+    # the hook goes to the chain's first product on the bulk-copy ring: its first block never
+    # fills its first stage, the consumers' bounded wait runs out, and the solve reports
+    # NN_ERR_TIMEOUT; the next solve equals a clean one bit for bit
+    import torch
+
+    m = synth.laplacian_5pt(64, shift=0.5)
+    b = synth.gaussian_rhs(m.n, 1, seed=3)
+    rp = torch.from_numpy(m.row_ptr.astype(np.int32)).cuda()
+    col = torch.from_numpy(m.col.astype(np.int32)).cuda()
+    val = torch.from_numpy(m.val).cuda()
+    B = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()
+    ws = nn.csr_workspace(m.n, m.nnz, 1, "f64")
+
+    def solve():
+        X = torch.empty_like(B)
+        st, res = nn.nn_solve_csr(rp, col, val, B, 2, 3, 0.0, X, ws)
+        torch.cuda.synchronize()
+        return st, X.cpu().numpy()
+
+    st0, x0 = solve()
+    assert st0 == nn.NN_OK
+    assert nn.nn_debug_withhold_signal(True) == nn.NN_OK
+    t0 = time.time()
+    st1, _ = solve()
+    assert st1 == nn.NN_ERR_TIMEOUT, st1
+    assert time.time() - t0 < 30.0
+    st2, x2 = solve()
+    assert st2 == nn.NN_OK and np.array_equal(x2, x0)
 
 
 def test_disarmed_hook_changes_nothing(nn):
