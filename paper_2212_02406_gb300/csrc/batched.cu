@@ -62,6 +62,17 @@ __host__ __device__ constexpr int bt_class(int cfg, int U) {
 
 enum : int { BM_RESID = 0, BM_ADD = 1 };
 
+// Row pitch (complex elements) of the shared-memory tiles of the CUDA-core classes. An exact
+// class (U a multiple of TG) pads its rows to the smallest pitch with pitch % 16 in {4, 12}:
+// the four rows that one warp of an 8 x 8 group touches then start 8 banks apart, so the
+// 16-byte loads of P (four rows, one k pair) take one wavefront instead of four and the
+// 8-byte stores of the epilogue (four rows of eight elements) two instead of four; the two
+// rows of a 16 x 16 group's warp fall in different banks as well. Other classes keep pitch U.
+__host__ __device__ constexpr int bt_pad_pitch(int U) {
+  return U % 16 <= 4 ? U - U % 16 + 4 : (U % 16 <= 12 ? U - U % 16 + 12 : U - U % 16 + 20);
+}
+__host__ __device__ constexpr int bt_simt_pitch(int U, int TG) { return U % TG == 0 ? bt_pad_pitch(U) : U; }
+
 // acc = P Q for this thread's part of a U x U complex group tile: thread (ti, tj) of the
 // TG x TG group owns rows ti + a TG and columns tj + b TG. UC > 0 fixes U = UC = T * TG at
 // compile time (no bounds tests, static addressing); UC = 0 handles any U <= T * TG.
@@ -70,6 +81,7 @@ __device__ __forceinline__ void group_acc(int U_rt, int ti, int tj, const float2
                                           float2 (&acc)[T][T]) {
   const int U = UC > 0 ? UC : U_rt;
   constexpr bool exact = UC > 0 && UC == T * TG;
+  const int ld = exact ? bt_pad_pitch(UC) : U;
 #pragma unroll
   for (int a = 0; a < T; ++a)
 #pragma unroll
@@ -81,12 +93,12 @@ __device__ __forceinline__ void group_acc(int U_rt, int ti, int tj, const float2
     for (int k = 0; k < UC; k += 2) {
       float4 pa2[T];
 #pragma unroll
-      for (int a = 0; a < T; ++a) pa2[a] = *reinterpret_cast<const float4*>(P + (ti + a * TG) * UC + k);
+      for (int a = 0; a < T; ++a) pa2[a] = *reinterpret_cast<const float4*>(P + (ti + a * TG) * ld + k);
       float2 q0[T], q1[T];
 #pragma unroll
       for (int b = 0; b < T; ++b) {
-        q0[b] = Q[k * UC + tj + b * TG];
-        q1[b] = Q[(k + 1) * UC + tj + b * TG];
+        q0[b] = Q[k * ld + tj + b * TG];
+        q1[b] = Q[(k + 1) * ld + tj + b * TG];
       }
 #pragma unroll
       for (int a = 0; a < T; ++a)
@@ -114,12 +126,12 @@ __device__ __forceinline__ void group_acc(int U_rt, int ti, int tj, const float2
 #pragma unroll
     for (int a = 0; a < T; ++a) {
       const int i = ti + a * TG;
-      pa[a] = (exact || i < U) ? P[i * U + k] : make_float2(0.f, 0.f);
+      pa[a] = (exact || i < U) ? P[i * ld + k] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int b = 0; b < T; ++b) {
       const int j = tj + b * TG;
-      qb[b] = (exact || j < U) ? Q[k * U + j] : make_float2(0.f, 0.f);
+      qb[b] = (exact || j < U) ? Q[k * ld + j] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int a = 0; a < T; ++a)
@@ -142,6 +154,7 @@ __device__ __forceinline__ float group_store(int U_rt, int ti, int tj, const flo
                                              const float2* D, int mode) {
   const int U = UC > 0 ? UC : U_rt;
   constexpr bool exact = UC > 0 && UC == T * TG;
+  const int ld = exact ? bt_pad_pitch(UC) : U;
   float ss = 0.f;
 #pragma unroll
   for (int a = 0; a < T; ++a) {
@@ -156,10 +169,10 @@ __device__ __forceinline__ float group_store(int U_rt, int ti, int tj, const flo
         v = make_float2((i == j ? 1.f : 0.f) - acc[a][b].x, -acc[a][b].y);
         ss = fmaf(v.x, v.x, fmaf(v.y, v.y, ss));
       } else {
-        const float2 d = D[i * U + j];
+        const float2 d = D[i * ld + j];
         v = make_float2(d.x + acc[a][b].x, d.y + acc[a][b].y);
       }
-      out[i * U + j] = v;
+      out[i * ld + j] = v;
     }
   }
   return ss;
@@ -216,22 +229,27 @@ template <int TG, int T, int UC>
 __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, float2* smem, float* red_warp,
                              float* red_grp) {
   constexpr int NTHR = TG * TG;
+  if (UC > 0) U = UC;  // exact classes: compile-time size (static addressing and divisions)
   const int groups = BT_THREADS / NTHR;
   const int g = threadIdx.x / NTHR;
   const int lt = threadIdx.x % NTHR;
   const int ti = lt / TG, tj = lt % TG;
   const bool active = g < groups && g < cnt;
   const int uu = U * U;
+  // tiles are U x ld (ld = bt_simt_pitch); element e of the matrix (row-major) sits at
+  // (e / U) * ld + e % U
+  const int ld = UC > 0 && UC == T * TG ? bt_pad_pitch(UC) : U;
+  const int tile = U * ld;
   const int b = active ? p.plan[PLAN_HDR + start + g] : -1;
-  float2* base = smem + size_t(g < groups ? g : 0) * bt_buffers(p.depth) * uu;
+  float2* base = smem + size_t(g < groups ? g : 0) * bt_buffers(p.depth) * tile;
   float2* Ab = base;
-  float2* Xb = base + uu;
-  float2* Rb = base + 2 * uu;
-  float2* Tb = p.depth >= 3 ? base + 3 * uu : Rb;
+  float2* Xb = base + tile;
+  float2* Rb = base + 2 * tile;
+  float2* Tb = p.depth >= 3 ? base + 3 * tile : Rb;
   const int64_t off = active ? p.offsets[b] : 0;
 
   if (active) {
-    for (int e = lt; e < uu; e += NTHR) Ab[e] = p.A[off + e];
+    for (int e = lt; e < uu; e += NTHR) Ab[(e / U) * ld + e % U] = p.A[off + e];
   }
   __syncthreads();
   if (active) {
@@ -240,11 +258,11 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
       const int i = e / U, j = e % U;
       float2 v = make_float2(0.f, 0.f);
       if (i == j) {
-        const float2 a = Ab[i * U + i];
+        const float2 a = Ab[i * ld + i];
         const float den = a.x * a.x + a.y * a.y;
         v = make_float2(c * a.x / den, -c * a.y / den);
       }
-      Xb[e] = v;
+      Xb[i * ld + j] = v;
     }
   }
   __syncthreads();
@@ -263,10 +281,10 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
       if (!frozen) {
         for (int e = lt; e < uu; e += NTHR) {
           const int i = e / U, j = e % U;
-          const float2 a = Ab[e];
-          const float2 xj = Xb[j * U + j];
+          const float2 a = Ab[i * ld + j];
+          const float2 xj = Xb[j * ld + j];
           const float2 r = make_float2((i == j ? 1.f : 0.f) - (a.x * xj.x - a.y * xj.y), -(a.x * xj.y + a.y * xj.x));
-          Rb[e] = r;
+          Rb[i * ld + j] = r;
           ss = fmaf(r.x, r.x, fmaf(r.y, r.y, ss));
         }
       }
@@ -296,11 +314,12 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
       if (!frozen) {
         for (int e = lt; e < uu; e += NTHR) {
           const int i = e / U, j = e % U;
-          const float2 a = Ab[i * U + i];
+          const float2 a = Ab[i * ld + i];
           const float den = a.x * a.x + a.y * a.y;
           const float2 xi = make_float2(cdamp * a.x / den, -cdamp * a.y / den);
-          const float2 t = make_float2(t_cur[e].x + (i == j ? 1.f : 0.f), t_cur[e].y);
-          Xb[e] = make_float2(xi.x * t.x - xi.y * t.y, xi.x * t.y + xi.y * t.x);
+          const float2 te = t_cur[i * ld + j];
+          const float2 t = make_float2(te.x + (i == j ? 1.f : 0.f), te.y);
+          Xb[i * ld + j] = make_float2(xi.x * t.x - xi.y * t.y, xi.x * t.y + xi.y * t.x);
         }
       }
     } else {
@@ -309,7 +328,7 @@ __device__ void process_item(const BatchedParams& p, int U, int start, int cnt, 
     __syncthreads();
   }
   if (active) {
-    for (int e = lt; e < uu; e += NTHR) p.X[off + e] = Xb[e];
+    for (int e = lt; e < uu; e += NTHR) p.X[off + e] = Xb[(e / U) * ld + e % U];
     if (lt == 0) {
       p.residual[b] = s_last;
       p.status[b] = st;
@@ -1576,7 +1595,7 @@ int bt_init() {
 int group_count(int U, int cfg) {
   if (cfg >= 2) return 1;
   const int by_threads = cfg == 0 ? BT_THREADS / 64 : 1;
-  const int per = bt_buffers(2) * U * U * int(sizeof(float2));
+  const int per = bt_buffers(2) * U * bt_simt_pitch(U, cfg == 0 ? 8 : 16) * int(sizeof(float2));
   int by_smem = BT_SMEM_SIMT / per;
   return std::max(1, std::min(by_threads, by_smem));
 }

@@ -101,6 +101,19 @@ def test_tile_configs_agree(nn, cfg):
     _check(bt, x, res, st, 2, 4, 1.0 / 128.0)
 
 
+@pytest.mark.parametrize("cfg", [0, 1])
+@pytest.mark.parametrize("depth", [2, 3])
+def test_exact_tile_classes_with_padded_rows(nn, cfg, depth):
+    # U a multiple of the thread group's side runs the exact class, whose shared-memory rows are
+    # padded (pitch != U); several matrices of each size per work item for the 8 x 8 groups,
+    # and four buffers per matrix at depth 3
+    sizes = (8, 16, 24, 32, 48, 64)
+    bt = synth.mimo_gram_batch(72, seed=23 + depth, sizes=sizes)
+    assert set(int(u) for u in bt.sizes) == set(sizes)
+    x, res, st = _run(nn, bt, depth, 3, 1.0 / 128.0, cfg_by_u={u: cfg for u in range(1, 65)})
+    assert _check(bt, x, res, st, depth, 3, 1.0 / 128.0) == bt.count
+
+
 @pytest.mark.parametrize("depth", [1, 2, 3])
 @pytest.mark.parametrize("damping", [0.0, 1.0 / 128.0])
 def test_tensor_core_items_match_oracle(nn, depth, damping):
