@@ -4,7 +4,8 @@
 Default workload (one "step" = one full NN inversion to the stop tolerance):
 dense SPD precision sweep, N = 8192, A = Q diag(lambda) Q^T with Q from QR of an N(0,1)
 matrix and lambda log-uniform on [1, kappa = 1e2], X_0 = 2/(lambda_min + lambda_max) I,
-inception depth 2, mixed BF16 tensor-core chain refined to s = ||I - A X||_F / N < 1e-6.
+inception depth 2, mixed tensor-core chain on power-of-two scaled FP16 operand pieces (FP32
+accumulate; ``--dtype mixed_bf16`` for BF16 pieces) refined to s = ||I - A X||_F / N < 1e-6.
 
 Prints one JSON line (rank 0). ``value`` is whole-job algorithmic TFLOP/s (2 N^3 per GEMM,
 (L+1) GEMMs per nest plus the final residual, split passes not counted); ``ms_per_step`` is the
@@ -54,7 +55,8 @@ def parse_args():
     ap.add_argument("--cond", type=float, default=1e2, help="cond(A) of the normal-equations workload")
     ap.add_argument("--kappa", type=float, default=1e2)
     ap.add_argument("--depth", type=int, default=2)
-    ap.add_argument("--dtype", default="mixed_bf16", choices=["mixed_bf16", "f32", "f64", "f64_df", "f64_emu", "mixed_emu"])
+    ap.add_argument("--dtype", default="mixed_f16",
+                    choices=["mixed_bf16", "mixed_f16", "f32", "f64", "f64_df", "f64_emu", "mixed_emu"])
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--damping", type=float, default=1.0 / 128.0)
@@ -248,7 +250,7 @@ def dense_config(args, n, world):
             "gemm_tiling": {0: "auto (2-SM MMA, cta_group::2, split last wave)", 1: "single-CTA tiles",
                             3: "2-SM MMA (cta_group::2)",
                             4: "2-SM MMA, last wave split into 256x128 halves"}[args.gemm_variant],
-            "l2": "inputs larger than L2: A fp64 512 MiB, BF16 operands 128 MiB each per GEMM"}
+            "l2": "inputs larger than L2: A fp64 512 MiB, 16-bit operand pieces 128 MiB each per GEMM"}
 
 
 def time_dense_call(abi, A, X0, opts, dtype, stream, steps, warmup=1):
@@ -310,7 +312,7 @@ def dense_baselines(args, abi, n_main, A_main, X0_main, alpha_main, stream, dev)
                              "residual": res["residual"]}
     A2, alpha2 = make_dense_inputs(2048, args.kappa, args.seed + 1, dev)
     X02 = torch_scalar_x0(A2, alpha2)
-    for dt, x0s in (("f64", 0.0), ("f32", 0.0), ("mixed_bf16", alpha2)):
+    for dt, x0s in (("f64", 0.0), ("f32", 0.0), ("mixed_bf16", alpha2), ("mixed_f16", alpha2)):
         o = abi.make_opts(args.depth, args.tol, 64, dt, x0_scalar=x0s)
         ms, st, res, _ = time_dense_call(abi, A2, X02, o, dt, stream, steps=3)
         out[f"{dt}_n2048"] = {"ms": round(ms, 3), "status_ok": st == abi.NN_OK, "nests": res["nests"],
@@ -403,7 +405,7 @@ def run_dense(args, rank, world, local_rank):
                     "launches": tc_launches, "avg_launch_ms": round(tc_ms / tc_launches, 4),
                     "fp64_equivalent_tflops": round(tc_flops / (tc_ms / 1e3) / 1e12, 3),
                     "flops_per_launch": "2 Np^3 per BF16 slice product, all products of one emulated FP64 GEMM"}
-    elif tc_launches > 0 and tc_ms > 0 and args.dtype != "mixed_bf16":
+    elif tc_launches > 0 and tc_ms > 0 and args.dtype not in ("mixed_bf16", "mixed_f16"):
         achieved = tc_flops / (tc_ms / 1e3) / 1e12
         sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
         peak = simt_peak_tflops(args.dtype, sm_mhz)
@@ -413,27 +415,30 @@ def run_dense(args, rank, world, local_rank):
                     "peak_source": f"{args.dtype} CUDA-core peak from unit counts at {sm_mhz:.0f} MHz",
                     "launches": tc_launches, "avg_launch_ms": round(tc_ms / tc_launches, 4)}
     elif tc_launches > 0 and tc_ms > 0:
-        # algorithmic work per launch: one N x N x N product, 2 N^3 FLOP, however many BF16 piece
-        # passes it takes; the passes' tensor work is reported separately (kernel_efficiency)
+        # algorithmic work per launch: one N x N x N product, 2 N^3 FLOP, however many 16-bit
+        # piece passes it takes; the passes' tensor work is reported separately (kernel_efficiency).
+        # FP16 and BF16 share the nominal dense tensor rate: the measured BF16 peak serves both.
         achieved = tc_launches * 2.0 * float(n) ** 3 / (tc_ms / 1e3) / 1e12
         hw_achieved = tc_flops / (tc_ms / 1e3) / 1e12
         peak, label, burst = bf16_peak(peaks, peak_src, clocks)
+        if args.dtype == "mixed_f16":
+            label += " (fp16 operands: same nominal dense rate as bf16, ratio 1)"
         kernel = "nn::tc::gemm_tc_kernel" if args.gemm_variant == 1 else "nn::tc::gemm_tc_2sm_kernel"
         # ncu DRAM bytes per launch (mean over one step) of the profiled default configuration
         traffic = None
         if (args.gemm_variant in (0, 4) and n == 8192 and args.kappa == 1e2 and args.depth == 2
-                and args.tol == 1e-6 and args.seed == 0):
+                and args.tol == 1e-6 and args.seed == 0 and args.dtype == "mixed_f16"):
             traffic = profile_traffic("gemm_tc_2sm_dense_n8192.md", ["gemm_tc.cu", "nn_dense.cu"])
         roofline = {"kernel": kernel, "bound": "tensor", "achieved": round(achieved, 2),
                     "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                     "frac_of_burst": round(achieved / burst, 4), "traffic": traffic,
                     "peak_source": label, "launches": tc_launches,
                     "avg_launch_ms": round(tc_ms / tc_launches, 4),
-                    "flops_per_launch": "2 N^3: one N x N x N product per launch (BF16 piece passes not counted)",
+                    "flops_per_launch": "2 N^3: one N x N x N product per launch (piece passes not counted)",
                     "kernel_efficiency": {"hw_tflops": round(hw_achieved, 2), "frac": round(hw_achieved / peak, 4),
                                           "passes_per_launch": round(tc_flops / (tc_launches * 2.0 * float(
                                               ((n + 127) // 128) * 128) ** 3), 3),
-                                          "note": "tensor work of every BF16 pass (2 Np^3 each) over the same time"}}
+                                          "note": "tensor work of every piece pass (2 Np^3 each) over the same time"}}
 
     # e2e: the host-buffer C-ABI call, H2D of A and X_0 and D2H of X inside the timed region
     e2e = None
@@ -478,9 +483,9 @@ def run_dense(args, rank, world, local_rank):
 
     refined = None
     baselines = None
-    if args.dtype == "mixed_bf16" and not args.no_refined:
+    if args.dtype in ("mixed_bf16", "mixed_f16") and not args.no_refined:
         refined = dense_refined(args, abi, A, X0, alpha, stream)
-    if args.dtype == "mixed_bf16" and not args.no_baselines:
+    if args.dtype in ("mixed_bf16", "mixed_f16") and not args.no_baselines:
         baselines = dense_baselines(args, abi, n, A, X0, alpha, stream, dev)
 
     cpu = None
@@ -495,7 +500,8 @@ def run_dense(args, rank, world, local_rank):
         "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms_per_step, 3), "time_to_eps_ms": round(ms_per_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"mixed_bf16": "bf16 (tcgen05, fp32 accumulate; refine with split bf16)", "f32": "f32",
+        "dtype": {"mixed_bf16": "bf16 (tcgen05, fp32 accumulate; refine with split bf16)",
+                  "mixed_f16": "f16 (tcgen05, fp32 accumulate; power-of-two scaled split f16 pieces)", "f32": "f32",
                   "f64": "f64", "f64_emu": "f64 (emulated: exact bf16 slices on tcgen05)",
                   "mixed_emu": "bf16 pieces, then f64 emulated with exact bf16 slices (tcgen05)"}[args.dtype],
         "data": "synthetic",
@@ -531,7 +537,7 @@ def run_normal(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     n, cond, depth, tol = args.n, args.cond, args.depth, 1e-10
-    dtype = "f64" if args.dtype in ("mixed_bf16", "f64_df") else args.dtype
+    dtype = "f64" if args.dtype in ("mixed_bf16", "mixed_f16", "f64_df") else args.dtype
     a, sig = synth.general_svd(n, cond, seed=args.seed + rank)
     b = synth.gaussian_rhs(n, 1, seed=args.seed + rank + 1)
     A = torch.from_numpy(a).to(dev)
@@ -679,7 +685,7 @@ def run_sparse_sharded(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     grid, depth, nests = 2048, 2, 5
-    if args.dtype not in ("mixed_bf16", "f64", "f32"):
+    if args.dtype not in ("mixed_bf16", "mixed_f16", "f64", "f32"):
         raise SystemExit("the sharded sparse chain runs FP64 or FP32")
     dtype = np.float32 if args.dtype == "f32" else np.float64
     m = synth.laplacian_5pt(grid, grid * world, shift=0.5, dtype=dtype)

@@ -64,10 +64,20 @@ typedef enum nn_dtype {
                         slice products summed exactly in FP32 and the groups in FP64).
                         Accurate to a few units of 2^-53 normwise. Workspace grows by two sets
                         of BF16 slices (about 2.8 GB at N = 8192)                            */
-  NN_MIXED_EMU = 5   /* dense chain: NN_MIXED_BF16 until the iterate nears the BF16 pieces' floor
+  NN_MIXED_EMU = 5,  /* dense chain: NN_MIXED_BF16 until the iterate nears the BF16 pieces' floor
                         with tol below it, then NN_F64_EMU nests from that iterate (FP64 copy);
                         history and status cover both stages, pieces[k] = 0 for the FP64
                         nests. Reaches FP64-level residuals at a fraction of NN_F64_EMU's cost */
+  NN_MIXED_F16 = 6   /* NN_MIXED_BF16 with FP16 operand pieces (11 significant bits against
+                        BF16's 8, same tensor-core rate): each level's rounding floor is 2^-3
+                        (one piece) to 2^-6 (two) of BF16's, so the chain stays at one piece
+                        longer and certifies a tol with fewer passes. FP16's range is kept by
+                        exact power-of-two scales: every row of A by its own (largest entry
+                        to [2^13, 2^14)), X_k by one from ||X_k||_F, R and T by 2^12. The
+                        entries of R_k and T must stay below 16 in magnitude, which holds
+                        under the convergence condition ||I - A X_0||_2 < 1 (Theorem); beyond
+                        it the pieces overflow, s_k turns non-finite and the call returns
+                        NN_ERR_DIVERGED                                                       */
 } nn_dtype;
 
 /* ---- starting matrix X_0 = Theta (Section II-A, Eq. (normalization), Appendix 1) --------- */

@@ -28,9 +28,9 @@ STATUS_NAMES = {0: "ok", 1: "arg", 2: "diverged", 3: "not_converged", 4: "oom_bu
 NN_RESIDUAL_NOALLOC_MAX_N = 1440
 NN_BATCHED_KERNELS = 22
 
-NN_F64, NN_F32, NN_MIXED_BF16, NN_F64_DF, NN_F64_EMU, NN_MIXED_EMU = 0, 1, 2, 3, 4, 5
+NN_F64, NN_F32, NN_MIXED_BF16, NN_F64_DF, NN_F64_EMU, NN_MIXED_EMU, NN_MIXED_F16 = 0, 1, 2, 3, 4, 5, 6
 DTYPES = {"f64": NN_F64, "f32": NN_F32, "mixed_bf16": NN_MIXED_BF16, "f64_df": NN_F64_DF,
-          "f64_emu": NN_F64_EMU, "mixed_emu": NN_MIXED_EMU}
+          "f64_emu": NN_F64_EMU, "mixed_emu": NN_MIXED_EMU, "mixed_f16": NN_MIXED_F16}
 NN_PC_PAN_SCHREIBER, NN_PC_SCALAR, NN_PC_TRACE, NN_PC_JACOBI, NN_PC_THETA2 = 0, 1, 2, 3, 4
 PRECONDS = {"pan_schreiber": 0, "scalar": 1, "trace": 2, "jacobi": 3, "theta2": 4}
 NN_MAX_HISTORY = 65

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 #include <stddef.h>
 
@@ -28,6 +29,20 @@ namespace nn {
 
 // Device-side error codes written to the workspace's error word.
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD_ARG = 2 };
+
+// One operand piece of x for the tensor cores: its 16-bit pattern, BF16 (half = false) or FP16
+// (half = true), rounded to nearest even, and its value in *val. Piece buffers hold either
+// format; a product reads both operands in the same one.
+__device__ __forceinline__ uint16_t piece_bits(float x, bool half, float* val) {
+  if (half) {
+    const __half h = __float2half_rn(x);
+    *val = __half2float(h);
+    return __half_as_ushort(h);
+  }
+  const __nv_bfloat16 b = __float2bfloat16_rn(x);
+  *val = __bfloat162float(b);
+  return __bfloat16_as_ushort(b);
+}
 
 // Spin limit for every device-side wait: about one second of wall time measured with
 // %globaltimer (nanoseconds). A wait past it records DEV_TIMEOUT and gives up.

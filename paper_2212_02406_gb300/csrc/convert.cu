@@ -50,19 +50,28 @@ __device__ __forceinline__ void split_hi_lo(double v, float& hi, float& lo) {
   }
 }
 
-// The three pieces of hi + lo (|lo| at most half an FP32 ulp of hi); returns hi.
-__device__ __forceinline__ float pieces3_hl(float hi, float lo, __nv_bfloat16 (&p)[3]) {
-  p[0] = __float2bfloat16_rn(hi);
-  const float t = (hi - __bfloat162float(p[0])) + lo;
-  p[1] = __float2bfloat16_rn(t);
-  p[2] = __float2bfloat16_rn(t - __bfloat162float(p[1]));
+// The three pieces (bit patterns, BF16 or FP16) of s (hi + lo) (|lo| at most half an FP32 ulp of
+// hi, s a power of two: the scaling is exact); returns hi. Each remainder before a rounding is
+// exact in FP32.
+__device__ __forceinline__ float pieces3_hl(float hi, float lo, float s, bool half, uint16_t (&p)[3]) {
+  float v0, v1, v2;
+  const float hs = hi * s;
+  p[0] = piece_bits(hs, half, &v0);
+  const float t = (hs - v0) + lo * s;
+  p[1] = piece_bits(t, half, &v1);
+  p[2] = piece_bits(t - v1, half, &v2);
   return hi;
 }
 
-__device__ __forceinline__ float pieces3(double v, __nv_bfloat16 (&p)[3]) {
+__device__ __forceinline__ float pieces3(double v, float s, bool half, uint16_t (&p)[3]) {
   float hi, lo;
   split_hi_lo(v, hi, lo);
-  return pieces3_hl(hi, lo, p);
+  return pieces3_hl(hi, lo, s, half, p);
+}
+
+// The piece scale of padded row i under fmt.
+__device__ __forceinline__ float row_piece_scale(const PieceFmt& fmt, int i) {
+  return fmt.row_scale != nullptr ? fmt.scale * fmt.row_scale[i] : fmt.scale;
 }
 
 // scale v + d as an unevaluated FP32 pair (hi, lo), hi the FP32 rounding of the pair's sum, from
@@ -124,15 +133,16 @@ __device__ __forceinline__ void split_load4(const double* src, int64_t lds, int 
 }
 
 // Splits the n x n matrix scale * src + diag * I (FP64 arithmetic; AFFINE = false: src as is)
-// into its FP32 rounding and BF16 pieces.
+// into its FP32 rounding and operand pieces (format and piece scales: fmt).
 // DUAL (with AFFINE): the same pass also writes the three row-major pieces of src itself to
-// dual_row, with its per-block sums of squares in dual_sumsq (one read of src for both).
+// dual_row (format dual_fmt), with its per-block sums of squares in dual_sumsq (one read of src
+// for both).
 template <typename S, bool AFFINE, bool DUAL = false>
 __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int np, float* __restrict__ f32,
                              PiecePtrs row, int n_row, PiecePtrs col, int n_col, double* __restrict__ sumsq,
-                             double scale, double diag, PiecePtrs dual_row = PiecePtrs{},
-                             double* __restrict__ dual_sumsq = nullptr, int yb0 = 0) {
-  __shared__ __nv_bfloat16 tile[3][SPLIT_R][SPLIT_C + 2];  // odd word pitch: conflict-free columns
+                             double scale, double diag, PieceFmt fmt, PiecePtrs dual_row = PiecePtrs{},
+                             double* __restrict__ dual_sumsq = nullptr, int yb0 = 0, PieceFmt dual_fmt = PieceFmt{}) {
+  __shared__ uint16_t tile[3][SPLIT_R][SPLIT_C + 2];  // odd word pitch: conflict-free columns
   __shared__ float red[ROWS];
   // yb0: first block row (a launch may cover a panel of rows; partial sums keep global indices)
   const int yb = int(blockIdx.y) + yb0;
@@ -159,22 +169,24 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
 #pragma unroll
       for (int e = 0; e < 4; ++e) split_hi_lo(v[e], vh[e], vl[e]);
     }
+    const float ps = row_piece_scale(fmt, i);
     if (DUAL) {
-      __nv_bfloat16 pd[4][3];
+      uint16_t pd[4][3];
+      const float ds = row_piece_scale(dual_fmt, i);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float h = pieces3_hl(vh[e], vl[e], pd[e]);
+        const float h = pieces3_hl(vh[e], vl[e], ds, dual_fmt.half, pd[e]);
         ss_src = fmaf(h, h, ss_src);
       }
       const int64_t off = int64_t(i) * np + jj;
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        const uint32_t lo2 = uint32_t(__bfloat16_as_ushort(pd[0][q])) | (uint32_t(__bfloat16_as_ushort(pd[1][q])) << 16);
-        const uint32_t hi2 = uint32_t(__bfloat16_as_ushort(pd[2][q])) | (uint32_t(__bfloat16_as_ushort(pd[3][q])) << 16);
+        const uint32_t lo2 = uint32_t(pd[0][q]) | (uint32_t(pd[1][q]) << 16);
+        const uint32_t hi2 = uint32_t(pd[2][q]) | (uint32_t(pd[3][q]) << 16);
         *reinterpret_cast<uint2*>(dual_row.p[q] + off) = make_uint2(lo2, hi2);
       }
     }
-    __nv_bfloat16 pc[4][3];
+    uint16_t pc[4][3];
     float hi[4];
     if (AFFINE) {
       // scale v + diag I in FP32 pairs (padding rows and columns stay zero)
@@ -187,13 +199,13 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
           const bool on = i == jj + e;
           affine_hi_lo(vh[e], vl[e], sh, sl, on ? dh : 0.f, on ? dl : 0.f, h, l);
         }
-        hi[e] = pieces3_hl(h, l, pc[e]);
+        hi[e] = pieces3_hl(h, l, ps, fmt.half, pc[e]);
         ss = fmaf(hi[e], hi[e], ss);
       }
     } else {
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        hi[e] = pieces3(v[e], pc[e]);
+        hi[e] = pieces3(v[e], ps, fmt.half, pc[e]);
         ss = fmaf(hi[e], hi[e], ss);
       }
     }
@@ -203,8 +215,8 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       if (q >= n_row) break;
-      const uint32_t lo2 = uint32_t(__bfloat16_as_ushort(pc[0][q])) | (uint32_t(__bfloat16_as_ushort(pc[1][q])) << 16);
-      const uint32_t hi2 = uint32_t(__bfloat16_as_ushort(pc[2][q])) | (uint32_t(__bfloat16_as_ushort(pc[3][q])) << 16);
+      const uint32_t lo2 = uint32_t(pc[0][q]) | (uint32_t(pc[1][q]) << 16);
+      const uint32_t hi2 = uint32_t(pc[2][q]) | (uint32_t(pc[3][q]) << 16);
       *reinterpret_cast<uint2*>(row.p[q] + off) = make_uint2(lo2, hi2);
     }
 #pragma unroll
@@ -253,8 +265,7 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
         uint32_t w[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-          w[e] = uint32_t(__bfloat16_as_ushort(tile[q][r0 + 2 * e][c])) |
-                 (uint32_t(__bfloat16_as_ushort(tile[q][r0 + 2 * e + 1][c])) << 16);
+          w[e] = uint32_t(tile[q][r0 + 2 * e][c]) | (uint32_t(tile[q][r0 + 2 * e + 1][c]) << 16);
         *reinterpret_cast<uint4*>(col.p[q] + off) = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
@@ -434,6 +445,32 @@ __global__ void fill_diag_kernel(const double* __restrict__ A, int64_t lda, int 
   X[int64_t(i) * ldx + j] = v;
 }
 
+// One warp per padded row i in [row0, row1): scale[i] = 2^e with max_j |src_ij| 2^e in
+// [2^13, 2^14) (exponent of the maximum from frexp), inv[i] = 2^-e; zero, non-finite and
+// padding rows get 1.
+__global__ void row_piece_scale_kernel(const double* __restrict__ src, int64_t lds, int n, int row0, int row1,
+                                       float* __restrict__ scale, float* __restrict__ inv) {
+  const int i = row0 + int(blockIdx.x) * 8 + int(threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= row1) return;
+  double m = 0.0;
+  if (i < n)
+    for (int j = lane; j < n; j += 32) m = fmax(m, fabs(src[int64_t(i) * lds + j]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) {
+    int e = 0;
+    if (m > 0.0 && isfinite(m)) {
+      int ex = 0;
+      (void)frexp(m, &ex);  // m = f 2^ex, f in [0.5, 1): m 2^(14 - ex) in [2^13, 2^14)
+      e = 14 - ex;
+      e = e > 100 ? 100 : (e < -100 ? -100 : e);
+    }
+    scale[i] = ldexpf(1.0f, e);
+    inv[i] = ldexpf(1.0f, -e);
+  }
+}
+
 }  // namespace
 
 // Rows [row0, row1) of the padded matrix (row1 < 0: to np); both multiples of the block height.
@@ -444,7 +481,7 @@ static bool split_rows(int np, int& row0, int& row1) {
 
 int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
                  __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
-                 double* sumsq_partial, int row0, int row1) {
+                 double* sumsq_partial, int row0, int row1, PieceFmt fmt) {
   if (np % SPLIT_C != 0 || n > np || n_row < 0 || n_row > 3 || n_col < 0 || n_col > 3) return NN_ERR_ARG;
   if (!split_rows(np, row0, row1)) return NN_ERR_ARG;
   PiecePtrs r{}, c{};
@@ -452,32 +489,34 @@ int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np,
   for (int q = 0; q < n_col; ++q) c.p[q] = col_pieces[q];
   dim3 grid(np / SPLIT_C, (row1 - row0) / SPLIT_R), block(32, ROWS);
   split_kernel<double, false><<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial, 1.0,
-                                                      0.0, PiecePtrs{}, nullptr, row0 / SPLIT_R);
+                                                      0.0, fmt, PiecePtrs{}, nullptr, row0 / SPLIT_R);
   NN_CUDA_TRY(cudaGetLastError());
   return NN_OK;
 }
 
 int split_matrix_f32(cudaStream_t st, const float* src, int64_t lds, int n, int np, __nv_bfloat16* const* row_pieces,
-                     int n_row, __nv_bfloat16* const* col_pieces, int n_col) {
+                     int n_row, __nv_bfloat16* const* col_pieces, int n_col, PieceFmt fmt) {
   if (np % SPLIT_C != 0 || n > np || n_row < 0 || n_row > 3 || n_col < 0 || n_col > 3) return NN_ERR_ARG;
   PiecePtrs r{}, c{};
   for (int q = 0; q < n_row; ++q) r.p[q] = row_pieces[q];
   for (int q = 0; q < n_col; ++q) c.p[q] = col_pieces[q];
   dim3 grid(np / SPLIT_C, np / SPLIT_R), block(32, ROWS);
-  split_kernel<float, false><<<grid, block, 0, st>>>(src, lds, n, np, nullptr, r, n_row, c, n_col, nullptr, 1.0, 0.0);
+  split_kernel<float, false><<<grid, block, 0, st>>>(src, lds, n, np, nullptr, r, n_row, c, n_col, nullptr, 1.0, 0.0,
+                                                     fmt);
   NN_CUDA_TRY(cudaGetLastError());
   return NN_OK;
 }
 
 static int split_affine(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
                         __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
-                        double* sumsq_partial, double scale, double diag) {
+                        double* sumsq_partial, double scale, double diag, PieceFmt fmt) {
   if (np % SPLIT_C != 0 || n > np || n_row < 0 || n_row > 3 || n_col < 0 || n_col > 3) return NN_ERR_ARG;
   PiecePtrs r{}, c{};
   for (int q = 0; q < n_row; ++q) r.p[q] = row_pieces[q];
   for (int q = 0; q < n_col; ++q) c.p[q] = col_pieces[q];
   dim3 grid(np / SPLIT_C, np / SPLIT_R), block(32, ROWS);
-  split_kernel<double, true><<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial, scale, diag);
+  split_kernel<double, true><<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial, scale, diag,
+                                                     fmt);
   NN_CUDA_TRY(cudaGetLastError());
   return NN_OK;
 }
@@ -485,7 +524,8 @@ static int split_affine(cudaStream_t st, const double* src, int64_t lds, int n, 
 int split_matrix_dual(cudaStream_t st, const double* src, int64_t lds, int n, int np,
                       __nv_bfloat16* const* src_row_pieces, double* src_sumsq_partial, float* f32,
                       __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
-                      double* sumsq_partial, double scale, double diag, int row0, int row1) {
+                      double* sumsq_partial, double scale, double diag, int row0, int row1, PieceFmt fmt,
+                      PieceFmt src_fmt) {
   if (np % SPLIT_C != 0 || n > np || n_row < 0 || n_row > 3 || n_col < 0 || n_col > 3 || sumsq_partial == nullptr ||
       src_sumsq_partial == nullptr)
     return NN_ERR_ARG;
@@ -498,16 +538,29 @@ int split_matrix_dual(cudaStream_t st, const double* src, int64_t lds, int n, in
     d.p[q] = src_row_pieces[q];
   }
   dim3 grid(np / SPLIT_C, (row1 - row0) / SPLIT_R), block(32, ROWS);
+  if (fmt.half != src_fmt.half) return NN_ERR_ARG;  // one product reads both in one format
   split_kernel<double, true, true><<<grid, block, 0, st>>>(src, lds, n, np, f32, r, n_row, c, n_col, sumsq_partial,
-                                                           scale, diag, d, src_sumsq_partial, row0 / SPLIT_R);
+                                                           scale, diag, fmt, d, src_sumsq_partial, row0 / SPLIT_R,
+                                                           src_fmt);
   NN_CUDA_TRY(cudaGetLastError());
   return NN_OK;
 }
 
 int split_matrix_affine(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
                         __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
-                        double* sumsq_partial, double scale, double diag) {
-  return split_affine(st, src, lds, n, np, f32, row_pieces, n_row, col_pieces, n_col, sumsq_partial, scale, diag);
+                        double* sumsq_partial, double scale, double diag, PieceFmt fmt) {
+  return split_affine(st, src, lds, n, np, f32, row_pieces, n_row, col_pieces, n_col, sumsq_partial, scale, diag,
+                      fmt);
+}
+
+int row_piece_scales(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* scale, float* inv,
+                     int row0, int row1) {
+  if (row1 < 0) row1 = np;
+  if (n > np || row0 < 0 || row0 > row1 || row1 > np || scale == nullptr || inv == nullptr) return NN_ERR_ARG;
+  if (row1 == row0) return NN_OK;
+  row_piece_scale_kernel<<<(row1 - row0 + 7) / 8, 256, 0, st>>>(src, lds, n, row0, row1, scale, inv);
+  NN_CUDA_TRY(cudaGetLastError());
+  return NN_OK;
 }
 
 int split_blocks(int np) { return (np / SPLIT_C) * (np / SPLIT_R); }

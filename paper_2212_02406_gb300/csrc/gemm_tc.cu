@@ -98,6 +98,13 @@ struct Params {
   double* cvt_dst;
   int64_t cvt_ld;
   int cvt_n;
+  // FP16 operand pieces (see TcGemmArgs): idesc_xor clears the descriptor's BF16 type bits,
+  // in_scale (and in_row[row]) multiply the accumulator, out_scale the written pieces.
+  int half;
+  uint32_t idesc_xor;
+  float in_scale;
+  const float* in_row;
+  float out_scale;
   int cvt_vec;
   // Failure-detection test hook: the MMA issuer withholds the first accumulator-ready signal, so
   // the epilogue's bounded wait runs out (nn_debug_withhold_signal).
@@ -129,19 +136,20 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
 }
 
 __device__ __forceinline__ void store_pieces_row(__nv_bfloat16* const* pieces, int n_pieces, int64_t off,
-                                                 const float (&v)[32]) {
+                                                 const float (&v)[32], float scale, bool half) {
   float rem[32];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) rem[j] = v[j];
+  for (int j = 0; j < 32; ++j) rem[j] = v[j] * scale;
   for (int p = 0; p < n_pieces; ++p) {
     uint32_t packed[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      __nv_bfloat16 lo = __float2bfloat16_rn(rem[2 * j]);
-      __nv_bfloat16 hi = __float2bfloat16_rn(rem[2 * j + 1]);
-      rem[2 * j] -= __bfloat162float(lo);
-      rem[2 * j + 1] -= __bfloat162float(hi);
-      packed[j] = uint32_t(__bfloat16_as_ushort(lo)) | (uint32_t(__bfloat16_as_ushort(hi)) << 16);
+      float vlo, vhi;
+      const uint16_t lo = piece_bits(rem[2 * j], half, &vlo);
+      const uint16_t hi = piece_bits(rem[2 * j + 1], half, &vhi);
+      rem[2 * j] -= vlo;
+      rem[2 * j + 1] -= vhi;
+      packed[j] = uint32_t(lo) | (uint32_t(hi) << 16);
     }
     uint4* dst = reinterpret_cast<uint4*>(pieces[p] + off);
 #pragma unroll
@@ -187,25 +195,36 @@ __device__ __forceinline__ void epilogue_chunk(const Params& p, const uint32_t (
   }
   float v[32];
   const int64_t off = int64_t(gr) * ld + gc0;
+  // FP16 pieces carry power-of-two scales: the product of the operands' scales leaves the
+  // accumulator (exact)
+  float acc[32];
+  if (p.half) {
+    const float f = p.in_row != nullptr ? p.in_scale * p.in_row[gr] : p.in_scale;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = __uint_as_float(raw[j]) * f;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = __uint_as_float(raw[j]);
+  }
   if (p.mode == EPI_ADD) {
     const float4* src = reinterpret_cast<const float4*>(p.add + off);
 #pragma unroll
     for (int j4 = 0; j4 < 8; ++j4) {
       float4 a4 = src[j4];
-      v[4 * j4 + 0] = a4.x + __uint_as_float(raw[4 * j4 + 0]);
-      v[4 * j4 + 1] = a4.y + __uint_as_float(raw[4 * j4 + 1]);
-      v[4 * j4 + 2] = a4.z + __uint_as_float(raw[4 * j4 + 2]);
-      v[4 * j4 + 3] = a4.w + __uint_as_float(raw[4 * j4 + 3]);
+      v[4 * j4 + 0] = a4.x + acc[4 * j4 + 0];
+      v[4 * j4 + 1] = a4.y + acc[4 * j4 + 1];
+      v[4 * j4 + 2] = a4.z + acc[4 * j4 + 2];
+      v[4 * j4 + 3] = a4.w + acc[4 * j4 + 3];
     }
   } else if (p.mode == EPI_RESIDUAL) {
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int gc = gc0 + j;
-      v[j] = ((gr == gc && gr < p.n_id) ? 1.0f : 0.0f) - __uint_as_float(raw[j]);
+      v[j] = ((gr == gc && gr < p.n_id) ? 1.0f : 0.0f) - acc[j];
     }
   } else {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(raw[j]);
+    for (int j = 0; j < 32; ++j) v[j] = acc[j];
   }
   if (p.affine) {
 #pragma unroll
@@ -235,18 +254,19 @@ __device__ __forceinline__ void epilogue_chunk(const Params& p, const uint32_t (
 #pragma unroll
     for (int j4 = 0; j4 < 8; ++j4) dst[j4] = make_float4(v[4 * j4], v[4 * j4 + 1], v[4 * j4 + 2], v[4 * j4 + 3]);
   }
-  if (p.n_row > 0) store_pieces_row(p.row_pieces, p.n_row, off, v);
+  if (p.n_row > 0) store_pieces_row(p.row_pieces, p.n_row, off, v, p.out_scale, p.half != 0);
   if (p.n_col > 0) {
     float rem[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) rem[j] = v[j];
+    for (int j = 0; j < 32; ++j) rem[j] = v[j] * p.out_scale;
     for (int pc = 0; pc < p.n_col; ++pc) {
-      __nv_bfloat16* dst = p.col_pieces[pc] + gr;
+      uint16_t* dst = reinterpret_cast<uint16_t*>(p.col_pieces[pc]) + gr;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        __nv_bfloat16 b = __float2bfloat16_rn(rem[j]);
-        rem[j] -= __bfloat162float(b);
-        dst[int64_t(gc0 + j) * ld] = b;  // lanes write consecutive rows: 64-byte runs
+        float b;
+        const uint16_t bits = piece_bits(rem[j], p.half != 0, &b);
+        rem[j] -= b;
+        dst[int64_t(gc0 + j) * ld] = bits;  // lanes write consecutive rows: 64-byte runs
       }
     }
   }
@@ -365,7 +385,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const __grid_consta
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             // +32 bytes along K inside the 128-byte swizzled row = +2 in the address field
-            tc_mma_bf16(d_tmem, adesc + uint64_t(2 * kk), bdesc + uint64_t(2 * kk), IDESC,
+            tc_mma_bf16(d_tmem, adesc + uint64_t(2 * kk), bdesc + uint64_t(2 * kk), IDESC ^ p.idesc_xor,
                         (it > 0 || kk > 0) ? 1u : 0u);
           }
           tc_commit(&empty[stage]);
@@ -549,7 +569,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_2sm_kernel(const __grid_co
         if (!mbar_wait(&acc_empty[acc], acc_phase ^ 1u, abort_flag, p.err)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + uint32_t(acc * BN);
-        const uint32_t idesc = w < p.split_from ? IDESC_P2 : IDESC_P2_HALF;
+        const uint32_t idesc = (w < p.split_from ? IDESC_P2 : IDESC_P2_HALF) ^ p.idesc_xor;
         bool ok = true;
         for (int it = 0; it < total_k; ++it) {
           if (!mbar_wait(&full[stage], phase, abort_flag, p.err)) {
@@ -729,7 +749,7 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
   if (!a.emu && a.mode == EPI_ADD && a.add == nullptr) return NN_ERR_ARG;
   if (a.cvt_dst != nullptr && (a.emu || a.cvt_src == nullptr || a.cvt_n < 1 || a.cvt_n > a.np || a.cvt_ld < a.cvt_n))
     return NN_ERR_ARG;
-  if (a.emu && a.affine) return NN_ERR_ARG;
+  if (a.emu && (a.affine || a.half)) return NN_ERR_ARG;
   if (a.emu && (a.emu_acc == nullptr || a.emu_gexp == nullptr || (a.emu_last && a.emu_out == nullptr) ||
                 (a.emu_last && a.mode == EPI_ADD && a.emu_add == nullptr) || a.n_row != 0 || a.n_col != 0 ||
                 a.out_f32 != nullptr || a.emu_n < 1 || a.emu_n > a.np))
@@ -781,6 +801,12 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
   p.cvt_ld = a.cvt_ld;
   p.cvt_n = a.cvt_n;
   p.cvt_vec = (a.cvt_ld % 2 == 0 && (reinterpret_cast<uintptr_t>(a.cvt_dst) & 15) == 0) ? 1 : 0;
+  p.half = a.half ? 1 : 0;
+  // A and B types (bits 7-9, 10-12): BF16 = 1, FP16 = 0; both operands always share one type
+  p.idesc_xor = a.half ? ((1u << 7) | (1u << 10)) : 0u;
+  p.in_scale = a.in_scale;
+  p.in_row = a.in_row;
+  p.out_scale = a.out_scale;
   p.withhold = tc_take_withhold();
   // Variant choice: the 2-SM MMA with a split last wave by default where the size allows it, else
   // single-CTA tiles.

@@ -72,6 +72,15 @@ struct TcGemmArgs {
   double* cvt_dst = nullptr;
   int64_t cvt_ld = 0;
   int cvt_n = 0;
+  // FP16 operand pieces (half): both operands of every segment are FP16 and the written pieces
+  // too. The accumulator is multiplied by in_scale and, when in_row is given, by in_row[row]
+  // (device, one factor per output row) before `mode`; the written pieces hold the result times
+  // out_scale (FP32 output, sums of squares and side copy unscaled). All factors are powers of
+  // two (exact). BF16 chains leave the defaults.
+  bool half = false;
+  float in_scale = 1.0f;
+  const float* in_row = nullptr;
+  float out_scale = 1.0f;
   // Optional events recorded on the stream immediately before and after the kernel launch (after
   // the host has prepared it), so that their interval is the kernel's device time.
   cudaEvent_t ev_before = nullptr, ev_after = nullptr;
@@ -102,6 +111,14 @@ int gemm_f64_emu(cudaStream_t st, int n, const double* A, int64_t lda, const dou
 bool tc_supported();
 
 // ---- conversion / preconditioner / reduction kernels (convert.cu) -----------------------
+// Format of written operand pieces: BF16 (half = false) or FP16; each value is multiplied by
+// scale and, when row_scale is given, by row_scale[row] (device) before it is cut into pieces
+// (powers of two: exact). The FP32 copy and the sums of squares stay unscaled.
+struct PieceFmt {
+  bool half = false;
+  float scale = 1.0f;
+  const float* row_scale = nullptr;
+};
 // Splits an n x n FP64 matrix (leading dim lds) into an Np-padded FP32 copy and BF16
 // pieces (row-major and/or transposed). Any output may be null. Padding is zero.
 // sumsq_partial (nullable) receives one sum of squares per 32 x 32 block (split_blocks(np) entries).
@@ -109,21 +126,28 @@ bool tc_supported();
 // of A whose host copy has arrived; the partial sums keep their global positions.
 int split_matrix(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
                  __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
-                 double* sumsq_partial, int row0 = 0, int row1 = -1);
+                 double* sumsq_partial, int row0 = 0, int row1 = -1, PieceFmt fmt = PieceFmt{});
 // The same for scale * src + diag * I (FP64 arithmetic): element-wise products with a scalar
 // X_0 (R_0 = I - a A; at depth 1, X_1 = 2 a I - a^2 A).
 int split_matrix_affine(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* f32,
                         __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
-                        double* sumsq_partial, double scale, double diag);
+                        double* sumsq_partial, double scale, double diag, PieceFmt fmt = PieceFmt{});
 // One pass over src for both: the three row-major pieces of src with its per-block sums of squares
 // (as split_matrix), and the outputs of split_matrix_affine for scale * src + diag * I.
+// fmt: the affine output's pieces; src_fmt: src's (the same half flag).
 int split_matrix_dual(cudaStream_t st, const double* src, int64_t lds, int n, int np,
                       __nv_bfloat16* const* src_row_pieces, double* src_sumsq_partial, float* f32,
                       __nv_bfloat16* const* row_pieces, int n_row, __nv_bfloat16* const* col_pieces, int n_col,
-                      double* sumsq_partial, double scale, double diag, int row0 = 0, int row1 = -1);
+                      double* sumsq_partial, double scale, double diag, int row0 = 0, int row1 = -1,
+                      PieceFmt fmt = PieceFmt{}, PieceFmt src_fmt = PieceFmt{});
 // BF16 pieces of an FP32 matrix (the same pieces the GEMM epilogue writes for it).
 int split_matrix_f32(cudaStream_t st, const float* src, int64_t lds, int n, int np, __nv_bfloat16* const* row_pieces,
-                     int n_row, __nv_bfloat16* const* col_pieces, int n_col);
+                     int n_row, __nv_bfloat16* const* col_pieces, int n_col, PieceFmt fmt = PieceFmt{});
+// FP16 row scales of an n x n FP64 matrix, padded rows [row0, row1) of np (row1 < 0: to np):
+// scale[i] = 2^e_i with the row's largest |entry| times 2^e_i in [2^13, 2^14), inv[i] = 2^-e_i
+// (1 for zero and padding rows).
+int row_piece_scales(cudaStream_t st, const double* src, int64_t lds, int n, int np, float* scale, float* inv,
+                     int row0 = 0, int row1 = -1);
 int split_blocks(int np);
 // dst (FP64, ldd) = src (FP32, lds), n x n.
 int f32_to_f64(cudaStream_t st, const float* src, int64_t lds, int n, double* dst, int64_t ldd);

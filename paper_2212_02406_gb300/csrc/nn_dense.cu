@@ -33,6 +33,10 @@ struct Simt32Ws {
 };
 struct MixedWs {
   int np;
+  // FP16 operand pieces (NN_MIXED_F16): A's pieces carry per-row scales a_scale (inverse a_rinv)
+  bool half;
+  float* a_scale;
+  float* a_rinv;
   double* split_partial;  // one per 32 x 32 block of the split kernel
   double* split_partial2;  // the second set of a two-output split
   __nv_bfloat16* a_row[3];
@@ -87,9 +91,12 @@ void carve_f32(Carver& c, int64_t n, Simt32Ws& w) {
   w.T[1] = c.take<float>(e);
 }
 
-void carve_mixed(Carver& c, int64_t n, MixedWs& w) {
+void carve_mixed(Carver& c, int64_t n, MixedWs& w, int dtype) {
   w.np = int((n + 127) / 128 * 128);
+  w.half = dtype == NN_MIXED_F16;
   const size_t e = size_t(w.np) * size_t(w.np);
+  w.a_scale = c.take<float>(size_t(w.np));
+  w.a_rinv = c.take<float>(size_t(w.np));
   w.split_partial = c.take<double>(size_t(split_blocks(w.np)));
   w.split_partial2 = c.take<double>(size_t(split_blocks(w.np)));
   for (int i = 0; i < 3; ++i) w.a_row[i] = c.take<__nv_bfloat16>(e);
@@ -120,7 +127,7 @@ size_t ws_bytes(int64_t n, int dtype) {
     // nn_residual in FP32 converts X into this space as well
   } else {
     MixedWs w;
-    carve_mixed(c, n, w);
+    carve_mixed(c, n, w, dtype);
     if (dtype == NN_MIXED_EMU) {
       Simt64Ws w64;
       carve_f64(c, n, w64);
@@ -131,7 +138,8 @@ size_t ws_bytes(int64_t n, int dtype) {
 }
 
 bool valid_dtype(int d) {
-  return d == NN_F64 || d == NN_F32 || d == NN_MIXED_BF16 || d == NN_F64_EMU || d == NN_MIXED_EMU;
+  return d == NN_F64 || d == NN_F32 || d == NN_MIXED_BF16 || d == NN_F64_EMU || d == NN_MIXED_EMU ||
+         d == NN_MIXED_F16;
 }
 
 // Reads count (<= 8) doubles from cm.scal and the device error word with one copy (they share
@@ -478,36 +486,63 @@ static int level_x_pieces(int L) { return L <= 1 ? 1 : (L <= 3 ? 2 : 3); }
 static int level_t_pieces(int L) { return L <= 1 ? 1 : (L <= 3 ? NN_POLICY_T_MID : 3); }
 // pieces of both operands of the Horner products R T_j (second order in the residual)
 static int level_h_pieces(int L) { return (L == 2 || L == 3) ? 1 : level_x_pieces(L); }
-static int stable_level(double kest) {
+// FP16 pieces (half) keep 11 significant bits where BF16 keeps 8: every power of 2^-8 below
+// becomes one of 2^-11.
+static int stable_level(double kest, bool half) {
+  const int b = half ? 11 : 8;
   for (int L = 1; L <= 3; ++L) {
     const int p = level_x_pieces(L);
-    if (ldexp(kest, -(8 * p + 1)) * kStable <= 1.0) return L;
+    if (ldexp(kest, -(b * p + 1)) * kStable <= 1.0) return L;
   }
   return 4;
 }
-// rms error floor of a residual measured at level L (0: exact, the element-wise R_0)
-static double level_floor(int L, double c, double n) {
+// rms error floor of a residual measured at level L (0: exact, the element-wise R_0). FP16
+// pieces: the BF16 piece constants times 2^-3 per piece (the ratio of the two formats' unit
+// roundoffs), three pieces beyond FP32 (2^-33). The tensor core's accumulation of FP16 products
+// (22 significant bits against BF16's 16) loses more to its alignment: 8.0e-10 c N against
+// 5.4e-10 c N. Measured on GB300 with X an FP64 inverse (N = 1024..8192, kappa = 1e2 and 1e4):
+// one FP16 piece 2.77-2.84e-4 c (2^-11.8 c); two or three pieces 7.1-7.8e-10 c N at kappa = 1e2,
+// 5.9e-10 c N at 1e4, where the accumulation term dominates.
+static double level_floor(int L, double c, double n, bool half) {
   if (L <= 0) return 0.0;
-  const double pieces = c * (L == 1 ? 0x1.27p-9 : (L == 2 ? 0x1.15p-18 : 0x1p-25));
-  const double acc = 5.4e-10 * c * n;
+  const double pieces = half ? c * (L == 1 ? 0x1.27p-12 : (L == 2 ? 0x1.15p-24 : 0x1p-33))
+                             : c * (L == 1 ? 0x1.27p-9 : (L == 2 ? 0x1.15p-18 : 0x1p-25));
+  const double acc = (half ? 8.0e-10 : 5.4e-10) * c * n;
   return sqrt(pieces * pieces + acc * acc);
 }
 // lowest level whose floor lies under 0.8 tol (3 if none does, 1 for tol <= 0)
-static int top_level(double tol, double c, double n) {
+static int top_level(double tol, double c, double n, bool half) {
   if (!(tol > 0)) return 3;
   for (int L = 1; L <= 3; ++L)
-    if (level_floor(L, c, n) < 0.8 * tol) return L;
+    if (level_floor(L, c, n, half) < 0.8 * tol) return L;
   return 3;
+}
+// FP16 piece scales: R_k and T_j are scaled by kPieceRT (entries below 16 stay under FP16's
+// 65504), X_k by the power of two that puts `bound` (an upper bound of its entries) at or under
+// 2^14; 1 for BF16 pieces.
+constexpr float kPieceRT = 4096.0f;
+static float x_piece_scale(double bound, bool half) {
+  if (!half || !(bound > 0) || !isfinite(bound)) return 1.0f;
+  int ex = 0;
+  (void)frexp(16384.0 / bound, &ex);  // 2^14 / bound in [2^(ex-1), 2^ex): exact, scale-covariant
+  int e = ex - 1;
+  e = e > 60 ? 60 : (e < -60 ? -60 : e);
+  return ldexpf(1.0f, e);
 }
 
 // Re-splits X_0 into buffer set 0 (pieces, FP32 master) and its norm into cm.scal[1].
 struct X0Source {
   const double* x0;
   int64_t ldx0;
+  float scale = 1.0f;  // FP16 piece scale of X_0
 };
 int load_x0(cudaStream_t st, int n, const MixedWs& w, const Common& cm, const X0Source& src) {
   const int sb = split_blocks(w.np);
-  NN_TRY(split_matrix(st, src.x0, src.ldx0, n, w.np, w.x32[0], w.x_row[0], 3, w.x_col[0], 3, w.split_partial));
+  PieceFmt fx;
+  fx.half = w.half;
+  fx.scale = src.scale;
+  NN_TRY(split_matrix(st, src.x0, src.ldx0, n, w.np, w.x32[0], w.x_row[0], 3, w.x_col[0], 3, w.split_partial, 0, -1,
+                      fx));
   NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0, cm.scal + 1));
   return NN_OK;
 }
@@ -558,6 +593,28 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
   const double n15 = double(n) * sqrt(double(n));
   int level = initial_level(o);
   const int r0_pre_hp = level_t_pieces(level);
+  // FP16 pieces: the piece scale of each X buffer (set when its pieces are written), R and T at
+  // kPieceRT, A per row (w.a_scale)
+  const bool half = w.half;
+  const float rt_scale = half ? kPieceRT : 1.0f;
+  float xs[2] = {half ? x0src.scale : 1.0f, 1.0f};
+  PieceFmt rt_fmt;
+  rt_fmt.half = half;
+  rt_fmt.scale = rt_scale;
+  auto x_fmt = [&](int b) {
+    PieceFmt f;
+    f.half = half;
+    f.scale = xs[b];
+    return f;
+  };
+  auto set_half = [&](TcGemmArgs& g, float in_scale, const float* in_row, float out_scale) {
+    g.half = half;
+    if (half) {
+      g.in_scale = in_scale;
+      g.in_row = in_row;
+      g.out_scale = out_scale;
+    }
+  };
   int cur = 0;
   int k = 0;
   bool copy_next = false;  // the next residual's iterate is predicted to be returned
@@ -570,7 +627,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
   int xlev[2] = {0, 0};
   auto ensure_pieces = [&](int b, int need_r, int need_c) -> int {
     if (xr[b] >= need_r && xc[b] >= need_c) return NN_OK;
-    NN_TRY(split_matrix_f32(st, w.x32[b], np, n, np, w.x_row[b], 3, w.x_col[b], 3));
+    NN_TRY(split_matrix_f32(st, w.x32[b], np, n, np, w.x_row[b], 3, w.x_col[b], 3, x_fmt(b)));
     xr[b] = xc[b] = 3;
     res->launches += 1;
     return NN_OK;
@@ -605,6 +662,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       dout->nests = k;
     }
     NN_TRY(ensure_pieces(cur, 0, level_res_pieces(L)));
+    set_half(g, 1.0f / xs[cur], w.a_rinv, rt_scale);
     int grid = 0;
     NN_TRY(tc_product(st, g, level_res_pieces(L), level_res_pieces(L), w.a_row, w.x_col[cur], cm, res, &grid,
                       &timer));
@@ -626,7 +684,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       res->launches += 1;
     } else {
       NN_TRY(split_matrix_affine(st, A, lda, n, np, rows ? w.r32 : nullptr, w.r_row, rows ? hp : 0, w.r_col, hp,
-                                 w.split_partial, -alpha, 1.0));
+                                 w.split_partial, -alpha, 1.0, rt_fmt));
       NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0 / double(n), cm.scal));
       res->launches += 2;
     }
@@ -667,6 +725,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       if (!scalar_x0) {
         NN_TRY(load_x0(st, n, w, cm, x0src));
         xr[0] = xc[0] = 3;
+        xs[0] = half ? x0src.scale : 1.0f;
         res->launches += 2;
       }
       NN_TRY(measure(level, &s));
@@ -674,16 +733,16 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     const double c = a_frob * x_frob / n15;
     const double dn = double(n);
     // false: tol lies under what BF16 pieces can certify (the level-3 floor is above 0.8 tol)
-    const bool certifiable = !(o.tol > 0) || level_floor(3, c, dn) < 0.8 * o.tol;
+    const bool certifiable = !(o.tol > 0) || level_floor(3, c, dn, half) < 0.8 * o.tol;
     // NN_MIXED_EMU hands an uncertifiable tol to emulated nests: level 3 would gain nothing
-    const int l_top = (o.dtype == NN_MIXED_EMU && !certifiable) ? 2 : top_level(o.tol, c, dn);
+    const int l_top = (o.dtype == NN_MIXED_EMU && !certifiable) ? 2 : top_level(o.tol, c, dn, half);
     {
       int target = level;
       if (isfinite(s)) {
-        const int ls = stable_level(a_frob * x_frob / dn);
+        const int ls = stable_level(a_frob * x_frob / dn, half);
         if (target < ls) target = ls;
-        while (target < l_top && s < kRise * level_floor(target, c, dn)) ++target;
-        if (k >= 1 && s > 0.9 * res->history[k - 1] && s < 30.0 * level_floor(level, c, dn) && level < 4)
+        while (target < l_top && s < kRise * level_floor(target, c, dn, half)) ++target;
+        if (k >= 1 && s > 0.9 * res->history[k - 1] && s < 30.0 * level_floor(level, c, dn, half) && level < 4)
           target = target > (level <= 2 ? 3 : 4) ? target : (level <= 2 ? 3 : 4);
         if (o.refine_below > 0 && s * sqrt_n < o.refine_below && target < 3) target = 3;
         if (o.tol > 0 && s < o.tol && target < l_top) target = l_top;
@@ -716,7 +775,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     res->nests = k;
     res->residual = s;
     // the residual X_k has, with the floor of the residual that produced it (certified estimate)
-    const double e_fix = level_floor(xlev[cur], c, dn);
+    const double e_fix = level_floor(xlev[cur], c, dn, half);
     const double s_cert = sqrt(s * s + e_fix * e_fix);
     res->residual_est = s_cert;
     int verdict = judge(o, k, res->history);
@@ -727,16 +786,17 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     // At the top level, two nests in a row within 30 floors without a 10% gain: the residual
     // has reached the arithmetic floor, so more nests cannot reach tol.
     if (verdict < 0 && level == 4 && k >= 2 && o.tol > 0 && s > 0.9 * res->history[k - 1] &&
-        res->history[k - 1] > 0.9 * res->history[k - 2] && s < 30.0 * level_floor(4, c, dn))
+        res->history[k - 1] > 0.9 * res->history[k - 2] && s < 30.0 * level_floor(4, c, dn, half))
       verdict = NN_ERR_NOT_CONVERGED;
     // NN_MIXED_EMU: a tolerance below the BF16-piece floors is reached by emulated FP64 nests;
     // hand the iterate over once the pieces can no longer bring s down (within 4 level-2 floors:
     // level 3 only gains the tensor core's FP32 accumulation floor at twice the passes).
-    if (verdict < 0 && o.dtype == NN_MIXED_EMU && !certifiable && s < 4.0 * level_floor(2, c, dn))
+    if (verdict < 0 && o.dtype == NN_MIXED_EMU && !certifiable && s < 4.0 * level_floor(2, c, dn, half))
       verdict = NN_ERR_NOT_CONVERGED;
     // NN_MIXED_BF16 with a tol it cannot certify: once s is under the level-3 floor, more nests
     // lower the measured residual but not the true one (about the floor), so the run ends there.
-    if (verdict < 0 && o.dtype == NN_MIXED_BF16 && !certifiable && level >= 3 && s < level_floor(3, c, dn))
+    if (verdict < 0 && (o.dtype == NN_MIXED_BF16 || o.dtype == NN_MIXED_F16) && !certifiable && level >= 3 &&
+        s < level_floor(3, c, dn, half))
       verdict = NN_ERR_NOT_CONVERGED;
     if (verdict >= 0) {
       res->status = verdict;
@@ -758,11 +818,11 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
         const double lp = double(nest_depth(o, k - 1)), lk = double(nest_depth(o, k));
         s_pred = s * pow(ratio, (lp + 1.0) * lk / lp);
         if (level < 3) {
-          while (next_level < l_top && s_pred < kRise * level_floor(next_level, c, dn)) ++next_level;
+          while (next_level < l_top && s_pred < kRise * level_floor(next_level, c, dn, half)) ++next_level;
           if (o.tol > 0 && s_pred < o.tol && next_level < l_top) next_level = l_top;
         }
         likely_final = o.tol > 0 && s_pred < 0.5 * o.tol && next_level >= l_top &&
-                       hypot(s_pred, level_floor(level, c, dn)) < 0.9 * o.tol;
+                       hypot(s_pred, level_floor(level, c, dn, half)) < 0.9 * o.tol;
       }
     }
     // NN_MIXED_EMU with tol below the BF16 pieces' floor: once X_{k+1} is predicted to lie within
@@ -788,7 +848,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       }
     }
     const bool handover = o.dtype == NN_MIXED_EMU && !certifiable && s_slow >= 0 &&
-                          s_slow < 4.0 * level_floor(2, c, dn) && k + 1 < o.max_nests;
+                          s_slow < 4.0 * level_floor(2, c, dn, half) && k + 1 < o.max_nests;
     if (handover) likely_final = false;
     // Horner: T_1 = R (its column pieces), T_{j+1} = R + R T_j. With a scalar X_0 the first
     // nest's last Horner product also leaves T in FP32 over R's FP32 copy (each element read as
@@ -810,6 +870,9 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       if (dout != nullptr && dout->buf == (cur ^ 1)) dout->nests = -1;
       return NN_OK;
     };
+    // FP16 piece scale of X_{k+1} from ||X_{k+1}||_F <= (1 + ||T||_2) ||X_k||_F, ||T||_2 <= L when
+    // ||R_k||_2 < 1 (T = R + ... + R^L)
+    const float xs_next = x_piece_scale((1.0 + double(nest_depth(o, k))) * x_frob, half);
     __nv_bfloat16* const* t_cur = w.r_col;
     for (int j = 1; j < nest_depth(o, k); ++j) {
       TcGemmArgs g;
@@ -819,10 +882,13 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       g.add = w.r32;
       g.n_col = ht;
       for (int i = 0; i < 3; ++i) g.col_pieces[i] = w.t_col[j & 1][i];
+      set_half(g, 1.0f / (rt_scale * rt_scale), nullptr, rt_scale);
       int grid = 0;
       if (update0 && j == nest_depth(o, k) - 1) {
         // the first nest's last Horner product writes X_1 = alpha (I + T) straight from its
         // epilogue (FP32 master, row and column pieces, ||X_1||_F): no T, no separate pass
+        xs[cur ^ 1] = xs_next;
+        g.out_scale = half ? xs_next : 1.0f;
         g.affine = true;
         g.aff_scale = float(alpha);
         g.aff_diag = float(alpha);
@@ -853,8 +919,9 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
         NN_TRY(before_x_write());
         xlev[cur ^ 1] = level;
         xr[cur ^ 1] = xc[cur ^ 1] = 3;
+        xs[cur ^ 1] = xs_next;
         NN_TRY(split_matrix_affine(st, A, lda, n, np, w.x32[cur ^ 1], w.x_row[cur ^ 1], 3, w.x_col[cur ^ 1], 3,
-                                   w.split_partial, -alpha * alpha, 2.0 * alpha));
+                                   w.split_partial, -alpha * alpha, 2.0 * alpha, x_fmt(cur ^ 1)));
         NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0, cm.scal + 1));
         res->launches += 2;
       }
@@ -877,6 +944,8 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
         g.col_pieces[i] = w.x_col[cur ^ 1][i];
       }
       g.partial = cm.partial;
+      xs[cur ^ 1] = xs_next;
+      set_half(g, 1.0f / (xs[cur] * rt_scale), nullptr, xs_next);
       int grid = 0;
       NN_TRY(tc_product(st, g, hp, ht, w.x_row[cur], t_cur, cm, res, &grid, &timer));
       NN_TRY(reduce_rms(st, cm.partial, grid, 1.0, cm.scal + 1));
@@ -919,13 +988,21 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
 // to Np); with X_0 = alpha I the same pass also writes R_0 = I - alpha A at the starting level.
 int split_a_panels(cudaStream_t st, const double* A, int64_t lda, int n, const MixedWs& w, const nn_opts& o, int row0,
                    int row1) {
+  // FP16 pieces: each row of A at its own power-of-two scale, R_0 at kPieceRT
+  PieceFmt fa, fr;
+  fa.half = fr.half = w.half;
+  if (w.half) {
+    NN_TRY(row_piece_scales(st, A, lda, n, w.np, w.a_scale, w.a_rinv, row0, row1));
+    fa.row_scale = w.a_scale;
+    fr.scale = kPieceRT;
+  }
   if (o.x0_scalar > 0) {
     const int hp = level_t_pieces(initial_level(o));
     const bool rows = max_depth(o) >= 2;
     return split_matrix_dual(st, A, lda, n, w.np, w.a_row, w.split_partial, rows ? w.r32 : nullptr, w.r_row,
-                             rows ? hp : 0, w.r_col, hp, w.split_partial2, -o.x0_scalar, 1.0, row0, row1);
+                             rows ? hp : 0, w.r_col, hp, w.split_partial2, -o.x0_scalar, 1.0, row0, row1, fr, fa);
   }
-  return split_matrix(st, A, lda, n, w.np, nullptr, w.a_row, 3, nullptr, 0, w.split_partial, row0, row1);
+  return split_matrix(st, A, lda, n, w.np, nullptr, w.a_row, 3, nullptr, 0, w.split_partial, row0, row1, fa);
 }
 
 int check_opts(const nn_opts* o, int64_t n) {
@@ -989,7 +1066,7 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
   } else {
     if (!tc_supported()) return NN_ERR_UNSUPPORTED;
     MixedWs w;
-    carve_mixed(c, n, w);
+    carve_mixed(c, n, w, o.dtype);
     Simt64Ws w64{};
     void* ews = nullptr;
     size_t eb = 0;
@@ -1006,8 +1083,19 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     const bool r0_pre = o.x0_scalar > 0;
     if (!a_presplit) NN_TRY(split_a_panels(st, A, lda, ni, w, o, 0, -1));
     NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0, cm.scal + 2));
-    const X0Source x0src{X0, ldx0};
-    if (o.x0_scalar <= 0) NN_TRY(load_x0(st, ni, w, cm, x0src));  // a scalar X_0 needs no pieces
+    X0Source x0src{X0, ldx0};
+    if (o.x0_scalar <= 0) {  // a scalar X_0 needs no pieces
+      if (w.half) {
+        // FP16 pieces of X_0 at the scale that puts ||X_0||_F (>= its entries) under 2^14
+        NN_TRY(frob_f64(st, X0, ldx0, ni, cm.partial, cm.n_partial, cm.scal + 3));
+        double x0_frob = 0;
+        NN_CUDA_TRY(cudaMemcpyAsync(&x0_frob, cm.scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+        NN_CUDA_TRY(cudaStreamSynchronize(st));
+        x0src.scale = x_piece_scale(x0_frob, true);
+        res->launches += 2;
+      }
+      NN_TRY(load_x0(st, ni, w, cm, x0src));
+    }
     double a_frob = 0;
     NN_CUDA_TRY(cudaMemcpyAsync(&a_frob, cm.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
     NN_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1070,7 +1158,8 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
   // and update). Precision passes, re-measured residuals and rolled-back nests are not counted.
   double gemms = 1.0;
   for (int k = 0; k < res->nests; ++k) gemms += double(nest_depth(o, k) + 1);
-  if ((o.dtype == NN_MIXED_BF16 || o.dtype == NN_MIXED_EMU) && o.x0_scalar > 0) gemms -= res->nests >= 1 ? 2.0 : 1.0;
+  if ((o.dtype == NN_MIXED_BF16 || o.dtype == NN_MIXED_EMU || o.dtype == NN_MIXED_F16) && o.x0_scalar > 0)
+    gemms -= res->nests >= 1 ? 2.0 : 1.0;
   res->flops = 2.0 * double(n) * double(n) * double(n) * gemms;
   NN_CUDA_TRY(cudaStreamSynchronize(st));
   int dev_err = 0;
@@ -1171,7 +1260,7 @@ int invert_host_impl(const double* A_host, int64_t n, const double* X0_host, int
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // a scalar preconditioner on the mixed chain: X_0 = pc_scalar I is never materialised
   nn_opts oh = *opts;
-  const bool mixed = opts->dtype == NN_MIXED_BF16 || opts->dtype == NN_MIXED_EMU;
+  const bool mixed = opts->dtype == NN_MIXED_BF16 || opts->dtype == NN_MIXED_EMU || opts->dtype == NN_MIXED_F16;
   if (X0_host == nullptr && pc_kind == NN_PC_SCALAR && mixed && pc_scalar > 0) oh.x0_scalar = pc_scalar;
   // Mixed chain, large N: A travels in row panels on a copy stream, and each panel is split into
   // its BF16 pieces (and R_0) as soon as it has arrived, so the split overlaps the copy.
@@ -1181,7 +1270,7 @@ int invert_host_impl(const double* A_host, int64_t n, const double* X0_host, int
     Common cmw;
     carve_common(cw, n, oh.dtype, cmw);
     MixedWs ww;
-    carve_mixed(cw, n, ww);  // the same carving as invert_device's
+    carve_mixed(cw, n, ww, oh.dtype);  // the same carving as invert_device's
     if (!cw.ok) return NN_ERR_OOM_BUDGET;
     constexpr int kPanels = 8;
     cudaStream_t cs = nullptr;
@@ -1234,7 +1323,8 @@ int invert_host_impl(const double* A_host, int64_t n, const double* X0_host, int
   ho.host = X_host;
   ho.dev = dX;
   ho.n = int(n);
-  const bool spec = opts->dtype == NN_MIXED_BF16 && (opts->tol > 0 || opts->fwd_tol > 0);
+  const bool spec =
+      (opts->dtype == NN_MIXED_BF16 || opts->dtype == NN_MIXED_F16) && (opts->tol > 0 || opts->fwd_tol > 0);
   if (spec) {
     NN_CUDA_TRY(cudaStreamCreateWithFlags(&ho.side, cudaStreamNonBlocking));
     if (cudaEventCreateWithFlags(&ho.ready, cudaEventDisableTiming) != cudaSuccess ||

@@ -160,7 +160,7 @@ int run_job(nn_server* s, const Job& j, cudaStream_t st, nn_completion* c) {
   // A scalar X_0 on the mixed chain (the scalar preconditioner, or Theta_1 = I / Tr(A) from the
   // host copy of A) is passed as the x0_scalar hint and never materialised.
   double alpha = 0.0;
-  const bool mixed = r.dtype == NN_MIXED_BF16 || r.dtype == NN_MIXED_EMU;
+  const bool mixed = r.dtype == NN_MIXED_BF16 || r.dtype == NN_MIXED_EMU || r.dtype == NN_MIXED_F16;
   if (mixed && r.precond == NN_PC_SCALAR) alpha = r.pc_scalar;
   if (mixed && r.precond == NN_PC_TRACE) {
     double tr = 0.0;
@@ -291,7 +291,8 @@ int nn_server_create(const nn_server_opts* opts, nn_server** out) {
 int nn_server_submit(nn_server* s, const nn_request* r) {
   if (s == nullptr || r == nullptr || r->A == nullptr || r->n < 1 || r->nrhs < 0) return NN_ERR_ARG;
   if (r->nrhs > 0 && r->B == nullptr) return NN_ERR_ARG;
-  if (r->dtype != NN_F64 && r->dtype != NN_F32 && r->dtype != NN_MIXED_BF16 && r->dtype != NN_MIXED_EMU)
+  if (r->dtype != NN_F64 && r->dtype != NN_F32 && r->dtype != NN_MIXED_BF16 && r->dtype != NN_MIXED_EMU &&
+      r->dtype != NN_MIXED_F16)
     return NN_ERR_ARG;
   if (r->precond < NN_PC_PAN_SCHREIBER || r->precond > NN_PC_THETA2) return NN_ERR_ARG;
   const size_t bytes = request_bytes(r->n, r->nrhs, r->dtype);

@@ -1,9 +1,10 @@
 """Full-size parity of the dense mixed path at the benchmarked configuration, through the
 benchmark's own call.
 
-N = 8192, A = Q diag(lambda) Q^T (Q from QR of an N(0,1) matrix, lambda log-uniform on
-[1, 1e2]), X_0 = 2/(lambda_min + lambda_max) I passed as the x0_scalar hint (the first nest
-element-wise), depth 2, tol 1e-6: the call bench.py times. The oracle cannot run N = 8192 nests
+Both mixed forms (BF16 and FP16 operand pieces) at N = 8192, A = Q diag(lambda) Q^T (Q from
+QR of an N(0,1) matrix, lambda log-uniform on [1, 1e2]), X_0 = 2/(lambda_min + lambda_max) I
+passed as the x0_scalar hint (the first nest element-wise), depth 2, tol 1e-6: the call bench.py
+times. The oracle cannot run N = 8192 nests
 in a test, so the checks use what holds at any size and is computable one output at a time:
 * the nest count equals the first k where the spectral closed form
   sqrt(sum_j (1 - alpha lambda_j)^(2 3^k)) / N drops below tol (Appendix 2: R_k = R_0^(3^k));
@@ -27,7 +28,8 @@ from oracle import dense
 pytestmark = pytest.mark.gpu
 
 
-def test_mixed_bf16_n8192_kappa1e2_depth2_bench_call():
+@pytest.mark.parametrize("dtype", ["mixed_bf16", "mixed_f16"])
+def test_mixed_n8192_kappa1e2_depth2_bench_call(dtype):
     import torch
 
     from paper_2212_02406_gb300 import abi, build
@@ -37,10 +39,10 @@ def test_mixed_bf16_n8192_kappa1e2_depth2_bench_call():
     A, Q, lam = synth.spd_spectrum_torch(n, kappa, seed=0, device="cuda")
     alpha = 2.0 / (lam[0] + lam[-1])
     X0 = torch.empty_like(A)
-    ws = abi.workspace(n, "mixed_bf16")
+    ws = abi.workspace(n, dtype)
     assert abi.nn_init_precond(A, "scalar", alpha, X0, ws) == abi.NN_OK
     X = torch.empty_like(A)
-    opts = abi.make_opts(depth, tol, 64, "mixed_bf16", x0_scalar=alpha)  # the bench's call
+    opts = abi.make_opts(depth, tol, 64, dtype, x0_scalar=alpha)  # the bench's call
     st, res = abi.nn_invert(A, X0, opts, X, ws)
     torch.cuda.synchronize()
     assert st == abi.NN_OK, res
@@ -78,7 +80,8 @@ def test_mixed_bf16_n8192_kappa1e2_depth2_bench_call():
     assert rel <= 2 * math.sqrt(n) * s_est, rel
 
 
-def test_mixed_bf16_n2048_hinted_equals_oracle_nests():
+@pytest.mark.parametrize("dtype", ["mixed_bf16", "mixed_f16"])
+def test_mixed_n2048_hinted_equals_oracle_nests(dtype):
     import torch
 
     from paper_2212_02406_gb300 import abi, build
@@ -91,8 +94,8 @@ def test_mixed_bf16_n2048_hinted_equals_oracle_nests():
     A = torch.from_numpy(a).cuda()
     X0 = torch.from_numpy(x0).cuda()
     X = torch.empty_like(A)
-    ws = abi.workspace(n, "mixed_bf16")
-    st, res = abi.nn_invert(A, X0, abi.make_opts(depth, tol, 40, "mixed_bf16", x0_scalar=alpha), X, ws)
+    ws = abi.workspace(n, dtype)
+    st, res = abi.nn_invert(A, X0, abi.make_opts(depth, tol, 40, dtype, x0_scalar=alpha), X, ws)
     torch.cuda.synchronize()
     assert st == abi.NN_OK, res
     x = X.cpu().numpy()
