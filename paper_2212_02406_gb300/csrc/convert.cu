@@ -454,8 +454,18 @@ __global__ void row_piece_scale_kernel(const double* __restrict__ src, int64_t l
   const int lane = threadIdx.x & 31;
   if (i >= row1) return;
   double m = 0.0;
-  if (i < n)
-    for (int j = lane; j < n; j += 32) m = fmax(m, fabs(src[int64_t(i) * lds + j]));
+  if (i < n) {
+    // four independent maxima, four loads in flight per lane
+    const double* row = src + int64_t(i) * lds;
+    double m4[4] = {0.0, 0.0, 0.0, 0.0};
+    int j = lane;
+    for (; j + 96 < n; j += 128) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) m4[u] = fmax(m4[u], fabs(row[j + 32 * u]));
+    }
+    for (; j < n; j += 32) m4[0] = fmax(m4[0], fabs(row[j]));
+    m = fmax(fmax(m4[0], m4[1]), fmax(m4[2], m4[3]));
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (lane == 0) {
