@@ -32,10 +32,12 @@ enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD_ARG = 2 };
 
 // One operand piece of x for the tensor cores: its 16-bit pattern, BF16 (half = false) or FP16
 // (half = true), rounded to nearest even, and its value in *val. Piece buffers hold either
-// format; a product reads both operands in the same one.
-__device__ __forceinline__ uint16_t piece_bits(float x, bool half, float* val) {
+// format; a product reads both operands in the same one. r8 (FP16 only): x is first rounded to
+// 8 significant bits (BF16's), for operands whose products need no more: fewer toggling
+// multiplier bits draw less power, which under the power cap keeps the clock up.
+__device__ __forceinline__ uint16_t piece_bits(float x, bool half, float* val, bool r8 = false) {
   if (half) {
-    const __half h = __float2half_rn(x);
+    const __half h = __float2half_rn(r8 ? __bfloat162float(__float2bfloat16_rn(x)) : x);
     *val = __half2float(h);
     return __half_as_ushort(h);
   }

@@ -53,20 +53,21 @@ __device__ __forceinline__ void split_hi_lo(double v, float& hi, float& lo) {
 // The three pieces (bit patterns, BF16 or FP16) of s (hi + lo) (|lo| at most half an FP32 ulp of
 // hi, s a power of two: the scaling is exact); returns hi. Each remainder before a rounding is
 // exact in FP32.
-__device__ __forceinline__ float pieces3_hl(float hi, float lo, float s, bool half, uint16_t (&p)[3]) {
+__device__ __forceinline__ float pieces3_hl(float hi, float lo, float s, bool half, uint16_t (&p)[3],
+                                            bool r8 = false) {
   float v0, v1, v2;
   const float hs = hi * s;
-  p[0] = piece_bits(hs, half, &v0);
+  p[0] = piece_bits(hs, half, &v0, r8);
   const float t = (hs - v0) + lo * s;
   p[1] = piece_bits(t, half, &v1);
   p[2] = piece_bits(t - v1, half, &v2);
   return hi;
 }
 
-__device__ __forceinline__ float pieces3(double v, float s, bool half, uint16_t (&p)[3]) {
+__device__ __forceinline__ float pieces3(double v, float s, bool half, uint16_t (&p)[3], bool r8 = false) {
   float hi, lo;
   split_hi_lo(v, hi, lo);
-  return pieces3_hl(hi, lo, s, half, p);
+  return pieces3_hl(hi, lo, s, half, p, r8);
 }
 
 // The piece scale of padded row i under fmt.
@@ -175,7 +176,7 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
       const float ds = row_piece_scale(dual_fmt, i);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float h = pieces3_hl(vh[e], vl[e], ds, dual_fmt.half, pd[e]);
+        const float h = pieces3_hl(vh[e], vl[e], ds, dual_fmt.half, pd[e], dual_fmt.r8);
         ss_src = fmaf(h, h, ss_src);
       }
       const int64_t off = int64_t(i) * np + jj;
@@ -199,13 +200,13 @@ __global__ void split_kernel(const S* __restrict__ src, int64_t lds, int n, int 
           const bool on = i == jj + e;
           affine_hi_lo(vh[e], vl[e], sh, sl, on ? dh : 0.f, on ? dl : 0.f, h, l);
         }
-        hi[e] = pieces3_hl(h, l, ps, fmt.half, pc[e]);
+        hi[e] = pieces3_hl(h, l, ps, fmt.half, pc[e], fmt.r8);
         ss = fmaf(hi[e], hi[e], ss);
       }
     } else {
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        hi[e] = pieces3(v[e], ps, fmt.half, pc[e]);
+        hi[e] = pieces3(v[e], ps, fmt.half, pc[e], fmt.r8);
         ss = fmaf(hi[e], hi[e], ss);
       }
     }

@@ -105,6 +105,7 @@ struct Params {
   float in_scale;
   const float* in_row;
   float out_scale;
+  int out_r8;
   int cvt_vec;
   // Failure-detection test hook: the MMA issuer withholds the first accumulator-ready signal, so
   // the epilogue's bounded wait runs out (nn_debug_withhold_signal).
@@ -136,7 +137,7 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
 }
 
 __device__ __forceinline__ void store_pieces_row(__nv_bfloat16* const* pieces, int n_pieces, int64_t off,
-                                                 const float (&v)[32], float scale, bool half) {
+                                                 const float (&v)[32], float scale, bool half, bool r8) {
   float rem[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) rem[j] = v[j] * scale;
@@ -145,8 +146,8 @@ __device__ __forceinline__ void store_pieces_row(__nv_bfloat16* const* pieces, i
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       float vlo, vhi;
-      const uint16_t lo = piece_bits(rem[2 * j], half, &vlo);
-      const uint16_t hi = piece_bits(rem[2 * j + 1], half, &vhi);
+      const uint16_t lo = piece_bits(rem[2 * j], half, &vlo, r8);
+      const uint16_t hi = piece_bits(rem[2 * j + 1], half, &vhi, r8);
       rem[2 * j] -= vlo;
       rem[2 * j + 1] -= vhi;
       packed[j] = uint32_t(lo) | (uint32_t(hi) << 16);
@@ -254,7 +255,7 @@ __device__ __forceinline__ void epilogue_chunk(const Params& p, const uint32_t (
 #pragma unroll
     for (int j4 = 0; j4 < 8; ++j4) dst[j4] = make_float4(v[4 * j4], v[4 * j4 + 1], v[4 * j4 + 2], v[4 * j4 + 3]);
   }
-  if (p.n_row > 0) store_pieces_row(p.row_pieces, p.n_row, off, v, p.out_scale, p.half != 0);
+  if (p.n_row > 0) store_pieces_row(p.row_pieces, p.n_row, off, v, p.out_scale, p.half != 0, p.out_r8 != 0);
   if (p.n_col > 0) {
     float rem[32];
 #pragma unroll
@@ -264,7 +265,7 @@ __device__ __forceinline__ void epilogue_chunk(const Params& p, const uint32_t (
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         float b;
-        const uint16_t bits = piece_bits(rem[j], p.half != 0, &b);
+        const uint16_t bits = piece_bits(rem[j], p.half != 0, &b, p.out_r8 != 0);
         rem[j] -= b;
         dst[int64_t(gc0 + j) * ld] = bits;  // lanes write consecutive rows: 64-byte runs
       }
@@ -807,6 +808,7 @@ int gemm_tc(cudaStream_t st, const TcGemmArgs& a, int* grid_used) {
   p.in_scale = a.in_scale;
   p.in_row = a.in_row;
   p.out_scale = a.out_scale;
+  p.out_r8 = a.out_r8 ? 1 : 0;
   p.withhold = tc_take_withhold();
   // Variant choice: the 2-SM MMA with a split last wave by default where the size allows it, else
   // single-CTA tiles.

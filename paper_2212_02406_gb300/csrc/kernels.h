@@ -81,6 +81,7 @@ struct TcGemmArgs {
   float in_scale = 1.0f;
   const float* in_row = nullptr;
   float out_scale = 1.0f;
+  bool out_r8 = false;  // FP16 pieces written at 8 significant bits (piece_bits)
   // Optional events recorded on the stream immediately before and after the kernel launch (after
   // the host has prepared it), so that their interval is the kernel's device time.
   cudaEvent_t ev_before = nullptr, ev_after = nullptr;
@@ -118,6 +119,7 @@ struct PieceFmt {
   bool half = false;
   float scale = 1.0f;
   const float* row_scale = nullptr;
+  bool r8 = false;  // FP16 pieces at 8 significant bits (piece_bits)
 };
 // Splits an n x n FP64 matrix (leading dim lds) into an Np-padded FP32 copy and BF16
 // pieces (row-major and/or transposed). Any output may be null. Padding is zero.

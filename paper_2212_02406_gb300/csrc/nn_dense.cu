@@ -594,7 +594,11 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
   int level = initial_level(o);
   const int r0_pre_hp = level_t_pieces(level);
   // FP16 pieces: the piece scale of each X buffer (set when its pieces are written), R and T at
-  // kPieceRT, A per row (w.a_scale)
+  // kPieceRT, A per row (w.a_scale). R and T in one piece (levels 1-3) are written at 8
+  // significant bits, as BF16 pieces would be: the Horner product R T_j is second order in the
+  // residual and T's rounding reaches the next residual unamplified (about 2^-9 s_k), while X
+  // and A, whose rounding the residual and the update amplify, keep all 11 bits. Products with
+  // 8-bit operands draw less power at the cap.
   const bool half = w.half;
   const float rt_scale = half ? kPieceRT : 1.0f;
   float xs[2] = {half ? x0src.scale : 1.0f, 1.0f};
@@ -663,6 +667,7 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
     }
     NN_TRY(ensure_pieces(cur, 0, level_res_pieces(L)));
     set_half(g, 1.0f / xs[cur], w.a_rinv, rt_scale);
+    g.out_r8 = half && hp == 1;
     int grid = 0;
     NN_TRY(tc_product(st, g, level_res_pieces(L), level_res_pieces(L), w.a_row, w.x_col[cur], cm, res, &grid,
                       &timer));
@@ -683,8 +688,10 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       NN_TRY(reduce_rms(st, w.split_partial2, sb, 1.0 / double(n), cm.scal));
       res->launches += 1;
     } else {
+      PieceFmt f0 = rt_fmt;
+      f0.r8 = half && hp == 1;
       NN_TRY(split_matrix_affine(st, A, lda, n, np, rows ? w.r32 : nullptr, w.r_row, rows ? hp : 0, w.r_col, hp,
-                                 w.split_partial, -alpha, 1.0, rt_fmt));
+                                 w.split_partial, -alpha, 1.0, f0));
       NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0 / double(n), cm.scal));
       res->launches += 2;
     }
@@ -883,12 +890,14 @@ int run_mixed(cudaStream_t st, int n, const double* A, int64_t lda, const MixedW
       g.n_col = ht;
       for (int i = 0; i < 3; ++i) g.col_pieces[i] = w.t_col[j & 1][i];
       set_half(g, 1.0f / (rt_scale * rt_scale), nullptr, rt_scale);
+      g.out_r8 = half && ht == 1;
       int grid = 0;
       if (update0 && j == nest_depth(o, k) - 1) {
         // the first nest's last Horner product writes X_1 = alpha (I + T) straight from its
         // epilogue (FP32 master, row and column pieces, ||X_1||_F): no T, no separate pass
         xs[cur ^ 1] = xs_next;
         g.out_scale = half ? xs_next : 1.0f;
+        g.out_r8 = false;  // X keeps every FP16 bit
         g.affine = true;
         g.aff_scale = float(alpha);
         g.aff_diag = float(alpha);
@@ -999,6 +1008,7 @@ int split_a_panels(cudaStream_t st, const double* A, int64_t lda, int n, const M
   if (o.x0_scalar > 0) {
     const int hp = level_t_pieces(initial_level(o));
     const bool rows = max_depth(o) >= 2;
+    fr.r8 = w.half && hp == 1;  // R_0 in one piece: 8 significant bits (see run_mixed)
     return split_matrix_dual(st, A, lda, n, w.np, w.a_row, w.split_partial, rows ? w.r32 : nullptr, w.r_row,
                              rows ? hp : 0, w.r_col, hp, w.split_partial2, -o.x0_scalar, 1.0, row0, row1, fr, fa);
   }
