@@ -58,13 +58,14 @@ def test_result_struct_matches_header(lib):
 def test_workspace_sizes(lib):
     assert abi.nn_workspace_bytes(0, "f64") == 0
     assert abi.nn_workspace_bytes(16, 99) == 0
-    for dt in ("f64", "f32", "mixed_bf16"):
+    for dt in ("f64", "f32", "mixed_bf16", "mixed_f16"):
         a = abi.nn_workspace_bytes(100, dt)
         b = abi.nn_workspace_bytes(1000, dt)
         assert 0 < a < b
         assert abi.nn_workspace_bytes_host(1000, dt) >= b + 3 * 1000 * 1000 * 8
-    # the mixed path pads to multiples of 128
+    # the mixed path pads to multiples of 128; FP16 and BF16 pieces share one layout
     assert abi.nn_workspace_bytes(129, "mixed_bf16") == abi.nn_workspace_bytes(256, "mixed_bf16")
+    assert abi.nn_workspace_bytes(1000, "mixed_f16") == abi.nn_workspace_bytes(1000, "mixed_bf16")
 
 
 def test_argument_errors_are_status_codes(lib):
@@ -175,3 +176,19 @@ def test_batched_plan_layout(lib, cfg_by_u):
     assert mask == sum(1 << c for c in range(ncls) if class_first[c + 1] > class_first[c])
     if cfg_by_u and cfg_by_u.get(64) == 2:
         assert n_tc > 0 and all(int(items[i, 0]) in (48, 64) for i in range(n_tc))
+
+
+def test_dtype_constants_match_header():
+    # the binding's dtype numbers are the header's enum values
+    import os
+    import re
+
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "nn.h")).read()
+    block = hdr[hdr.index("typedef enum nn_dtype"):]
+    block = block[:block.index("} nn_dtype;")]
+    block = re.sub(r"/\*.*?\*/", "", block, flags=re.S)
+    values = {name: int(v) for name, v in re.findall(r"(NN_\w+)\s*=\s*(\d+)", block)}
+    assert values["NN_MIXED_F16"] == abi.NN_MIXED_F16 == abi.DTYPES["mixed_f16"]
+    for name, key in (("NN_F64", "f64"), ("NN_F32", "f32"), ("NN_MIXED_BF16", "mixed_bf16"),
+                      ("NN_F64_DF", "f64_df"), ("NN_F64_EMU", "f64_emu"), ("NN_MIXED_EMU", "mixed_emu")):
+        assert values[name] == abi.DTYPES[key], name
