@@ -72,12 +72,13 @@ def test_normal_solve_badly_conditioned_matches_library(nn):
     assert err <= 64 * cond ** 2 * U64 + n * res["residual"]
 
 
-def test_normal_solve_mixed_precision_runs_to_its_floor(nn):
-    # the mixed BF16 chain on W (cond(W) = 100): converges to tol 1e-5 and solves to about n tol
+@pytest.mark.parametrize("dtype", ["mixed_bf16", "mixed_f16"])
+def test_normal_solve_mixed_precision_runs_to_its_floor(nn, dtype):
+    # the mixed chains on W (cond(W) = 100): converge to tol 1e-5 and solve to about n tol
     n, cond = 256, 10.0
     a, _ = synth.general_svd(n, cond, seed=41)
     b = synth.gaussian_rhs(n, 1, seed=42)
-    st, res, x = _solve(nn, a, b, 2, 1e-5, 40, dtype="mixed_bf16")
+    st, res, x = _solve(nn, a, b, 2, 1e-5, 40, dtype=dtype)
     assert st == nn.NN_OK and res["residual"] < 1e-5
     true = np.linalg.solve(a, b)
     assert np.linalg.norm(x - true) / np.linalg.norm(true) <= n * 2e-5
