@@ -99,9 +99,9 @@ typedef struct nn_opts {
   double tol;          /* stop at the first k with s_k < tol; tol <= 0 runs exactly max_nests     */
   int max_nests;       /* 0 .. NN_MAX_HISTORY-1                                                   */
   int dtype;           /* nn_dtype                                                                */
-  double refine_below; /* NN_MIXED_BF16: also use level-3 residuals once s_k * sqrt(N) < refine_below
+  double refine_below; /* NN_MIXED_BF16 / NN_MIXED_F16: also use level-3 residuals once s_k * sqrt(N) < refine_below
                           (<= 0: off; the floor-based level schedule alone decides)             */
-  int bulk_pieces;     /* NN_MIXED_BF16: starting precision level 1..4 (0 = 1): the BF16 pieces of
+  int bulk_pieces;     /* NN_MIXED_BF16 / NN_MIXED_F16: starting precision level 1..4 (0 = 1): the pieces of
                           the first residuals (1, 2, 3, 3) and updates (1, 2, 2, 3); the chain
                           raises the level itself as the residual nears each level's floor     */
   int flags;           /* NN_FLAG_* bits                                                           */
@@ -112,7 +112,7 @@ typedef struct nn_opts {
                           L_0..L_{k-1} X_k is the Neumann series of order prod(L_j + 1) - 1    */
   int schedule_len;    /* entries of depth_schedule, 0 .. NN_MAX_HISTORY (0: every nest `depth`) */
   double x0_scalar;    /* > 0: the caller asserts X_0 = x0_scalar * I (X0 must still be passed).
-                          NN_MIXED_BF16 / NN_MIXED_EMU then run the first nest's residual
+                          NN_MIXED_BF16 / NN_MIXED_F16 / NN_MIXED_EMU then run the first nest's residual
                           R_0 = I - x0_scalar A and update X_1 = x0_scalar (I + T) element-wise
                           (no GEMM, no pieces of X_0); the other dtypes read X0 as usual.
                           nn_result.flops then leaves those two products out. */
@@ -134,7 +134,7 @@ typedef struct nn_result {
   int nests;                       /* nests applied; the returned X is X_nests                     */
   double residual;                 /* s_nests, the last residual measured                          */
   double history[NN_MAX_HISTORY];  /* s_0 .. s_nests                                               */
-  int pieces[NN_MAX_HISTORY];      /* BF16 pieces used for residual k (0 for FP64/FP32 paths)      */
+  int pieces[NN_MAX_HISTORY];      /* operand pieces used for residual k (0 for FP64/FP32 paths)   */
   int gemms;                       /* GEMM launches issued                                         */
   double flops;                    /* algorithmic FLOPs: 2 N^3 per product of the method that ran as a
                                       GEMM ((L+1) per nest + the final residual, less products run
@@ -142,13 +142,13 @@ typedef struct nn_result {
                                       not counted                                                  */
   double hw_flops;                 /* tensor-core FLOPs issued, split passes included              */
   int launches;                    /* kernel launches issued by the call                           */
-  int tc_launches;                 /* GEMM launches of the chain: tcgen05 for NN_MIXED_BF16,       */
+  int tc_launches;                 /* GEMM launches of the chain: tcgen05 for the mixed dtypes,    */
                                    /* CUDA-core for NN_F64 / NN_F32                                */
   double tc_ms;                    /* summed CUDA-event time of those launches (NN_FLAG_TIME_KERNELS) */
-  double tc_flops;                 /* 2 Np^3 per BF16 product pass (mixed) or 2 N^3 per GEMM (F64/F32) */
+  double tc_flops;                 /* 2 Np^3 per piece product pass (mixed) or 2 N^3 per GEMM (F64/F32) */
   double residual_est;             /* the residual the returned X has, as certified by the stop test:
                                       equal to `residual` for FP64, FP32 and emulated residuals; for
-                                      BF16-piece residuals sqrt(residual^2 + e^2), e the error floor
+                                      piece residuals (mixed dtypes) sqrt(residual^2 + e^2), e the error floor
                                       of the residual that produced X (the pieces' rounding and the
                                       tensor core's FP32 accumulation: the chain converges to the X
                                       whose measured residual vanishes, so the measured value lies
@@ -156,7 +156,7 @@ typedef struct nn_result {
                                       a tol under the arithmetic's floor ends NN_ERR_NOT_CONVERGED */
 } nn_result;
 
-/* Tensor-core GEMM tiling for the NN_MIXED_BF16 chain (a process-wide tuning knob; the
+/* Tensor-core GEMM tiling for the mixed chains (a process-wide tuning knob; the
  * element-wise outputs of every variant are bitwise identical, only the per-CTA grouping of the
  * residual's sum of squares differs): 0 = automatic (variant 4 when the padded size is a
  * multiple of 256, else 1), 1 = single-CTA 128 x 256 tiles, 3 = CTA pairs issuing one
@@ -205,7 +205,7 @@ int nn_invert(const double* A, int64_t n, int64_t lda, const double* X0, int64_t
 /* Same as nn_invert with HOST buffers: A, X0 and X are host FP64 arrays (leading dimension
  * n; page-locked memory lets the copies run at full speed). The call copies A and X0 to the
  * device, runs, and copies X back, and returns after X is in host memory. For NN_MIXED_BF16
- * with tol > 0, the nest predicted to be the last has its iterate converted and copied back on
+ * and NN_MIXED_F16 with tol > 0, the nest predicted to be the last has its iterate converted and copied back on
  * a side stream while the confirming residual runs; when the residual confirms the stop that
  * copy is the result (otherwise X is copied after the run). Needs
  * nn_workspace_bytes_host(n, dtype) of device workspace. */
@@ -438,8 +438,9 @@ typedef struct nn_request {
   const double* B;
   double* Y;
   double* X;
-  int dtype;            /* NN_F64, NN_F32, NN_MIXED_BF16 or NN_MIXED_EMU (BF16-piece nests, then
-                           emulated FP64 nests where tol lies under what the pieces certify)   */
+  int dtype;            /* NN_F64, NN_F32, NN_MIXED_BF16, NN_MIXED_F16 or NN_MIXED_EMU (BF16-piece
+                           nests, then emulated FP64 nests where tol lies under what the pieces
+                           certify)                                                            */
   int precond;          /* nn_pc                                                               */
   double pc_scalar;
 } nn_request;
