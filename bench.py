@@ -440,31 +440,62 @@ def run_dense(args, rank, world, local_rank):
                                               ((n + 127) // 128) * 128) ** 3), 3),
                                           "note": "tensor work of every piece pass (2 Np^3 each) over the same time"}}
 
-    # e2e: the host-buffer C-ABI call, H2D of A and X_0 and D2H of X inside the timed region
+    # e2e: the host-buffer C-ABI call, H2D of A and D2H of X inside the timed region. Two host
+    # threads keep two calls in flight (each its own stream, workspace and output buffer), so one
+    # inversion's copies overlap the other's chain; the latency of one call at a time is
+    # reported beside it.
     e2e = None
     if not args.no_e2e:
+        import threading
+
         # the user's call for this workload: host A in, X_0 = alpha I built on the device, host X out
         a_pin = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
-        x_pin = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
         a_pin.copy_(A)
+        x_pins = [torch.empty((n, n), dtype=torch.float64, pin_memory=True) for _ in range(2)]
         del ws
         torch.cuda.empty_cache()
-        wsh = abi.workspace(n, args.dtype, host=True, device=dev)
-        an, xn = a_pin.numpy(), x_pin.numpy()
+        wsh = [abi.workspace(n, args.dtype, host=True, device=dev) for _ in range(2)]
+        e_streams = [torch.cuda.Stream(dev) for _ in range(2)]
+        an, xns = a_pin.numpy(), [x.numpy() for x in x_pins]
         opts_e = abi.make_opts(args.depth, args.tol, 64, args.dtype)
-        st, _ = abi.nn_invert_host_pc(an, "scalar", alpha, opts_e, xn, wsh, stream)  # warm
+
+        def call(i):
+            return abi.nn_invert_host_pc(an, "scalar", alpha, opts_e, xns[i], wsh[i], e_streams[i])
+
+        for i in range(2):
+            call(i)  # warm
+        k_lat = max(1, min(args.steps, 3))
         barrier()
         t0 = time.perf_counter()
-        k_e2e = max(1, min(args.steps, 3))
-        for _ in range(k_e2e):
-            st, r = abi.nn_invert_host_pc(an, "scalar", alpha, opts_e, xn, wsh, stream)
+        for _ in range(k_lat):
+            st, r = call(0)
         barrier()
-        te = (time.perf_counter() - t0) / k_e2e
+        lat = (time.perf_counter() - t0) / k_lat
+        statuses = [st]
+        per_thread = max(1, min(args.steps, 3))
+
+        def worker(i):
+            for _ in range(per_thread):
+                s_i, _ = call(i)
+                statuses.append(s_i)
+
+        threads = [threading.Thread(target=worker, args=(i,)) for i in range(2)]
+        barrier()
+        t0 = time.perf_counter()
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        barrier()
+        te = (time.perf_counter() - t0) / (2 * per_thread)
         e2e = {"value": round(r["flops"] * world / te / 1e12, 3), "unit": "TFLOP/s",
                "ms_per_step": round(te * 1e3, 3), "h2d_bytes_per_step": n * n * 8,
-               "d2h_bytes_per_step": n * n * 8, "steps": k_e2e, "ok": st == abi.NN_OK,
+               "d2h_bytes_per_step": n * n * 8, "steps": 2 * per_thread,
+               "ok": all(x == abi.NN_OK for x in statuses),
+               "latency_ms": round(lat * 1e3, 3), "in_flight": 2,
                "call": "nn_invert_host_pc (X_0 = alpha I built on the device; the likely-final iterate "
-                       "copied back while its residual runs)"}
+                       "copied back while its residual runs), two calls in flight from two host threads "
+                       "(own streams, workspaces and output buffers); latency_ms: one call at a time"}
         del wsh
 
     # Independent FP64 check of the returned X on sampled rows of R = I - A X (host).
@@ -957,28 +988,30 @@ def run_batched(args, rank, world, local_rank):
         g.replay()
         torch.cuda.synchronize(dev)
     # end to end through the public call: per step the batch's A from pinned host memory, the
-    # call, and X, residual and status back to pinned host memory; steps alternate between two
-    # streams with their own device buffers, so one step's copies overlap the other's kernels
+    # call, and X, residual and status back to pinned host memory; steps rotate over three
+    # streams with their own device buffers, so one step's A copy, another's kernels and a third's
+    # X copy run at once (the two copy directions and the kernels are separate engines)
     e2e = None
     if not args.no_e2e and world == 1:
+        nb = 3
         A_h = torch.from_numpy(bt.data).pin_memory()
-        X_h = [torch.empty_like(A_h).pin_memory() for _ in range(2)]
-        res_h = [torch.empty(count, dtype=torch.float32).pin_memory() for _ in range(2)]
-        st_h = [torch.empty(count, dtype=torch.int32).pin_memory() for _ in range(2)]
+        X_h = [torch.empty_like(A_h).pin_memory() for _ in range(nb)]
+        res_h = [torch.empty(count, dtype=torch.float32).pin_memory() for _ in range(nb)]
+        st_h = [torch.empty(count, dtype=torch.int32).pin_memory() for _ in range(nb)]
         bufs = [(A, X, res, st, ws)] + [(torch.empty_like(A), torch.empty_like(X), torch.empty_like(res),
-                                         torch.empty_like(st), torch.empty_like(ws))]
-        streams = [torch.cuda.Stream(dev) for _ in range(2)]
-        e_steps = 20
+                                         torch.empty_like(st), torch.empty_like(ws)) for _ in range(nb - 1)]
+        streams = [torch.cuda.Stream(dev) for _ in range(nb)]
+        e_steps = 21
 
         def e2e_step(k):
-            a_d, x_d, r_d, s_d, w_d = bufs[k % 2]
-            with torch.cuda.stream(streams[k % 2]):
+            a_d, x_d, r_d, s_d, w_d = bufs[k % nb]
+            with torch.cuda.stream(streams[k % nb]):
                 a_d.copy_(A_h, non_blocking=True)
                 assert abi.nn_invert_batched_c64(a_d, offs, sizes, plan, depth, nests, damping, x_d, r_d, s_d, w_d,
                                                  classes=classes) == 0
-                X_h[k % 2].copy_(x_d, non_blocking=True)
-                res_h[k % 2].copy_(r_d, non_blocking=True)
-                st_h[k % 2].copy_(s_d, non_blocking=True)
+                X_h[k % nb].copy_(x_d, non_blocking=True)
+                res_h[k % nb].copy_(r_d, non_blocking=True)
+                st_h[k % nb].copy_(s_d, non_blocking=True)
 
         for k in range(4):
             e2e_step(k)
@@ -993,7 +1026,7 @@ def run_batched(args, rank, world, local_rank):
                "d2h_bytes_per_step": int(X_h[0].numel() * X_h[0].element_size() + 4 * count + 4 * count),
                "steps": e_steps, "ok": bool(all(np.all(s.numpy() == 0) for s in st_h)),
                "call": "nn_invert_batched_c64 (A in, X, residual and status out, pinned host buffers; steps "
-                       "alternate between two streams, wall clock between two device synchronisations)"}
+                       "rotate over three streams, wall clock between two device synchronisations)"}
     # the CPU oracle as it stands (complex128 loop) on a bounded sample of the same batch
     cpu = None
     if not args.no_cpu and rank == 0:
