@@ -150,7 +150,7 @@ def test_disarmed_hook_changes_nothing(nn):
 
 @pytest.mark.parametrize("bad", [np.nan, np.inf])
 @pytest.mark.parametrize("dtype,hint", [("f64", False), ("f32", False), ("mixed_bf16", False), ("mixed_bf16", True),
-                                        ("mixed_emu", True)])
+                                        ("mixed_f16", False), ("mixed_f16", True), ("mixed_emu", True)])
 def test_non_finite_matrix_diverges(nn, bad, dtype, hint):
     n = 200
     a, q, lam = synth.spd_spectrum(n, 1e2, seed=9)
@@ -168,7 +168,7 @@ def test_non_finite_start_diverges(nn):
     a, q, lam = synth.spd_spectrum(n, 1e2, seed=10)
     x0 = dense.precond_scalar(n, 2.0 / (lam[0] + lam[-1]))
     x0[3, 3] = np.nan
-    for dtype in ("f64", "mixed_bf16"):
+    for dtype in ("f64", "mixed_bf16", "mixed_f16"):
         st, res, _ = _invert(nn, a, x0, dtype)
         assert st == nn.NN_ERR_DIVERGED, (dtype, res)
 
