@@ -409,7 +409,7 @@ int nn_invert_batched(const void* A, const int64_t* offsets, const int32_t* size
  * options, arithmetic `dtype`) and, if nrhs > 0, solves Y = X B for B (host FP64, row-major
  * N x nrhs). X (host, N x N) and Y (host, N x nrhs) receive the results when not NULL. Host
  * buffers must stay valid until the request's completion is polled; pinned memory gives
- * asynchronous copies. This is the serving form of the spec workload; the paper itself
+ * asynchronous copies. This is a serving form of the dense inversion; the paper itself
  * describes single inversions (Algorithm 1) and linear solves (Corollary 3).
  *
  * The server allocates no device memory: `arena` (device, arena_bytes) is the HBM budget
