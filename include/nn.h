@@ -74,7 +74,7 @@ typedef enum nn_dtype {
                         longer and certifies a tol with fewer passes. FP16's range is kept by
                         exact power-of-two scales: every row of A by its own (largest entry
                         to [2^13, 2^14)), X_k by one from ||X_k||_F, R and T by 2^12. The
-                        entries of R_k and T must stay below 16 in magnitude, which holds
+                        entries of R_k and T must stay below 15.97 in magnitude, which holds
                         under the convergence condition ||I - A X_0||_2 < 1 (Theorem); beyond
                         it the pieces overflow, s_k turns non-finite and the call returns
                         NN_ERR_DIVERGED                                                       */
