@@ -66,6 +66,30 @@ def test_one_fp16_piece_rms_error_matches_the_floor_constant():
     assert abs(np.log2(rel_bf / rel16) - 3.0) < 0.05
 
 
+def test_two_piece_floor_constants():
+    # Two pieces per operand, products A0 X0 + A0 X1 + A1 X0: the error is A1 X1 (the product of
+    # the two one-piece roundings) plus each operand's two-piece remainder carried through the
+    # product, three independent terms: sqrt(2 r2^2 + r1^4) in units of c, with r1, r2 the rms
+    # relative remainders after one and two pieces. Pinned against the constants the schedule
+    # uses: 0x1.15p-18 for BF16 (2^-17.9, measured on the GPU) and 0x1.15p-24 for FP16.
+    # (values in [1, 2^14): the range the scales give the operands, where the second FP16 piece
+    # is a normal number)
+    r = synth.rng(13)
+    x = (r.uniform(1.0, 2.0, size=400000) * np.exp2(r.integers(0, 14, size=400000))).astype(np.float32)
+    for rnd, const in ((_bf16, "0x1.15p-18"), (_f16, "0x1.15p-24")):
+        p0 = rnd(x)
+        rem1 = (x - p0).astype(np.float32)
+        p1 = rnd(rem1)
+        rem2 = (rem1 - p1).astype(np.float32)
+        r1 = np.sqrt(np.mean((rem1 / x) ** 2))
+        r2 = np.sqrt(np.mean((rem2 / x) ** 2))
+        model = np.sqrt(2.0 * r2 ** 2 + r1 ** 4)
+        # within 0.2 in log2: an FP32 value's two FP16 pieces leave only its last two bits, so
+        # the model's FP16 remainder sits a little above the BF16 constant times 2^-6 (2^-23.7
+        # against 2^-23.9); at level 2 the accumulation floor dominates that term anyway
+        assert abs(np.log2(model) - np.log2(float.fromhex(const))) < 0.2, (const, np.log2(model))
+
+
 def test_scaled_pieces_are_finite_and_exact_to_their_width():
     # a matrix with rows over 2^80 of range: after the row scales no piece overflows, two
     # pieces hold each FP32 value to 2^-22 of its row's largest entry, three to 2^-33
