@@ -1091,8 +1091,12 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
     const int sb = split_blocks(w.np);
     // with X_0 = alpha I the same pass over A also writes R_0 = I - alpha A for the first residual
     const bool r0_pre = o.x0_scalar > 0;
-    if (!a_presplit) NN_TRY(split_a_panels(st, A, lda, ni, w, o, 0, -1));
+    if (!a_presplit) {
+      NN_TRY(split_a_panels(st, A, lda, ni, w, o, 0, -1));
+      res->launches += w.half ? 2 : 1;  // FP16: the row scales' pass, then the split
+    }
     NN_TRY(reduce_rms(st, w.split_partial, sb, 1.0, cm.scal + 2));
+    res->launches += 1;
     X0Source x0src{X0, ldx0};
     if (o.x0_scalar <= 0) {  // a scalar X_0 needs no pieces
       if (w.half) {
@@ -1105,11 +1109,11 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
         res->launches += 2;
       }
       NN_TRY(load_x0(st, ni, w, cm, x0src));
+      res->launches += 2;
     }
     double a_frob = 0;
     NN_CUDA_TRY(cudaMemcpyAsync(&a_frob, cm.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
     NN_CUDA_TRY(cudaStreamSynchronize(st));
-    res->launches += 4;
     // X written before the run ends must not be read by it (X overlapping A or X_0: no early copy)
     auto span = [&](const double* p, int64_t ld) {
       return std::make_pair(reinterpret_cast<uintptr_t>(p),
@@ -1153,15 +1157,15 @@ int invert_device(const double* A, int64_t n, int64_t lda, const double* X0, int
       res->residual_est = r2.residual_est;
       res->status = r2.status;
       res->gemms += r2.gemms;
-      res->launches += r2.launches + 1;
+      res->launches += r2.launches + 2;  // with the widening before and the copy after
       res->tc_launches += r2.tc_launches;
       res->tc_ms += r2.tc_ms;
       res->tc_flops += r2.tc_flops;
       NN_TRY(copy_f64(st, w64.X[fin2], n, ni, X, ldx));
     } else if (ho != nullptr ? !ho->valid : !(dout.buf == fin && dout.nests == res->nests)) {
       NN_TRY(f32_to_f64(st, w.x32[fin], w.np, ni, X, ldx));
+      res->launches += 1;
     }
-    res->launches += 3;
   }
   // Algorithmic work of the method: (L+1) GEMMs per nest plus the final residual, less the
   // products that ran element-wise (X_0 = alpha I on the mixed chains: the first nest's residual
@@ -1300,7 +1304,7 @@ int invert_host_impl(const double* A_host, int64_t n, const double* X0_host, int
                              cudaMemcpyHostToDevice, cs) == cudaSuccess;
       ok = ok && cudaEventRecord(ev[p], cs) == cudaSuccess && cudaStreamWaitEvent(st, ev[p], 0) == cudaSuccess;
       ok = ok && split_a_panels(st, dA, n, int(n), ww, oh, r0, r1) == NN_OK;
-      res->launches += 1;
+      res->launches += ww.half ? 2 : 1;
       if (r1 == ww.np) break;
     }
     // On failure, queued copies and splits may still read the caller's A and write the
